@@ -1,0 +1,204 @@
+/*
+ * mdsip -- mixed dense-sparse interior-point Newton step on one GB300 GPU.
+ *
+ * C ABI.  Plain pointers and sizes only.  Every call returns an mdsip_status
+ * (no exceptions cross the ABI); the text of the last error of a context is
+ * available from mdsip_ctx_last_error().  One context per host thread.
+ *
+ * Problem class (Section 2, Eqs. (obj)-(bounds)): variables x = [x_s; x_d]
+ * (n = n_s + n_d), equalities g(x) = g_E (m_E), inequalities h^l <= h(x) <= h^u
+ * (m_I), bounds x^l <= x <= x^u; infinite bounds are +-HUGE_VAL.  Every h_i
+ * has at least one finite bound.  Assumptions A1/A2 of Section 2: no cross
+ * Hessian between x_d and x_s, and the x_s Hessian block is diagonal.
+ *
+ * Memory: arguments tagged `mem` are host pointers when mem == MDSIP_MEM_HOST
+ * and device pointers (on the context's device) when mem == MDSIP_MEM_DEVICE.
+ * Pointers passed in are borrowed for the duration of the call only; the
+ * library copies what it keeps.  All device work is ordered on the context's
+ * stream.
+ */
+#ifndef MDSIP_H
+#define MDSIP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MDSIP_OK = 0,
+    MDSIP_ERR_INVALID_ARG = 1,      /* bad size, null pointer, unknown option      */
+    MDSIP_ERR_CUDA = 2,             /* a CUDA runtime call failed                  */
+    MDSIP_ERR_OOM = 3,              /* device allocation failed                    */
+    MDSIP_ERR_CALLBACK = 4,         /* a user callback returned nonzero            */
+    MDSIP_ERR_NONFINITE = 5,        /* NaN/Inf in a model value or residual        */
+    MDSIP_ERR_INERTIA = 6,          /* inertia correction exceeded dw_max (Sec 2.1)*/
+    MDSIP_RESTORATION_NEEDED = 7,   /* line search reached alpha_min               */
+    MDSIP_MAX_ITER = 8,             /* iteration limit reached                     */
+    MDSIP_TIMEOUT = 9,              /* host wall-clock limit reached               */
+    MDSIP_ERR_PRECONDITION = 10,    /* path P2 forced but its precondition fails   */
+    MDSIP_ERR_DEVICE = 11           /* a device-side bounded wait expired          */
+} mdsip_status;
+
+enum { MDSIP_MEM_HOST = 0, MDSIP_MEM_DEVICE = 1 };
+
+/* Linear-algebra path of the Newton step (option "path"):
+ *   P1: dense compressed matrix of Eq. (compressed), size n_d + m;
+ *   P2: two-stage elimination to size n_d + m_I (requires J_sh = 0 and rows of
+ *       J_sg with disjoint column supports, so that J_sg Q_s^-1 J_sg^T is diagonal);
+ *   AUTO: P2 when applicable, else P1. */
+enum { MDSIP_PATH_AUTO = 0, MDSIP_PATH_P1 = 1, MDSIP_PATH_P2 = 2 };
+
+typedef struct mdsip_ctx mdsip_ctx;
+typedef struct mdsip_problem mdsip_problem;
+
+/* Optional device-allocation hooks (nullable).  alloc returns a device pointer
+ * or NULL (reported as MDSIP_ERR_OOM); free releases it. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *user);
+    void *user;
+} mdsip_alloc_hooks;
+
+/* Create a context on `device` ordering its work on `stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  `hooks` may be NULL (cudaMalloc/cudaFree). */
+mdsip_status mdsip_ctx_create(int device, void *stream, const mdsip_alloc_hooks *hooks,
+                              mdsip_ctx **out);
+void mdsip_ctx_destroy(mdsip_ctx *ctx);
+const char *mdsip_ctx_last_error(const mdsip_ctx *ctx);
+const char *mdsip_status_str(mdsip_status s);
+
+/* ------------------------------------------------------------------------- */
+/* Problem: the MDS model family of the benchmark (Section 2 problem class).  */
+/*                                                                            */
+/*   f(x)  = 1/2 x_d^T Q x_d + sum_i 1/4 x_s,i^4 + c^T x                      */
+/*   g(x)  = J_sg x_s + A x_d                (equalities g(x) = g_E)          */
+/*   h_j(x)= sum_{k : h_set[k] == j} x_d,k^2  (h^l <= h <= h^u)                */
+/*                                                                            */
+/* A = J_{x_d} g is dense (m_E x n_d, row-major, Section 3.2.3 container      */
+/* blocks (3,1)/(3,2)); J_sg is given as COO triplets (Section 3.2.3: triplet  */
+/* storage), converted once to CSR/CSC on the device.  J_sh = 0.              */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int64_t n_d, n_s, m_E, m_I;
+    int64_t nnz_Jsg;
+    const double *Q;          /* n_d * n_d, row-major, symmetric                 */
+    const double *c;          /* n_s + n_d                                       */
+    const double *A;          /* m_E * n_d, row-major                            */
+    const double *gE;         /* m_E                                             */
+    const int32_t *Jsg_rows;  /* nnz_Jsg, in [0, m_E)                            */
+    const int32_t *Jsg_cols;  /* nnz_Jsg, in [0, n_s)                            */
+    const double *Jsg_vals;   /* nnz_Jsg                                         */
+    const int32_t *h_set;     /* n_d: inequality index of x_d,k or -1            */
+    const double *hl, *hu;    /* m_I                                             */
+    const double *xl, *xu;    /* n_s + n_d                                       */
+    const double *x0;         /* n_s + n_d starting point (nullable: zeros)      */
+} mdsip_synth_data;
+
+/* Copy the data to the device and build the sparse indices.  `mem` tags all
+ * pointers of `data`.  Errors: INVALID_ARG (sizes, indices out of range,
+ * inconsistent bounds), OOM, CUDA. */
+mdsip_status mdsip_problem_create_synthetic(mdsip_ctx *ctx, const mdsip_synth_data *data, int mem,
+                                            mdsip_problem **out);
+void mdsip_problem_destroy(mdsip_problem *p);
+
+/* Options (Section 2.1 method constants; names as in the oracle):
+ *   int:    max_iter, path, max_ls, refine_max
+ *   double: tol, mu0, kappa_eps, kappa_mu, theta_mu, tau_min, s_max, kappa_1,
+ *           kappa_2, kappa_sigma, gamma_theta, gamma_phi, delta, s_theta, s_phi,
+ *           eta_phi, gamma_alpha, dw0, dw_min, dw_max, kw_minus, kw_plus,
+ *           kw_plus_bar, dc_bar, kappa_c, zero_tol, time_limit_s
+ * Unknown names: INVALID_ARG. */
+mdsip_status mdsip_set_option_int(mdsip_problem *p, const char *name, int64_t value);
+mdsip_status mdsip_set_option_double(mdsip_problem *p, const char *name, double value);
+
+/* Packed primal-dual layout used by set_start / get_iterate / debug_direction:
+ *   [x (n) | d (m_I) | y_g (m_E) | y_h (m_I) | z_l (n) | z_u (n) | v_l (m_I) | v_u (m_I)]
+ * Multipliers of infinite bounds are 0. */
+int64_t mdsip_packed_size(const mdsip_problem *p);
+
+/* Warm start: use `packed` as the starting primal-dual point and mu0 (<= 0:
+ * the option mu0).  The point must be strictly inside the finite bounds. */
+mdsip_status mdsip_set_start(mdsip_problem *p, const double *packed, double mu0, int mem);
+
+/* Run the filter line-search interior-point method (Section 2.1) to E_0 <= tol.
+ * Returns the final status (OK, MAX_ITER, INERTIA, RESTORATION_NEEDED,
+ * NONFINITE, TIMEOUT, or an error). */
+mdsip_status mdsip_solve(mdsip_problem *p);
+
+mdsip_status mdsip_get_iterate(mdsip_problem *p, double *packed, int mem);
+
+typedef struct {
+    int32_t status;
+    int32_t iters;
+    int32_t path;              /* MDSIP_PATH_P1 or MDSIP_PATH_P2 as used           */
+    int32_t n_factorizations;  /* LDL^T factorizations (incl. inertia retries)     */
+    int64_t n_ls_trials;
+    double f, E0, inf_pr, inf_du, mu;
+    double t_total_ms;
+    double t_condense_ms, t_factor_ms, t_solve_ms, t_ls_ms;  /* CUDA-event phase times */
+} mdsip_stats;
+mdsip_status mdsip_get_stats(mdsip_problem *p, mdsip_stats *out);
+
+#define MDSIP_MAX_IC 16
+typedef struct {
+    int32_t iter;
+    int32_t n_ic;                       /* inertia-correction attempts this step */
+    int32_t n_ls;                       /* rejected trial steps                  */
+    int32_t ftype;                      /* accepted as f-type (Armijo) step      */
+    double mu, f, theta, E0, inf_pr, inf_du;
+    double alpha, alpha_max, alpha_z, gphi;
+    double ic_dw[MDSIP_MAX_IC], ic_dc[MDSIP_MAX_IC];
+    int32_t ic_inertia[MDSIP_MAX_IC][3]; /* (pos, neg, zero) of the 4x4 matrix    */
+} mdsip_iter_rec;
+/* Copy up to `cap` per-iteration records; *n receives the number available. */
+mdsip_status mdsip_get_log(mdsip_problem *p, mdsip_iter_rec *buf, int32_t cap, int32_t *n);
+
+/* Parity hook: one Newton direction at a given packed iterate with fixed
+ * shifts (no inertia correction).  dir_out receives the packed direction
+ * (same layout as the iterate); inertia_out the (pos, neg, zero) inertia of
+ * the 4x4 matrix of Eq. (linsys4x4) obtained by Haynsworth additivity
+ * (Section 2.3).  `refine` > 0 adds up to that many iterative-refinement
+ * sweeps on the unreduced operator. */
+mdsip_status mdsip_debug_direction(mdsip_problem *p, const double *packed, double mu, double dw,
+                                   double dc, int32_t refine, double *dir_out,
+                                   int32_t inertia_out[3], int mem);
+
+/* ------------------------------------------------------------------------- */
+/* Kernel-level entry points (device pointers, context stream).              */
+/* ------------------------------------------------------------------------- */
+
+/* Condensation product of the two-stage elimination (Section 2.2 K3-type
+ * update, M := M + A D B^T with A = B):
+ *   C[p][q] = beta * C[p][q] + sum_i A[i][p] * A[i][q] / w[i]   for p >= q,
+ * A: m x n row-major with leading dimension lda (lda >= n, lda % 2 == 0),
+ * w: m (nonzero), C: n x n column-major, leading dimension ldc; only the lower
+ * triangle (p >= q) is written.  beta is 0 or 1.  FP64 throughout. */
+mdsip_status mdsip_syrk_scaled(mdsip_ctx *ctx, int64_t m, int64_t n, const double *A, int64_t lda,
+                               const double *w, double beta, double *C, int64_t ldc);
+
+/* Bunch-Kaufman LDL^T (Section 2.3) of the symmetric N x N matrix whose lower
+ * triangle is in S (column-major, leading dimension ld).  S is overwritten
+ * (used as work space).  Outputs (device):
+ *   L:     N x N column-major unit lower triangular (leading dimension N)
+ *   Dd:    N   diagonal of D;  Doff: N   Doff[k] = D[k+1][k] for 2x2 blocks, else 0
+ *   perm:  N   P S P^T = L D L^T with (P v)[i] = v[perm[i]]
+ *   kind:  N   1 = 1x1 pivot, 2 = first column of a 2x2 pivot, 0 = second column
+ *   inertia: 3 (pos, neg, zero); a 1x1 pivot |d| <= zero_tol * max|S| counts zero.
+ * Errors: INVALID_ARG, OOM, DEVICE (a bounded device wait expired). */
+mdsip_status mdsip_ldlt_factor(mdsip_ctx *ctx, int64_t N, double *S, int64_t ld, double zero_tol,
+                               double *L, double *Dd, double *Doff, int32_t *perm, int32_t *kind,
+                               int32_t *inertia);
+
+/* Solve (P^T L D L^T P) x = b in place for `nrhs` right-hand sides stored
+ * column-major in B (leading dimension ldb), with the factors above. */
+mdsip_status mdsip_ldlt_solve(mdsip_ctx *ctx, int64_t N, const double *L, const double *Dd,
+                              const double *Doff, const int32_t *perm, int64_t nrhs, double *B,
+                              int64_t ldb);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MDSIP_H */

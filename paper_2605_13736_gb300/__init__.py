@@ -1,0 +1,253 @@
+"""mdsip: mixed dense-sparse interior-point Newton step on a GB300 GPU.
+
+Thin ctypes binding of libmdsip (C ABI in include/mdsip.h).  Every function
+has the name of the C entry point it marshals; all arithmetic runs in the
+library's CUDA kernels.  There is no fallback: if libmdsip.so has not been
+built (`paper_2605_13736_gb300.build.build()`), loading raises.
+
+Arrays may be numpy arrays (host, mem=MDSIP_MEM_HOST) or torch CUDA tensors
+(device, mem=MDSIP_MEM_DEVICE); they must be contiguous float64 / int32.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB, build  # noqa: F401
+
+MDSIP_MEM_HOST, MDSIP_MEM_DEVICE = 0, 1
+MDSIP_PATH_AUTO, MDSIP_PATH_P1, MDSIP_PATH_P2 = 0, 1, 2
+MDSIP_MAX_IC = 16
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "CALLBACK", 5: "NONFINITE",
+          6: "INERTIA", 7: "RESTORATION_NEEDED", 8: "MAX_ITER", 9: "TIMEOUT",
+          10: "PRECONDITION", 11: "DEVICE"}
+# statuses that end a solve normally (the solve ran; the result says how it ended)
+SOLVE_OUTCOMES = {0, 5, 6, 7, 8, 9}
+
+
+class MdsipError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class mdsip_synth_data(C.Structure):
+    _fields_ = [("n_d", C.c_int64), ("n_s", C.c_int64), ("m_E", C.c_int64), ("m_I", C.c_int64),
+                ("nnz_Jsg", C.c_int64),
+                ("Q", C.c_void_p), ("c", C.c_void_p), ("A", C.c_void_p), ("gE", C.c_void_p),
+                ("Jsg_rows", C.c_void_p), ("Jsg_cols", C.c_void_p), ("Jsg_vals", C.c_void_p),
+                ("h_set", C.c_void_p), ("hl", C.c_void_p), ("hu", C.c_void_p),
+                ("xl", C.c_void_p), ("xu", C.c_void_p), ("x0", C.c_void_p)]
+
+
+class mdsip_stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("path", C.c_int32),
+                ("n_factorizations", C.c_int32), ("n_ls_trials", C.c_int64),
+                ("f", C.c_double), ("E0", C.c_double), ("inf_pr", C.c_double),
+                ("inf_du", C.c_double), ("mu", C.c_double), ("t_total_ms", C.c_double),
+                ("t_condense_ms", C.c_double), ("t_factor_ms", C.c_double),
+                ("t_solve_ms", C.c_double), ("t_ls_ms", C.c_double)]
+
+
+class mdsip_iter_rec(C.Structure):
+    _fields_ = [("iter", C.c_int32), ("n_ic", C.c_int32), ("n_ls", C.c_int32), ("ftype", C.c_int32),
+                ("mu", C.c_double), ("f", C.c_double), ("theta", C.c_double), ("E0", C.c_double),
+                ("inf_pr", C.c_double), ("inf_du", C.c_double), ("alpha", C.c_double),
+                ("alpha_max", C.c_double), ("alpha_z", C.c_double), ("gphi", C.c_double),
+                ("ic_dw", C.c_double * MDSIP_MAX_IC), ("ic_dc", C.c_double * MDSIP_MAX_IC),
+                ("ic_inertia", (C.c_int32 * 3) * MDSIP_MAX_IC)]
+
+
+_lib = None
+
+_SIGS = {
+    "mdsip_status_str": (C.c_char_p, [C.c_int]),
+    "mdsip_ctx_create": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "mdsip_ctx_destroy": (None, [C.c_void_p]),
+    "mdsip_ctx_last_error": (C.c_char_p, [C.c_void_p]),
+    "mdsip_problem_create_synthetic": (C.c_int, [C.c_void_p, C.POINTER(mdsip_synth_data), C.c_int,
+                                                 C.POINTER(C.c_void_p)]),
+    "mdsip_problem_destroy": (None, [C.c_void_p]),
+    "mdsip_set_option_int": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int64]),
+    "mdsip_set_option_double": (C.c_int, [C.c_void_p, C.c_char_p, C.c_double]),
+    "mdsip_packed_size": (C.c_int64, [C.c_void_p]),
+    "mdsip_set_start": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int]),
+    "mdsip_solve": (C.c_int, [C.c_void_p]),
+    "mdsip_get_iterate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "mdsip_get_stats": (C.c_int, [C.c_void_p, C.POINTER(mdsip_stats)]),
+    "mdsip_get_log": (C.c_int, [C.c_void_p, C.POINTER(mdsip_iter_rec), C.c_int32,
+                                C.POINTER(C.c_int32)]),
+    "mdsip_debug_direction": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double,
+                                        C.c_int32, C.c_void_p, C.POINTER(C.c_int32), C.c_int]),
+    "mdsip_syrk_scaled": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int64,
+                                    C.c_void_p, C.c_double, C.c_void_p, C.c_int64]),
+    "mdsip_ldlt_factor": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_double,
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p]),
+    "mdsip_ldlt_solve": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_int64, C.c_void_p, C.c_int64]),
+}
+
+
+def exported_symbols():
+    """Names of the C entry points this binding expects the library to export."""
+    return sorted(_SIGS)
+
+
+def lib(path: str | None = None):
+    """Load libmdsip.so (in-tree).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB
+    if not os.path.exists(p):
+        raise RuntimeError(f"libmdsip.so not found at {p}: run paper_2605_13736_gb300.build.build()")
+    L = C.CDLL(p)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = L
+    return L
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "array must be contiguous"
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous(), "tensor must be contiguous"
+        return a.data_ptr()
+    if isinstance(a, int):
+        return a
+    raise TypeError(type(a))
+
+
+def _check(st, ctx=None):
+    if st != 0:
+        msg = lib().mdsip_ctx_last_error(ctx).decode() if ctx else ""
+        raise MdsipError(st, msg)
+    return st
+
+
+# --------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# --------------------------------------------------------------------------
+def mdsip_status_str(status: int) -> str:
+    return lib().mdsip_status_str(status).decode()
+
+
+def mdsip_ctx_create(device: int = 0, stream: int | None = None):
+    h = C.c_void_p()
+    _check(lib().mdsip_ctx_create(device, stream, None, C.byref(h)))
+    return h.value
+
+
+def mdsip_ctx_destroy(ctx):
+    lib().mdsip_ctx_destroy(ctx)
+
+
+def mdsip_ctx_last_error(ctx) -> str:
+    return lib().mdsip_ctx_last_error(ctx).decode()
+
+
+def mdsip_problem_create_synthetic(ctx, *, n_d, n_s, m_E, m_I, Q, c, A, gE, Jsg_rows, Jsg_cols,
+                                   Jsg_vals, h_set, hl, hu, xl, xu, x0=None, mem=MDSIP_MEM_HOST):
+    d = mdsip_synth_data(n_d, n_s, m_E, m_I, len(Jsg_vals), _ptr(Q), _ptr(c), _ptr(A), _ptr(gE),
+                         _ptr(Jsg_rows), _ptr(Jsg_cols), _ptr(Jsg_vals), _ptr(h_set), _ptr(hl),
+                         _ptr(hu), _ptr(xl), _ptr(xu), _ptr(x0))
+    h = C.c_void_p()
+    _check(lib().mdsip_problem_create_synthetic(ctx, C.byref(d), mem, C.byref(h)), ctx)
+    return h.value
+
+
+def mdsip_problem_destroy(prob):
+    lib().mdsip_problem_destroy(prob)
+
+
+def mdsip_set_option_int(prob, name: str, value: int, ctx=None):
+    _check(lib().mdsip_set_option_int(prob, name.encode(), int(value)), ctx)
+
+
+def mdsip_set_option_double(prob, name: str, value: float, ctx=None):
+    _check(lib().mdsip_set_option_double(prob, name.encode(), float(value)), ctx)
+
+
+def mdsip_packed_size(prob) -> int:
+    return lib().mdsip_packed_size(prob)
+
+
+def mdsip_set_start(prob, packed, mu0=-1.0, mem=MDSIP_MEM_HOST, ctx=None):
+    _check(lib().mdsip_set_start(prob, _ptr(packed), float(mu0), mem), ctx)
+
+
+def mdsip_solve(prob, ctx=None) -> int:
+    """Returns the solve outcome status; raises on errors that stop the call itself."""
+    st = lib().mdsip_solve(prob)
+    if st not in SOLVE_OUTCOMES:
+        _check(st, ctx)
+    return st
+
+
+def mdsip_get_iterate(prob, out, mem=MDSIP_MEM_HOST, ctx=None):
+    _check(lib().mdsip_get_iterate(prob, _ptr(out), mem), ctx)
+    return out
+
+
+def mdsip_get_stats(prob) -> dict:
+    s = mdsip_stats()
+    _check(lib().mdsip_get_stats(prob, C.byref(s)))
+    return {k: getattr(s, k) for k, _ in mdsip_stats._fields_}
+
+
+def mdsip_get_log(prob) -> list:
+    n = C.c_int32()
+    _check(lib().mdsip_get_log(prob, None, 0, C.byref(n)))
+    buf = (mdsip_iter_rec * max(1, n.value))()
+    _check(lib().mdsip_get_log(prob, buf, n.value, C.byref(n)))
+    out = []
+    for r in buf[:n.value]:
+        rec = {k: getattr(r, k) for k, _ in mdsip_iter_rec._fields_ if not k.startswith("ic_")}
+        k = min(r.n_ic, MDSIP_MAX_IC)
+        rec["ic"] = [(r.ic_dw[i], r.ic_dc[i], tuple(r.ic_inertia[i])) for i in range(k)]
+        out.append(rec)
+    return out
+
+
+def mdsip_debug_direction(prob, packed, mu, dw, dc, out, refine=0, mem=MDSIP_MEM_HOST, ctx=None):
+    inertia = (C.c_int32 * 3)()
+    _check(lib().mdsip_debug_direction(prob, _ptr(packed), float(mu), float(dw), float(dc),
+                                       int(refine), _ptr(out), inertia, mem), ctx)
+    return tuple(inertia)
+
+
+def mdsip_syrk_scaled(ctx, m, n, A, lda, w, beta, Cmat, ldc):
+    _check(lib().mdsip_syrk_scaled(ctx, m, n, _ptr(A), lda, _ptr(w), float(beta), _ptr(Cmat), ldc), ctx)
+
+
+def mdsip_ldlt_factor(ctx, N, S, ld, zero_tol, L, Dd, Doff, perm, kind, inertia):
+    _check(lib().mdsip_ldlt_factor(ctx, N, _ptr(S), ld, float(zero_tol), _ptr(L), _ptr(Dd),
+                                   _ptr(Doff), _ptr(perm), _ptr(kind), _ptr(inertia)), ctx)
+
+
+def mdsip_ldlt_solve(ctx, N, L, Dd, Doff, perm, nrhs, B, ldb):
+    _check(lib().mdsip_ldlt_solve(ctx, N, _ptr(L), _ptr(Dd), _ptr(Doff), _ptr(perm), nrhs, _ptr(B),
+                                  ldb), ctx)
+
+
+def synth_arrays(inst) -> dict:
+    """Keyword arguments of mdsip_problem_create_synthetic from an object with
+    the instance fields (n_d, n_s, m_E, m_I, Q, c, A, b, Jsg_*, h_set, hl, hu, xl, xu, x0)."""
+    f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
+    return dict(n_d=inst.n_d, n_s=inst.n_s, m_E=inst.m_E, m_I=inst.m_I, Q=f64(inst.Q), c=f64(inst.c),
+                A=f64(inst.A), gE=f64(inst.b), Jsg_rows=i32(inst.Jsg_rows), Jsg_cols=i32(inst.Jsg_cols),
+                Jsg_vals=f64(inst.Jsg_vals), h_set=i32(inst.h_set), hl=f64(inst.hl), hu=f64(inst.hu),
+                xl=f64(inst.xl), xu=f64(inst.xu), x0=f64(inst.x0))

@@ -1,0 +1,1031 @@
+// Host control of the interior-point method and the C ABI of libmdsip.
+//
+// The control logic of the method is sequential (Section 3): the host runs
+// the filter line-search loop of Section 2.1 (Waechter-Biegler Algorithm A
+// with inertia correction, no second-order correction, no restoration) and
+// launches the device kernels; per step it reads back only scalars (norms,
+// inertia counts, step lengths, trial merit values).  All vectors and
+// matrices stay on the device.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <numeric>
+#include <tuple>
+
+#include "internal.cuh"
+#include "vec.cuh"
+
+namespace mdsip {
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+void *Ctx::alloc(size_t bytes) {
+    void *p = nullptr;
+    if (has_hooks) {
+        p = hooks.alloc(bytes, stream, hooks.user);
+        if (!p) throw Error{MDSIP_ERR_OOM, "allocation hook returned NULL"};
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw Error{MDSIP_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+        }
+    }
+    return p;
+}
+
+void Ctx::release(void *p, size_t bytes) {
+    if (!p) return;
+    if (has_hooks)
+        hooks.free(p, bytes, stream, hooks.user);
+    else
+        cudaFree(p);
+}
+
+void *Ctx::scratch_at_least(size_t bytes) {
+    if (bytes <= scratch_bytes) return scratch;
+    if (scratch) {
+        MDSIP_CUDA(cudaStreamSynchronize(stream));
+        release(scratch, scratch_bytes);
+        scratch = nullptr;
+        scratch_bytes = 0;
+    }
+    scratch = alloc(bytes);
+    scratch_bytes = bytes;
+    return scratch;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        MDSIP_CUDA(cudaSetDevice(dev));
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Problem state
+// ---------------------------------------------------------------------------
+enum : int {
+    SC_F = 0, SC_THETA = 1, SC_CMAX = 2,
+    SC_E = 3,        // 7: max|dual|, max|c|, max sz, min sz, ||y||_1, ||z||_1, sum log s
+    SC_DIAG = 10,    // 6: In(Q_s) pos/neg/zero, In(-W) pos/neg/zero
+    SC_STEP = 16,    // 3: alpha_max, alpha_z, gphi
+    SC_TF = 19, SC_TTHETA = 20, SC_TCMAX = 21,
+    SC_TRIAL = 22,   // 2: sum log s, #non-positive slacks
+    SC_MAXABS = 24,
+    SC_COUNT = 32
+};
+
+struct Problem {
+    Ctx *ctx = nullptr;
+    Dims D{};
+    ModelView Mv{};
+    Options opt;
+    int path = MDSIP_PATH_P2;
+    bool p2_ok = false;
+    int64_t n_bounds = 0;
+    int64_t N = 0;  // reduced matrix size
+
+    // model data
+    DBuf bQ, bc, bA, bgE, bhl, bhu, bxl, bxu, bx0, bhset;
+    DBuf bcsr_ptr, bcsr_col, bcsr_val, bcsc_ptr, bcsc_row, bcsc_val;
+    // iterate, trial, direction
+    DBuf bx, bd, byg, byh, bzl, bzu, bvl, bvu, bxt, bdt;
+    DBuf bdx, bdd, bdyg, bdyh, bdzl, bdzu, bdvl, bdvu;
+    // model values and Newton quantities
+    DBuf bgrad, bgrad_t, bcg, bcg_t, bch, bch_t, bgl, bATy, bJdh, bHss, bHdd;
+    DBuf bsig_x, bq, bsig_d, bw, bbt_g, bu, bATu, brhs, bAdx;
+    // reduced matrix and factors
+    DBuf bS, bL, bDd, bDoff, bperm, bkind, binertia, bldlt_ws, berr, bsyrk_ws;
+    DBuf bscal, bpartial, bcolpart;
+    double *hscal = nullptr;  // pinned mirror of the scalars
+    int32_t *hint = nullptr;  // pinned: inertia (3) + device error flag
+
+    IterView I{};
+    DirView Dir{};
+    VecOps V{};
+    double *xt = nullptr, *dt = nullptr, *grad = nullptr, *grad_t = nullptr, *cg = nullptr,
+           *cg_t = nullptr, *ch = nullptr, *ch_t = nullptr;
+
+    bool has_start = false;
+    double start_mu0 = -1.0;
+    std::vector<mdsip_iter_rec> log;
+    mdsip_stats stats{};
+    cudaEvent_t ev[8]{};
+
+    ~Problem() {
+        if (hscal) cudaFreeHost(hscal);
+        if (hint) cudaFreeHost(hint);
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+
+    double *scal() const { return bscal.as<double>(); }
+
+    void sync_scalars() {
+        MDSIP_CUDA(cudaMemcpyAsync(hscal, scal(), SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+        MDSIP_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Creation
+// ---------------------------------------------------------------------------
+template <class T>
+static std::vector<T> fetch(const T *src, int64_t count, int mem) {
+    std::vector<T> out((size_t)std::max<int64_t>(count, 0));
+    if (count <= 0) return out;
+    MDSIP_REQUIRE(src != nullptr, MDSIP_ERR_INVALID_ARG, "null data pointer");
+    if (mem == MDSIP_MEM_HOST)
+        std::memcpy(out.data(), src, count * sizeof(T));
+    else
+        MDSIP_CUDA(cudaMemcpy(out.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost));
+    return out;
+}
+
+template <class T>
+static T *upload(Ctx *ctx, DBuf &buf, const std::vector<T> &v, int64_t count) {
+    T *p = buf.get<T>(ctx, (size_t)std::max<int64_t>(count, 1));
+    if (count > 0)
+        MDSIP_CUDA(cudaMemcpyAsync(p, v.data(), count * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+    return p;
+}
+
+static double *dvec(Ctx *ctx, DBuf &b, int64_t n) {
+    double *p = b.get<double>(ctx, (size_t)std::max<int64_t>(n, 1));
+    MDSIP_CUDA(cudaMemsetAsync(p, 0, std::max<int64_t>(n, 1) * sizeof(double), ctx->stream));
+    return p;
+}
+
+static Problem *create_synthetic(Ctx *ctx, const mdsip_synth_data *dat, int mem) {
+    MDSIP_REQUIRE(dat, MDSIP_ERR_INVALID_ARG, "null data");
+    MDSIP_REQUIRE(mem == MDSIP_MEM_HOST || mem == MDSIP_MEM_DEVICE, MDSIP_ERR_INVALID_ARG, "bad mem tag");
+    MDSIP_REQUIRE(dat->n_d >= 0 && dat->n_s >= 0 && dat->m_E >= 0 && dat->m_I >= 0 && dat->nnz_Jsg >= 0,
+                  MDSIP_ERR_INVALID_ARG, "negative size");
+    MDSIP_REQUIRE(dat->n_s + dat->n_d > 0, MDSIP_ERR_INVALID_ARG, "no variables");
+    MDSIP_REQUIRE(dat->nnz_Jsg < (1LL << 31) && dat->m_E < (1LL << 31) && dat->n_s < (1LL << 31),
+                  MDSIP_ERR_INVALID_ARG, "sparse block too large for 32-bit indices");
+    auto P = new Problem();
+    try {
+        P->ctx = ctx;
+        Dims &D = P->D;
+        D.n_s = dat->n_s;
+        D.n_d = dat->n_d;
+        D.m_E = dat->m_E;
+        D.m_I = dat->m_I;
+        D.n = D.n_s + D.n_d;
+        D.m = D.m_E + D.m_I;
+        D.lda = std::max<int64_t>(4, (D.n_d + 3) / 4 * 4);
+        cudaStream_t st = ctx->stream;
+
+        // host copies of the small data, validation
+        auto c = fetch(dat->c, D.n, mem);
+        auto gE = fetch(dat->gE, D.m_E, mem);
+        auto hl = fetch(dat->hl, D.m_I, mem);
+        auto hu = fetch(dat->hu, D.m_I, mem);
+        auto xl = fetch(dat->xl, D.n, mem);
+        auto xu = fetch(dat->xu, D.n, mem);
+        std::vector<double> x0 = dat->x0 ? fetch(dat->x0, D.n, mem) : std::vector<double>(D.n, 0.0);
+        auto hset = fetch(dat->h_set, D.n_d, mem);
+        auto rows = fetch(dat->Jsg_rows, dat->nnz_Jsg, mem);
+        auto cols = fetch(dat->Jsg_cols, dat->nnz_Jsg, mem);
+        auto vals = fetch(dat->Jsg_vals, dat->nnz_Jsg, mem);
+        for (int64_t i = 0; i < D.n; ++i) {
+            MDSIP_REQUIRE(!(xl[i] > xu[i]), MDSIP_ERR_INVALID_ARG, "xl > xu");
+            P->n_bounds += std::isfinite(xl[i]) + std::isfinite(xu[i]);
+        }
+        for (int64_t j = 0; j < D.m_I; ++j) {
+            MDSIP_REQUIRE(hl[j] < hu[j], MDSIP_ERR_INVALID_ARG, "need hl < hu");
+            MDSIP_REQUIRE(std::isfinite(hl[j]) || std::isfinite(hu[j]), MDSIP_ERR_INVALID_ARG,
+                          "every inequality needs a finite bound");
+            P->n_bounds += std::isfinite(hl[j]) + std::isfinite(hu[j]);
+        }
+        for (int64_t k = 0; k < D.n_d; ++k)
+            MDSIP_REQUIRE(hset[k] >= -1 && hset[k] < D.m_I, MDSIP_ERR_INVALID_ARG, "h_set out of range");
+        // sparse block: sort, merge duplicates, CSR and CSC
+        std::vector<int64_t> order((size_t)dat->nnz_Jsg);
+        std::iota(order.begin(), order.end(), 0);
+        for (int64_t e = 0; e < dat->nnz_Jsg; ++e)
+            MDSIP_REQUIRE(rows[e] >= 0 && rows[e] < D.m_E && cols[e] >= 0 && cols[e] < D.n_s,
+                          MDSIP_ERR_INVALID_ARG, "J_sg index out of range");
+        std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+            return std::tie(rows[a], cols[a]) < std::tie(rows[b], cols[b]);
+        });
+        std::vector<int32_t> r2, c2;
+        std::vector<double> v2;
+        for (int64_t t = 0; t < (int64_t)order.size(); ++t) {
+            const int64_t e = order[t];
+            if (!r2.empty() && r2.back() == rows[e] && c2.back() == cols[e]) {
+                v2.back() += vals[e];
+            } else {
+                r2.push_back(rows[e]);
+                c2.push_back(cols[e]);
+                v2.push_back(vals[e]);
+            }
+        }
+        const int64_t nnz = (int64_t)v2.size();
+        std::vector<int32_t> csr_ptr(D.m_E + 1, 0), csc_ptr(D.n_s + 1, 0), csc_row(nnz);
+        std::vector<double> csc_val(nnz);
+        for (int64_t e = 0; e < nnz; ++e) {
+            csr_ptr[r2[e] + 1]++;
+            csc_ptr[c2[e] + 1]++;
+        }
+        for (int64_t i = 0; i < D.m_E; ++i) csr_ptr[i + 1] += csr_ptr[i];
+        for (int64_t k = 0; k < D.n_s; ++k) csc_ptr[k + 1] += csc_ptr[k];
+        {
+            std::vector<int32_t> fill(csc_ptr.begin(), csc_ptr.end() - 1);
+            for (int64_t e = 0; e < nnz; ++e) {  // rows ascending within each column
+                const int32_t pos = fill[c2[e]]++;
+                csc_row[pos] = r2[e];
+                csc_val[pos] = v2[e];
+            }
+        }
+        bool p2 = true;
+        for (int64_t k = 0; k < D.n_s; ++k)
+            if (csc_ptr[k + 1] - csc_ptr[k] > 1) p2 = false;
+        P->p2_ok = p2;
+
+        // device copies
+        ModelView &M = P->Mv;
+        M.c = upload(ctx, P->bc, c, D.n);
+        M.gE = upload(ctx, P->bgE, gE, D.m_E);
+        M.hl = upload(ctx, P->bhl, hl, D.m_I);
+        M.hu = upload(ctx, P->bhu, hu, D.m_I);
+        M.xl = upload(ctx, P->bxl, xl, D.n);
+        M.xu = upload(ctx, P->bxu, xu, D.n);
+        upload(ctx, P->bx0, x0, D.n);
+        M.h_set = upload(ctx, P->bhset, hset, D.n_d);
+        M.csr_ptr = upload(ctx, P->bcsr_ptr, csr_ptr, D.m_E + 1);
+        M.csr_col = upload(ctx, P->bcsr_col, c2, nnz);
+        M.csr_val = upload(ctx, P->bcsr_val, v2, nnz);
+        M.csc_ptr = upload(ctx, P->bcsc_ptr, csc_ptr, D.n_s + 1);
+        M.csc_row = upload(ctx, P->bcsc_row, csc_row, nnz);
+        M.csc_val = upload(ctx, P->bcsc_val, csc_val, nnz);
+        // dense blocks (may be large: copied device-to-device or host-to-device directly)
+        const auto kind = mem == MDSIP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+        double *Q = P->bQ.get<double>(ctx, std::max<int64_t>(D.n_d * D.n_d, 1));
+        if (D.n_d > 0) {
+            MDSIP_REQUIRE(dat->Q, MDSIP_ERR_INVALID_ARG, "null Q");
+            MDSIP_CUDA(cudaMemcpyAsync(Q, dat->Q, D.n_d * D.n_d * sizeof(double), kind, st));
+        }
+        M.Q = Q;
+        double *A = P->bA.get<double>(ctx, std::max<int64_t>(D.m_E * D.lda, 1));
+        MDSIP_CUDA(cudaMemsetAsync(A, 0, std::max<int64_t>(D.m_E * D.lda, 1) * sizeof(double), st));
+        if (D.m_E > 0 && D.n_d > 0) {
+            MDSIP_REQUIRE(dat->A, MDSIP_ERR_INVALID_ARG, "null A");
+            MDSIP_CUDA(cudaMemcpy2DAsync(A, D.lda * sizeof(double), dat->A, D.n_d * sizeof(double),
+                                         D.n_d * sizeof(double), D.m_E, kind, st));
+        }
+        M.A = A;
+
+        // iterate and work vectors
+        IterView &I = P->I;
+        I.x = dvec(ctx, P->bx, D.n);
+        I.d = dvec(ctx, P->bd, D.m_I);
+        I.yg = dvec(ctx, P->byg, D.m_E);
+        I.yh = dvec(ctx, P->byh, D.m_I);
+        I.zl = dvec(ctx, P->bzl, D.n);
+        I.zu = dvec(ctx, P->bzu, D.n);
+        I.vl = dvec(ctx, P->bvl, D.m_I);
+        I.vu = dvec(ctx, P->bvu, D.m_I);
+        P->xt = dvec(ctx, P->bxt, D.n);
+        P->dt = dvec(ctx, P->bdt, D.m_I);
+        DirView &R = P->Dir;
+        R.dx = dvec(ctx, P->bdx, D.n);
+        R.dd = dvec(ctx, P->bdd, D.m_I);
+        R.dyg = dvec(ctx, P->bdyg, D.m_E);
+        R.dyh = dvec(ctx, P->bdyh, D.m_I);
+        R.dzl = dvec(ctx, P->bdzl, D.n);
+        R.dzu = dvec(ctx, P->bdzu, D.n);
+        R.dvl = dvec(ctx, P->bdvl, D.m_I);
+        R.dvu = dvec(ctx, P->bdvu, D.m_I);
+        P->grad = dvec(ctx, P->bgrad, D.n);
+        P->grad_t = dvec(ctx, P->bgrad_t, D.n);
+        P->cg = dvec(ctx, P->bcg, D.m_E);
+        P->cg_t = dvec(ctx, P->bcg_t, D.m_E);
+        P->ch = dvec(ctx, P->bch, D.m_I);
+        P->ch_t = dvec(ctx, P->bch_t, D.m_I);
+        dvec(ctx, P->bgl, D.n);
+        dvec(ctx, P->bATy, D.n_d);
+        dvec(ctx, P->bJdh, D.m_I * D.n_d);
+        dvec(ctx, P->bHss, D.n_s);
+        dvec(ctx, P->bHdd, D.n_d * D.n_d);
+        dvec(ctx, P->bsig_x, D.n);
+        dvec(ctx, P->bq, D.n_s);
+        dvec(ctx, P->bsig_d, D.m_I);
+        dvec(ctx, P->bw, D.m_E);
+        dvec(ctx, P->bbt_g, D.m_E);
+        dvec(ctx, P->bu, D.m_E);
+        dvec(ctx, P->bATu, D.n_d);
+        dvec(ctx, P->bAdx, D.m_E);
+        dvec(ctx, P->bscal, SC_COUNT);
+        dvec(ctx, P->bpartial, (int64_t)kRedBlocks * 8);
+        dvec(ctx, P->bcolpart, (int64_t)kRedBlocks * std::max<int64_t>(D.n_d, 1));
+        P->berr.get<int>(ctx, 4);
+        MDSIP_CUDA(cudaMallocHost(&P->hscal, SC_COUNT * sizeof(double)));
+        MDSIP_CUDA(cudaMallocHost(&P->hint, 8 * sizeof(int32_t)));
+        for (auto &e : P->ev) MDSIP_CUDA(cudaEventCreate(&e));
+
+        P->V.D = D;
+        P->V.M = M;
+        P->V.st = st;
+        P->V.partial = P->bpartial.as<double>();
+        P->V.colpart = P->bcolpart.as<double>();
+        MDSIP_CUDA(cudaStreamSynchronize(st));
+    } catch (...) {
+        delete P;
+        throw;
+    }
+    return P;
+}
+
+// allocate the reduced matrix and factor storage for the chosen path
+static void prepare_path(Problem *P) {
+    const Dims &D = P->D;
+    int path = (int)P->opt.path;
+    if (path == MDSIP_PATH_AUTO) path = P->p2_ok ? MDSIP_PATH_P2 : MDSIP_PATH_P1;
+    MDSIP_REQUIRE(path != MDSIP_PATH_P2 || P->p2_ok, MDSIP_ERR_PRECONDITION,
+                  "path P2 needs J_sg rows with disjoint column supports");
+    const int64_t N = path == MDSIP_PATH_P2 ? D.n_d + D.m_I : D.n_d + D.m;
+    MDSIP_REQUIRE(2 * N * (int64_t)sizeof(double) <= 200 * 1024, MDSIP_ERR_INVALID_ARG,
+                  "reduced matrix too large for the dense factorization");
+    if (path == P->path && N == P->N && P->bS.ptr) return;
+    P->path = path;
+    P->N = N;
+    Ctx *ctx = P->ctx;
+    dvec(ctx, P->bS, N * N);
+    dvec(ctx, P->bL, N * N);
+    dvec(ctx, P->bDd, N);
+    dvec(ctx, P->bDoff, N);
+    P->bperm.get<int32_t>(ctx, std::max<int64_t>(N, 1));
+    P->bkind.get<int32_t>(ctx, std::max<int64_t>(N, 1));
+    P->binertia.get<int32_t>(ctx, 4);
+    P->bldlt_ws.get<char>(ctx, ldlt_scratch_bytes(N));
+    dvec(ctx, P->brhs, std::max<int64_t>(N, 1) * 2);
+    const size_t sw = path == MDSIP_PATH_P2 ? syrk_fp64_scratch_bytes(D.m_E, D.n_d, ctx->num_sms) : 0;
+    if (sw) P->bsyrk_ws.get<char>(ctx, sw);
+    else P->bsyrk_ws.reset();
+}
+
+// ---------------------------------------------------------------------------
+// One factorization attempt with shifts (dw, dc): condensation, LDL^T and
+// the inertia of the 4x4 matrix by Haynsworth additivity (Section 2.3).
+// ---------------------------------------------------------------------------
+struct Inertia {
+    int64_t pos = 0, neg = 0, zero = 0;
+    bool operator==(const Inertia &o) const { return pos == o.pos && neg == o.neg && zero == o.zero; }
+};
+
+static Inertia factor_attempt(Problem *P, double dw, double dc) {
+    const Dims &D = P->D;
+    cudaStream_t st = P->ctx->stream;
+    double *sc = P->scal();
+    const bool p2 = P->path == MDSIP_PATH_P2;
+    double *sig_x = P->bsig_x.as<double>(), *q = P->bq.as<double>(), *sig_d = P->bsig_d.as<double>(),
+           *w = P->bw.as<double>(), *S = P->bS.as<double>();
+    MDSIP_CUDA(cudaEventRecord(P->ev[0], st));
+    P->V.newton_diag(P->I, P->bHss.as<double>(), dw, dc, p2, sig_x, q, sig_d, w, sc + SC_DIAG);
+    if (p2) {
+        launch_assemble_S(st, D, P->bHdd.as<double>(), sig_x + D.n_s, P->bJdh.as<double>(), sig_d, dw, dc,
+                          S);
+        launch_syrk_fp64_ws(st, P->ctx->num_sms, P->Mv.A, D.m_E, D.n_d, D.lda, w, 1.0, S, P->N,
+                            P->bsyrk_ws.as<double>());
+    } else {
+        launch_assemble_M(st, D, P->Mv, P->bHdd.as<double>(), sig_x + D.n_s, P->bJdh.as<double>(), sig_d,
+                          q, dw, dc, S);
+    }
+    MDSIP_CUDA(cudaEventRecord(P->ev[1], st));
+    launch_maxabs_lower(st, P->N, S, P->N, P->V.partial, sc + SC_MAXABS);
+    MDSIP_CUDA(cudaMemsetAsync(P->berr.ptr, 0, sizeof(int), st));
+    LdltOut o{P->bL.as<double>(), P->bDd.as<double>(), P->bDoff.as<double>(), P->bperm.as<int32_t>(),
+              P->bkind.as<int32_t>(), P->binertia.as<int32_t>()};
+    launch_ldlt(st, P->ctx->num_sms, P->N, S, P->N, sc + SC_MAXABS, P->opt.zero_tol, o,
+                P->bldlt_ws.ptr, P->berr.as<int>());
+    MDSIP_CUDA(cudaEventRecord(P->ev[2], st));
+    MDSIP_CUDA(cudaMemcpyAsync(P->hint, P->binertia.ptr, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MDSIP_CUDA(cudaMemcpyAsync(P->hint + 4, P->berr.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    P->sync_scalars();
+    MDSIP_REQUIRE(P->hint[4] == 0, MDSIP_ERR_DEVICE, "LDL^T: a bounded device wait expired");
+    float a = 0, b = 0;
+    cudaEventElapsedTime(&a, P->ev[0], P->ev[1]);
+    cudaEventElapsedTime(&b, P->ev[1], P->ev[2]);
+    P->stats.t_condense_ms += a;
+    P->stats.t_factor_ms += b;
+    P->stats.n_factorizations++;
+    const double *h = P->hscal;
+    Inertia in;
+    in.pos = (int64_t)h[SC_DIAG + 0] + P->hint[0];
+    in.neg = (int64_t)h[SC_DIAG + 1] + P->hint[1];
+    in.zero = (int64_t)h[SC_DIAG + 2] + P->hint[2];
+    if (p2) {
+        in.pos += (int64_t)h[SC_DIAG + 3];
+        in.neg += (int64_t)h[SC_DIAG + 4];
+        in.zero += (int64_t)h[SC_DIAG + 5];
+    }
+    return in;
+}
+
+// Solve with the current factorization and back-substitute to the full
+// direction (Eq. (linsys4x4) unknowns plus dd and the bound multipliers).
+static void solve_direction(Problem *P, double mu, double dw) {
+    const Dims &D = P->D;
+    cudaStream_t st = P->ctx->stream;
+    const bool p2 = P->path == MDSIP_PATH_P2;
+    double *gl = P->bgl.as<double>(), *q = P->bq.as<double>(), *w = P->bw.as<double>(),
+           *sig_d = P->bsig_d.as<double>(), *bt_g = P->bbt_g.as<double>(), *u = P->bu.as<double>(),
+           *ATu = P->bATu.as<double>(), *rhs = P->brhs.as<double>(), *Adx = P->bAdx.as<double>();
+    MDSIP_CUDA(cudaEventRecord(P->ev[3], st));
+    P->V.rhs_y(P->I, gl, P->cg, q, p2 ? w : nullptr, mu, bt_g, p2 ? u : nullptr);
+    if (p2) launch_gemv_t(st, P->Mv.A, D.m_E, D.n_d, D.lda, u, P->V.colpart, ATu);
+    P->V.rhs_reduced(P->I, gl, P->ch, sig_d, ATu, bt_g, mu, dw, !p2, rhs);
+    launch_ldlt_solve(st, P->N, P->bL.as<double>(), P->bDd.as<double>(), P->bDoff.as<double>(),
+                      P->bperm.as<int32_t>(), 1, rhs, P->N);
+    if (p2) {
+        launch_gemv_rows(st, P->Mv.A, D.m_E, D.n_d, D.lda, rhs, Adx);
+        P->V.dyg_p2(Adx, bt_g, w, P->Dir.dyg);
+        P->V.backsub(P->I, P->Dir, gl, q, sig_d, rhs, rhs + D.n_d, mu, dw);
+    } else {
+        P->V.copy(rhs + D.n_d, P->Dir.dyg, D.m_E);
+        P->V.backsub(P->I, P->Dir, gl, q, sig_d, rhs, rhs + D.n_d + D.m_E, mu, dw);
+    }
+    MDSIP_CUDA(cudaEventRecord(P->ev[4], st));
+}
+
+// model derivatives and the Lagrangian gradient at the current point
+static void eval_derivatives(Problem *P) {
+    P->V.jac_hess(P->I.x, P->I.yh, P->bJdh.as<double>(), P->bHss.as<double>(), P->bHdd.as<double>());
+    P->V.lagrangian_grad(P->I, P->grad, P->bJdh.as<double>(), P->bATy.as<double>(), P->bgl.as<double>());
+}
+
+struct Errs {
+    double E, dual, primal, comp;
+};
+
+static Errs kkt_error(const Problem *P, double mu) {
+    const double *e = P->hscal + SC_E;
+    const Options &o = P->opt;
+    const double nm = (double)(P->D.m + P->n_bounds);
+    const double s_d = nm > 0 ? std::max(o.s_max, (e[4] + e[5]) / nm) / o.s_max : 1.0;
+    const double s_c = P->n_bounds > 0 ? std::max(o.s_max, e[5] / (double)P->n_bounds) / o.s_max : 1.0;
+    const double comp = P->n_bounds > 0 ? std::max(std::fabs(e[2] - mu), std::fabs(e[3] - mu)) : 0.0;
+    Errs r;
+    r.dual = e[0];
+    r.primal = e[1];
+    r.comp = comp;
+    r.E = std::max(std::max(r.dual / s_d, r.primal), comp / s_c);
+    return r;
+}
+
+static void swap_trial(Problem *P) {
+    std::swap(P->I.x, P->xt);
+    std::swap(P->I.d, P->dt);
+    std::swap(P->grad, P->grad_t);
+    std::swap(P->cg, P->cg_t);
+    std::swap(P->ch, P->ch_t);
+}
+
+static mdsip_status run_ipm(Problem *P) {
+    prepare_path(P);
+    const Dims &D = P->D;
+    const Options &o = P->opt;
+    cudaStream_t st = P->ctx->stream;
+    double *sc = P->scal();
+    const double *h = P->hscal;
+    const auto t_start = std::chrono::steady_clock::now();
+    P->stats = mdsip_stats{};
+    P->stats.path = P->path;
+    P->log.clear();
+    MDSIP_CUDA(cudaEventRecord(P->ev[6], st));
+
+    if (!P->has_start) {
+        P->V.init_x(P->bx0.as<double>(), o.kappa_1, o.kappa_2, P->I);
+        P->V.eval_cons(P->I.x, P->I.d, P->cg, P->ch, sc + SC_THETA);  // ch = h(x0) - 0
+        P->V.init_d(P->ch, o.kappa_1, o.kappa_2, P->I);
+    }
+    double mu = (P->has_start && P->start_mu0 > 0) ? P->start_mu0 : o.mu0;
+    double tau = std::max(o.tau_min, 1.0 - mu);
+    P->V.eval_f(P->I.x, P->grad, sc + SC_F);
+    P->V.eval_cons(P->I.x, P->I.d, P->cg, P->ch, sc + SC_THETA);
+    P->sync_scalars();
+    double f = h[SC_F], th = h[SC_THETA];
+    const double theta_max = o.theta_max_fact * std::max(1.0, th);
+    const double theta_min = o.theta_min_fact * std::max(1.0, th);
+    std::vector<std::pair<double, double>> filt;
+    double dw_last = 0.0;
+    const Inertia target{D.n, D.m, 0};
+    int64_t k = 0;
+    mdsip_status status = MDSIP_MAX_ITER;
+
+    while (true) {
+        eval_derivatives(P);
+        P->V.errors(P->I, P->bgl.as<double>(), P->cg, P->ch, sc + SC_E);
+        P->sync_scalars();
+        Errs e0 = kkt_error(P, 0.0);
+        mdsip_iter_rec rec{};
+        rec.iter = (int32_t)k;
+        rec.mu = mu;
+        rec.f = f;
+        rec.theta = th;
+        rec.E0 = e0.E;
+        rec.inf_pr = e0.primal;
+        rec.inf_du = e0.dual;
+        if (!std::isfinite(e0.E)) { status = MDSIP_ERR_NONFINITE; P->log.push_back(rec); break; }
+        if (e0.E <= o.tol) { status = MDSIP_OK; P->log.push_back(rec); break; }
+        if (k >= o.max_iter) { status = MDSIP_MAX_ITER; P->log.push_back(rec); break; }
+        if (o.time_limit_s > 0) {
+            const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+            if (el > o.time_limit_s) { status = MDSIP_TIMEOUT; P->log.push_back(rec); break; }
+        }
+        // A.3 barrier update
+        while (true) {
+            const double Emu = kkt_error(P, mu).E;
+            if (Emu <= o.kappa_eps * mu) {
+                const double mu_new = std::max(o.tol / 10.0, std::min(o.kappa_mu * mu, std::pow(mu, o.theta_mu)));
+                if (mu_new == mu) break;
+                mu = mu_new;
+                tau = std::max(o.tau_min, 1.0 - mu);
+                filt.clear();
+                if (k == 0) continue;
+            }
+            break;
+        }
+        rec.mu = mu;
+        const double logsum = h[SC_E + 6];
+        // A.4 direction with inertia correction
+        double dw = 0.0, dc = 0.0;
+        auto record = [&](const Inertia &in) {
+            if (rec.n_ic < MDSIP_MAX_IC) {
+                rec.ic_dw[rec.n_ic] = dw;
+                rec.ic_dc[rec.n_ic] = dc;
+                rec.ic_inertia[rec.n_ic][0] = (int32_t)in.pos;
+                rec.ic_inertia[rec.n_ic][1] = (int32_t)in.neg;
+                rec.ic_inertia[rec.n_ic][2] = (int32_t)in.zero;
+            }
+            rec.n_ic++;
+        };
+        Inertia in = factor_attempt(P, dw, dc);
+        record(in);
+        bool ic_failed = false;
+        if (!(in == target)) {
+            if (in.zero > 0) dc = o.dc_bar * std::pow(mu, o.kappa_c);
+            dw = dw_last == 0.0 ? o.dw0 : std::max(o.dw_min, o.kw_minus * dw_last);
+            while (true) {
+                in = factor_attempt(P, dw, dc);
+                record(in);
+                if (in == target) { dw_last = dw; break; }
+                dw = dw_last == 0.0 ? o.kw_plus_bar * dw : o.kw_plus * dw;
+                if (dw > o.dw_max) { ic_failed = true; break; }
+            }
+        }
+        if (rec.n_ic > MDSIP_MAX_IC) rec.n_ic = MDSIP_MAX_IC;
+        if (ic_failed) { status = MDSIP_ERR_INERTIA; P->log.push_back(rec); break; }
+        solve_direction(P, mu, dw);
+        // A.5 line search
+        P->V.step_scalars(P->I, P->Dir, P->grad, tau, mu, sc + SC_STEP);
+        P->sync_scalars();
+        {
+            float a = 0;
+            cudaEventElapsedTime(&a, P->ev[3], P->ev[4]);
+            P->stats.t_solve_ms += a;
+        }
+        const double alpha_max = std::min(1.0, h[SC_STEP + 0]);
+        const double alpha_z = std::min(1.0, h[SC_STEP + 1]);
+        const double gphi = h[SC_STEP + 2];
+        const double phi_k = f - mu * logsum;
+        const double th_k = th;
+        double a_min;
+        if (gphi < 0 && th_k <= theta_min)
+            a_min = o.gamma_alpha * std::min({o.gamma_theta, o.gamma_phi * th_k / (-gphi),
+                                              o.delta * std::pow(th_k, o.s_theta) / std::pow(-gphi, o.s_phi)});
+        else if (gphi < 0)
+            a_min = o.gamma_alpha * std::min(o.gamma_theta, o.gamma_phi * th_k / (-gphi));
+        else
+            a_min = o.gamma_alpha * o.gamma_theta;
+        double alpha = alpha_max;
+        int64_t n_ls = 0;
+        bool accepted = false, ftype = false, armijo = false;
+        double f_t = 0, th_t = 0;
+        MDSIP_CUDA(cudaEventRecord(P->ev[5], st));
+        while (true) {
+            P->V.trial(P->I, P->Dir, alpha, P->xt, P->dt, sc + SC_TRIAL);
+            P->V.eval_f(P->xt, P->grad_t, sc + SC_TF);
+            P->V.eval_cons(P->xt, P->dt, P->cg_t, P->ch_t, sc + SC_TTHETA);
+            P->sync_scalars();
+            f_t = h[SC_TF];
+            th_t = h[SC_TTHETA];
+            const bool inside = h[SC_TRIAL + 1] == 0.0;
+            const double phi_t = inside ? f_t - mu * h[SC_TRIAL] : INFINITY;
+            ftype = gphi < 0 && alpha * std::pow(-gphi, o.s_phi) > o.delta * std::pow(th_k, o.s_theta);
+            armijo = phi_t <= phi_k + o.eta_phi * alpha * gphi;
+            bool ok = false;
+            if (inside && std::isfinite(phi_t) && std::isfinite(th_t)) {
+                if (th_k <= theta_min && ftype)
+                    ok = armijo;
+                else
+                    ok = th_t <= (1 - o.gamma_theta) * th_k || phi_t <= phi_k - o.gamma_phi * th_k;
+                if (ok) {
+                    ok = th_t < theta_max;
+                    for (auto &fe : filt)
+                        if (th_t >= fe.first && phi_t >= fe.second) ok = false;
+                }
+            }
+            P->stats.n_ls_trials++;
+            if (ok) { accepted = true; break; }
+            n_ls++;
+            alpha *= 0.5;
+            if (alpha < a_min || n_ls >= o.max_ls) break;
+        }
+        {
+            MDSIP_CUDA(cudaEventRecord(P->ev[7], st));
+            MDSIP_CUDA(cudaEventSynchronize(P->ev[7]));
+            float a = 0;
+            cudaEventElapsedTime(&a, P->ev[5], P->ev[7]);
+            P->stats.t_ls_ms += a;
+        }
+        rec.alpha_max = alpha_max;
+        rec.alpha_z = alpha_z;
+        rec.n_ls = (int32_t)n_ls;
+        rec.gphi = gphi;
+        if (!accepted) { status = MDSIP_RESTORATION_NEEDED; P->log.push_back(rec); break; }
+        rec.alpha = alpha;
+        rec.ftype = (ftype && armijo) ? 1 : 0;
+        // A.7 filter augmentation
+        if (!(ftype && armijo))
+            filt.emplace_back((1 - o.gamma_theta) * th_k, phi_k - o.gamma_phi * th_k);
+        // A.6 accept: the trial becomes the iterate
+        swap_trial(P);
+        P->V.accept(P->I, P->Dir, alpha, alpha_z, mu, o.kappa_sigma);
+        f = f_t;
+        th = th_t;
+        P->log.push_back(rec);
+        ++k;
+    }
+    MDSIP_CUDA(cudaEventRecord(P->ev[7], st));
+    MDSIP_CUDA(cudaEventSynchronize(P->ev[7]));
+    float tt = 0;
+    cudaEventElapsedTime(&tt, P->ev[6], P->ev[7]);
+    P->stats.t_total_ms = tt;
+    P->stats.status = status;
+    P->stats.iters = (int32_t)k;
+    P->stats.f = f;
+    P->stats.mu = mu;
+    if (!P->log.empty()) {
+        P->stats.E0 = P->log.back().E0;
+        P->stats.inf_pr = P->log.back().inf_pr;
+        P->stats.inf_du = P->log.back().inf_du;
+    }
+    return status;
+}
+
+// packed layout offsets
+static void packed_offsets(const Dims &D, int64_t off[9]) {
+    const int64_t sizes[8] = {D.n, D.m_I, D.m_E, D.m_I, D.n, D.n, D.m_I, D.m_I};
+    off[0] = 0;
+    for (int i = 0; i < 8; ++i) off[i + 1] = off[i] + sizes[i];
+}
+
+static void copy_packed(Problem *P, double *const dst_or_src[8], const double *packed, double *out,
+                        int mem, bool to_device) {
+    int64_t off[9];
+    packed_offsets(P->D, off);
+    const bool dev = mem == MDSIP_MEM_DEVICE;
+    for (int i = 0; i < 8; ++i) {
+        const int64_t cnt = off[i + 1] - off[i];
+        if (cnt <= 0) continue;
+        if (to_device)
+            MDSIP_CUDA(cudaMemcpyAsync(dst_or_src[i], packed + off[i], cnt * sizeof(double),
+                                       dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                       P->ctx->stream));
+        else
+            MDSIP_CUDA(cudaMemcpyAsync(out + off[i], dst_or_src[i], cnt * sizeof(double),
+                                       dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                       P->ctx->stream));
+    }
+    MDSIP_CUDA(cudaStreamSynchronize(P->ctx->stream));
+}
+
+static void iterate_ptrs(Problem *P, double *p[8]) {
+    p[0] = P->I.x; p[1] = P->I.d; p[2] = P->I.yg; p[3] = P->I.yh;
+    p[4] = P->I.zl; p[5] = P->I.zu; p[6] = P->I.vl; p[7] = P->I.vu;
+}
+
+static void debug_direction(Problem *P, const double *packed, double mu, double dw, double dc,
+                            double *dir_out, int32_t inertia_out[3], int mem) {
+    prepare_path(P);
+    double *ptr[8];
+    iterate_ptrs(P, ptr);
+    copy_packed(P, ptr, packed, nullptr, mem, true);
+    double *sc = P->scal();
+    P->V.eval_f(P->I.x, P->grad, sc + SC_F);
+    P->V.eval_cons(P->I.x, P->I.d, P->cg, P->ch, sc + SC_THETA);
+    eval_derivatives(P);
+    const Inertia in = factor_attempt(P, dw, dc);
+    solve_direction(P, mu, dw);
+    double *dp[8] = {P->Dir.dx, P->Dir.dd, P->Dir.dyg, P->Dir.dyh,
+                     P->Dir.dzl, P->Dir.dzu, P->Dir.dvl, P->Dir.dvu};
+    copy_packed(P, dp, nullptr, dir_out, mem, false);
+    if (inertia_out) {
+        inertia_out[0] = (int32_t)in.pos;
+        inertia_out[1] = (int32_t)in.neg;
+        inertia_out[2] = (int32_t)in.zero;
+    }
+}
+
+static bool set_option(Options &o, const std::string &name, double v, bool is_int) {
+    struct D { const char *n; double *p; };
+    struct I { const char *n; int64_t *p; };
+    const D dopts[] = {{"tol", &o.tol}, {"mu0", &o.mu0}, {"kappa_eps", &o.kappa_eps},
+                       {"kappa_mu", &o.kappa_mu}, {"theta_mu", &o.theta_mu}, {"tau_min", &o.tau_min},
+                       {"s_max", &o.s_max}, {"kappa_1", &o.kappa_1}, {"kappa_2", &o.kappa_2},
+                       {"kappa_sigma", &o.kappa_sigma}, {"gamma_theta", &o.gamma_theta},
+                       {"gamma_phi", &o.gamma_phi}, {"delta", &o.delta}, {"s_theta", &o.s_theta},
+                       {"s_phi", &o.s_phi}, {"eta_phi", &o.eta_phi}, {"gamma_alpha", &o.gamma_alpha},
+                       {"theta_max_fact", &o.theta_max_fact}, {"theta_min_fact", &o.theta_min_fact},
+                       {"dw0", &o.dw0}, {"dw_min", &o.dw_min}, {"dw_max", &o.dw_max},
+                       {"kw_minus", &o.kw_minus}, {"kw_plus", &o.kw_plus}, {"kw_plus_bar", &o.kw_plus_bar},
+                       {"dc_bar", &o.dc_bar}, {"kappa_c", &o.kappa_c}, {"zero_tol", &o.zero_tol},
+                       {"time_limit_s", &o.time_limit_s}};
+    const I iopts[] = {{"max_iter", &o.max_iter}, {"path", &o.path}, {"max_ls", &o.max_ls},
+                       {"refine_max", &o.refine_max}};
+    if (is_int) {
+        for (auto &e : iopts)
+            if (name == e.n) { *e.p = (int64_t)v; return true; }
+    } else {
+        for (auto &e : dopts)
+            if (name == e.n) { *e.p = v; return true; }
+    }
+    return false;
+}
+
+}  // namespace mdsip
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+using namespace mdsip;
+
+// Opaque handles are the internal objects themselves.
+static inline Ctx *C_(mdsip_ctx *c) { return reinterpret_cast<Ctx *>(c); }
+static inline const Ctx *C_(const mdsip_ctx *c) { return reinterpret_cast<const Ctx *>(c); }
+static inline Problem *P_(mdsip_problem *p) { return reinterpret_cast<Problem *>(p); }
+static inline const Problem *P_(const mdsip_problem *p) { return reinterpret_cast<const Problem *>(p); }
+
+template <class F>
+static mdsip_status guarded(Ctx *ctx, F &&fn) {
+    try {
+        fn();
+        return MDSIP_OK;
+    } catch (const Error &e) {
+        if (ctx) ctx->last_error = e.msg;
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        if (ctx) ctx->last_error = "host allocation failed";
+        return MDSIP_ERR_OOM;
+    } catch (...) {
+        if (ctx) ctx->last_error = "unknown error";
+        return MDSIP_ERR_CUDA;
+    }
+}
+
+extern "C" {
+
+const char *mdsip_status_str(mdsip_status s) {
+    switch (s) {
+        case MDSIP_OK: return "OK";
+        case MDSIP_ERR_INVALID_ARG: return "INVALID_ARG";
+        case MDSIP_ERR_CUDA: return "CUDA";
+        case MDSIP_ERR_OOM: return "OOM";
+        case MDSIP_ERR_CALLBACK: return "CALLBACK";
+        case MDSIP_ERR_NONFINITE: return "NONFINITE";
+        case MDSIP_ERR_INERTIA: return "INERTIA";
+        case MDSIP_RESTORATION_NEEDED: return "RESTORATION_NEEDED";
+        case MDSIP_MAX_ITER: return "MAX_ITER";
+        case MDSIP_TIMEOUT: return "TIMEOUT";
+        case MDSIP_ERR_PRECONDITION: return "PRECONDITION";
+        case MDSIP_ERR_DEVICE: return "DEVICE";
+    }
+    return "UNKNOWN";
+}
+
+mdsip_status mdsip_ctx_create(int device, void *stream, const mdsip_alloc_hooks *hooks,
+                              mdsip_ctx **out) {
+    if (!out) return MDSIP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (hooks && (!hooks->alloc || !hooks->free)) return MDSIP_ERR_INVALID_ARG;
+    auto *c = new Ctx();
+    mdsip_status s = guarded(c, [&] {
+        int count = 0;
+        MDSIP_CUDA(cudaGetDeviceCount(&count));
+        MDSIP_REQUIRE(device >= 0 && device < count, MDSIP_ERR_INVALID_ARG, "no such device");
+        DeviceGuard g(device);
+        c->device = device;
+        c->stream = static_cast<cudaStream_t>(stream);
+        if (hooks) {
+            c->hooks = *hooks;
+            c->has_hooks = true;
+        }
+        MDSIP_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
+    });
+    if (s != MDSIP_OK) {
+        delete c;
+        return s;
+    }
+    *out = reinterpret_cast<mdsip_ctx *>(c);
+    return MDSIP_OK;
+}
+
+void mdsip_ctx_destroy(mdsip_ctx *hctx) {
+    if (!hctx) return;
+    Ctx *ctx = C_(hctx);
+    try {
+        DeviceGuard g(ctx->device);
+        if (ctx->scratch) {
+            cudaStreamSynchronize(ctx->stream);
+            ctx->release(ctx->scratch, ctx->scratch_bytes);
+        }
+    } catch (...) {
+    }
+    delete ctx;
+}
+
+const char *mdsip_ctx_last_error(const mdsip_ctx *ctx) { return ctx ? C_(ctx)->last_error.c_str() : ""; }
+
+mdsip_status mdsip_problem_create_synthetic(mdsip_ctx *hctx, const mdsip_synth_data *data, int mem,
+                                            mdsip_problem **out) {
+    if (!hctx || !out) return MDSIP_ERR_INVALID_ARG;
+    Ctx *ctx = C_(hctx);
+    *out = nullptr;
+    return guarded(ctx, [&] {
+        DeviceGuard g(ctx->device);
+        Problem *p = create_synthetic(ctx, data, mem);
+        *out = reinterpret_cast<mdsip_problem *>(p);
+    });
+}
+
+void mdsip_problem_destroy(mdsip_problem *hp) {
+    if (!hp) return;
+    Problem *p = P_(hp);
+    try {
+        DeviceGuard g(p->ctx->device);
+        cudaStreamSynchronize(p->ctx->stream);
+        delete p;
+    } catch (...) {
+    }
+}
+
+mdsip_status mdsip_set_option_int(mdsip_problem *hp, const char *name, int64_t value) {
+    if (!hp || !name) return MDSIP_ERR_INVALID_ARG;
+    Problem *p = P_(hp);
+    return guarded(p->ctx, [&] {
+        MDSIP_REQUIRE(set_option(p->opt, name, (double)value, true), MDSIP_ERR_INVALID_ARG,
+                      std::string("unknown int option ") + name);
+        MDSIP_REQUIRE(p->opt.path >= 0 && p->opt.path <= 2, MDSIP_ERR_INVALID_ARG, "bad path");
+    });
+}
+
+mdsip_status mdsip_set_option_double(mdsip_problem *hp, const char *name, double value) {
+    if (!hp || !name) return MDSIP_ERR_INVALID_ARG;
+    Problem *p = P_(hp);
+    return guarded(p->ctx, [&] {
+        MDSIP_REQUIRE(set_option(p->opt, name, value, false), MDSIP_ERR_INVALID_ARG,
+                      std::string("unknown double option ") + name);
+    });
+}
+
+int64_t mdsip_packed_size(const mdsip_problem *hp) {
+    if (!hp) return 0;
+    const Problem *p = P_(hp);
+    return 3 * p->D.n + 4 * p->D.m_I + p->D.m_E;
+}
+
+mdsip_status mdsip_set_start(mdsip_problem *hp, const double *packed, double mu0, int mem) {
+    if (!hp || !packed) return MDSIP_ERR_INVALID_ARG;
+    Problem *p = P_(hp);
+    return guarded(p->ctx, [&] {
+        DeviceGuard g(p->ctx->device);
+        double *ptr[8];
+        iterate_ptrs(p, ptr);
+        copy_packed(p, ptr, packed, nullptr, mem, true);
+        p->has_start = true;
+        p->start_mu0 = mu0;
+    });
+}
+
+mdsip_status mdsip_solve(mdsip_problem *hp) {
+    if (!hp) return MDSIP_ERR_INVALID_ARG;
+    Problem *p = P_(hp);
+    mdsip_status result = MDSIP_OK;
+    mdsip_status s = guarded(p->ctx, [&] {
+        DeviceGuard g(p->ctx->device);
+        result = run_ipm(p);
+    });
+    if (s != MDSIP_OK) {
+        p->stats.status = s;
+        return s;
+    }
+    return result;
+}
+
+mdsip_status mdsip_get_iterate(mdsip_problem *hp, double *packed, int mem) {
+    if (!hp || !packed) return MDSIP_ERR_INVALID_ARG;
+    Problem *p = P_(hp);
+    return guarded(p->ctx, [&] {
+        DeviceGuard g(p->ctx->device);
+        double *ptr[8];
+        iterate_ptrs(p, ptr);
+        copy_packed(p, ptr, nullptr, packed, mem, false);
+    });
+}
+
+mdsip_status mdsip_get_stats(mdsip_problem *hp, mdsip_stats *out) {
+    if (!hp || !out) return MDSIP_ERR_INVALID_ARG;
+    Problem *p = P_(hp);
+    *out = p->stats;
+    return MDSIP_OK;
+}
+
+mdsip_status mdsip_get_log(mdsip_problem *hp, mdsip_iter_rec *buf, int32_t cap, int32_t *n) {
+    if (!hp || !n) return MDSIP_ERR_INVALID_ARG;
+    Problem *p = P_(hp);
+    *n = (int32_t)p->log.size();
+    if (buf && cap > 0) std::memcpy(buf, p->log.data(), std::min<size_t>(cap, p->log.size()) * sizeof(mdsip_iter_rec));
+    return MDSIP_OK;
+}
+
+mdsip_status mdsip_debug_direction(mdsip_problem *hp, const double *packed, double mu, double dw,
+                                   double dc, int32_t refine, double *dir_out,
+                                   int32_t inertia_out[3], int mem) {
+    if (!hp || !packed || !dir_out) return MDSIP_ERR_INVALID_ARG;
+    Problem *p = P_(hp);
+    (void)refine;
+    return guarded(p->ctx, [&] {
+        DeviceGuard g(p->ctx->device);
+        debug_direction(p, packed, mu, dw, dc, dir_out, inertia_out, mem);
+    });
+}
+
+mdsip_status mdsip_syrk_scaled(mdsip_ctx *hctx, int64_t m, int64_t n, const double *A, int64_t lda,
+                               const double *w, double beta, double *C, int64_t ldc) {
+    if (!hctx) return MDSIP_ERR_INVALID_ARG;
+    Ctx *ctx = C_(hctx);
+    return guarded(ctx, [&] {
+        DeviceGuard g(ctx->device);
+        MDSIP_REQUIRE(m >= 0 && n >= 0 && lda >= n && lda % 2 == 0 && ldc >= n, MDSIP_ERR_INVALID_ARG,
+                      "syrk: bad sizes");
+        MDSIP_REQUIRE(beta == 0.0 || beta == 1.0, MDSIP_ERR_INVALID_ARG, "syrk: beta must be 0 or 1");
+        MDSIP_REQUIRE((reinterpret_cast<uintptr_t>(A) & 15) == 0, MDSIP_ERR_INVALID_ARG,
+                      "syrk: A must be 16-byte aligned");
+        MDSIP_REQUIRE(n == 0 || (A && w && C) || m == 0, MDSIP_ERR_INVALID_ARG, "syrk: null pointer");
+        launch_syrk_fp64(ctx, A, m, n, lda, w, beta, C, ldc);
+    });
+}
+
+mdsip_status mdsip_ldlt_factor(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld, double zero_tol,
+                               double *L, double *Dd, double *Doff, int32_t *perm, int32_t *kind,
+                               int32_t *inertia) {
+    if (!hctx) return MDSIP_ERR_INVALID_ARG;
+    Ctx *ctx = C_(hctx);
+    return guarded(ctx, [&] {
+        DeviceGuard g(ctx->device);
+        MDSIP_REQUIRE(N >= 0 && ld == N, MDSIP_ERR_INVALID_ARG, "ldlt: need ld == N");
+        MDSIP_REQUIRE(inertia, MDSIP_ERR_INVALID_ARG, "ldlt: null inertia");
+        if (N == 0) {
+            MDSIP_CUDA(cudaMemsetAsync(inertia, 0, 3 * sizeof(int32_t), ctx->stream));
+            return;
+        }
+        MDSIP_REQUIRE(S && L && Dd && Doff && perm && kind, MDSIP_ERR_INVALID_ARG, "ldlt: null pointer");
+        const size_t ws = ldlt_scratch_bytes(N) + 64 + 8 * kRedBlocks + 64;
+        char *w = static_cast<char *>(ctx->scratch_at_least(ws));
+        double *partial = reinterpret_cast<double *>(w + ldlt_scratch_bytes(N) + 64);
+        double *maxabs = partial + kRedBlocks;
+        int *err = reinterpret_cast<int *>(w + ldlt_scratch_bytes(N));
+        MDSIP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+        launch_maxabs_lower(ctx->stream, N, S, ld, partial, maxabs);
+        LdltOut o{L, Dd, Doff, perm, kind, inertia};
+        launch_ldlt(ctx->stream, ctx->num_sms, N, S, ld, maxabs, zero_tol, o, w, err);
+        int herr = 0;
+        MDSIP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        MDSIP_CUDA(cudaStreamSynchronize(ctx->stream));
+        MDSIP_REQUIRE(herr == 0, MDSIP_ERR_DEVICE, "ldlt: a bounded device wait expired");
+    });
+}
+
+mdsip_status mdsip_ldlt_solve(mdsip_ctx *hctx, int64_t N, const double *L, const double *Dd,
+                              const double *Doff, const int32_t *perm, int64_t nrhs, double *B,
+                              int64_t ldb) {
+    if (!hctx) return MDSIP_ERR_INVALID_ARG;
+    Ctx *ctx = C_(hctx);
+    return guarded(ctx, [&] {
+        DeviceGuard g(ctx->device);
+        MDSIP_REQUIRE(N >= 0 && nrhs >= 0 && ldb >= N, MDSIP_ERR_INVALID_ARG, "ldlt_solve: bad sizes");
+        launch_ldlt_solve(ctx->stream, N, L, Dd, Doff, perm, nrhs, B, ldb);
+    });
+}
+
+}  // extern "C"

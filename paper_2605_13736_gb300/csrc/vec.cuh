@@ -1,0 +1,63 @@
+// Launch wrappers of the fused vector kernels (vec.cu).
+#pragma once
+#include "internal.cuh"
+
+namespace mdsip {
+
+struct IterView {
+    double *x, *d, *yg, *yh, *zl, *zu, *vl, *vu;
+};
+
+struct DirView {
+    double *dx, *dd, *dyg, *dyh, *dzl, *dzu, *dvl, *dvu;
+};
+
+// All launches on one stream; `partial` holds kRedBlocks x 8 doubles and
+// `colpart` kRedBlocks x n_d doubles of reduction scratch.
+struct VecOps {
+    Dims D;
+    ModelView M;
+    cudaStream_t st;
+    double *partial;
+    double *colpart;
+
+    void eval_f(const double *x, double *grad, double *out_scalar);
+    void eval_cons(const double *x, const double *d, double *cg, double *ch, double *out2);
+    void jac_hess(const double *x, const double *yh, double *Jdh, double *Hss, double *Hdd);
+    void lagrangian_grad(const IterView &I, const double *grad, const double *Jdh, double *ATy,
+                         double *gl);
+    void errors(const IterView &I, const double *gl, const double *cg, const double *ch,
+                double *out7);
+    void newton_diag(const IterView &I, const double *Hss, double dw, double dc, bool want_w,
+                     double *sig_x, double *q, double *sig_d, double *w, double *out6);
+    void rhs_y(const IterView &I, const double *gl, const double *cg, const double *q,
+               const double *w, double mu, double *bt_g, double *u);
+    void rhs_reduced(const IterView &I, const double *gl, const double *ch, const double *sig_d,
+                     const double *ATu, const double *bt_g, double mu, double dw, bool p1,
+                     double *rhs);
+    void dyg_p2(const double *Adx, const double *bt_g, const double *w, double *dyg);
+    void copy(const double *src, double *dst, int64_t n);
+    void backsub(const IterView &I, const DirView &Dir, const double *gl, const double *q,
+                 const double *sig_d, const double *sol_dxd, const double *sol_dyh, double mu,
+                 double dw);
+    void step_scalars(const IterView &I, const DirView &Dir, const double *grad, double tau,
+                      double mu, double *out3);
+    void trial(const IterView &I, const DirView &Dir, double alpha, double *xt, double *dt,
+               double *out2);
+    void accept(const IterView &I, const DirView &Dir, double alpha, double alpha_z, double mu,
+                double ks);
+    void init_x(const double *x0, double k1, double k2, const IterView &I);
+    void init_d(const double *ch, double k1, double k2, const IterView &I);
+};
+
+// Reduced-matrix assembly (assemble.cu).
+// P2:  S = [[Hdd + diag(sig_xd + dw), Jdh^T], [Jdh, -1/(sig_d + dw) - dc]]  (lower, col-major, ld = N)
+//      (the A^T W^-1 A term is added by the SYRK afterwards)
+void launch_assemble_S(cudaStream_t s, const Dims &D, const double *Hdd, const double *sig_xd,
+                       const double *Jdh, const double *sig_d, double dw, double dc, double *S);
+// P1:  M of Eq. (compressed) (lower, col-major, ld = N = n_d + m)
+void launch_assemble_M(cudaStream_t s, const Dims &D, const ModelView &Mv, const double *Hdd,
+                       const double *sig_xd, const double *Jdh, const double *sig_d, const double *q,
+                       double dw, double dc, double *Mat);
+
+}  // namespace mdsip

@@ -1,0 +1,129 @@
+"""Newton-step and whole-solve parity of the GPU path against the oracle.
+
+* direction parity: from the same iterate and shifts, the GPU direction (P1
+  and P2 paths, through mdsip_debug_direction) equals the oracle's solve of
+  the full 4x4 system of Eq. (linsys4x4) to a relative 1e-10, and the GPU's
+  Haynsworth inertia equals the oracle's LDL^T inertia exactly;
+* the benchmark family member 0 (n_d=32, n_s=2000, m_E=1000, m_I=1) and its
+  nonconvex variant: the GPU run has the oracle's iteration count and
+  inertia-correction sequence, and the final objective within 1e-8 relative.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import paper_2605_13736_gb300 as m
+import synth
+from oracle import ipm
+from oracle.model import SynthModel
+from gpu_util import make_ctx, make_problem, pack_dir
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = make_ctx()
+    yield c
+    m.mdsip_ctx_destroy(c)
+
+
+def _point(it):
+    return ipm.Point(it["x"], it["d"], it["yg"], it["yh"], it["zl"], it["zu"], it["vl"], it["vu"])
+
+
+CASES = [
+    # (n_d, m_E, m_I, sigma_a, seed, q_shift)
+    (4, 6, 2, 0.3, 1, 0.1),
+    (5, 40, 1, 0.3, 2, 0.1),
+    (33, 70, 3, 0.1, 3, 0.1),
+    (6, 9, 1, 0.3, 4, -3.0),      # indefinite Q: wrong inertia at dw = 0
+    (70, 130, 7, 0.05, 5, 0.1),   # reduced size 77 (P2) / 207 (P1), several BK tiles
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("path", [m.MDSIP_PATH_P1, m.MDSIP_PATH_P2])
+@pytest.mark.parametrize("dw,dc", [(0.0, 0.0), (1e-4, 0.0), (3.0, 1e-7)])
+def test_direction_parity(ctx, case, path, dw, dc):
+    n_d, m_E, m_I, sa, seed, qs = case
+    inst = synth.make_instance(n_d, m_E, m_I, sa, seed=seed, q_shift=qs)
+    model = SynthModel(inst)
+    it = synth.random_iterate(inst, seed + 100)
+    pt = _point(it)
+    mu = 0.05
+    want = ipm.direction_at(model, pt, mu, dw, dc, "full")
+    prob = make_problem(ctx, inst, path)
+    try:
+        out = np.zeros(m.mdsip_packed_size(prob))
+        inertia = m.mdsip_debug_direction(prob, pt.packed(), mu, dw, dc, out, ctx=ctx)
+    finally:
+        m.mdsip_problem_destroy(prob)
+    assert inertia == tuple(want["inertia"])
+    ref = pack_dir(want)
+    rel = np.linalg.norm(out - ref) / np.linalg.norm(ref)
+    assert rel <= 1e-10, rel
+
+
+def _golden(name):
+    with open(os.path.join(HERE, "golden", name + ".json")) as fh:
+        return json.load(fh)
+
+
+def _inst_for(case):
+    if case["kind"] == "config":
+        return synth.make_config(case["k"])
+    return synth.make_instance(case["n_d"], case["m_E"], case["m_I"], case["sigma_a"],
+                               seed=case["seed"], q_shift=case["q_shift"])
+
+
+@pytest.mark.parametrize("name", ["mds0_full", "mds0_nonconvex_full"])
+@pytest.mark.parametrize("path", [m.MDSIP_PATH_P1, m.MDSIP_PATH_P2])
+def test_solve_matches_oracle_trajectory(ctx, name, path):
+    g = _golden(name)
+    inst = _inst_for(g["case"])
+    prob = make_problem(ctx, inst, path)
+    try:
+        st = m.mdsip_solve(prob, ctx)
+        stats = m.mdsip_get_stats(prob)
+        log = m.mdsip_get_log(prob)
+    finally:
+        m.mdsip_problem_destroy(prob)
+    assert m.STATUS[st] == g["status"] == "OK"
+    assert stats["iters"] == g["iters"]
+    assert stats["E0"] <= 1e-8
+    assert abs(stats["f"] - g["f"]) <= 1e-8 * abs(g["f"])
+    # inertia-correction sequence: every attempt's shift and inertia
+    for rec, grec in zip(log, g["log"]):
+        want = grec.get("ic", [])
+        got = rec["ic"]
+        assert len(got) == len(want), (rec["iter"], got, want)
+        for (dw, dc, inr), (gdw, gdc, ginr) in zip(got, want):
+            assert tuple(inr) == tuple(ginr)
+            assert dw == pytest.approx(gdw, rel=1e-12, abs=0)
+            assert dc == pytest.approx(gdc, rel=1e-12, abs=0)
+
+
+def test_directions_along_oracle_trajectory(ctx):
+    """Directions from the oracle's own iterates of configs[0] (P2 condensed
+    oracle for the iterates; full 4x4 solve for the reference direction)."""
+    inst = synth.make_config(0)
+    model = SynthModel(inst)
+    opt = ipm.Options(linsolve="p2", max_iter=6)
+    r = ipm.solve(model, opt=opt)
+    pt = r["point"]
+    mu = r["mu"]
+    want = ipm.direction_at(model, pt, mu, 0.0, 0.0, "full")
+    for path in (m.MDSIP_PATH_P1, m.MDSIP_PATH_P2):
+        prob = make_problem(ctx, inst, path)
+        try:
+            out = np.zeros(m.mdsip_packed_size(prob))
+            inertia = m.mdsip_debug_direction(prob, pt.packed(), mu, 0.0, 0.0, out, ctx=ctx)
+        finally:
+            m.mdsip_problem_destroy(prob)
+        assert inertia == tuple(want["inertia"])
+        ref = pack_dir(want)
+        assert np.linalg.norm(out - ref) / np.linalg.norm(ref) <= 1e-10

@@ -1,0 +1,131 @@
+"""Kernel-level parity on the GPU, through the C ABI:
+
+* the FP64 condensation product A^T diag(1/w) A against the oracle's
+  definition (numpy product), element by element, at sizes that span several
+  64x64 tiles, split-K and ragged edges;
+* the Bunch-Kaufman LDL^T against the oracle's plain Bunch-Kaufman
+  (oracle.bk): inertia bit-exact, the same 1x1/2x2 pattern and permutation,
+  D to 1e-10, the factorization reconstructs the input, and the solve.
+"""
+import numpy as np
+import pytest
+
+import paper_2605_13736_gb300 as m
+from oracle.bk import bk_ldlt
+from gpu_util import dev, make_ctx, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = make_ctx()
+    yield c
+    m.mdsip_ctx_destroy(c)
+
+
+@pytest.mark.parametrize("mrows,n", [(1, 1), (37, 5), (1000, 64), (1037, 130), (5000, 257), (20011, 64)])
+def test_syrk_matches_definition(ctx, mrows, n):
+    torch = torch_cuda()
+    rng = np.random.default_rng(mrows + n)
+    A = rng.standard_normal((mrows, n)) * 0.1
+    w = rng.uniform(0.5, 4.0, mrows)
+    lda = n + (n & 1)
+    Ap = np.zeros((mrows, lda))
+    Ap[:, :n] = A
+    C0 = rng.standard_normal((n, n))
+    for beta in (0.0, 1.0):
+        Cd = dev(C0.T.copy())             # column-major storage of C0
+        m.mdsip_syrk_scaled(ctx, mrows, n, dev(Ap), lda, dev(w), beta, Cd, n)
+        torch.cuda.synchronize()
+        got = Cd.cpu().numpy().T           # back to row-major view: got[p, q] = C[p][q]
+        want = A.T @ (A / w[:, None]) + beta * C0
+        scale = np.abs(A).T @ (np.abs(A) / w[:, None]) + abs(beta) * np.abs(C0)
+        low = np.tril_indices(n)
+        err = np.abs(got[low] - want[low]) / np.maximum(scale[low], 1e-300)
+        assert err.max() <= 1e-13, err.max()
+        up = np.triu_indices(n, 1)
+        np.testing.assert_array_equal(got[up], C0[up])    # upper triangle untouched
+
+
+def _sym(rng, n, kind):
+    if kind == "rand":
+        a = rng.standard_normal((n, n))
+        return a + a.T
+    if kind == "zero_diag":
+        a = rng.standard_normal((n, n))
+        a = a + a.T
+        np.fill_diagonal(a, 0.0)
+        return a
+    k = n // 2
+    h = rng.standard_normal((k, k))
+    h = h @ h.T / max(k, 1) + 0.1 * np.eye(k)
+    j = rng.standard_normal((n - k, k))
+    out = np.zeros((n, n))
+    out[:k, :k] = h
+    out[k:, :k] = j
+    out[:k, k:] = j.T
+    out[k:, k:] = -1e-3 * np.eye(n - k)
+    return out
+
+
+def _gpu_ldlt(ctx, K):
+    torch = torch_cuda()
+    N = K.shape[0]
+    S = dev(np.asfortranarray(np.tril(K)).T.copy())   # column-major lower triangle
+    L = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+    Dd = torch.zeros(N, dtype=torch.float64, device="cuda")
+    Doff = torch.zeros(N, dtype=torch.float64, device="cuda")
+    perm = torch.zeros(N, dtype=torch.int32, device="cuda")
+    kind = torch.zeros(N, dtype=torch.int32, device="cuda")
+    inertia = torch.zeros(3, dtype=torch.int32, device="cuda")
+    m.mdsip_ldlt_factor(ctx, N, S, N, 1e-14, L, Dd, Doff, perm, kind, inertia)
+    torch.cuda.synchronize()
+    Lh = np.tril(L.cpu().numpy().T)            # L stored column-major
+    return dict(L=Lh, Dd=Dd.cpu().numpy(), Doff=Doff.cpu().numpy(), perm=perm.cpu().numpy(),
+                kind=kind.cpu().numpy(), inertia=tuple(int(v) for v in inertia.cpu().numpy()),
+                dev=(L, Dd, Doff, perm))
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 17, 33, 100, 257, 600, 1033])
+@pytest.mark.parametrize("kind", ["rand", "zero_diag", "saddle"])
+def test_ldlt_matches_oracle_bunch_kaufman(ctx, N, kind):
+    torch = torch_cuda()
+    rng = np.random.default_rng(N * 7 + len(kind))
+    K = _sym(rng, N, kind)
+    g = _gpu_ldlt(ctx, K)
+    o = bk_ldlt(K)
+    assert g["inertia"] == o["inertia"]
+    np.testing.assert_array_equal(g["kind"], o["kind"])
+    np.testing.assert_array_equal(g["perm"], o["perm"])
+    # entries of D carry a forward error of order N u max|K| (u = 2^-53) from
+    # the N rank-1/rank-2 updates each side performs in its own order
+    tol_d = 1e-13 * N * max(1.0, np.abs(K).max())
+    np.testing.assert_allclose(g["Dd"], np.diag(o["D"]), rtol=1e-10, atol=tol_d)
+    np.testing.assert_allclose(g["Doff"], np.concatenate([np.diag(o["D"], -1), [0.0]]), rtol=1e-10, atol=tol_d)
+    D = np.diag(g["Dd"]) + np.diag(g["Doff"][:-1], -1) + np.diag(g["Doff"][:-1], 1)
+    p = g["perm"]
+    R = K[np.ix_(p, p)] - g["L"] @ D @ g["L"].T
+    assert np.abs(R).max() <= 1e-11 * max(1.0, np.abs(K).max()) * max(1, N) ** 0.5
+    if g["inertia"][2] == 0:
+        B = rng.standard_normal((2, N))
+        Bd = dev(B.copy())
+        L, Dd, Doff, perm = g["dev"]
+        m.mdsip_ldlt_solve(ctx, N, L, Dd, Doff, perm, 2, Bd, N)
+        torch.cuda.synchronize()
+        X = Bd.cpu().numpy()
+        for r in range(2):
+            res = K @ X[r] - B[r]
+            assert np.abs(res).max() <= 1e-9 * (np.abs(K).max() * np.abs(X[r]).max() + np.abs(B[r]).max())
+
+
+def test_ldlt_singular_and_edge_cases(ctx):
+    g = _gpu_ldlt(ctx, np.zeros((5, 5)))
+    assert g["inertia"] == (0, 0, 5)
+    g = _gpu_ldlt(ctx, np.array([[0.0, 1.0], [1.0, 0.0]]))
+    assert g["inertia"] == (1, 1, 0) and list(g["kind"]) == [2, 0]
+    d = np.array([3.0, -2.0, 1.0, -5.0, 0.5])
+    g = _gpu_ldlt(ctx, np.diag(d))
+    assert g["inertia"] == (3, 2, 0)
+    np.testing.assert_array_equal(g["perm"], np.arange(5))
+    np.testing.assert_array_equal(g["Dd"], d)
