@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Throughput of the mixed dense-sparse interior-point Newton step on GB300.
+
+A step is one IPM iteration (Section 2.1) on the benchmark family member
+(default 1: n_d=2000, n_s=200000, m_E=100000, m_I=50, plain FP64): model
+evaluation, residuals and norms, diagonal scaling, condensation (the FP64
+A^T W^-1 A product), Bunch-Kaufman LDL^T with inertia (and inertia-correction
+retries), solves, back-substitution, fraction-to-boundary, line-search trials
+and the accept/barrier update.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mdsip|reference]
+
+W warm-up steps run from the default starting point; then exactly K steps run
+from the W-th iterate (warm start), timed with CUDA events on the library's
+stream between barriers.  One full solve to E_0 <= 1e-8 is timed after that
+(solves/s).  `e2e` repeats the K steps through the public API with the
+iterate copied from pinned host memory before each step and back after it.
+With N > 1 (torchrun) every rank solves its own instance (independent
+problems, weak scaling); the value is the sum of steps over the max time.
+`--impl reference` times the CPU oracle on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Newton steps/sec and solves/sec to 1e-8 KKT error, vs plain FP64 GPU path"
+UNIT = "Newton steps/s"
+# FP64 ALU peak of a GB300: 152 SMs x 2 DFMA/clk (4 flop) x 2.07 GHz.  A DFMA
+# microbenchmark reached 1.20 TFLOP/s at ~1.97 GHz on this machine.
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+# DRAM bytes per launch of the FP64 condensation kernel from an ncu capture
+# of the current kernel (profiles/syrk_fp64_mds1.md); None when not captured.
+SYRK_TRAFFIC_BYTES = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mdsip", choices=["mdsip", "reference"])
+    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--no-solve", action="store_true", help="skip the timed full solve")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=2, help="oracle steps in the CPU baseline sample")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# ranks
+# --------------------------------------------------------------------------
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world, backend):
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group(backend=backend)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_scalar(x: float, op: str, world: int, device=None) -> float:
+    """max or sum of a float over ranks (identity for one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                                 f".clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        try:
+            with open(self.path) as fh:
+                for line in fh:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                        rows.append(parts)
+        finally:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# --------------------------------------------------------------------------
+def oracle_steps(inst, warm: int, steps: int):
+    """Time `steps` IPM iterations of the oracle (condensed P2 form) after `warm`."""
+    from oracle import ipm
+    from oracle.model import SynthModel
+    model = SynthModel(inst)
+    opt = ipm.Options(linsolve="p2", max_iter=warm)
+    start, mu = None, None
+    if warm > 0:
+        r = ipm.solve(model, opt=opt)
+        start, mu = r["point"], r["mu"]
+    opt = ipm.Options(linsolve="p2", max_iter=steps)
+    t0 = time.perf_counter()
+    r = ipm.solve(model, opt=opt, start=start, mu0=mu)
+    el = time.perf_counter() - t0
+    return r["iters"], el
+
+
+def workload_name(cfg):
+    import synth
+    p = synth.CONFIGS[cfg]
+    return (f"mds{cfg}: plain FP64 MDS NLP, n_d={p['n_d']}, n_s={2 * p['m_E']}, m_E={p['m_E']}, "
+            f"m_I={p['m_I']}, a_i~N(0,{p['sigma_a']}^2), seed={cfg}")
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import synth
+    inst = synth.make_config(args.config)
+    n, el = oracle_steps(inst, args.warmup, args.steps)
+    value = n / el
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": n, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(n, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(args.config), "path": "P2 (two-stage elimination)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n} IPM iterations of the FP64 numpy/scipy oracle (condensed P2 "
+                                       f"form) after {args.warmup} warm-up iterations"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def run_gpu(args):
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+
+    import paper_2605_13736_gb300 as m
+    import synth
+
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    m.build()
+    # every rank solves its own instance (independent problems)
+    seed = args.config if rank == 0 else 1000 * args.config + rank
+    inst = synth.make_config(args.config, seed=seed)
+    stream = torch.cuda.current_stream().cuda_stream
+    ctx = m.mdsip_ctx_create(local, stream)
+    prob = m.mdsip_problem_create_synthetic(ctx, **m.synth_arrays(inst))
+    psize = m.mdsip_packed_size(prob)
+    try:
+        # warm-up: W steps from the default start
+        m.mdsip_set_option_int(prob, "max_iter", args.warmup, ctx)
+        m.mdsip_solve(prob, ctx)
+        w_stats = m.mdsip_get_stats(prob)
+        packed = torch.empty(psize, dtype=torch.float64, device=dev)
+        m.mdsip_get_iterate(prob, packed, m.MDSIP_MEM_DEVICE, ctx)
+        mu_w = w_stats["mu"]
+        # timed: exactly K steps from the W-th iterate
+        m.mdsip_set_option_int(prob, "max_iter", args.steps, ctx)
+        m.mdsip_set_start(prob, packed, mu_w, m.MDSIP_MEM_DEVICE, ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        launches0 = m.mdsip_launch_count()
+        with ClockSampler(local) as clk:
+            barrier(world)
+            torch.cuda.synchronize()
+            e0.record()
+            st = m.mdsip_solve(prob, ctx)
+            e1.record()
+            torch.cuda.synchronize()
+            barrier(world)
+        launches = m.mdsip_launch_count() - launches0
+        stats = m.mdsip_get_stats(prob)
+        elapsed = e0.elapsed_time(e1) / 1e3
+        steps_done = stats["iters"]
+        t_max = reduce_scalar(elapsed, "max", world, dev)
+        units = reduce_scalar(steps_done, "sum", world, dev)
+        value = units / t_max
+
+        # full solve to 1e-8 from the default start
+        solve = None
+        if not args.no_solve:
+            m.mdsip_set_start(prob, None)
+            m.mdsip_set_option_int(prob, "max_iter", 200, ctx)
+            barrier(world)
+            torch.cuda.synchronize()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record()
+            sst = m.mdsip_solve(prob, ctx)
+            s1.record()
+            torch.cuda.synchronize()
+            ss = m.mdsip_get_stats(prob)
+            sec = s0.elapsed_time(s1) / 1e3
+            sec_max = reduce_scalar(sec, "max", world, dev)
+            solve = {"status": m.STATUS[sst], "iters": ss["iters"], "E0": ss["E0"], "f": ss["f"],
+                     "seconds": sec, "solves_per_s": reduce_scalar(1.0, "sum", world, dev) / sec_max,
+                     "newton_steps_per_s": reduce_scalar(ss["iters"], "sum", world, dev) / sec_max,
+                     "factorizations": ss["n_factorizations"]}
+
+        # end to end through the public API with host buffers
+        host = torch.empty(psize, dtype=torch.float64, pin_memory=True)
+        hview = host.numpy()
+        hview[:] = packed.cpu().numpy()
+        m.mdsip_set_option_int(prob, "max_iter", 1, ctx)
+        mu_e = mu_w
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_e2e = 0
+        for _ in range(args.steps):
+            m.mdsip_set_start(prob, hview, mu_e, m.MDSIP_MEM_HOST, ctx)   # H2D from pinned memory
+            m.mdsip_solve(prob, ctx)
+            m.mdsip_get_iterate(prob, hview, m.MDSIP_MEM_HOST, ctx)       # D2H into pinned memory
+            es = m.mdsip_get_stats(prob)
+            mu_e = es["mu"]
+            n_e2e += es["iters"]
+        torch.cuda.synchronize()
+        e2e_t = time.perf_counter() - t0
+        e2e_max = reduce_scalar(e2e_t, "max", world, dev)
+        e2e_units = reduce_scalar(n_e2e, "sum", world, dev)
+    finally:
+        m.mdsip_problem_destroy(prob)
+        m.mdsip_ctx_destroy(ctx)
+
+    if rank != 0:
+        return
+    D = dict(n_d=inst.n_d, n_s=inst.n_s, m_E=inst.m_E, m_I=inst.m_I)
+    flops = D["n_d"] * (D["n_d"] + 1) / 2 * D["m_E"] * 2.0
+    syrk_ms = stats["t_syrk_ms"] / max(1, stats["n_syrk"])
+    achieved = flops / (syrk_ms / 1e3) / 1e12 if stats["n_syrk"] else None
+    roofline = {"kernel": "k_syrk_fp64 (A^T W^-1 A, FP64 DFMA)", "bound": "alu",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
+                "traffic": SYRK_TRAFFIC_BYTES,
+                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (FP64 is not in MEASURED_PEAKS.json)",
+                "flops_per_launch": flops, "avg_launch_ms": syrk_ms, "launches": stats["n_syrk"],
+                "share_of_step": stats["t_syrk_ms"] / (1e3 * elapsed) if elapsed else None}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        n_cpu, el = oracle_steps(inst, 0, args.cpu_steps)
+        cpu = {"value": n_cpu / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{n_cpu} IPM iterations from the default start of the FP64 numpy/scipy oracle "
+                         f"(condensed P2 form, multithreaded BLAS) on the same instance"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / max(1, steps_done),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(args.config), "path": "P2 (two-stage elimination)",
+                   "reduced_N": D["n_d"] + D["m_I"], "steps_timed": steps_done, "status": m.STATUS[st],
+                   "l2": "no flush: every step streams A (m_E x n_d FP64 = "
+                         f"{D['m_E'] * D['n_d'] * 8 / 1e9:.2f} GB) > 135 MB L2",
+                   "parallelism": f"replicas x{world} (independent instances)"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_units / e2e_max, "unit": UNIT, "h2d_bytes_per_step": psize * 8,
+                "d2h_bytes_per_step": psize * 8},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "solve": solve,
+        "phase_ms_per_step": {k: stats[k] / max(1, steps_done) for k in
+                              ("t_condense_ms", "t_factor_ms", "t_solve_ms", "t_ls_ms", "t_syrk_ms",
+                               "t_ldlt_ms")},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

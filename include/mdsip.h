@@ -120,7 +120,8 @@ mdsip_status mdsip_set_option_double(mdsip_problem *p, const char *name, double 
 int64_t mdsip_packed_size(const mdsip_problem *p);
 
 /* Warm start: use `packed` as the starting primal-dual point and mu0 (<= 0:
- * the option mu0).  The point must be strictly inside the finite bounds. */
+ * the option mu0).  The point must be strictly inside the finite bounds.
+ * packed == NULL clears the warm start (next solve starts from x0). */
 mdsip_status mdsip_set_start(mdsip_problem *p, const double *packed, double mu0, int mem);
 
 /* Run the filter line-search interior-point method (Section 2.1) to E_0 <= tol.
@@ -139,6 +140,9 @@ typedef struct {
     double f, E0, inf_pr, inf_du, mu;
     double t_total_ms;
     double t_condense_ms, t_factor_ms, t_solve_ms, t_ls_ms;  /* CUDA-event phase times */
+    double t_syrk_ms, t_ldlt_ms;  /* CUDA-event time of the condensation-product and the
+                                     LDL^T kernels alone (stream of the launches)        */
+    int32_t n_syrk, n_ldlt;       /* launches of those kernels                          */
 } mdsip_stats;
 mdsip_status mdsip_get_stats(mdsip_problem *p, mdsip_stats *out);
 
@@ -165,6 +169,9 @@ mdsip_status mdsip_get_log(mdsip_problem *p, mdsip_iter_rec *buf, int32_t cap, i
 mdsip_status mdsip_debug_direction(mdsip_problem *p, const double *packed, double mu, double dw,
                                    double dc, int32_t refine, double *dir_out,
                                    int32_t inertia_out[3], int mem);
+
+/* Number of CUDA kernels this library has launched in the process so far. */
+int64_t mdsip_launch_count(void);
 
 /* ------------------------------------------------------------------------- */
 /* Kernel-level entry points (device pointers, context stream).              */

@@ -49,7 +49,9 @@ class mdsip_stats(C.Structure):
                 ("f", C.c_double), ("E0", C.c_double), ("inf_pr", C.c_double),
                 ("inf_du", C.c_double), ("mu", C.c_double), ("t_total_ms", C.c_double),
                 ("t_condense_ms", C.c_double), ("t_factor_ms", C.c_double),
-                ("t_solve_ms", C.c_double), ("t_ls_ms", C.c_double)]
+                ("t_solve_ms", C.c_double), ("t_ls_ms", C.c_double),
+                ("t_syrk_ms", C.c_double), ("t_ldlt_ms", C.c_double),
+                ("n_syrk", C.c_int32), ("n_ldlt", C.c_int32)]
 
 
 class mdsip_iter_rec(C.Structure):
@@ -82,6 +84,7 @@ _SIGS = {
                                 C.POINTER(C.c_int32)]),
     "mdsip_debug_direction": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double,
                                         C.c_int32, C.c_void_p, C.POINTER(C.c_int32), C.c_int]),
+    "mdsip_launch_count": (C.c_int64, []),
     "mdsip_syrk_scaled": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int64,
                                     C.c_void_p, C.c_double, C.c_void_p, C.c_int64]),
     "mdsip_ldlt_factor": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_double,
@@ -226,6 +229,10 @@ def mdsip_debug_direction(prob, packed, mu, dw, dc, out, refine=0, mem=MDSIP_MEM
     _check(lib().mdsip_debug_direction(prob, _ptr(packed), float(mu), float(dw), float(dc),
                                        int(refine), _ptr(out), inertia, mem), ctx)
     return tuple(inertia)
+
+
+def mdsip_launch_count() -> int:
+    return lib().mdsip_launch_count()
 
 
 def mdsip_syrk_scaled(ctx, m, n, A, lda, w, beta, Cmat, ldc):

@@ -34,7 +34,12 @@ struct Error {
         if (!(cond)) throw ::mdsip::Error{st, text};                                       \
     } while (0)
 
-#define MDSIP_LAUNCHED() MDSIP_CUDA(cudaGetLastError())
+void count_launch();
+#define MDSIP_LAUNCHED()                   \
+    do {                                   \
+        ::mdsip::count_launch();           \
+        MDSIP_CUDA(cudaGetLastError());    \
+    } while (0)
 
 // ---------------------------------------------------------------------------
 // Context

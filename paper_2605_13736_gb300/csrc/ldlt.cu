@@ -220,9 +220,10 @@ __global__ void __launch_bounds__(kBkThreads) k_bk_factor(BKParams p) {
         if (kp != kk) {
             for (int j = cta; j < k; j += nb) {
                 if (tid == 0) {
+                    // written by another CTA in an earlier step: read through L2
                     double *Lj = p.L + (int64_t)j * N;
-                    const double t = Lj[kk];
-                    Lj[kk] = Lj[kp];
+                    const double t = __ldcg(Lj + kk);
+                    Lj[kk] = __ldcg(Lj + kp);
                     Lj[kp] = t;
                 }
             }
@@ -413,6 +414,7 @@ void launch_ldlt(cudaStream_t s, int num_sms, int64_t N, const double *S, int64_
     void *args[] = {&p};
     MDSIP_CUDA(cudaLaunchCooperativeKernel((const void *)k_bk_factor, dim3(grid), dim3(kBkThreads),
                                            args, smem, s));
+    count_launch();
 }
 
 void launch_ldlt_solve(cudaStream_t s, int64_t N, const double *L, const double *Dd,

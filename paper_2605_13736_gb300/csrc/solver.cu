@@ -11,11 +11,15 @@
 #include <cstring>
 #include <numeric>
 #include <tuple>
+#include <atomic>
 
 #include "internal.cuh"
 #include "vec.cuh"
 
 namespace mdsip {
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------------------
 // Context
@@ -116,7 +120,7 @@ struct Problem {
     double start_mu0 = -1.0;
     std::vector<mdsip_iter_rec> log;
     mdsip_stats stats{};
-    cudaEvent_t ev[8]{};
+    cudaEvent_t ev[12]{};
 
     ~Problem() {
         if (hscal) cudaFreeHost(hscal);
@@ -394,8 +398,10 @@ static Inertia factor_attempt(Problem *P, double dw, double dc) {
     if (p2) {
         launch_assemble_S(st, D, P->bHdd.as<double>(), sig_x + D.n_s, P->bJdh.as<double>(), sig_d, dw, dc,
                           S);
+        MDSIP_CUDA(cudaEventRecord(P->ev[8], st));
         launch_syrk_fp64_ws(st, P->ctx->num_sms, P->Mv.A, D.m_E, D.n_d, D.lda, w, 1.0, S, P->N,
                             P->bsyrk_ws.as<double>());
+        MDSIP_CUDA(cudaEventRecord(P->ev[9], st));
     } else {
         launch_assemble_M(st, D, P->Mv, P->bHdd.as<double>(), sig_x + D.n_s, P->bJdh.as<double>(), sig_d,
                           q, dw, dc, S);
@@ -405,6 +411,7 @@ static Inertia factor_attempt(Problem *P, double dw, double dc) {
     MDSIP_CUDA(cudaMemsetAsync(P->berr.ptr, 0, sizeof(int), st));
     LdltOut o{P->bL.as<double>(), P->bDd.as<double>(), P->bDoff.as<double>(), P->bperm.as<int32_t>(),
               P->bkind.as<int32_t>(), P->binertia.as<int32_t>()};
+    MDSIP_CUDA(cudaEventRecord(P->ev[10], st));
     launch_ldlt(st, P->ctx->num_sms, P->N, S, P->N, sc + SC_MAXABS, P->opt.zero_tol, o,
                 P->bldlt_ws.ptr, P->berr.as<int>());
     MDSIP_CUDA(cudaEventRecord(P->ev[2], st));
@@ -412,12 +419,20 @@ static Inertia factor_attempt(Problem *P, double dw, double dc) {
     MDSIP_CUDA(cudaMemcpyAsync(P->hint + 4, P->berr.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     P->sync_scalars();
     MDSIP_REQUIRE(P->hint[4] == 0, MDSIP_ERR_DEVICE, "LDL^T: a bounded device wait expired");
-    float a = 0, b = 0;
+    float a = 0, b = 0, c = 0;
     cudaEventElapsedTime(&a, P->ev[0], P->ev[1]);
     cudaEventElapsedTime(&b, P->ev[1], P->ev[2]);
     P->stats.t_condense_ms += a;
     P->stats.t_factor_ms += b;
     P->stats.n_factorizations++;
+    if (p2) {
+        cudaEventElapsedTime(&c, P->ev[8], P->ev[9]);
+        P->stats.t_syrk_ms += c;
+        P->stats.n_syrk++;
+    }
+    cudaEventElapsedTime(&c, P->ev[10], P->ev[2]);
+    P->stats.t_ldlt_ms += c;
+    P->stats.n_ldlt++;
     const double *h = P->hscal;
     Inertia in;
     in.pos = (int64_t)h[SC_DIAG + 0] + P->hint[0];
@@ -905,8 +920,13 @@ int64_t mdsip_packed_size(const mdsip_problem *hp) {
 }
 
 mdsip_status mdsip_set_start(mdsip_problem *hp, const double *packed, double mu0, int mem) {
-    if (!hp || !packed) return MDSIP_ERR_INVALID_ARG;
+    if (!hp) return MDSIP_ERR_INVALID_ARG;
     Problem *p = P_(hp);
+    if (!packed) {
+        p->has_start = false;
+        p->start_mu0 = -1.0;
+        return MDSIP_OK;
+    }
     return guarded(p->ctx, [&] {
         DeviceGuard g(p->ctx->device);
         double *ptr[8];
@@ -933,8 +953,13 @@ mdsip_status mdsip_solve(mdsip_problem *hp) {
 }
 
 mdsip_status mdsip_get_iterate(mdsip_problem *hp, double *packed, int mem) {
-    if (!hp || !packed) return MDSIP_ERR_INVALID_ARG;
+    if (!hp) return MDSIP_ERR_INVALID_ARG;
     Problem *p = P_(hp);
+    if (!packed) {
+        p->has_start = false;
+        p->start_mu0 = -1.0;
+        return MDSIP_OK;
+    }
     return guarded(p->ctx, [&] {
         DeviceGuard g(p->ctx->device);
         double *ptr[8];
@@ -969,6 +994,8 @@ mdsip_status mdsip_debug_direction(mdsip_problem *hp, const double *packed, doub
         debug_direction(p, packed, mu, dw, dc, dir_out, inertia_out, mem);
     });
 }
+
+int64_t mdsip_launch_count(void) { return (int64_t)g_launches.load(); }
 
 mdsip_status mdsip_syrk_scaled(mdsip_ctx *hctx, int64_t m, int64_t n, const double *A, int64_t lda,
                                const double *w, double beta, double *C, int64_t ldc) {
