@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-solve", action="store_true", help="skip the timed full solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2, help="oracle steps in the CPU baseline sample")
+    ap.add_argument("--kernel", choices=["syrk", "ldlt"], default=None,
+                    help="time one kernel-level C-ABI call instead of the Newton step")
+    ap.add_argument("--m", type=int, default=100000, help="--kernel syrk: rows of A")
+    ap.add_argument("--n", type=int, default=2000, help="--kernel syrk: columns of A; ldlt: N")
     return ap.parse_args()
 
 
@@ -333,8 +337,73 @@ def run_gpu(args):
     print(json.dumps(line))
 
 
+def run_kernel(args):
+    """Kernel-level timing: `--kernel syrk` (A^T diag(1/w) A, FP64, m x n) or
+    `--kernel ldlt` (Bunch-Kaufman LDL^T of an N x N KKT-like matrix)."""
+    import numpy as np
+    import torch
+
+    import paper_2605_13736_gb300 as m
+    m.build()
+    ctx = m.mdsip_ctx_create(0, torch.cuda.current_stream().cuda_stream)
+    rng = np.random.default_rng(0)
+    times = []
+    try:
+        if args.kernel == "syrk":
+            mm, n = args.m, args.n
+            lda = n + (n & 1)
+            A = torch.zeros((mm, lda), dtype=torch.float64, device="cuda")
+            A[:, :n] = torch.randn((mm, n), dtype=torch.float64, device="cuda") * 0.01
+            w = torch.rand(mm, dtype=torch.float64, device="cuda") + 0.5
+            Cm = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+            flops = n * (n + 1) / 2 * mm * 2.0
+            call = lambda: m.mdsip_syrk_scaled(ctx, mm, n, A, lda, w, 0.0, Cm, n)
+        else:
+            N = args.n
+            k = N * 40 // 41
+            G = rng.standard_normal((k, k))
+            H = G @ G.T / k + 0.1 * np.eye(k)
+            J = rng.standard_normal((N - k, k))
+            K = np.zeros((N, N))
+            K[:k, :k] = H
+            K[k:, :k] = J
+            K[:k, k:] = J.T
+            K[k:, k:] = -np.eye(N - k)
+            S0 = torch.as_tensor(np.tril(K).T.copy()).cuda()
+            S = torch.empty_like(S0)
+            L = torch.empty((N, N), dtype=torch.float64, device="cuda")
+            Dd = torch.empty(N, dtype=torch.float64, device="cuda")
+            Doff = torch.empty_like(Dd)
+            perm = torch.empty(N, dtype=torch.int32, device="cuda")
+            kind = torch.empty_like(perm)
+            inr = torch.empty(3, dtype=torch.int32, device="cuda")
+            flops = N ** 3 / 3.0
+
+            def call():
+                S.copy_(S0)
+                m.mdsip_ldlt_factor(ctx, N, S, N, 1e-14, L, Dd, Doff, perm, kind, inr)
+        for it in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            call()
+            e1.record()
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+    finally:
+        m.mdsip_ctx_destroy(ctx)
+    ms = statistics.median(times)
+    print(json.dumps({"kernel": args.kernel, "m": args.m, "n": args.n, "ms_median": ms,
+                      "ms_all": times, "tflops": flops / (ms / 1e3) / 1e12,
+                      "frac_fp64_peak": flops / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS}))
+
+
 def main():
     args = parse()
+    if args.kernel:
+        run_kernel(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
