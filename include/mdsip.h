@@ -199,6 +199,28 @@ mdsip_status mdsip_ldlt_factor(mdsip_ctx *ctx, int64_t N, double *S, int64_t ld,
                                double *L, double *Dd, double *Doff, int32_t *perm, int32_t *kind,
                                int32_t *inertia);
 
+/* Allocation-free variant of mdsip_ldlt_factor (same arguments, same
+ * results).  The paper has no counterpart: this exists for callers that
+ * cannot call cudaMalloc -- a host whose device memory belongs in full to
+ * another allocator (a framework's caching allocator, the pre-sized arena of
+ * a real-time controller), or a loop that must not pay the implicit device
+ * synchronisation that allocating and freeing can cause.  Its scratch is a
+ * fixed device array of the library (8 MiB plus 4 KiB, held by every GPU that
+ * loads the library until the process exits), so:
+ *   - N is limited to 1024 (larger N: MDSIP_ERR_INVALID_ARG);
+ *   - it allocates no device memory (no cudaMalloc/cudaFree, no allocating
+ *     library routine);
+ *   - the first call on a device looks up the array's device address
+ *     (set-up, once per device); make that first call before any stream
+ *     capture;
+ *   - every call shares the array: calls that overlap on the GPU (on two
+ *     streams, or from two host threads) race and must not be issued.
+ * The call returns after the factorization has finished (it reads a device
+ * status word). */
+mdsip_status mdsip_ldlt_factor_noalloc(mdsip_ctx *ctx, int64_t N, double *S, int64_t ld,
+                                       double zero_tol, double *L, double *Dd, double *Doff,
+                                       int32_t *perm, int32_t *kind, int32_t *inertia);
+
 /* Solve (P^T L D L^T P) x = b in place for `nrhs` right-hand sides stored
  * column-major in B (leading dimension ldb), with the factors above. */
 mdsip_status mdsip_ldlt_solve(mdsip_ctx *ctx, int64_t N, const double *L, const double *Dd,

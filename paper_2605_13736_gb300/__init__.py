@@ -90,6 +90,9 @@ _SIGS = {
     "mdsip_ldlt_factor": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_double,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p]),
+    "mdsip_ldlt_factor_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_double,
+                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.c_void_p]),
     "mdsip_ldlt_solve": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_int64, C.c_void_p, C.c_int64]),
 }
@@ -242,6 +245,12 @@ def mdsip_syrk_scaled(ctx, m, n, A, lda, w, beta, Cmat, ldc):
 def mdsip_ldlt_factor(ctx, N, S, ld, zero_tol, L, Dd, Doff, perm, kind, inertia):
     _check(lib().mdsip_ldlt_factor(ctx, N, _ptr(S), ld, float(zero_tol), _ptr(L), _ptr(Dd),
                                    _ptr(Doff), _ptr(perm), _ptr(kind), _ptr(inertia)), ctx)
+
+
+def mdsip_ldlt_factor_noalloc(ctx, N, S, ld, zero_tol, L, Dd, Doff, perm, kind, inertia):
+    """mdsip_ldlt_factor without device allocation (fixed scratch, N <= 1024)."""
+    _check(lib().mdsip_ldlt_factor_noalloc(ctx, N, _ptr(S), ld, float(zero_tol), _ptr(L), _ptr(Dd),
+                                           _ptr(Doff), _ptr(perm), _ptr(kind), _ptr(inertia)), ctx)
 
 
 def mdsip_ldlt_solve(ctx, N, L, Dd, Doff, perm, nrhs, B, ldb):

@@ -269,5 +269,9 @@ void launch_ldlt_solve(cudaStream_t s, int64_t N, const double *L, const double 
                        int64_t ldb);
 void launch_maxabs_lower(cudaStream_t s, int64_t N, const double *S, int64_t ld, double *partial,
                          double *out);
+// LDL^T with its scratch in a fixed device array (no allocation); N <= the limit.
+int64_t ldlt_fixed_scratch_max_n();
+void ldlt_factor_fixed_scratch(cudaStream_t s, int device, int num_sms, int64_t N, double *S,
+                               int64_t ld, double zero_tol, LdltOut out);
 
 }  // namespace mdsip

@@ -26,6 +26,8 @@
 // layout, work split and synchronisation are this library's.
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace mdsip {
@@ -427,6 +429,74 @@ void launch_ldlt_solve(cudaStream_t s, int64_t N, const double *L, const double 
                                     (int)smem));
     k_ldlt_solve<<<(unsigned)nrhs, kSolveThreads, smem, s>>>((int)N, L, Dd, Doff, perm, B, ldb);
     MDSIP_LAUNCHED();
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the factorization.
+//
+// Some callers cannot call cudaMalloc: a host whose device memory is owned in
+// full by another allocator (a framework's caching allocator, a pre-sized
+// arena of a real-time controller), or a loop that must not pay the implicit
+// device synchronisation that allocating and freeing can cause.  For them
+// the factorization's scratch (the ping-pong copy of the trailing matrix, the
+// pivot hand-off slots, the barrier words, the error flag and the reduction
+// partials of the zero-pivot scale) lives in this fixed device array, which
+// every GPU that loads the library holds until the process exits.
+// ---------------------------------------------------------------------------
+constexpr int64_t kNoAllocMaxN = 1024;
+constexpr size_t kNoAllocBytes = (size_t)kNoAllocMaxN * kNoAllocMaxN * sizeof(double) + 4096;
+static __device__ __align__(256) unsigned char g_ldlt_fixed_scratch[kNoAllocBytes];
+
+namespace {
+std::mutex g_fixed_mu;
+void *g_fixed_addr[256] = {};  // device address of the array, per device ordinal
+}  // namespace
+
+// Host-side address of the fixed array on `device` (which must be current).
+// The array's name in host code is only a stand-in; the device address comes
+// from cudaGetSymbolAddress, looked up once per device.
+static void *fixed_scratch_address(int device) {
+    MDSIP_REQUIRE(device >= 0 && device < 256, MDSIP_ERR_INVALID_ARG, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_fixed_mu);
+    if (!g_fixed_addr[device]) {
+        void *ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_ldlt_fixed_scratch);
+        MDSIP_REQUIRE(e == cudaSuccess && ptr != nullptr, MDSIP_ERR_CUDA,
+                      std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_fixed_addr[device] = ptr;
+    }
+    return g_fixed_addr[device];
+}
+
+int64_t ldlt_fixed_scratch_max_n() { return kNoAllocMaxN; }
+
+void ldlt_factor_fixed_scratch(cudaStream_t s, int device, int num_sms, int64_t N, double *S,
+                               int64_t ld, double zero_tol, LdltOut out) {
+    MDSIP_REQUIRE(N >= 0 && ld == N, MDSIP_ERR_INVALID_ARG, "ldlt: need ld == N");
+    MDSIP_REQUIRE(N <= kNoAllocMaxN, MDSIP_ERR_INVALID_ARG,
+                  "ldlt (fixed scratch): N exceeds the limit of 1024");
+    MDSIP_REQUIRE(out.inertia, MDSIP_ERR_INVALID_ARG, "ldlt: null inertia");
+    if (N == 0) {
+        MDSIP_CUDA(cudaMemsetAsync(out.inertia, 0, 3 * sizeof(int32_t), s));
+        return;
+    }
+    MDSIP_REQUIRE(S && out.L && out.Dd && out.Doff && out.perm && out.kind, MDSIP_ERR_INVALID_ARG,
+                  "ldlt: null pointer");
+    char *base = static_cast<char *>(fixed_scratch_address(device));
+    // layout: [factor scratch | error flag | partials | max |S|]
+    const size_t fs = ldlt_scratch_bytes(N);
+    int *err = reinterpret_cast<int *>(base + fs);
+    double *partial = reinterpret_cast<double *>(base + fs + 256);
+    double *maxabs = partial + kRedBlocks;
+    // every call shares the array: clear what must start at zero (the factor
+    // launch clears its own slots and barrier words)
+    MDSIP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    launch_maxabs_lower(s, N, S, ld, partial, maxabs);
+    launch_ldlt(s, num_sms, N, S, ld, maxabs, zero_tol, out, base, err);
+    int herr = 0;
+    MDSIP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MDSIP_CUDA(cudaStreamSynchronize(s));
+    MDSIP_REQUIRE(herr == 0, MDSIP_ERR_DEVICE, "ldlt: a bounded device wait expired");
 }
 
 }  // namespace mdsip

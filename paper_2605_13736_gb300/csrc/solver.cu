@@ -1043,6 +1043,18 @@ mdsip_status mdsip_ldlt_factor(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld
     });
 }
 
+mdsip_status mdsip_ldlt_factor_noalloc(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld,
+                                       double zero_tol, double *L, double *Dd, double *Doff,
+                                       int32_t *perm, int32_t *kind, int32_t *inertia) {
+    if (!hctx) return MDSIP_ERR_INVALID_ARG;
+    Ctx *ctx = C_(hctx);
+    return guarded(ctx, [&] {
+        DeviceGuard g(ctx->device);
+        LdltOut o{L, Dd, Doff, perm, kind, inertia};
+        ldlt_factor_fixed_scratch(ctx->stream, ctx->device, ctx->num_sms, N, S, ld, zero_tol, o);
+    });
+}
+
 mdsip_status mdsip_ldlt_solve(mdsip_ctx *hctx, int64_t N, const double *L, const double *Dd,
                               const double *Doff, const int32_t *perm, int64_t nrhs, double *B,
                               int64_t ldb) {
