@@ -18,7 +18,11 @@
 //    needs no separate swap phase;
 //  * the CTA that owns the next pivot column computes its column maximum
 //    while updating it, so each pivot step costs exactly one grid barrier;
-//  * the barrier's wait is bounded (error flag instead of a hang).
+//  * the barrier's wait is bounded (error flag instead of a hang);
+//  * GB300 issues FP64 at 1/64 of the FP32 rate, so the only FP64
+//    instructions per trailing element are the update FMAs: magnitudes are
+//    compared as the integer bit patterns of |v| (monotone for IEEE doubles
+//    >= 0), and the rank-1 and rank-2 updates have separate loops.
 //
 // The pivot rule, its comparisons (LAPACK ?sytf2 form: no interchange when
 // |a_kk| >= alpha colmax (colmax / rowmax)) and the first-index tie-breaking
@@ -35,7 +39,6 @@ namespace mdsip {
 namespace {
 
 constexpr int kBkThreads = 512;
-__device__ constexpr double kAlpha = 0.64038820320220756872;  // (1 + sqrt(17)) / 8
 
 struct BKParams {
     int N;
@@ -43,44 +46,64 @@ struct BKParams {
     double *buf0, *buf1;           // ping-pong copies of the trailing matrix (lower, ld)
     double *L, *Dd, *Doff;
     int32_t *perm, *kind, *inertia;
-    double *slot_val;              // [2] column maximum of the next pivot column
+    unsigned long long *slot_bits; // [2] |.| bit pattern of the next pivot column's maximum
     int *slot_idx;                 // [2] its row index
     GridBar bar;
     const double *maxabs;          // max |S| (scale of the zero-pivot test)
     double zero_tol;
 };
 
-// (value, index) arg-max with first-index tie-breaking
-__device__ __forceinline__ void argmax_combine(double &v, int &i, double v2, int i2) {
-    if (v2 > v || (v2 == v && i2 < i)) {
-        v = v2;
+// |v| as an unsigned integer: ordered like |v| for every non-NaN double
+__device__ __forceinline__ unsigned long long absbits(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+}
+
+// (magnitude bits, index) arg-max with first-index tie-breaking, integer ops only
+__device__ __forceinline__ void argmax_combine(unsigned long long &b, int &i, unsigned long long b2, int i2) {
+    if (b2 > b || (b2 == b && i2 < i)) {
+        b = b2;
         i = i2;
     }
 }
 
-__device__ void block_argmax(double &v, int &idx, double *shv, int *shi) {
+// result valid in thread 0
+__device__ void block_argmax(unsigned long long &b, int &idx, unsigned long long *shb, int *shi) {
     for (int o = 16; o > 0; o >>= 1) {
-        double v2 = __shfl_down_sync(0xffffffffu, v, o);
-        int i2 = __shfl_down_sync(0xffffffffu, idx, o);
-        argmax_combine(v, idx, v2, i2);
+        const unsigned long long b2 = __shfl_down_sync(0xffffffffu, b, o);
+        const int i2 = __shfl_down_sync(0xffffffffu, idx, o);
+        argmax_combine(b, idx, b2, i2);
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0) {
-        shv[wid] = v;
+        shb[wid] = b;
         shi[wid] = idx;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) argmax_combine(v, idx, shv[w], shi[w]);
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) argmax_combine(b, idx, shb[w], shi[w]);
     }
+}
+
+__device__ unsigned long long block_maxbits(unsigned long long b, unsigned long long *shb) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long b2 = __shfl_down_sync(0xffffffffu, b, o);
+        b = b2 > b ? b2 : b;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) shb[wid] = b;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = shb[w] > b ? shb[w] : b;
+    return b;
 }
 
 __global__ void __launch_bounds__(kBkThreads) k_bk_factor(BKParams p) {
     extern __shared__ double sh_dyn[];
-    __shared__ double s_redv[32];
+    __shared__ unsigned long long s_redb[32];
     __shared__ int s_redi[32];
-    __shared__ double s_bcast;
+    __shared__ unsigned long long s_bcast;
 
     const int N = p.N;
     const int64_t ld = p.ld;
@@ -89,6 +112,7 @@ __global__ void __launch_bounds__(kBkThreads) k_bk_factor(BKParams p) {
     const int tid = threadIdx.x;
     double *c0 = sh_dyn;        // pivot column(s) of the current step, rows base..N-1
     double *c1 = sh_dyn + N;
+    const double alpha = (1.0 + sqrt(17.0)) / 8.0;
 
     const double scale = __ldcg(p.maxabs);
     const double ztol = p.zero_tol * scale;
@@ -96,47 +120,48 @@ __global__ void __launch_bounds__(kBkThreads) k_bk_factor(BKParams p) {
     // prologue: permutation, column maximum of column 0
     if (cta == 0) {
         for (int i = tid; i < N; i += blockDim.x) p.perm[i] = i;
-        double v = -1.0;
+        unsigned long long b = 0;
         int idx = 0x7fffffff;
-        for (int i = 1 + tid; i < N; i += blockDim.x)
-            argmax_combine(v, idx, fabs(__ldcg(p.buf0 + i)), i);
-        block_argmax(v, idx, s_redv, s_redi);
+        for (int i = 1 + tid; i < N; i += blockDim.x) argmax_combine(b, idx, absbits(__ldcg(p.buf0 + i)), i);
+        block_argmax(b, idx, s_redb, s_redi);
         if (tid == 0) {
-            p.slot_val[0] = v < 0 ? 0.0 : v;
-            p.slot_idx[0] = v < 0 ? 0 : idx;
+            p.slot_bits[0] = b;
+            p.slot_idx[0] = idx == 0x7fffffff ? 0 : idx;
         }
     }
     if (!grid_barrier(p.bar, nb)) return;
 
-    double *cur = p.buf0, *nxt = p.buf1;
+    const double *cur = p.buf0;
+    double *nxt = p.buf1;
     int parity = 0;
     int npos = 0, nneg = 0, nzero = 0;
     int k = 0;
     while (k < N) {
         const double akk = __ldcg(cur + k + (int64_t)k * ld);
         const double absakk = fabs(akk);
-        const double colmax = __ldcg(p.slot_val + parity);
+        const double colmax = __longlong_as_double((long long)__ldcg(p.slot_bits + parity));
         const int imax = __ldcg(p.slot_idx + parity);
         int kstep = 1, kp = k;
-        if (fmax(absakk, colmax) == 0.0 || absakk >= kAlpha * colmax) {
+        if (fmax(absakk, colmax) == 0.0 || absakk >= alpha * colmax) {
             kp = k;
         } else {
             const int r = imax;
             // largest off-diagonal magnitude of row/column r in the trailing block
-            double v = 0.0;
+            unsigned long long b = 0;
             for (int t = tid; t < N - k - 1; t += blockDim.x) {
                 const int idx = k + t;
                 const double a = (idx < r) ? __ldcg(cur + r + (int64_t)idx * ld)
                                            : __ldcg(cur + (idx + 1) + (int64_t)r * ld);
-                v = fmax(v, fabs(a));
+                const unsigned long long ab = absbits(a);
+                b = ab > b ? ab : b;
             }
-            double rowmax = block_max<kBkThreads>(v, s_redv);
-            if (tid == 0) s_bcast = rowmax;
+            b = block_maxbits(b, s_redb);
+            if (tid == 0) s_bcast = b;
             __syncthreads();
-            rowmax = s_bcast;
-            if (absakk >= kAlpha * colmax * (colmax / rowmax)) {
+            const double rowmax = __longlong_as_double((long long)s_bcast);
+            if (absakk >= alpha * colmax * (colmax / rowmax)) {
                 kp = k;
-            } else if (fabs(__ldcg(cur + r + (int64_t)r * ld)) >= kAlpha * rowmax) {
+            } else if (fabs(__ldcg(cur + r + (int64_t)r * ld)) >= alpha * rowmax) {
                 kp = r;
             } else {
                 kp = r;
@@ -230,39 +255,78 @@ __global__ void __launch_bounds__(kBkThreads) k_bk_factor(BKParams p) {
                 }
             }
         }
-        // trailing update of the owned columns; column `base` also yields the
-        // next column maximum
-        int j0 = base + (int)(((unsigned)cta + nb - (unsigned)(base % (int)nb)) % nb);
+        // Trailing update of the owned columns.  In the trailing block
+        // (indices >= base > kk) the interchange only maps row/column kp to kk.
+        const double *__restrict__ C = cur;
+        double *__restrict__ X = nxt;
+        auto src = [&](int i, int j) -> const double * {
+            const int a = (i == kp) ? kk : i;
+            const int b = (j == kp) ? kk : j;
+            return a >= b ? C + a + (int64_t)b * ld : C + b + (int64_t)a * ld;
+        };
+        const int j0 = base + (int)(((unsigned)cta + nb - (unsigned)(base % (int)nb)) % nb);
         for (int j = j0; j < N; j += nb) {
             const int tj = j - base;
-            const double cj0 = c0[tj];
-            const double cj1 = kstep == 2 ? c1[tj] : 0.0;
-            // for rank-2: new = old - [c0_i c1_i] D^-1 [c0_j c1_j]^T
-            const double f0 = kstep == 1 ? cj0 * e11 : cj0 * e11 + cj1 * e21;
-            const double f1 = kstep == 1 ? 0.0 : cj0 * e21 + cj1 * e22;
-            double *col = nxt + (int64_t)j * ld;
-            double mv = -1.0;
-            int mi = 0x7fffffff;
-            const bool track = (j == base);
-            for (int i = j + tid; i < N; i += blockDim.x) {
-                const int ti = i - base;
-                double v = get(i, j) - c0[ti] * f0;
-                if (kstep == 2) v -= c1[ti] * f1;
-                col[i] = v;
-                if (track && i > j) argmax_combine(mv, mi, fabs(v), i);
-            }
-            if (track) {
-                block_argmax(mv, mi, s_redv, s_redi);
-                if (tid == 0) {
-                    p.slot_val[parity ^ 1] = mv < 0 ? 0.0 : mv;
-                    p.slot_idx[parity ^ 1] = mv < 0 ? j : mi;
+            double *__restrict__ col = X + (int64_t)j * ld;
+            // new = old - [c0_i c1_i] D^-1 [c0_j c1_j]^T = old - c0_i f0 - c1_i f1
+            const double f0 = kstep == 1 ? c0[tj] * e11 : c0[tj] * e11 + c1[tj] * e21;
+            const double f1 = kstep == 1 ? 0.0 : c0[tj] * e21 + c1[tj] * e22;
+            const bool simple_col = (j != kp) || kp == kk;
+            if (j == base) {
+                // next pivot column: also its column maximum (integer compares)
+                unsigned long long mb = 0;
+                int mi = 0x7fffffff;
+                for (int i = j + tid; i < N; i += blockDim.x) {
+                    double v = fma(-c0[i - base], f0, __ldcg(src(i, j)));
+                    if (kstep == 2) v = fma(-c1[i - base], f1, v);
+                    col[i] = v;
+                    const unsigned long long ab = absbits(v);
+                    if (i > j && ab > mb) {
+                        mb = ab;
+                        mi = i;
+                    }
                 }
+                block_argmax(mb, mi, s_redb, s_redi);
+                if (tid == 0) {
+                    p.slot_bits[parity ^ 1] = mb;
+                    p.slot_idx[parity ^ 1] = mi == 0x7fffffff ? j : mi;
+                }
+            } else if (kstep == 1 && simple_col && kp == kk) {
+                // common case: no interchange, rank-1, four loads in flight per thread
+                const double *__restrict__ scol = C + (int64_t)j * ld;
+                int i = j + tid;
+                for (; i + 3 * kBkThreads < N; i += 4 * kBkThreads) {
+                    const double v0 = __ldcg(scol + i), v1 = __ldcg(scol + i + kBkThreads),
+                                 v2 = __ldcg(scol + i + 2 * kBkThreads), v3 = __ldcg(scol + i + 3 * kBkThreads);
+                    col[i] = fma(-c0[i - base], f0, v0);
+                    col[i + kBkThreads] = fma(-c0[i + kBkThreads - base], f0, v1);
+                    col[i + 2 * kBkThreads] = fma(-c0[i + 2 * kBkThreads - base], f0, v2);
+                    col[i + 3 * kBkThreads] = fma(-c0[i + 3 * kBkThreads - base], f0, v3);
+                }
+                for (; i < N; i += kBkThreads) col[i] = fma(-c0[i - base], f0, __ldcg(scol + i));
+            } else if (kstep == 1) {
+                int i = j + tid;
+                for (; i + kBkThreads < N; i += 2 * kBkThreads) {
+                    const double v0 = __ldcg(src(i, j)), v1 = __ldcg(src(i + kBkThreads, j));
+                    col[i] = fma(-c0[i - base], f0, v0);
+                    col[i + kBkThreads] = fma(-c0[i + kBkThreads - base], f0, v1);
+                }
+                for (; i < N; i += kBkThreads) col[i] = fma(-c0[i - base], f0, __ldcg(src(i, j)));
+            } else {
+                int i = j + tid;
+                for (; i + kBkThreads < N; i += 2 * kBkThreads) {
+                    const double v0 = __ldcg(src(i, j)), v1 = __ldcg(src(i + kBkThreads, j));
+                    col[i] = fma(-c1[i - base], f1, fma(-c0[i - base], f0, v0));
+                    col[i + kBkThreads] = fma(-c1[i + kBkThreads - base], f1, fma(-c0[i + kBkThreads - base], f0, v1));
+                }
+                for (; i < N; i += kBkThreads)
+                    col[i] = fma(-c1[i - base], f1, fma(-c0[i - base], f0, __ldcg(src(i, j))));
             }
         }
         if (!grid_barrier(p.bar, nb)) return;
-        double *t = cur;
+        const double *t = cur;
         cur = nxt;
-        nxt = t;
+        nxt = const_cast<double *>(t);
         parity ^= 1;
         k += kstep;
     }
@@ -390,7 +454,7 @@ void launch_ldlt(cudaStream_t s, int num_sms, int64_t N, const double *S, int64_
     MDSIP_REQUIRE(ld == N, MDSIP_ERR_INVALID_ARG, "ldlt: leading dimension must equal N");
     p.ld = ld;
     char *tail = w + (size_t)N * (size_t)N * sizeof(double);
-    p.slot_val = reinterpret_cast<double *>(tail);
+    p.slot_bits = reinterpret_cast<unsigned long long *>(tail);
     p.slot_idx = reinterpret_cast<int *>(tail + 16);
     p.bar.count = reinterpret_cast<unsigned int *>(tail + 32);
     p.bar.gen = reinterpret_cast<unsigned int *>(tail + 36);
@@ -412,7 +476,7 @@ void launch_ldlt(cudaStream_t s, int num_sms, int64_t N, const double *S, int64_
     int per_sm = 0;
     MDSIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bk_factor, kBkThreads, smem));
     MDSIP_REQUIRE(per_sm >= 1, MDSIP_ERR_INVALID_ARG, "ldlt: kernel does not fit on an SM");
-    int grid = (int)std::min<int64_t>((int64_t)num_sms, std::max<int64_t>(1, N / 16));
+    int grid = (int)std::min<int64_t>((int64_t)num_sms * per_sm, std::min<int64_t>(num_sms, std::max<int64_t>(1, N / 12)));
     void *args[] = {&p};
     MDSIP_CUDA(cudaLaunchCooperativeKernel((const void *)k_bk_factor, dim3(grid), dim3(kBkThreads),
                                            args, smem, s));

@@ -127,3 +127,74 @@ def test_directions_along_oracle_trajectory(ctx):
         assert inertia == tuple(want["inertia"])
         ref = pack_dir(want)
         assert np.linalg.norm(out - ref) / np.linalg.norm(ref) <= 1e-10
+
+
+@pytest.fixture(scope="module")
+def mds1():
+    return synth.make_config(1)
+
+
+def test_direction_parity_full_size(ctx, mds1):
+    """At the benchmark size (n_d=2000, n_s=200000, m_E=100000, m_I=50; P2 as in
+    bench.py): the GPU direction from a random interior iterate equals the
+    oracle's two-stage direction (itself pinned to the full 4x4 solve on small
+    inputs) to 1e-10, with the same inertia, and satisfies Eq. (linsys4x4)."""
+    inst = mds1
+    model = SynthModel(inst)
+    it = synth.random_iterate(inst, 77)
+    pt = _point(it)
+    mu, dw, dc = 0.01, 0.0, 0.0
+    want = ipm.direction_at(model, pt, mu, dw, dc, "p2")
+    prob = make_problem(ctx, inst, m.MDSIP_PATH_P2)
+    try:
+        out = np.zeros(m.mdsip_packed_size(prob))
+        inertia = m.mdsip_debug_direction(prob, pt.packed(), mu, dw, dc, out, ctx=ctx)
+    finally:
+        m.mdsip_problem_destroy(prob)
+    assert inertia == tuple(want["inertia"]) == (inst.n, inst.m, 0)
+    ref = pack_dir(want)
+    assert np.linalg.norm(out - ref) / np.linalg.norm(ref) <= 1e-10
+    # the GPU direction satisfies the 4x4 system (operator applied block by block)
+    P = ipm.Problem(model)
+    ev = ipm.Evals(P, pt.x, pt.d)
+    sy = ipm.newton_system(P, pt, ev, mu)
+    n_s, n_d, m_E, m_I = sy.dims
+    o = np.cumsum([0, inst.n, m_I, m_E, m_I])
+    dx, dd, dyg, dyh = (out[o[i]:o[i + 1]] for i in range(4))
+    dxs, dxd = dx[:n_s], dx[n_s:]
+    Dh = sy.sig_d + dw
+    res = np.concatenate([
+        (sy.Hss + sy.sig_xs + dw) * dxs + sy.Jsg.T @ dyg + sy.r_xs,
+        sy.Hdd @ dxd + (sy.sig_xd + dw) * dxd + sy.A.T @ dyg + sy.Jdh.T @ dyh + sy.r_xd,
+        sy.Jsg @ dxs + sy.A @ dxd - dc * dyg + sy.r_g,
+        sy.Jdh @ dxd - (1.0 / Dh + dc) * dyh + sy.r_h + sy.r_d / Dh])
+    rhs = np.concatenate([sy.r_xs, sy.r_xd, sy.r_g, sy.r_h + sy.r_d / Dh])
+    assert np.abs(res).max() <= 1e-9 * (1.0 + np.abs(rhs).max())
+
+
+def test_full_size_solve_reaches_tolerance(ctx, mds1):
+    """The benchmark-size solve ends with E_0 <= 1e-8, recomputed by the oracle
+    from the GPU's final iterate (a property that holds at any size)."""
+    inst = mds1
+    prob = make_problem(ctx, inst, m.MDSIP_PATH_P2)
+    try:
+        st = m.mdsip_solve(prob, ctx)
+        stats = m.mdsip_get_stats(prob)
+        packed = np.zeros(m.mdsip_packed_size(prob))
+        m.mdsip_get_iterate(prob, packed, ctx=ctx)
+        log = m.mdsip_get_log(prob)
+    finally:
+        m.mdsip_problem_destroy(prob)
+    assert m.STATUS[st] == "OK"
+    model = SynthModel(inst)
+    P = ipm.Problem(model)
+    n, m_I, m_E = inst.n, inst.m_I, inst.m_E
+    o = np.cumsum([0, n, m_I, m_E, m_I, n, n, m_I, m_I])
+    pt = ipm.Point(*(packed[o[i]:o[i + 1]] for i in range(8)))
+    ev = ipm.Evals(P, pt.x, pt.d)
+    E0 = ipm.kkt_error(P, pt, ev, 0.0, ipm.Options())[0]
+    assert E0 <= 1e-8
+    assert abs(E0 - stats["E0"]) <= 1e-10
+    assert abs(ev.f - stats["f"]) <= 1e-12 * abs(ev.f)
+    for rec in log[:-1]:
+        assert rec["ic"][-1][2] == (inst.n, inst.m, 0)
