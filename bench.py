@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--no-solve", action="store_true", help="skip the timed full solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2, help="oracle steps in the CPU baseline sample")
-    ap.add_argument("--kernel", choices=["syrk", "ldlt"], default=None,
+    ap.add_argument("--variants", default="bf16,tf32",
+                    help="tensor-core precisions also timed on the same instance (comma list, '' for none)")
+    ap.add_argument("--kernel", choices=["syrk", "syrk_bf16", "syrk_tf32", "ldlt"], default=None,
                     help="time one kernel-level C-ABI call instead of the Newton step")
     ap.add_argument("--m", type=int, default=100000, help="--kernel syrk: rows of A")
     ap.add_argument("--n", type=int, default=2000, help="--kernel syrk: columns of A; ldlt: N")
@@ -290,6 +292,55 @@ def run_gpu(args):
         e2e_t = time.perf_counter() - t0
         e2e_max = reduce_scalar(e2e_t, "max", world, dev)
         e2e_units = reduce_scalar(n_e2e, "sum", world, dev)
+
+        # the same K steps and full solve with the tensor-core condensation product
+        variants = {}
+        for name in [v for v in args.variants.split(",") if v]:
+            prec = {"bf16": m.MDSIP_PREC_BF16, "tf32": m.MDSIP_PREC_TF32}[name]
+            m.mdsip_set_option_int(prob, "precision", prec, ctx)
+            m.mdsip_set_option_int(prob, "max_iter", args.steps, ctx)
+            m.mdsip_set_start(prob, packed, mu_w, m.MDSIP_MEM_DEVICE, ctx)
+            m.mdsip_solve(prob, ctx)                     # warm the tensor-core workspace
+            m.mdsip_set_start(prob, packed, mu_w, m.MDSIP_MEM_DEVICE, ctx)
+            barrier(world)
+            torch.cuda.synchronize()
+            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            v0.record()
+            m.mdsip_solve(prob, ctx)
+            v1.record()
+            torch.cuda.synchronize()
+            vs = m.mdsip_get_stats(prob)
+            vt = reduce_scalar(v0.elapsed_time(v1) / 1e3, "max", world, dev)
+            vunits = reduce_scalar(vs["iters"], "sum", world, dev)
+            rec = {"value": vunits / vt, "unit": UNIT, "ms_per_step": 1e3 * vt / max(1, vs["iters"]),
+                   "refine_sweeps_per_step": vs["n_refine"] / max(1, vs["iters"]),
+                   "fp64_fallbacks": vs["n_fp64_fallback"],
+                   "syrk_ms_per_launch": vs["t_syrk_ms"] / max(1, vs["n_syrk"]),
+                   "phase_ms_per_step": {k: vs[k] / max(1, vs["iters"]) for k in
+                                         ("t_condense_ms", "t_factor_ms", "t_refine_ms", "t_ls_ms",
+                                          "t_syrk_ms", "t_ldlt_ms")}}
+            if not args.no_solve:
+                m.mdsip_set_start(prob, None)
+                m.mdsip_set_option_int(prob, "max_iter", 200, ctx)
+                torch.cuda.synchronize()
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record()
+                sst = m.mdsip_solve(prob, ctx)
+                s1.record()
+                torch.cuda.synchronize()
+                ss = m.mdsip_get_stats(prob)
+                sec = reduce_scalar(s0.elapsed_time(s1) / 1e3, "max", world, dev)
+                rec["solve"] = {"status": m.STATUS[sst], "iters": ss["iters"], "E0": ss["E0"], "f": ss["f"],
+                                "seconds": sec,
+                                "solves_per_s": reduce_scalar(1.0, "sum", world, dev) / sec,
+                                "refine_sweeps": ss["n_refine"], "fp64_fallbacks": ss["n_fp64_fallback"],
+                                "f_rel_diff_vs_fp64": (abs(ss["f"] - solve["f"]) / abs(solve["f"])
+                                                        if solve else None)}
+                rec["speedup_vs_fp64_solves"] = (rec["solve"]["solves_per_s"] / solve["solves_per_s"]
+                                                 if solve else None)
+            rec["speedup_vs_fp64_steps"] = rec["value"] / value
+            variants[name] = rec
+            m.mdsip_set_option_int(prob, "precision", m.MDSIP_PREC_FP64, ctx)
     finally:
         m.mdsip_problem_destroy(prob)
         m.mdsip_ctx_destroy(ctx)
@@ -330,6 +381,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "solve": solve,
+        "variants": variants,
         "phase_ms_per_step": {k: stats[k] / max(1, steps_done) for k in
                               ("t_condense_ms", "t_factor_ms", "t_solve_ms", "t_ls_ms", "t_syrk_ms",
                                "t_ldlt_ms")},
@@ -358,6 +410,14 @@ def run_kernel(args):
             Cm = torch.zeros((n, n), dtype=torch.float64, device="cuda")
             flops = n * (n + 1) / 2 * mm * 2.0
             call = lambda: m.mdsip_syrk_scaled(ctx, mm, n, A, lda, w, 0.0, Cm, n)
+        elif args.kernel in ("syrk_bf16", "syrk_tf32"):
+            mm, n = args.m, args.n
+            A = torch.randn((mm, n), dtype=torch.float64, device="cuda") * 0.01
+            w = torch.rand(mm, dtype=torch.float64, device="cuda") + 0.5
+            Cm = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+            flops = n * (n + 1) / 2 * mm * 2.0
+            prec = m.MDSIP_PREC_BF16 if args.kernel == "syrk_bf16" else m.MDSIP_PREC_TF32
+            call = lambda: m.mdsip_syrk_scaled_tc(ctx, mm, n, A, n, w, 0.0, Cm, n, prec)
         else:
             N = args.n
             k = N * 40 // 41

@@ -51,6 +51,12 @@ enum { MDSIP_MEM_HOST = 0, MDSIP_MEM_DEVICE = 1 };
  *   AUTO: P2 when applicable, else P1. */
 enum { MDSIP_PATH_AUTO = 0, MDSIP_PATH_P1 = 1, MDSIP_PATH_P2 = 2 };
 
+/* Arithmetic of the condensation product (option "precision"): FP64 on the
+ * DFMA pipe, or tensor cores (tcgen05) with TF32 / BF16 operands and FP32
+ * accumulation, the Newton direction then refined in FP64 on the unreduced
+ * system. */
+enum { MDSIP_PREC_FP64 = 0, MDSIP_PREC_TF32 = 1, MDSIP_PREC_BF16 = 2 };
+
 typedef struct mdsip_ctx mdsip_ctx;
 typedef struct mdsip_problem mdsip_problem;
 
@@ -105,7 +111,7 @@ mdsip_status mdsip_problem_create_synthetic(mdsip_ctx *ctx, const mdsip_synth_da
 void mdsip_problem_destroy(mdsip_problem *p);
 
 /* Options (Section 2.1 method constants; names as in the oracle):
- *   int:    max_iter, path, max_ls, refine_max
+ *   int:    max_iter, path, max_ls, refine_max, precision (MDSIP_PREC_*)
  *   double: tol, mu0, kappa_eps, kappa_mu, theta_mu, tau_min, s_max, kappa_1,
  *           kappa_2, kappa_sigma, gamma_theta, gamma_phi, delta, s_theta, s_phi,
  *           eta_phi, gamma_alpha, dw0, dw_min, dw_max, kw_minus, kw_plus,
@@ -143,6 +149,10 @@ typedef struct {
     double t_syrk_ms, t_ldlt_ms;  /* CUDA-event time of the condensation-product and the
                                      LDL^T kernels alone (stream of the launches)        */
     int32_t n_syrk, n_ldlt;       /* launches of those kernels                          */
+    int64_t n_refine;             /* iterative-refinement sweeps over the solve         */
+    int32_t n_fp64_fallback;      /* steps re-factored in FP64 after refinement stalled */
+    int32_t precision;            /* MDSIP_PREC_* of the condensation product           */
+    double t_refine_ms;           /* CUDA-event time of the direction solves incl. refinement */
 } mdsip_stats;
 mdsip_status mdsip_get_stats(mdsip_problem *p, mdsip_stats *out);
 
@@ -156,6 +166,9 @@ typedef struct {
     double alpha, alpha_max, alpha_z, gphi;
     double ic_dw[MDSIP_MAX_IC], ic_dc[MDSIP_MAX_IC];
     int32_t ic_inertia[MDSIP_MAX_IC][3]; /* (pos, neg, zero) of the 4x4 matrix    */
+    int32_t n_refine;                   /* refinement sweeps of this step         */
+    int32_t fp64_fallback;              /* 1 if the step was re-factored in FP64  */
+    double refine_res;                  /* final ||b - K u||inf / (||b|| + ||K u||) */
 } mdsip_iter_rec;
 /* Copy up to `cap` per-iteration records; *n receives the number available. */
 mdsip_status mdsip_get_log(mdsip_problem *p, mdsip_iter_rec *buf, int32_t cap, int32_t *n);
@@ -185,6 +198,15 @@ int64_t mdsip_launch_count(void);
  * triangle (p >= q) is written.  beta is 0 or 1.  FP64 throughout. */
 mdsip_status mdsip_syrk_scaled(mdsip_ctx *ctx, int64_t m, int64_t n, const double *A, int64_t lda,
                                const double *w, double beta, double *C, int64_t ldc);
+
+/* The same product on the tensor cores: precision MDSIP_PREC_TF32 or
+ * MDSIP_PREC_BF16 operands A[i][p] * w_i^-1/2 (rounded to that type), FP32
+ * accumulation over K ranges, FP64 sum of the ranges.  Arguments as above
+ * (w > 0 required).  Relative error per entry of order the operand type's
+ * unit roundoff times sum_i |A[i][p] A[i][q]| / w_i. */
+mdsip_status mdsip_syrk_scaled_tc(mdsip_ctx *ctx, int64_t m, int64_t n, const double *A, int64_t lda,
+                                  const double *w, double beta, double *C, int64_t ldc,
+                                  int precision);
 
 /* Bunch-Kaufman LDL^T (Section 2.3) of the symmetric N x N matrix whose lower
  * triangle is in S (column-major, leading dimension ld).  S is overwritten

@@ -19,6 +19,7 @@ from .build import LIB, build  # noqa: F401
 
 MDSIP_MEM_HOST, MDSIP_MEM_DEVICE = 0, 1
 MDSIP_PATH_AUTO, MDSIP_PATH_P1, MDSIP_PATH_P2 = 0, 1, 2
+MDSIP_PREC_FP64, MDSIP_PREC_TF32, MDSIP_PREC_BF16 = 0, 1, 2
 MDSIP_MAX_IC = 16
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "CALLBACK", 5: "NONFINITE",
@@ -51,7 +52,9 @@ class mdsip_stats(C.Structure):
                 ("t_condense_ms", C.c_double), ("t_factor_ms", C.c_double),
                 ("t_solve_ms", C.c_double), ("t_ls_ms", C.c_double),
                 ("t_syrk_ms", C.c_double), ("t_ldlt_ms", C.c_double),
-                ("n_syrk", C.c_int32), ("n_ldlt", C.c_int32)]
+                ("n_syrk", C.c_int32), ("n_ldlt", C.c_int32),
+                ("n_refine", C.c_int64), ("n_fp64_fallback", C.c_int32), ("precision", C.c_int32),
+                ("t_refine_ms", C.c_double)]
 
 
 class mdsip_iter_rec(C.Structure):
@@ -60,7 +63,8 @@ class mdsip_iter_rec(C.Structure):
                 ("inf_pr", C.c_double), ("inf_du", C.c_double), ("alpha", C.c_double),
                 ("alpha_max", C.c_double), ("alpha_z", C.c_double), ("gphi", C.c_double),
                 ("ic_dw", C.c_double * MDSIP_MAX_IC), ("ic_dc", C.c_double * MDSIP_MAX_IC),
-                ("ic_inertia", (C.c_int32 * 3) * MDSIP_MAX_IC)]
+                ("ic_inertia", (C.c_int32 * 3) * MDSIP_MAX_IC),
+                ("n_refine", C.c_int32), ("fp64_fallback", C.c_int32), ("refine_res", C.c_double)]
 
 
 _lib = None
@@ -87,6 +91,8 @@ _SIGS = {
     "mdsip_launch_count": (C.c_int64, []),
     "mdsip_syrk_scaled": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int64,
                                     C.c_void_p, C.c_double, C.c_void_p, C.c_int64]),
+    "mdsip_syrk_scaled_tc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int64,
+                                       C.c_void_p, C.c_double, C.c_void_p, C.c_int64, C.c_int]),
     "mdsip_ldlt_factor": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_double,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p]),
@@ -240,6 +246,11 @@ def mdsip_launch_count() -> int:
 
 def mdsip_syrk_scaled(ctx, m, n, A, lda, w, beta, Cmat, ldc):
     _check(lib().mdsip_syrk_scaled(ctx, m, n, _ptr(A), lda, _ptr(w), float(beta), _ptr(Cmat), ldc), ctx)
+
+
+def mdsip_syrk_scaled_tc(ctx, m, n, A, lda, w, beta, Cmat, ldc, precision):
+    _check(lib().mdsip_syrk_scaled_tc(ctx, m, n, _ptr(A), lda, _ptr(w), float(beta), _ptr(Cmat), ldc,
+                                      int(precision)), ctx)
 
 
 def mdsip_ldlt_factor(ctx, N, S, ld, zero_tol, L, Dd, Doff, perm, kind, inertia):

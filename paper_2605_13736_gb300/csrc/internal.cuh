@@ -104,7 +104,10 @@ struct Options {
            kw_plus_bar = 100.0, dc_bar = 1e-8, kappa_c = 0.25;
     double zero_tol = 1e-14;
     int64_t path = MDSIP_PATH_AUTO;
-    int64_t refine_max = 0;
+    int64_t refine_max = -1;          // -1: 0 for FP64, 30 for tensor-core products
+    int64_t precision = MDSIP_PREC_FP64;
+    double refine_tol = 1e-14;
+    double refine_fallback_tol = 1e-10;
     double time_limit_s = 0.0;
 };
 
@@ -254,6 +257,20 @@ size_t syrk_fp64_scratch_bytes(int64_t m, int64_t n, int num_sms);
 void launch_syrk_fp64_ws(cudaStream_t s, int num_sms, const double *A, int64_t m, int64_t n,
                          int64_t lda, const double *w, double beta, double *C, int64_t ldc,
                          double *work);
+
+// Tensor-core SYRK (syrk_tc.cu)
+struct TcPlan {
+    int tiles, nsplit, slabs_per_split, total_slabs, elems_per_slab;
+    int64_t ldt;
+    size_t work_floats;
+};
+int64_t syrk_tc_ld(int64_t m);
+TcPlan syrk_tc_plan(int64_t m, int64_t n, int num_sms, int precision);
+size_t syrk_tc_workspace_bytes(const TcPlan &pl, int64_t n, int precision);
+void launch_transpose_f32(cudaStream_t s, const double *A, int64_t m, int64_t n, int64_t lda, float *AfT,
+                          int64_t ldt);
+void launch_syrk_tc(cudaStream_t s, int num_sms, int precision, const float *AfT, int64_t m, int64_t n,
+                    const double *w, double beta, double *C, int64_t ldc, void *ws, int *err_dev);
 
 // Bunch-Kaufman LDL^T
 struct LdltOut {

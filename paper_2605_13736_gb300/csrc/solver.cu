@@ -14,6 +14,7 @@
 #include <atomic>
 
 #include "internal.cuh"
+#include "refine.cuh"
 #include "vec.cuh"
 
 namespace mdsip {
@@ -82,6 +83,7 @@ enum : int {
     SC_TF = 19, SC_TTHETA = 20, SC_TCMAX = 21,
     SC_TRIAL = 22,   // 2: sum log s, #non-positive slacks
     SC_MAXABS = 24,
+    SC_REF = 25,     // 4: ||r||inf, ||b||inf, ||K u||inf, ||u||inf
     SC_COUNT = 32
 };
 
@@ -106,6 +108,10 @@ struct Problem {
     DBuf bsig_x, bq, bsig_d, bw, bbt_g, bu, bATu, brhs, bAdx;
     // reduced matrix and factors
     DBuf bS, bL, bDd, bDoff, bperm, bkind, binertia, bldlt_ws, berr, bsyrk_ws;
+    // tensor-core condensation and refinement
+    DBuf bAfT, btc_ws, btc_err, bref_b, bref_u, bref_r, bref_d, btmp_nd2;
+    bool aft_ready = false;
+    int64_t tc_prec = -1;
     DBuf bscal, bpartial, bcolpart;
     double *hscal = nullptr;  // pinned mirror of the scalars
     int32_t *hint = nullptr;  // pinned: inertia (3) + device error flag
@@ -375,6 +381,34 @@ static void prepare_path(Problem *P) {
     const size_t sw = path == MDSIP_PATH_P2 ? syrk_fp64_scratch_bytes(D.m_E, D.n_d, ctx->num_sms) : 0;
     if (sw) P->bsyrk_ws.get<char>(ctx, sw);
     else P->bsyrk_ws.reset();
+    if (path == MDSIP_PATH_P2) {
+        const int64_t nm = D.n + D.m;
+        dvec(ctx, P->bref_b, nm);
+        dvec(ctx, P->bref_u, nm);
+        dvec(ctx, P->bref_r, nm);
+        dvec(ctx, P->bref_d, nm);
+        dvec(ctx, P->btmp_nd2, D.n_d);
+    }
+}
+
+// Tensor-core condensation: FP32 transposed copy of A (once; A is constant
+// for the model family) and the per-call workspace.
+static void prepare_tc(Problem *P) {
+    const int prec = (int)P->opt.precision;
+    if (prec == MDSIP_PREC_FP64 || P->path != MDSIP_PATH_P2) return;
+    Ctx *ctx = P->ctx;
+    const Dims &D = P->D;
+    const TcPlan pl = syrk_tc_plan(D.m_E, D.n_d, ctx->num_sms, prec);
+    if (!P->aft_ready) {
+        float *AfT = P->bAfT.get<float>(ctx, (size_t)std::max<int64_t>(D.n_d, 1) * pl.ldt);
+        launch_transpose_f32(ctx->stream, P->Mv.A, D.m_E, D.n_d, D.lda, AfT, pl.ldt);
+        P->aft_ready = true;
+    }
+    if (P->tc_prec != prec) {
+        P->btc_ws.get<char>(ctx, syrk_tc_workspace_bytes(pl, D.n_d, prec));
+        P->btc_err.get<int>(ctx, 4);
+        P->tc_prec = prec;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -386,7 +420,7 @@ struct Inertia {
     bool operator==(const Inertia &o) const { return pos == o.pos && neg == o.neg && zero == o.zero; }
 };
 
-static Inertia factor_attempt(Problem *P, double dw, double dc) {
+static Inertia factor_attempt(Problem *P, double dw, double dc, bool force_fp64 = false) {
     const Dims &D = P->D;
     cudaStream_t st = P->ctx->stream;
     double *sc = P->scal();
@@ -399,8 +433,14 @@ static Inertia factor_attempt(Problem *P, double dw, double dc) {
         launch_assemble_S(st, D, P->bHdd.as<double>(), sig_x + D.n_s, P->bJdh.as<double>(), sig_d, dw, dc,
                           S);
         MDSIP_CUDA(cudaEventRecord(P->ev[8], st));
-        launch_syrk_fp64_ws(st, P->ctx->num_sms, P->Mv.A, D.m_E, D.n_d, D.lda, w, 1.0, S, P->N,
-                            P->bsyrk_ws.as<double>());
+        if (P->opt.precision != MDSIP_PREC_FP64 && !force_fp64) {
+            MDSIP_CUDA(cudaMemsetAsync(P->btc_err.ptr, 0, sizeof(int), st));
+            launch_syrk_tc(st, P->ctx->num_sms, (int)P->opt.precision, P->bAfT.as<float>(), D.m_E, D.n_d, w,
+                           1.0, S, P->N, P->btc_ws.ptr, P->btc_err.as<int>());
+        } else {
+            launch_syrk_fp64_ws(st, P->ctx->num_sms, P->Mv.A, D.m_E, D.n_d, D.lda, w, 1.0, S, P->N,
+                                P->bsyrk_ws.as<double>());
+        }
         MDSIP_CUDA(cudaEventRecord(P->ev[9], st));
     } else {
         launch_assemble_M(st, D, P->Mv, P->bHdd.as<double>(), sig_x + D.n_s, P->bJdh.as<double>(), sig_d,
@@ -417,8 +457,11 @@ static Inertia factor_attempt(Problem *P, double dw, double dc) {
     MDSIP_CUDA(cudaEventRecord(P->ev[2], st));
     MDSIP_CUDA(cudaMemcpyAsync(P->hint, P->binertia.ptr, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     MDSIP_CUDA(cudaMemcpyAsync(P->hint + 4, P->berr.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    const bool tc = p2 && P->opt.precision != MDSIP_PREC_FP64 && !force_fp64;
+    if (tc) MDSIP_CUDA(cudaMemcpyAsync(P->hint + 5, P->btc_err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     P->sync_scalars();
     MDSIP_REQUIRE(P->hint[4] == 0, MDSIP_ERR_DEVICE, "LDL^T: a bounded device wait expired");
+    MDSIP_REQUIRE(!tc || P->hint[5] == 0, MDSIP_ERR_DEVICE, "tensor-core product: a bounded device wait expired");
     float a = 0, b = 0, c = 0;
     cudaEventElapsedTime(&a, P->ev[0], P->ev[1]);
     cudaEventElapsedTime(&b, P->ev[1], P->ev[2]);
@@ -472,6 +515,96 @@ static void solve_direction(Problem *P, double mu, double dw) {
     MDSIP_CUDA(cudaEventRecord(P->ev[4], st));
 }
 
+struct RefineResult {
+    bool ok;
+    int sweeps;
+    double res;  // ||b - K u||inf / (||b||inf + ||K u||inf)
+};
+
+// Direction through the FP64 residual of the unreduced system, refined with
+// the current factor (path P2).  ok = false when the residual stays above
+// refine_fallback_tol (the caller then re-factors with the FP64 product).
+static RefineResult solve_direction_refined(Problem *P, double mu, double dw, double dc, int max_sweeps) {
+    const Dims &D = P->D;
+    cudaStream_t st = P->ctx->stream;
+    Refiner R{};
+    R.D = D;
+    R.M = P->Mv;
+    R.st = st;
+    R.N = P->N;
+    R.L = P->bL.as<double>();
+    R.Dd = P->bDd.as<double>();
+    R.Doff = P->bDoff.as<double>();
+    R.perm = P->bperm.as<int32_t>();
+    R.q = P->bq.as<double>();
+    R.w = P->bw.as<double>();
+    R.sig_xd = P->bsig_x.as<double>() + D.n_s;
+    R.sig_d = P->bsig_d.as<double>();
+    R.Jdh = P->bJdh.as<double>();
+    R.Hdd = P->bHdd.as<double>();
+    R.bt_g = P->bbt_g.as<double>();
+    R.tmp_m = P->bAdx.as<double>();
+    R.tmp_nd = P->bATu.as<double>();
+    R.tmp_nd2 = P->btmp_nd2.as<double>();
+    R.rhsS = P->brhs.as<double>();
+    R.colpart = P->V.colpart;
+    R.partial = P->V.partial;
+    double *b = P->bref_b.as<double>(), *u = P->bref_u.as<double>(), *r = P->bref_r.as<double>(),
+           *d = P->bref_d.as<double>();
+    const double *h = P->hscal;
+    MDSIP_CUDA(cudaEventRecord(P->ev[3], st));
+    R.rhs(P->I, P->bgl.as<double>(), P->cg, P->ch, R.sig_d, mu, dw, b);
+    R.approx_solve(b, u);
+    RefineResult out{false, 0, INFINITY};
+    double rprev = INFINITY;
+    while (true) {
+        R.residual(b, u, dw, dc, r, P->scal() + SC_REF);
+        P->sync_scalars();
+        const double rinf = h[SC_REF], scale = h[SC_REF + 1] + h[SC_REF + 2];
+        out.res = scale > 0 ? rinf / scale : 0.0;
+        if (!std::isfinite(out.res)) break;
+        if (rinf <= P->opt.refine_tol * scale) break;
+        if (out.sweeps >= max_sweeps || (out.sweeps > 0 && rinf > 0.5 * rprev)) break;
+        R.approx_solve(r, d);
+        R.axpy(D.n + D.m, d, u);
+        out.sweeps++;
+        rprev = rinf;
+    }
+    out.ok = std::isfinite(out.res) && out.res <= P->opt.refine_fallback_tol;
+    R.direction(P->I, P->Dir, u, mu, dw);
+    MDSIP_CUDA(cudaEventRecord(P->ev[4], st));
+    P->stats.n_refine += out.sweeps;
+    return out;
+}
+
+static int refine_sweeps(const Problem *P) {
+    if (P->opt.refine_max >= 0) return (int)P->opt.refine_max;
+    return P->opt.precision == MDSIP_PREC_FP64 ? 0 : 30;
+}
+
+static bool use_refined(const Problem *P) {
+    return P->path == MDSIP_PATH_P2 && (P->opt.precision != MDSIP_PREC_FP64 || refine_sweeps(P) > 0);
+}
+
+// Direction with the current factor; with a tensor-core product that does
+// not refine to tolerance, re-factor with the FP64 product and solve again.
+static RefineResult direction_step(Problem *P, double mu, double dw, double dc) {
+    if (!use_refined(P)) {
+        solve_direction(P, mu, dw);
+        return RefineResult{true, 0, 0.0};
+    }
+    RefineResult rr = solve_direction_refined(P, mu, dw, dc, refine_sweeps(P));
+    if (!rr.ok && P->opt.precision != MDSIP_PREC_FP64) {
+        factor_attempt(P, dw, dc, true);
+        P->stats.n_fp64_fallback++;
+        RefineResult r2 = solve_direction_refined(P, mu, dw, dc, std::max(refine_sweeps(P), 3));
+        r2.sweeps += rr.sweeps;
+        r2.ok = false;  // marks the fallback in the log
+        return r2;
+    }
+    return rr;
+}
+
 // model derivatives and the Lagrangian gradient at the current point
 static void eval_derivatives(Problem *P) {
     P->V.jac_hess(P->I.x, P->I.yh, P->bJdh.as<double>(), P->bHss.as<double>(), P->bHdd.as<double>());
@@ -507,6 +640,7 @@ static void swap_trial(Problem *P) {
 
 static mdsip_status run_ipm(Problem *P) {
     prepare_path(P);
+    prepare_tc(P);
     const Dims &D = P->D;
     const Options &o = P->opt;
     cudaStream_t st = P->ctx->stream;
@@ -515,6 +649,7 @@ static mdsip_status run_ipm(Problem *P) {
     const auto t_start = std::chrono::steady_clock::now();
     P->stats = mdsip_stats{};
     P->stats.path = P->path;
+    P->stats.precision = (P->path == MDSIP_PATH_P2) ? (int32_t)P->opt.precision : MDSIP_PREC_FP64;
     P->log.clear();
     MDSIP_CUDA(cudaEventRecord(P->ev[6], st));
 
@@ -600,7 +735,10 @@ static mdsip_status run_ipm(Problem *P) {
         }
         if (rec.n_ic > MDSIP_MAX_IC) rec.n_ic = MDSIP_MAX_IC;
         if (ic_failed) { status = MDSIP_ERR_INERTIA; P->log.push_back(rec); break; }
-        solve_direction(P, mu, dw);
+        const RefineResult rr = direction_step(P, mu, dw, dc);
+        rec.n_refine = rr.sweeps;
+        rec.fp64_fallback = rr.ok ? 0 : 1;
+        rec.refine_res = rr.res;
         // A.5 line search
         P->V.step_scalars(P->I, P->Dir, P->grad, tau, mu, sc + SC_STEP);
         P->sync_scalars();
@@ -608,6 +746,7 @@ static mdsip_status run_ipm(Problem *P) {
             float a = 0;
             cudaEventElapsedTime(&a, P->ev[3], P->ev[4]);
             P->stats.t_solve_ms += a;
+            P->stats.t_refine_ms += a;
         }
         const double alpha_max = std::min(1.0, h[SC_STEP + 0]);
         const double alpha_z = std::min(1.0, h[SC_STEP + 1]);
@@ -731,8 +870,9 @@ static void iterate_ptrs(Problem *P, double *p[8]) {
 }
 
 static void debug_direction(Problem *P, const double *packed, double mu, double dw, double dc,
-                            double *dir_out, int32_t inertia_out[3], int mem) {
+                            int32_t refine, double *dir_out, int32_t inertia_out[3], int mem) {
     prepare_path(P);
+    prepare_tc(P);
     double *ptr[8];
     iterate_ptrs(P, ptr);
     copy_packed(P, ptr, packed, nullptr, mem, true);
@@ -741,7 +881,15 @@ static void debug_direction(Problem *P, const double *packed, double mu, double 
     P->V.eval_cons(P->I.x, P->I.d, P->cg, P->ch, sc + SC_THETA);
     eval_derivatives(P);
     const Inertia in = factor_attempt(P, dw, dc);
-    solve_direction(P, mu, dw);
+    const int64_t saved = P->opt.refine_max;
+    if (refine > 0) P->opt.refine_max = refine;
+    try {
+        direction_step(P, mu, dw, dc);
+    } catch (...) {
+        P->opt.refine_max = saved;
+        throw;
+    }
+    P->opt.refine_max = saved;
     double *dp[8] = {P->Dir.dx, P->Dir.dd, P->Dir.dyg, P->Dir.dyh,
                      P->Dir.dzl, P->Dir.dzu, P->Dir.dvl, P->Dir.dvu};
     copy_packed(P, dp, nullptr, dir_out, mem, false);
@@ -765,9 +913,10 @@ static bool set_option(Options &o, const std::string &name, double v, bool is_in
                        {"dw0", &o.dw0}, {"dw_min", &o.dw_min}, {"dw_max", &o.dw_max},
                        {"kw_minus", &o.kw_minus}, {"kw_plus", &o.kw_plus}, {"kw_plus_bar", &o.kw_plus_bar},
                        {"dc_bar", &o.dc_bar}, {"kappa_c", &o.kappa_c}, {"zero_tol", &o.zero_tol},
-                       {"time_limit_s", &o.time_limit_s}};
+                       {"time_limit_s", &o.time_limit_s}, {"refine_tol", &o.refine_tol},
+                       {"refine_fallback_tol", &o.refine_fallback_tol}};
     const I iopts[] = {{"max_iter", &o.max_iter}, {"path", &o.path}, {"max_ls", &o.max_ls},
-                       {"refine_max", &o.refine_max}};
+                       {"refine_max", &o.refine_max}, {"precision", &o.precision}};
     if (is_int) {
         for (auto &e : iopts)
             if (name == e.n) { *e.p = (int64_t)v; return true; }
@@ -901,6 +1050,7 @@ mdsip_status mdsip_set_option_int(mdsip_problem *hp, const char *name, int64_t v
         MDSIP_REQUIRE(set_option(p->opt, name, (double)value, true), MDSIP_ERR_INVALID_ARG,
                       std::string("unknown int option ") + name);
         MDSIP_REQUIRE(p->opt.path >= 0 && p->opt.path <= 2, MDSIP_ERR_INVALID_ARG, "bad path");
+        MDSIP_REQUIRE(p->opt.precision >= 0 && p->opt.precision <= 2, MDSIP_ERR_INVALID_ARG, "bad precision");
     });
 }
 
@@ -988,10 +1138,9 @@ mdsip_status mdsip_debug_direction(mdsip_problem *hp, const double *packed, doub
                                    int32_t inertia_out[3], int mem) {
     if (!hp || !packed || !dir_out) return MDSIP_ERR_INVALID_ARG;
     Problem *p = P_(hp);
-    (void)refine;
     return guarded(p->ctx, [&] {
         DeviceGuard g(p->ctx->device);
-        debug_direction(p, packed, mu, dw, dc, dir_out, inertia_out, mem);
+        debug_direction(p, packed, mu, dw, dc, refine, dir_out, inertia_out, mem);
     });
 }
 
@@ -1010,6 +1159,35 @@ mdsip_status mdsip_syrk_scaled(mdsip_ctx *hctx, int64_t m, int64_t n, const doub
                       "syrk: A must be 16-byte aligned");
         MDSIP_REQUIRE(n == 0 || (A && w && C) || m == 0, MDSIP_ERR_INVALID_ARG, "syrk: null pointer");
         launch_syrk_fp64(ctx, A, m, n, lda, w, beta, C, ldc);
+    });
+}
+
+mdsip_status mdsip_syrk_scaled_tc(mdsip_ctx *hctx, int64_t m, int64_t n, const double *A, int64_t lda,
+                                  const double *w, double beta, double *C, int64_t ldc,
+                                  int precision) {
+    if (!hctx) return MDSIP_ERR_INVALID_ARG;
+    Ctx *ctx = C_(hctx);
+    return guarded(ctx, [&] {
+        DeviceGuard g(ctx->device);
+        MDSIP_REQUIRE(m >= 0 && n >= 0 && lda >= n && ldc >= n, MDSIP_ERR_INVALID_ARG, "syrk_tc: bad sizes");
+        MDSIP_REQUIRE(beta == 0.0 || beta == 1.0, MDSIP_ERR_INVALID_ARG, "syrk_tc: beta must be 0 or 1");
+        MDSIP_REQUIRE(precision == MDSIP_PREC_TF32 || precision == MDSIP_PREC_BF16, MDSIP_ERR_INVALID_ARG,
+                      "syrk_tc: precision must be TF32 or BF16");
+        if (n == 0) return;
+        MDSIP_REQUIRE(A && w && C, MDSIP_ERR_INVALID_ARG, "syrk_tc: null pointer");
+        const TcPlan pl = syrk_tc_plan(m, n, ctx->num_sms, precision);
+        const size_t aft = ((size_t)n * pl.ldt * sizeof(float) + 1023) / 1024 * 1024;
+        const size_t wsb = syrk_tc_workspace_bytes(pl, n, precision);
+        char *base = static_cast<char *>(ctx->scratch_at_least(aft + wsb + 256));
+        float *AfT = reinterpret_cast<float *>(base);
+        int *err = reinterpret_cast<int *>(base + aft + wsb);
+        MDSIP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+        launch_transpose_f32(ctx->stream, A, m, n, lda, AfT, pl.ldt);
+        launch_syrk_tc(ctx->stream, ctx->num_sms, precision, AfT, m, n, w, beta, C, ldc, base + aft, err);
+        int herr = 0;
+        MDSIP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        MDSIP_CUDA(cudaStreamSynchronize(ctx->stream));
+        MDSIP_REQUIRE(herr == 0, MDSIP_ERR_DEVICE, "syrk_tc: a bounded device wait expired");
     });
 }
 

@@ -1,0 +1,432 @@
+// Condensation product on the 5th-generation tensor cores (mixed precision):
+//
+//     C[p][q] = beta C[p][q] + sum_i A[i][p] A[i][q] / w_i       (p >= q)
+//
+// computed as C = At At^T with At = (diag(w^-1/2) A)^T in BF16 (kind::f16) or
+// FP32 read as TF32 (kind::tf32), FP32 accumulation in tensor memory, and
+// FP64 summation of the split-K partials.  The FP64 caller wins the accuracy
+// back with iterative refinement of the Newton system.
+//
+// Structure (one CTA = one 128x128 lower-triangle tile x one K range):
+//   * warp 0 lane 0 streams 128-byte-wide K slabs of the two row blocks of
+//     At with TMA (128-byte swizzle) into a 3-stage shared-memory ring;
+//   * warp 1 lane 0 issues tcgen05.mma (M = N = 128, four K steps per slab)
+//     into a 128-column FP32 accumulator in TMEM and releases each stage with
+//     tcgen05.commit on its mbarrier;
+//   * all four warps read the accumulator with tcgen05.ld (32 lanes each)
+//     and write the partial tile, transposed for coalesced reduction.
+// Every mbarrier wait is bounded; on expiry the kernel raises an error flag
+// instead of hanging.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+#include "internal.cuh"
+
+namespace mdsip {
+
+namespace {
+
+constexpr int TC_TILE = 128;
+constexpr int TC_THREADS = 128;
+constexpr int TC_STAGES = 3;
+constexpr int SLAB_BYTES = 128;                        // K bytes per row and stage
+constexpr int TILE_BYTES = TC_TILE * SLAB_BYTES;       // 16 KiB per operand and stage
+constexpr uint32_t TMEM_COLS = 128;
+constexpr long long kWaitLimitCycles = 2000000000LL;   // ~1 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// wait for completion of the phase with the given parity; false on expiry
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > kWaitLimitCycles) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand in the 128-byte-swizzle
+// canonical layout (8-row x 128-byte atoms, atoms 1024 bytes apart along M/N).
+__device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+    d |= (uint64_t)1 << 16;                      // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                      // descriptor version
+    d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulator, A/B of one type, both K-major, M = N = 128.
+template <bool TF32>
+__host__ __device__ constexpr uint32_t instr_desc() {
+    return (1u << 4)                            // D = F32
+           | ((TF32 ? 2u : 1u) << 7)            // A = TF32 / BF16
+           | ((TF32 ? 2u : 1u) << 10)           // B = TF32 / BF16
+           | ((uint32_t)(TC_TILE >> 3) << 17)   // N / 8
+           | ((uint32_t)(TC_TILE >> 4) << 24);  // M / 16
+}
+
+template <bool TF32>
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    constexpr uint32_t idesc = instr_desc<TF32>();
+    if constexpr (TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+            ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+            ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+    }
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tile_of(int t, int &tp, int &tq) {
+    int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= t) ++r;
+    while (r * (r + 1) / 2 > t) --r;
+    tp = r;
+    tq = t - r * (r + 1) / 2;
+}
+
+struct TcArgs {
+    int tiles;            // lower-triangle tiles
+    int slabs_per_split;  // K slabs per split
+    int total_slabs;      // K slabs overall
+    int elems_per_slab;   // 64 (BF16) or 32 (TF32)
+    float *work;          // [split][tile][128 q][128 p] partial tiles
+    int *err;
+};
+
+constexpr size_t kTcSmemBytes = 1024 + 2 * TC_STAGES * TILE_BYTES + 256;
+
+template <bool TF32>
+__global__ void __launch_bounds__(TC_THREADS, 2) k_syrk_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + TC_STAGES * TILE_BYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + 2 * TC_STAGES * TILE_BYTES);
+    uint64_t *empty = full + TC_STAGES;
+    uint64_t *accum = empty + TC_STAGES;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int tp, tq;
+    tile_of(blockIdx.x, tp, tq);
+    const int split = blockIdx.y;
+    const int s0 = split * a.slabs_per_split;
+    const int s1 = min(a.total_slabs, s0 + a.slabs_per_split);
+    const int nslab = max(0, s1 - s0);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // producer: TMA loads of the two 128-row blocks of At for each K slab
+        for (int it = 0; it < nslab; ++it) {
+            const int st = it % TC_STAGES, rnd = it / TC_STAGES;
+            if (!mbar_wait(&empty[st], (rnd & 1) ^ 1)) {
+                atomicExch(a.err, 1);
+                break;
+            }
+            mbar_expect_tx(&full[st], 2 * TILE_BYTES);
+            const int kx = (s0 + it) * a.elems_per_slab;
+            tma_load_2d(sA + st * TILE_BYTES, &tmap, &full[st], kx, tp * TC_TILE);
+            tma_load_2d(sB + st * TILE_BYTES, &tmap, &full[st], kx, tq * TC_TILE);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: 4 K steps of 32 bytes per slab
+        for (int it = 0; it < nslab; ++it) {
+            const int st = it % TC_STAGES, rnd = it / TC_STAGES;
+            if (!mbar_wait(&full[st], rnd & 1)) {
+                atomicExch(a.err, 1);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t ab = smem_u32(sA + st * TILE_BYTES), bb = smem_u32(sB + st * TILE_BYTES);
+#pragma unroll
+            for (int k = 0; k < SLAB_BYTES / 32; ++k)
+                tc_mma<TF32>(tmem, sw128_kmajor_desc(ab + 32 * k), sw128_kmajor_desc(bb + 32 * k),
+                             (it > 0 || k > 0) ? 1u : 0u);
+            tc_commit(&empty[st]);
+        }
+        tc_commit(accum);
+    }
+    __syncwarp();
+    // epilogue: TMEM lanes 32w..32w+31 are rows p of the tile
+    const bool ok = mbar_wait(accum, 0);
+    tc_fence_after();
+    float *out = a.work + ((size_t)split * a.tiles + blockIdx.x) * (TC_TILE * TC_TILE);
+    const int row = warp * 32 + lane;
+    if (ok && nslab > 0) {
+#pragma unroll 1
+        for (int c = 0; c < TC_TILE / 32; ++c) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) out[(size_t)(c * 32 + j) * TC_TILE + row] = __uint_as_float(r[j]);
+        }
+    } else {
+        if (!ok) atomicExch(a.err, 1);
+        for (int c = 0; c < TC_TILE; ++c) out[(size_t)c * TC_TILE + row] = 0.0f;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// AfT[p][i] = (float) A[i][p]  (transposed FP32 copy, zero padded to ldt)
+__global__ void k_transpose_f32(const double *__restrict__ A, int64_t m, int64_t n, int64_t lda,
+                                float *__restrict__ AfT, int64_t ldt) {
+    __shared__ float t[32][33];
+    const int64_t i0 = (int64_t)blockIdx.x * 32, p0 = (int64_t)blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t i = i0 + r, p = p0 + threadIdx.x;
+        t[r][threadIdx.x] = (i < m && p < n) ? (float)A[i * lda + p] : 0.0f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t p = p0 + r, i = i0 + threadIdx.x;
+        if (p < n && i < ldt) AfT[p * ldt + i] = t[threadIdx.x][r];
+    }
+}
+
+// rs[i] = w_i^-1/2 in FP32 (zero beyond m)
+__global__ void k_rsqrt_w(int64_t m, int64_t mp, const double *__restrict__ w, float *__restrict__ rs) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < mp; i += (int64_t)gridDim.x * blockDim.x)
+        rs[i] = i < m ? rsqrtf((float)w[i]) : 0.0f;
+}
+
+// At[p][i] = AfT[p][i] * rs[i], BF16 or FP32, 4 elements per thread
+template <bool TF32>
+__global__ void k_scale_rows(int64_t n, int64_t ldt, const float *__restrict__ AfT, const float *__restrict__ rs,
+                             void *__restrict__ At) {
+    const int64_t total4 = n * ldt / 4;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total4; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = (e * 4) % ldt;
+        const float4 v = reinterpret_cast<const float4 *>(AfT)[e];
+        const float4 s = *reinterpret_cast<const float4 *>(rs + i);
+        const float4 o = make_float4(v.x * s.x, v.y * s.y, v.z * s.z, v.w * s.w);
+        if constexpr (TF32) {
+            reinterpret_cast<float4 *>(At)[e] = o;
+        } else {
+            __nv_bfloat162 lo = __floats2bfloat162_rn(o.x, o.y), hi = __floats2bfloat162_rn(o.z, o.w);
+            uint2 pk;
+            pk.x = *reinterpret_cast<uint32_t *>(&lo);
+            pk.y = *reinterpret_cast<uint32_t *>(&hi);
+            reinterpret_cast<uint2 *>(At)[e] = pk;
+        }
+    }
+}
+
+// C[p][q] = beta C[p][q] + sum_split work[split][tile(p,q)][q % 128][p % 128]   (p >= q)
+__global__ void k_tc_reduce(int64_t n, int tiles, int nsplit, const float *__restrict__ work, double beta,
+                            double *__restrict__ C, int64_t ldc) {
+    for (int64_t q = blockIdx.x; q < n; q += gridDim.x) {
+        const int tq = (int)(q / TC_TILE);
+        for (int64_t p = q + threadIdx.x; p < n; p += blockDim.x) {
+            const int tp = (int)(p / TC_TILE);
+            const int t = tp * (tp + 1) / 2 + tq;
+            const size_t off = (size_t)(q % TC_TILE) * TC_TILE + (size_t)(p % TC_TILE);
+            double s = 0.0;
+            for (int k = 0; k < nsplit; ++k) s += (double)work[((size_t)k * tiles + t) * (TC_TILE * TC_TILE) + off];
+            double *c = C + p + q * ldc;
+            *c = (beta != 0.0 ? *c : 0.0) + s;
+        }
+    }
+}
+
+// driver entry point for tensor-map encoding (no link-time libcuda dependency)
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_fn() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    static cudaError_t status = cudaSuccess;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        status = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+        if (status == cudaSuccess && q == cudaDriverEntryPointSuccess) fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    MDSIP_REQUIRE(fn != nullptr, MDSIP_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
+    return fn;
+}
+
+}  // namespace
+
+int64_t syrk_tc_ld(int64_t m) { return (std::max<int64_t>(m, 1) + 63) / 64 * 64; }
+
+void launch_transpose_f32(cudaStream_t s, const double *A, int64_t m, int64_t n, int64_t lda, float *AfT,
+                          int64_t ldt) {
+    if (n <= 0) return;
+    const dim3 grid((unsigned)ceil_div(ldt, 32), (unsigned)ceil_div(n, 32));
+    k_transpose_f32<<<grid, dim3(32, 8), 0, s>>>(A, m, n, lda, AfT, ldt);
+    MDSIP_LAUNCHED();
+}
+
+TcPlan syrk_tc_plan(int64_t m, int64_t n, int num_sms, int precision) {
+    TcPlan pl{};
+    const int64_t ldt = syrk_tc_ld(m);
+    const int64_t nt = (n + TC_TILE - 1) / TC_TILE;
+    pl.tiles = (int)(nt * (nt + 1) / 2);
+    pl.elems_per_slab = precision == MDSIP_PREC_TF32 ? 32 : 64;
+    pl.total_slabs = (int)(ldt / pl.elems_per_slab);
+    // split-K so that (tile, split) items fill whole waves of two CTAs per SM
+    double best = 0.0;
+    pl.nsplit = 1;
+    for (int s = 1; s <= 64; ++s) {
+        if (s > 1 && pl.total_slabs / s < 8) break;
+        const double waves = (double)pl.tiles * s / (2.0 * num_sms);
+        const double eff = waves / std::ceil(waves);
+        if (eff > best + 0.005) {
+            best = eff;
+            pl.nsplit = s;
+        }
+        if (eff >= 0.985) break;
+    }
+    pl.slabs_per_split = (pl.total_slabs + pl.nsplit - 1) / pl.nsplit;
+    pl.nsplit = (pl.total_slabs + pl.slabs_per_split - 1) / pl.slabs_per_split;  // no empty split
+    pl.ldt = ldt;
+    pl.work_floats = (size_t)pl.nsplit * pl.tiles * TC_TILE * TC_TILE;
+    return pl;
+}
+
+// AfT: n x ldt FP32 transposed copy of A (launch_transpose_f32).  ws holds
+// rs (ldt floats), At (n x ldt BF16/FP32) and the split partials, laid out by
+// syrk_tc_workspace_bytes.  err_dev: device int, must be 0 on entry.
+size_t syrk_tc_workspace_bytes(const TcPlan &pl, int64_t n, int precision) {
+    const size_t esz = precision == MDSIP_PREC_TF32 ? 4 : 2;
+    auto al = [](size_t b) { return (b + 1023) / 1024 * 1024; };
+    return al(pl.ldt * 4) + al((size_t)n * pl.ldt * esz) + al(pl.work_floats * 4);
+}
+
+void launch_syrk_tc(cudaStream_t s, int num_sms, int precision, const float *AfT, int64_t m, int64_t n,
+                    const double *w, double beta, double *C, int64_t ldc, void *ws, int *err_dev) {
+    if (n <= 0) return;
+    MDSIP_REQUIRE(precision == MDSIP_PREC_TF32 || precision == MDSIP_PREC_BF16, MDSIP_ERR_INVALID_ARG,
+                  "syrk_tc: precision must be TF32 or BF16");
+    const bool tf32 = precision == MDSIP_PREC_TF32;
+    const TcPlan pl = syrk_tc_plan(m, n, num_sms, precision);
+    auto al = [](size_t b) { return (b + 1023) / 1024 * 1024; };
+    char *base = static_cast<char *>(ws);
+    float *rs = reinterpret_cast<float *>(base);
+    void *At = base + al(pl.ldt * 4);
+    float *work = reinterpret_cast<float *>(base + al(pl.ldt * 4) + al((size_t)n * pl.ldt * (tf32 ? 4 : 2)));
+
+    k_rsqrt_w<<<std::max(1, std::min(4096, ceil_div(pl.ldt, 256))), 256, 0, s>>>(m, pl.ldt, w, rs);
+    MDSIP_LAUNCHED();
+    const int64_t total4 = n * pl.ldt / 4;
+    const int sg = std::max(1, std::min(num_sms * 16, ceil_div(total4, 256)));
+    if (tf32)
+        k_scale_rows<true><<<sg, 256, 0, s>>>(n, pl.ldt, AfT, rs, At);
+    else
+        k_scale_rows<false><<<sg, 256, 0, s>>>(n, pl.ldt, AfT, rs, At);
+    MDSIP_LAUNCHED();
+
+    // tensor map over At: inner dimension K (ldt elements), outer n rows
+    CUtensorMap tmap;
+    const cuuint64_t gdim[2] = {(cuuint64_t)pl.ldt, (cuuint64_t)n};
+    const cuuint64_t gstride[1] = {(cuuint64_t)pl.ldt * (tf32 ? 4 : 2)};
+    const cuuint32_t box[2] = {(cuuint32_t)pl.elems_per_slab, (cuuint32_t)TC_TILE};
+    const cuuint32_t estride[2] = {1, 1};
+    const CUresult r = encode_fn()(&tmap, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                                   At, gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    MDSIP_REQUIRE(r == CUDA_SUCCESS, MDSIP_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+
+    TcArgs a{};
+    a.tiles = pl.tiles;
+    a.slabs_per_split = pl.slabs_per_split;
+    a.total_slabs = pl.total_slabs;
+    a.elems_per_slab = pl.elems_per_slab;
+    a.work = work;
+    a.err = err_dev;
+    const dim3 grid((unsigned)pl.tiles, (unsigned)pl.nsplit);
+    if (tf32) {
+        MDSIP_CUDA(cudaFuncSetAttribute(k_syrk_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes));
+        k_syrk_tc<true><<<grid, TC_THREADS, kTcSmemBytes, s>>>(tmap, a);
+    } else {
+        MDSIP_CUDA(cudaFuncSetAttribute(k_syrk_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes));
+        k_syrk_tc<false><<<grid, TC_THREADS, kTcSmemBytes, s>>>(tmap, a);
+    }
+    MDSIP_LAUNCHED();
+    k_tc_reduce<<<(unsigned)std::min<int64_t>(n, 4096), 256, 0, s>>>(n, pl.tiles, pl.nsplit, work, beta, C, ldc);
+    MDSIP_LAUNCHED();
+}
+
+}  // namespace mdsip

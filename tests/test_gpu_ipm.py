@@ -198,3 +198,84 @@ def test_full_size_solve_reaches_tolerance(ctx, mds1):
     assert abs(ev.f - stats["f"]) <= 1e-12 * abs(ev.f)
     for rec in log[:-1]:
         assert rec["ic"][-1][2] == (inst.n, inst.m, 0)
+
+
+TC_PRECS = [m.MDSIP_PREC_BF16, m.MDSIP_PREC_TF32]
+
+
+@pytest.mark.parametrize("prec", TC_PRECS)
+@pytest.mark.parametrize("case", CASES[:3] + CASES[4:])
+def test_direction_parity_tensor_core_refined(ctx, case, prec):
+    """Condensation product on the tensor cores (BF16 / TF32, FP32 accumulation),
+    direction refined in FP64 on the unreduced system: equal to the oracle's
+    full 4x4 solve to 1e-10 with the same inertia."""
+    n_d, m_E, m_I, sa, seed, qs = case
+    inst = synth.make_instance(n_d, m_E, m_I, sa, seed=seed, q_shift=qs)
+    model = SynthModel(inst)
+    pt = _point(synth.random_iterate(inst, seed + 100))
+    mu = 0.05
+    want = ipm.direction_at(model, pt, mu, 0.0, 0.0, "full")
+    prob = make_problem(ctx, inst, m.MDSIP_PATH_P2)
+    try:
+        m.mdsip_set_option_int(prob, "precision", prec, ctx)
+        out = np.zeros(m.mdsip_packed_size(prob))
+        inertia = m.mdsip_debug_direction(prob, pt.packed(), mu, 0.0, 0.0, out, refine=40, ctx=ctx)
+    finally:
+        m.mdsip_problem_destroy(prob)
+    assert inertia == tuple(want["inertia"])
+    ref = pack_dir(want)
+    assert np.linalg.norm(out - ref) / np.linalg.norm(ref) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", TC_PRECS)
+def test_tensor_core_solve_matches_oracle_trajectory(ctx, prec):
+    g = _golden("mds0_full")
+    inst = _inst_for(g["case"])
+    prob = make_problem(ctx, inst, m.MDSIP_PATH_P2)
+    try:
+        m.mdsip_set_option_int(prob, "precision", prec, ctx)
+        st = m.mdsip_solve(prob, ctx)
+        stats = m.mdsip_get_stats(prob)
+        log = m.mdsip_get_log(prob)
+    finally:
+        m.mdsip_problem_destroy(prob)
+    assert m.STATUS[st] == "OK" and stats["E0"] <= 1e-8
+    assert stats["precision"] == prec
+    assert stats["iters"] == g["iters"]
+    assert abs(stats["f"] - g["f"]) <= 1e-8 * abs(g["f"])
+    for rec, grec in zip(log, g["log"]):
+        assert [tuple(c[2]) for c in rec["ic"]] == [tuple(c[2]) for c in grec.get("ic", [])]
+    assert sum(r["n_refine"] for r in log) > 0
+
+
+@pytest.mark.parametrize("prec", TC_PRECS)
+def test_tensor_core_full_size(ctx, mds1, prec):
+    """Benchmark size with the tensor-core product: refined direction equal to
+    the oracle's to 1e-10, and the solve ends at E_0 <= 1e-8 (recomputed by the
+    oracle) with the FP64 path's objective."""
+    inst = mds1
+    model = SynthModel(inst)
+    pt = _point(synth.random_iterate(inst, 77))
+    want = ipm.direction_at(model, pt, 0.01, 0.0, 0.0, "p2")
+    prob = make_problem(ctx, inst, m.MDSIP_PATH_P2)
+    try:
+        m.mdsip_set_option_int(prob, "precision", prec, ctx)
+        out = np.zeros(m.mdsip_packed_size(prob))
+        inertia = m.mdsip_debug_direction(prob, pt.packed(), 0.01, 0.0, 0.0, out, refine=40, ctx=ctx)
+        assert inertia == tuple(want["inertia"])
+        ref = pack_dir(want)
+        assert np.linalg.norm(out - ref) / np.linalg.norm(ref) <= 1e-10
+        st = m.mdsip_solve(prob, ctx)
+        stats = m.mdsip_get_stats(prob)
+        packed = np.zeros(m.mdsip_packed_size(prob))
+        m.mdsip_get_iterate(prob, packed, ctx=ctx)
+    finally:
+        m.mdsip_problem_destroy(prob)
+    assert m.STATUS[st] == "OK"
+    P = ipm.Problem(model)
+    n, m_I, m_E = inst.n, inst.m_I, inst.m_E
+    o = np.cumsum([0, n, m_I, m_E, m_I, n, n, m_I, m_I])
+    fin = ipm.Point(*(packed[o[i]:o[i + 1]] for i in range(8)))
+    ev = ipm.Evals(P, fin.x, fin.d)
+    assert ipm.kkt_error(P, fin, ev, 0.0, ipm.Options())[0] <= 1e-8
+    assert abs(ev.f - (-36167.45406568737)) <= 1e-8 * 36167.45406568737

@@ -129,3 +129,30 @@ def test_ldlt_singular_and_edge_cases(ctx):
     assert g["inertia"] == (3, 2, 0)
     np.testing.assert_array_equal(g["perm"], np.arange(5))
     np.testing.assert_array_equal(g["Dd"], d)
+
+
+@pytest.mark.parametrize("prec", [m.MDSIP_PREC_BF16, m.MDSIP_PREC_TF32])
+@pytest.mark.parametrize("mrows,n", [(64, 8), (1000, 64), (5000, 130), (20011, 300)])
+def test_syrk_tensor_core_matches_definition(ctx, prec, mrows, n):
+    """tcgen05 product vs the FP64 definition: error per entry within the
+    operand type's rounding (BF16 2^-8, TF32 2^-10 per product, both operands
+    rounded) plus FP32 accumulation, relative to sum_i |A_ip A_iq| / w_i."""
+    torch = torch_cuda()
+    rng = np.random.default_rng(mrows * 3 + n + prec)
+    A = rng.standard_normal((mrows, n)) * 0.1
+    w = rng.uniform(0.05, 4.0, mrows)
+    C0 = rng.standard_normal((n, n))
+    want = A.T @ (A / w[:, None]) + C0
+    scale = np.abs(A).T @ (np.abs(A) / w[:, None])
+    Cd = dev(C0.T.copy())
+    m.mdsip_syrk_scaled_tc(ctx, mrows, n, dev(A), n, dev(w), 1.0, Cd, n, prec)
+    torch.cuda.synchronize()
+    got = Cd.cpu().numpy().T
+    low = np.tril_indices(n)
+    rel = np.abs(got[low] - want[low]) / scale[low]
+    bound = 2.0 ** -7 if prec == m.MDSIP_PREC_BF16 else 2.0 ** -9
+    assert rel.max() <= bound, rel.max()
+    # and it is a real low-precision product, not an FP64 one in disguise
+    assert rel.max() > 1e-9
+    up = np.triu_indices(n, 1)
+    np.testing.assert_array_equal(got[up], C0.T.T[up])
