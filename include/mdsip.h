@@ -227,7 +227,7 @@ mdsip_status mdsip_ldlt_factor(mdsip_ctx *ctx, int64_t N, double *S, int64_t ld,
  * another allocator (a framework's caching allocator, the pre-sized arena of
  * a real-time controller), or a loop that must not pay the implicit device
  * synchronisation that allocating and freeing can cause.  Its scratch is a
- * fixed device array of the library (8 MiB plus 4 KiB, held by every GPU that
+ * fixed device array of the library (8 MiB plus 16 KiB, held by every GPU that
  * loads the library until the process exits), so:
  *   - N is limited to 1024 (larger N: MDSIP_ERR_INVALID_ARG);
  *   - it allocates no device memory (no cudaMalloc/cudaFree, no allocating

@@ -286,6 +286,10 @@ void launch_ldlt_solve(cudaStream_t s, int64_t N, const double *L, const double 
                        int64_t ldb);
 void launch_maxabs_lower(cudaStream_t s, int64_t N, const double *S, int64_t ld, double *partial,
                          double *out);
+size_t ldlt_solve_scratch_bytes(int64_t N);
+void launch_ldlt_solve_coop(cudaStream_t s, int num_sms, int64_t N, const double *L, const double *Dd,
+                            const double *Doff, const int32_t *perm, int64_t nrhs, double *B, int64_t ldb,
+                            void *scratch, int *err_dev);
 // LDL^T with its scratch in a fixed device array (no allocation); N <= the limit.
 int64_t ldlt_fixed_scratch_max_n();
 void ldlt_factor_fixed_scratch(cudaStream_t s, int device, int num_sms, int64_t N, double *S,

@@ -16,9 +16,13 @@
 //    the trailing matrix is read from the old buffer through the
 //    transposition and written to the other buffer (ping-pong), so a step
 //    needs no separate swap phase;
-//  * the CTA that owns the next pivot column computes its column maximum
-//    while updating it, so each pivot step costs exactly one grid barrier;
-//  * the barrier's wait is bounded (error flag instead of a hang);
+//  * the CTA that owns the next pivot column updates it first, computes its
+//    column maximum and publishes both with a release flag; a CTA reads only
+//    its own columns and the published pivot column(s), so the other CTAs
+//    wait for that flag alone (no grid barrier), except in the steps that
+//    read row r of the trailing block (the row-maximum test and the
+//    interchange), which are bracketed by two grid barriers;
+//  * every wait is bounded (error flag instead of a hang);
 //  * GB300 issues FP64 at 1/64 of the FP32 rate, so the only FP64
 //    instructions per trailing element are the update FMAs: magnitudes are
 //    compared as the integer bit patterns of |v| (monotone for IEEE doubles
@@ -46,8 +50,9 @@ struct BKParams {
     double *buf0, *buf1;           // ping-pong copies of the trailing matrix (lower, ld)
     double *L, *Dd, *Doff;
     int32_t *perm, *kind, *inertia;
-    unsigned long long *slot_bits; // [2] |.| bit pattern of the next pivot column's maximum
-    int *slot_idx;                 // [2] its row index
+    unsigned long long *slot_bits; // [N + 1] |.| bit pattern of step s's pivot-column maximum
+    int *slot_idx;                 // [N + 1] its row index
+    unsigned int *pub;             // number of steps whose pivot data are published
     GridBar bar;
     const double *maxabs;          // max |S| (scale of the zero-pivot test)
     double zero_tol;
@@ -99,6 +104,29 @@ __device__ unsigned long long block_maxbits(unsigned long long b, unsigned long 
     return b;
 }
 
+// wait until *pub >= target (bounded); all threads of the CTA return the same result
+__device__ __forceinline__ bool wait_published(const unsigned int *pub, unsigned int target, int *err) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile const unsigned int *vp = pub;
+        if (*vp < target) {
+            const long long t0 = clock64();
+            while (*vp < target) {
+                if (*((volatile int *)err) != 0 || clock64() - t0 > kBarrierLimitCycles) {
+                    atomicExch(err, 1);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 __global__ void __launch_bounds__(kBkThreads) k_bk_factor(BKParams p) {
     extern __shared__ double sh_dyn[];
     __shared__ unsigned long long s_redb[32];
@@ -127,24 +155,47 @@ __global__ void __launch_bounds__(kBkThreads) k_bk_factor(BKParams p) {
         if (tid == 0) {
             p.slot_bits[0] = b;
             p.slot_idx[0] = idx == 0x7fffffff ? 0 : idx;
+            __threadfence();
+            atomicExch(p.pub, 1u);
         }
     }
-    if (!grid_barrier(p.bar, nb)) return;
 
     const double *cur = p.buf0;
     double *nxt = p.buf1;
-    int parity = 0;
+    int step = 0;
     int npos = 0, nneg = 0, nzero = 0;
     int k = 0;
     while (k < N) {
+        // The owner of column k+1 (the next pivot column unless this step takes
+        // a 2x2 pivot or an interchange) prefetches its own, already final,
+        // entries before waiting for the pivot data.
+        constexpr int kPf = 4;
+        double pf[kPf];
+        const bool own_next = k + 1 < N && (unsigned)(k + 1) % nb == (unsigned)cta;
+        if (own_next) {
+#pragma unroll
+            for (int u = 0; u < kPf; ++u) {
+                const int i = k + 1 + tid + u * kBkThreads;
+                pf[u] = i < N ? __ldcg(cur + i + (int64_t)(k + 1) * ld) : 0.0;
+            }
+        }
+        // pivot data of this step (column k and its maximum) published by its owner
+        if (!wait_published(p.pub, (unsigned)step + 1u, p.bar.err)) return;
         const double akk = __ldcg(cur + k + (int64_t)k * ld);
         const double absakk = fabs(akk);
-        const double colmax = __longlong_as_double((long long)__ldcg(p.slot_bits + parity));
-        const int imax = __ldcg(p.slot_idx + parity);
+        const double colmax = __longlong_as_double((long long)__ldcg(p.slot_bits + step));
+        const int imax = __ldcg(p.slot_idx + step);
+        // column k below the diagonal, loaded speculatively for the common
+        // no-interchange 1x1 pivot (same round trip as the pivot value)
+        for (int t = tid; t < N - k - 1; t += blockDim.x) c0[t] = __ldcg(cur + (k + 1 + t) + (int64_t)k * ld);
         int kstep = 1, kp = k;
-        if (fmax(absakk, colmax) == 0.0 || absakk >= alpha * colmax) {
+        const bool rowtest = !(fmax(absakk, colmax) == 0.0 || absakk >= alpha * colmax);
+        if (!rowtest) {
             kp = k;
         } else {
+            // row r lies in every CTA's columns: all CTAs must have finished the
+            // previous step before it is read
+            if (!grid_barrier(p.bar, nb)) return;
             const int r = imax;
             // largest off-diagonal magnitude of row/column r in the trailing block
             unsigned long long b = 0;
@@ -176,16 +227,23 @@ __global__ void __launch_bounds__(kBkThreads) k_bk_factor(BKParams p) {
             if (a < b) { int t = a; a = b; b = t; }
             return __ldcg(cur + a + (int64_t)b * ld);
         };
-        const double d11 = get(k, k);
+        const bool plain = kstep == 1 && kp == k;   // c0 already holds the pivot column
+        const double d11 = plain ? akk : get(k, k);
         const double d21 = kstep == 2 ? get(k + 1, k) : 0.0;
         const double d22 = kstep == 2 ? get(k + 1, k + 1) : 0.0;
         const int base = k + kstep;
         const int len = N - base;
-        for (int t = tid; t < len; t += blockDim.x) {
-            c0[t] = get(base + t, k);
-            if (kstep == 2) c1[t] = get(base + t, k + 1);
+        if (!plain) {
+            __syncthreads();
+            for (int t = tid; t < len; t += blockDim.x) {
+                c0[t] = get(base + t, k);
+                if (kstep == 2) c1[t] = get(base + t, k + 1);
+            }
         }
         __syncthreads();
+        // with a row test the reads above may touch any CTA's columns: nobody
+        // writes this buffer's columns again (next step) before all have read
+        if (rowtest && !grid_barrier(p.bar, nb)) return;
         // D^-1 entries
         double e11, e21, e22;
         if (kstep == 1) {
@@ -265,69 +323,132 @@ __global__ void __launch_bounds__(kBkThreads) k_bk_factor(BKParams p) {
             return a >= b ? C + a + (int64_t)b * ld : C + b + (int64_t)a * ld;
         };
         const int j0 = base + (int)(((unsigned)cta + nb - (unsigned)(base % (int)nb)) % nb);
-        for (int j = j0; j < N; j += nb) {
+        // next pivot column: updated first, with its column maximum (integer compares)
+        auto tracked = [&](int j) {
             const int tj = j - base;
             double *__restrict__ col = X + (int64_t)j * ld;
-            // new = old - [c0_i c1_i] D^-1 [c0_j c1_j]^T = old - c0_i f0 - c1_i f1
             const double f0 = kstep == 1 ? c0[tj] * e11 : c0[tj] * e11 + c1[tj] * e21;
             const double f1 = kstep == 1 ? 0.0 : c0[tj] * e21 + c1[tj] * e22;
-            const bool simple_col = (j != kp) || kp == kk;
-            if (j == base) {
-                // next pivot column: also its column maximum (integer compares)
-                unsigned long long mb = 0;
-                int mi = 0x7fffffff;
-                for (int i = j + tid; i < N; i += blockDim.x) {
-                    double v = fma(-c0[i - base], f0, __ldcg(src(i, j)));
-                    if (kstep == 2) v = fma(-c1[i - base], f1, v);
-                    col[i] = v;
-                    const unsigned long long ab = absbits(v);
-                    if (i > j && ab > mb) {
-                        mb = ab;
-                        mi = i;
+            unsigned long long mb = 0;
+            int mi = 0x7fffffff;
+            int i = j + tid;
+            if (plain && j == k + 1 && own_next) {
+                // prefetched old values (no interchange: src(i, j) is column j itself)
+#pragma unroll
+                for (int u = 0; u < kPf; ++u, i += kBkThreads) {
+                    if (i < N) {
+                        const double v = fma(-c0[i - base], f0, pf[u]);
+                        col[i] = v;
+                        const unsigned long long ab = absbits(v);
+                        if (i > j && ab > mb) {
+                            mb = ab;
+                            mi = i;
+                        }
                     }
                 }
-                block_argmax(mb, mi, s_redb, s_redi);
-                if (tid == 0) {
-                    p.slot_bits[parity ^ 1] = mb;
-                    p.slot_idx[parity ^ 1] = mi == 0x7fffffff ? j : mi;
+            }
+            for (; i < N; i += blockDim.x) {
+                double v = fma(-c0[i - base], f0, __ldcg(src(i, j)));
+                if (kstep == 2) v = fma(-c1[i - base], f1, v);
+                col[i] = v;
+                const unsigned long long ab = absbits(v);
+                if (i > j && ab > mb) {
+                    mb = ab;
+                    mi = i;
                 }
-            } else if (kstep == 1 && simple_col && kp == kk) {
-                // common case: no interchange, rank-1, four loads in flight per thread
+            }
+            block_argmax(mb, mi, s_redb, s_redi);
+            if (tid == 0) {
+                p.slot_bits[step + 1] = mb;
+                p.slot_idx[step + 1] = mi == 0x7fffffff ? j : mi;
+                __threadfence();   // column j and the slot before the flag
+                atomicExch(p.pub, (unsigned)step + 2u);
+            }
+        };
+        if (kstep == 1 && kp == kk) {
+            // common case: rank-1, no interchange; two columns (8 loads) in flight per thread
+            int j = j0;
+            if (j == base && j < N) {
+                tracked(j);
+                j += nb;
+            }
+            constexpr int T = kBkThreads;
+            for (; j + (int)nb < N; j += 2 * nb) {
+                const int j1 = j + nb;
+                const double fa = c0[j - base] * e11, fb = c0[j1 - base] * e11;
+                const double *__restrict__ sa = C + (int64_t)j * ld;
+                const double *__restrict__ sb = C + (int64_t)j1 * ld;
+                double *__restrict__ da = X + (int64_t)j * ld;
+                double *__restrict__ db = X + (int64_t)j1 * ld;
+                int ia = j + tid, ib = j1 + tid;
+                for (; ib + 3 * T < N; ia += 4 * T, ib += 4 * T) {
+                    const double a0 = __ldcg(sa + ia), a1 = __ldcg(sa + ia + T), a2 = __ldcg(sa + ia + 2 * T),
+                                 a3 = __ldcg(sa + ia + 3 * T);
+                    const double b0 = __ldcg(sb + ib), b1 = __ldcg(sb + ib + T), b2 = __ldcg(sb + ib + 2 * T),
+                                 b3 = __ldcg(sb + ib + 3 * T);
+                    da[ia] = fma(-c0[ia - base], fa, a0);
+                    da[ia + T] = fma(-c0[ia + T - base], fa, a1);
+                    da[ia + 2 * T] = fma(-c0[ia + 2 * T - base], fa, a2);
+                    da[ia + 3 * T] = fma(-c0[ia + 3 * T - base], fa, a3);
+                    db[ib] = fma(-c0[ib - base], fb, b0);
+                    db[ib + T] = fma(-c0[ib + T - base], fb, b1);
+                    db[ib + 2 * T] = fma(-c0[ib + 2 * T - base], fb, b2);
+                    db[ib + 3 * T] = fma(-c0[ib + 3 * T - base], fb, b3);
+                }
+                for (; ia < N; ia += T) da[ia] = fma(-c0[ia - base], fa, __ldcg(sa + ia));
+                for (; ib < N; ib += T) db[ib] = fma(-c0[ib - base], fb, __ldcg(sb + ib));
+            }
+            for (; j < N; j += nb) {
+                const double f0 = c0[j - base] * e11;
                 const double *__restrict__ scol = C + (int64_t)j * ld;
+                double *__restrict__ col = X + (int64_t)j * ld;
                 int i = j + tid;
-                for (; i + 3 * kBkThreads < N; i += 4 * kBkThreads) {
-                    const double v0 = __ldcg(scol + i), v1 = __ldcg(scol + i + kBkThreads),
-                                 v2 = __ldcg(scol + i + 2 * kBkThreads), v3 = __ldcg(scol + i + 3 * kBkThreads);
+                for (; i + 3 * T < N; i += 4 * T) {
+                    const double v0 = __ldcg(scol + i), v1 = __ldcg(scol + i + T), v2 = __ldcg(scol + i + 2 * T),
+                                 v3 = __ldcg(scol + i + 3 * T);
                     col[i] = fma(-c0[i - base], f0, v0);
-                    col[i + kBkThreads] = fma(-c0[i + kBkThreads - base], f0, v1);
-                    col[i + 2 * kBkThreads] = fma(-c0[i + 2 * kBkThreads - base], f0, v2);
-                    col[i + 3 * kBkThreads] = fma(-c0[i + 3 * kBkThreads - base], f0, v3);
+                    col[i + T] = fma(-c0[i + T - base], f0, v1);
+                    col[i + 2 * T] = fma(-c0[i + 2 * T - base], f0, v2);
+                    col[i + 3 * T] = fma(-c0[i + 3 * T - base], f0, v3);
                 }
-                for (; i < N; i += kBkThreads) col[i] = fma(-c0[i - base], f0, __ldcg(scol + i));
-            } else if (kstep == 1) {
-                int i = j + tid;
-                for (; i + kBkThreads < N; i += 2 * kBkThreads) {
-                    const double v0 = __ldcg(src(i, j)), v1 = __ldcg(src(i + kBkThreads, j));
-                    col[i] = fma(-c0[i - base], f0, v0);
-                    col[i + kBkThreads] = fma(-c0[i + kBkThreads - base], f0, v1);
+                for (; i < N; i += T) col[i] = fma(-c0[i - base], f0, __ldcg(scol + i));
+            }
+        } else {
+            for (int j = j0; j < N; j += nb) {
+                if (j == base) {
+                    tracked(j);
+                    continue;
                 }
-                for (; i < N; i += kBkThreads) col[i] = fma(-c0[i - base], f0, __ldcg(src(i, j)));
-            } else {
-                int i = j + tid;
-                for (; i + kBkThreads < N; i += 2 * kBkThreads) {
-                    const double v0 = __ldcg(src(i, j)), v1 = __ldcg(src(i + kBkThreads, j));
-                    col[i] = fma(-c1[i - base], f1, fma(-c0[i - base], f0, v0));
-                    col[i + kBkThreads] = fma(-c1[i + kBkThreads - base], f1, fma(-c0[i + kBkThreads - base], f0, v1));
+                const int tj = j - base;
+                double *__restrict__ col = X + (int64_t)j * ld;
+                // new = old - [c0_i c1_i] D^-1 [c0_j c1_j]^T = old - c0_i f0 - c1_i f1
+                const double f0 = kstep == 1 ? c0[tj] * e11 : c0[tj] * e11 + c1[tj] * e21;
+                const double f1 = kstep == 1 ? 0.0 : c0[tj] * e21 + c1[tj] * e22;
+                if (kstep == 1) {
+                    int i = j + tid;
+                    for (; i + kBkThreads < N; i += 2 * kBkThreads) {
+                        const double v0 = __ldcg(src(i, j)), v1 = __ldcg(src(i + kBkThreads, j));
+                        col[i] = fma(-c0[i - base], f0, v0);
+                        col[i + kBkThreads] = fma(-c0[i + kBkThreads - base], f0, v1);
+                    }
+                    for (; i < N; i += kBkThreads) col[i] = fma(-c0[i - base], f0, __ldcg(src(i, j)));
+                } else {
+                    int i = j + tid;
+                    for (; i + kBkThreads < N; i += 2 * kBkThreads) {
+                        const double v0 = __ldcg(src(i, j)), v1 = __ldcg(src(i + kBkThreads, j));
+                        col[i] = fma(-c1[i - base], f1, fma(-c0[i - base], f0, v0));
+                        col[i + kBkThreads] =
+                            fma(-c1[i + kBkThreads - base], f1, fma(-c0[i + kBkThreads - base], f0, v1));
+                    }
+                    for (; i < N; i += kBkThreads)
+                        col[i] = fma(-c1[i - base], f1, fma(-c0[i - base], f0, __ldcg(src(i, j))));
                 }
-                for (; i < N; i += kBkThreads)
-                    col[i] = fma(-c1[i - base], f1, fma(-c0[i - base], f0, __ldcg(src(i, j))));
             }
         }
-        if (!grid_barrier(p.bar, nb)) return;
         const double *t = cur;
         cur = nxt;
         nxt = const_cast<double *>(t);
-        parity ^= 1;
+        ++step;
         k += kstep;
     }
     if (cta == 0 && tid == 0) {
@@ -412,6 +533,152 @@ k_ldlt_solve(int N, const double *__restrict__ L, const double *__restrict__ Dd,
     for (int i = tid; i < N; i += blockDim.x) b[perm[i]] = y[i];
 }
 
+// ---------------------------------------------------------------------------
+// Multi-CTA solve (cooperative launch, one bounded grid barrier per 32-row
+// block).  Forward L y = P b, block B = rows [32B, 32B + 32):
+//   CTA 0   : solves the diagonal block B (one warp), then applies blocks B-1
+//             and B to the rows of block B+1;
+//   others  : apply block B-1 to the rows at and beyond block B+2;
+// so at step B block B has received every earlier block.  The backward
+// solve L^T z = D^-1 y mirrors it from the last block up.
+// ---------------------------------------------------------------------------
+constexpr int kSolveBS = 32;
+constexpr int kSolveCoopThreads = 256;
+
+struct SolveParams {
+    int N;
+    const double *L, *Dd, *Doff;
+    const int32_t *perm;
+    double *b;
+    double *y;  // N scratch
+    GridBar bar;
+};
+
+__global__ void __launch_bounds__(kSolveCoopThreads) k_ldlt_solve_coop(SolveParams p) {
+    __shared__ double s_y[2 * kSolveBS];
+    const int N = p.N;
+    const unsigned nb = gridDim.x;
+    const int cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nblk = (N + kSolveBS - 1) / kSolveBS;
+    const double *__restrict__ L = p.L;
+    double *y = p.y;
+    const int64_t gt = (int64_t)cta * blockDim.x + tid, gs = (int64_t)nb * blockDim.x;
+    for (int64_t i = gt; i < N; i += gs) y[i] = p.b[p.perm[i]];
+    if (!grid_barrier(p.bar, nb)) return;
+    // rows [r0, r1) of the "others" share, split across CTAs 1..nb-1 (or all rows when nb == 1)
+    auto others_apply = [&](int blk, int r_begin, bool forward) {
+        if (blk < 0 || blk >= nblk) return;
+        const int c0 = blk * kSolveBS, bw = min(kSolveBS, N - c0);
+        const int workers = nb > 1 ? (int)nb - 1 : 1;
+        const int widx = nb > 1 ? cta - 1 : 0;
+        if (nb > 1 && cta == 0) return;
+        const int r_lo = forward ? r_begin : 0;
+        const int r_hi = forward ? N : r_begin;
+        for (int64_t r = r_lo + (int64_t)widx * blockDim.x + tid; r < r_hi; r += (int64_t)workers * blockDim.x) {
+            double acc = 0.0;
+            if (forward) {
+                for (int j = 0; j < bw; ++j) acc = fma(L[r + (int64_t)(c0 + j) * N], __ldcg(y + c0 + j), acc);
+            } else {
+                for (int i = 0; i < bw; ++i) acc = fma(L[(c0 + i) + r * (int64_t)N], __ldcg(y + c0 + i), acc);
+            }
+            y[r] = __ldcg(y + r) - acc;
+        }
+    };
+    // forward
+    for (int B = 0; B < nblk; ++B) {
+        const int jb = B * kSolveBS, bw = min(kSolveBS, N - jb);
+        if (cta == 0) {
+            if (wid == 0) {
+                double yi = lane < bw ? __ldcg(y + jb + lane) : 0.0;
+                for (int j = 0; j < bw; ++j) {
+                    const double yj = __shfl_sync(0xffffffffu, yi, j);
+                    if (lane > j && lane < bw) yi = fma(-L[(jb + lane) + (int64_t)(jb + j) * N], yj, yi);
+                }
+                if (lane < bw) {
+                    y[jb + lane] = yi;
+                    s_y[kSolveBS + lane] = yi;
+                }
+                if (B > 0) s_y[lane] = __ldcg(y + jb - kSolveBS + lane);
+            }
+            __syncthreads();
+            // blocks B-1 and B applied to block B+1's rows: 8 threads per row
+            const int nr = jb + kSolveBS;
+            if (B + 1 < nblk) {
+                const int r = nr + (tid >> 3), part = tid & 7;
+                const int rows = min(kSolveBS, N - nr);
+                double acc = 0.0;
+                if ((tid >> 3) < rows) {
+                    for (int c = part * 8; c < part * 8 + 8; ++c) {
+                        const int blk = c < kSolveBS ? B - 1 : B;
+                        if (blk < 0) continue;
+                        const int col = blk * kSolveBS + (c % kSolveBS);
+                        if (col >= N) continue;
+                        acc = fma(L[r + (int64_t)col * N], s_y[c], acc);
+                    }
+                }
+                for (int o = 4; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, 8);
+                if (part == 0 && (tid >> 3) < rows) y[r] = __ldcg(y + r) - acc;
+            }
+        }
+        others_apply(B - 1, jb + 2 * kSolveBS, true);
+        if (!grid_barrier(p.bar, nb)) return;
+    }
+    // the last block's contribution beyond itself does not exist; D^-1
+    for (int64_t k = gt; k < N; k += gs) {
+        const double off = p.Doff[k];
+        if (off != 0.0) {
+            const double a = p.Dd[k], c = p.Dd[k + 1];
+            const double det = a * c - off * off;
+            const double u = __ldcg(y + k), v = __ldcg(y + k + 1);
+            y[k] = (c * u - off * v) / det;
+            y[k + 1] = (a * v - off * u) / det;
+        } else if (k == 0 || p.Doff[k - 1] == 0.0) {
+            y[k] = __ldcg(y + k) / p.Dd[k];
+        }
+    }
+    if (!grid_barrier(p.bar, nb)) return;
+    // backward: blocks from the last one up
+    for (int B = nblk - 1; B >= 0; --B) {
+        const int jb = B * kSolveBS, bw = min(kSolveBS, N - jb);
+        if (cta == 0) {
+            if (wid == 0) {
+                double yi = lane < bw ? __ldcg(y + jb + lane) : 0.0;
+                for (int j = bw - 1; j >= 0; --j) {
+                    const double yj = __shfl_sync(0xffffffffu, yi, j);
+                    if (lane < j) yi = fma(-L[(jb + j) + (int64_t)(jb + lane) * N], yj, yi);
+                }
+                if (lane < bw) {
+                    y[jb + lane] = yi;
+                    s_y[lane] = yi;
+                }
+                if (B + 1 < nblk) {
+                    const int nb1 = min(kSolveBS, N - (jb + kSolveBS));
+                    s_y[kSolveBS + lane] = lane < nb1 ? __ldcg(y + jb + kSolveBS + lane) : 0.0;
+                }
+            }
+            __syncthreads();
+            // blocks B and B+1 applied to block B-1's rows
+            if (B > 0) {
+                const int pr = jb - kSolveBS;
+                const int r = pr + (tid >> 3), part = tid & 7;
+                double acc = 0.0;
+                for (int c = part * 8; c < part * 8 + 8; ++c) {
+                    const int blk = c < kSolveBS ? B : B + 1;
+                    if (blk >= nblk) continue;
+                    const int row = blk * kSolveBS + (c % kSolveBS);
+                    if (row >= N) continue;
+                    acc = fma(L[row + (int64_t)r * N], s_y[c], acc);
+                }
+                for (int o = 4; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, 8);
+                if (part == 0) y[r] = __ldcg(y + r) - acc;
+            }
+        }
+        others_apply(B + 1, jb - kSolveBS, false);
+        if (!grid_barrier(p.bar, nb)) return;
+    }
+    for (int64_t i = gt; i < N; i += gs) p.b[p.perm[i]] = __ldcg(y + i);
+}
+
 __global__ void k_maxabs_lower(int64_t N, const double *S, int64_t ld, double *partial) {
     __shared__ double sh[32];
     double v = 0.0;
@@ -424,8 +691,11 @@ __global__ void k_maxabs_lower(int64_t N, const double *S, int64_t ld, double *p
 }  // namespace
 
 size_t ldlt_scratch_bytes(int64_t N) {
-    // ping-pong buffer (N x N), slots, barrier words
-    return (size_t)N * (size_t)N * sizeof(double) + 256;
+    // ping-pong buffer (N x N), then 64 bytes of barrier/flag words, then the
+    // per-step pivot slots (N + 1 maxima and indices)
+    const size_t b = (size_t)N * (size_t)N * sizeof(double) + 64 +
+                     (size_t)(N + 1) * (sizeof(unsigned long long) + sizeof(int)) + 256;
+    return (b + 255) / 256 * 256;  // callers place 8-byte data right after it
 }
 
 void launch_maxabs_lower(cudaStream_t s, int64_t N, const double *S, int64_t ld, double *partial,
@@ -446,6 +716,7 @@ void launch_ldlt(cudaStream_t s, int num_sms, int64_t N, const double *S, int64_
         return;
     }
     char *w = static_cast<char *>(scratch);
+    MDSIP_REQUIRE((reinterpret_cast<uintptr_t>(w) & 255) == 0, MDSIP_ERR_INVALID_ARG, "ldlt: misaligned scratch");
     BKParams p{};
     p.N = (int)N;
     p.buf0 = const_cast<double *>(S);
@@ -454,12 +725,13 @@ void launch_ldlt(cudaStream_t s, int num_sms, int64_t N, const double *S, int64_
     MDSIP_REQUIRE(ld == N, MDSIP_ERR_INVALID_ARG, "ldlt: leading dimension must equal N");
     p.ld = ld;
     char *tail = w + (size_t)N * (size_t)N * sizeof(double);
-    p.slot_bits = reinterpret_cast<unsigned long long *>(tail);
-    p.slot_idx = reinterpret_cast<int *>(tail + 16);
-    p.bar.count = reinterpret_cast<unsigned int *>(tail + 32);
-    p.bar.gen = reinterpret_cast<unsigned int *>(tail + 36);
+    p.bar.count = reinterpret_cast<unsigned int *>(tail);
+    p.bar.gen = reinterpret_cast<unsigned int *>(tail + 4);
+    p.pub = reinterpret_cast<unsigned int *>(tail + 8);
     p.bar.err = err_dev;
     MDSIP_CUDA(cudaMemsetAsync(tail, 0, 64, s));
+    p.slot_bits = reinterpret_cast<unsigned long long *>(tail + 64);
+    p.slot_idx = reinterpret_cast<int *>(tail + 64 + (size_t)(N + 1) * sizeof(unsigned long long));
     p.L = out.L;
     p.Dd = out.Dd;
     p.Doff = out.Doff;
@@ -481,6 +753,39 @@ void launch_ldlt(cudaStream_t s, int num_sms, int64_t N, const double *S, int64_
     MDSIP_CUDA(cudaLaunchCooperativeKernel((const void *)k_bk_factor, dim3(grid), dim3(kBkThreads),
                                            args, smem, s));
     count_launch();
+}
+
+// scratch: N doubles + 64 bytes of barrier words (ldlt_solve_scratch_bytes)
+size_t ldlt_solve_scratch_bytes(int64_t N) { return ((size_t)std::max<int64_t>(N, 1) * sizeof(double) + 255) / 256 * 256 + 64; }
+
+void launch_ldlt_solve_coop(cudaStream_t s, int num_sms, int64_t N, const double *L, const double *Dd,
+                            const double *Doff, const int32_t *perm, int64_t nrhs, double *B, int64_t ldb,
+                            void *scratch, int *err_dev) {
+    if (N <= 0 || nrhs <= 0) return;
+    char *w = static_cast<char *>(scratch);
+    const size_t ybytes = ((size_t)N * sizeof(double) + 255) / 256 * 256;
+    SolveParams p{};
+    p.N = (int)N;
+    p.L = L;
+    p.Dd = Dd;
+    p.Doff = Doff;
+    p.perm = perm;
+    p.y = reinterpret_cast<double *>(w);
+    p.bar.count = reinterpret_cast<unsigned int *>(w + ybytes);
+    p.bar.gen = reinterpret_cast<unsigned int *>(w + ybytes + 4);
+    p.bar.err = err_dev;
+    int per_sm = 0;
+    MDSIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ldlt_solve_coop, kSolveCoopThreads, 0));
+    MDSIP_REQUIRE(per_sm >= 1, MDSIP_ERR_INVALID_ARG, "ldlt_solve: kernel does not fit on an SM");
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(num_sms, N / 16));
+    for (int64_t r = 0; r < nrhs; ++r) {
+        MDSIP_CUDA(cudaMemsetAsync(w + ybytes, 0, 64, s));
+        p.b = B + r * ldb;
+        void *args[] = {&p};
+        MDSIP_CUDA(cudaLaunchCooperativeKernel((const void *)k_ldlt_solve_coop, dim3(grid),
+                                               dim3(kSolveCoopThreads), args, 0, s));
+        count_launch();
+    }
 }
 
 void launch_ldlt_solve(cudaStream_t s, int64_t N, const double *L, const double *Dd,
@@ -508,7 +813,12 @@ void launch_ldlt_solve(cudaStream_t s, int64_t N, const double *L, const double 
 // every GPU that loads the library holds until the process exits.
 // ---------------------------------------------------------------------------
 constexpr int64_t kNoAllocMaxN = 1024;
-constexpr size_t kNoAllocBytes = (size_t)kNoAllocMaxN * kNoAllocMaxN * sizeof(double) + 4096;
+constexpr size_t kNoAllocBytes = (size_t)kNoAllocMaxN * kNoAllocMaxN * sizeof(double) + 16384;
+static_assert((size_t)kNoAllocMaxN * kNoAllocMaxN * sizeof(double) + 64 +
+                      (size_t)(kNoAllocMaxN + 1) * (sizeof(unsigned long long) + sizeof(int)) + 256 + 256 +
+                      (size_t)(kRedBlocks + 1) * sizeof(double) <=
+                  kNoAllocBytes,
+              "fixed scratch too small for the factorization's layout");
 static __device__ __align__(256) unsigned char g_ldlt_fixed_scratch[kNoAllocBytes];
 
 namespace {
@@ -552,6 +862,8 @@ void ldlt_factor_fixed_scratch(cudaStream_t s, int device, int num_sms, int64_t 
     int *err = reinterpret_cast<int *>(base + fs);
     double *partial = reinterpret_cast<double *>(base + fs + 256);
     double *maxabs = partial + kRedBlocks;
+    MDSIP_REQUIRE(((reinterpret_cast<uintptr_t>(partial) | reinterpret_cast<uintptr_t>(base)) & 255) == 0,
+                  MDSIP_ERR_INVALID_ARG, "ldlt (fixed scratch): misaligned layout");
     // every call shares the array: clear what must start at zero (the factor
     // launch clears its own slots and barrier words)
     MDSIP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));

@@ -220,7 +220,7 @@ void Refiner::approx_solve(const double *b, double *sol) {
     launch_gemv_t(st, M.A, D.m_E, D.n_d, D.lda, tmp_m, colpart, tmp_nd);
     k_rhs_S<<<grid_for(std::max(D.n_d, D.m_I)), 256, 0, st>>>(D, b, tmp_nd, rhsS);
     MDSIP_LAUNCHED();
-    launch_ldlt_solve(st, N, L, Dd, Doff, perm, 1, rhsS, N);
+    launch_ldlt_solve_coop(st, num_sms, N, L, Dd, Doff, perm, 1, rhsS, N, solve_ws, solve_err);
     launch_gemv_rows(st, M.A, D.m_E, D.n_d, D.lda, rhsS, tmp_m);
     k_sol_gdh<<<grid_for(std::max(D.m_E, D.n_d)), 256, 0, st>>>(D, tmp_m, bt_g, w, rhsS, sol);
     MDSIP_LAUNCHED();
@@ -228,14 +228,21 @@ void Refiner::approx_solve(const double *b, double *sol) {
     MDSIP_LAUNCHED();
 }
 
+void Refiner::track_Au(bool init) {
+    if (init) {
+        MDSIP_CUDA(cudaMemcpyAsync(Au_run, tmp_m, D.m_E * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+        axpy(D.m_E, tmp_m, Au_run);
+    }
+}
+
 void Refiner::residual(const double *b, const double *u, double dw, double dc, double *r, double *out4) {
-    launch_gemv_rows(st, M.A, D.m_E, D.n_d, D.lda, u + D.n_s, tmp_m);           // A u_d
     launch_gemv_t(st, M.A, D.m_E, D.n_d, D.lda, u + D.n, colpart, tmp_nd);     // A^T u_g
     k_hdd_gemv<<<std::max(1, std::min(4096, ceil_div(D.n_d * 32, 256))), 256, 0, st>>>(D.n_d, Hdd, u + D.n_s,
                                                                                       tmp_nd2);
     MDSIP_LAUNCHED();
-    k_residual<<<kRedBlocks, NT, 0, st>>>(D, M, b, u, q, sig_xd, sig_d, Jdh, tmp_m, tmp_nd, tmp_nd2, dw, dc, r,
-                                          partial);
+    k_residual<<<kRedBlocks, NT, 0, st>>>(D, M, b, u, q, sig_xd, sig_d, Jdh, Au_run, tmp_nd, tmp_nd2, dw, dc,
+                                          r, partial);
     MDSIP_LAUNCHED();
     launch_finalize_max(st, partial, 4, out4);
 }

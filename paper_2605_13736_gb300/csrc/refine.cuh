@@ -12,17 +12,23 @@ struct Refiner {
     int64_t N;
     const double *L, *Dd, *Doff;
     const int32_t *perm;
+    int num_sms;
+    void *solve_ws;   // ldlt_solve_scratch_bytes(N)
+    int *solve_err;
     // Newton quantities of the current attempt
     const double *q, *w, *sig_xd, *sig_d, *Jdh, *Hdd;
     // scratch: bt_g, tmp_m (m_E), tmp_nd, tmp_nd2 (n_d), rhsS (N), colpart, partial
     double *bt_g, *tmp_m, *tmp_nd, *tmp_nd2, *rhsS, *colpart, *partial;
+    double *Au_run;   // A u_d of the current solution, kept as a running sum (m_E)
 
     // b = right-hand side of Eq. (linsys4x4), packed [s | d | g | h]
     void rhs(const IterView &I, const double *gl, const double *cg, const double *ch, const double *sig_d,
              double mu, double dw, double *b);
     // sol = S~^-1-based solve of K sol = b (two-stage elimination with the factor)
     void approx_solve(const double *b, double *sol);
-    // r = b - K u in FP64; out4 = (||r||inf, ||b||inf, ||K u||inf, ||u||inf)
+    // after approx_solve: Au_run = A sol_d (init) or Au_run += A sol_d
+    void track_Au(bool init);
+    // r = b - K u in FP64 (A u_d taken from Au_run); out4 = (||r||inf, ||b||inf, ||K u||inf, ||u||inf)
     void residual(const double *b, const double *u, double dw, double dc, double *r, double *out4);
     void axpy(int64_t n, const double *x, double *y);
     // full direction (incl. dd and the bound-multiplier steps) from the packed solution

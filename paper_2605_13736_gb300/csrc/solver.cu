@@ -109,7 +109,7 @@ struct Problem {
     // reduced matrix and factors
     DBuf bS, bL, bDd, bDoff, bperm, bkind, binertia, bldlt_ws, berr, bsyrk_ws;
     // tensor-core condensation and refinement
-    DBuf bAfT, btc_ws, btc_err, bref_b, bref_u, bref_r, bref_d, btmp_nd2;
+    DBuf bAfT, btc_ws, btc_err, bref_b, bref_u, bref_r, bref_d, btmp_nd2, bsolve_ws, bsolve_err, bAu_run;
     bool aft_ready = false;
     int64_t tc_prec = -1;
     DBuf bscal, bpartial, bcolpart;
@@ -377,6 +377,9 @@ static void prepare_path(Problem *P) {
     P->bkind.get<int32_t>(ctx, std::max<int64_t>(N, 1));
     P->binertia.get<int32_t>(ctx, 4);
     P->bldlt_ws.get<char>(ctx, ldlt_scratch_bytes(N));
+    P->bsolve_ws.get<char>(ctx, ldlt_solve_scratch_bytes(N));
+    P->bsolve_err.get<int>(ctx, 4);
+    MDSIP_CUDA(cudaMemsetAsync(P->bsolve_err.ptr, 0, sizeof(int), ctx->stream));
     dvec(ctx, P->brhs, std::max<int64_t>(N, 1) * 2);
     const size_t sw = path == MDSIP_PATH_P2 ? syrk_fp64_scratch_bytes(D.m_E, D.n_d, ctx->num_sms) : 0;
     if (sw) P->bsyrk_ws.get<char>(ctx, sw);
@@ -388,6 +391,7 @@ static void prepare_path(Problem *P) {
         dvec(ctx, P->bref_r, nm);
         dvec(ctx, P->bref_d, nm);
         dvec(ctx, P->btmp_nd2, D.n_d);
+        dvec(ctx, P->bAu_run, D.m_E);
     }
 }
 
@@ -502,8 +506,9 @@ static void solve_direction(Problem *P, double mu, double dw) {
     P->V.rhs_y(P->I, gl, P->cg, q, p2 ? w : nullptr, mu, bt_g, p2 ? u : nullptr);
     if (p2) launch_gemv_t(st, P->Mv.A, D.m_E, D.n_d, D.lda, u, P->V.colpart, ATu);
     P->V.rhs_reduced(P->I, gl, P->ch, sig_d, ATu, bt_g, mu, dw, !p2, rhs);
-    launch_ldlt_solve(st, P->N, P->bL.as<double>(), P->bDd.as<double>(), P->bDoff.as<double>(),
-                      P->bperm.as<int32_t>(), 1, rhs, P->N);
+    launch_ldlt_solve_coop(st, P->ctx->num_sms, P->N, P->bL.as<double>(), P->bDd.as<double>(),
+                           P->bDoff.as<double>(), P->bperm.as<int32_t>(), 1, rhs, P->N, P->bsolve_ws.ptr,
+                           P->bsolve_err.as<int>());
     if (p2) {
         launch_gemv_rows(st, P->Mv.A, D.m_E, D.n_d, D.lda, rhs, Adx);
         P->V.dyg_p2(Adx, bt_g, w, P->Dir.dyg);
@@ -536,6 +541,9 @@ static RefineResult solve_direction_refined(Problem *P, double mu, double dw, do
     R.Dd = P->bDd.as<double>();
     R.Doff = P->bDoff.as<double>();
     R.perm = P->bperm.as<int32_t>();
+    R.num_sms = P->ctx->num_sms;
+    R.solve_ws = P->bsolve_ws.ptr;
+    R.solve_err = P->bsolve_err.as<int>();
     R.q = P->bq.as<double>();
     R.w = P->bw.as<double>();
     R.sig_xd = P->bsig_x.as<double>() + D.n_s;
@@ -549,12 +557,14 @@ static RefineResult solve_direction_refined(Problem *P, double mu, double dw, do
     R.rhsS = P->brhs.as<double>();
     R.colpart = P->V.colpart;
     R.partial = P->V.partial;
+    R.Au_run = P->bAu_run.as<double>();
     double *b = P->bref_b.as<double>(), *u = P->bref_u.as<double>(), *r = P->bref_r.as<double>(),
            *d = P->bref_d.as<double>();
     const double *h = P->hscal;
     MDSIP_CUDA(cudaEventRecord(P->ev[3], st));
     R.rhs(P->I, P->bgl.as<double>(), P->cg, P->ch, R.sig_d, mu, dw, b);
     R.approx_solve(b, u);
+    R.track_Au(true);
     RefineResult out{false, 0, INFINITY};
     double rprev = INFINITY;
     while (true) {
@@ -566,6 +576,7 @@ static RefineResult solve_direction_refined(Problem *P, double mu, double dw, do
         if (rinf <= P->opt.refine_tol * scale) break;
         if (out.sweeps >= max_sweeps || (out.sweeps > 0 && rinf > 0.5 * rprev)) break;
         R.approx_solve(r, d);
+        R.track_Au(false);
         R.axpy(D.n + D.m, d, u);
         out.sweeps++;
         rprev = rinf;
@@ -588,7 +599,22 @@ static bool use_refined(const Problem *P) {
 
 // Direction with the current factor; with a tensor-core product that does
 // not refine to tolerance, re-factor with the FP64 product and solve again.
+static void check_solve_flag(Problem *P) {
+    MDSIP_CUDA(cudaMemcpyAsync(P->hint + 6, P->bsolve_err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                               P->ctx->stream));
+    MDSIP_CUDA(cudaStreamSynchronize(P->ctx->stream));
+    MDSIP_REQUIRE(P->hint[6] == 0, MDSIP_ERR_DEVICE, "LDL^T solve: a bounded device wait expired");
+}
+
+static RefineResult direction_step_(Problem *P, double mu, double dw, double dc);
+
 static RefineResult direction_step(Problem *P, double mu, double dw, double dc) {
+    const RefineResult r = direction_step_(P, mu, dw, dc);
+    check_solve_flag(P);
+    return r;
+}
+
+static RefineResult direction_step_(Problem *P, double mu, double dw, double dc) {
     if (!use_refined(P)) {
         solve_direction(P, mu, dw);
         return RefineResult{true, 0, 0.0};
@@ -1210,6 +1236,8 @@ mdsip_status mdsip_ldlt_factor(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld
         double *partial = reinterpret_cast<double *>(w + ldlt_scratch_bytes(N) + 64);
         double *maxabs = partial + kRedBlocks;
         int *err = reinterpret_cast<int *>(w + ldlt_scratch_bytes(N));
+        MDSIP_REQUIRE((reinterpret_cast<uintptr_t>(partial) & 7) == 0, MDSIP_ERR_INVALID_ARG,
+                      "ldlt: misaligned scratch layout");
         MDSIP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
         launch_maxabs_lower(ctx->stream, N, S, ld, partial, maxabs);
         LdltOut o{L, Dd, Doff, perm, kind, inertia};
@@ -1241,7 +1269,17 @@ mdsip_status mdsip_ldlt_solve(mdsip_ctx *hctx, int64_t N, const double *L, const
     return guarded(ctx, [&] {
         DeviceGuard g(ctx->device);
         MDSIP_REQUIRE(N >= 0 && nrhs >= 0 && ldb >= N, MDSIP_ERR_INVALID_ARG, "ldlt_solve: bad sizes");
-        launch_ldlt_solve(ctx->stream, N, L, Dd, Doff, perm, nrhs, B, ldb);
+        if (N == 0 || nrhs == 0) return;
+        MDSIP_REQUIRE(L && Dd && Doff && perm && B, MDSIP_ERR_INVALID_ARG, "ldlt_solve: null pointer");
+        const size_t ws = ldlt_solve_scratch_bytes(N);
+        char *w = static_cast<char *>(ctx->scratch_at_least(ws + 256));
+        int *err = reinterpret_cast<int *>(w + ws);
+        MDSIP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+        launch_ldlt_solve_coop(ctx->stream, ctx->num_sms, N, L, Dd, Doff, perm, nrhs, B, ldb, w, err);
+        int herr = 0;
+        MDSIP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        MDSIP_CUDA(cudaStreamSynchronize(ctx->stream));
+        MDSIP_REQUIRE(herr == 0, MDSIP_ERR_DEVICE, "ldlt_solve: a bounded device wait expired");
     });
 }
 

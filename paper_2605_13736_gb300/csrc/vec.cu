@@ -14,6 +14,38 @@ constexpr int NT = kRedThreads;
 
 __device__ __forceinline__ bool fin(double v) { return isfinite(v); }
 
+// dot(row, v) over n entries for one warp; row and v 16-byte aligned when
+// vec; four independent 16-byte loads and accumulators per lane.  Result in
+// every lane.
+__device__ __forceinline__ double warp_row_dot(const double *__restrict__ row, const double *__restrict__ v,
+                                               int64_t n, bool vec, int lane) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    if (vec) {
+        const double2 *r2 = reinterpret_cast<const double2 *>(row);
+        const double2 *v2 = reinterpret_cast<const double2 *>(v);
+        const int64_t n2 = n / 2;
+        int64_t k = lane;
+        for (; k + 96 < n2; k += 128) {
+            const double2 a0 = __ldg(r2 + k), a1 = __ldg(r2 + k + 32), a2 = __ldg(r2 + k + 64), a3 = __ldg(r2 + k + 96);
+            const double2 b0 = v2[k], b1 = v2[k + 32], b2 = v2[k + 64], b3 = v2[k + 96];
+            s0 = fma(a0.x, b0.x, fma(a0.y, b0.y, s0));
+            s1 = fma(a1.x, b1.x, fma(a1.y, b1.y, s1));
+            s2 = fma(a2.x, b2.x, fma(a2.y, b2.y, s2));
+            s3 = fma(a3.x, b3.x, fma(a3.y, b3.y, s3));
+        }
+        for (; k < n2; k += 32) {
+            const double2 a0 = __ldg(r2 + k), b0 = v2[k];
+            s0 = fma(a0.x, b0.x, fma(a0.y, b0.y, s0));
+        }
+        if ((n & 1) && lane == 0) s1 = fma(row[n - 1], v[n - 1], s1);
+    } else {
+        for (int64_t k = lane; k < n; k += 32) s0 = fma(row[k], v[k], s0);
+    }
+    double s = (s0 + s1) + (s2 + s3);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
 // partial slot of quantity q for this block
 __device__ __forceinline__ double *slot(double *partial, int q) {
     return partial + (size_t)q * kRedBlocks + blockIdx.x;
@@ -83,22 +115,9 @@ __global__ void __launch_bounds__(NT) k_eval_cons(Dims D, ModelView M, const dou
     const int64_t nw = ((int64_t)gridDim.x * NT) >> 5;
     const double *xd = x + D.n_s;
     double s1 = 0.0, mx = 0.0;
-    const int64_t n2 = D.n_d / 2;
+    const bool vec = (reinterpret_cast<uintptr_t>(xd) & 15) == 0;
     for (int64_t i = gw; i < D.m_E; i += nw) {
-        const double2 *row = reinterpret_cast<const double2 *>(M.A + i * D.lda);
-        const double2 *x2 = reinterpret_cast<const double2 *>(xd);
-        double s = 0.0;
-        if ((reinterpret_cast<uintptr_t>(xd) & 15) == 0) {
-            for (int64_t k = lane; k < n2; k += 32) {
-                const double2 a = __ldg(row + k);
-                const double2 b = x2[k];
-                s += a.x * b.x + a.y * b.y;
-            }
-            if ((D.n_d & 1) && lane == 0) s += M.A[i * D.lda + D.n_d - 1] * xd[D.n_d - 1];
-        } else {
-            for (int64_t k = lane; k < D.n_d; k += 32) s += M.A[i * D.lda + k] * xd[k];
-        }
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        double s = warp_row_dot(M.A + i * D.lda, xd, D.n_d, vec, lane);
         if (lane == 0) {
             for (int e = M.csr_ptr[i]; e < M.csr_ptr[i + 1]; ++e) s += M.csr_val[e] * x[M.csr_col[e]];
             const double r = s - M.gE[i];
@@ -158,22 +177,8 @@ __global__ void __launch_bounds__(NT) k_gemv_rows(const double *__restrict__ A, 
     const int64_t nw = ((int64_t)gridDim.x * NT) >> 5;
     const bool vec = ((lda & 1) == 0) && ((reinterpret_cast<uintptr_t>(v) & 15) == 0) &&
                      ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
-    const int64_t n2 = n / 2;
     for (int64_t i = gw; i < m; i += nw) {
-        double s = 0.0;
-        if (vec) {
-            const double2 *row = reinterpret_cast<const double2 *>(A + i * lda);
-            const double2 *v2 = reinterpret_cast<const double2 *>(v);
-            for (int64_t k = lane; k < n2; k += 32) {
-                const double2 a = __ldg(row + k);
-                const double2 b = v2[k];
-                s += a.x * b.x + a.y * b.y;
-            }
-            if ((n & 1) && lane == 0) s += A[i * lda + n - 1] * v[n - 1];
-        } else {
-            for (int64_t k = lane; k < n; k += 32) s += A[i * lda + k] * v[k];
-        }
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        const double s = warp_row_dot(A + i * lda, v, n, vec, lane);
         if (lane == 0) out[i] = s;
     }
 }
@@ -190,13 +195,27 @@ __global__ void __launch_bounds__(NT) k_gemv_t(const double *__restrict__ A, int
         double acc[kGtCols];
 #pragma unroll
         for (int c = 0; c < kGtCols; ++c) acc[c] = 0.0;
-        for (int64_t i = r0; i < r1; ++i) {
+        int64_t i = r0;
+        for (; i + 1 < r1; i += 2) {
+            const double u0 = u[i], u1 = u[i + 1];
+            const double *row0 = A + i * lda, *row1 = row0 + lda;
+            double a0[kGtCols], a1[kGtCols];
+#pragma unroll
+            for (int c = 0; c < kGtCols; ++c) {
+                const int64_t p = c0 + threadIdx.x + (int64_t)c * NT;
+                a0[c] = p < n ? __ldg(row0 + p) : 0.0;
+                a1[c] = p < n ? __ldg(row1 + p) : 0.0;
+            }
+#pragma unroll
+            for (int c = 0; c < kGtCols; ++c) acc[c] = fma(a1[c], u1, fma(a0[c], u0, acc[c]));
+        }
+        for (; i < r1; ++i) {
             const double ui = u[i];
             const double *row = A + i * lda;
 #pragma unroll
             for (int c = 0; c < kGtCols; ++c) {
                 const int64_t p = c0 + threadIdx.x + (int64_t)c * NT;
-                if (p < n) acc[c] += __ldg(row + p) * ui;
+                if (p < n) acc[c] = fma(__ldg(row + p), ui, acc[c]);
             }
         }
 #pragma unroll
