@@ -458,6 +458,7 @@ static Inertia factor_attempt(Problem *P, double dw, double dc, bool force_fp64 
     MDSIP_CUDA(cudaEventRecord(P->ev[10], st));
     launch_ldlt(st, P->ctx->num_sms, P->N, S, P->N, sc + SC_MAXABS, P->opt.zero_tol, o,
                 P->bldlt_ws.ptr, P->berr.as<int>());
+    launch_ldlt_solve_prepare(st, P->N, P->bL.as<double>(), P->bsolve_ws.ptr);
     MDSIP_CUDA(cudaEventRecord(P->ev[2], st));
     MDSIP_CUDA(cudaMemcpyAsync(P->hint, P->binertia.ptr, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     MDSIP_CUDA(cudaMemcpyAsync(P->hint + 4, P->berr.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -1275,6 +1276,7 @@ mdsip_status mdsip_ldlt_solve(mdsip_ctx *hctx, int64_t N, const double *L, const
         char *w = static_cast<char *>(ctx->scratch_at_least(ws + 256));
         int *err = reinterpret_cast<int *>(w + ws);
         MDSIP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+        launch_ldlt_solve_prepare(ctx->stream, N, L, w);
         launch_ldlt_solve_coop(ctx->stream, ctx->num_sms, N, L, Dd, Doff, perm, nrhs, B, ldb, w, err);
         int herr = 0;
         MDSIP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
