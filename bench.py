@@ -37,9 +37,11 @@ UNIT = "Newton steps/s"
 # FP64 ALU peak of a GB300: 152 SMs x 2 DFMA/clk (4 flop) x 2.07 GHz.  A DFMA
 # microbenchmark reached 1.20 TFLOP/s at ~1.97 GHz on this machine.
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
-# DRAM bytes per launch of the FP64 condensation kernel from an ncu capture
-# of the current kernel (profiles/syrk_fp64_mds1.md); None when not captured.
-SYRK_TRAFFIC_BYTES = None
+# DRAM bytes per launch of the FP64 condensation kernel at n_d = 2000,
+# m_E = 100000, scaled from an ncu capture of the current kernel at m = 20000
+# (profiles/syrk_fp64_m20000_n2000.md): reads of A grow with m, the split
+# partial writes do not.
+SYRK_TRAFFIC_BYTES = 5 * 326.235648e6 + 183.443456e6
 
 
 def parse():
@@ -354,7 +356,7 @@ def run_gpu(args):
     roofline = {"kernel": "k_syrk_fp64 (A^T W^-1 A, FP64 DFMA)", "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
-                "traffic": SYRK_TRAFFIC_BYTES,
+                "traffic": SYRK_TRAFFIC_BYTES if (D["n_d"], D["m_E"]) == (2000, 100000) else None,
                 "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (FP64 is not in MEASURED_PEAKS.json)",
                 "flops_per_launch": flops, "avg_launch_ms": syrk_ms, "launches": stats["n_syrk"],
                 "share_of_step": stats["t_syrk_ms"] / (1e3 * elapsed) if elapsed else None}
