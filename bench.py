@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=2, help="oracle steps in the CPU baseline sample")
     ap.add_argument("--variants", default="bf16,tf32",
                     help="tensor-core precisions also timed on the same instance (comma list, '' for none)")
+    ap.add_argument("--batch-count", type=int, default=32,
+                    help="instances of the batched measurement (0: skip); n_d ~ U{64..batch-max-nd}")
+    ap.add_argument("--batch-max-nd", type=int, default=512)
     ap.add_argument("--kernel", choices=["syrk", "syrk_bf16", "syrk_tf32", "ldlt"], default=None,
                     help="time one kernel-level C-ABI call instead of the Newton step")
     ap.add_argument("--m", type=int, default=100000, help="--kernel syrk: rows of A")
@@ -205,6 +208,48 @@ def run_reference(args):
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
+def run_batch(args, m, torch, local):
+    """Many independent instances (one IPM solve each): sequential on one stream
+    vs mdsip_batch_solve with one context/stream per instance."""
+    import numpy as np
+    import synth
+    rng = np.random.default_rng(7)
+    sizes = rng.integers(64, args.batch_max_nd + 1, size=args.batch_count)
+    insts = [synth.make_instance(int(nd), int(50 * nd), 50, 0.01, seed=1000 + i) for i, nd in enumerate(sizes)]
+    out = {"instances": len(insts), "n_d_range": [int(sizes.min()), int(sizes.max())],
+           "shape": "n_s = 100 n_d, m_E = 50 n_d, m_I = 50, a_i ~ N(0, 0.01^2), seeds 1000+i"}
+    streams = [torch.cuda.Stream(device=local) for _ in insts]
+    ctxs = [m.mdsip_ctx_create(local, st.cuda_stream) for st in streams]
+    probs = [m.mdsip_problem_create_synthetic(c, **m.synth_arrays(inst)) for c, inst in zip(ctxs, insts)]
+    try:
+        for name, prec in (("fp64", m.MDSIP_PREC_FP64), ("bf16", m.MDSIP_PREC_BF16)):
+            for p in probs:
+                m.mdsip_set_option_int(p, "precision", prec)
+            m.mdsip_batch_solve(probs[:4])                   # warm the workspaces of a few
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            seq = [m.mdsip_solve(p) for p in probs]
+            t_seq = time.perf_counter() - t0
+            iters = sum(m.mdsip_get_stats(p)["iters"] for p in probs)
+            t0 = time.perf_counter()
+            bst = m.mdsip_batch_solve(probs)
+            torch.cuda.synchronize()
+            t_bat = time.perf_counter() - t0
+            out[name] = {"sequential_solves_per_s": len(probs) / t_seq, "batched_solves_per_s": len(probs) / t_bat,
+                         "batched_newton_steps_per_s": iters / t_bat,
+                         "speedup": t_seq / t_bat,
+                         "all_ok": all(m.STATUS[x] == "OK" for x in seq + bst),
+                         "statuses_sequential": {k: [m.STATUS[x] for x in seq].count(k) for k in set(m.STATUS[x] for x in seq)},
+                         "statuses_batched": {k: [m.STATUS[x] for x in bst].count(k) for k in set(m.STATUS[x] for x in bst)},
+                         "max_E0": max(m.mdsip_get_stats(p)["E0"] for p in probs)}
+    finally:
+        for p in probs:
+            m.mdsip_problem_destroy(p)
+        for c in ctxs:
+            m.mdsip_ctx_destroy(c)
+    return out
+
+
 def run_gpu(args):
     rank, world, local = dist_env()
     import numpy as np
@@ -349,6 +394,7 @@ def run_gpu(args):
 
     if rank != 0:
         return
+    batch = run_batch(args, m, torch, local) if (args.batch_count > 0 and world == 1) else None
     D = dict(n_d=inst.n_d, n_s=inst.n_s, m_E=inst.m_E, m_I=inst.m_I)
     flops = D["n_d"] * (D["n_d"] + 1) / 2 * D["m_E"] * 2.0
     syrk_ms = stats["t_syrk_ms"] / max(1, stats["n_syrk"])
@@ -384,6 +430,7 @@ def run_gpu(args):
         "clocks": clk.summary(),
         "solve": solve,
         "variants": variants,
+        "batched": batch,
         "phase_ms_per_step": {k: stats[k] / max(1, steps_done) for k in
                               ("t_condense_ms", "t_factor_ms", "t_solve_ms", "t_ls_ms", "t_syrk_ms",
                                "t_ldlt_ms")},

@@ -108,6 +108,53 @@ typedef struct {
  * inconsistent bounds), OOM, CUDA. */
 mdsip_status mdsip_problem_create_synthetic(mdsip_ctx *ctx, const mdsip_synth_data *data, int mem,
                                             mdsip_problem **out);
+/* ------------------------------------------------------------------------- */
+/* Problem given by callbacks (Section 2 problem statement; Section 3.3:     */
+/* dense blocks are passed as double* with a leading dimension).             */
+/*                                                                           */
+/* Every pointer a callback receives is a device pointer on the context's    */
+/* device; `stream` is the context's stream and all the callback's device    */
+/* work must be ordered on it.  A callback returns 0 on success; any other   */
+/* value stops the call in progress with MDSIP_ERR_CALLBACK.  Variables are  */
+/* x = [x_s (n_s); x_d (n_d)].  Requirements: J_sh = 0 (inequalities depend  */
+/* on x_d only), the x_s Hessian block is diagonal (A2), no cross Hessian   */
+/* (A1).                                                                     */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    /* f(x) into f[0] */
+    int (*eval_f)(void *user, void *stream, const double *x, double *f);
+    /* grad f(x) into grad[0..n) */
+    int (*eval_grad_f)(void *user, void *stream, const double *x, double *grad);
+    /* g(x) into g[0..m_E) and h(x) into h[0..m_I) (values, not residuals) */
+    int (*eval_cons)(void *user, void *stream, const double *x, double *g, double *h);
+    /* Jacobian blocks at x: Jsg_vals[e] = d g_row(e) / d x_s,col(e) in the order of the
+     * triplets given at creation; A[i * lda + k] = d g_i / d x_d,k; Jdh[j * ldh + k] = d h_j / d x_d,k */
+    int (*eval_jac)(void *user, void *stream, const double *x, double *Jsg_vals, double *A, int64_t lda,
+                    double *Jdh, int64_t ldh);
+    /* Hessian of f + y_g^T g + y_h^T h: Hss[i] = diagonal of the x_s block,
+     * Hdd[p * ldd + q] = dense x_d block */
+    int (*eval_hess)(void *user, void *stream, const double *x, const double *yg, const double *yh,
+                     double *Hss, double *Hdd, int64_t ldd);
+} mdsip_callbacks;
+
+typedef struct {
+    int64_t n_d, n_s, m_E, m_I;
+    int64_t nnz_Jsg;
+} mdsip_dims;
+
+/* Create a problem evaluated by `cb` (copied; `user` is passed back
+ * unchanged).  Jsg_rows/Jsg_cols (nnz_Jsg, `mem`-tagged) give the sparsity of
+ * J_sg; the values come from eval_jac.  Bounds must be set with
+ * mdsip_set_bounds before solving.  Errors: INVALID_ARG, OOM, CUDA. */
+mdsip_status mdsip_problem_create(mdsip_ctx *ctx, const mdsip_dims *dims, const int32_t *Jsg_rows,
+                                  const int32_t *Jsg_cols, const mdsip_callbacks *cb, void *user,
+                                  int mem, mdsip_problem **out);
+
+/* Bounds of a callback problem (all `mem`-tagged; +-HUGE_VAL = none):
+ * xl, xu (n), hl, hu (m_I), g_E (m_E), x0 (n, nullable = zeros). */
+mdsip_status mdsip_set_bounds(mdsip_problem *p, const double *xl, const double *xu, const double *hl,
+                              const double *hu, const double *gE, const double *x0, int mem);
+
 void mdsip_problem_destroy(mdsip_problem *p);
 
 /* Options (Section 2.1 method constants; names as in the oracle):
@@ -136,6 +183,16 @@ mdsip_status mdsip_set_start(mdsip_problem *p, const double *packed, double mu0,
 mdsip_status mdsip_solve(mdsip_problem *p);
 
 mdsip_status mdsip_get_iterate(mdsip_problem *p, double *packed, int mem);
+
+/* Solve `count` independent problems concurrently (the "many instances"
+ * setting of Section 1.1: one IPM solve per contingency scenario).  Problems
+ * that share a context run one after another on its stream; problems on
+ * different contexts (each with its own stream) run concurrently, one host
+ * worker thread per context, at most `max_concurrent` at a time (<= 0: no
+ * limit).  statuses[i] receives problem i's mdsip_solve status.  Returns OK
+ * when every problem was attempted (check the statuses), or INVALID_ARG. */
+mdsip_status mdsip_batch_solve(mdsip_problem *const *problems, int32_t count, int32_t max_concurrent,
+                               int32_t *statuses);
 
 typedef struct {
     int32_t status;

@@ -44,6 +44,25 @@ class mdsip_synth_data(C.Structure):
                 ("xl", C.c_void_p), ("xu", C.c_void_p), ("x0", C.c_void_p)]
 
 
+EVAL_F = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p)
+EVAL_GRAD_F = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p)
+EVAL_CONS = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p)
+EVAL_JAC = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                       C.c_void_p, C.c_int64)
+EVAL_HESS = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                        C.c_void_p, C.c_int64)
+
+
+class mdsip_callbacks(C.Structure):
+    _fields_ = [("eval_f", EVAL_F), ("eval_grad_f", EVAL_GRAD_F), ("eval_cons", EVAL_CONS),
+                ("eval_jac", EVAL_JAC), ("eval_hess", EVAL_HESS)]
+
+
+class mdsip_dims(C.Structure):
+    _fields_ = [("n_d", C.c_int64), ("n_s", C.c_int64), ("m_E", C.c_int64), ("m_I", C.c_int64),
+                ("nnz_Jsg", C.c_int64)]
+
+
 class mdsip_stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("path", C.c_int32),
                 ("n_factorizations", C.c_int32), ("n_ls_trials", C.c_int64),
@@ -76,6 +95,11 @@ _SIGS = {
     "mdsip_ctx_last_error": (C.c_char_p, [C.c_void_p]),
     "mdsip_problem_create_synthetic": (C.c_int, [C.c_void_p, C.POINTER(mdsip_synth_data), C.c_int,
                                                  C.POINTER(C.c_void_p)]),
+    "mdsip_problem_create": (C.c_int, [C.c_void_p, C.POINTER(mdsip_dims), C.c_void_p, C.c_void_p,
+                                       C.POINTER(mdsip_callbacks), C.c_void_p, C.c_int,
+                                       C.POINTER(C.c_void_p)]),
+    "mdsip_set_bounds": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p, C.c_int]),
     "mdsip_problem_destroy": (None, [C.c_void_p]),
     "mdsip_set_option_int": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int64]),
     "mdsip_set_option_double": (C.c_int, [C.c_void_p, C.c_char_p, C.c_double]),
@@ -83,6 +107,7 @@ _SIGS = {
     "mdsip_set_start": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int]),
     "mdsip_solve": (C.c_int, [C.c_void_p]),
     "mdsip_get_iterate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "mdsip_batch_solve": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
     "mdsip_get_stats": (C.c_int, [C.c_void_p, C.POINTER(mdsip_stats)]),
     "mdsip_get_log": (C.c_int, [C.c_void_p, C.POINTER(mdsip_iter_rec), C.c_int32,
                                 C.POINTER(C.c_int32)]),
@@ -180,8 +205,39 @@ def mdsip_problem_create_synthetic(ctx, *, n_d, n_s, m_E, m_I, Q, c, A, gE, Jsg_
     return h.value
 
 
+_CALLBACK_KEEPALIVE = {}
+
+
+def mdsip_problem_create(ctx, *, n_d, n_s, m_E, m_I, Jsg_rows, Jsg_cols, eval_f, eval_grad_f, eval_cons,
+                         eval_jac, eval_hess, mem=MDSIP_MEM_HOST):
+    """Problem evaluated by Python callables (device pointers as ints):
+    eval_f(stream, x, f), eval_grad_f(stream, x, grad), eval_cons(stream, x, g, h),
+    eval_jac(stream, x, Jsg_vals, A, lda, Jdh, ldh), eval_hess(stream, x, yg, yh, Hss, Hdd, ldd);
+    each returns 0 on success."""
+    def wrap(fn):
+        def inner(user, stream, *args):
+            try:
+                return int(fn(stream, *args))
+            except Exception:       # an exception in a callback is a failed callback
+                return 1
+        return inner
+    cbs = mdsip_callbacks(EVAL_F(wrap(eval_f)), EVAL_GRAD_F(wrap(eval_grad_f)), EVAL_CONS(wrap(eval_cons)),
+                          EVAL_JAC(wrap(eval_jac)), EVAL_HESS(wrap(eval_hess)))
+    dims = mdsip_dims(n_d, n_s, m_E, m_I, len(Jsg_rows))
+    h = C.c_void_p()
+    _check(lib().mdsip_problem_create(ctx, C.byref(dims), _ptr(Jsg_rows), _ptr(Jsg_cols), C.byref(cbs), None,
+                                      mem, C.byref(h)), ctx)
+    _CALLBACK_KEEPALIVE[h.value] = cbs
+    return h.value
+
+
+def mdsip_set_bounds(prob, xl, xu, hl, hu, gE, x0=None, mem=MDSIP_MEM_HOST, ctx=None):
+    _check(lib().mdsip_set_bounds(prob, _ptr(xl), _ptr(xu), _ptr(hl), _ptr(hu), _ptr(gE), _ptr(x0), mem), ctx)
+
+
 def mdsip_problem_destroy(prob):
     lib().mdsip_problem_destroy(prob)
+    _CALLBACK_KEEPALIVE.pop(prob, None)
 
 
 def mdsip_set_option_int(prob, name: str, value: int, ctx=None):
@@ -206,6 +262,15 @@ def mdsip_solve(prob, ctx=None) -> int:
     if st not in SOLVE_OUTCOMES:
         _check(st, ctx)
     return st
+
+
+def mdsip_batch_solve(probs, max_concurrent=0) -> list:
+    """Solve independent problems concurrently (one worker per context); returns their statuses."""
+    n = len(probs)
+    arr = (C.c_void_p * max(1, n))(*probs)
+    st = (C.c_int32 * max(1, n))()
+    _check(lib().mdsip_batch_solve(arr, n, int(max_concurrent), st))
+    return [int(v) for v in st[:n]]
 
 
 def mdsip_get_iterate(prob, out, mem=MDSIP_MEM_HOST, ctx=None):

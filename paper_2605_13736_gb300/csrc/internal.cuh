@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -235,6 +236,27 @@ __device__ __forceinline__ bool grid_barrier(const GridBar &b, unsigned int nblo
 }
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Runs a configuration call (e.g. a kernel attribute, which is global to the
+// kernel on a device) once per device, thread-safely; returns its result.
+struct PerDeviceOnce {
+    std::mutex mu;
+    bool done[64] = {};
+    cudaError_t err[64] = {};
+    template <class F>
+    cudaError_t run(F &&f) {
+        int dev = 0;
+        const cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return f();
+        std::lock_guard<std::mutex> lk(mu);
+        if (!done[dev]) {
+            err[dev] = f();
+            done[dev] = true;
+        }
+        return err[dev];
+    }
+};
 
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in the .cu files).

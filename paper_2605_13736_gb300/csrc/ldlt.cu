@@ -43,6 +43,7 @@ namespace mdsip {
 namespace {
 
 constexpr int kBkThreads = 512;
+constexpr size_t kMaxDynSmem = 200 * 1024;   // dynamic shared memory bound of the LDL^T kernels
 
 struct BKParams {
     int N;
@@ -801,9 +802,13 @@ void launch_ldlt(cudaStream_t s, int num_sms, int64_t N, const double *S, int64_
     p.zero_tol = zero_tol;
 
     const size_t smem = 2 * (size_t)N * sizeof(double);
-    MDSIP_REQUIRE(smem <= 200 * 1024, MDSIP_ERR_INVALID_ARG, "ldlt: N too large for this kernel");
-    MDSIP_CUDA(cudaFuncSetAttribute(k_bk_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
+    MDSIP_REQUIRE(smem <= kMaxDynSmem, MDSIP_ERR_INVALID_ARG, "ldlt: N too large for this kernel");
+    // The attribute is global to the kernel: set once to the bound every launch
+    // respects (launches of different N may run concurrently from several threads).
+    static PerDeviceOnce once;
+    MDSIP_CUDA(once.run([] {
+        return cudaFuncSetAttribute(k_bk_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem);
+    }));
     int per_sm = 0;
     MDSIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bk_factor, kBkThreads, smem));
     MDSIP_REQUIRE(per_sm >= 1, MDSIP_ERR_INVALID_ARG, "ldlt: kernel does not fit on an SM");
@@ -867,9 +872,11 @@ void launch_ldlt_solve(cudaStream_t s, int64_t N, const double *L, const double 
                        int64_t ldb) {
     if (N <= 0 || nrhs <= 0) return;
     const size_t smem = (size_t)N * sizeof(double);
-    MDSIP_REQUIRE(smem <= 200 * 1024, MDSIP_ERR_INVALID_ARG, "ldlt_solve: N too large");
-    MDSIP_CUDA(cudaFuncSetAttribute(k_ldlt_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
+    MDSIP_REQUIRE(smem <= kMaxDynSmem, MDSIP_ERR_INVALID_ARG, "ldlt_solve: N too large");
+    static PerDeviceOnce once;
+    MDSIP_CUDA(once.run([] {
+        return cudaFuncSetAttribute(k_ldlt_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem);
+    }));
     k_ldlt_solve<<<(unsigned)nrhs, kSolveThreads, smem, s>>>((int)N, L, Dd, Doff, perm, B, ldb);
     MDSIP_LAUNCHED();
 }

@@ -12,6 +12,8 @@
 #include <numeric>
 #include <tuple>
 #include <atomic>
+#include <map>
+#include <thread>
 
 #include "internal.cuh"
 #include "refine.cuh"
@@ -94,6 +96,7 @@ struct Problem {
     Options opt;
     int path = MDSIP_PATH_P2;
     bool p2_ok = false;
+    bool sparse_dup = false;
     int64_t n_bounds = 0;
     int64_t N = 0;  // reduced matrix size
 
@@ -121,6 +124,14 @@ struct Problem {
     VecOps V{};
     double *xt = nullptr, *dt = nullptr, *grad = nullptr, *grad_t = nullptr, *cg = nullptr,
            *cg_t = nullptr, *ch = nullptr, *ch_t = nullptr;
+
+    // model: 0 = the built-in benchmark family, 1 = user callbacks
+    int model_kind = 0;
+    mdsip_callbacks cb{};
+    void *user = nullptr;
+    bool bounds_set = true;
+    DBuf bJsg_user, bperm_csr, bperm_csc, bg_raw, bh_raw;
+    int64_t nnz = 0;
 
     bool has_start = false;
     double start_mu0 = -1.0;
@@ -167,132 +178,127 @@ static T *upload(Ctx *ctx, DBuf &buf, const std::vector<T> &v, int64_t count) {
     return p;
 }
 
+// copy into an existing allocation (pointers held elsewhere stay valid)
+template <class T>
+static void fill(Ctx *ctx, DBuf &buf, const std::vector<T> &v, int64_t count) {
+    MDSIP_REQUIRE(buf.ptr != nullptr && (size_t)std::max<int64_t>(count, 0) * sizeof(T) <= buf.bytes,
+                  MDSIP_ERR_INVALID_ARG, "internal: buffer too small");
+    if (count > 0)
+        MDSIP_CUDA(cudaMemcpyAsync(buf.ptr, v.data(), count * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+}
+
 static double *dvec(Ctx *ctx, DBuf &b, int64_t n) {
     double *p = b.get<double>(ctx, (size_t)std::max<int64_t>(n, 1));
     MDSIP_CUDA(cudaMemsetAsync(p, 0, std::max<int64_t>(n, 1) * sizeof(double), ctx->stream));
     return p;
 }
 
-static Problem *create_synthetic(Ctx *ctx, const mdsip_synth_data *dat, int mem) {
-    MDSIP_REQUIRE(dat, MDSIP_ERR_INVALID_ARG, "null data");
-    MDSIP_REQUIRE(mem == MDSIP_MEM_HOST || mem == MDSIP_MEM_DEVICE, MDSIP_ERR_INVALID_ARG, "bad mem tag");
-    MDSIP_REQUIRE(dat->n_d >= 0 && dat->n_s >= 0 && dat->m_E >= 0 && dat->m_I >= 0 && dat->nnz_Jsg >= 0,
-                  MDSIP_ERR_INVALID_ARG, "negative size");
-    MDSIP_REQUIRE(dat->n_s + dat->n_d > 0, MDSIP_ERR_INVALID_ARG, "no variables");
-    MDSIP_REQUIRE(dat->nnz_Jsg < (1LL << 31) && dat->m_E < (1LL << 31) && dat->n_s < (1LL << 31),
+// Sparse indices of J_sg: CSR and CSC (int32), duplicates summed; perm_csr /
+// perm_csc map each stored position to the index of its triplet (used to
+// refresh the values of a callback model; duplicates are rejected there).
+struct SparseBuild {
+    std::vector<int32_t> csr_ptr, csr_col, csc_ptr, csc_row, perm_csr, perm_csc;
+    std::vector<double> csr_val, csc_val;
+    bool has_dup = false;
+    bool p2_ok = true;
+};
+
+static SparseBuild build_sparse(const Dims &D, const std::vector<int32_t> &rows, const std::vector<int32_t> &cols,
+                                const std::vector<double> &vals) {
+    SparseBuild b;
+    const int64_t n_in = (int64_t)rows.size();
+    for (int64_t e = 0; e < n_in; ++e)
+        MDSIP_REQUIRE(rows[e] >= 0 && rows[e] < D.m_E && cols[e] >= 0 && cols[e] < D.n_s, MDSIP_ERR_INVALID_ARG,
+                      "J_sg index out of range");
+    std::vector<int64_t> order((size_t)n_in);
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int64_t a, int64_t c) {
+        return std::tie(rows[a], cols[a], a) < std::tie(rows[c], cols[c], c);
+    });
+    std::vector<int32_t> r2, c2, src;
+    for (int64_t t = 0; t < n_in; ++t) {
+        const int64_t e = order[t];
+        if (!r2.empty() && r2.back() == rows[e] && c2.back() == cols[e]) {
+            b.csr_val.back() += vals[e];
+            b.has_dup = true;
+        } else {
+            r2.push_back(rows[e]);
+            c2.push_back(cols[e]);
+            b.csr_val.push_back(vals[e]);
+            src.push_back((int32_t)e);
+        }
+    }
+    const int64_t nnz = (int64_t)r2.size();
+    b.csr_ptr.assign(D.m_E + 1, 0);
+    b.csc_ptr.assign(D.n_s + 1, 0);
+    b.csc_row.resize(nnz);
+    b.csc_val.resize(nnz);
+    b.perm_csc.resize(nnz);
+    for (int64_t e = 0; e < nnz; ++e) {
+        b.csr_ptr[r2[e] + 1]++;
+        b.csc_ptr[c2[e] + 1]++;
+    }
+    for (int64_t i = 0; i < D.m_E; ++i) b.csr_ptr[i + 1] += b.csr_ptr[i];
+    for (int64_t k = 0; k < D.n_s; ++k) b.csc_ptr[k + 1] += b.csc_ptr[k];
+    std::vector<int32_t> fill(b.csc_ptr.begin(), b.csc_ptr.end() - 1);
+    for (int64_t e = 0; e < nnz; ++e) {  // rows ascending within each column
+        const int32_t pos = fill[c2[e]]++;
+        b.csc_row[pos] = r2[e];
+        b.csc_val[pos] = b.csr_val[e];
+        b.perm_csc[pos] = src[e];
+    }
+    for (int64_t k = 0; k < D.n_s; ++k)
+        if (b.csc_ptr[k + 1] - b.csc_ptr[k] > 1) b.p2_ok = false;
+    b.csr_col = std::move(c2);
+    b.perm_csr = std::move(src);
+    return b;
+}
+
+// Common part of both problem kinds: dimensions, sparse indices, iterate and
+// work vectors.  Bounds, g_E and x0 buffers are allocated (filled by the caller).
+static Problem *create_common(Ctx *ctx, int64_t n_d, int64_t n_s, int64_t m_E, int64_t m_I,
+                              const std::vector<int32_t> &rows, const std::vector<int32_t> &cols,
+                              const std::vector<double> &vals) {
+    MDSIP_REQUIRE(n_d >= 0 && n_s >= 0 && m_E >= 0 && m_I >= 0, MDSIP_ERR_INVALID_ARG, "negative size");
+    MDSIP_REQUIRE(n_s + n_d > 0, MDSIP_ERR_INVALID_ARG, "no variables");
+    MDSIP_REQUIRE((int64_t)rows.size() < (1LL << 31) && m_E < (1LL << 31) && n_s < (1LL << 31),
                   MDSIP_ERR_INVALID_ARG, "sparse block too large for 32-bit indices");
     auto P = new Problem();
     try {
         P->ctx = ctx;
         Dims &D = P->D;
-        D.n_s = dat->n_s;
-        D.n_d = dat->n_d;
-        D.m_E = dat->m_E;
-        D.m_I = dat->m_I;
+        D.n_s = n_s;
+        D.n_d = n_d;
+        D.m_E = m_E;
+        D.m_I = m_I;
         D.n = D.n_s + D.n_d;
         D.m = D.m_E + D.m_I;
         D.lda = std::max<int64_t>(4, (D.n_d + 3) / 4 * 4);
         cudaStream_t st = ctx->stream;
-
-        // host copies of the small data, validation
-        auto c = fetch(dat->c, D.n, mem);
-        auto gE = fetch(dat->gE, D.m_E, mem);
-        auto hl = fetch(dat->hl, D.m_I, mem);
-        auto hu = fetch(dat->hu, D.m_I, mem);
-        auto xl = fetch(dat->xl, D.n, mem);
-        auto xu = fetch(dat->xu, D.n, mem);
-        std::vector<double> x0 = dat->x0 ? fetch(dat->x0, D.n, mem) : std::vector<double>(D.n, 0.0);
-        auto hset = fetch(dat->h_set, D.n_d, mem);
-        auto rows = fetch(dat->Jsg_rows, dat->nnz_Jsg, mem);
-        auto cols = fetch(dat->Jsg_cols, dat->nnz_Jsg, mem);
-        auto vals = fetch(dat->Jsg_vals, dat->nnz_Jsg, mem);
-        for (int64_t i = 0; i < D.n; ++i) {
-            MDSIP_REQUIRE(!(xl[i] > xu[i]), MDSIP_ERR_INVALID_ARG, "xl > xu");
-            P->n_bounds += std::isfinite(xl[i]) + std::isfinite(xu[i]);
-        }
-        for (int64_t j = 0; j < D.m_I; ++j) {
-            MDSIP_REQUIRE(hl[j] < hu[j], MDSIP_ERR_INVALID_ARG, "need hl < hu");
-            MDSIP_REQUIRE(std::isfinite(hl[j]) || std::isfinite(hu[j]), MDSIP_ERR_INVALID_ARG,
-                          "every inequality needs a finite bound");
-            P->n_bounds += std::isfinite(hl[j]) + std::isfinite(hu[j]);
-        }
-        for (int64_t k = 0; k < D.n_d; ++k)
-            MDSIP_REQUIRE(hset[k] >= -1 && hset[k] < D.m_I, MDSIP_ERR_INVALID_ARG, "h_set out of range");
-        // sparse block: sort, merge duplicates, CSR and CSC
-        std::vector<int64_t> order((size_t)dat->nnz_Jsg);
-        std::iota(order.begin(), order.end(), 0);
-        for (int64_t e = 0; e < dat->nnz_Jsg; ++e)
-            MDSIP_REQUIRE(rows[e] >= 0 && rows[e] < D.m_E && cols[e] >= 0 && cols[e] < D.n_s,
-                          MDSIP_ERR_INVALID_ARG, "J_sg index out of range");
-        std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
-            return std::tie(rows[a], cols[a]) < std::tie(rows[b], cols[b]);
-        });
-        std::vector<int32_t> r2, c2;
-        std::vector<double> v2;
-        for (int64_t t = 0; t < (int64_t)order.size(); ++t) {
-            const int64_t e = order[t];
-            if (!r2.empty() && r2.back() == rows[e] && c2.back() == cols[e]) {
-                v2.back() += vals[e];
-            } else {
-                r2.push_back(rows[e]);
-                c2.push_back(cols[e]);
-                v2.push_back(vals[e]);
-            }
-        }
-        const int64_t nnz = (int64_t)v2.size();
-        std::vector<int32_t> csr_ptr(D.m_E + 1, 0), csc_ptr(D.n_s + 1, 0), csc_row(nnz);
-        std::vector<double> csc_val(nnz);
-        for (int64_t e = 0; e < nnz; ++e) {
-            csr_ptr[r2[e] + 1]++;
-            csc_ptr[c2[e] + 1]++;
-        }
-        for (int64_t i = 0; i < D.m_E; ++i) csr_ptr[i + 1] += csr_ptr[i];
-        for (int64_t k = 0; k < D.n_s; ++k) csc_ptr[k + 1] += csc_ptr[k];
-        {
-            std::vector<int32_t> fill(csc_ptr.begin(), csc_ptr.end() - 1);
-            for (int64_t e = 0; e < nnz; ++e) {  // rows ascending within each column
-                const int32_t pos = fill[c2[e]]++;
-                csc_row[pos] = r2[e];
-                csc_val[pos] = v2[e];
-            }
-        }
-        bool p2 = true;
-        for (int64_t k = 0; k < D.n_s; ++k)
-            if (csc_ptr[k + 1] - csc_ptr[k] > 1) p2 = false;
-        P->p2_ok = p2;
-
-        // device copies
+        SparseBuild sb = build_sparse(D, rows, cols, vals);
+        P->p2_ok = sb.p2_ok;
+        P->nnz = (int64_t)sb.csr_val.size();
+        P->sparse_dup = sb.has_dup;
         ModelView &M = P->Mv;
-        M.c = upload(ctx, P->bc, c, D.n);
-        M.gE = upload(ctx, P->bgE, gE, D.m_E);
-        M.hl = upload(ctx, P->bhl, hl, D.m_I);
-        M.hu = upload(ctx, P->bhu, hu, D.m_I);
-        M.xl = upload(ctx, P->bxl, xl, D.n);
-        M.xu = upload(ctx, P->bxu, xu, D.n);
-        upload(ctx, P->bx0, x0, D.n);
-        M.h_set = upload(ctx, P->bhset, hset, D.n_d);
-        M.csr_ptr = upload(ctx, P->bcsr_ptr, csr_ptr, D.m_E + 1);
-        M.csr_col = upload(ctx, P->bcsr_col, c2, nnz);
-        M.csr_val = upload(ctx, P->bcsr_val, v2, nnz);
-        M.csc_ptr = upload(ctx, P->bcsc_ptr, csc_ptr, D.n_s + 1);
-        M.csc_row = upload(ctx, P->bcsc_row, csc_row, nnz);
-        M.csc_val = upload(ctx, P->bcsc_val, csc_val, nnz);
-        // dense blocks (may be large: copied device-to-device or host-to-device directly)
-        const auto kind = mem == MDSIP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-        double *Q = P->bQ.get<double>(ctx, std::max<int64_t>(D.n_d * D.n_d, 1));
-        if (D.n_d > 0) {
-            MDSIP_REQUIRE(dat->Q, MDSIP_ERR_INVALID_ARG, "null Q");
-            MDSIP_CUDA(cudaMemcpyAsync(Q, dat->Q, D.n_d * D.n_d * sizeof(double), kind, st));
-        }
-        M.Q = Q;
-        double *A = P->bA.get<double>(ctx, std::max<int64_t>(D.m_E * D.lda, 1));
-        MDSIP_CUDA(cudaMemsetAsync(A, 0, std::max<int64_t>(D.m_E * D.lda, 1) * sizeof(double), st));
-        if (D.m_E > 0 && D.n_d > 0) {
-            MDSIP_REQUIRE(dat->A, MDSIP_ERR_INVALID_ARG, "null A");
-            MDSIP_CUDA(cudaMemcpy2DAsync(A, D.lda * sizeof(double), dat->A, D.n_d * sizeof(double),
-                                         D.n_d * sizeof(double), D.m_E, kind, st));
-        }
-        M.A = A;
+        M.csr_ptr = upload(ctx, P->bcsr_ptr, sb.csr_ptr, D.m_E + 1);
+        M.csr_col = upload(ctx, P->bcsr_col, sb.csr_col, P->nnz);
+        M.csr_val = upload(ctx, P->bcsr_val, sb.csr_val, P->nnz);
+        M.csc_ptr = upload(ctx, P->bcsc_ptr, sb.csc_ptr, D.n_s + 1);
+        M.csc_row = upload(ctx, P->bcsc_row, sb.csc_row, P->nnz);
+        M.csc_val = upload(ctx, P->bcsc_val, sb.csc_val, P->nnz);
+        upload(ctx, P->bperm_csr, sb.perm_csr, P->nnz);
+        upload(ctx, P->bperm_csc, sb.perm_csc, P->nnz);
+        M.c = dvec(ctx, P->bc, D.n);
+        M.gE = dvec(ctx, P->bgE, D.m_E);
+        M.hl = dvec(ctx, P->bhl, D.m_I);
+        M.hu = dvec(ctx, P->bhu, D.m_I);
+        M.xl = dvec(ctx, P->bxl, D.n);
+        M.xu = dvec(ctx, P->bxu, D.n);
+        dvec(ctx, P->bx0, D.n);
+        M.Q = dvec(ctx, P->bQ, 0);
+        M.h_set = P->bhset.get<int32_t>(ctx, std::max<int64_t>(D.n_d, 1));
+        MDSIP_CUDA(cudaMemsetAsync(P->bhset.ptr, 0xff, std::max<int64_t>(D.n_d, 1) * sizeof(int32_t), st));
+        M.A = dvec(ctx, P->bA, D.m_E * D.lda);
 
         // iterate and work vectors
         IterView &I = P->I;
@@ -341,18 +347,162 @@ static Problem *create_synthetic(Ctx *ctx, const mdsip_synth_data *dat, int mem)
         MDSIP_CUDA(cudaMallocHost(&P->hscal, SC_COUNT * sizeof(double)));
         MDSIP_CUDA(cudaMallocHost(&P->hint, 8 * sizeof(int32_t)));
         for (auto &e : P->ev) MDSIP_CUDA(cudaEventCreate(&e));
-
         P->V.D = D;
         P->V.M = M;
         P->V.st = st;
         P->V.partial = P->bpartial.as<double>();
         P->V.colpart = P->bcolpart.as<double>();
-        MDSIP_CUDA(cudaStreamSynchronize(st));
     } catch (...) {
         delete P;
         throw;
     }
     return P;
+}
+
+// bounds, g_E, x0 from host vectors (validated); counts the finite bounds
+static void set_bounds_host(Problem *P, const std::vector<double> &xl, const std::vector<double> &xu,
+                            const std::vector<double> &hl, const std::vector<double> &hu,
+                            const std::vector<double> &gE, const std::vector<double> &x0) {
+    const Dims &D = P->D;
+    int64_t nb = 0;
+    for (int64_t i = 0; i < D.n; ++i) {
+        MDSIP_REQUIRE(!(xl[i] > xu[i]), MDSIP_ERR_INVALID_ARG, "xl > xu");
+        nb += std::isfinite(xl[i]) + std::isfinite(xu[i]);
+    }
+    for (int64_t j = 0; j < D.m_I; ++j) {
+        MDSIP_REQUIRE(hl[j] < hu[j], MDSIP_ERR_INVALID_ARG, "need hl < hu");
+        MDSIP_REQUIRE(std::isfinite(hl[j]) || std::isfinite(hu[j]), MDSIP_ERR_INVALID_ARG,
+                      "every inequality needs a finite bound");
+        nb += std::isfinite(hl[j]) + std::isfinite(hu[j]);
+    }
+    P->n_bounds = nb;
+    Ctx *ctx = P->ctx;
+    fill(ctx, P->bxl, xl, D.n);
+    fill(ctx, P->bxu, xu, D.n);
+    fill(ctx, P->bhl, hl, D.m_I);
+    fill(ctx, P->bhu, hu, D.m_I);
+    fill(ctx, P->bgE, gE, D.m_E);
+    fill(ctx, P->bx0, x0, D.n);
+    MDSIP_CUDA(cudaStreamSynchronize(ctx->stream));
+    P->bounds_set = true;
+}
+
+static Problem *create_synthetic(Ctx *ctx, const mdsip_synth_data *dat, int mem) {
+    MDSIP_REQUIRE(dat, MDSIP_ERR_INVALID_ARG, "null data");
+    MDSIP_REQUIRE(mem == MDSIP_MEM_HOST || mem == MDSIP_MEM_DEVICE, MDSIP_ERR_INVALID_ARG, "bad mem tag");
+    MDSIP_REQUIRE(dat->n_d >= 0 && dat->n_s >= 0 && dat->m_E >= 0 && dat->m_I >= 0 && dat->nnz_Jsg >= 0,
+                  MDSIP_ERR_INVALID_ARG, "negative size");
+    const int64_t n = dat->n_s + dat->n_d;
+    auto rows = fetch(dat->Jsg_rows, dat->nnz_Jsg, mem);
+    auto cols = fetch(dat->Jsg_cols, dat->nnz_Jsg, mem);
+    auto vals = fetch(dat->Jsg_vals, dat->nnz_Jsg, mem);
+    Problem *P = create_common(ctx, dat->n_d, dat->n_s, dat->m_E, dat->m_I, rows, cols, vals);
+    try {
+        const Dims &D = P->D;
+        cudaStream_t st = ctx->stream;
+        auto c = fetch(dat->c, n, mem);
+        auto gE = fetch(dat->gE, D.m_E, mem);
+        auto hl = fetch(dat->hl, D.m_I, mem);
+        auto hu = fetch(dat->hu, D.m_I, mem);
+        auto xl = fetch(dat->xl, n, mem);
+        auto xu = fetch(dat->xu, n, mem);
+        std::vector<double> x0 = dat->x0 ? fetch(dat->x0, n, mem) : std::vector<double>(n, 0.0);
+        auto hset = fetch(dat->h_set, D.n_d, mem);
+        for (int64_t k = 0; k < D.n_d; ++k)
+            MDSIP_REQUIRE(hset[k] >= -1 && hset[k] < D.m_I, MDSIP_ERR_INVALID_ARG, "h_set out of range");
+        ModelView &M = P->Mv;
+        fill(ctx, P->bc, c, n);
+        fill(ctx, P->bhset, hset, D.n_d);
+        const auto kind = mem == MDSIP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+        double *Q = P->bQ.get<double>(ctx, std::max<int64_t>(D.n_d * D.n_d, 1));
+        if (D.n_d > 0) {
+            MDSIP_REQUIRE(dat->Q, MDSIP_ERR_INVALID_ARG, "null Q");
+            MDSIP_CUDA(cudaMemcpyAsync(Q, dat->Q, D.n_d * D.n_d * sizeof(double), kind, st));
+        }
+        M.Q = Q;
+        if (D.m_E > 0 && D.n_d > 0) {
+            MDSIP_REQUIRE(dat->A, MDSIP_ERR_INVALID_ARG, "null A");
+            MDSIP_CUDA(cudaMemcpy2DAsync(P->bA.ptr, D.lda * sizeof(double), dat->A, D.n_d * sizeof(double),
+                                         D.n_d * sizeof(double), D.m_E, kind, st));
+        }
+        P->V.M = M;
+        set_bounds_host(P, xl, xu, hl, hu, gE, x0);
+    } catch (...) {
+        delete P;
+        throw;
+    }
+    return P;
+}
+
+static Problem *create_callbacks(Ctx *ctx, const mdsip_dims *dims, const int32_t *rows_p, const int32_t *cols_p,
+                                 const mdsip_callbacks *cb, void *user, int mem) {
+    MDSIP_REQUIRE(dims && cb, MDSIP_ERR_INVALID_ARG, "null dims or callbacks");
+    MDSIP_REQUIRE(mem == MDSIP_MEM_HOST || mem == MDSIP_MEM_DEVICE, MDSIP_ERR_INVALID_ARG, "bad mem tag");
+    MDSIP_REQUIRE(cb->eval_f && cb->eval_grad_f && cb->eval_cons && cb->eval_jac && cb->eval_hess,
+                  MDSIP_ERR_INVALID_ARG, "every callback is required");
+    MDSIP_REQUIRE(dims->nnz_Jsg >= 0, MDSIP_ERR_INVALID_ARG, "negative nnz");
+    auto rows = fetch(rows_p, dims->nnz_Jsg, mem);
+    auto cols = fetch(cols_p, dims->nnz_Jsg, mem);
+    std::vector<double> zeros((size_t)dims->nnz_Jsg, 0.0);
+    Problem *P = create_common(ctx, dims->n_d, dims->n_s, dims->m_E, dims->m_I, rows, cols, zeros);
+    if (P->sparse_dup) {
+        delete P;
+        throw Error{MDSIP_ERR_INVALID_ARG, "duplicate J_sg triplets"};
+    }
+    P->model_kind = 1;
+    P->cb = *cb;
+    P->user = user;
+    P->bounds_set = false;
+    dvec(ctx, P->bJsg_user, P->nnz);
+    dvec(ctx, P->bg_raw, P->D.m_E);
+    dvec(ctx, P->bh_raw, P->D.m_I);
+    MDSIP_CUDA(cudaStreamSynchronize(ctx->stream));
+    return P;
+}
+
+// ---------------------------------------------------------------------------
+// Model evaluation: built-in family or callbacks
+// ---------------------------------------------------------------------------
+static void cb_check(int rc, const char *what) {
+    if (rc != 0) throw Error{MDSIP_ERR_CALLBACK, std::string("callback ") + what + " returned " + std::to_string(rc)};
+}
+
+static void model_f(Problem *P, const double *x, double *grad, double *fout) {
+    if (P->model_kind == 0) {
+        P->V.eval_f(x, grad, fout);
+        return;
+    }
+    void *st = static_cast<void *>(P->ctx->stream);
+    cb_check(P->cb.eval_f(P->user, st, x, fout), "eval_f");
+    cb_check(P->cb.eval_grad_f(P->user, st, x, grad), "eval_grad_f");
+}
+
+static void model_cons(Problem *P, const double *x, const double *d, double *cg, double *ch, double *out2) {
+    if (P->model_kind == 0) {
+        P->V.eval_cons(x, d, cg, ch, out2);
+        return;
+    }
+    cb_check(P->cb.eval_cons(P->user, static_cast<void *>(P->ctx->stream), x, P->bg_raw.as<double>(),
+                             P->bh_raw.as<double>()),
+             "eval_cons");
+    P->V.cons_from_values(P->bg_raw.as<double>(), P->bh_raw.as<double>(), d, cg, ch, out2);
+}
+
+static void model_jac_hess(Problem *P, const double *x, const double *yg, const double *yh) {
+    if (P->model_kind == 0) {
+        P->V.jac_hess(x, yh, P->bJdh.as<double>(), P->bHss.as<double>(), P->bHdd.as<double>());
+        return;
+    }
+    const Dims &D = P->D;
+    void *st = static_cast<void *>(P->ctx->stream);
+    cb_check(P->cb.eval_jac(P->user, st, x, P->bJsg_user.as<double>(), P->bA.as<double>(), D.lda,
+                            P->bJdh.as<double>(), D.n_d),
+             "eval_jac");
+    P->V.gather(P->nnz, P->bJsg_user.as<double>(), P->bperm_csr.as<int32_t>(), P->bcsr_val.as<double>());
+    P->V.gather(P->nnz, P->bJsg_user.as<double>(), P->bperm_csc.as<int32_t>(), P->bcsc_val.as<double>());
+    cb_check(P->cb.eval_hess(P->user, st, x, yg, yh, P->bHss.as<double>(), P->bHdd.as<double>(), D.n_d),
+             "eval_hess");
+    P->aft_ready = false;  // the tensor-core copy of A follows the Jacobian
 }
 
 // allocate the reduced matrix and factor storage for the chosen path
@@ -403,11 +553,7 @@ static void prepare_tc(Problem *P) {
     Ctx *ctx = P->ctx;
     const Dims &D = P->D;
     const TcPlan pl = syrk_tc_plan(D.m_E, D.n_d, ctx->num_sms, prec);
-    if (!P->aft_ready) {
-        float *AfT = P->bAfT.get<float>(ctx, (size_t)std::max<int64_t>(D.n_d, 1) * pl.ldt);
-        launch_transpose_f32(ctx->stream, P->Mv.A, D.m_E, D.n_d, D.lda, AfT, pl.ldt);
-        P->aft_ready = true;
-    }
+    if (!P->bAfT.ptr) P->bAfT.get<float>(ctx, (size_t)std::max<int64_t>(D.n_d, 1) * pl.ldt);
     if (P->tc_prec != prec) {
         P->btc_ws.get<char>(ctx, syrk_tc_workspace_bytes(pl, D.n_d, prec));
         P->btc_err.get<int>(ctx, 4);
@@ -438,6 +584,11 @@ static Inertia factor_attempt(Problem *P, double dw, double dc, bool force_fp64 
                           S);
         MDSIP_CUDA(cudaEventRecord(P->ev[8], st));
         if (P->opt.precision != MDSIP_PREC_FP64 && !force_fp64) {
+            if (!P->aft_ready) {  // FP32 transposed copy of the current A
+                const TcPlan pl = syrk_tc_plan(D.m_E, D.n_d, P->ctx->num_sms, (int)P->opt.precision);
+                launch_transpose_f32(st, P->Mv.A, D.m_E, D.n_d, D.lda, P->bAfT.as<float>(), pl.ldt);
+                P->aft_ready = true;
+            }
             MDSIP_CUDA(cudaMemsetAsync(P->btc_err.ptr, 0, sizeof(int), st));
             launch_syrk_tc(st, P->ctx->num_sms, (int)P->opt.precision, P->bAfT.as<float>(), D.m_E, D.n_d, w,
                            1.0, S, P->N, P->btc_ws.ptr, P->btc_err.as<int>());
@@ -634,7 +785,7 @@ static RefineResult direction_step_(Problem *P, double mu, double dw, double dc)
 
 // model derivatives and the Lagrangian gradient at the current point
 static void eval_derivatives(Problem *P) {
-    P->V.jac_hess(P->I.x, P->I.yh, P->bJdh.as<double>(), P->bHss.as<double>(), P->bHdd.as<double>());
+    model_jac_hess(P, P->I.x, P->I.yg, P->I.yh);
     P->V.lagrangian_grad(P->I, P->grad, P->bJdh.as<double>(), P->bATy.as<double>(), P->bgl.as<double>());
 }
 
@@ -666,6 +817,7 @@ static void swap_trial(Problem *P) {
 }
 
 static mdsip_status run_ipm(Problem *P) {
+    MDSIP_REQUIRE(P->bounds_set, MDSIP_ERR_INVALID_ARG, "bounds not set (mdsip_set_bounds)");
     prepare_path(P);
     prepare_tc(P);
     const Dims &D = P->D;
@@ -682,13 +834,13 @@ static mdsip_status run_ipm(Problem *P) {
 
     if (!P->has_start) {
         P->V.init_x(P->bx0.as<double>(), o.kappa_1, o.kappa_2, P->I);
-        P->V.eval_cons(P->I.x, P->I.d, P->cg, P->ch, sc + SC_THETA);  // ch = h(x0) - 0
+        model_cons(P, P->I.x, P->I.d, P->cg, P->ch, sc + SC_THETA);  // ch = h(x0) - 0
         P->V.init_d(P->ch, o.kappa_1, o.kappa_2, P->I);
     }
     double mu = (P->has_start && P->start_mu0 > 0) ? P->start_mu0 : o.mu0;
     double tau = std::max(o.tau_min, 1.0 - mu);
-    P->V.eval_f(P->I.x, P->grad, sc + SC_F);
-    P->V.eval_cons(P->I.x, P->I.d, P->cg, P->ch, sc + SC_THETA);
+    model_f(P, P->I.x, P->grad, sc + SC_F);
+    model_cons(P, P->I.x, P->I.d, P->cg, P->ch, sc + SC_THETA);
     P->sync_scalars();
     double f = h[SC_F], th = h[SC_THETA];
     const double theta_max = o.theta_max_fact * std::max(1.0, th);
@@ -795,8 +947,8 @@ static mdsip_status run_ipm(Problem *P) {
         MDSIP_CUDA(cudaEventRecord(P->ev[5], st));
         while (true) {
             P->V.trial(P->I, P->Dir, alpha, P->xt, P->dt, sc + SC_TRIAL);
-            P->V.eval_f(P->xt, P->grad_t, sc + SC_TF);
-            P->V.eval_cons(P->xt, P->dt, P->cg_t, P->ch_t, sc + SC_TTHETA);
+            model_f(P, P->xt, P->grad_t, sc + SC_TF);
+            model_cons(P, P->xt, P->dt, P->cg_t, P->ch_t, sc + SC_TTHETA);
             P->sync_scalars();
             f_t = h[SC_TF];
             th_t = h[SC_TTHETA];
@@ -904,8 +1056,9 @@ static void debug_direction(Problem *P, const double *packed, double mu, double 
     iterate_ptrs(P, ptr);
     copy_packed(P, ptr, packed, nullptr, mem, true);
     double *sc = P->scal();
-    P->V.eval_f(P->I.x, P->grad, sc + SC_F);
-    P->V.eval_cons(P->I.x, P->I.d, P->cg, P->ch, sc + SC_THETA);
+    MDSIP_REQUIRE(P->bounds_set, MDSIP_ERR_INVALID_ARG, "bounds not set (mdsip_set_bounds)");
+    model_f(P, P->I.x, P->grad, sc + SC_F);
+    model_cons(P, P->I.x, P->I.d, P->cg, P->ch, sc + SC_THETA);
     eval_derivatives(P);
     const Inertia in = factor_attempt(P, dw, dc);
     const int64_t saved = P->opt.refine_max;
@@ -1059,6 +1212,35 @@ mdsip_status mdsip_problem_create_synthetic(mdsip_ctx *hctx, const mdsip_synth_d
     });
 }
 
+mdsip_status mdsip_problem_create(mdsip_ctx *hctx, const mdsip_dims *dims, const int32_t *Jsg_rows,
+                                  const int32_t *Jsg_cols, const mdsip_callbacks *cb, void *user, int mem,
+                                  mdsip_problem **out) {
+    if (!hctx || !out) return MDSIP_ERR_INVALID_ARG;
+    Ctx *ctx = C_(hctx);
+    *out = nullptr;
+    return guarded(ctx, [&] {
+        DeviceGuard g(ctx->device);
+        Problem *p = create_callbacks(ctx, dims, Jsg_rows, Jsg_cols, cb, user, mem);
+        *out = reinterpret_cast<mdsip_problem *>(p);
+    });
+}
+
+mdsip_status mdsip_set_bounds(mdsip_problem *hp, const double *xl, const double *xu, const double *hl,
+                              const double *hu, const double *gE, const double *x0, int mem) {
+    if (!hp) return MDSIP_ERR_INVALID_ARG;
+    Problem *p = P_(hp);
+    return guarded(p->ctx, [&] {
+        DeviceGuard g(p->ctx->device);
+        MDSIP_REQUIRE(mem == MDSIP_MEM_HOST || mem == MDSIP_MEM_DEVICE, MDSIP_ERR_INVALID_ARG, "bad mem tag");
+        const Dims &D = p->D;
+        auto vxl = fetch(xl, D.n, mem), vxu = fetch(xu, D.n, mem);
+        auto vhl = fetch(hl, D.m_I, mem), vhu = fetch(hu, D.m_I, mem);
+        auto vgE = fetch(gE, D.m_E, mem);
+        std::vector<double> vx0 = x0 ? fetch(x0, D.n, mem) : std::vector<double>(D.n, 0.0);
+        set_bounds_host(p, vxl, vxu, vhl, vhu, vgE, vx0);
+    });
+}
+
 void mdsip_problem_destroy(mdsip_problem *hp) {
     if (!hp) return;
     Problem *p = P_(hp);
@@ -1127,6 +1309,38 @@ mdsip_status mdsip_solve(mdsip_problem *hp) {
         return s;
     }
     return result;
+}
+
+mdsip_status mdsip_batch_solve(mdsip_problem *const *problems, int32_t count, int32_t max_concurrent,
+                               int32_t *statuses) {
+    if (count < 0 || (count > 0 && (!problems || !statuses))) return MDSIP_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < count; ++i)
+        if (!problems[i]) return MDSIP_ERR_INVALID_ARG;
+    // one group per context: a context's stream (and its last-error text) is used by one thread
+    std::map<Ctx *, std::vector<int32_t>> by_ctx;
+    for (int32_t i = 0; i < count; ++i) by_ctx[P_(problems[i])->ctx].push_back(i);
+    std::vector<std::vector<int32_t>> groups;
+    for (auto &kv : by_ctx) groups.push_back(kv.second);
+    const int ngroups = (int)groups.size();
+    int nthreads = max_concurrent > 0 ? std::min<int>(max_concurrent, ngroups) : ngroups;
+    nthreads = std::max(1, nthreads);
+    std::atomic<int> next{0};
+    auto worker = [&] {
+        while (true) {
+            const int g = next.fetch_add(1);
+            if (g >= ngroups) break;
+            for (int32_t i : groups[g]) statuses[i] = (int32_t)mdsip_solve(problems[i]);
+        }
+    };
+    std::vector<std::thread> pool;
+    try {
+        for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker);
+    } catch (...) {
+        // could not start more threads: the remaining groups run on the calling thread
+    }
+    worker();
+    for (auto &t : pool) t.join();
+    return MDSIP_OK;
 }
 
 mdsip_status mdsip_get_iterate(mdsip_problem *hp, double *packed, int mem) {

@@ -417,13 +417,19 @@ void launch_syrk_tc(cudaStream_t s, int num_sms, int precision, const float *AfT
     a.work = work;
     a.err = err_dev;
     const dim3 grid((unsigned)pl.tiles, (unsigned)pl.nsplit);
-    if (tf32) {
-        MDSIP_CUDA(cudaFuncSetAttribute(k_syrk_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes));
+    static PerDeviceOnce once;
+    MDSIP_CUDA(once.run([] {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_syrk_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_syrk_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kTcSmemBytes);
+        return e;
+    }));
+    if (tf32)
         k_syrk_tc<true><<<grid, TC_THREADS, kTcSmemBytes, s>>>(tmap, a);
-    } else {
-        MDSIP_CUDA(cudaFuncSetAttribute(k_syrk_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes));
+    else
         k_syrk_tc<false><<<grid, TC_THREADS, kTcSmemBytes, s>>>(tmap, a);
-    }
     MDSIP_LAUNCHED();
     k_tc_reduce<<<(unsigned)std::min<int64_t>(n, 4096), 256, 0, s>>>(n, pl.tiles, pl.nsplit, work, beta, C, ldc);
     MDSIP_LAUNCHED();

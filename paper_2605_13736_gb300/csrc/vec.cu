@@ -675,6 +675,37 @@ __global__ void k_init_d(Dims D, ModelView M, const double *__restrict__ ch, dou
         I.d[j] = push_inside(ch[j], M.hl[j], M.hu[j], k1, k2);
 }
 
+__global__ void __launch_bounds__(NT) k_cons_from_values(Dims D, ModelView M, const double *__restrict__ g,
+                                                         const double *__restrict__ h, const double *__restrict__ d,
+                                                         double *__restrict__ cg, double *__restrict__ ch,
+                                                         double *partial) {
+    __shared__ double sh[32];
+    double s1 = 0.0, mx = 0.0;
+    const int64_t gtid = (int64_t)blockIdx.x * NT + threadIdx.x, gsz = (int64_t)gridDim.x * NT;
+    for (int64_t i = gtid; i < D.m_E; i += gsz) {
+        const double r = g[i] - M.gE[i];
+        cg[i] = r;
+        s1 += fabs(r);
+        mx = fmax(mx, fabs(r));
+    }
+    for (int64_t j = gtid; j < D.m_I; j += gsz) {
+        const double r = h[j] - d[j];
+        ch[j] = r;
+        s1 += fabs(r);
+        mx = fmax(mx, fabs(r));
+    }
+    const double a = block_sum<NT>(s1, sh);
+    if (threadIdx.x == 0) *slot(partial, 0) = a;
+    const double b = block_max<NT>(mx, sh);
+    if (threadIdx.x == 0) *slot(partial, 1) = b;
+}
+
+__global__ void k_gather(int64_t n, const double *__restrict__ src, const int32_t *__restrict__ idx,
+                         double *__restrict__ dst) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[idx[i]];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -819,6 +850,20 @@ void VecOps::init_x(const double *x0, double k1, double k2, const IterView &I) {
 
 void VecOps::init_d(const double *ch, double k1, double k2, const IterView &I) {
     k_init_d<<<elem_grid(D.m_I), 256, 0, st>>>(D, M, ch, k1, k2, I);
+    MDSIP_LAUNCHED();
+}
+
+void VecOps::cons_from_values(const double *g, const double *h, const double *d, double *cg, double *ch,
+                              double *out2) {
+    k_cons_from_values<<<kRedBlocks, NT, 0, st>>>(D, M, g, h, d, cg, ch, partial);
+    MDSIP_LAUNCHED();
+    launch_finalize_sum(st, partial, 1, out2);
+    launch_finalize_max(st, partial + kRedBlocks, 1, out2 + 1);
+}
+
+void VecOps::gather(int64_t n, const double *src, const int32_t *idx, double *dst) {
+    if (n <= 0) return;
+    k_gather<<<elem_grid(n), 256, 0, st>>>(n, src, idx, dst);
     MDSIP_LAUNCHED();
 }
 

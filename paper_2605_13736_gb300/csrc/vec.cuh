@@ -48,6 +48,11 @@ struct VecOps {
                 double ks);
     void init_x(const double *x0, double k1, double k2, const IterView &I);
     void init_d(const double *ch, double k1, double k2, const IterView &I);
+    // residuals from model values given by a callback: cg = g - g_E, ch = h - d
+    void cons_from_values(const double *g, const double *h, const double *d, double *cg, double *ch,
+                          double *out2);
+    // dst[i] = src[idx[i]]
+    void gather(int64_t n, const double *src, const int32_t *idx, double *dst);
 };
 
 // Reduced-matrix assembly (assemble.cu).
