@@ -150,8 +150,10 @@ mdsip_status mdsip_problem_create(mdsip_ctx *ctx, const mdsip_dims *dims, const 
                                   const int32_t *Jsg_cols, const mdsip_callbacks *cb, void *user,
                                   int mem, mdsip_problem **out);
 
-/* Bounds of a callback problem (all `mem`-tagged; +-HUGE_VAL = none):
- * xl, xu (n), hl, hu (m_I), g_E (m_E), x0 (n, nullable = zeros). */
+/* Bounds and right-hand sides of any problem (all `mem`-tagged; +-HUGE_VAL =
+ * none): xl, xu (n), hl, hu (m_I), g_E (m_E), x0 (n, nullable = zeros).
+ * Required once for a callback problem; on a synthetic problem it replaces
+ * the values given at creation (a member of a parametric family). */
 mdsip_status mdsip_set_bounds(mdsip_problem *p, const double *xl, const double *xu, const double *hl,
                               const double *hu, const double *gE, const double *x0, int mem);
 
@@ -183,6 +185,26 @@ mdsip_status mdsip_set_start(mdsip_problem *p, const double *packed, double mu0,
 mdsip_status mdsip_solve(mdsip_problem *p);
 
 mdsip_status mdsip_get_iterate(mdsip_problem *p, double *packed, int mem);
+
+/* ---- Learned warm start (not part of the paper's method) -----------------
+ * A network maps the parameters of a parametric family to a predicted
+ * packed primal-dual point followed by log mu0 (packed_size + 1 values); the
+ * plain method started from it remains the judge of the result (E_0 <= tol).
+ *
+ * mdsip_warmstart_target: after a solve of p, write the training target for
+ * that instance: the final packed iterate, then log of the barrier parameter
+ * of the first logged iteration whose E_0 <= e0_level (the final one if none
+ * is).  out: packed_size + 1 doubles, `mem`-tagged.  INVALID_ARG if p has not
+ * been solved.
+ *
+ * mdsip_set_start_predicted: warm start from a prediction (packed_size + 1
+ * floats, `mem`-tagged): mu0 = exp(log mu0) kept inside [tol / 10, option
+ * mu0]; x and d pushed inside their bounds by the Section 3.6 rule of W&B
+ * with kappa_1 = kappa_2 = push (0 < push < 0.5); each finite-bound
+ * multiplier at least mu0 / its slack; multipliers of infinite bounds 0; y as
+ * predicted.  Bounds must be set.  mdsip_set_start(p, NULL, ..) clears it. */
+mdsip_status mdsip_warmstart_target(mdsip_problem *p, double e0_level, double *out, int mem);
+mdsip_status mdsip_set_start_predicted(mdsip_problem *p, const float *pred, double push, int mem);
 
 /* Solve `count` independent problems concurrently (the "many instances"
  * setting of Section 1.1: one IPM solve per contingency scenario).  Problems
@@ -305,6 +327,67 @@ mdsip_status mdsip_ldlt_factor_noalloc(mdsip_ctx *ctx, int64_t N, double *S, int
 mdsip_status mdsip_ldlt_solve(mdsip_ctx *ctx, int64_t N, const double *L, const double *Dd,
                               const double *Doff, const int32_t *perm, int64_t nrhs, double *B,
                               int64_t ldb);
+
+/* ---- Warm-start network ----------------------------------------------------
+ * Two ReLU hidden layers of width n_hidden:
+ *   h1 = relu(W1 xn + b1), h2 = relu(W2 h1 + b2), yn = W3 h2 + b3,
+ * xn = (x - in_mean) / in_std per input, y = yn * out_std + out_mean per
+ * output.  Training minimises L = sum (yn - (y* - out_mean) / out_std)^2 / (B
+ * n_out) over a batch of B rows with Adam (bias-corrected; defaults beta1 0.9,
+ * beta2 0.999, eps 1e-8).  Every contraction runs in BF16 on the tensor cores
+ * with FP32 accumulation; parameters, gradients and moments are FP32.  BF16
+ * rounding (to nearest even) is applied to xn, W1, W2, W3, h1, h2, dL/dyn and
+ * the hidden-layer gradients dL/dz2, dL/dz1; bias gradients are sums of the
+ * rounded values.
+ *
+ * Parameter vector (FP32): W1 (n_hidden x n_in, row-major) | b1 | W2 (n_hidden
+ * x n_hidden) | b2 | W3 (n_out x n_hidden) | b3, each block starting at the
+ * offset mdsip_mlp_param_offsets returns (multiples of 4 floats; gaps are
+ * ignored).  New networks have zero parameters, zero means and unit standard
+ * deviations.
+ *
+ * X (inputs) and Y (targets) are DEVICE pointers to FP64 row-major matrices
+ * with row strides ldx >= n_in and ldy >= n_out; idx (device int32, nullable
+ * = rows 0..batch-1) selects the batch rows.  Errors: INVALID_ARG, OOM, CUDA,
+ * DEVICE (a tensor-core pipeline wait expired). */
+typedef struct mdsip_mlp mdsip_mlp;
+
+/* The contraction every layer uses: C[m][n] = sum_k A[m][k] B[n][k] with A
+ * (M x K) and B (N x K) BF16 row-major (raw 16-bit patterns; rows 16-byte
+ * aligned: lda, ldb multiples of 8), FP32 accumulation on the tensor cores,
+ * C FP32 row-major (ldc >= N).  Device pointers. */
+mdsip_status mdsip_gemm_bf16(mdsip_ctx *ctx, int64_t M, int64_t N, int64_t K, const uint16_t *A, int64_t lda,
+                             const uint16_t *B, int64_t ldb, float *C, int64_t ldc);
+
+mdsip_status mdsip_mlp_create(mdsip_ctx *ctx, int64_t n_in, int64_t n_hidden, int64_t n_out, mdsip_mlp **out);
+void mdsip_mlp_destroy(mdsip_mlp *m);
+int64_t mdsip_mlp_num_params(const mdsip_mlp *m);
+mdsip_status mdsip_mlp_param_offsets(const mdsip_mlp *m, int64_t offsets[6]);
+/* Set (`mem`-tagged, num_params floats) or read the parameters; setting them
+ * resets the Adam moments and step count. */
+mdsip_status mdsip_mlp_set_params(mdsip_mlp *m, const float *params, int mem);
+mdsip_status mdsip_mlp_get_params(mdsip_mlp *m, float *params, int mem);
+mdsip_status mdsip_mlp_set_adam(mdsip_mlp *m, double beta1, double beta2, double eps);
+/* Standardisation (`mem`-tagged floats; a NULL argument leaves that vector
+ * unchanged; standard deviations must be positive). */
+mdsip_status mdsip_mlp_set_scaling(mdsip_mlp *m, const float *in_mean, const float *in_std, const float *out_mean,
+                                   const float *out_std, int mem);
+mdsip_status mdsip_mlp_get_scaling(mdsip_mlp *m, float *in_mean, float *in_std, float *out_mean, float *out_std,
+                                   int mem);
+/* Column means and standard deviations of `count` rows of X and Y (FP64
+ * sums; a standard deviation below 1e-6 max(1, |mean|) is raised to it). */
+mdsip_status mdsip_mlp_fit_scaling(mdsip_mlp *m, const double *X, int64_t ldx, const double *Y, int64_t ldy,
+                                   int64_t count);
+/* Prediction y for `batch` rows of X into Y (device FP32, row stride ldy). */
+mdsip_status mdsip_mlp_forward(mdsip_mlp *m, const double *X, int64_t ldx, int64_t batch, float *Y, int64_t ldy);
+/* Loss (host, nullable) and gradient dL/dparams (device, num_params floats,
+ * nullable) of one batch, without updating the parameters. */
+mdsip_status mdsip_mlp_gradient(mdsip_mlp *m, const double *X, int64_t ldx, const double *Y, int64_t ldy,
+                                const int32_t *idx, int64_t batch, float *grad, double *loss);
+/* One Adam step with learning rate lr on one batch.  loss (host, nullable)
+ * receives the batch loss before the step; NULL avoids a synchronisation. */
+mdsip_status mdsip_mlp_train_step(mdsip_mlp *m, const double *X, int64_t ldx, const double *Y, int64_t ldy,
+                                  const int32_t *idx, int64_t batch, double lr, double *loss);
 
 #ifdef __cplusplus
 }

@@ -126,6 +126,28 @@ _SIGS = {
                                             C.c_void_p]),
     "mdsip_ldlt_solve": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_int64, C.c_void_p, C.c_int64]),
+    "mdsip_gemm_bf16": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_int64,
+                                  C.c_void_p, C.c_int64, C.c_void_p, C.c_int64]),
+    "mdsip_warmstart_target": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_int]),
+    "mdsip_set_start_predicted": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int]),
+    "mdsip_mlp_create": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.POINTER(C.c_void_p)]),
+    "mdsip_mlp_destroy": (None, [C.c_void_p]),
+    "mdsip_mlp_num_params": (C.c_int64, [C.c_void_p]),
+    "mdsip_mlp_param_offsets": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "mdsip_mlp_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "mdsip_mlp_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "mdsip_mlp_set_adam": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double]),
+    "mdsip_mlp_set_scaling": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_int]),
+    "mdsip_mlp_get_scaling": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_int]),
+    "mdsip_mlp_fit_scaling": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                        C.c_int64]),
+    "mdsip_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int64]),
+    "mdsip_mlp_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                     C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(C.c_double)]),
+    "mdsip_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                       C.c_void_p, C.c_int64, C.c_double, C.POINTER(C.c_double)]),
 }
 
 
@@ -332,6 +354,90 @@ def mdsip_ldlt_factor_noalloc(ctx, N, S, ld, zero_tol, L, Dd, Doff, perm, kind, 
 def mdsip_ldlt_solve(ctx, N, L, Dd, Doff, perm, nrhs, B, ldb):
     _check(lib().mdsip_ldlt_solve(ctx, N, _ptr(L), _ptr(Dd), _ptr(Doff), _ptr(perm), nrhs, _ptr(B),
                                   ldb), ctx)
+
+
+def mdsip_gemm_bf16(ctx, M, N, K, A, lda, B, ldb, Cmat, ldc):
+    """A, B: device bfloat16 tensors (row-major, leading dims lda, ldb); Cmat: device float32."""
+    _check(lib().mdsip_gemm_bf16(ctx, int(M), int(N), int(K), _ptr(A), int(lda), _ptr(B), int(ldb),
+                                 _ptr(Cmat), int(ldc)), ctx)
+
+
+def mdsip_warmstart_target(prob, e0_level, out, mem=MDSIP_MEM_HOST, ctx=None):
+    _check(lib().mdsip_warmstart_target(prob, float(e0_level), _ptr(out), mem), ctx)
+    return out
+
+
+def mdsip_set_start_predicted(prob, pred, push, mem=MDSIP_MEM_HOST, ctx=None):
+    _check(lib().mdsip_set_start_predicted(prob, _ptr(pred), float(push), mem), ctx)
+
+
+def mdsip_mlp_create(ctx, n_in, n_hidden, n_out):
+    out = C.c_void_p()
+    _check(lib().mdsip_mlp_create(ctx, int(n_in), int(n_hidden), int(n_out), C.byref(out)), ctx)
+    return out.value
+
+
+def mdsip_mlp_destroy(mlp):
+    if mlp:
+        lib().mdsip_mlp_destroy(mlp)
+
+
+def mdsip_mlp_num_params(mlp) -> int:
+    return int(lib().mdsip_mlp_num_params(mlp))
+
+
+def mdsip_mlp_param_offsets(mlp, ctx=None) -> list:
+    off = (C.c_int64 * 6)()
+    _check(lib().mdsip_mlp_param_offsets(mlp, off), ctx)
+    return [int(v) for v in off]
+
+
+def mdsip_mlp_set_params(mlp, params, mem=MDSIP_MEM_HOST, ctx=None):
+    _check(lib().mdsip_mlp_set_params(mlp, _ptr(params), mem), ctx)
+
+
+def mdsip_mlp_get_params(mlp, out, mem=MDSIP_MEM_HOST, ctx=None):
+    _check(lib().mdsip_mlp_get_params(mlp, _ptr(out), mem), ctx)
+    return out
+
+
+def mdsip_mlp_set_adam(mlp, beta1, beta2, eps, ctx=None):
+    _check(lib().mdsip_mlp_set_adam(mlp, float(beta1), float(beta2), float(eps)), ctx)
+
+
+def mdsip_mlp_set_scaling(mlp, in_mean=None, in_std=None, out_mean=None, out_std=None,
+                          mem=MDSIP_MEM_HOST, ctx=None):
+    _check(lib().mdsip_mlp_set_scaling(mlp, _ptr(in_mean), _ptr(in_std), _ptr(out_mean),
+                                       _ptr(out_std), mem), ctx)
+
+
+def mdsip_mlp_get_scaling(mlp, in_mean=None, in_std=None, out_mean=None, out_std=None,
+                          mem=MDSIP_MEM_HOST, ctx=None):
+    _check(lib().mdsip_mlp_get_scaling(mlp, _ptr(in_mean), _ptr(in_std), _ptr(out_mean),
+                                       _ptr(out_std), mem), ctx)
+
+
+def mdsip_mlp_fit_scaling(mlp, X, ldx, Y, ldy, count, ctx=None):
+    _check(lib().mdsip_mlp_fit_scaling(mlp, _ptr(X), int(ldx), _ptr(Y), int(ldy), int(count)), ctx)
+
+
+def mdsip_mlp_forward(mlp, X, ldx, batch, Y, ldy, ctx=None):
+    _check(lib().mdsip_mlp_forward(mlp, _ptr(X), int(ldx), int(batch), _ptr(Y), int(ldy)), ctx)
+    return Y
+
+
+def mdsip_mlp_gradient(mlp, X, ldx, Y, ldy, idx, batch, grad, ctx=None) -> float:
+    loss = C.c_double()
+    _check(lib().mdsip_mlp_gradient(mlp, _ptr(X), int(ldx), _ptr(Y), int(ldy), _ptr(idx), int(batch),
+                                    _ptr(grad), C.byref(loss)), ctx)
+    return loss.value
+
+
+def mdsip_mlp_train_step(mlp, X, ldx, Y, ldy, idx, batch, lr, want_loss=True, ctx=None):
+    loss = C.c_double()
+    _check(lib().mdsip_mlp_train_step(mlp, _ptr(X), int(ldx), _ptr(Y), int(ldy), _ptr(idx), int(batch),
+                                      float(lr), C.byref(loss) if want_loss else None), ctx)
+    return loss.value if want_loss else None
 
 
 def synth_arrays(inst) -> dict:

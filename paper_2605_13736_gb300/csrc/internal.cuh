@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <mutex>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -60,6 +61,36 @@ struct Ctx {
     void release(void *p, size_t bytes);
     void *scratch_at_least(size_t bytes);
 };
+
+// Makes `dev` current for the scope of the object.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        MDSIP_CUDA(cudaSetDevice(dev));
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// Runs fn, turning exceptions into a status and the context's last error.
+template <class F>
+inline mdsip_status guarded(Ctx *ctx, F &&fn) {
+    try {
+        fn();
+        return MDSIP_OK;
+    } catch (const Error &e) {
+        if (ctx) ctx->last_error = e.msg;
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        if (ctx) ctx->last_error = "host allocation failed";
+        return MDSIP_ERR_OOM;
+    } catch (...) {
+        if (ctx) ctx->last_error = "unknown error";
+        return MDSIP_ERR_CUDA;
+    }
+}
 
 // A device buffer owned through the context's allocator.
 struct DBuf {

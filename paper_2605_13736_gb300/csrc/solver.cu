@@ -63,16 +63,6 @@ void *Ctx::scratch_at_least(size_t bytes) {
     return scratch;
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        MDSIP_CUDA(cudaSetDevice(dev));
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
 
 // ---------------------------------------------------------------------------
 // Problem state
@@ -1120,22 +1110,6 @@ static inline const Ctx *C_(const mdsip_ctx *c) { return reinterpret_cast<const 
 static inline Problem *P_(mdsip_problem *p) { return reinterpret_cast<Problem *>(p); }
 static inline const Problem *P_(const mdsip_problem *p) { return reinterpret_cast<const Problem *>(p); }
 
-template <class F>
-static mdsip_status guarded(Ctx *ctx, F &&fn) {
-    try {
-        fn();
-        return MDSIP_OK;
-    } catch (const Error &e) {
-        if (ctx) ctx->last_error = e.msg;
-        return e.status;
-    } catch (const std::bad_alloc &) {
-        if (ctx) ctx->last_error = "host allocation failed";
-        return MDSIP_ERR_OOM;
-    } catch (...) {
-        if (ctx) ctx->last_error = "unknown error";
-        return MDSIP_ERR_CUDA;
-    }
-}
 
 extern "C" {
 
@@ -1296,6 +1270,67 @@ mdsip_status mdsip_set_start(mdsip_problem *hp, const double *packed, double mu0
     });
 }
 
+mdsip_status mdsip_set_start_predicted(mdsip_problem *hp, const float *pred, double push, int mem) {
+    if (!hp) return MDSIP_ERR_INVALID_ARG;
+    Problem *p = P_(hp);
+    return guarded(p->ctx, [&] {
+        MDSIP_REQUIRE(pred != nullptr, MDSIP_ERR_INVALID_ARG, "null prediction");
+        MDSIP_REQUIRE(push > 0.0 && push < 0.5, MDSIP_ERR_INVALID_ARG, "push must lie in (0, 0.5)");
+        MDSIP_REQUIRE(mem == MDSIP_MEM_HOST || mem == MDSIP_MEM_DEVICE, MDSIP_ERR_INVALID_ARG, "bad mem tag");
+        MDSIP_REQUIRE(p->bounds_set, MDSIP_ERR_INVALID_ARG, "bounds not set (mdsip_set_bounds)");
+        DeviceGuard g(p->ctx->device);
+        const int64_t np = mdsip_packed_size(hp);
+        cudaStream_t st = p->ctx->stream;
+        DBuf tmp;
+        const float *dpred = pred;
+        float logmu = 0.0f;
+        if (mem == MDSIP_MEM_HOST) {
+            float *d = tmp.get<float>(p->ctx, (size_t)np + 1);
+            MDSIP_CUDA(cudaMemcpyAsync(d, pred, ((size_t)np + 1) * sizeof(float), cudaMemcpyHostToDevice, st));
+            dpred = d;
+            logmu = pred[np];
+        } else {
+            MDSIP_CUDA(cudaMemcpyAsync(&logmu, pred + np, sizeof(float), cudaMemcpyDeviceToHost, st));
+            MDSIP_CUDA(cudaStreamSynchronize(st));
+        }
+        // mu0 from the predicted log mu0, kept inside [tol / 10, option mu0]
+        const double lo = std::log(p->opt.tol / 10.0), hi = std::log(p->opt.mu0);
+        const double lm = std::isfinite((double)logmu) ? std::min(hi, std::max(lo, (double)logmu)) : hi;
+        const double mu0 = std::exp(lm);
+        p->V.start_predicted(dpred, push, mu0, p->I);
+        MDSIP_CUDA(cudaStreamSynchronize(st));
+        p->has_start = true;
+        p->start_mu0 = mu0;
+    });
+}
+
+mdsip_status mdsip_warmstart_target(mdsip_problem *hp, double e0_level, double *out, int mem) {
+    if (!hp || !out) return MDSIP_ERR_INVALID_ARG;
+    Problem *p = P_(hp);
+    return guarded(p->ctx, [&] {
+        MDSIP_REQUIRE(mem == MDSIP_MEM_HOST || mem == MDSIP_MEM_DEVICE, MDSIP_ERR_INVALID_ARG, "bad mem tag");
+        MDSIP_REQUIRE(!p->log.empty(), MDSIP_ERR_INVALID_ARG, "no solve recorded");
+        DeviceGuard g(p->ctx->device);
+        double mu = p->log.back().mu;
+        for (const mdsip_iter_rec &r : p->log)
+            if (r.E0 <= e0_level) {
+                mu = r.mu;
+                break;
+            }
+        double *ptr[8];
+        iterate_ptrs(p, ptr);
+        copy_packed(p, ptr, nullptr, out, mem, false);
+        const int64_t np = mdsip_packed_size(hp);
+        const double lm = std::log(mu);
+        if (mem == MDSIP_MEM_HOST) {
+            out[np] = lm;
+        } else {
+            MDSIP_CUDA(cudaMemcpyAsync(out + np, &lm, sizeof(double), cudaMemcpyHostToDevice, p->ctx->stream));
+            MDSIP_CUDA(cudaStreamSynchronize(p->ctx->stream));
+        }
+    });
+}
+
 mdsip_status mdsip_solve(mdsip_problem *hp) {
     if (!hp) return MDSIP_ERR_INVALID_ARG;
     Problem *p = P_(hp);
@@ -1344,13 +1379,8 @@ mdsip_status mdsip_batch_solve(mdsip_problem *const *problems, int32_t count, in
 }
 
 mdsip_status mdsip_get_iterate(mdsip_problem *hp, double *packed, int mem) {
-    if (!hp) return MDSIP_ERR_INVALID_ARG;
+    if (!hp || !packed) return MDSIP_ERR_INVALID_ARG;
     Problem *p = P_(hp);
-    if (!packed) {
-        p->has_start = false;
-        p->start_mu0 = -1.0;
-        return MDSIP_OK;
-    }
     return guarded(p->ctx, [&] {
         DeviceGuard g(p->ctx->device);
         double *ptr[8];

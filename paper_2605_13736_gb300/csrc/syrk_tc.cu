@@ -23,6 +23,7 @@
 #include <mutex>
 
 #include "internal.cuh"
+#include "tc.cuh"
 
 namespace mdsip {
 
@@ -34,105 +35,16 @@ constexpr int TC_STAGES = 3;
 constexpr int SLAB_BYTES = 128;                        // K bytes per row and stage
 constexpr int TILE_BYTES = TC_TILE * SLAB_BYTES;       // 16 KiB per operand and stage
 constexpr uint32_t TMEM_COLS = 128;
-constexpr long long kWaitLimitCycles = 2000000000LL;   // ~1 s
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// wait for completion of the phase with the given parity; false on expiry
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    const uint32_t a = smem_u32(bar);
-    const long long t0 = clock64();
-    while (true) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (clock64() - t0 > kWaitLimitCycles) return false;
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tc_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand in the 128-byte-swizzle
-// canonical layout (8-row x 128-byte atoms, atoms 1024 bytes apart along M/N).
-__device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
-    d |= (uint64_t)1 << 16;                      // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: 8 rows x 128 B
-    d |= (uint64_t)1 << 46;                      // descriptor version
-    d |= (uint64_t)2 << 61;                      // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor: FP32 accumulator, A/B of one type, both K-major, M = N = 128.
-template <bool TF32>
-__host__ __device__ constexpr uint32_t instr_desc() {
-    return (1u << 4)                            // D = F32
-           | ((TF32 ? 2u : 1u) << 7)            // A = TF32 / BF16
-           | ((TF32 ? 2u : 1u) << 10)           // B = TF32 / BF16
-           | ((uint32_t)(TC_TILE >> 3) << 17)   // N / 8
-           | ((uint32_t)(TC_TILE >> 4) << 24);  // M / 16
-}
-
-template <bool TF32>
-__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-    constexpr uint32_t idesc = instr_desc<TF32>();
-    if constexpr (TF32) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
-            ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-    } else {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-            ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-    }
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
+using tc::commit;
+using tc::mbar_expect_tx;
+using tc::mbar_init;
+using tc::mbar_wait;
+using tc::smem_u32;
+using tc::sw128_kmajor_desc;
+using tc::tma_load_2d;
+using tc::tmem_ld32;
+using tc::fence_after;
+using tc::fence_before;
 
 __device__ __forceinline__ void tile_of(int t, int &tp, int &tq) {
     int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
@@ -182,14 +94,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_syrk_tc(const __grid_constant
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        tc::tmem_alloc(tmem_slot, TMEM_COLS);
     }
-    tc_fence_before();
+    fence_before();
     __syncthreads();
-    tc_fence_after();
+    fence_after();
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0 && lane == 0) {
@@ -213,20 +122,20 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_syrk_tc(const __grid_constant
                 atomicExch(a.err, 1);
                 break;
             }
-            tc_fence_after();
+            fence_after();
             const uint32_t ab = smem_u32(sA + st * TILE_BYTES), bb = smem_u32(sB + st * TILE_BYTES);
 #pragma unroll
             for (int k = 0; k < SLAB_BYTES / 32; ++k)
-                tc_mma<TF32>(tmem, sw128_kmajor_desc(ab + 32 * k), sw128_kmajor_desc(bb + 32 * k),
-                             (it > 0 || k > 0) ? 1u : 0u);
-            tc_commit(&empty[st]);
+                tc::mma<TF32, tc::instr_desc(TF32, TC_TILE, TC_TILE)>(
+                    tmem, sw128_kmajor_desc(ab + 32 * k), sw128_kmajor_desc(bb + 32 * k), (it > 0 || k > 0) ? 1u : 0u);
+            commit(&empty[st]);
         }
-        tc_commit(accum);
+        commit(accum);
     }
     __syncwarp();
     // epilogue: TMEM lanes 32w..32w+31 are rows p of the tile
     const bool ok = mbar_wait(accum, 0);
-    tc_fence_after();
+    fence_after();
     float *out = a.work + ((size_t)split * a.tiles + blockIdx.x) * (TC_TILE * TC_TILE);
     const int row = warp * 32 + lane;
     if (ok && nslab > 0) {
@@ -241,10 +150,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_syrk_tc(const __grid_constant
         if (!ok) atomicExch(a.err, 1);
         for (int c = 0; c < TC_TILE; ++c) out[(size_t)c * TC_TILE + row] = 0.0f;
     }
-    tc_fence_before();
+    fence_before();
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        tc::tmem_dealloc(tmem, TMEM_COLS);
 }
 
 // AfT[p][i] = (float) A[i][p]  (transposed FP32 copy, zero padded to ldt)
@@ -306,24 +215,6 @@ __global__ void k_tc_reduce(int64_t n, int tiles, int nsplit, const float *__res
             *c = (beta != 0.0 ? *c : 0.0) + s;
         }
     }
-}
-
-// driver entry point for tensor-map encoding (no link-time libcuda dependency)
-using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-EncodeTiledFn encode_fn() {
-    static std::once_flag once;
-    static EncodeTiledFn fn = nullptr;
-    static cudaError_t status = cudaSuccess;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q{};
-        status = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
-        if (status == cudaSuccess && q == cudaDriverEntryPointSuccess) fn = reinterpret_cast<EncodeTiledFn>(p);
-    });
-    MDSIP_REQUIRE(fn != nullptr, MDSIP_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
-    return fn;
 }
 
 }  // namespace
@@ -399,15 +290,8 @@ void launch_syrk_tc(cudaStream_t s, int num_sms, int precision, const float *AfT
 
     // tensor map over At: inner dimension K (ldt elements), outer n rows
     CUtensorMap tmap;
-    const cuuint64_t gdim[2] = {(cuuint64_t)pl.ldt, (cuuint64_t)n};
-    const cuuint64_t gstride[1] = {(cuuint64_t)pl.ldt * (tf32 ? 4 : 2)};
-    const cuuint32_t box[2] = {(cuuint32_t)pl.elems_per_slab, (cuuint32_t)TC_TILE};
-    const cuuint32_t estride[2] = {1, 1};
-    const CUresult r = encode_fn()(&tmap, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                                   At, gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    MDSIP_REQUIRE(r == CUDA_SUCCESS, MDSIP_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    tc::encode_2d(&tmap, At, tf32, (uint64_t)pl.ldt, (uint64_t)n, (uint64_t)pl.ldt, (uint32_t)pl.elems_per_slab,
+                  (uint32_t)TC_TILE);
 
     TcArgs a{};
     a.tiles = pl.tiles;
@@ -434,5 +318,44 @@ void launch_syrk_tc(cudaStream_t s, int num_sms, int precision, const float *AfT
     k_tc_reduce<<<(unsigned)std::min<int64_t>(n, 4096), 256, 0, s>>>(n, pl.tiles, pl.nsplit, work, beta, C, ldc);
     MDSIP_LAUNCHED();
 }
+
+namespace tc {
+
+// driver entry point for tensor-map encoding (no link-time libcuda dependency)
+namespace {
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_fn() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+        if (e == cudaSuccess && q == cudaDriverEntryPointSuccess) fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    MDSIP_REQUIRE(fn != nullptr, MDSIP_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
+    return fn;
+}
+}  // namespace
+
+void encode_2d(CUtensorMap *map, const void *base, bool f32, uint64_t inner, uint64_t outer, uint64_t ld,
+               uint32_t box_inner, uint32_t box_outer) {
+    const size_t esz = f32 ? 4 : 2;
+    MDSIP_REQUIRE(reinterpret_cast<uintptr_t>(base) % 16 == 0 && (ld * esz) % 16 == 0 && ld >= inner,
+                  MDSIP_ERR_INVALID_ARG, "tensor map: base or row stride not 16-byte aligned");
+    const cuuint64_t gdim[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    const cuuint64_t gstride[1] = {(cuuint64_t)(ld * esz)};
+    const cuuint32_t box[2] = {box_inner, box_outer};
+    const cuuint32_t estride[2] = {1, 1};
+    const CUresult r = encode_fn()(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                                   const_cast<void *>(base), gdim, gstride, box, estride,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    MDSIP_REQUIRE(r == CUDA_SUCCESS, MDSIP_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+}
+
+}  // namespace tc
 
 }  // namespace mdsip

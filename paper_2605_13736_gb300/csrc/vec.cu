@@ -675,6 +675,35 @@ __global__ void k_init_d(Dims D, ModelView M, const double *__restrict__ ch, dou
         I.d[j] = push_inside(ch[j], M.hl[j], M.hu[j], k1, k2);
 }
 
+// Warm start from a prediction in the packed layout [x | d | y_g | y_h | z_l |
+// z_u | v_l | v_u]: primal values pushed inside the bounds (the Section 3.6
+// rule of W&B with kappa_1 = kappa_2 = push), each finite-bound multiplier
+// raised to at least mu0 / (its slack), so that every complementarity
+// product is at least mu0; multipliers of infinite bounds are 0.
+__global__ void k_start_predicted(Dims D, ModelView M, const float *__restrict__ pred, double push, double mu0,
+                                  IterView I) {
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    const int64_t o_d = D.n, o_yg = o_d + D.m_I, o_yh = o_yg + D.m_E, o_zl = o_yh + D.m_I, o_zu = o_zl + D.n,
+                  o_vl = o_zu + D.n, o_vu = o_vl + D.m_I;
+    for (int64_t i = gtid; i < D.n; i += gsz) {
+        const double lo = M.xl[i], hi = M.xu[i];
+        const double x = push_inside((double)pred[i], lo, hi, push, push);
+        I.x[i] = x;
+        I.zl[i] = isfinite(lo) ? fmax((double)pred[o_zl + i], mu0 / (x - lo)) : 0.0;
+        I.zu[i] = isfinite(hi) ? fmax((double)pred[o_zu + i], mu0 / (hi - x)) : 0.0;
+    }
+    for (int64_t i = gtid; i < D.m_E; i += gsz) I.yg[i] = (double)pred[o_yg + i];
+    for (int64_t j = gtid; j < D.m_I; j += gsz) {
+        const double lo = M.hl[j], hi = M.hu[j];
+        const double d = push_inside((double)pred[o_d + j], lo, hi, push, push);
+        I.d[j] = d;
+        I.yh[j] = (double)pred[o_yh + j];
+        I.vl[j] = isfinite(lo) ? fmax((double)pred[o_vl + j], mu0 / (d - lo)) : 0.0;
+        I.vu[j] = isfinite(hi) ? fmax((double)pred[o_vu + j], mu0 / (hi - d)) : 0.0;
+    }
+}
+
 __global__ void __launch_bounds__(NT) k_cons_from_values(Dims D, ModelView M, const double *__restrict__ g,
                                                          const double *__restrict__ h, const double *__restrict__ d,
                                                          double *__restrict__ cg, double *__restrict__ ch,
@@ -850,6 +879,11 @@ void VecOps::init_x(const double *x0, double k1, double k2, const IterView &I) {
 
 void VecOps::init_d(const double *ch, double k1, double k2, const IterView &I) {
     k_init_d<<<elem_grid(D.m_I), 256, 0, st>>>(D, M, ch, k1, k2, I);
+    MDSIP_LAUNCHED();
+}
+
+void VecOps::start_predicted(const float *pred, double push, double mu0, const IterView &I) {
+    k_start_predicted<<<elem_grid(std::max(D.n, D.m_E)), 256, 0, st>>>(D, M, pred, push, mu0, I);
     MDSIP_LAUNCHED();
 }
 

@@ -48,6 +48,9 @@ struct VecOps {
                 double ks);
     void init_x(const double *x0, double k1, double k2, const IterView &I);
     void init_d(const double *ch, double k1, double k2, const IterView &I);
+    // Warm start from a predicted packed point `pred` (FP32): x and d pushed
+    // inside their bounds by `push`, bound multipliers at least mu0 / slack.
+    void start_predicted(const float *pred, double push, double mu0, const IterView &I);
     // residuals from model values given by a callback: cg = g - g_E, ch = h - d
     void cons_from_values(const double *g, const double *h, const double *d, double *cg, double *ch,
                           double *out2);

@@ -25,7 +25,8 @@ from __future__ import annotations
 import dataclasses
 import numpy as np
 
-__all__ = ["Instance", "CONFIGS", "make_instance", "make_config", "random_iterate"]
+__all__ = ["Instance", "CONFIGS", "make_instance", "make_config", "random_iterate", "FAMILY",
+           "family_rhs", "draw_family_params", "mlp_init"]
 
 
 @dataclasses.dataclass
@@ -63,7 +64,13 @@ CONFIGS = {
     0: dict(n_d=32, m_E=1000, m_I=1, sigma_a=0.1),        # plain FP64, reduced matrix 1033^2
     1: dict(n_d=2000, m_E=100000, m_I=50, sigma_a=0.01),  # plain FP64, OPF-like scale
     2: dict(n_d=4000, m_E=200000, m_I=50, sigma_a=0.01),  # mixed-precision scale
+    4: dict(n_d=512, m_E=25600, m_I=50, sigma_a=0.01),    # parametric family (warm start)
 }
+
+# Parametric family for the learned warm start: the instance of CONFIGS[4]
+# (seed 4) with b = b0 (1 + 0.2 p[block(i)]), p in R^64 ~ U(-1, 1), and
+# block(i) = i // 400 (64 blocks of 400 equality rows).
+FAMILY = dict(config=4, n_p=64, amplitude=0.2)
 
 
 def make_instance(n_d: int, m_E: int, m_I: int, sigma_a: float, seed: int,
@@ -137,3 +144,35 @@ def random_iterate(inst: Instance, seed: int, spread: float = 1.0) -> dict:
     yg = rng.uniform(-1.0, 1.0, size=inst.m_E)
     yh = rng.uniform(0.0, 1.0, size=m_I)
     return dict(x=x, d=d, yg=yg, yh=yh, zl=zl, zu=zu, vl=vl, vu=vu)
+
+
+def family_rhs(inst: Instance, p: np.ndarray, amplitude: float = 0.2) -> np.ndarray:
+    """Equality right-hand side of family member p: b0 (1 + amplitude p[block(i)]).
+
+    The m_E rows are cut into len(p) consecutive blocks of m_E // len(p) rows
+    (the last block takes the remainder)."""
+    p = np.asarray(p, dtype=np.float64)
+    n_p = p.shape[0]
+    size = max(1, inst.m_E // n_p)
+    block = np.minimum(np.arange(inst.m_E) // size, n_p - 1)
+    return inst.b * (1.0 + amplitude * p[block])
+
+
+def draw_family_params(count: int, n_p: int, seed: int) -> np.ndarray:
+    """count x n_p parameter vectors, i.i.d. U(-1, 1)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.uniform(-1.0, 1.0, size=(count, n_p))
+
+
+def mlp_init(n_in: int, n_hidden: int, n_out: int, seed: int, out_scale: float = 0.1) -> dict:
+    """Initial weights of the warm-start network: uniform(-r, r) with
+    r = sqrt(6 / fan_in) for the two hidden layers (He), r = out_scale
+    sqrt(3 / fan_in) for the output layer; zero biases.  FP32."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+
+    def u(rows, cols, r):
+        return rng.uniform(-r, r, size=(rows, cols)).astype(np.float32)
+
+    return dict(W1=u(n_hidden, n_in, np.sqrt(6.0 / n_in)), b1=np.zeros(n_hidden, np.float32),
+                W2=u(n_hidden, n_hidden, np.sqrt(6.0 / n_hidden)), b2=np.zeros(n_hidden, np.float32),
+                W3=u(n_out, n_hidden, out_scale * np.sqrt(3.0 / n_hidden)), b3=np.zeros(n_out, np.float32))
