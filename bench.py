@@ -44,6 +44,15 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 SYRK_TRAFFIC_BYTES = 5 * 326.235648e6 + 183.443456e6
 
 
+def measured_peak(key):
+    """A peak from MEASURED_PEAKS.json (None if the file or key is absent)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -59,10 +68,18 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=32,
                     help="instances of the batched measurement (0: skip); n_d ~ U{64..batch-max-nd}")
     ap.add_argument("--batch-max-nd", type=int, default=512)
-    ap.add_argument("--kernel", choices=["syrk", "syrk_bf16", "syrk_tf32", "ldlt"], default=None,
+    ap.add_argument("--ws-train", type=int, default=512,
+                    help="learned warm start: training solves of the parametric family (0: skip)")
+    ap.add_argument("--ws-eval", type=int, default=64, help="learned warm start: held-out members")
+    ap.add_argument("--ws-epochs", type=int, default=100)
+    ap.add_argument("--ws-workers", type=int, default=8, help="concurrent problems (contexts)")
+    ap.add_argument("--ws-only", action="store_true",
+                    help="run only the learned warm-start measurement and print its own JSON line")
+    ap.add_argument("--kernel", choices=["syrk", "syrk_bf16", "syrk_tf32", "ldlt", "gemm_bf16"], default=None,
                     help="time one kernel-level C-ABI call instead of the Newton step")
     ap.add_argument("--m", type=int, default=100000, help="--kernel syrk: rows of A")
-    ap.add_argument("--n", type=int, default=2000, help="--kernel syrk: columns of A; ldlt: N")
+    ap.add_argument("--n", type=int, default=2000, help="--kernel syrk: columns of A; ldlt: N; gemm: N")
+    ap.add_argument("--k", type=int, default=512, help="--kernel gemm_bf16: K")
     return ap.parse_args()
 
 
@@ -250,6 +267,83 @@ def run_batch(args, m, torch, local):
     return out
 
 
+def run_warmstart(args, m, torch, local):
+    """Learned warm start on the parametric family (configs[4] structure:
+    n_d = 512, n_s = 51 200, m_E = 25 600, m_I = 50, b = b0 (1 + 0.2 p),
+    p in R^64): cold solves of training members -> network trained on the GPU
+    -> warm-started solves of held-out members against their cold solves.
+    Mixed-precision (BF16 condensation + FP64 refinement) solves throughout."""
+    import numpy as np
+    import synth
+    from paper_2605_13736_gb300 import warmstart as ws
+    fam = synth.FAMILY
+    inst = synth.make_config(fam["config"])
+    n_p, W = fam["n_p"], args.ws_workers
+    streams = [torch.cuda.Stream(device=local) for _ in range(W)]
+    ctxs = [m.mdsip_ctx_create(local, st.cuda_stream) for st in streams]
+    probs = [m.mdsip_problem_create_synthetic(c, **m.synth_arrays(inst)) for c in ctxs]
+    for p, c in zip(probs, ctxs):
+        m.mdsip_set_option_int(p, "precision", m.MDSIP_PREC_BF16, c)
+
+    def set_member(prob, p):
+        m.mdsip_set_bounds(prob, inst.xl, inst.xu, inst.hl, inst.hu,
+                           synth.family_rhs(inst, p, fam["amplitude"]), inst.x0)
+
+    net = None
+    try:
+        P = m.mdsip_packed_size(probs[0])
+        train_p = synth.draw_family_params(args.ws_train, n_p, seed=41)
+        eval_p = synth.draw_family_params(args.ws_eval, n_p, seed=42)
+        dev = torch.device("cuda", local)
+        X = torch.from_numpy(train_p).to(dev)
+        Y = torch.zeros((args.ws_train, P + 1), dtype=torch.float64, device=dev)
+        gen = ws.solve_family(probs, set_member, train_p, Y, e0_level=1e-3)
+        ok = gen["statuses"] == 0
+        H = 512
+        net = ws.WarmStartNet(ctxs[0], n_p, P, hidden=H, init=synth.mlp_init(n_p, H, P + 1, seed=3))
+        batch = min(256, args.ws_train)
+        losses, t_train = net.train(X, Y, args.ws_train, epochs=args.ws_epochs, batch=batch, lr=1e-3,
+                                    lr_final=3e-5, seed=4)
+        steps = args.ws_epochs * max(1, args.ws_train // batch)
+        Xe = torch.from_numpy(eval_p).to(dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        pred = net.predict(Xe, args.ws_eval)
+        torch.cuda.synchronize(dev)
+        t_pred = time.perf_counter() - t0
+        cold = ws.solve_cold(probs, set_member, eval_p)
+        warm = ws.solve_warm(probs, set_member, eval_p, pred, push=1e-4)
+        frel = np.abs(warm["f"] - cold["f"]) / np.maximum(1.0, np.abs(cold["f"]))
+        hist = lambda st: {m.STATUS[k]: int(v) for k, v in zip(*np.unique(st, return_counts=True))}
+        return {
+            "family": f"n_d={inst.n_d}, n_s={inst.n_s}, m_E={inst.m_E}, m_I={inst.m_I}, b = b0 (1 + 0.2 p), "
+                      f"p ~ U(-1,1)^{n_p} on blocks of {inst.m_E // n_p} rows; BF16 condensation + FP64 refinement",
+            "network": f"MLP {n_p}->{H}->{H}->{P + 1} (packed primal-dual point + log mu0), BF16 tcgen05 GEMMs, "
+                       f"FP32 Adam",
+            "train_members": args.ws_train, "eval_members": args.ws_eval, "workers": W,
+            "data_generation": {"solves_per_s": args.ws_train / gen["seconds"], "seconds": gen["seconds"],
+                                "mean_iters": float(gen["iters"].mean()), "statuses": hist(gen["statuses"])},
+            "training": {"epochs": args.ws_epochs, "batch": batch, "adam_steps": steps, "seconds": t_train,
+                         "ms_per_step": 1e3 * t_train / max(1, steps), "loss_first_epoch": losses[0],
+                         "loss_last_epoch": losses[-1], "usable_targets": int(ok.sum())},
+            "inference_ms": 1e3 * t_pred,
+            "cold": {"solves_per_s": args.ws_eval / cold["seconds"], "mean_iters": float(cold["iters"].mean()),
+                     "statuses": hist(cold["statuses"]), "max_E0": float(cold["E0"].max())},
+            "warm": {"solves_per_s": args.ws_eval / warm["seconds"], "mean_iters": float(warm["iters"].mean()),
+                     "mean_iters_incl_fallback": float(warm["total_iters"].mean()),
+                     "fallbacks": int(warm["fallbacks"]), "statuses": hist(warm["statuses"]),
+                     "max_E0": float(warm["E0"].max()), "max_f_rel_diff_vs_cold": float(frel.max())},
+            "speedup_solves_per_s": cold["seconds"] / warm["seconds"],
+        }
+    finally:
+        if net is not None:
+            net.close()
+        for p in probs:
+            m.mdsip_problem_destroy(p)
+        for c in ctxs:
+            m.mdsip_ctx_destroy(c)
+
+
 def run_gpu(args):
     rank, world, local = dist_env()
     import numpy as np
@@ -395,6 +489,7 @@ def run_gpu(args):
     if rank != 0:
         return
     batch = run_batch(args, m, torch, local) if (args.batch_count > 0 and world == 1) else None
+    wstart = run_warmstart(args, m, torch, local) if (args.ws_train > 0 and world == 1) else None
     D = dict(n_d=inst.n_d, n_s=inst.n_s, m_E=inst.m_E, m_I=inst.m_I)
     flops = D["n_d"] * (D["n_d"] + 1) / 2 * D["m_E"] * 2.0
     syrk_ms = stats["t_syrk_ms"] / max(1, stats["n_syrk"])
@@ -431,11 +526,31 @@ def run_gpu(args):
         "solve": solve,
         "variants": variants,
         "batched": batch,
+        "warm_start": wstart,
         "phase_ms_per_step": {k: stats[k] / max(1, steps_done) for k in
                               ("t_condense_ms", "t_factor_ms", "t_solve_ms", "t_ls_ms", "t_syrk_ms",
                                "t_ldlt_ms")},
     }
     print(json.dumps(line))
+
+
+def run_ws_only(args):
+    """The learned warm-start measurement alone, as its own JSON line (rank 0;
+    other ranks exit)."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import torch
+    import paper_2605_13736_gb300 as m
+    m.build()
+    torch.cuda.set_device(local)
+    with ClockSampler(local) as clk:
+        ws = run_warmstart(args, m, torch, local)
+    print(json.dumps({"metric": "solves/s to 1e-8 KKT error, learned warm start vs cold start (same solver)",
+                      "value": ws["warm"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+                      "higher_is_better": True, "dtype": "bf16+f64", "data": "synthetic",
+                      "config": {"workload": "parametric family " + ws["family"]},
+                      "clocks": clk.summary(), "warm_start": ws}))
 
 
 def run_kernel(args):
@@ -467,6 +582,15 @@ def run_kernel(args):
             flops = n * (n + 1) / 2 * mm * 2.0
             prec = m.MDSIP_PREC_BF16 if args.kernel == "syrk_bf16" else m.MDSIP_PREC_TF32
             call = lambda: m.mdsip_syrk_scaled_tc(ctx, mm, n, A, n, w, 0.0, Cm, n, prec)
+        elif args.kernel == "gemm_bf16":
+            # the warm-start network's output layer: (batch m) x (outputs n) x (hidden k)
+            M, N, K = args.m, args.n, args.k
+            ld = (K + 7) // 8 * 8
+            A = torch.randn((M, ld), device="cuda").to(torch.bfloat16)
+            B = torch.randn((N, ld), device="cuda").to(torch.bfloat16)
+            Cm = torch.empty((M, N), dtype=torch.float32, device="cuda")
+            flops = 2.0 * M * N * K
+            call = lambda: m.mdsip_gemm_bf16(ctx, M, N, K, A, ld, B, ld, Cm, N)
         else:
             N = args.n
             k = N * 40 // 41
@@ -503,9 +627,18 @@ def run_kernel(args):
     finally:
         m.mdsip_ctx_destroy(ctx)
     ms = statistics.median(times)
-    print(json.dumps({"kernel": args.kernel, "m": args.m, "n": args.n, "ms_median": ms,
-                      "ms_all": times, "tflops": flops / (ms / 1e3) / 1e12,
-                      "frac_fp64_peak": flops / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS}))
+    tf = flops / (ms / 1e3) / 1e12
+    out = {"kernel": args.kernel, "m": args.m, "n": args.n, "ms_median": ms, "ms_all": times, "tflops": tf}
+    if args.kernel in ("syrk", "ldlt"):
+        out["frac_fp64_peak"] = tf / FP64_PEAK_TFLOPS
+    else:
+        peak = measured_peak("bf16_tflops")
+        if args.kernel == "syrk_tf32" and peak:
+            peak = peak / 2.0      # nominal TF32 : BF16 dense ratio 1.1 : 2.25
+        out["k"] = args.k if args.kernel == "gemm_bf16" else None
+        out["peak_tflops"] = peak
+        out["frac_of_measured_peak"] = tf / peak if peak else None
+    print(json.dumps(out))
 
 
 def main():
@@ -515,6 +648,8 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+    elif args.ws_only:
+        run_ws_only(args)
     else:
         run_gpu(args)
 

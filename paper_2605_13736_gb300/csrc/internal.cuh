@@ -340,11 +340,12 @@ void launch_ldlt_solve(cudaStream_t s, int64_t N, const double *L, const double 
 void launch_maxabs_lower(cudaStream_t s, int64_t N, const double *S, int64_t ld, double *partial,
                          double *out);
 size_t ldlt_solve_scratch_bytes(int64_t N);
-// inverses of the diagonal blocks of L (into the solve scratch); after each factorization
-void launch_ldlt_solve_prepare(cudaStream_t s, int64_t N, const double *L, void *scratch);
-void launch_ldlt_solve_coop(cudaStream_t s, int num_sms, int64_t N, const double *L, const double *Dd,
-                            const double *Doff, const int32_t *perm, int64_t nrhs, double *B, int64_t ldb,
-                            void *scratch, int *err_dev);
+// tiles of L for the solve (FP64, or FP32 when fp32), into the solve scratch; after each factorization
+void launch_ldlt_solve_prepare(cudaStream_t s, int64_t N, const double *L, void *scratch, bool fp32);
+// b_r <- K^-1 b_r with the prepared tiles (same fp32 flag)
+void launch_ldlt_solve_coop(cudaStream_t s, int num_sms, int64_t N, const double *Dd, const double *Doff,
+                            const int32_t *perm, int64_t nrhs, double *B, int64_t ldb, void *scratch, int *err_dev,
+                            bool fp32);
 // LDL^T with its scratch in a fixed device array (no allocation); N <= the limit.
 int64_t ldlt_fixed_scratch_max_n();
 void ldlt_factor_fixed_scratch(cudaStream_t s, int device, int num_sms, int64_t N, double *S,

@@ -534,211 +534,6 @@ k_ldlt_solve(int N, const double *__restrict__ L, const double *__restrict__ Dd,
     for (int i = tid; i < N; i += blockDim.x) b[perm[i]] = y[i];
 }
 
-// ---------------------------------------------------------------------------
-// Multi-CTA solve (cooperative launch, one bounded grid barrier per 64-row
-// block), using the inverses of the 64x64 unit-lower diagonal blocks of L
-// (computed once per factorization by k_inv_diag_blocks).  Forward L y = P b,
-// block B = rows [64B, 64B + 64):
-//   CTA 0   : y_B <- inv(L_BB) y_B (block B has received every earlier block),
-//             then applies blocks B-1 and B to the rows of block B+1;
-//   others  : apply block B-1 to the rows at and beyond block B+2.
-// The backward solve L^T z = D^-1 y mirrors it from the last block up.
-// ---------------------------------------------------------------------------
-constexpr int kSolveBS = 64;
-constexpr int kSolveCoopThreads = 256;
-
-// Linv[b][i][c] = inverse of the unit-lower block L[64b + i][64b + c]
-__global__ void __launch_bounds__(kSolveBS) k_inv_diag_blocks(int N, const double *__restrict__ L,
-                                                            double *__restrict__ Linv) {
-    __shared__ double T[kSolveBS][kSolveBS + 1];
-    const int b = blockIdx.x, jb = b * kSolveBS, bw = min(kSolveBS, N - jb);
-    const int c = threadIdx.x;
-    for (int j = 0; j < bw; ++j)
-        if (c < bw) T[c][j] = L[(jb + c) + (int64_t)(jb + j) * N];   // T[row][col]
-    __syncthreads();
-    // column c of the inverse: forward substitution on e_c
-    double x[kSolveBS];
-#pragma unroll
-    for (int i = 0; i < kSolveBS; ++i) x[i] = 0.0;
-    if (c < bw) {
-#pragma unroll
-        for (int i = 0; i < kSolveBS; ++i) {
-            if (i < bw) {
-                double v = (i == c) ? 1.0 : 0.0;
-#pragma unroll
-                for (int j = 0; j < kSolveBS; ++j)
-                    if (j < i) v = fma(-T[i][j], x[j], v);
-                x[i] = i < c ? 0.0 : v;
-            }
-        }
-    }
-    double *out = Linv + (size_t)b * kSolveBS * kSolveBS;
-#pragma unroll
-    for (int i = 0; i < kSolveBS; ++i)
-        if (c < kSolveBS) out[i * kSolveBS + c] = (c < bw && i < bw) ? x[i] : 0.0;
-}
-
-struct SolveParams {
-    int N;
-    const double *L, *Linv, *Dd, *Doff;
-    const int32_t *perm;
-    double *b;
-    double *y;  // N scratch
-    GridBar bar;
-};
-
-__global__ void __launch_bounds__(kSolveCoopThreads) k_ldlt_solve_coop(SolveParams p) {
-    __shared__ double s_y[2 * kSolveBS];
-    __shared__ double s_o[kSolveBS];
-    const int N = p.N;
-    const unsigned nb = gridDim.x;
-    const int cta = blockIdx.x, tid = threadIdx.x;
-    const int nblk = (N + kSolveBS - 1) / kSolveBS;
-    const double *__restrict__ L = p.L;
-    double *y = p.y;
-    const int64_t gt = (int64_t)cta * blockDim.x + tid, gs = (int64_t)nb * blockDim.x;
-    for (int64_t i = gt; i < N; i += gs) y[i] = p.b[p.perm[i]];
-    if (!grid_barrier(p.bar, nb)) return;
-    const int workers = nb > 1 ? (int)nb - 1 : 1;
-    const int widx = nb > 1 ? cta - 1 : 0;
-    const bool is_worker = nb == 1 || cta > 0;
-    const int r4 = tid >> 2, q4 = tid & 3;   // CTA 0: 64 rows x 4 quarters
-    // ---------------- forward ----------------
-    for (int B = 0; B < nblk; ++B) {
-        const int jb = B * kSolveBS, bw = min(kSolveBS, N - jb);
-        if (cta == 0) {
-            // y_B <- inv(L_BB) y_B
-            const double *Li = p.Linv + (size_t)B * kSolveBS * kSolveBS;
-            if (tid < kSolveBS) s_o[tid] = tid < bw ? __ldcg(y + jb + tid) : 0.0;
-            if (tid < kSolveBS) s_y[tid] = (B > 0) ? __ldcg(y + jb - kSolveBS + tid) : 0.0;
-            __syncthreads();
-            double acc = 0.0;
-#pragma unroll
-            for (int c = 0; c < kSolveBS / 4; ++c) {
-                const int col = q4 * (kSolveBS / 4) + c;
-                acc = fma(Li[r4 * kSolveBS + col], s_o[col], acc);
-            }
-            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-            __syncthreads();
-            if (q4 == 0 && r4 < bw) {
-                y[jb + r4] = acc;
-                s_y[kSolveBS + r4] = acc;
-            }
-            __syncthreads();
-            // blocks B-1 and B applied to block B+1's rows (64 rows x 128 columns)
-            if (B + 1 < nblk) {
-                const int nr = jb + kSolveBS, rows = min(kSolveBS, N - nr);
-                const int r = nr + r4;
-                double a2 = 0.0;
-                if (r4 < rows) {
-#pragma unroll 8
-                    for (int c = 0; c < kSolveBS / 2; ++c) {
-                        const int cc = q4 * (kSolveBS / 2) + c;    // 0..127
-                        const int blk = cc < kSolveBS ? B - 1 : B;
-                        if (blk < 0) continue;
-                        const int col = blk * kSolveBS + (cc % kSolveBS);
-                        a2 = fma(L[r + (int64_t)col * N], s_y[cc], a2);
-                    }
-                }
-                a2 += __shfl_xor_sync(0xffffffffu, a2, 1);
-                a2 += __shfl_xor_sync(0xffffffffu, a2, 2);
-                if (q4 == 0 && r4 < rows) y[r] = __ldcg(y + r) - a2;
-            }
-        }
-        if (is_worker && B >= 1) {
-            // block B-1 applied to rows >= 64 (B + 2)
-            const int c0 = (B - 1) * kSolveBS;
-            __syncthreads();   // s_y may still be read by CTA 0's part (single-CTA grid)
-            if (tid < kSolveBS) s_y[tid] = __ldcg(y + c0 + tid);
-            __syncthreads();
-            for (int64_t r = (int64_t)jb + 2 * kSolveBS + (int64_t)widx * blockDim.x + tid; r < N;
-                 r += (int64_t)workers * blockDim.x) {
-                double acc = 0.0;
-#pragma unroll 16
-                for (int j = 0; j < kSolveBS; ++j) acc = fma(L[r + (int64_t)(c0 + j) * N], s_y[j], acc);
-                y[r] = __ldcg(y + r) - acc;
-            }
-        }
-        if (!grid_barrier(p.bar, nb)) return;
-    }
-    // ---------------- D^-1 ----------------
-    for (int64_t k = gt; k < N; k += gs) {
-        const double off = p.Doff[k];
-        if (off != 0.0) {
-            const double a = p.Dd[k], c = p.Dd[k + 1];
-            const double det = a * c - off * off;
-            const double u = __ldcg(y + k), v = __ldcg(y + k + 1);
-            y[k] = (c * u - off * v) / det;
-            y[k + 1] = (a * v - off * u) / det;
-        } else if (k == 0 || p.Doff[k - 1] == 0.0) {
-            y[k] = __ldcg(y + k) / p.Dd[k];
-        }
-    }
-    if (!grid_barrier(p.bar, nb)) return;
-    // ---------------- backward ----------------
-    for (int B = nblk - 1; B >= 0; --B) {
-        const int jb = B * kSolveBS, bw = min(kSolveBS, N - jb);
-        if (cta == 0) {
-            // z_B <- inv(L_BB)^T y_B
-            const double *Li = p.Linv + (size_t)B * kSolveBS * kSolveBS;
-            if (tid < kSolveBS) s_o[tid] = tid < bw ? __ldcg(y + jb + tid) : 0.0;
-            if (tid < kSolveBS) {
-                const int nb1 = B + 1 < nblk ? min(kSolveBS, N - (jb + kSolveBS)) : 0;
-                s_y[kSolveBS + tid] = tid < nb1 ? __ldcg(y + jb + kSolveBS + tid) : 0.0;
-            }
-            __syncthreads();
-            double acc = 0.0;
-#pragma unroll
-            for (int c = 0; c < kSolveBS / 4; ++c) {
-                const int row = q4 * (kSolveBS / 4) + c;
-                acc = fma(Li[row * kSolveBS + r4], s_o[row], acc);
-            }
-            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-            __syncthreads();
-            if (q4 == 0 && r4 < bw) {
-                y[jb + r4] = acc;
-                s_y[r4] = acc;
-            }
-            __syncthreads();
-            // blocks B and B+1 applied to block B-1's rows
-            if (B > 0) {
-                const int r = jb - kSolveBS + r4;
-                double a2 = 0.0;
-#pragma unroll 8
-                for (int c = 0; c < kSolveBS / 2; ++c) {
-                    const int cc = q4 * (kSolveBS / 2) + c;
-                    const int blk = cc < kSolveBS ? B : B + 1;
-                    if (blk >= nblk) continue;
-                    const int row = blk * kSolveBS + (cc % kSolveBS);
-                    if (row >= N) continue;
-                    a2 = fma(L[row + (int64_t)r * N], s_y[cc], a2);
-                }
-                a2 += __shfl_xor_sync(0xffffffffu, a2, 1);
-                a2 += __shfl_xor_sync(0xffffffffu, a2, 2);
-                if (q4 == 0) y[r] = __ldcg(y + r) - a2;
-            }
-        }
-        if (is_worker && B + 1 < nblk) {
-            // block B+1 applied to rows < 64 (B - 1)
-            const int c0 = (B + 1) * kSolveBS, w1 = min(kSolveBS, N - c0);
-            __syncthreads();   // s_y may still be read by CTA 0's part (single-CTA grid)
-            if (tid < kSolveBS) s_y[tid] = tid < w1 ? __ldcg(y + c0 + tid) : 0.0;
-            __syncthreads();
-            const int64_t r_hi = (int64_t)jb - kSolveBS;
-            for (int64_t r = (int64_t)widx * blockDim.x + tid; r < r_hi; r += (int64_t)workers * blockDim.x) {
-                double acc = 0.0;
-                const double *Lr = L + c0 + r * (int64_t)N;
-                for (int i = 0; i < w1; ++i) acc = fma(Lr[i], s_y[i], acc);
-                y[r] = __ldcg(y + r) - acc;
-            }
-        }
-        if (!grid_barrier(p.bar, nb)) return;
-    }
-    for (int64_t i = gt; i < N; i += gs) p.b[p.perm[i]] = __ldcg(y + i);
-}
-
 __global__ void k_maxabs_lower(int64_t N, const double *S, int64_t ld, double *partial) {
     __shared__ double sh[32];
     double v = 0.0;
@@ -817,54 +612,6 @@ void launch_ldlt(cudaStream_t s, int num_sms, int64_t N, const double *S, int64_
     MDSIP_CUDA(cudaLaunchCooperativeKernel((const void *)k_bk_factor, dim3(grid), dim3(kBkThreads),
                                            args, smem, s));
     count_launch();
-}
-
-// scratch: y (N doubles), 64 bytes of barrier words, inverse diagonal blocks
-size_t ldlt_solve_scratch_bytes(int64_t N) {
-    const size_t yb = ((size_t)std::max<int64_t>(N, 1) * sizeof(double) + 255) / 256 * 256;
-    const size_t nblk = (size_t)((std::max<int64_t>(N, 1) + kSolveBS - 1) / kSolveBS);
-    return yb + 256 + nblk * kSolveBS * kSolveBS * sizeof(double);
-}
-
-// inverse diagonal blocks of L into the solve scratch (once per factorization)
-void launch_ldlt_solve_prepare(cudaStream_t s, int64_t N, const double *L, void *scratch) {
-    if (N <= 0) return;
-    const size_t yb = ((size_t)N * sizeof(double) + 255) / 256 * 256;
-    double *Linv = reinterpret_cast<double *>(static_cast<char *>(scratch) + yb + 256);
-    const int nblk = (int)((N + kSolveBS - 1) / kSolveBS);
-    k_inv_diag_blocks<<<nblk, kSolveBS, 0, s>>>((int)N, L, Linv);
-    MDSIP_LAUNCHED();
-}
-
-void launch_ldlt_solve_coop(cudaStream_t s, int num_sms, int64_t N, const double *L, const double *Dd,
-                            const double *Doff, const int32_t *perm, int64_t nrhs, double *B, int64_t ldb,
-                            void *scratch, int *err_dev) {
-    if (N <= 0 || nrhs <= 0) return;
-    char *w = static_cast<char *>(scratch);
-    const size_t ybytes = ((size_t)N * sizeof(double) + 255) / 256 * 256;
-    SolveParams p{};
-    p.N = (int)N;
-    p.L = L;
-    p.Linv = reinterpret_cast<const double *>(w + ybytes + 256);
-    p.Dd = Dd;
-    p.Doff = Doff;
-    p.perm = perm;
-    p.y = reinterpret_cast<double *>(w);
-    p.bar.count = reinterpret_cast<unsigned int *>(w + ybytes);
-    p.bar.gen = reinterpret_cast<unsigned int *>(w + ybytes + 4);
-    p.bar.err = err_dev;
-    int per_sm = 0;
-    MDSIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ldlt_solve_coop, kSolveCoopThreads, 0));
-    MDSIP_REQUIRE(per_sm >= 1, MDSIP_ERR_INVALID_ARG, "ldlt_solve: kernel does not fit on an SM");
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(num_sms, N / 16));
-    for (int64_t r = 0; r < nrhs; ++r) {
-        MDSIP_CUDA(cudaMemsetAsync(w + ybytes, 0, 64, s));
-        p.b = B + r * ldb;
-        void *args[] = {&p};
-        MDSIP_CUDA(cudaLaunchCooperativeKernel((const void *)k_ldlt_solve_coop, dim3(grid),
-                                               dim3(kSolveCoopThreads), args, 0, s));
-        count_launch();
-    }
 }
 
 void launch_ldlt_solve(cudaStream_t s, int64_t N, const double *L, const double *Dd,

@@ -220,7 +220,7 @@ void Refiner::approx_solve(const double *b, double *sol) {
     launch_gemv_t(st, M.A, D.m_E, D.n_d, D.lda, tmp_m, colpart, tmp_nd);
     k_rhs_S<<<grid_for(std::max(D.n_d, D.m_I)), 256, 0, st>>>(D, b, tmp_nd, rhsS);
     MDSIP_LAUNCHED();
-    launch_ldlt_solve_coop(st, num_sms, N, L, Dd, Doff, perm, 1, rhsS, N, solve_ws, solve_err);
+    launch_ldlt_solve_coop(st, num_sms, N, Dd, Doff, perm, 1, rhsS, N, solve_ws, solve_err, solve_fp32);
     launch_gemv_rows(st, M.A, D.m_E, D.n_d, D.lda, rhsS, tmp_m);
     k_sol_gdh<<<grid_for(std::max(D.m_E, D.n_d)), 256, 0, st>>>(D, tmp_m, bt_g, w, rhsS, sol);
     MDSIP_LAUNCHED();

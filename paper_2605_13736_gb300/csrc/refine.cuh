@@ -14,6 +14,7 @@ struct Refiner {
     const int32_t *perm;
     int num_sms;
     void *solve_ws;   // ldlt_solve_scratch_bytes(N)
+    bool solve_fp32;  // the prepared tiles are FP32
     int *solve_err;
     // Newton quantities of the current attempt
     const double *q, *w, *sig_xd, *sig_d, *Jdh, *Hdd;

@@ -124,6 +124,7 @@ struct Problem {
     int64_t nnz = 0;
 
     bool has_start = false;
+    bool solve_fp32 = false;  // tiles of the current factor are FP32 (refined tensor-core path)
     double start_mu0 = -1.0;
     std::vector<mdsip_iter_rec> log;
     mdsip_stats stats{};
@@ -599,7 +600,9 @@ static Inertia factor_attempt(Problem *P, double dw, double dc, bool force_fp64 
     MDSIP_CUDA(cudaEventRecord(P->ev[10], st));
     launch_ldlt(st, P->ctx->num_sms, P->N, S, P->N, sc + SC_MAXABS, P->opt.zero_tol, o,
                 P->bldlt_ws.ptr, P->berr.as<int>());
-    launch_ldlt_solve_prepare(st, P->N, P->bL.as<double>(), P->bsolve_ws.ptr);
+    // the refined tensor-core path solves with FP32 tiles of L; the FP64 path with FP64 tiles
+    P->solve_fp32 = p2 && P->opt.precision != MDSIP_PREC_FP64 && !force_fp64;
+    launch_ldlt_solve_prepare(st, P->N, P->bL.as<double>(), P->bsolve_ws.ptr, P->solve_fp32);
     MDSIP_CUDA(cudaEventRecord(P->ev[2], st));
     MDSIP_CUDA(cudaMemcpyAsync(P->hint, P->binertia.ptr, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     MDSIP_CUDA(cudaMemcpyAsync(P->hint + 4, P->berr.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -648,9 +651,9 @@ static void solve_direction(Problem *P, double mu, double dw) {
     P->V.rhs_y(P->I, gl, P->cg, q, p2 ? w : nullptr, mu, bt_g, p2 ? u : nullptr);
     if (p2) launch_gemv_t(st, P->Mv.A, D.m_E, D.n_d, D.lda, u, P->V.colpart, ATu);
     P->V.rhs_reduced(P->I, gl, P->ch, sig_d, ATu, bt_g, mu, dw, !p2, rhs);
-    launch_ldlt_solve_coop(st, P->ctx->num_sms, P->N, P->bL.as<double>(), P->bDd.as<double>(),
-                           P->bDoff.as<double>(), P->bperm.as<int32_t>(), 1, rhs, P->N, P->bsolve_ws.ptr,
-                           P->bsolve_err.as<int>());
+    launch_ldlt_solve_coop(st, P->ctx->num_sms, P->N, P->bDd.as<double>(), P->bDoff.as<double>(),
+                           P->bperm.as<int32_t>(), 1, rhs, P->N, P->bsolve_ws.ptr, P->bsolve_err.as<int>(),
+                           P->solve_fp32);
     if (p2) {
         launch_gemv_rows(st, P->Mv.A, D.m_E, D.n_d, D.lda, rhs, Adx);
         P->V.dyg_p2(Adx, bt_g, w, P->Dir.dyg);
@@ -686,6 +689,7 @@ static RefineResult solve_direction_refined(Problem *P, double mu, double dw, do
     R.num_sms = P->ctx->num_sms;
     R.solve_ws = P->bsolve_ws.ptr;
     R.solve_err = P->bsolve_err.as<int>();
+    R.solve_fp32 = P->solve_fp32;
     R.q = P->bq.as<double>();
     R.w = P->bw.as<double>();
     R.sig_xd = P->bsig_x.as<double>() + D.n_s;
@@ -1520,8 +1524,8 @@ mdsip_status mdsip_ldlt_solve(mdsip_ctx *hctx, int64_t N, const double *L, const
         char *w = static_cast<char *>(ctx->scratch_at_least(ws + 256));
         int *err = reinterpret_cast<int *>(w + ws);
         MDSIP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
-        launch_ldlt_solve_prepare(ctx->stream, N, L, w);
-        launch_ldlt_solve_coop(ctx->stream, ctx->num_sms, N, L, Dd, Doff, perm, nrhs, B, ldb, w, err);
+        launch_ldlt_solve_prepare(ctx->stream, N, L, w, false);
+        launch_ldlt_solve_coop(ctx->stream, ctx->num_sms, N, Dd, Doff, perm, nrhs, B, ldb, w, err, false);
         int herr = 0;
         MDSIP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
         MDSIP_CUDA(cudaStreamSynchronize(ctx->stream));

@@ -57,50 +57,46 @@ def unpack_params(mlp, flat, n_in, n_hidden, n_out) -> dict:
     return out
 
 
-def _run_batches(problems, members, prepare):
+def _run_batches(problems, members, prepare, after=None):
     """Solve members in groups of len(problems); prepare(problem, i) loads
-    member i.  Returns (statuses, iterations, seconds)."""
-    statuses = np.zeros(len(members), dtype=np.int32)
-    iters = np.zeros(len(members), dtype=np.int32)
+    member i, after(problem, i, status) runs once it is solved.  Returns
+    dict(statuses, iters, f, E0, seconds)."""
+    n = len(members)
+    out = dict(statuses=np.zeros(n, dtype=np.int32), iters=np.zeros(n, dtype=np.int32),
+               f=np.zeros(n), E0=np.zeros(n))
     t0 = time.perf_counter()
     W = len(problems)
-    for s in range(0, len(members), W):
-        group = list(range(s, min(len(members), s + W)))
+    for s in range(0, n, W):
+        group = list(range(s, min(n, s + W)))
         for j, i in enumerate(group):
             prepare(problems[j], i)
         st = mdsip_batch_solve(problems[:len(group)])
         for j, i in enumerate(group):
-            statuses[i] = st[j]
-            iters[i] = mdsip_get_stats(problems[j])["iters"]
-    return statuses, iters, time.perf_counter() - t0
+            stats = mdsip_get_stats(problems[j])
+            out["statuses"][i] = st[j]
+            out["iters"][i] = stats["iters"]
+            out["f"][i] = stats["f"]
+            out["E0"][i] = stats["E0"]
+            if after is not None:
+                after(problems[j], i, st[j])
+    out["seconds"] = time.perf_counter() - t0
+    return out
 
 
-def solve_family(problems, set_member, params, targets=None, e0_level=1e-3, on_solved=None):
+def solve_family(problems, set_member, params, targets=None, e0_level=1e-3):
     """Cold-start solves of members params[i]; if ``targets`` (device float64
     tensor, rows >= len(params), row length packed_size + 1) is given, row i
-    receives member i's training target.  Returns (statuses, iterations,
-    seconds)."""
+    receives member i's training target (members that do not reach status OK
+    leave their row unchanged).  Returns dict(statuses, iters, f, E0, seconds)."""
     def prepare(prob, i):
         set_member(prob, params[i])
         mdsip_set_start(prob, None)
 
-    statuses = np.zeros(len(params), dtype=np.int32)
-    iters = np.zeros(len(params), dtype=np.int32)
-    t0 = time.perf_counter()
-    W = len(problems)
-    for s in range(0, len(params), W):
-        group = list(range(s, min(len(params), s + W)))
-        for j, i in enumerate(group):
-            prepare(problems[j], i)
-        st = mdsip_batch_solve(problems[:len(group)])
-        for j, i in enumerate(group):
-            statuses[i] = st[j]
-            iters[i] = mdsip_get_stats(problems[j])["iters"]
-            if targets is not None and st[j] == 0:
-                mdsip_warmstart_target(problems[j], e0_level, targets[i], MDSIP_MEM_DEVICE)
-            if on_solved is not None:
-                on_solved(problems[j], i, st[j])
-    return statuses, iters, time.perf_counter() - t0
+    def after(prob, i, status):
+        if targets is not None and status == 0:
+            mdsip_warmstart_target(prob, e0_level, targets[i], MDSIP_MEM_DEVICE)
+
+    return _run_batches(problems, params, prepare, after)
 
 
 class WarmStartNet:
@@ -167,34 +163,37 @@ def solve_warm(problems, set_member, params, pred, push=1e-4, fallback=True):
     """Solve members params[i] started from pred[i] (device float32 rows of
     packed_size + 1); members whose status is not OK are solved again from the
     cold start when ``fallback``.  Returns dict(statuses, iters (warm attempt),
-    total_iters (incl. fallback), fallbacks, seconds)."""
+    total_iters (incl. fallback), f, E0, fallbacks, seconds)."""
     def prepare(prob, i):
         set_member(prob, params[i])
         mdsip_set_start_predicted(prob, pred[i], push, MDSIP_MEM_DEVICE)
 
-    statuses, iters, secs = _run_batches(problems, params, prepare)
-    total = iters.copy()
-    bad = [i for i in range(len(params)) if statuses[i] != 0]
+    r = _run_batches(problems, params, prepare)
+    r["total_iters"] = r["iters"].copy()
+    bad = [i for i in range(len(params)) if r["statuses"][i] != 0]
+    r["fallbacks"] = len(bad)
     if fallback and bad:
         def prepare_cold(prob, k):
             set_member(prob, params[bad[k]])
             mdsip_set_start(prob, None)
-        st2, it2, s2 = _run_batches(problems, bad, prepare_cold)
+        r2 = _run_batches(problems, bad, prepare_cold)
         for k, i in enumerate(bad):
-            statuses[i] = st2[k]
-            total[i] += it2[k]
-        secs += s2
-    return dict(statuses=statuses, iters=iters, total_iters=total, fallbacks=len(bad), seconds=secs)
+            r["statuses"][i] = r2["statuses"][k]
+            r["total_iters"][i] += r2["iters"][k]
+            r["f"][i] = r2["f"][k]
+            r["E0"][i] = r2["E0"][k]
+        r["seconds"] += r2["seconds"]
+    return r
 
 
 def solve_cold(problems, set_member, params):
-    """Plain cold-start solves (the reference the warm start is measured against)."""
+    """Plain cold-start solves (the reference the warm start is measured
+    against).  Returns dict(statuses, iters, f, E0, seconds)."""
     def prepare(prob, i):
         set_member(prob, params[i])
         mdsip_set_start(prob, None)
 
-    statuses, iters, secs = _run_batches(problems, params, prepare)
-    return dict(statuses=statuses, iters=iters, seconds=secs)
+    return _run_batches(problems, params, prepare)
 
 
 def output_size(problem) -> int:

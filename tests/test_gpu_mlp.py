@@ -263,8 +263,8 @@ def test_trained_network_reduces_iterations():
         eval_p = synth.draw_family_params(24, n_p, seed=2)
         X = torch.from_numpy(train_p).cuda()
         Y = torch.zeros((len(train_p), P + 1), dtype=torch.float64, device="cuda")
-        st, _, _ = ws.solve_family(probs, set_member, train_p, Y, e0_level=1e-3)
-        assert np.all(st == 0)
+        fam = ws.solve_family(probs, set_member, train_p, Y, e0_level=1e-3)
+        assert np.all(fam["statuses"] == 0)
         net = ws.WarmStartNet(ctxs[0], n_p, P, hidden=128, init=synth.mlp_init(n_p, 128, P + 1, seed=3))
         losses, _ = net.train(X, Y, len(train_p), epochs=200, batch=64, lr=3e-3, lr_final=1e-4, seed=4)
         assert losses[-1] < 0.2 * losses[0]
