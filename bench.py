@@ -75,7 +75,8 @@ def parse():
     ap.add_argument("--ws-workers", type=int, default=8, help="concurrent problems (contexts)")
     ap.add_argument("--ws-only", action="store_true",
                     help="run only the learned warm-start measurement and print its own JSON line")
-    ap.add_argument("--kernel", choices=["syrk", "syrk_bf16", "syrk_tf32", "ldlt", "gemm_bf16"], default=None,
+    ap.add_argument("--kernel", choices=["syrk", "syrk_bf16", "syrk_tf32", "ldlt", "ldlt_solve", "gemm_bf16"],
+                    default=None,
                     help="time one kernel-level C-ABI call instead of the Newton step")
     ap.add_argument("--m", type=int, default=100000, help="--kernel syrk: rows of A")
     ap.add_argument("--n", type=int, default=2000, help="--kernel syrk: columns of A; ldlt: N; gemm: N")
@@ -615,6 +616,13 @@ def run_kernel(args):
             def call():
                 S.copy_(S0)
                 m.mdsip_ldlt_factor(ctx, N, S, N, 1e-14, L, Dd, Doff, perm, kind, inr)
+            if args.kernel == "ldlt_solve":
+                call()
+                rhs = torch.randn((4, N), dtype=torch.float64, device="cuda")
+                flops = 2.0 * N * N * 4
+
+                def call():
+                    m.mdsip_ldlt_solve(ctx, N, L, Dd, Doff, perm, 4, rhs, N)
         for it in range(args.warmup + args.steps):
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -629,7 +637,7 @@ def run_kernel(args):
     ms = statistics.median(times)
     tf = flops / (ms / 1e3) / 1e12
     out = {"kernel": args.kernel, "m": args.m, "n": args.n, "ms_median": ms, "ms_all": times, "tflops": tf}
-    if args.kernel in ("syrk", "ldlt"):
+    if args.kernel in ("syrk", "ldlt", "ldlt_solve"):
         out["frac_fp64_peak"] = tf / FP64_PEAK_TFLOPS
     else:
         peak = measured_peak("bf16_tflops")

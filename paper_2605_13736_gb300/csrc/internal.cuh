@@ -333,7 +333,11 @@ struct LdltOut {
 size_t ldlt_scratch_bytes(int64_t N);
 void launch_ldlt(cudaStream_t s, int num_sms, int64_t N, const double *S, int64_t ld,
                  const double *maxabs_dev, double zero_tol, LdltOut out, void *scratch,
-                 int *err_dev);
+                 int *err_dev, bool fp32_update = false);
+size_t ldlt_blocked_scratch_bytes(int64_t N);
+bool ldlt_blocked_available(int64_t N);
+void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, const double *maxabs_dev,
+                         double zero_tol, LdltOut out, void *scratch, bool fp32_update);
 void launch_ldlt_solve(cudaStream_t s, int64_t N, const double *L, const double *Dd,
                        const double *Doff, const int32_t *perm, int64_t nrhs, double *B,
                        int64_t ldb);

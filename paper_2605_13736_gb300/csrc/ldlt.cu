@@ -545,12 +545,16 @@ __global__ void k_maxabs_lower(int64_t N, const double *S, int64_t ld, double *p
 
 }  // namespace
 
-size_t ldlt_scratch_bytes(int64_t N) {
+static size_t ldlt_unblocked_scratch_bytes(int64_t N) {
     // ping-pong buffer (N x N), then 64 bytes of barrier/flag words, then the
     // per-step pivot slots (N + 1 maxima and indices)
     const size_t b = (size_t)N * (size_t)N * sizeof(double) + 64 +
                      (size_t)(N + 1) * (sizeof(unsigned long long) + sizeof(int)) + 256;
     return (b + 255) / 256 * 256;  // callers place 8-byte data right after it
+}
+
+size_t ldlt_scratch_bytes(int64_t N) {
+    return std::max(ldlt_unblocked_scratch_bytes(N), ldlt_blocked_scratch_bytes(N));
 }
 
 void launch_maxabs_lower(cudaStream_t s, int64_t N, const double *S, int64_t ld, double *partial,
@@ -563,9 +567,9 @@ void launch_maxabs_lower(cudaStream_t s, int64_t N, const double *S, int64_t ld,
 // S: lower triangle with leading dimension ld, overwritten.  scratch:
 // ldlt_scratch_bytes(N) bytes of device memory.  err_dev: device int set to 1
 // when a bounded wait expires (must be 0 on entry).
-void launch_ldlt(cudaStream_t s, int num_sms, int64_t N, const double *S, int64_t ld,
-                 const double *maxabs_dev, double zero_tol, LdltOut out, void *scratch,
-                 int *err_dev) {
+static void launch_ldlt_unblocked(cudaStream_t s, int num_sms, int64_t N, const double *S, int64_t ld,
+                                  const double *maxabs_dev, double zero_tol, LdltOut out, void *scratch,
+                                  int *err_dev) {
     if (N <= 0) {
         MDSIP_CUDA(cudaMemsetAsync(out.inertia, 0, 3 * sizeof(int32_t), s));
         return;
@@ -612,6 +616,21 @@ void launch_ldlt(cudaStream_t s, int num_sms, int64_t N, const double *S, int64_
     MDSIP_CUDA(cudaLaunchCooperativeKernel((const void *)k_bk_factor, dim3(grid), dim3(kBkThreads),
                                            args, smem, s));
     count_launch();
+}
+
+// The factorization of the Newton step: the blocked kernels (ldlt_blocked.cu)
+// when this device can run their thread-block cluster, else the unblocked
+// persistent kernel.  fp32_update: trailing products of the blocked form in
+// FP32 (refined mixed-precision path).
+void launch_ldlt(cudaStream_t s, int num_sms, int64_t N, const double *S, int64_t ld,
+                 const double *maxabs_dev, double zero_tol, LdltOut out, void *scratch,
+                 int *err_dev, bool fp32_update) {
+    if (N > 0 && ld == N && ldlt_blocked_available(N)) {
+        launch_ldlt_blocked(s, num_sms, N, const_cast<double *>(S), maxabs_dev, zero_tol, out, scratch,
+                            fp32_update);
+        return;
+    }
+    launch_ldlt_unblocked(s, num_sms, N, S, ld, maxabs_dev, zero_tol, out, scratch, err_dev);
 }
 
 void launch_ldlt_solve(cudaStream_t s, int64_t N, const double *L, const double *Dd,
@@ -696,7 +715,7 @@ void ldlt_factor_fixed_scratch(cudaStream_t s, int device, int num_sms, int64_t 
     // launch clears its own slots and barrier words)
     MDSIP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     launch_maxabs_lower(s, N, S, ld, partial, maxabs);
-    launch_ldlt(s, num_sms, N, S, ld, maxabs, zero_tol, out, base, err);
+    launch_ldlt_unblocked(s, num_sms, N, S, ld, maxabs, zero_tol, out, base, err);
     int herr = 0;
     MDSIP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     MDSIP_CUDA(cudaStreamSynchronize(s));

@@ -1,0 +1,627 @@
+// Blocked Bunch-Kaufman LDL^T with inertia (Section 2.3): the same pivot rule
+// as the unblocked kernel in ldlt.cu (alpha = (1 + sqrt 17) / 8, LAPACK
+// ?sytf2 comparisons, first-index ties), organised as panels of NB columns
+// whose updates of the trailing matrix are delayed and applied once per panel.
+//
+// Panel (one thread-block cluster, the column pivot chain):
+//   the panel's NB + 1 columns (rows k..N-1) are distributed by contiguous row
+//   ranges over the cluster's CTAs and live in shared memory together with W,
+//   the panel's updated columns.  For each column j the cluster
+//     - updates it with the panel's earlier columns, W(:, j) = A(:, j) - L W(j, :)^T,
+//     - finds the column maximum (integer compares of |.| bit patterns, a
+//       cluster barrier, every CTA combining all CTAs' candidates through
+//       distributed shared memory, so all take the same decision),
+//     - if the rule needs it, updates column r = argmax the same way and takes
+//       its maximum,
+//     - interchanges rows/columns kk <-> kp (copying the raw column kk into
+//       position kp: column kk becomes L anyway; swapping rows kk, kp of the
+//       panel's L and W columns, of the earlier L columns, and of perm),
+//     - forms the L column(s) from W and D (1x1 or 2x2).
+//   Pivot values, the pivot test and the inertia count stay in FP64.
+// Trailing update (all SMs): A22 -= L21 W21^T on the lower triangle, W = L D;
+//   FP64 for the FP64 path, FP32 products subtracted from the FP64 matrix for
+//   the refined mixed-precision path (the update has K = NB, so it is bound by
+//   the L2 traffic of A22, not by arithmetic).
+// Panel state (next column, inertia counts) lives in device memory, so the
+// host enqueues all panels without reading anything back.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace mdsip {
+
+namespace {
+
+constexpr int kPanelThreads = 512;
+constexpr int kUpdThreads = 256;
+constexpr int kUT = 64;   // trailing-update tile edge
+
+struct PanelState {
+    int k;       // first column of the next panel
+    int kb;      // columns factored by the last panel
+    int npos, nneg, nzero;
+    int pad[3];
+};
+
+struct Cand {                  // one CTA's candidate of a cluster-wide arg-max
+    unsigned long long bits;   // |v| bit pattern
+    int idx;                   // global row (first index on ties)
+    int pad;
+    double val;                // diagonal value, when this CTA owns it
+};
+
+struct PanelArgs {
+    int N, NB, C, R;           // order, panel width, cluster size, row capacity per CTA
+    double *A;                 // lower triangle, column-major, ld N (updated in place)
+    double *L, *Dd, *Doff;
+    int32_t *perm, *kind;
+    double *Wg;                // W of the last panel: N x (NB + 1), column-major, ld N
+    PanelState *st;
+    const double *maxabs;
+    double zero_tol;
+};
+
+__device__ __forceinline__ unsigned long long absbits64(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+}
+
+__device__ __forceinline__ void cand_combine(unsigned long long &b, int &i, unsigned long long b2, int i2) {
+    if (b2 > b || (b2 == b && i2 < i)) {
+        b = b2;
+        i = i2;
+    }
+}
+
+// warp arg-max (first index on ties); result in lane 0
+__device__ __forceinline__ void warp_cand(unsigned long long &b, int &idx) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long b2 = __shfl_down_sync(0xffffffffu, b, o);
+        const int i2 = __shfl_down_sync(0xffffffffu, idx, o);
+        cand_combine(b, idx, b2, i2);
+    }
+}
+
+// block arg-max into *out (bits, idx); val = *diag (a shared-memory value
+// written before the call, read after the barrier; 0 if diag is null).
+// One __syncthreads; *out is complete when warp 0 returns.
+__device__ void block_cand_to(unsigned long long b, int idx, const double *diag, unsigned long long *sb,
+                              int *si, Cand *out) {
+    warp_cand(b, idx);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sb[wid] = b;
+        si[wid] = idx;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+        b = lane < nw ? sb[lane] : 0ULL;
+        idx = lane < nw ? si[lane] : 0x7fffffff;
+        warp_cand(b, idx);
+        if (lane == 0) {
+            out->bits = b;
+            out->idx = idx;
+            out->val = diag ? *diag : 0.0;
+        }
+    }
+}
+
+// Cluster-wide arg-max of the candidates cand[slot] of all C CTAs (C <= 32),
+// computed by warp 0: lane c reads CTA c's candidate, a shuffle reduction
+// combines them (first index on ties); lane 0 returns true with the result
+// and the diagonal value held by CTA `vrank`.
+__device__ bool cluster_cand(cg::cluster_group &cl, Cand *cand, int slot, int C, int vrank, Cand &res) {
+    if (threadIdx.x >= 32) return false;
+    const int c = threadIdx.x;
+    unsigned long long b = 0;
+    int idx = 0x7fffffff;
+    double v = 0.0;
+    if (c < C) {
+        const Cand *o = cl.map_shared_rank(cand, c) + slot;
+        b = o->bits;
+        idx = o->idx;
+        v = o->val;
+    }
+    const double vsel = __shfl_sync(0xffffffffu, v, vrank);
+    warp_cand(b, idx);
+    res.bits = b;
+    res.idx = idx;
+    res.val = vsel;
+    return c == 0;
+}
+
+__global__ void __launch_bounds__(kPanelThreads, 1) k_bk_panel(PanelArgs a) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int C = a.C, N = a.N, NB = a.NB, S = NB + 1;
+    const int tid = threadIdx.x;
+    extern __shared__ double smem[];
+    double *Ap = smem;                       // R x S: raw A columns, then L columns
+    double *Wp = Ap + (size_t)a.R * S;       // R x S: updated columns
+    double *wrow = Wp + (size_t)a.R * S;     // S: row j (or r) of W
+    Cand *cand = reinterpret_cast<Cand *>(wrow + S);   // [2]: column and row candidates
+    __shared__ unsigned long long s_b[32];
+    __shared__ int s_i[32];
+    __shared__ double s_d[6];
+    __shared__ double s_sc[2];
+    __shared__ int s_dec[3];
+
+    const int k = a.st->k;
+    if (k >= N) return;                      // uniform over the cluster
+    const int rows = N - k;
+    const int R = (rows + C - 1) / C;
+    const int r0 = min(N, k + rank * R), r1 = min(N, r0 + R);
+    const int ncols = min(S, N - k);
+    const double alpha = 0.6403882032022076;   // (1 + sqrt 17) / 8
+    const double ztol = a.zero_tol * __ldg(a.maxabs);
+    auto owner = [&](int i) { return (i - k) / R; };
+    auto rAp = [&](int i) -> double * { return cl.map_shared_rank(Ap, owner(i)) + (size_t)(i - (k + owner(i) * R)) * S; };
+    auto rWp = [&](int i) -> double * { return cl.map_shared_rank(Wp, owner(i)) + (size_t)(i - (k + owner(i) * R)) * S; };
+
+    // load the panel's columns (lower part) for the owned rows
+    const int nrows = max(0, r1 - r0);
+    for (int e = tid; e < nrows * ncols; e += kPanelThreads) {   // rows fastest: coalesced columns
+        const int t = e / nrows, lr = e % nrows, i = r0 + lr;
+        Ap[(size_t)lr * S + t] = i >= k + t ? a.A[i + (int64_t)(k + t) * N] : 0.0;
+    }
+    int npos = 0, nneg = 0, nzero = 0;
+    cl.sync();
+
+    // tpr threads per row for the row-times-W-row products (a power of two,
+    // as many as fit one pass over the owned rows)
+    int tpr = 1;
+    while (tpr < 32 && 2 * tpr * R <= kPanelThreads) tpr *= 2;
+    const int q4 = tid & (tpr - 1), rsub = tid / tpr, rpp = kPanelThreads / tpr;
+    int jj = 0;
+    while (jj < NB && k + jj < N) {
+        const int j = k + jj;
+        // ---- W(:, jj) = A(:, j) - L(:, 0:jj) W(j, 0:jj)^T over the owned rows >= j
+        if (tid < jj) wrow[tid] = rWp(j)[tid];
+        __syncthreads();
+        unsigned long long b = 0;
+        int bi = 0x7fffffff;
+        for (int lr0 = 0; lr0 < r1 - r0; lr0 += rpp) {
+            const int lr = lr0 + rsub, i = r0 + lr;
+            double s = 0.0;
+            if (lr < r1 - r0 && i >= j)
+                for (int t = q4; t < jj; t += tpr) s = fma(Ap[(size_t)lr * S + t], wrow[t], s);
+            for (int o = 1; o < tpr; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lr < r1 - r0 && i >= j && q4 == 0) {
+                const double v = Ap[(size_t)lr * S + jj] - s;
+                Wp[(size_t)lr * S + jj] = v;
+                if (i > j) cand_combine(b, bi, absbits64(v), i);
+            }
+        }
+        block_cand_to(b, bi, (j >= r0 && j < r1) ? Wp + (size_t)(j - r0) * S + jj : nullptr, s_b, s_i, &cand[0]);
+        cl.sync();   // #1
+        {
+            Cand res;
+            if (cluster_cand(cl, cand, 0, C, owner(j), res)) {
+                // scalar FP64 decisions by one thread (GB300 issues FP64 at 1/64
+                // rate: 512 threads repeating them would cost microseconds)
+                const double absakk = fabs(res.val);
+                const double colmax = __longlong_as_double((long long)res.bits);
+                s_dec[0] = res.idx == 0x7fffffff ? j : res.idx;
+                const bool plain = fmax(absakk, colmax) == 0.0 || absakk >= alpha * colmax;
+                s_dec[1] = plain ? 0 : 1;
+                s_sc[0] = absakk;
+                s_sc[1] = colmax;
+                if (plain) {   // 1x1 pivot, no interchange: D and its inverse now
+                    s_d[0] = res.val;
+                    s_d[1] = s_d[2] = 0.0;
+                    s_d[3] = res.val != 0.0 ? 1.0 / res.val : 0.0;
+                    s_d[4] = s_d[5] = 0.0;
+                }
+            }
+        }
+        __syncthreads();
+        const int imax = s_dec[0];
+        int kstep = 1, kp = j;
+        bool copy_r = false;
+        if (s_dec[1]) {
+            const int r = imax;
+            // ---- V = column r updated: V(i) = A_sym(i, r) - L(i, 0:jj) W(r, 0:jj)^T into W(:, jj+1)
+            if (tid < jj) wrow[tid] = rWp(r)[tid];
+            __syncthreads();
+            unsigned long long b2 = 0;
+            int bi2 = 0x7fffffff;
+            const bool r_in_panel = r - k < S;
+            for (int lr0 = 0; lr0 < r1 - r0; lr0 += rpp) {
+                const int lr = lr0 + rsub, i = r0 + lr;
+                const bool act = lr < r1 - r0 && i >= j;
+                double s = 0.0;
+                if (act)
+                    for (int t = q4; t < jj; t += tpr) s = fma(Ap[(size_t)lr * S + t], wrow[t], s);
+                for (int o = 1; o < tpr; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (act && q4 == 0) {
+                    double air;
+                    if (i < r)
+                        air = (i - k < S) ? rAp(r)[i - k] : a.A[r + (int64_t)i * N];
+                    else
+                        air = r_in_panel ? Ap[(size_t)lr * S + (r - k)] : a.A[i + (int64_t)r * N];
+                    const double v = air - s;
+                    Wp[(size_t)lr * S + jj + 1] = v;
+                    if (i != r) cand_combine(b2, bi2, absbits64(v), i);
+                }
+            }
+            block_cand_to(b2, bi2, (r >= r0 && r < r1) ? Wp + (size_t)(r - r0) * S + jj + 1 : nullptr, s_b, s_i,
+                          &cand[1]);
+            cl.sync();   // #2
+            {
+                Cand res;
+                if (cluster_cand(cl, cand, 1, C, owner(r), res)) {
+                    const double absakk = s_sc[0], colmax = s_sc[1];
+                    const double rowmax = __longlong_as_double((long long)res.bits);
+                    if (absakk >= alpha * colmax * (colmax / rowmax)) s_dec[2] = 0;   // 1x1, no interchange
+                    else if (fabs(res.val) >= alpha * rowmax) s_dec[2] = 1;         // 1x1 on V, interchange
+                    else s_dec[2] = 2;                                              // 2x2, interchange
+                }
+            }
+            __syncthreads();
+            if (s_dec[2] == 1) {
+                kp = r;
+                copy_r = true;   // the pivot column is V
+            } else if (s_dec[2] == 2) {
+                kp = r;
+                kstep = 2;
+            }
+        }
+        const int kk = j + kstep - 1;
+        if (copy_r) {
+            for (int lr = tid; lr < r1 - r0; lr += kPanelThreads)
+                if (r0 + lr >= j) Wp[(size_t)lr * S + jj] = Wp[(size_t)lr * S + jj + 1];
+        }
+        if (kp != kk) {
+            cl.sync();   // every CTA is done with this column's reads of rows kk and kp
+            const bool kp_in_panel = kp - k < S;
+            // raw column kk moves to position kp (kk's own column becomes L)
+            if (kk >= r0 && kk < r1 && tid == 0) {
+                const double v = Ap[(size_t)(kk - r0) * S + (kk - k)];
+                if (kp_in_panel) rAp(kp)[kp - k] = v;
+                else a.A[kp + (int64_t)kp * N] = v;
+            }
+            for (int lr = tid; lr < r1 - r0; lr += kPanelThreads) {
+                const int i = r0 + lr;
+                if (i > kk && i < kp) {          // A(kp, i) = A(i, kk)
+                    const double v = Ap[(size_t)lr * S + (kk - k)];
+                    if (i - k < S) rAp(kp)[i - k] = v;
+                    else a.A[kp + (int64_t)i * N] = v;
+                } else if (i > kp) {             // A(i, kp) = A(i, kk)
+                    const double v = Ap[(size_t)lr * S + (kk - k)];
+                    if (kp_in_panel) Ap[(size_t)lr * S + (kp - k)] = v;
+                    else a.A[i + (int64_t)kp * N] = v;
+                }
+            }
+            // rows kk <-> kp of the panel's L columns (t < jj) and W columns (t <= kk - k)
+            if (kk >= r0 && kk < r1) {
+                double *ak = Ap + (size_t)(kk - r0) * S, *wk = Wp + (size_t)(kk - r0) * S;
+                double *ap = rAp(kp), *wp = rWp(kp);
+                for (int t = tid; t < jj; t += kPanelThreads) {
+                    const double x = ak[t];
+                    ak[t] = ap[t];
+                    ap[t] = x;
+                }
+                for (int t = tid; t <= kk - k; t += kPanelThreads) {
+                    const double x = wk[t];
+                    wk[t] = wp[t];
+                    wp[t] = x;
+                }
+            }
+            // rows kk <-> kp of the earlier panels' L columns
+            for (int t = rank * kPanelThreads + tid; t < k; t += C * kPanelThreads) {
+                double *Lt = a.L + (int64_t)t * N;
+                const double x = Lt[kk];
+                Lt[kk] = Lt[kp];
+                Lt[kp] = x;
+            }
+            if (rank == 0 && tid == 0) {
+                const int x = a.perm[kk];
+                a.perm[kk] = a.perm[kp];
+                a.perm[kp] = x;
+            }
+            cl.sync();
+        }
+        // ---- D block and L column(s)
+        const bool d_ready = s_dec[1] == 0;   // plain 1x1: D was formed with the decision
+        if (tid == 0 && !d_ready) {
+            const double d11 = rWp(j)[jj];
+            const double d21 = kstep == 2 ? rWp(j + 1)[jj] : 0.0;
+            const double d22 = kstep == 2 ? rWp(j + 1)[jj + 1] : 0.0;
+            s_d[0] = d11;
+            s_d[1] = d21;
+            s_d[2] = d22;
+            if (kstep == 1) {
+                s_d[3] = d11 != 0.0 ? 1.0 / d11 : 0.0;
+                s_d[4] = s_d[5] = 0.0;
+            } else {
+                const double det = d11 * d22 - d21 * d21;
+                s_d[3] = d22 / det;
+                s_d[4] = -d21 / det;
+                s_d[5] = d11 / det;
+            }
+        }
+        if (!d_ready) __syncthreads();
+        const double d11 = s_d[0], d21 = s_d[1], d22 = s_d[2];
+        const double e11 = s_d[3], e21 = s_d[4], e22 = s_d[5];
+        for (int lr = tid; lr < r1 - r0; lr += kPanelThreads) {
+            const int i = r0 + lr;
+            double *arow = Ap + (size_t)lr * S;
+            const double *wr = Wp + (size_t)lr * S;
+            if (kstep == 1) {
+                if (i > j) arow[jj] = wr[jj] * e11;
+            } else {
+                if (i >= j + 2) {
+                    const double x = wr[jj], y = wr[jj + 1];
+                    arow[jj] = x * e11 + y * e21;
+                    arow[jj + 1] = x * e21 + y * e22;
+                } else if (i == j + 1) {
+                    arow[jj] = 0.0;
+                }
+            }
+        }
+        if (rank == 0 && tid == 0) {
+            if (kstep == 1) {
+                a.Dd[j] = d11;
+                a.Doff[j] = 0.0;
+                a.kind[j] = 1;
+                if (d11 == 0.0 || fabs(d11) <= ztol) ++nzero;
+                else if (d11 > 0.0) ++npos;
+                else ++nneg;
+            } else {
+                a.Dd[j] = d11;
+                a.Doff[j] = d21;
+                a.Dd[j + 1] = d22;
+                a.Doff[j + 1] = 0.0;
+                a.kind[j] = 2;
+                a.kind[j + 1] = 0;
+                ++npos;
+                ++nneg;
+            }
+        }
+        jj += kstep;
+        cl.sync();   // #4
+    }
+    const int kb = jj;
+    // ---- write back: L columns (strict lower, unit diagonal), W rows below the
+    // panel for the trailing update, and the panel's raw columns not factored
+    for (int e = tid; e < nrows * ncols; e += kPanelThreads) {
+        const int t = e / nrows, lr = e % nrows, i = r0 + lr;
+        const double v = Ap[(size_t)lr * S + t];
+        if (t < kb) {
+            if (i > k + t) a.L[i + (int64_t)(k + t) * N] = v;
+            else if (i == k + t) a.L[i + (int64_t)i * N] = 1.0;
+            if (i >= k + kb) a.Wg[i + (int64_t)t * N] = Wp[(size_t)lr * S + t];
+        } else if (i >= k + t) {
+            a.A[i + (int64_t)(k + t) * N] = v;
+        }
+    }
+    if (rank == 0 && tid == 0) {
+        a.st->k = k + kb;
+        a.st->kb = kb;
+        a.st->npos += npos;
+        a.st->nneg += nneg;
+        a.st->nzero += nzero;
+    }
+}
+
+// A(i, c) -= sum_{t < kb} L(i, k + t) W(c, t)  for k + kb <= c <= i < N.
+// Block = one 64 x 64 tile of the trailing lower triangle (tiles beyond the
+// actual trailing size return).  256 threads, 4 x 4 outputs each.
+template <typename T>
+__global__ void __launch_bounds__(kUpdThreads) k_bk_trailing(int N, int NB, double *__restrict__ A,
+                                                             const double *__restrict__ L,
+                                                             const double *__restrict__ Wg,
+                                                             const PanelState *__restrict__ st) {
+    extern __shared__ unsigned char usmem[];
+    const int S = NB + 1;
+    T *Lt = reinterpret_cast<T *>(usmem);          // [S][64]: Lt[t][r]
+    T *Wt = Lt + (size_t)S * kUT;                   // [S][64]: Wt[t][c]
+    const int kb = st->kb;
+    const int k0 = st->k - kb;                      // first column of the last panel
+    const int base = st->k;
+    if (base >= N || kb <= 0) return;
+    int tr = (int)((sqrt(8.0 * (double)blockIdx.x + 1.0) - 1.0) * 0.5);
+    while ((tr + 1) * (tr + 2) / 2 <= (int)blockIdx.x) ++tr;
+    while (tr * (tr + 1) / 2 > (int)blockIdx.x) --tr;
+    const int tc = (int)blockIdx.x - tr * (tr + 1) / 2;
+    const int i0 = base + tr * kUT, c0 = base + tc * kUT;
+    if (i0 >= N) return;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < kb * kUT; e += kUpdThreads) {
+        const int t = e / kUT, r = e % kUT;
+        const int i = i0 + r, c = c0 + r;
+        Lt[t * kUT + r] = (T)(i < N ? L[i + (int64_t)(k0 + t) * N] : 0.0);
+        Wt[t * kUT + r] = (T)(c < N ? Wg[c + (int64_t)t * N] : 0.0);
+    }
+    __syncthreads();
+    const int tx = tid & 15, ty = tid >> 4;   // rows tx + 16 u, columns ty + 16 v
+    T acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = (T)0;
+    for (int t = 0; t < kb; ++t) {
+        T lv[4], wv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) lv[u] = Lt[t * kUT + tx + 16 * u];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) wv[v] = Wt[t * kUT + ty + 16 * v];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fma(lv[u], wv[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int c = c0 + ty + 16 * v;
+        if (c >= N) continue;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + tx + 16 * u;
+            if (i < N && i >= c) A[i + (int64_t)c * N] -= (double)acc[u][v];
+        }
+    }
+}
+
+__global__ void k_bk_init(int N, int32_t *perm, PanelState *st) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) perm[i] = i;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->k = 0;
+        st->kb = 0;
+        st->npos = st->nneg = st->nzero = 0;
+    }
+}
+
+__global__ void k_bk_finish(const PanelState *st, int32_t *inertia) {
+    inertia[0] = st->npos;
+    inertia[1] = st->nneg;
+    inertia[2] = st->nzero;
+}
+
+struct BlockedConfig {
+    int C = 0, NB = 0, R = 0;
+    size_t smem = 0;
+};
+
+size_t panel_smem(int R, int NB) {
+    const int S = NB + 1;
+    return (2 * (size_t)R * S + S) * sizeof(double) + 2 * sizeof(Cand) + 64;
+}
+
+// cluster size and panel width for order N on this device (C = 0: unavailable)
+BlockedConfig blocked_config(int64_t N) {
+    static std::mutex mu;
+    static int clusters16[64] = {};   // 1: size 16 allowed, -1: not, 0: unknown
+    int dev = 0;
+    MDSIP_CUDA(cudaGetDevice(&dev));
+    constexpr size_t kSmemCap = 220 * 1024;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev >= 0 && dev < 64 && clusters16[dev] == 0) {
+            cudaError_t e = cudaFuncSetAttribute(k_bk_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bk_panel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            int ok16 = 0;
+            if (e == cudaSuccess) {
+                cudaLaunchConfig_t cfg{};
+                cfg.gridDim = dim3(16);
+                cfg.blockDim = dim3(kPanelThreads);
+                cfg.dynamicSmemBytes = kSmemCap;
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeClusterDimension;
+                at[0].val.clusterDim.x = 16;
+                at[0].val.clusterDim.y = 1;
+                at[0].val.clusterDim.z = 1;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                int nclusters = 0;
+                if (cudaOccupancyMaxActiveClusters(&nclusters, (void *)k_bk_panel, &cfg) == cudaSuccess && nclusters >= 1)
+                    ok16 = 1;
+            }
+            cudaGetLastError();
+            clusters16[dev] = ok16 ? 1 : -1;
+        }
+    }
+    BlockedConfig c;
+    c.C = (dev >= 0 && dev < 64 && clusters16[dev] == 1) ? 16 : 8;
+    for (int nb : {64, 32, 16, 8}) {
+        const int R = (int)((N + c.C - 1) / c.C);
+        if (panel_smem(R, nb) <= kSmemCap) {
+            c.NB = nb;
+            c.R = R;
+            c.smem = panel_smem(R, nb);
+            return c;
+        }
+    }
+    c.C = 0;
+    return c;
+}
+
+}  // namespace
+
+// scratch use: W of the last panel (N x 65 doubles) and the panel state
+size_t ldlt_blocked_scratch_bytes(int64_t N) {
+    return ((size_t)std::max<int64_t>(N, 1) * 65 * sizeof(double) + 255) / 256 * 256 + 256;
+}
+
+bool ldlt_blocked_available(int64_t N) { return blocked_config(N).C > 0; }
+
+// S (lower, ld N) is overwritten.  scratch: ldlt_blocked_scratch_bytes(N),
+// 256-byte aligned.  fp32_update: trailing products in FP32.
+void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, const double *maxabs_dev,
+                         double zero_tol, LdltOut out, void *scratch, bool fp32_update) {
+    if (N <= 0) {
+        MDSIP_CUDA(cudaMemsetAsync(out.inertia, 0, 3 * sizeof(int32_t), s));
+        return;
+    }
+    const BlockedConfig cfg = blocked_config(N);
+    MDSIP_REQUIRE(cfg.C > 0, MDSIP_ERR_INVALID_ARG, "ldlt: N too large for the blocked factorization");
+    char *w = static_cast<char *>(scratch);
+    MDSIP_REQUIRE((reinterpret_cast<uintptr_t>(w) & 255) == 0, MDSIP_ERR_INVALID_ARG, "ldlt: misaligned scratch");
+    double *Wg = reinterpret_cast<double *>(w);
+    PanelState *st = reinterpret_cast<PanelState *>(w + ((size_t)N * 65 * sizeof(double) + 255) / 256 * 256);
+    k_bk_init<<<std::max(1, std::min(1024, ceil_div(N, 256))), 256, 0, s>>>((int)N, out.perm, st);
+    MDSIP_LAUNCHED();
+
+    PanelArgs a{};
+    a.N = (int)N;
+    a.NB = cfg.NB;
+    a.C = cfg.C;
+    a.R = cfg.R;
+    a.A = S;
+    a.L = out.L;
+    a.Dd = out.Dd;
+    a.Doff = out.Doff;
+    a.perm = out.perm;
+    a.kind = out.kind;
+    a.Wg = Wg;
+    a.st = st;
+    a.maxabs = maxabs_dev;
+    a.zero_tol = zero_tol;
+
+    cudaLaunchConfig_t lc{};
+    lc.gridDim = dim3(cfg.C);
+    lc.blockDim = dim3(kPanelThreads);
+    lc.dynamicSmemBytes = cfg.smem;
+    lc.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cfg.C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+
+    const size_t usm = 2 * (size_t)(cfg.NB + 1) * kUT * (fp32_update ? sizeof(float) : sizeof(double));
+    static PerDeviceOnce once;
+    MDSIP_CUDA(once.run([] {
+        cudaError_t e = cudaFuncSetAttribute(k_bk_trailing<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(2 * 65 * kUT * sizeof(double)));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_bk_trailing<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(2 * 65 * kUT * sizeof(float)));
+        return e;
+    }));
+    const int npanels = (int)((N + cfg.NB - 1) / cfg.NB);
+    for (int p = 0; p < npanels; ++p) {
+        MDSIP_CUDA(cudaLaunchKernelEx(&lc, k_bk_panel, a));
+        count_launch();
+        // trailing matrix after panel p starts at column >= (p + 1) NB
+        const int64_t rest = N - (int64_t)(p + 1) * cfg.NB;
+        if (rest <= 0) continue;
+        const int64_t nt = (rest + kUT - 1) / kUT;
+        const unsigned tiles = (unsigned)(nt * (nt + 1) / 2);
+        if (fp32_update)
+            k_bk_trailing<float><<<tiles, kUpdThreads, usm, s>>>((int)N, cfg.NB, S, out.L, Wg, st);
+        else
+            k_bk_trailing<double><<<tiles, kUpdThreads, usm, s>>>((int)N, cfg.NB, S, out.L, Wg, st);
+        MDSIP_LAUNCHED();
+    }
+    k_bk_finish<<<1, 1, 0, s>>>(st, out.inertia);
+    MDSIP_LAUNCHED();
+}
+
+}  // namespace mdsip

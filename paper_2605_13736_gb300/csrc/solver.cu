@@ -598,8 +598,9 @@ static Inertia factor_attempt(Problem *P, double dw, double dc, bool force_fp64 
     LdltOut o{P->bL.as<double>(), P->bDd.as<double>(), P->bDoff.as<double>(), P->bperm.as<int32_t>(),
               P->bkind.as<int32_t>(), P->binertia.as<int32_t>()};
     MDSIP_CUDA(cudaEventRecord(P->ev[10], st));
+    const bool tc_factor = p2 && P->opt.precision != MDSIP_PREC_FP64 && !force_fp64;
     launch_ldlt(st, P->ctx->num_sms, P->N, S, P->N, sc + SC_MAXABS, P->opt.zero_tol, o,
-                P->bldlt_ws.ptr, P->berr.as<int>());
+                P->bldlt_ws.ptr, P->berr.as<int>(), tc_factor);
     // the refined tensor-core path solves with FP32 tiles of L; the FP64 path with FP64 tiles
     P->solve_fp32 = p2 && P->opt.precision != MDSIP_PREC_FP64 && !force_fp64;
     launch_ldlt_solve_prepare(st, P->N, P->bL.as<double>(), P->bsolve_ws.ptr, P->solve_fp32);

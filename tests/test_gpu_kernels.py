@@ -119,6 +119,23 @@ def test_ldlt_matches_oracle_bunch_kaufman(ctx, N, kind):
             assert np.abs(res).max() <= 1e-9 * (np.abs(K).max() * np.abs(X[r]).max() + np.abs(B[r]).max())
 
 
+@pytest.mark.parametrize("N,kind", [(2600, "saddle"), (4200, "zero_diag")])
+def test_ldlt_large_orders(ctx, N, kind):
+    """Orders that take many panels and (at 4200) the narrower panel width:
+    reconstruction and the inertia of numpy.linalg.eigvalsh."""
+    rng = np.random.default_rng(N)
+    K = _sym(rng, N, kind)
+    g = _gpu_ldlt(ctx, K)
+    ev = np.linalg.eigvalsh(K)
+    tol = 1e-9 * np.abs(ev).max()
+    assert np.min(np.abs(ev)) > tol
+    assert g["inertia"] == (int((ev > 0).sum()), int((ev < 0).sum()), 0)
+    D = np.diag(g["Dd"]) + np.diag(g["Doff"][:-1], -1) + np.diag(g["Doff"][:-1], 1)
+    p = g["perm"]
+    R = K[np.ix_(p, p)] - g["L"] @ D @ g["L"].T
+    assert np.abs(R).max() <= 1e-11 * max(1.0, np.abs(K).max()) * N ** 0.5
+
+
 def test_ldlt_singular_and_edge_cases(ctx):
     g = _gpu_ldlt(ctx, np.zeros((5, 5)))
     assert g["inertia"] == (0, 0, 5)
