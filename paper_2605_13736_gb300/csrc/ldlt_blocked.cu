@@ -17,11 +17,14 @@
 //       position kp: column kk becomes L anyway; swapping rows kk, kp of the
 //       panel's L and W columns, of the earlier L columns, and of perm),
 //     - forms the L column(s) from W and D (1x1 or 2x2).
-//   Pivot values, the pivot test and the inertia count stay in FP64.
+//   Pivot values, the pivot test, D and the inertia count stay in FP64.
 // Trailing update (all SMs): A22 -= L21 W21^T on the lower triangle, W = L D;
 //   FP64 for the FP64 path, FP32 products subtracted from the FP64 matrix for
 //   the refined mixed-precision path (the update has K = NB, so it is bound by
-//   the L2 traffic of A22, not by arithmetic).
+//   the L2 traffic of A22, not by arithmetic).  On that path the panel's own
+//   column updates also take FP32 products (from FP32 shadows of L and of the
+//   broadcast W row): at 1/64 of the FP32 rate, FP64 products were the largest
+//   part of each column's time.
 // Panel state (next column, inertia counts) lives in device memory, so the
 // host enqueues all panels without reading anything back.
 #include <cooperative_groups.h>
@@ -76,13 +79,16 @@ __device__ __forceinline__ void cand_combine(unsigned long long &b, int &i, unsi
     }
 }
 
-// warp arg-max (first index on ties); result in lane 0
+// warp arg-max (first index on ties), result in every lane: three warp
+// reductions (maximum of the high words, maximum of the low words among the
+// lanes holding that high word, minimum index among the lanes holding both)
 __device__ __forceinline__ void warp_cand(unsigned long long &b, int &idx) {
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long b2 = __shfl_down_sync(0xffffffffu, b, o);
-        const int i2 = __shfl_down_sync(0xffffffffu, idx, o);
-        cand_combine(b, idx, b2, i2);
-    }
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+    const bool top = hi == mhi && lo == mlo;
+    idx = __reduce_min_sync(0xffffffffu, top ? idx : 0x7fffffff);
+    b = ((unsigned long long)mhi << 32) | mlo;
 }
 
 // block arg-max into *out (bits, idx); val = *diag (a shared-memory value
@@ -110,6 +116,22 @@ __device__ void block_cand_to(unsigned long long b, int idx, const double *diag,
     }
 }
 
+// 1/d by Newton-Raphson iteration x <- x (2 - d x) (two steps, as fused
+// multiply-adds) from the single-precision reciprocal of d: each step squares
+// the relative error, 2^-23 -> 2^-46 -> below the double rounding.  Takes six
+// FP64 instructions; d outside the normal float range goes through the
+// division operator.
+__device__ __forceinline__ double rcp_newton(double d) {
+    if (d == 0.0) return 0.0;
+    const float df = (float)d;
+    if (!(fabsf(df) >= 1.17549435e-38f && fabsf(df) <= 3.0e38f)) return 1.0 / d;
+    double x = (double)__frcp_rn(df);
+    double e = fma(-d, x, 1.0);
+    x = fma(x, e, x);
+    e = fma(-d, x, 1.0);
+    return fma(x, e, x);
+}
+
 // Cluster-wide arg-max of the candidates cand[slot] of all C CTAs (C <= 32),
 // computed by warp 0: lane c reads CTA c's candidate, a shuffle reduction
 // combines them (first index on ties); lane 0 returns true with the result
@@ -134,6 +156,10 @@ __device__ bool cluster_cand(cg::cluster_group &cl, Cand *cand, int slot, int C,
     return c == 0;
 }
 
+// F32: the panel's column updates (the products with earlier L columns) in
+// FP32 from single-precision shadows of L and of the broadcast W row (the
+// refined mixed-precision path); pivot tests, D and inertia stay FP64.
+template <bool F32>
 __global__ void __launch_bounds__(kPanelThreads, 1) k_bk_panel(PanelArgs a) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
@@ -143,8 +169,15 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_bk_panel(PanelArgs a) {
     double *Ap = smem;                       // R x S: raw A columns, then L columns
     double *Wp = Ap + (size_t)a.R * S;       // R x S: updated columns
     double *wrow = Wp + (size_t)a.R * S;     // S: row j (or r) of W
-    Cand *cand = reinterpret_cast<Cand *>(wrow + S);   // [2]: column and row candidates
+    // candidates [parity of the column step][column / row maximum]: double
+    // buffered, so a CTA that starts the next column before a slower one has
+    // read this column's candidates writes the other pair
+    Cand *cand = reinterpret_cast<Cand *>(wrow + S);
+    float *Apf = reinterpret_cast<float *>(cand + 4);   // F32 only: R x S shadow of the L columns
+    float *wrowf = Apf + (size_t)a.R * S;                // F32 only: S
     __shared__ unsigned long long s_b[32];
+    __shared__ Cand s_cand;
+    __shared__ double s_rcp;
     __shared__ int s_i[32];
     __shared__ double s_d[6];
     __shared__ double s_sc[2];
@@ -176,47 +209,61 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_bk_panel(PanelArgs a) {
     int tpr = 1;
     while (tpr < 32 && 2 * tpr * R <= kPanelThreads) tpr *= 2;
     const int q4 = tid & (tpr - 1), rsub = tid / tpr, rpp = kPanelThreads / tpr;
-    int jj = 0;
+    int jj = 0, it = 0;
     while (jj < NB && k + jj < N) {
         const int j = k + jj;
+        Cand *cpair = cand + 2 * (it & 1);
         // ---- W(:, jj) = A(:, j) - L(:, 0:jj) W(j, 0:jj)^T over the owned rows >= j
-        if (tid < jj) wrow[tid] = rWp(j)[tid];
+        if (tid < jj) {
+            const double v = rWp(j)[tid];
+            if constexpr (F32) wrowf[tid] = (float)v;
+            else wrow[tid] = v;
+        }
         __syncthreads();
         unsigned long long b = 0;
         int bi = 0x7fffffff;
         for (int lr0 = 0; lr0 < r1 - r0; lr0 += rpp) {
             const int lr = lr0 + rsub, i = r0 + lr;
-            double s = 0.0;
-            if (lr < r1 - r0 && i >= j)
-                for (int t = q4; t < jj; t += tpr) s = fma(Ap[(size_t)lr * S + t], wrow[t], s);
-            for (int o = 1; o < tpr; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            double s;
+            if constexpr (F32) {
+                float sf = 0.0f;
+                if (lr < r1 - r0 && i >= j)
+                    for (int t = q4; t < jj; t += tpr) sf = fmaf(Apf[(size_t)lr * S + t], wrowf[t], sf);
+                for (int o = 1; o < tpr; o <<= 1) sf += __shfl_xor_sync(0xffffffffu, sf, o);
+                s = (double)sf;
+            } else {
+                s = 0.0;
+                if (lr < r1 - r0 && i >= j)
+                    for (int t = q4; t < jj; t += tpr) s = fma(Ap[(size_t)lr * S + t], wrow[t], s);
+                for (int o = 1; o < tpr; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            }
             if (lr < r1 - r0 && i >= j && q4 == 0) {
                 const double v = Ap[(size_t)lr * S + jj] - s;
                 Wp[(size_t)lr * S + jj] = v;
                 if (i > j) cand_combine(b, bi, absbits64(v), i);
             }
         }
-        block_cand_to(b, bi, (j >= r0 && j < r1) ? Wp + (size_t)(j - r0) * S + jj : nullptr, s_b, s_i, &cand[0]);
+        block_cand_to(b, bi, (j >= r0 && j < r1) ? Wp + (size_t)(j - r0) * S + jj : nullptr, s_b, s_i, &cpair[0]);
         cl.sync();   // #1
         {
             Cand res;
-            if (cluster_cand(cl, cand, 0, C, owner(j), res)) {
-                // scalar FP64 decisions by one thread (GB300 issues FP64 at 1/64
-                // rate: 512 threads repeating them would cost microseconds)
-                const double absakk = fabs(res.val);
-                const double colmax = __longlong_as_double((long long)res.bits);
-                s_dec[0] = res.idx == 0x7fffffff ? j : res.idx;
-                const bool plain = fmax(absakk, colmax) == 0.0 || absakk >= alpha * colmax;
-                s_dec[1] = plain ? 0 : 1;
-                s_sc[0] = absakk;
-                s_sc[1] = colmax;
-                if (plain) {   // 1x1 pivot, no interchange: D and its inverse now
-                    s_d[0] = res.val;
-                    s_d[1] = s_d[2] = 0.0;
-                    s_d[3] = res.val != 0.0 ? 1.0 / res.val : 0.0;
-                    s_d[4] = s_d[5] = 0.0;
-                }
-            }
+            if (cluster_cand(cl, cpair, 0, C, owner(j), res)) s_cand = res;
+        }
+        __syncthreads();
+        // scalar FP64 work by single threads of two warps in parallel (GB300
+        // issues FP64 at 1/64 rate: 512 threads repeating it would cost
+        // microseconds): the pivot test in warp 0, the reciprocal of the
+        // diagonal (used when the test keeps it) in warp 1
+        if (tid == 0) {
+            const double absakk = fabs(s_cand.val);
+            const double colmax = __longlong_as_double((long long)s_cand.bits);
+            s_dec[0] = s_cand.idx == 0x7fffffff ? j : s_cand.idx;
+            const bool plain = fmax(absakk, colmax) == 0.0 || absakk >= alpha * colmax;
+            s_dec[1] = plain ? 0 : 1;
+            s_sc[0] = absakk;
+            s_sc[1] = colmax;
+        } else if (tid == 32) {
+            s_rcp = rcp_newton(s_cand.val);
         }
         __syncthreads();
         const int imax = s_dec[0];
@@ -225,7 +272,11 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_bk_panel(PanelArgs a) {
         if (s_dec[1]) {
             const int r = imax;
             // ---- V = column r updated: V(i) = A_sym(i, r) - L(i, 0:jj) W(r, 0:jj)^T into W(:, jj+1)
-            if (tid < jj) wrow[tid] = rWp(r)[tid];
+            if (tid < jj) {
+                const double v = rWp(r)[tid];
+                if constexpr (F32) wrowf[tid] = (float)v;
+                else wrow[tid] = v;
+            }
             __syncthreads();
             unsigned long long b2 = 0;
             int bi2 = 0x7fffffff;
@@ -233,10 +284,19 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_bk_panel(PanelArgs a) {
             for (int lr0 = 0; lr0 < r1 - r0; lr0 += rpp) {
                 const int lr = lr0 + rsub, i = r0 + lr;
                 const bool act = lr < r1 - r0 && i >= j;
-                double s = 0.0;
-                if (act)
-                    for (int t = q4; t < jj; t += tpr) s = fma(Ap[(size_t)lr * S + t], wrow[t], s);
-                for (int o = 1; o < tpr; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                double s;
+                if constexpr (F32) {
+                    float sf = 0.0f;
+                    if (act)
+                        for (int t = q4; t < jj; t += tpr) sf = fmaf(Apf[(size_t)lr * S + t], wrowf[t], sf);
+                    for (int o = 1; o < tpr; o <<= 1) sf += __shfl_xor_sync(0xffffffffu, sf, o);
+                    s = (double)sf;
+                } else {
+                    s = 0.0;
+                    if (act)
+                        for (int t = q4; t < jj; t += tpr) s = fma(Ap[(size_t)lr * S + t], wrow[t], s);
+                    for (int o = 1; o < tpr; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                }
                 if (act && q4 == 0) {
                     double air;
                     if (i < r)
@@ -249,11 +309,11 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_bk_panel(PanelArgs a) {
                 }
             }
             block_cand_to(b2, bi2, (r >= r0 && r < r1) ? Wp + (size_t)(r - r0) * S + jj + 1 : nullptr, s_b, s_i,
-                          &cand[1]);
+                          &cpair[1]);
             cl.sync();   // #2
             {
                 Cand res;
-                if (cluster_cand(cl, cand, 1, C, owner(r), res)) {
+                if (cluster_cand(cl, cpair, 1, C, owner(r), res)) {
                     const double absakk = s_sc[0], colmax = s_sc[1];
                     const double rowmax = __longlong_as_double((long long)res.bits);
                     if (absakk >= alpha * colmax * (colmax / rowmax)) s_dec[2] = 0;   // 1x1, no interchange
@@ -305,6 +365,15 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_bk_panel(PanelArgs a) {
                     ak[t] = ap[t];
                     ap[t] = x;
                 }
+                if constexpr (F32) {
+                    float *fk = Apf + (size_t)(kk - r0) * S;
+                    float *fp = cl.map_shared_rank(Apf, owner(kp)) + (size_t)(kp - (k + owner(kp) * R)) * S;
+                    for (int t = tid; t < jj; t += kPanelThreads) {
+                        const float x = fk[t];
+                        fk[t] = fp[t];
+                        fp[t] = x;
+                    }
+                }
                 for (int t = tid; t <= kk - k; t += kPanelThreads) {
                     const double x = wk[t];
                     wk[t] = wp[t];
@@ -326,7 +395,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_bk_panel(PanelArgs a) {
             cl.sync();
         }
         // ---- D block and L column(s)
-        const bool d_ready = s_dec[1] == 0;   // plain 1x1: D was formed with the decision
+        const bool d_ready = s_dec[1] == 0;   // plain 1x1: d = the diagonal, 1/d = s_rcp
         if (tid == 0 && !d_ready) {
             const double d11 = rWp(j)[jj];
             const double d21 = kstep == 2 ? rWp(j + 1)[jj] : 0.0;
@@ -335,35 +404,45 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_bk_panel(PanelArgs a) {
             s_d[1] = d21;
             s_d[2] = d22;
             if (kstep == 1) {
-                s_d[3] = d11 != 0.0 ? 1.0 / d11 : 0.0;
+                s_d[3] = rcp_newton(d11);
                 s_d[4] = s_d[5] = 0.0;
             } else {
-                const double det = d11 * d22 - d21 * d21;
-                s_d[3] = d22 / det;
-                s_d[4] = -d21 / det;
-                s_d[5] = d11 / det;
+                const double inv = rcp_newton(d11 * d22 - d21 * d21);
+                s_d[3] = d22 * inv;
+                s_d[4] = -d21 * inv;
+                s_d[5] = d11 * inv;
             }
         }
         if (!d_ready) __syncthreads();
-        const double d11 = s_d[0], d21 = s_d[1], d22 = s_d[2];
-        const double e11 = s_d[3], e21 = s_d[4], e22 = s_d[5];
+        const double d11 = d_ready ? s_cand.val : s_d[0];
+        const double d21 = d_ready ? 0.0 : s_d[1], d22 = d_ready ? 0.0 : s_d[2];
+        const double e11 = d_ready ? s_rcp : s_d[3], e21 = d_ready ? 0.0 : s_d[4], e22 = d_ready ? 0.0 : s_d[5];
         for (int lr = tid; lr < r1 - r0; lr += kPanelThreads) {
             const int i = r0 + lr;
             double *arow = Ap + (size_t)lr * S;
             const double *wr = Wp + (size_t)lr * S;
+            float *frow = Apf + (size_t)lr * S;
             if (kstep == 1) {
-                if (i > j) arow[jj] = wr[jj] * e11;
+                if (i > j) {
+                    arow[jj] = wr[jj] * e11;
+                    if constexpr (F32) frow[jj] = (float)arow[jj];
+                }
             } else {
                 if (i >= j + 2) {
                     const double x = wr[jj], y = wr[jj + 1];
                     arow[jj] = x * e11 + y * e21;
                     arow[jj + 1] = x * e21 + y * e22;
+                    if constexpr (F32) {
+                        frow[jj] = (float)arow[jj];
+                        frow[jj + 1] = (float)arow[jj + 1];
+                    }
                 } else if (i == j + 1) {
                     arow[jj] = 0.0;
+                    if constexpr (F32) frow[jj] = 0.0f;
                 }
             }
         }
-        if (rank == 0 && tid == 0) {
+        if (rank == 0 && tid == kPanelThreads - 32) {   // a warp without L rows at these sizes
             if (kstep == 1) {
                 a.Dd[j] = d11;
                 a.Doff[j] = 0.0;
@@ -383,8 +462,12 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_bk_panel(PanelArgs a) {
             }
         }
         jj += kstep;
-        cl.sync();   // #4
+        ++it;
+        // No cluster barrier here: the next column reads only W rows finished
+        // before this column's last barrier, writes W columns no CTA still
+        // reads, and its candidates go to the other buffer pair.
     }
+    cl.sync();   // no CTA leaves while another may still read its shared memory
     const int kb = jj;
     // ---- write back: L columns (strict lower, unit diagonal), W rows below the
     // panel for the trailing update, and the panel's raw columns not factored
@@ -399,7 +482,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_bk_panel(PanelArgs a) {
             a.A[i + (int64_t)(k + t) * N] = v;
         }
     }
-    if (rank == 0 && tid == 0) {
+    if (rank == 0 && tid == kPanelThreads - 32) {   // the thread that counted the inertia
         a.st->k = k + kb;
         a.st->kb = kb;
         a.st->npos += npos;
@@ -487,13 +570,14 @@ struct BlockedConfig {
     size_t smem = 0;
 };
 
-size_t panel_smem(int R, int NB) {
+size_t panel_smem(int R, int NB, bool f32) {
     const int S = NB + 1;
-    return (2 * (size_t)R * S + S) * sizeof(double) + 2 * sizeof(Cand) + 64;
+    return (2 * (size_t)R * S + S) * sizeof(double) + 4 * sizeof(Cand) + (f32 ? ((size_t)R * S + S) * sizeof(float) : 0) +
+           64;
 }
 
 // cluster size and panel width for order N on this device (C = 0: unavailable)
-BlockedConfig blocked_config(int64_t N) {
+BlockedConfig blocked_config(int64_t N, bool f32) {
     static std::mutex mu;
     static int clusters16[64] = {};   // 1: size 16 allowed, -1: not, 0: unknown
     int dev = 0;
@@ -502,8 +586,11 @@ BlockedConfig blocked_config(int64_t N) {
     {
         std::lock_guard<std::mutex> lk(mu);
         if (dev >= 0 && dev < 64 && clusters16[dev] == 0) {
-            cudaError_t e = cudaFuncSetAttribute(k_bk_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bk_panel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            cudaError_t e = cudaSuccess;
+            for (const void *fn : {(const void *)k_bk_panel<false>, (const void *)k_bk_panel<true>}) {
+                if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+                if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            }
             int ok16 = 0;
             if (e == cudaSuccess) {
                 cudaLaunchConfig_t cfg{};
@@ -518,7 +605,10 @@ BlockedConfig blocked_config(int64_t N) {
                 cfg.attrs = at;
                 cfg.numAttrs = 1;
                 int nclusters = 0;
-                if (cudaOccupancyMaxActiveClusters(&nclusters, (void *)k_bk_panel, &cfg) == cudaSuccess && nclusters >= 1)
+                int n32 = 0;
+                if (cudaOccupancyMaxActiveClusters(&nclusters, (void *)k_bk_panel<false>, &cfg) == cudaSuccess &&
+                    nclusters >= 1 &&
+                    cudaOccupancyMaxActiveClusters(&n32, (void *)k_bk_panel<true>, &cfg) == cudaSuccess && n32 >= 1)
                     ok16 = 1;
             }
             cudaGetLastError();
@@ -529,10 +619,10 @@ BlockedConfig blocked_config(int64_t N) {
     c.C = (dev >= 0 && dev < 64 && clusters16[dev] == 1) ? 16 : 8;
     for (int nb : {64, 32, 16, 8}) {
         const int R = (int)((N + c.C - 1) / c.C);
-        if (panel_smem(R, nb) <= kSmemCap) {
+        if (panel_smem(R, nb, f32) <= kSmemCap) {
             c.NB = nb;
             c.R = R;
-            c.smem = panel_smem(R, nb);
+            c.smem = panel_smem(R, nb, f32);
             return c;
         }
     }
@@ -547,7 +637,7 @@ size_t ldlt_blocked_scratch_bytes(int64_t N) {
     return ((size_t)std::max<int64_t>(N, 1) * 65 * sizeof(double) + 255) / 256 * 256 + 256;
 }
 
-bool ldlt_blocked_available(int64_t N) { return blocked_config(N).C > 0; }
+bool ldlt_blocked_available(int64_t N) { return blocked_config(N, true).C > 0 && blocked_config(N, false).C > 0; }
 
 // S (lower, ld N) is overwritten.  scratch: ldlt_blocked_scratch_bytes(N),
 // 256-byte aligned.  fp32_update: trailing products in FP32.
@@ -557,7 +647,7 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
         MDSIP_CUDA(cudaMemsetAsync(out.inertia, 0, 3 * sizeof(int32_t), s));
         return;
     }
-    const BlockedConfig cfg = blocked_config(N);
+    const BlockedConfig cfg = blocked_config(N, fp32_update);
     MDSIP_REQUIRE(cfg.C > 0, MDSIP_ERR_INVALID_ARG, "ldlt: N too large for the blocked factorization");
     char *w = static_cast<char *>(scratch);
     MDSIP_REQUIRE((reinterpret_cast<uintptr_t>(w) & 255) == 0, MDSIP_ERR_INVALID_ARG, "ldlt: misaligned scratch");
@@ -607,7 +697,10 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
     }));
     const int npanels = (int)((N + cfg.NB - 1) / cfg.NB);
     for (int p = 0; p < npanels; ++p) {
-        MDSIP_CUDA(cudaLaunchKernelEx(&lc, k_bk_panel, a));
+        if (fp32_update)
+            MDSIP_CUDA(cudaLaunchKernelEx(&lc, k_bk_panel<true>, a));
+        else
+            MDSIP_CUDA(cudaLaunchKernelEx(&lc, k_bk_panel<false>, a));
         count_launch();
         // trailing matrix after panel p starts at column >= (p + 1) NB
         const int64_t rest = N - (int64_t)(p + 1) * cfg.NB;
