@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--m", type=int, default=100000, help="--kernel syrk: rows of A")
     ap.add_argument("--n", type=int, default=2000, help="--kernel syrk: columns of A; ldlt: N; gemm: N")
     ap.add_argument("--k", type=int, default=512, help="--kernel gemm_bf16: K")
+    ap.add_argument("--fp32-update", action="store_true",
+                    help="--kernel ldlt: the mixed-precision factorization (FP32 update products)")
     return ap.parse_args()
 
 
@@ -613,9 +615,11 @@ def run_kernel(args):
             inr = torch.empty(3, dtype=torch.int32, device="cuda")
             flops = N ** 3 / 3.0
 
+            flags = m.MDSIP_LDLT_FP32_UPDATES if args.fp32_update else 0
+
             def call():
                 S.copy_(S0)
-                m.mdsip_ldlt_factor(ctx, N, S, N, 1e-14, L, Dd, Doff, perm, kind, inr)
+                m.mdsip_ldlt_factor_ex(ctx, N, S, N, 1e-14, flags, L, Dd, Doff, perm, kind, inr)
             if args.kernel == "ldlt_solve":
                 call()
                 rhs = torch.randn((4, N), dtype=torch.float64, device="cuda")

@@ -300,6 +300,17 @@ mdsip_status mdsip_ldlt_factor(mdsip_ctx *ctx, int64_t N, double *S, int64_t ld,
                                double *L, double *Dd, double *Doff, int32_t *perm, int32_t *kind,
                                int32_t *inertia);
 
+/* mdsip_ldlt_factor with options.  flags: 0, or MDSIP_LDLT_FP32_UPDATES
+ * (the mixed-precision factorization of the refined path: the panels'
+ * column updates and the trailing updates take FP32 products subtracted from
+ * the FP64 matrix; pivot tests, D and the inertia stay FP64; the result is an
+ * approximate factor meant for iterative refinement, and the unblocked kernel
+ * used where thread-block clusters are unavailable ignores the flag). */
+#define MDSIP_LDLT_FP32_UPDATES 1
+mdsip_status mdsip_ldlt_factor_ex(mdsip_ctx *ctx, int64_t N, double *S, int64_t ld, double zero_tol,
+                                  int32_t flags, double *L, double *Dd, double *Doff, int32_t *perm,
+                                  int32_t *kind, int32_t *inertia);
+
 /* Allocation-free variant of mdsip_ldlt_factor (same arguments, same
  * results).  The paper has no counterpart: this exists for callers that
  * cannot call cudaMalloc -- a host whose device memory belongs in full to

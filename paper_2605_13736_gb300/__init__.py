@@ -121,6 +121,9 @@ _SIGS = {
     "mdsip_ldlt_factor": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_double,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p]),
+    "mdsip_ldlt_factor_ex": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_double, C.c_int32,
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p]),
     "mdsip_ldlt_factor_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_double,
                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                             C.c_void_p]),
@@ -343,6 +346,14 @@ def mdsip_syrk_scaled_tc(ctx, m, n, A, lda, w, beta, Cmat, ldc, precision):
 def mdsip_ldlt_factor(ctx, N, S, ld, zero_tol, L, Dd, Doff, perm, kind, inertia):
     _check(lib().mdsip_ldlt_factor(ctx, N, _ptr(S), ld, float(zero_tol), _ptr(L), _ptr(Dd),
                                    _ptr(Doff), _ptr(perm), _ptr(kind), _ptr(inertia)), ctx)
+
+
+MDSIP_LDLT_FP32_UPDATES = 1
+
+
+def mdsip_ldlt_factor_ex(ctx, N, S, ld, zero_tol, flags, L, Dd, Doff, perm, kind, inertia):
+    _check(lib().mdsip_ldlt_factor_ex(ctx, N, _ptr(S), ld, float(zero_tol), int(flags), _ptr(L), _ptr(Dd),
+                                      _ptr(Doff), _ptr(perm), _ptr(kind), _ptr(inertia)), ctx)
 
 
 def mdsip_ldlt_factor_noalloc(ctx, N, S, ld, zero_tol, L, Dd, Doff, perm, kind, inertia):

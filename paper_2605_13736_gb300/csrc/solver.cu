@@ -1467,9 +1467,30 @@ mdsip_status mdsip_syrk_scaled_tc(mdsip_ctx *hctx, int64_t m, int64_t n, const d
     });
 }
 
+static mdsip_status ldlt_factor_impl(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld, double zero_tol,
+                                     double *L, double *Dd, double *Doff, int32_t *perm, int32_t *kind,
+                                     int32_t *inertia, bool fp32_update);
+
 mdsip_status mdsip_ldlt_factor(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld, double zero_tol,
                                double *L, double *Dd, double *Doff, int32_t *perm, int32_t *kind,
                                int32_t *inertia) {
+    return ldlt_factor_impl(hctx, N, S, ld, zero_tol, L, Dd, Doff, perm, kind, inertia, false);
+}
+
+mdsip_status mdsip_ldlt_factor_ex(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld, double zero_tol,
+                                  int32_t flags, double *L, double *Dd, double *Doff, int32_t *perm,
+                                  int32_t *kind, int32_t *inertia) {
+    if (flags & ~MDSIP_LDLT_FP32_UPDATES) {
+        if (hctx) C_(hctx)->last_error = "ldlt: unknown flags";
+        return MDSIP_ERR_INVALID_ARG;
+    }
+    return ldlt_factor_impl(hctx, N, S, ld, zero_tol, L, Dd, Doff, perm, kind, inertia,
+                            (flags & MDSIP_LDLT_FP32_UPDATES) != 0);
+}
+
+static mdsip_status ldlt_factor_impl(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld, double zero_tol,
+                                     double *L, double *Dd, double *Doff, int32_t *perm, int32_t *kind,
+                                     int32_t *inertia, bool fp32_update) {
     if (!hctx) return MDSIP_ERR_INVALID_ARG;
     Ctx *ctx = C_(hctx);
     return guarded(ctx, [&] {
@@ -1491,7 +1512,7 @@ mdsip_status mdsip_ldlt_factor(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld
         MDSIP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
         launch_maxabs_lower(ctx->stream, N, S, ld, partial, maxabs);
         LdltOut o{L, Dd, Doff, perm, kind, inertia};
-        launch_ldlt(ctx->stream, ctx->num_sms, N, S, ld, maxabs, zero_tol, o, w, err);
+        launch_ldlt(ctx->stream, ctx->num_sms, N, S, ld, maxabs, zero_tol, o, w, err, fp32_update);
         int herr = 0;
         MDSIP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
         MDSIP_CUDA(cudaStreamSynchronize(ctx->stream));

@@ -136,6 +136,33 @@ def test_ldlt_large_orders(ctx, N, kind):
     assert np.abs(R).max() <= 1e-11 * max(1.0, np.abs(K).max()) * N ** 0.5
 
 
+@pytest.mark.parametrize("N,kind", [(600, "saddle"), (2100, "saddle"), (300, "zero_diag")])
+def test_ldlt_fp32_updates(ctx, N, kind):
+    """The mixed-precision factorization (FP32 update products, FP64 pivots):
+    inertia of numpy.linalg.eigvalsh and a reconstruction at FP32 accuracy."""
+    torch = torch_cuda()
+    rng = np.random.default_rng(N + 5)
+    K = _sym(rng, N, kind)
+    S = dev(np.asfortranarray(np.tril(K)).T.copy())
+    L = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+    Dd = torch.zeros(N, dtype=torch.float64, device="cuda")
+    Doff = torch.zeros(N, dtype=torch.float64, device="cuda")
+    perm = torch.zeros(N, dtype=torch.int32, device="cuda")
+    kd = torch.zeros(N, dtype=torch.int32, device="cuda")
+    inr = torch.zeros(3, dtype=torch.int32, device="cuda")
+    m.mdsip_ldlt_factor_ex(ctx, N, S, N, 1e-14, m.MDSIP_LDLT_FP32_UPDATES, L, Dd, Doff, perm, kd, inr)
+    torch.cuda.synchronize()
+    ev = np.linalg.eigvalsh(K)
+    assert tuple(int(v) for v in inr.cpu().numpy()) == (int((ev > 0).sum()), int((ev < 0).sum()), 0)
+    Lh = np.tril(L.cpu().numpy().T)
+    dd, do, p = Dd.cpu().numpy(), Doff.cpu().numpy(), perm.cpu().numpy()
+    D = np.diag(dd) + np.diag(do[:-1], -1) + np.diag(do[:-1], 1)
+    R = K[np.ix_(p, p)] - Lh @ D @ Lh.T
+    assert np.abs(R).max() <= 1e-4 * np.abs(K).max()
+    with pytest.raises(m.MdsipError):
+        m.mdsip_ldlt_factor_ex(ctx, N, S, N, 1e-14, 2, L, Dd, Doff, perm, kd, inr)
+
+
 def test_ldlt_singular_and_edge_cases(ctx):
     g = _gpu_ldlt(ctx, np.zeros((5, 5)))
     assert g["inertia"] == (0, 0, 5)
