@@ -87,14 +87,17 @@ __global__ void k_sol_s(Dims D, ModelView M, const double *__restrict__ b, const
 }
 
 // Hu = H_dd u_d (warp per row)
-__global__ void k_hdd_gemv(int64_t n_d, const double *__restrict__ Hdd, const double *__restrict__ ud,
+// Hu[p] = (H_dd u_d)[p] for p < n_d and (J_dh u_d)[p - n_d] for p < n_d + m_I
+// (one warp per row)
+__global__ void k_hdd_gemv(int64_t n_d, int64_t m_I, const double *__restrict__ Hdd,
+                           const double *__restrict__ Jdh, const double *__restrict__ ud,
                            double *__restrict__ Hu) {
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t p = gw; p < n_d; p += nw) {
+    for (int64_t p = gw; p < n_d + m_I; p += nw) {
         double s0 = 0.0, s1 = 0.0;
-        const double *row = Hdd + p * n_d;
+        const double *row = p < n_d ? Hdd + p * n_d : Jdh + (p - n_d) * n_d;
         int64_t k = lane;
         for (; k + 32 < n_d; k += 64) {
             s0 = fma(row[k], ud[k], s0);
@@ -107,7 +110,7 @@ __global__ void k_hdd_gemv(int64_t n_d, const double *__restrict__ Hdd, const do
     }
 }
 
-// r = b - K u, with Au = A u_d, ATug = A^T u_g and Hu = H_dd u_d precomputed.
+// r = b - K u, with Au = A u_d, ATug = A^T u_g and Hu = [H_dd u_d; J_dh u_d] precomputed.
 // Reductions: 0 ||r||_inf, 1 ||b||_inf, 2 ||b - r||_inf (= ||K u||_inf), 3 ||u||_inf
 __global__ void __launch_bounds__(NT) k_residual(Dims D, ModelView M, const double *__restrict__ b,
                                                  const double *__restrict__ u, const double *__restrict__ q,
@@ -144,9 +147,7 @@ __global__ void __launch_bounds__(NT) k_residual(Dims D, ModelView M, const doub
         put(D.n + i, Ku);
     }
     for (int64_t j = gtid; j < D.m_I; j += gsz) {
-        double Ku = -(1.0 / (sig_d[j] + dw) + dc) * uh[j];
-        const double *row = Jdh + j * D.n_d;
-        for (int64_t k = 0; k < D.n_d; ++k) Ku += row[k] * ud[k];
+        const double Ku = -(1.0 / (sig_d[j] + dw) + dc) * uh[j] + Hu[D.n_d + j];   // + (J_dh u_d)_j
         put(D.n + D.m_E + j, Ku);
     }
     double x;
@@ -238,8 +239,8 @@ void Refiner::track_Au(bool init) {
 
 void Refiner::residual(const double *b, const double *u, double dw, double dc, double *r, double *out4) {
     launch_gemv_t(st, M.A, D.m_E, D.n_d, D.lda, u + D.n, colpart, tmp_nd);     // A^T u_g
-    k_hdd_gemv<<<std::max(1, std::min(4096, ceil_div(D.n_d * 32, 256))), 256, 0, st>>>(D.n_d, Hdd, u + D.n_s,
-                                                                                      tmp_nd2);
+    k_hdd_gemv<<<std::max(1, std::min(4096, ceil_div((D.n_d + D.m_I) * 32, 256))), 256, 0, st>>>(
+        D.n_d, D.m_I, Hdd, Jdh, u + D.n_s, tmp_nd2);
     MDSIP_LAUNCHED();
     k_residual<<<kRedBlocks, NT, 0, st>>>(D, M, b, u, q, sig_xd, sig_d, Jdh, Au_run, tmp_nd, tmp_nd2, dw, dc,
                                           r, partial);

@@ -18,7 +18,7 @@ struct Refiner {
     int *solve_err;
     // Newton quantities of the current attempt
     const double *q, *w, *sig_xd, *sig_d, *Jdh, *Hdd;
-    // scratch: bt_g, tmp_m (m_E), tmp_nd, tmp_nd2 (n_d), rhsS (N), colpart, partial
+    // scratch: bt_g, tmp_m (m_E), tmp_nd (n_d), tmp_nd2 (n_d + m_I), rhsS (N), colpart, partial
     double *bt_g, *tmp_m, *tmp_nd, *tmp_nd2, *rhsS, *colpart, *partial;
     double *Au_run;   // A u_d of the current solution, kept as a running sum (m_E)
 

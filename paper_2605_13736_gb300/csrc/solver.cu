@@ -105,7 +105,7 @@ struct Problem {
     DBuf bAfT, btc_ws, btc_err, bref_b, bref_u, bref_r, bref_d, btmp_nd2, bsolve_ws, bsolve_err, bAu_run;
     bool aft_ready = false;
     int64_t tc_prec = -1;
-    DBuf bscal, bpartial, bcolpart;
+    DBuf bscal, bpartial, bcolpart, browtmp;
     double *hscal = nullptr;  // pinned mirror of the scalars
     int32_t *hint = nullptr;  // pinned: inertia (3) + device error flag
 
@@ -334,6 +334,7 @@ static Problem *create_common(Ctx *ctx, int64_t n_d, int64_t n_s, int64_t m_E, i
         dvec(ctx, P->bscal, SC_COUNT);
         dvec(ctx, P->bpartial, (int64_t)kRedBlocks * 8);
         dvec(ctx, P->bcolpart, (int64_t)kRedBlocks * std::max<int64_t>(D.n_d, 1));
+        dvec(ctx, P->browtmp, std::max<int64_t>(D.m_E, 1));
         P->berr.get<int>(ctx, 4);
         MDSIP_CUDA(cudaMallocHost(&P->hscal, SC_COUNT * sizeof(double)));
         MDSIP_CUDA(cudaMallocHost(&P->hint, 8 * sizeof(int32_t)));
@@ -343,6 +344,7 @@ static Problem *create_common(Ctx *ctx, int64_t n_d, int64_t n_s, int64_t m_E, i
         P->V.st = st;
         P->V.partial = P->bpartial.as<double>();
         P->V.colpart = P->bcolpart.as<double>();
+        P->V.rowtmp = P->browtmp.as<double>();
     } catch (...) {
         delete P;
         throw;
@@ -531,7 +533,7 @@ static void prepare_path(Problem *P) {
         dvec(ctx, P->bref_u, nm);
         dvec(ctx, P->bref_r, nm);
         dvec(ctx, P->bref_d, nm);
-        dvec(ctx, P->btmp_nd2, D.n_d);
+        dvec(ctx, P->btmp_nd2, D.n_d + D.m_I);
         dvec(ctx, P->bAu_run, D.m_E);
     }
 }

@@ -14,38 +14,6 @@ constexpr int NT = kRedThreads;
 
 __device__ __forceinline__ bool fin(double v) { return isfinite(v); }
 
-// dot(row, v) over n entries for one warp; row and v 16-byte aligned when
-// vec; four independent 16-byte loads and accumulators per lane.  Result in
-// every lane.
-__device__ __forceinline__ double warp_row_dot(const double *__restrict__ row, const double *__restrict__ v,
-                                               int64_t n, bool vec, int lane) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    if (vec) {
-        const double2 *r2 = reinterpret_cast<const double2 *>(row);
-        const double2 *v2 = reinterpret_cast<const double2 *>(v);
-        const int64_t n2 = n / 2;
-        int64_t k = lane;
-        for (; k + 96 < n2; k += 128) {
-            const double2 a0 = __ldg(r2 + k), a1 = __ldg(r2 + k + 32), a2 = __ldg(r2 + k + 64), a3 = __ldg(r2 + k + 96);
-            const double2 b0 = v2[k], b1 = v2[k + 32], b2 = v2[k + 64], b3 = v2[k + 96];
-            s0 = fma(a0.x, b0.x, fma(a0.y, b0.y, s0));
-            s1 = fma(a1.x, b1.x, fma(a1.y, b1.y, s1));
-            s2 = fma(a2.x, b2.x, fma(a2.y, b2.y, s2));
-            s3 = fma(a3.x, b3.x, fma(a3.y, b3.y, s3));
-        }
-        for (; k < n2; k += 32) {
-            const double2 a0 = __ldg(r2 + k), b0 = v2[k];
-            s0 = fma(a0.x, b0.x, fma(a0.y, b0.y, s0));
-        }
-        if ((n & 1) && lane == 0) s1 = fma(row[n - 1], v[n - 1], s1);
-    } else {
-        for (int64_t k = lane; k < n; k += 32) s0 = fma(row[k], v[k], s0);
-    }
-    double s = (s0 + s1) + (s2 + s3);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    return s;
-}
-
 // partial slot of quantity q for this block
 __device__ __forceinline__ double *slot(double *partial, int q) {
     return partial + (size_t)q * kRedBlocks + blockIdx.x;
@@ -107,24 +75,23 @@ __global__ void __launch_bounds__(NT) k_eval_f(Dims D, ModelView M, const double
 // the dense row of A), ch = h(x) - d.  Reductions: sum |c|, max |c|.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(NT) k_eval_cons(Dims D, ModelView M, const double *__restrict__ x,
-                                                  const double *__restrict__ d, double *__restrict__ cg,
-                                                  double *__restrict__ ch, double *partial) {
+                                                  const double *__restrict__ Axd, const double *__restrict__ d,
+                                                  double *__restrict__ cg, double *__restrict__ ch,
+                                                  double *partial) {
     __shared__ double sh[32];
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * NT) >> 5;
     const double *xd = x + D.n_s;
     double s1 = 0.0, mx = 0.0;
-    const bool vec = (reinterpret_cast<uintptr_t>(xd) & 15) == 0;
-    for (int64_t i = gw; i < D.m_E; i += nw) {
-        double s = warp_row_dot(M.A + i * D.lda, xd, D.n_d, vec, lane);
-        if (lane == 0) {
-            for (int e = M.csr_ptr[i]; e < M.csr_ptr[i + 1]; ++e) s += M.csr_val[e] * x[M.csr_col[e]];
-            const double r = s - M.gE[i];
-            cg[i] = r;
-            s1 += fabs(r);
-            mx = fmax(mx, fabs(r));
-        }
+    // equalities: the dense part A x_d comes from the row-block pass (Axd)
+    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < D.m_E; i += (int64_t)gridDim.x * NT) {
+        double s = Axd[i];
+        for (int e = M.csr_ptr[i]; e < M.csr_ptr[i + 1]; ++e) s += M.csr_val[e] * x[M.csr_col[e]];
+        const double r = s - M.gE[i];
+        cg[i] = r;
+        s1 += fabs(r);
+        mx = fmax(mx, fabs(r));
     }
     for (int64_t j = gw; j < D.m_I; j += nw) {
         double s = 0.0;
@@ -168,18 +135,65 @@ __global__ void k_jac_hess(Dims D, ModelView M, const double *__restrict__ x,
 // ---------------------------------------------------------------------------
 // A passes
 // ---------------------------------------------------------------------------
-// out = A v  (warp per row, 16-byte loads)
+// out = A v: one warp per pair of rows, v staged in shared memory, four
+// 16-byte loads per row and lane in flight, two FP64 accumulators per row.  On
+// GB300 an FP64 pass over A is bound by the DFMA rate (2 flop per 8 bytes);
+// this form reached 0.48 ms for a 100 000 x 2 000 pass (a warp-per-row form
+// 0.56 ms, 32-row register-blocked forms 0.8-0.9 ms at one block per SM).
 __global__ void __launch_bounds__(NT) k_gemv_rows(const double *__restrict__ A, int64_t m, int64_t n,
                                                   int64_t lda, const double *__restrict__ v,
                                                   double *__restrict__ out) {
+    extern __shared__ double vs[];   // n rounded up to even, zero padded
+    const int64_t n2 = (n + 1) / 2;
+    for (int64_t k = threadIdx.x; k < 2 * n2; k += NT) vs[k] = k < n ? v[k] : 0.0;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * NT) >> 5;
-    const bool vec = ((lda & 1) == 0) && ((reinterpret_cast<uintptr_t>(v) & 15) == 0) &&
-                     ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
-    for (int64_t i = gw; i < m; i += nw) {
-        const double s = warp_row_dot(A + i * lda, v, n, vec, lane);
-        if (lane == 0) out[i] = s;
+    const double2 *x2 = reinterpret_cast<const double2 *>(vs);
+    const bool odd = (n & 1) != 0;
+    for (int64_t i = 2 * gw; i < m; i += 2 * nw) {
+        const bool two = i + 1 < m;
+        const double2 *r0 = reinterpret_cast<const double2 *>(A + i * lda);
+        const double2 *r1 = reinterpret_cast<const double2 *>(A + (two ? i + 1 : i) * lda);
+        double s0 = 0.0, s1 = 0.0, t0 = 0.0, t1 = 0.0;
+        int64_t k = lane;
+        const int64_t n2m = odd ? n2 - 1 : n2;   // the last pair of an odd n goes to the guarded tail
+        for (; k + 96 < n2m; k += 128) {
+            double2 a[4], c[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = __ldg(r0 + k + 32 * u);
+                c[u] = __ldg(r1 + k + 32 * u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const double2 b = x2[k + 32 * u];
+                if (u & 1) {
+                    s1 = fma(a[u].x, b.x, fma(a[u].y, b.y, s1));
+                    t1 = fma(c[u].x, b.x, fma(c[u].y, b.y, t1));
+                } else {
+                    s0 = fma(a[u].x, b.x, fma(a[u].y, b.y, s0));
+                    t0 = fma(c[u].x, b.x, fma(c[u].y, b.y, t0));
+                }
+            }
+        }
+        for (; k < n2; k += 32) {
+            const double2 b = x2[k];
+            double2 a0 = __ldg(r0 + k), c0 = __ldg(r1 + k);
+            if (odd && k == n2 - 1) a0.y = c0.y = 0.0;   // the padding column beyond n
+            s0 = fma(a0.x, b.x, fma(a0.y, b.y, s0));
+            t0 = fma(c0.x, b.x, fma(c0.y, b.y, t0));
+        }
+        double s = s0 + s1, t = t0 + t1;
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            t += __shfl_xor_sync(0xffffffffu, t, o);
+        }
+        if (lane == 0) {
+            out[i] = s;
+            if (two) out[i + 1] = t;
+        }
     }
 }
 
@@ -755,11 +769,20 @@ void launch_finalize_min(cudaStream_t s, const double *partial, int nq, double *
 
 static int elem_grid(int64_t n) { return std::max(1, std::min(4096, ceil_div(n, 256))); }
 
+// A: rows 16-byte aligned (lda even, A 16-byte aligned); n <= 24576 (v staged in shared memory)
 void launch_gemv_rows(cudaStream_t s, const double *A, int64_t m, int64_t n, int64_t lda,
                       const double *v, double *out) {
     if (m <= 0) return;
-    const int grid = std::max(1, std::min(8 * kRedBlocks, ceil_div(m, NT / 32)));
-    k_gemv_rows<<<grid, NT, 0, s>>>(A, m, n, lda, v, out);
+    MDSIP_REQUIRE((lda & 1) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0, MDSIP_ERR_INVALID_ARG,
+                  "gemv: rows of A must be 16-byte aligned");
+    const size_t smem = (size_t)((n + 1) / 2) * 2 * sizeof(double);
+    MDSIP_REQUIRE(smem <= 192 * 1024, MDSIP_ERR_INVALID_ARG, "gemv: n too large");
+    static PerDeviceOnce once;
+    MDSIP_CUDA(once.run([] {
+        return cudaFuncSetAttribute(k_gemv_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 192 * 1024);
+    }));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(4 * kRedBlocks, ceil_div(m, NT / 16)));
+    k_gemv_rows<<<grid, NT, smem, s>>>(A, m, n, lda, v, out);
     MDSIP_LAUNCHED();
 }
 
@@ -783,7 +806,8 @@ void VecOps::eval_f(const double *x, double *grad, double *out_scalar) {
 }
 
 void VecOps::eval_cons(const double *x, const double *d, double *cg, double *ch, double *out2) {
-    k_eval_cons<<<kRedBlocks, NT, 0, st>>>(D, M, x, d, cg, ch, partial);
+    if (D.m_E > 0) launch_gemv_rows(st, M.A, D.m_E, D.n_d, D.lda, x + D.n_s, rowtmp);
+    k_eval_cons<<<kRedBlocks, NT, 0, st>>>(D, M, x, rowtmp, d, cg, ch, partial);
     MDSIP_LAUNCHED();
     launch_finalize_sum(st, partial, 1, out2);
     launch_finalize_max(st, partial + kRedBlocks, 1, out2 + 1);

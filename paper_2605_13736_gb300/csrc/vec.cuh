@@ -13,13 +13,14 @@ struct DirView {
 };
 
 // All launches on one stream; `partial` holds kRedBlocks x 8 doubles and
-// `colpart` kRedBlocks x n_d doubles of reduction scratch.
+// `colpart` kRedBlocks x n_d doubles of reduction scratch, `rowtmp` m_E doubles.
 struct VecOps {
     Dims D;
     ModelView M;
     cudaStream_t st;
     double *partial;
     double *colpart;
+    double *rowtmp;   // m_E doubles: A x_d of the constraint evaluation
 
     void eval_f(const double *x, double *grad, double *out_scalar);
     void eval_cons(const double *x, const double *d, double *cg, double *ch, double *out2);
