@@ -318,6 +318,8 @@ struct TcPlan {
     size_t work_floats;
 };
 int64_t syrk_tc_ld(int64_t m);
+void launch_aft_dot(cudaStream_t s, int num_sms, const float *AfT, int64_t ldt, int64_t m, int64_t n,
+                    const double *v, float *vf, double *out);
 TcPlan syrk_tc_plan(int64_t m, int64_t n, int num_sms, int precision);
 size_t syrk_tc_workspace_bytes(const TcPlan &pl, int64_t n, int precision);
 void launch_transpose_f32(cudaStream_t s, const double *A, int64_t m, int64_t n, int64_t lda, float *AfT,

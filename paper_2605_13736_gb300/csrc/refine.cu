@@ -218,7 +218,10 @@ void Refiner::rhs(const IterView &I, const double *gl, const double *cg, const d
 void Refiner::approx_solve(const double *b, double *sol) {
     k_prep_g<<<grid_for(D.m_E), 256, 0, st>>>(D, M, b, q, w, bt_g, tmp_m);
     MDSIP_LAUNCHED();
-    launch_gemv_t(st, M.A, D.m_E, D.n_d, D.lda, tmp_m, colpart, tmp_nd);
+    if (solve_fp32 && AfT)   // approximate solve of a low-precision factor: FP32 A^T product
+        launch_aft_dot(st, num_sms, AfT, ldt, D.m_E, D.n_d, tmp_m, vf, tmp_nd);
+    else
+        launch_gemv_t(st, M.A, D.m_E, D.n_d, D.lda, tmp_m, colpart, tmp_nd);
     k_rhs_S<<<grid_for(std::max(D.n_d, D.m_I)), 256, 0, st>>>(D, b, tmp_nd, rhsS);
     MDSIP_LAUNCHED();
     launch_ldlt_solve_coop(st, num_sms, N, Dd, Doff, perm, 1, rhsS, N, solve_ws, solve_err, solve_fp32);

@@ -14,7 +14,12 @@ struct Refiner {
     const int32_t *perm;
     int num_sms;
     void *solve_ws;   // ldlt_solve_scratch_bytes(N)
-    bool solve_fp32;  // the prepared tiles are FP32
+    bool solve_fp32;  // the prepared tiles are FP32 (tensor-core factor)
+    // FP32 transposed copy of A (n_d x ldt) and an ldt-float scratch: with a
+    // tensor-core factor the approximate solve forms its A^T products from it
+    const float *AfT;
+    int64_t ldt;
+    float *vf;
     int *solve_err;
     // Newton quantities of the current attempt
     const double *q, *w, *sig_xd, *sig_d, *Jdh, *Hdd;

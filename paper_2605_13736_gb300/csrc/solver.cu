@@ -102,7 +102,7 @@ struct Problem {
     // reduced matrix and factors
     DBuf bS, bL, bDd, bDoff, bperm, bkind, binertia, bldlt_ws, berr, bsyrk_ws;
     // tensor-core condensation and refinement
-    DBuf bAfT, btc_ws, btc_err, bref_b, bref_u, bref_r, bref_d, btmp_nd2, bsolve_ws, bsolve_err, bAu_run;
+    DBuf bAfT, bvf, btc_ws, btc_err, bref_b, bref_u, bref_r, bref_d, btmp_nd2, bsolve_ws, bsolve_err, bAu_run;
     bool aft_ready = false;
     int64_t tc_prec = -1;
     DBuf bscal, bpartial, bcolpart, browtmp;
@@ -547,6 +547,7 @@ static void prepare_tc(Problem *P) {
     const Dims &D = P->D;
     const TcPlan pl = syrk_tc_plan(D.m_E, D.n_d, ctx->num_sms, prec);
     if (!P->bAfT.ptr) P->bAfT.get<float>(ctx, (size_t)std::max<int64_t>(D.n_d, 1) * pl.ldt);
+    if (!P->bvf.ptr) P->bvf.get<float>(ctx, (size_t)pl.ldt);
     if (P->tc_prec != prec) {
         P->btc_ws.get<char>(ctx, syrk_tc_workspace_bytes(pl, D.n_d, prec));
         P->btc_err.get<int>(ctx, 4);
@@ -693,6 +694,9 @@ static RefineResult solve_direction_refined(Problem *P, double mu, double dw, do
     R.solve_ws = P->bsolve_ws.ptr;
     R.solve_err = P->bsolve_err.as<int>();
     R.solve_fp32 = P->solve_fp32;
+    R.AfT = P->aft_ready ? P->bAfT.as<float>() : nullptr;
+    R.ldt = syrk_tc_ld(D.m_E);
+    R.vf = P->bvf.as<float>();
     R.q = P->bq.as<double>();
     R.w = P->bw.as<double>();
     R.sig_xd = P->bsig_x.as<double>() + D.n_s;

@@ -217,7 +217,54 @@ __global__ void k_tc_reduce(int64_t n, int tiles, int nsplit, const float *__res
     }
 }
 
+// vf[i] = (float) v[i] for i < m, 0 up to ldt
+__global__ void k_to_f32_padded(int64_t m, int64_t ldt, const double *__restrict__ v, float *__restrict__ vf) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ldt; i += (int64_t)gridDim.x * blockDim.x)
+        vf[i] = i < m ? (float)v[i] : 0.0f;
+}
+
+// out[p] = sum_i AfT[p][i] vf[i] (FP32 products and sums, one block per row of
+// AfT, i.e. per column of A; 16-byte loads)
+__global__ void __launch_bounds__(256) k_aft_dot(const float *__restrict__ AfT, int64_t ldt, int64_t n,
+                                                 const float *__restrict__ vf, double *__restrict__ out) {
+    __shared__ float red[8];
+    const int64_t q = ldt / 4;
+    const float4 *v4 = reinterpret_cast<const float4 *>(vf);
+    for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
+        const float4 *row = reinterpret_cast<const float4 *>(AfT + p * ldt);
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        for (int64_t k = threadIdx.x; k < q; k += 256) {
+            const float4 a = __ldg(row + k), b = __ldg(v4 + k);
+            s0 = fmaf(a.x, b.x, s0);
+            s1 = fmaf(a.y, b.y, s1);
+            s2 = fmaf(a.z, b.z, s2);
+            s3 = fmaf(a.w, b.w, s3);
+        }
+        float t = (s0 + s1) + (s2 + s3);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float u = 0.f;
+            for (int w = 0; w < 8; ++w) u += red[w];
+            out[p] = (double)u;
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
+
+// out = A^T v in FP32 from the transposed copy AfT (n x ldt, zero padded
+// beyond m): the approximate products of the refined path.  vf: ldt floats.
+void launch_aft_dot(cudaStream_t s, int num_sms, const float *AfT, int64_t ldt, int64_t m, int64_t n,
+                    const double *v, float *vf, double *out) {
+    if (n <= 0) return;
+    k_to_f32_padded<<<std::max(1, std::min(4096, ceil_div(ldt, 256))), 256, 0, s>>>(m, ldt, v, vf);
+    MDSIP_LAUNCHED();
+    k_aft_dot<<<(unsigned)std::min<int64_t>(n, (int64_t)num_sms * 8), 256, 0, s>>>(AfT, ldt, n, vf, out);
+    MDSIP_LAUNCHED();
+}
 
 int64_t syrk_tc_ld(int64_t m) { return (std::max<int64_t>(m, 1) + 63) / 64 * 64; }
 

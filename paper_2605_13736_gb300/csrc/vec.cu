@@ -240,13 +240,34 @@ __global__ void __launch_bounds__(NT) k_gemv_t(const double *__restrict__ A, int
     }
 }
 
-__global__ void k_colsum(const double *__restrict__ partial, int nparts, int64_t n,
-                         double *__restrict__ out) {
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nparts; ++b) s += partial[(size_t)b * n + p];
-        out[p] = s;
+// out[p] = sum_b partial[b][p]: a block per 32 columns, warp w summing the
+// partials b = w, w + 8, ... in order (coalesced 32-column rows, eight rows in
+// flight per warp), then the eight warp sums in order (deterministic).
+__global__ void __launch_bounds__(256) k_colsum(const double *__restrict__ partial, int nparts, int64_t n,
+                                                double *__restrict__ out) {
+    __shared__ double sp[8][33];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t p = (int64_t)blockIdx.x * 32 + lane;
+    double s = 0.0;
+    if (p < n) {
+        int b = wid;
+        for (; b + 24 < nparts; b += 32) {
+            const double a0 = partial[(size_t)b * n + p], a1 = partial[(size_t)(b + 8) * n + p];
+            const double a2 = partial[(size_t)(b + 16) * n + p], a3 = partial[(size_t)(b + 24) * n + p];
+            s += a0;
+            s += a1;
+            s += a2;
+            s += a3;
+        }
+        for (; b < nparts; b += 8) s += partial[(size_t)b * n + p];
+    }
+    sp[wid][lane] = s;
+    __syncthreads();
+    if (wid == 0 && p < n) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += sp[w][lane];
+        out[p] = t;
     }
 }
 
@@ -795,7 +816,7 @@ void launch_gemv_t(cudaStream_t s, const double *A, int64_t m, int64_t n, int64_
     }
     k_gemv_t<<<kRedBlocks, NT, 0, s>>>(A, m, n, lda, u, partial);
     MDSIP_LAUNCHED();
-    k_colsum<<<elem_grid(n), 256, 0, s>>>(partial, kRedBlocks, n, out);
+    k_colsum<<<(unsigned)ceil_div(n, 32), 256, 0, s>>>(partial, kRedBlocks, n, out);
     MDSIP_LAUNCHED();
 }
 
