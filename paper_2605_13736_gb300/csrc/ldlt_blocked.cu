@@ -55,6 +55,7 @@ struct Cand {                  // one CTA's candidate of a cluster-wide arg-max
     int idx;                   // global row (first index on ties)
     int pad;
     double val;                // diagonal value, when this CTA owns it
+    unsigned long long abits;  // bit pattern of alpha |v| (rounded), for the pivot test
 };
 
 struct PanelArgs {
@@ -91,11 +92,14 @@ __device__ __forceinline__ void warp_cand(unsigned long long &b, int &idx) {
     b = ((unsigned long long)mhi << 32) | mlo;
 }
 
-// block arg-max into *out (bits, idx); val = *diag (a shared-memory value
-// written before the call, read after the barrier; 0 if diag is null).
-// One __syncthreads; *out is complete when warp 0 returns.
+// block arg-max into *out (bits, idx, and alpha |max| as abits); val = *diag
+// (a shared-memory value written before the call, read after the barrier; 0
+// if diag is null).  One __syncthreads; *out is complete when warp 0 returns.
+// Since rounding is monotone, the cluster-wide maximum of the CTAs' abits is
+// the bit pattern of fl(alpha colmax): the common pivot test then needs no
+// FP64 instruction on the column's critical path.
 __device__ void block_cand_to(unsigned long long b, int idx, const double *diag, unsigned long long *sb,
-                              int *si, Cand *out) {
+                              int *si, Cand *out, double alpha) {
     warp_cand(b, idx);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
@@ -112,6 +116,7 @@ __device__ void block_cand_to(unsigned long long b, int idx, const double *diag,
             out->bits = b;
             out->idx = idx;
             out->val = diag ? *diag : 0.0;
+            out->abits = absbits64(alpha * __longlong_as_double((long long)b));
         }
     }
 }
@@ -139,7 +144,7 @@ __device__ __forceinline__ double rcp_newton(double d) {
 __device__ bool cluster_cand(cg::cluster_group &cl, Cand *cand, int slot, int C, int vrank, Cand &res) {
     if (threadIdx.x >= 32) return false;
     const int c = threadIdx.x;
-    unsigned long long b = 0;
+    unsigned long long b = 0, ab = 0;
     int idx = 0x7fffffff;
     double v = 0.0;
     if (c < C) {
@@ -147,12 +152,16 @@ __device__ bool cluster_cand(cg::cluster_group &cl, Cand *cand, int slot, int C,
         b = o->bits;
         idx = o->idx;
         v = o->val;
+        ab = o->abits;
     }
     const double vsel = __shfl_sync(0xffffffffu, v, vrank);
     warp_cand(b, idx);
+    const unsigned ahi = __reduce_max_sync(0xffffffffu, (unsigned)(ab >> 32));
+    const unsigned alo = __reduce_max_sync(0xffffffffu, (unsigned)(ab >> 32) == ahi ? (unsigned)ab : 0u);
     res.bits = b;
     res.idx = idx;
     res.val = vsel;
+    res.abits = ((unsigned long long)ahi << 32) | alo;
     return c == 0;
 }
 
@@ -243,7 +252,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_bk_panel(PanelArgs a) {
                 if (i > j) cand_combine(b, bi, absbits64(v), i);
             }
         }
-        block_cand_to(b, bi, (j >= r0 && j < r1) ? Wp + (size_t)(j - r0) * S + jj : nullptr, s_b, s_i, &cpair[0]);
+        block_cand_to(b, bi, (j >= r0 && j < r1) ? Wp + (size_t)(j - r0) * S + jj : nullptr, s_b, s_i, &cpair[0], alpha);
         cl.sync();   // #1
         {
             Cand res;
@@ -255,13 +264,14 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_bk_panel(PanelArgs a) {
         // microseconds): the pivot test in warp 0, the reciprocal of the
         // diagonal (used when the test keeps it) in warp 1
         if (tid == 0) {
-            const double absakk = fabs(s_cand.val);
-            const double colmax = __longlong_as_double((long long)s_cand.bits);
+            // |a_kk| >= alpha colmax, or both zero, as integer compares of the
+            // non-negative FP64 bit patterns
+            const unsigned long long akb = absbits64(s_cand.val);
             s_dec[0] = s_cand.idx == 0x7fffffff ? j : s_cand.idx;
-            const bool plain = fmax(absakk, colmax) == 0.0 || absakk >= alpha * colmax;
+            const bool plain = (akb == 0ULL && s_cand.bits == 0ULL) || akb >= s_cand.abits;
             s_dec[1] = plain ? 0 : 1;
-            s_sc[0] = absakk;
-            s_sc[1] = colmax;
+            s_sc[0] = __longlong_as_double((long long)akb);
+            s_sc[1] = __longlong_as_double((long long)s_cand.bits);
         } else if (tid == 32) {
             s_rcp = rcp_newton(s_cand.val);
         }
@@ -309,7 +319,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_bk_panel(PanelArgs a) {
                 }
             }
             block_cand_to(b2, bi2, (r >= r0 && r < r1) ? Wp + (size_t)(r - r0) * S + jj + 1 : nullptr, s_b, s_i,
-                          &cpair[1]);
+                          &cpair[1], alpha);
             cl.sync();   // #2
             {
                 Cand res;
