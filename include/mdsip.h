@@ -160,7 +160,10 @@ mdsip_status mdsip_set_bounds(mdsip_problem *p, const double *xl, const double *
 void mdsip_problem_destroy(mdsip_problem *p);
 
 /* Options (Section 2.1 method constants; names as in the oracle):
- *   int:    max_iter, path, max_ls, refine_max, precision (MDSIP_PREC_*)
+ *   int:    max_iter, path, max_ls, refine_max, precision (MDSIP_PREC_*),
+ *           graphs (1, default: from its second use for a given order, the
+ *           factorization phase -- scale of S, LDL^T, solve tiles -- runs as
+ *           one captured CUDA graph; 0: separate launches)
  *   double: tol, mu0, kappa_eps, kappa_mu, theta_mu, tau_min, s_max, kappa_1,
  *           kappa_2, kappa_sigma, gamma_theta, gamma_phi, delta, s_theta, s_phi,
  *           eta_phi, gamma_alpha, dw0, dw_min, dw_max, kw_minus, kw_plus,

@@ -141,6 +141,7 @@ struct Options {
     double refine_tol = 1e-14;
     double refine_fallback_tol = 1e-10;
     double time_limit_s = 0.0;
+    int64_t graphs = 1;               // 1: replay the factorization phase as a CUDA graph
 };
 
 // ---------------------------------------------------------------------------

@@ -22,7 +22,12 @@
 namespace mdsip {
 
 static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local long long t_launches = 0;   // this thread's launches (graph capture bookkeeping)
+void count_launch() {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    ++t_launches;
+}
+static void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------------------
 // Context
@@ -129,8 +134,27 @@ struct Problem {
     std::vector<mdsip_iter_rec> log;
     mdsip_stats stats{};
     cudaEvent_t ev[12]{};
+    // The factorization phase (scale of S, the LDL^T's kernels, the solve's
+    // tiles: about 70 launches with fixed arguments for a given order and
+    // precision) as a CUDA graph: captured on its second use, replayed after.
+    struct FactorGraph {
+        cudaGraphExec_t exec = nullptr;
+        int64_t N = -1;
+        double zero_tol = -1.0;
+        int uses = 0;
+        long long launches = 0;
+        bool disabled = false;
+    } fgraph[2];   // [0] FP64 updates, [1] FP32 updates
+
+    void drop_graphs() {
+        for (auto &g : fgraph) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            g = FactorGraph{};
+        }
+    }
 
     ~Problem() {
+        drop_graphs();
         if (hscal) cudaFreeHost(hscal);
         if (hint) cudaFreeHost(hint);
         for (auto &e : ev)
@@ -509,6 +533,7 @@ static void prepare_path(Problem *P) {
     MDSIP_REQUIRE(2 * N * (int64_t)sizeof(double) <= 200 * 1024, MDSIP_ERR_INVALID_ARG,
                   "reduced matrix too large for the dense factorization");
     if (path == P->path && N == P->N && P->bS.ptr) return;
+    P->drop_graphs();   // the captured factorizations point at the old buffers
     P->path = path;
     P->N = N;
     Ctx *ctx = P->ctx;
@@ -564,6 +589,67 @@ struct Inertia {
     bool operator==(const Inertia &o) const { return pos == o.pos && neg == o.neg && zero == o.zero; }
 };
 
+// Run the factorization phase `enqueue` on the problem's stream: eagerly on
+// its first use for an order, captured into a CUDA graph on the second (only
+// with the blocked factorization, whose launches need no host state), and as
+// one graph launch afterwards.  A capture that fails falls back to eager
+// launches for good.
+template <class F>
+static void run_factor_phase(Problem *P, int slot, F &&enqueue) {
+    Problem::FactorGraph &g = P->fgraph[slot];
+    cudaStream_t st = P->ctx->stream;
+    if (g.N != P->N || g.zero_tol != P->opt.zero_tol) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = Problem::FactorGraph{};
+        g.N = P->N;
+        g.zero_tol = P->opt.zero_tol;
+    }
+    if (g.exec) {
+        MDSIP_CUDA(cudaGraphLaunch(g.exec, st));
+        count_launches(g.launches);
+        return;
+    }
+    ++g.uses;
+    if (!P->opt.graphs || g.disabled || g.uses < 2 || !ldlt_blocked_available(P->N)) {
+        enqueue();
+        return;
+    }
+    const long long before = t_launches;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {   // e.g. legacy stream
+        cudaGetLastError();
+        g.disabled = true;
+        enqueue();
+        return;
+    }
+    try {
+        enqueue();
+    } catch (...) {
+        cudaStreamEndCapture(st, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        g.disabled = true;
+        throw;
+    }
+    const cudaError_t e = cudaStreamEndCapture(st, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+        g.exec = exec;
+        g.launches = t_launches - before;
+        g_launches.fetch_sub(g.launches, std::memory_order_relaxed);   // counted at replay
+    } else {
+        g.disabled = true;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (g.exec) {
+        MDSIP_CUDA(cudaGraphLaunch(g.exec, st));
+        count_launches(g.launches);
+    } else {
+        enqueue();
+    }
+}
+
 static Inertia factor_attempt(Problem *P, double dw, double dc, bool force_fp64 = false) {
     const Dims &D = P->D;
     cudaStream_t st = P->ctx->stream;
@@ -596,17 +682,20 @@ static Inertia factor_attempt(Problem *P, double dw, double dc, bool force_fp64 
                           q, dw, dc, S);
     }
     MDSIP_CUDA(cudaEventRecord(P->ev[1], st));
-    launch_maxabs_lower(st, P->N, S, P->N, P->V.partial, sc + SC_MAXABS);
-    MDSIP_CUDA(cudaMemsetAsync(P->berr.ptr, 0, sizeof(int), st));
-    LdltOut o{P->bL.as<double>(), P->bDd.as<double>(), P->bDoff.as<double>(), P->bperm.as<int32_t>(),
-              P->bkind.as<int32_t>(), P->binertia.as<int32_t>()};
     MDSIP_CUDA(cudaEventRecord(P->ev[10], st));
     const bool tc_factor = p2 && P->opt.precision != MDSIP_PREC_FP64 && !force_fp64;
-    launch_ldlt(st, P->ctx->num_sms, P->N, S, P->N, sc + SC_MAXABS, P->opt.zero_tol, o,
-                P->bldlt_ws.ptr, P->berr.as<int>(), tc_factor);
     // the refined tensor-core path solves with FP32 tiles of L; the FP64 path with FP64 tiles
-    P->solve_fp32 = p2 && P->opt.precision != MDSIP_PREC_FP64 && !force_fp64;
-    launch_ldlt_solve_prepare(st, P->N, P->bL.as<double>(), P->bsolve_ws.ptr, P->solve_fp32);
+    P->solve_fp32 = tc_factor;
+    auto factor_phase = [&] {
+        launch_maxabs_lower(st, P->N, S, P->N, P->V.partial, sc + SC_MAXABS);
+        MDSIP_CUDA(cudaMemsetAsync(P->berr.ptr, 0, sizeof(int), st));
+        LdltOut o{P->bL.as<double>(), P->bDd.as<double>(), P->bDoff.as<double>(), P->bperm.as<int32_t>(),
+                  P->bkind.as<int32_t>(), P->binertia.as<int32_t>()};
+        launch_ldlt(st, P->ctx->num_sms, P->N, S, P->N, sc + SC_MAXABS, P->opt.zero_tol, o, P->bldlt_ws.ptr,
+                    P->berr.as<int>(), tc_factor);
+        launch_ldlt_solve_prepare(st, P->N, P->bL.as<double>(), P->bsolve_ws.ptr, P->solve_fp32);
+    };
+    run_factor_phase(P, tc_factor ? 1 : 0, factor_phase);
     MDSIP_CUDA(cudaEventRecord(P->ev[2], st));
     MDSIP_CUDA(cudaMemcpyAsync(P->hint, P->binertia.ptr, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     MDSIP_CUDA(cudaMemcpyAsync(P->hint + 4, P->berr.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -1097,7 +1186,7 @@ static bool set_option(Options &o, const std::string &name, double v, bool is_in
                        {"time_limit_s", &o.time_limit_s}, {"refine_tol", &o.refine_tol},
                        {"refine_fallback_tol", &o.refine_fallback_tol}};
     const I iopts[] = {{"max_iter", &o.max_iter}, {"path", &o.path}, {"max_ls", &o.max_ls},
-                       {"refine_max", &o.refine_max}, {"precision", &o.precision}};
+                       {"refine_max", &o.refine_max}, {"precision", &o.precision}, {"graphs", &o.graphs}};
     if (is_int) {
         for (auto &e : iopts)
             if (name == e.n) { *e.p = (int64_t)v; return true; }
