@@ -163,7 +163,11 @@ void mdsip_problem_destroy(mdsip_problem *p);
  *   int:    max_iter, path, max_ls, refine_max, precision (MDSIP_PREC_*),
  *           graphs (1, default: from its second use for a given order, the
  *           factorization phase -- scale of S, LDL^T, solve tiles -- runs as
- *           one captured CUDA graph; 0: separate launches)
+ *           one captured CUDA graph; 0: separate launches),
+ *           autotune (1, default: the blocked LDL^T's panel width and, for
+ *           products below 4e10 multiply-adds, the FP64 product's tile edge
+ *           are chosen by timing the candidates at first use per device and
+ *           shape; 0: the analytic choices)
  *   double: tol, mu0, kappa_eps, kappa_mu, theta_mu, tau_min, s_max, kappa_1,
  *           kappa_2, kappa_sigma, gamma_theta, gamma_phi, delta, s_theta, s_phi,
  *           eta_phi, gamma_alpha, dw0, dw_min, dw_max, kw_minus, kw_plus,

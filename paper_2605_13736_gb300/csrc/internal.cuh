@@ -142,6 +142,7 @@ struct Options {
     double refine_fallback_tol = 1e-10;
     double time_limit_s = 0.0;
     int64_t graphs = 1;               // 1: replay the factorization phase as a CUDA graph
+    int64_t autotune = 1;             // 1: time tile-shape candidates at first use per shape
 };
 
 // ---------------------------------------------------------------------------
@@ -310,7 +311,7 @@ void launch_syrk_fp64(Ctx *ctx, const double *A, int64_t m, int64_t n, int64_t l
 size_t syrk_fp64_scratch_bytes(int64_t m, int64_t n, int num_sms);
 void launch_syrk_fp64_ws(cudaStream_t s, int num_sms, const double *A, int64_t m, int64_t n,
                          int64_t lda, const double *w, double beta, double *C, int64_t ldc,
-                         double *work);
+                         double *work, int bm = 0);
 
 // Tensor-core SYRK (syrk_tc.cu)
 struct TcPlan {
@@ -336,11 +337,12 @@ struct LdltOut {
 size_t ldlt_scratch_bytes(int64_t N);
 void launch_ldlt(cudaStream_t s, int num_sms, int64_t N, const double *S, int64_t ld,
                  const double *maxabs_dev, double zero_tol, LdltOut out, void *scratch,
-                 int *err_dev, bool fp32_update = false);
+                 int *err_dev, bool fp32_update = false, int nb = 0);
 size_t ldlt_blocked_scratch_bytes(int64_t N);
 bool ldlt_blocked_available(int64_t N);
+std::vector<int> ldlt_blocked_widths(int64_t N, bool f32);
 void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, const double *maxabs_dev,
-                         double zero_tol, LdltOut out, void *scratch, bool fp32_update);
+                         double zero_tol, LdltOut out, void *scratch, bool fp32_update, int nb = 0);
 void launch_ldlt_solve(cudaStream_t s, int64_t N, const double *L, const double *Dd,
                        const double *Doff, const int32_t *perm, int64_t nrhs, double *B,
                        int64_t ldb);

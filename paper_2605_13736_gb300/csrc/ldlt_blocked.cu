@@ -30,6 +30,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -586,8 +587,9 @@ size_t panel_smem(int R, int NB, bool f32) {
            64;
 }
 
-// cluster size and panel width for order N on this device (C = 0: unavailable)
-BlockedConfig blocked_config(int64_t N, bool f32) {
+// cluster size and panel width for order N on this device (C = 0: unavailable);
+// nb > 0 asks for that panel width if it fits
+BlockedConfig blocked_config(int64_t N, bool f32, int nb_want = 0) {
     static std::mutex mu;
     static int clusters16[64] = {};   // 1: size 16 allowed, -1: not, 0: unknown
     int dev = 0;
@@ -629,6 +631,7 @@ BlockedConfig blocked_config(int64_t N, bool f32) {
     c.C = (dev >= 0 && dev < 64 && clusters16[dev] == 1) ? 16 : 8;
     for (int nb : {64, 32, 16, 8}) {
         const int R = (int)((N + c.C - 1) / c.C);
+        if (nb_want > 0 && nb != nb_want) continue;
         if (panel_smem(R, nb, f32) <= kSmemCap) {
             c.NB = nb;
             c.R = R;
@@ -647,17 +650,26 @@ size_t ldlt_blocked_scratch_bytes(int64_t N) {
     return ((size_t)std::max<int64_t>(N, 1) * 65 * sizeof(double) + 255) / 256 * 256 + 256;
 }
 
+// panel widths that fit for order N (widest first)
+std::vector<int> ldlt_blocked_widths(int64_t N, bool f32) {
+    std::vector<int> out;
+    for (int nb : {64, 32, 16})
+        if (blocked_config(N, f32, nb).C > 0) out.push_back(nb);
+    return out;
+}
+
 bool ldlt_blocked_available(int64_t N) { return blocked_config(N, true).C > 0 && blocked_config(N, false).C > 0; }
 
 // S (lower, ld N) is overwritten.  scratch: ldlt_blocked_scratch_bytes(N),
 // 256-byte aligned.  fp32_update: trailing products in FP32.
 void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, const double *maxabs_dev,
-                         double zero_tol, LdltOut out, void *scratch, bool fp32_update) {
+                         double zero_tol, LdltOut out, void *scratch, bool fp32_update, int nb) {
     if (N <= 0) {
         MDSIP_CUDA(cudaMemsetAsync(out.inertia, 0, 3 * sizeof(int32_t), s));
         return;
     }
-    const BlockedConfig cfg = blocked_config(N, fp32_update);
+    BlockedConfig cfg = blocked_config(N, fp32_update, nb);
+    if (cfg.C == 0) cfg = blocked_config(N, fp32_update);
     MDSIP_REQUIRE(cfg.C > 0, MDSIP_ERR_INVALID_ARG, "ldlt: N too large for the blocked factorization");
     char *w = static_cast<char *>(scratch);
     MDSIP_REQUIRE((reinterpret_cast<uintptr_t>(w) & 255) == 0, MDSIP_ERR_INVALID_ARG, "ldlt: misaligned scratch");

@@ -105,7 +105,7 @@ struct Problem {
     DBuf bgrad, bgrad_t, bcg, bcg_t, bch, bch_t, bgl, bATy, bJdh, bHss, bHdd;
     DBuf bsig_x, bq, bsig_d, bw, bbt_g, bu, bATu, brhs, bAdx;
     // reduced matrix and factors
-    DBuf bS, bL, bDd, bDoff, bperm, bkind, binertia, bldlt_ws, berr, bsyrk_ws;
+    DBuf bS, bL, bDd, bDoff, bperm, bkind, binertia, bldlt_ws, berr, bsyrk_ws, btune;
     // tensor-core condensation and refinement
     DBuf bAfT, bvf, btc_ws, btc_err, bref_b, bref_u, bref_r, bref_d, btmp_nd2, bsolve_ws, bsolve_err, bAu_run;
     bool aft_ready = false;
@@ -589,6 +589,72 @@ struct Inertia {
     bool operator==(const Inertia &o) const { return pos == o.pos && neg == o.neg && zero == o.zero; }
 };
 
+// ---------------------------------------------------------------------------
+// Autotuning: tile shapes chosen by timing the candidates once per device and
+// shape (CUDA events on the problem's stream, one warm and one timed run each)
+// and remembered for the process.
+// ---------------------------------------------------------------------------
+enum TuneKind { TUNE_LDLT_PANEL = 0, TUNE_SYRK_TILE = 1 };
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int64_t, int64_t>, int> g_tune;
+
+static bool tune_get(int kind, int64_t a, int64_t b, int *v) {
+    int dev = 0;
+    MDSIP_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(std::make_tuple(dev, kind, a, b));
+    if (it == g_tune.end()) return false;
+    *v = it->second;
+    return true;
+}
+
+static void tune_put(int kind, int64_t a, int64_t b, int v) {
+    int dev = 0;
+    MDSIP_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[std::make_tuple(dev, kind, a, b)] = v;
+}
+
+// best of `cands` by the CUDA-event time of run(c) (after one warm run)
+template <class F>
+static int tune_pick(Problem *P, const std::vector<int> &cands, F &&run) {
+    cudaStream_t st = P->ctx->stream;
+    int best = cands.empty() ? 0 : cands[0];
+    float best_ms = INFINITY;
+    for (int c : cands) {
+        run(c);
+        MDSIP_CUDA(cudaEventRecord(P->ev[11], st));
+        run(c);
+        MDSIP_CUDA(cudaEventRecord(P->ev[7], st));
+        MDSIP_CUDA(cudaEventSynchronize(P->ev[7]));
+        float ms = 0.0f;
+        MDSIP_CUDA(cudaEventElapsedTime(&ms, P->ev[11], P->ev[7]));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    return best;
+}
+
+// Tile edge of the FP64 condensation product for this problem's A (tuned when
+// the product is small enough for the extra runs not to matter: the many-
+// instance setting, where the analytic choice is least reliable).
+static int tuned_syrk_tile(Problem *P) {
+    const Dims &D = P->D;
+    if (!P->opt.autotune || (double)D.m_E * D.n_d * D.n_d > 4e10) return 0;
+    int v = 0;
+    if (tune_get(TUNE_SYRK_TILE, D.m_E, D.n_d, &v)) return v;
+    double *C = P->btune.get<double>(P->ctx, (size_t)std::max<int64_t>(D.n_d * D.n_d, 1));
+    v = tune_pick(P, {64, 80}, [&](int bm) {
+        launch_syrk_fp64_ws(P->ctx->stream, P->ctx->num_sms, P->Mv.A, D.m_E, D.n_d, D.lda, P->bw.as<double>(),
+                            0.0, C, D.n_d, P->bsyrk_ws.as<double>(), bm);
+    });
+    P->btune.reset();
+    tune_put(TUNE_SYRK_TILE, D.m_E, D.n_d, v);
+    return v;
+}
+
 // Run the factorization phase `enqueue` on the problem's stream: eagerly on
 // its first use for an order, captured into a CUDA graph on the second (only
 // with the blocked factorization, whose launches need no host state), and as
@@ -650,6 +716,37 @@ static void run_factor_phase(Problem *P, int slot, F &&enqueue) {
     }
 }
 
+// Panel width of the blocked LDL^T for this order and update precision, tuned
+// on a copy of the current S (the trial factorizations overwrite S, L, D).
+static int tuned_ldlt_width(Problem *P, bool fp32) {
+    const int64_t N = P->N;
+    if (!P->opt.autotune || !ldlt_blocked_available(N)) return 0;
+    int v = 0;
+    if (tune_get(TUNE_LDLT_PANEL, N, fp32 ? 1 : 0, &v)) return v;
+    const std::vector<int> cands = ldlt_blocked_widths(N, fp32);
+    if (cands.size() < 2) {
+        v = cands.empty() ? 0 : cands[0];
+    } else {
+        cudaStream_t st = P->ctx->stream;
+        double *S = P->bS.as<double>(), *Ssave = P->btune.get<double>(P->ctx, (size_t)N * N);
+        double *sc = P->scal();
+        MDSIP_CUDA(cudaMemcpyAsync(Ssave, S, (size_t)N * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        v = tune_pick(P, cands, [&](int nb) {
+            MDSIP_CUDA(cudaMemcpyAsync(S, Ssave, (size_t)N * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            launch_maxabs_lower(st, N, S, N, P->V.partial, sc + SC_MAXABS);
+            LdltOut o{P->bL.as<double>(), P->bDd.as<double>(), P->bDoff.as<double>(), P->bperm.as<int32_t>(),
+                      P->bkind.as<int32_t>(), P->binertia.as<int32_t>()};
+            launch_ldlt(st, P->ctx->num_sms, N, S, N, sc + SC_MAXABS, P->opt.zero_tol, o, P->bldlt_ws.ptr,
+                        P->berr.as<int>(), fp32, nb);
+        });
+        MDSIP_CUDA(cudaMemcpyAsync(S, Ssave, (size_t)N * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        MDSIP_CUDA(cudaStreamSynchronize(st));
+        P->btune.reset();
+    }
+    tune_put(TUNE_LDLT_PANEL, N, fp32 ? 1 : 0, v);
+    return v;
+}
+
 static Inertia factor_attempt(Problem *P, double dw, double dc, bool force_fp64 = false) {
     const Dims &D = P->D;
     cudaStream_t st = P->ctx->stream;
@@ -673,8 +770,10 @@ static Inertia factor_attempt(Problem *P, double dw, double dc, bool force_fp64 
             launch_syrk_tc(st, P->ctx->num_sms, (int)P->opt.precision, P->bAfT.as<float>(), D.m_E, D.n_d, w,
                            1.0, S, P->N, P->btc_ws.ptr, P->btc_err.as<int>());
         } else {
+            const int bm = tuned_syrk_tile(P);
+            MDSIP_CUDA(cudaEventRecord(P->ev[8], st));   // the tile choice's trial runs are not the product
             launch_syrk_fp64_ws(st, P->ctx->num_sms, P->Mv.A, D.m_E, D.n_d, D.lda, w, 1.0, S, P->N,
-                                P->bsyrk_ws.as<double>());
+                                P->bsyrk_ws.as<double>(), bm);
         }
         MDSIP_CUDA(cudaEventRecord(P->ev[9], st));
     } else {
@@ -686,13 +785,15 @@ static Inertia factor_attempt(Problem *P, double dw, double dc, bool force_fp64 
     const bool tc_factor = p2 && P->opt.precision != MDSIP_PREC_FP64 && !force_fp64;
     // the refined tensor-core path solves with FP32 tiles of L; the FP64 path with FP64 tiles
     P->solve_fp32 = tc_factor;
+    const int nb = tuned_ldlt_width(P, tc_factor);
+    MDSIP_CUDA(cudaEventRecord(P->ev[10], st));   // the width's trial runs are not the factorization
     auto factor_phase = [&] {
         launch_maxabs_lower(st, P->N, S, P->N, P->V.partial, sc + SC_MAXABS);
         MDSIP_CUDA(cudaMemsetAsync(P->berr.ptr, 0, sizeof(int), st));
         LdltOut o{P->bL.as<double>(), P->bDd.as<double>(), P->bDoff.as<double>(), P->bperm.as<int32_t>(),
                   P->bkind.as<int32_t>(), P->binertia.as<int32_t>()};
         launch_ldlt(st, P->ctx->num_sms, P->N, S, P->N, sc + SC_MAXABS, P->opt.zero_tol, o, P->bldlt_ws.ptr,
-                    P->berr.as<int>(), tc_factor);
+                    P->berr.as<int>(), tc_factor, nb);
         launch_ldlt_solve_prepare(st, P->N, P->bL.as<double>(), P->bsolve_ws.ptr, P->solve_fp32);
     };
     run_factor_phase(P, tc_factor ? 1 : 0, factor_phase);
@@ -1186,7 +1287,8 @@ static bool set_option(Options &o, const std::string &name, double v, bool is_in
                        {"time_limit_s", &o.time_limit_s}, {"refine_tol", &o.refine_tol},
                        {"refine_fallback_tol", &o.refine_fallback_tol}};
     const I iopts[] = {{"max_iter", &o.max_iter}, {"path", &o.path}, {"max_ls", &o.max_ls},
-                       {"refine_max", &o.refine_max}, {"precision", &o.precision}, {"graphs", &o.graphs}};
+                       {"refine_max", &o.refine_max}, {"precision", &o.precision}, {"graphs", &o.graphs},
+                       {"autotune", &o.autotune}};
     if (is_int) {
         for (auto &e : iopts)
             if (name == e.n) { *e.p = (int64_t)v; return true; }

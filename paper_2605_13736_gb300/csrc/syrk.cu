@@ -171,12 +171,14 @@ struct Plan {
     int nsplit;
 };
 
-// Tile edge with the least executed work (ragged edge + diagonal tiles), then
-// the split count whose (tile, split) items fill whole waves of 2 CTAs per SM.
-Plan plan_for(int64_t m, int64_t n, int num_sms) {
+// Tile edge with the least executed work (ragged edge + diagonal tiles), or
+// bm_force (64 or 80) when given, then the split count whose (tile, split)
+// items fill whole waves of 2 CTAs per SM.
+Plan plan_for(int64_t m, int64_t n, int num_sms, int bm_force = 0) {
     Plan best{64, 0, 1};
     double best_work = 0;
     for (int bm : {64, 80}) {
+        if (bm_force && bm != bm_force) continue;
         const int64_t nt = (n + bm - 1) / bm;
         const int64_t T = nt * (nt + 1) / 2;
         const double work = (double)T * bm * bm;
@@ -203,18 +205,22 @@ Plan plan_for(int64_t m, int64_t n, int num_sms) {
 
 }  // namespace
 
+// enough for either tile edge
 size_t syrk_fp64_scratch_bytes(int64_t m, int64_t n, int num_sms) {
-    const Plan pl = plan_for(m, n, num_sms);
-    const size_t part = pl.nsplit > 1 ? (size_t)pl.nsplit * (size_t)n * (size_t)n * sizeof(double) : 0;
+    size_t part = 0;
+    for (int bm : {64, 80}) {
+        const Plan pl = plan_for(m, n, num_sms, bm);
+        if (pl.nsplit > 1) part = std::max(part, (size_t)pl.nsplit * (size_t)n * (size_t)n * sizeof(double));
+    }
     return part + ((size_t)std::max<int64_t>(m, 1) * sizeof(double) + 255) / 256 * 256;
 }
 
 // work: syrk_fp64_scratch_bytes(m, n, num_sms) bytes (split partials, then 1/w)
 void launch_syrk_fp64_ws(cudaStream_t st, int num_sms, const double *A, int64_t m, int64_t n,
                          int64_t lda, const double *w, double beta, double *C, int64_t ldc,
-                         double *work) {
+                         double *work, int bm) {
     if (n <= 0) return;
-    const Plan pl = plan_for(m, n, num_sms);
+    const Plan pl = plan_for(m, n, num_sms, bm == 64 || bm == 80 ? bm : 0);
     SyrkArgs a{};
     a.A = A;
     a.m = m;

@@ -122,3 +122,25 @@ def test_graph_replay_equals_separate_launches(prec):
             m.mdsip_ctx_destroy(ctx)
     np.testing.assert_array_equal(out[0][0], out[1][0])
     assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
+
+
+def test_autotuned_shapes_solve_to_the_same_optimum():
+    """Tile shapes chosen by the autotuner (panel width, product tile edge) give
+    the optimum of the analytic choices (a different rounding order only)."""
+    torch = torch_cuda()
+    m.build()
+    inst = synth.make_instance(150, 7500, 10, 0.02, seed=77)
+    res = []
+    stream = torch.cuda.Stream()
+    for tune in (0, 1):
+        ctx = m.mdsip_ctx_create(0, stream.cuda_stream)
+        p = make_problem(ctx, inst)
+        try:
+            m.mdsip_set_option_int(p, "autotune", tune, ctx)
+            assert m.mdsip_solve(p, ctx) == 0
+            res.append(m.mdsip_get_stats(p))
+        finally:
+            m.mdsip_problem_destroy(p)
+            m.mdsip_ctx_destroy(ctx)
+    assert all(r["E0"] <= 1e-8 for r in res)
+    assert abs(res[0]["f"] - res[1]["f"]) <= 1e-10 * max(1.0, abs(res[0]["f"]))
