@@ -68,6 +68,10 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=32,
                     help="instances of the batched measurement (0: skip); n_d ~ U{64..batch-max-nd}")
     ap.add_argument("--batch-max-nd", type=int, default=512)
+    ap.add_argument("--batch-concurrency", type=int, default=32,
+                    help="batched measurement: problems solved at once (host workers)")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the batched measurement and print its own JSON line")
     ap.add_argument("--ws-train", type=int, default=512,
                     help="learned warm start: training solves of the parametric family (0: skip)")
     ap.add_argument("--ws-eval", type=int, default=64, help="learned warm start: held-out members")
@@ -235,26 +239,30 @@ def run_batch(args, m, torch, local):
     import synth
     rng = np.random.default_rng(7)
     sizes = rng.integers(64, args.batch_max_nd + 1, size=args.batch_count)
-    insts = [synth.make_instance(int(nd), int(50 * nd), 50, 0.01, seed=1000 + i) for i, nd in enumerate(sizes)]
-    out = {"instances": len(insts), "n_d_range": [int(sizes.min()), int(sizes.max())],
-           "shape": "n_s = 100 n_d, m_E = 50 n_d, m_I = 50, a_i ~ N(0, 0.01^2), seeds 1000+i"}
-    streams = [torch.cuda.Stream(device=local) for _ in insts]
+    out = {"instances": len(sizes), "n_d_range": [int(sizes.min()), int(sizes.max())],
+           "shape": "n_s = 100 n_d, m_E = 50 n_d, m_I = 50, a_i ~ N(0, 0.01^2), seeds 1000+i",
+           "fp64_jacobian_gb": float(sum(50.0 * int(nd) * int(nd) * 8 for nd in sizes) / 1e9)}
+    streams = [torch.cuda.Stream(device=local) for _ in sizes]
     ctxs = [m.mdsip_ctx_create(local, st.cuda_stream) for st in streams]
-    probs = [m.mdsip_problem_create_synthetic(c, **m.synth_arrays(inst)) for c, inst in zip(ctxs, insts)]
+    probs = []
+    for i, (c, nd) in enumerate(zip(ctxs, sizes)):   # one host instance at a time
+        inst = synth.make_instance(int(nd), int(50 * nd), 50, 0.01, seed=1000 + i)
+        probs.append(m.mdsip_problem_create_synthetic(c, **m.synth_arrays(inst)))
+        del inst
     try:
         for name, prec in (("fp64", m.MDSIP_PREC_FP64), ("bf16", m.MDSIP_PREC_BF16)):
             for p in probs:
                 m.mdsip_set_option_int(p, "precision", prec)
             # one untimed pass over every instance: workspaces, autotuned shapes
             # (first use per shape) and captured factorization graphs
-            m.mdsip_batch_solve(probs)
+            m.mdsip_batch_solve(probs, args.batch_concurrency)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             seq = [m.mdsip_solve(p) for p in probs]
             t_seq = time.perf_counter() - t0
             iters = sum(m.mdsip_get_stats(p)["iters"] for p in probs)
             t0 = time.perf_counter()
-            bst = m.mdsip_batch_solve(probs)
+            bst = m.mdsip_batch_solve(probs, args.batch_concurrency)
             torch.cuda.synchronize()
             t_bat = time.perf_counter() - t0
             out[name] = {"sequential_solves_per_s": len(probs) / t_seq, "batched_solves_per_s": len(probs) / t_bat,
@@ -558,6 +566,24 @@ def run_ws_only(args):
                       "clocks": clk.summary(), "warm_start": ws}))
 
 
+def run_batch_only(args):
+    """The batched measurement alone, as its own JSON line (rank 0)."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import torch
+    import paper_2605_13736_gb300 as m
+    m.build()
+    torch.cuda.set_device(local)
+    with ClockSampler(local) as clk:
+        b = run_batch(args, m, torch, local)
+    print(json.dumps({"metric": "solves/s to 1e-8 KKT error, many independent instances (batched vs sequential)",
+                      "value": b["bf16"]["batched_solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+                      "higher_is_better": True, "dtype": "bf16+f64", "data": "synthetic",
+                      "config": {"workload": f"{b['instances']} instances, n_d in {b['n_d_range']}, " + b["shape"]},
+                      "clocks": clk.summary(), "batched": b}))
+
+
 def run_kernel(args):
     """Kernel-level timing: `--kernel syrk` (A^T diag(1/w) A, FP64, m x n) or
     `--kernel ldlt` (Bunch-Kaufman LDL^T of an N x N KKT-like matrix)."""
@@ -664,6 +690,8 @@ def main():
         run_reference(args)
     elif args.ws_only:
         run_ws_only(args)
+    elif args.batch_only:
+        run_batch_only(args)
     else:
         run_gpu(args)
 
