@@ -530,7 +530,7 @@ static void prepare_path(Problem *P) {
     MDSIP_REQUIRE(path != MDSIP_PATH_P2 || P->p2_ok, MDSIP_ERR_PRECONDITION,
                   "path P2 needs J_sg rows with disjoint column supports");
     const int64_t N = path == MDSIP_PATH_P2 ? D.n_d + D.m_I : D.n_d + D.m;
-    MDSIP_REQUIRE(2 * N * (int64_t)sizeof(double) <= 200 * 1024, MDSIP_ERR_INVALID_ARG,
+    MDSIP_REQUIRE(2 * N * (int64_t)sizeof(double) <= 200 * 1024 || ldlt_blocked_available(N), MDSIP_ERR_INVALID_ARG,
                   "reduced matrix too large for the dense factorization");
     if (path == P->path && N == P->N && P->bS.ptr) return;
     P->drop_graphs();   // the captured factorizations point at the old buffers
