@@ -87,6 +87,11 @@ def parse():
     ap.add_argument("--k", type=int, default=512, help="--kernel gemm_bf16: K")
     ap.add_argument("--fp32-update", action="store_true",
                     help="--kernel ldlt: the mixed-precision factorization (FP32 update products)")
+    ap.add_argument("--no-spec", action="store_true",
+                    help="--kernel ldlt --fp32-update: every panel pivots (no verified no-interchange panels)")
+    ap.add_argument("--ldlt-matrix", choices=["kkt", "ipm"], default="kkt",
+                    help="--kernel ldlt: kkt = [[H, J^T], [J, -I]] with J ~ N(0, 1) (pivots often); "
+                         "ipm = the P1 Newton-step shape of a convex problem (H + Sigma dominant, J small)")
     return ap.parse_args()
 
 
@@ -616,6 +621,7 @@ def run_kernel(args):
     ctx = m.mdsip_ctx_create(0, torch.cuda.current_stream().cuda_stream)
     rng = np.random.default_rng(0)
     times = []
+    panels = None
     try:
         if args.kernel == "syrk":
             mm, n = args.m, args.n
@@ -653,11 +659,14 @@ def run_kernel(args):
                 G = rng.standard_normal((k, k)) / np.sqrt(k)
                 H = 0.5 * (G + G.T) + 3.0 * np.eye(k)
             J = rng.standard_normal((N - k, k))
+            if args.ldlt_matrix == "ipm":
+                H = H + np.diag(rng.uniform(1.0, 3.0, k))
+                J *= 0.1
             K = np.zeros((N, N))
             K[:k, :k] = H
             K[k:, :k] = J
             K[:k, k:] = J.T
-            K[k:, k:] = -np.eye(N - k)
+            K[k:, k:] = -np.eye(N - k) if args.ldlt_matrix == "kkt" else -np.diag(rng.uniform(0.5, 2.0, N - k))
             S0 = torch.as_tensor(np.tril(K).T.copy()).cuda()
             S = torch.empty_like(S0)
             L = torch.empty((N, N), dtype=torch.float64, device="cuda")
@@ -669,6 +678,8 @@ def run_kernel(args):
             flops = N ** 3 / 3.0
 
             flags = m.MDSIP_LDLT_FP32_UPDATES if args.fp32_update else 0
+            if args.no_spec:
+                flags |= m.MDSIP_LDLT_NO_SPECULATION
 
             def call():
                 S.copy_(S0)
@@ -689,11 +700,15 @@ def run_kernel(args):
             torch.cuda.synchronize()
             if it >= args.warmup:
                 times.append(e0.elapsed_time(e1))
+        if args.kernel == "ldlt":
+            panels = m.mdsip_ldlt_panel_counts(ctx)
     finally:
         m.mdsip_ctx_destroy(ctx)
     ms = statistics.median(times)
     tf = flops / (ms / 1e3) / 1e12
     out = {"kernel": args.kernel, "m": args.m, "n": args.n, "ms_median": ms, "ms_all": times, "tflops": tf}
+    if panels is not None:
+        out["panels_no_interchange_kept_handed_back"] = panels
     if args.kernel in ("syrk", "ldlt", "ldlt_solve"):
         out["frac_fp64_peak"] = tf / FP64_PEAK_TFLOPS
     else:

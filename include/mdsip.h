@@ -167,7 +167,10 @@ void mdsip_problem_destroy(mdsip_problem *p);
  *           autotune (1, default: the blocked LDL^T's panel width and, for
  *           products below 4e10 multiply-adds, the FP64 product's tile edge
  *           are chosen by timing the candidates at first use per device and
- *           shape; 0: the analytic choices)
+ *           shape; 0: the analytic choices),
+ *           ldlt_spec (1, default: the mixed-precision factorization's
+ *           panels first try the verified no-interchange path described at
+ *           mdsip_ldlt_factor_ex; 0: every panel pivots)
  *   double: tol, mu0, kappa_eps, kappa_mu, theta_mu, tau_min, s_max, kappa_1,
  *           kappa_2, kappa_sigma, gamma_theta, gamma_phi, delta, s_theta, s_phi,
  *           eta_phi, gamma_alpha, dw0, dw_min, dw_max, kw_minus, kw_plus,
@@ -312,11 +315,26 @@ mdsip_status mdsip_ldlt_factor(mdsip_ctx *ctx, int64_t N, double *S, int64_t ld,
  * column updates and the trailing updates take FP32 products subtracted from
  * the FP64 matrix; pivot tests, D and the inertia stay FP64; the result is an
  * approximate factor meant for iterative refinement, and the unblocked kernel
- * used where thread-block clusters are unavailable ignores the flag). */
+ * used where thread-block clusters are unavailable ignores the flag), to
+ * which MDSIP_LDLT_NO_SPECULATION may be added.  Without it, each panel of
+ * the FP32-update factorization is first factored without interchanges and
+ * kept only if the Bunch-Kaufman rule (Section 2.3), evaluated on the
+ * computed columns, would have chosen a 1x1 pivot without interchange for
+ * every column of the panel (and no pivot is below zero_tol times the
+ * largest |S_ij|); otherwise the pivoting panel factors it from the
+ * unchanged matrix.  The flag makes every panel take the pivoting kernel. */
 #define MDSIP_LDLT_FP32_UPDATES 1
+#define MDSIP_LDLT_NO_SPECULATION 2
 mdsip_status mdsip_ldlt_factor_ex(mdsip_ctx *ctx, int64_t N, double *S, int64_t ld, double zero_tol,
                                   int32_t flags, double *L, double *Dd, double *Doff, int32_t *perm,
                                   int32_t *kind, int32_t *inertia);
+
+/* Panel counts of the last mdsip_ldlt_factor / mdsip_ldlt_factor_ex call on
+ * ctx (host array of 2): out2[0] = panels kept by the verified
+ * no-interchange path, out2[1] = panels it handed to the pivoting kernel.
+ * Both are 0 when that path did not run (FP64 updates, MDSIP_LDLT_NO_SPECULATION,
+ * or the unblocked kernel). */
+mdsip_status mdsip_ldlt_panel_counts(mdsip_ctx *ctx, int32_t *out2);
 
 /* Allocation-free variant of mdsip_ldlt_factor (same arguments, same
  * results).  The paper has no counterpart: this exists for callers that

@@ -124,6 +124,7 @@ _SIGS = {
     "mdsip_ldlt_factor_ex": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_double, C.c_int32,
                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p]),
+    "mdsip_ldlt_panel_counts": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mdsip_ldlt_factor_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_double,
                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                             C.c_void_p]),
@@ -349,11 +350,20 @@ def mdsip_ldlt_factor(ctx, N, S, ld, zero_tol, L, Dd, Doff, perm, kind, inertia)
 
 
 MDSIP_LDLT_FP32_UPDATES = 1
+MDSIP_LDLT_NO_SPECULATION = 2
 
 
 def mdsip_ldlt_factor_ex(ctx, N, S, ld, zero_tol, flags, L, Dd, Doff, perm, kind, inertia):
     _check(lib().mdsip_ldlt_factor_ex(ctx, N, _ptr(S), ld, float(zero_tol), int(flags), _ptr(L), _ptr(Dd),
                                       _ptr(Doff), _ptr(perm), _ptr(kind), _ptr(inertia)), ctx)
+
+
+def mdsip_ldlt_panel_counts(ctx):
+    """(panels kept by the no-interchange path, panels handed to the pivoting
+    kernel) of the last mdsip_ldlt_factor* call on ctx."""
+    out = (C.c_int32 * 2)()
+    _check(lib().mdsip_ldlt_panel_counts(ctx, out), ctx)
+    return int(out[0]), int(out[1])
 
 
 def mdsip_ldlt_factor_noalloc(ctx, N, S, ld, zero_tol, L, Dd, Doff, perm, kind, inertia):

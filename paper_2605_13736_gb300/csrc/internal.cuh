@@ -53,6 +53,7 @@ struct Ctx {
     bool has_hooks = false;
     int num_sms = 0;
     std::string last_error;
+    int32_t ldlt_panels[2] = {0, 0};   // of the last mdsip_ldlt_factor* call
     // grow-only scratch arena for kernel-level calls
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -143,6 +144,7 @@ struct Options {
     double time_limit_s = 0.0;
     int64_t graphs = 1;               // 1: replay the factorization phase as a CUDA graph
     int64_t autotune = 1;             // 1: time tile-shape candidates at first use per shape
+    int64_t ldlt_spec = 1;            // 1: mixed-precision LDL^T panels try the verified no-interchange path
 };
 
 // ---------------------------------------------------------------------------
@@ -333,16 +335,18 @@ void launch_syrk_tc(cudaStream_t s, int num_sms, int precision, const float *AfT
 struct LdltOut {
     double *L, *Dd, *Doff;
     int32_t *perm, *kind, *inertia;
+    int32_t *panels = nullptr;   // optional: panels taken by the no-interchange path, and handed back
 };
 size_t ldlt_scratch_bytes(int64_t N);
 void launch_ldlt(cudaStream_t s, int num_sms, int64_t N, const double *S, int64_t ld,
                  const double *maxabs_dev, double zero_tol, LdltOut out, void *scratch,
-                 int *err_dev, bool fp32_update = false, int nb = 0);
+                 int *err_dev, bool fp32_update = false, int nb = 0, bool spec = true);
 size_t ldlt_blocked_scratch_bytes(int64_t N);
 bool ldlt_blocked_available(int64_t N);
 std::vector<int> ldlt_blocked_widths(int64_t N, bool f32);
 void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, const double *maxabs_dev,
-                         double zero_tol, LdltOut out, void *scratch, bool fp32_update, int nb = 0);
+                         double zero_tol, LdltOut out, void *scratch, bool fp32_update, int nb = 0,
+                         bool spec = true);
 void launch_ldlt_solve(cudaStream_t s, int64_t N, const double *L, const double *Dd,
                        const double *Doff, const int32_t *perm, int64_t nrhs, double *B,
                        int64_t ldb);

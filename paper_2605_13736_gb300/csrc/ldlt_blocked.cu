@@ -48,7 +48,9 @@ struct PanelState {
     int k;       // first column of the next panel
     int kb;      // columns factored by the last panel
     int npos, nneg, nzero;
-    int pad[3];
+    int spec;    // 1: the last panel was taken by the verified no-interchange path
+    int nacc, nrej;   // panels that path accepted / handed to the pivoting panel
+    unsigned done;    // k_bk_spec CTAs done with the current panel (reset by the last)
 };
 
 struct Cand {                  // one CTA's candidate of a cluster-wide arg-max
@@ -65,6 +67,7 @@ struct PanelArgs {
     double *L, *Dd, *Doff;
     int32_t *perm, *kind;
     double *Wg;                // W of the last panel: N x (NB + 1), column-major, ld N
+    float *Lf, *Wf;            // F32: FP32 L and W columns of the last panel (N x (NB + 1), ld N)
     PanelState *st;
     const double *maxabs;
     double zero_tol;
@@ -193,6 +196,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_bk_panel(PanelArgs a) {
     __shared__ double s_sc[2];
     __shared__ int s_dec[3];
 
+    if (a.st->spec) return;                  // the panel was taken without interchanges
     const int k = a.st->k;
     if (k >= N) return;                      // uniform over the cluster
     const int rows = N - k;
@@ -488,7 +492,12 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_bk_panel(PanelArgs a) {
         if (t < kb) {
             if (i > k + t) a.L[i + (int64_t)(k + t) * N] = v;
             else if (i == k + t) a.L[i + (int64_t)i * N] = 1.0;
-            if (i >= k + kb) a.Wg[i + (int64_t)t * N] = Wp[(size_t)lr * S + t];
+            if constexpr (F32) {   // the FP32 trailing update reads FP32 copies
+                if (i > k + t) a.Lf[i + (int64_t)t * N] = Apf[(size_t)lr * S + t];
+                if (i >= k + kb) a.Wf[i + (int64_t)t * N] = (float)Wp[(size_t)lr * S + t];
+            } else {
+                if (i >= k + kb) a.Wg[i + (int64_t)t * N] = Wp[(size_t)lr * S + t];
+            }
         } else if (i >= k + t) {
             a.A[i + (int64_t)(k + t) * N] = v;
         }
@@ -509,6 +518,8 @@ template <typename T>
 __global__ void __launch_bounds__(kUpdThreads) k_bk_trailing(int N, int NB, double *__restrict__ A,
                                                              const double *__restrict__ L,
                                                              const double *__restrict__ Wg,
+                                                             const float *__restrict__ Lf,
+                                                             const float *__restrict__ Wf,
                                                              const PanelState *__restrict__ st) {
     extern __shared__ unsigned char usmem[];
     const int S = NB + 1;
@@ -528,8 +539,13 @@ __global__ void __launch_bounds__(kUpdThreads) k_bk_trailing(int N, int NB, doub
     for (int e = tid; e < kb * kUT; e += kUpdThreads) {
         const int t = e / kUT, r = e % kUT;
         const int i = i0 + r, c = c0 + r;
-        Lt[t * kUT + r] = (T)(i < N ? L[i + (int64_t)(k0 + t) * N] : 0.0);
-        Wt[t * kUT + r] = (T)(c < N ? Wg[c + (int64_t)t * N] : 0.0);
+        if constexpr (sizeof(T) == sizeof(float)) {   // the panel's FP32 copies
+            Lt[t * kUT + r] = i < N ? Lf[i + (int64_t)t * N] : 0.0f;
+            Wt[t * kUT + r] = c < N ? Wf[c + (int64_t)t * N] : 0.0f;
+        } else {
+            Lt[t * kUT + r] = (T)(i < N ? L[i + (int64_t)(k0 + t) * N] : 0.0);
+            Wt[t * kUT + r] = (T)(c < N ? Wg[c + (int64_t)t * N] : 0.0);
+        }
     }
     __syncthreads();
     const int tx = tid & 15, ty = tid >> 4;   // rows tx + 16 u, columns ty + 16 v
@@ -561,19 +577,272 @@ __global__ void __launch_bounds__(kUpdThreads) k_bk_trailing(int N, int NB, doub
     }
 }
 
+// ---------------------------------------------------------------------------
+// Verified no-interchange panel (refined mixed-precision path).
+//
+// On the Newton-step matrices of a convex problem the Bunch-Kaufman rule
+// almost always keeps the diagonal: the rule's choice at column j is a 1x1
+// pivot without interchange exactly when
+//     max(|a_jj|, colmax_j) = 0,  or  |a_jj| >= alpha colmax_j,  or
+//     |a_jj| >= alpha colmax_j (colmax_j / rowmax_r),
+// where colmax_j, r are the maximum and its row below the diagonal of the
+// column after j eliminations and rowmax_r the maximum off-diagonal entry of
+// row r of that active matrix.  If those decisions hold for every column of
+// a panel, the panel's Bunch-Kaufman factor is the factor without pivoting,
+// and that factor needs no cluster-wide arg-max per column: k_bk_spec
+// factors the panel without interchanges (all CTAs, each for a slice of the
+// rows, repeating the short pivot chain of the diagonal block), then its last
+// CTA evaluates the rule for every column from the computed values (column
+// maxima from the CTAs' candidates; the row maxima from row r recomputed with
+// the panel's earlier columns) and either accepts the panel or leaves it to
+// k_bk_panel, which then factors it with interchanges from the unchanged
+// matrix.  Decisions, D and the inertia stay FP64; the chain and the products
+// are FP32 as in the FP32-update panel.  A pivot with |d| <= zero_tol maxabs
+// also hands the panel over, so zero pivots keep the pivoting panel's rules.
+constexpr int kSpecThreads = 256;
+constexpr int kSpecRB = 32;   // rows below the diagonal block per CTA
+constexpr int kSpecP = 65;    // shared-memory row pitch (floats)
+
+struct ColCand {              // a CTA's maximum of one column
+    unsigned long long bits;
+    int idx;
+    int pad;
+};
+
+struct SpecArgs {
+    int N, NB;
+    const double *A;          // lower triangle, column-major, ld N (not written)
+    double *L, *Dd, *Doff;
+    int32_t *kind;
+    float *Lf, *Wf;           // FP32 L and W columns of the panel, ld N
+    ColCand *cand;            // [gridDim.x + 1][NB]: slot gridDim.x is the diagonal block's
+    PanelState *st;
+    const double *maxabs;
+    double zero_tol;
+};
+
+size_t spec_smem(int NB) {
+    return (size_t)3 * (NB + kSpecRB) * kSpecP * sizeof(float) + 2 * (size_t)NB * sizeof(double);
+}
+
+__global__ void __launch_bounds__(kSpecThreads) k_bk_spec(SpecArgs a) {
+    extern __shared__ double spsm[];
+    const int N = a.N, NB = a.NB, G = (int)gridDim.x, g = (int)blockIdx.x;
+    const int tid = threadIdx.x;
+    double *dd = spsm;                                      // NB: FP64 pivots
+    double *rr = dd + NB;                                   // NB: their reciprocals
+    float *Af = reinterpret_cast<float *>(rr + NB);         // rows x P: raw A, then the W columns
+    float *U = Af + (size_t)(NB + kSpecRB) * kSpecP;        // rows x P: sums of the panel's products
+    float *Ls = U + (size_t)(NB + kSpecRB) * kSpecP;        // rows x P: FP32 L columns
+    __shared__ int s_last;
+    const int k = a.st->k;
+    const int nb = min(NB, N - k);
+    const int rb0 = k + nb + g * kSpecRB;
+    const int nown = k < N ? max(0, min(N, rb0 + kSpecRB) - rb0) : 0;
+    const int nloc = nb + nown;
+    constexpr int P = kSpecP;
+    if (k < N && g > 0 && nown == 0) {           // no rows: empty candidates
+        for (int jj = tid; jj < nb; jj += kSpecThreads) a.cand[(size_t)g * NB + jj] = ColCand{0ULL, 0x7fffffff, 0};
+    } else if (k < N) {
+        // ---- load: the diagonal block (lower) and this CTA's rows below it
+        for (int e = tid; e < nloc * nb; e += kSpecThreads) {
+            const int c = e / nloc, i = e % nloc;            // rows fastest: coalesced columns
+            const int gi = i < nb ? k + i : rb0 + (i - nb);
+            Af[i * P + c] = (i >= nb || c <= i) ? (float)a.A[gi + (int64_t)(k + c) * N] : 0.0f;
+            U[i * P + c] = 0.0f;
+        }
+        __syncthreads();
+        // ---- the chain: column jj's working values sit in Af(:, jj) when step jj starts
+        const int tx = tid & 31, ty = tid >> 5;
+        for (int jj = 0; jj < nb; ++jj) {
+            const float rf = __frcp_rn(Af[jj * P + jj]);
+            const int c0 = jj + 1 + tx, c1 = c0 + 32;
+            const float w0 = c0 < nb ? Af[c0 * P + jj] : 0.0f;
+            const float w1 = c1 < nb ? Af[c1 * P + jj] : 0.0f;
+            for (int i = jj + 1 + ty; i < nloc; i += kSpecThreads / 32) {
+                const float lf = Af[i * P + jj] * rf;
+                const int cmax = i < nb ? i : nb - 1;
+                if (c0 <= cmax) {
+                    const float u = fmaf(lf, w0, U[i * P + c0]);
+                    U[i * P + c0] = u;
+                    if (tx == 0) {                            // c0 = jj + 1: column jj + 1 is final
+                        Af[i * P + c0] -= u;
+                        Ls[i * P + jj] = lf;
+                    }
+                } else if (tx == 0) {
+                    Ls[i * P + jj] = lf;
+                }
+                if (c1 <= cmax) U[i * P + c1] = fmaf(lf, w1, U[i * P + c1]);
+            }
+            __syncthreads();
+        }
+        // ---- FP64: pivots, reciprocals, W and L; column candidates
+        if (tid < nb) {
+            const double d = a.A[(k + tid) + (int64_t)(k + tid) * N] - (double)U[tid * P + tid];
+            dd[tid] = d;
+            rr[tid] = rcp_newton(d);
+        }
+        __syncthreads();
+        const int lane = tid & 31, wid = tid >> 5;
+        for (int jj = wid; jj < nb; jj += kSpecThreads / 32) {
+            unsigned long long b = 0;
+            int bi = 0x7fffffff;
+            if (lane < nown) {
+                const int li = nb + lane, i = rb0 + lane;
+                const double w = a.A[i + (int64_t)(k + jj) * N] - (double)U[li * P + jj];
+                a.L[i + (int64_t)(k + jj) * N] = w * rr[jj];
+                a.Lf[i + (int64_t)jj * N] = Ls[li * P + jj];
+                a.Wf[i + (int64_t)jj * N] = Af[li * P + jj];
+                b = absbits64(w);
+                bi = i;
+            }
+            warp_cand(b, bi);
+            if (lane == 0) a.cand[(size_t)g * NB + jj] = ColCand{b, bi, 0};
+            if (g == 0) {                                    // the diagonal block's rows
+                unsigned long long b2 = 0;
+                int bi2 = 0x7fffffff;
+                for (int li = jj + lane; li < nb; li += 32) {
+                    const int i = k + li;
+                    if (li == jj) {
+                        a.L[i + (int64_t)i * N] = 1.0;
+                        a.Dd[i] = dd[jj];
+                        a.Wf[i + (int64_t)jj * N] = Af[li * P + jj];
+                        continue;
+                    }
+                    const double w = a.A[i + (int64_t)(k + jj) * N] - (double)U[li * P + jj];
+                    a.L[i + (int64_t)(k + jj) * N] = w * rr[jj];
+                    a.Lf[i + (int64_t)jj * N] = Ls[li * P + jj];
+                    a.Wf[i + (int64_t)jj * N] = Af[li * P + jj];
+                    cand_combine(b2, bi2, absbits64(w), i);
+                }
+                warp_cand(b2, bi2);
+                if (lane == 0) a.cand[(size_t)G * NB + jj] = ColCand{b2, bi2, 0};
+            }
+        }
+    }
+    // ---- arrival; the last CTA decides
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(&a.st->done, 1u) == (unsigned)(G - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (k >= N) {
+        if (tid == 0) a.st->done = 0u;
+        return;
+    }
+    __shared__ unsigned long long s_cb[64];
+    __shared__ int s_ci[64];
+    __shared__ int s_fail[64];
+    __shared__ int s_reject;
+    __shared__ unsigned long long s_b[32];
+    __shared__ float s_wr[64];
+    const int lane = tid & 31, wid = tid >> 5;
+    const double alpha = 0.6403882032022076;   // (1 + sqrt 17) / 8
+    for (int jj = wid; jj < nb; jj += kSpecThreads / 32) {
+        unsigned long long b = 0;
+        int bi = 0x7fffffff;
+        for (int sl = lane; sl <= G; sl += 32) {
+            const ColCand *c = a.cand + (size_t)sl * NB + jj;
+            cand_combine(b, bi, __ldcg(&c->bits), __ldcg(&c->idx));
+        }
+        warp_cand(b, bi);
+        if (lane == 0) {
+            s_cb[jj] = b;
+            s_ci[jj] = bi;
+        }
+    }
+    if (tid == 0) s_reject = 0;
+    __syncthreads();
+    const double ztol = a.zero_tol * __ldg(a.maxabs);
+    if (tid < nb) {
+        const double d = __ldcg(&a.Dd[k + tid]);
+        const unsigned long long akb = absbits64(d), cb = s_cb[tid];
+        const double colmax = __longlong_as_double((long long)cb);
+        const bool plain = (akb == 0ULL && cb == 0ULL) || akb >= absbits64(alpha * colmax);
+        s_fail[tid] = plain ? 0 : 1;
+        // zero pivots, and values that are not finite, go to the pivoting panel
+        if (d == 0.0 || fabs(d) <= ztol || !isfinite(d) || !isfinite(colmax)) atomicOr(&s_reject, 1);
+    }
+    __syncthreads();
+    for (int jj = 0; jj < nb && !s_reject; ++jj) {
+        if (!s_fail[jj]) continue;
+        const int j = k + jj, r = s_ci[jj];
+        if (r <= j || r >= N) {           // no valid row: leave the panel to the pivoting kernel
+            if (tid == 0) s_reject = 1;
+            break;
+        }
+        if (tid < jj) s_wr[tid] = __ldcg(&a.Wf[r + (int64_t)tid * N]);
+        __syncthreads();
+        unsigned long long b = 0;   // row r's maximum off the diagonal (bit pattern)
+        for (int c = j + tid; c < N; c += kSpecThreads) {
+            if (c == r) continue;
+            float sf = 0.0f;
+            for (int t = 0; t < jj; ++t) sf = fmaf(__ldcg(&a.Lf[c + (int64_t)t * N]), s_wr[t], sf);
+            const double asym = c < r ? a.A[r + (int64_t)c * N] : a.A[c + (int64_t)r * N];
+            const unsigned long long vb = absbits64(asym - (double)sf);
+            b = vb > b ? vb : b;
+        }
+        {
+            const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(b >> 32));
+            const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(b >> 32) == hi ? (unsigned)b : 0u);
+            if (lane == 0) s_b[wid] = ((unsigned long long)hi << 32) | lo;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long rb = 0;
+            for (int w = 0; w < kSpecThreads / 32; ++w) rb = rb > s_b[w] ? rb : s_b[w];
+            const double absakk = fabs(__ldcg(&a.Dd[j]));
+            const double colmax = __longlong_as_double((long long)s_cb[jj]);
+            const double rowmax = __longlong_as_double((long long)rb);
+            if (!(absakk >= alpha * colmax * (colmax / rowmax))) s_reject = 1;
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    if (!s_reject) {
+        int pos = 0;
+        if (tid < nb) {
+            a.kind[k + tid] = 1;
+            a.Doff[k + tid] = 0.0;
+            pos = __ldcg(&a.Dd[k + tid]) > 0.0 ? 1 : 0;
+        }
+        const int np = __syncthreads_count(pos);
+        if (tid == 0) {
+            a.st->npos += np;
+            a.st->nneg += nb - np;
+            a.st->k = k + nb;
+            a.st->kb = nb;
+            a.st->spec = 1;
+            a.st->nacc += 1;
+        }
+    } else if (tid == 0) {
+        a.st->spec = 0;
+        a.st->nrej += 1;
+    }
+    if (tid == 0) a.st->done = 0u;
+}
+
 __global__ void k_bk_init(int N, int32_t *perm, PanelState *st) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) perm[i] = i;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->k = 0;
         st->kb = 0;
         st->npos = st->nneg = st->nzero = 0;
+        st->spec = 0;
+        st->nacc = st->nrej = 0;
+        st->done = 0u;
     }
 }
 
-__global__ void k_bk_finish(const PanelState *st, int32_t *inertia) {
+__global__ void k_bk_finish(const PanelState *st, int32_t *inertia, int32_t *panels) {
     inertia[0] = st->npos;
     inertia[1] = st->nneg;
     inertia[2] = st->nzero;
+    if (panels) {
+        panels[0] = st->nacc;
+        panels[1] = st->nrej;
+    }
 }
 
 struct BlockedConfig {
@@ -643,12 +912,30 @@ BlockedConfig blocked_config(int64_t N, bool f32, int nb_want = 0) {
     return c;
 }
 
+// scratch layout: W of the last panel (N x 65 doubles), the panel state, the
+// FP32 L and W columns of the last panel (N x 65 floats each; FP32-update
+// form) and the column candidates of the verified no-interchange panels
+// ((ceil(N / 32) + 2) x 64)
+struct BlockedScratch {
+    size_t wg, st, lf, wf, cand, total;
+};
+
+BlockedScratch blocked_scratch(int64_t N) {
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t n = (size_t)std::max<int64_t>(N, 1);
+    BlockedScratch l{};
+    l.wg = 0;
+    l.st = up(n * 65 * sizeof(double));
+    l.lf = l.st + 256;
+    l.wf = l.lf + up(n * 65 * sizeof(float));
+    l.cand = l.wf + up(n * 65 * sizeof(float));
+    l.total = l.cand + up(((n + kSpecRB - 1) / kSpecRB + 2) * 64 * sizeof(ColCand));
+    return l;
+}
+
 }  // namespace
 
-// scratch use: W of the last panel (N x 65 doubles) and the panel state
-size_t ldlt_blocked_scratch_bytes(int64_t N) {
-    return ((size_t)std::max<int64_t>(N, 1) * 65 * sizeof(double) + 255) / 256 * 256 + 256;
-}
+size_t ldlt_blocked_scratch_bytes(int64_t N) { return blocked_scratch(N).total; }
 
 // panel widths that fit for order N (widest first)
 std::vector<int> ldlt_blocked_widths(int64_t N, bool f32) {
@@ -661,9 +948,10 @@ std::vector<int> ldlt_blocked_widths(int64_t N, bool f32) {
 bool ldlt_blocked_available(int64_t N) { return blocked_config(N, true).C > 0 && blocked_config(N, false).C > 0; }
 
 // S (lower, ld N) is overwritten.  scratch: ldlt_blocked_scratch_bytes(N),
-// 256-byte aligned.  fp32_update: trailing products in FP32.
+// 256-byte aligned.  fp32_update: trailing products in FP32.  spec (with
+// fp32_update): each panel first tries the verified no-interchange path.
 void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, const double *maxabs_dev,
-                         double zero_tol, LdltOut out, void *scratch, bool fp32_update, int nb) {
+                         double zero_tol, LdltOut out, void *scratch, bool fp32_update, int nb, bool spec) {
     if (N <= 0) {
         MDSIP_CUDA(cudaMemsetAsync(out.inertia, 0, 3 * sizeof(int32_t), s));
         return;
@@ -673,8 +961,9 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
     MDSIP_REQUIRE(cfg.C > 0, MDSIP_ERR_INVALID_ARG, "ldlt: N too large for the blocked factorization");
     char *w = static_cast<char *>(scratch);
     MDSIP_REQUIRE((reinterpret_cast<uintptr_t>(w) & 255) == 0, MDSIP_ERR_INVALID_ARG, "ldlt: misaligned scratch");
-    double *Wg = reinterpret_cast<double *>(w);
-    PanelState *st = reinterpret_cast<PanelState *>(w + ((size_t)N * 65 * sizeof(double) + 255) / 256 * 256);
+    const BlockedScratch lay = blocked_scratch(N);
+    double *Wg = reinterpret_cast<double *>(w + lay.wg);
+    PanelState *st = reinterpret_cast<PanelState *>(w + lay.st);
     k_bk_init<<<std::max(1, std::min(1024, ceil_div(N, 256))), 256, 0, s>>>((int)N, out.perm, st);
     MDSIP_LAUNCHED();
 
@@ -690,6 +979,8 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
     a.perm = out.perm;
     a.kind = out.kind;
     a.Wg = Wg;
+    a.Lf = reinterpret_cast<float *>(w + lay.lf);
+    a.Wf = reinterpret_cast<float *>(w + lay.wf);
     a.st = st;
     a.maxabs = maxabs_dev;
     a.zero_tol = zero_tol;
@@ -717,8 +1008,36 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
                                      (int)(2 * 65 * kUT * sizeof(float)));
         return e;
     }));
+    spec = spec && fp32_update;
+    SpecArgs sa{};
+    if (spec) {
+        sa.N = (int)N;
+        sa.NB = cfg.NB;
+        sa.A = S;
+        sa.L = out.L;
+        sa.Dd = out.Dd;
+        sa.Doff = out.Doff;
+        sa.kind = out.kind;
+        sa.Lf = a.Lf;
+        sa.Wf = a.Wf;
+        sa.cand = reinterpret_cast<ColCand *>(w + lay.cand);
+        sa.st = st;
+        sa.maxabs = maxabs_dev;
+        sa.zero_tol = zero_tol;
+        static PerDeviceOnce once_spec;
+        MDSIP_CUDA(once_spec.run([] {
+            return cudaFuncSetAttribute(k_bk_spec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spec_smem(64));
+        }));
+    }
     const int npanels = (int)((N + cfg.NB - 1) / cfg.NB);
     for (int p = 0; p < npanels; ++p) {
+        if (spec) {
+            // rows below the diagonal block: at most N - (p + 1) NB (every panel takes >= NB columns)
+            const int64_t below = N - (int64_t)(p + 1) * cfg.NB;
+            const int G = (int)std::max<int64_t>(1, (below + kSpecRB - 1) / kSpecRB);
+            k_bk_spec<<<G, kSpecThreads, spec_smem(cfg.NB), s>>>(sa);
+            MDSIP_LAUNCHED();
+        }
         if (fp32_update)
             MDSIP_CUDA(cudaLaunchKernelEx(&lc, k_bk_panel<true>, a));
         else
@@ -730,12 +1049,12 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
         const int64_t nt = (rest + kUT - 1) / kUT;
         const unsigned tiles = (unsigned)(nt * (nt + 1) / 2);
         if (fp32_update)
-            k_bk_trailing<float><<<tiles, kUpdThreads, usm, s>>>((int)N, cfg.NB, S, out.L, Wg, st);
+            k_bk_trailing<float><<<tiles, kUpdThreads, usm, s>>>((int)N, cfg.NB, S, out.L, Wg, a.Lf, a.Wf, st);
         else
-            k_bk_trailing<double><<<tiles, kUpdThreads, usm, s>>>((int)N, cfg.NB, S, out.L, Wg, st);
+            k_bk_trailing<double><<<tiles, kUpdThreads, usm, s>>>((int)N, cfg.NB, S, out.L, Wg, a.Lf, a.Wf, st);
         MDSIP_LAUNCHED();
     }
-    k_bk_finish<<<1, 1, 0, s>>>(st, out.inertia);
+    k_bk_finish<<<1, 1, 0, s>>>(st, out.inertia, out.panels);
     MDSIP_LAUNCHED();
 }
 

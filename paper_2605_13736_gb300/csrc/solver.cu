@@ -737,7 +737,7 @@ static int tuned_ldlt_width(Problem *P, bool fp32) {
             LdltOut o{P->bL.as<double>(), P->bDd.as<double>(), P->bDoff.as<double>(), P->bperm.as<int32_t>(),
                       P->bkind.as<int32_t>(), P->binertia.as<int32_t>()};
             launch_ldlt(st, P->ctx->num_sms, N, S, N, sc + SC_MAXABS, P->opt.zero_tol, o, P->bldlt_ws.ptr,
-                        P->berr.as<int>(), fp32, nb);
+                        P->berr.as<int>(), fp32, nb, P->opt.ldlt_spec != 0);
         });
         MDSIP_CUDA(cudaMemcpyAsync(S, Ssave, (size_t)N * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
         MDSIP_CUDA(cudaStreamSynchronize(st));
@@ -793,7 +793,7 @@ static Inertia factor_attempt(Problem *P, double dw, double dc, bool force_fp64 
         LdltOut o{P->bL.as<double>(), P->bDd.as<double>(), P->bDoff.as<double>(), P->bperm.as<int32_t>(),
                   P->bkind.as<int32_t>(), P->binertia.as<int32_t>()};
         launch_ldlt(st, P->ctx->num_sms, P->N, S, P->N, sc + SC_MAXABS, P->opt.zero_tol, o, P->bldlt_ws.ptr,
-                    P->berr.as<int>(), tc_factor, nb);
+                    P->berr.as<int>(), tc_factor, nb, P->opt.ldlt_spec != 0);
         launch_ldlt_solve_prepare(st, P->N, P->bL.as<double>(), P->bsolve_ws.ptr, P->solve_fp32);
     };
     run_factor_phase(P, tc_factor ? 1 : 0, factor_phase);
@@ -1288,7 +1288,7 @@ static bool set_option(Options &o, const std::string &name, double v, bool is_in
                        {"refine_fallback_tol", &o.refine_fallback_tol}};
     const I iopts[] = {{"max_iter", &o.max_iter}, {"path", &o.path}, {"max_ls", &o.max_ls},
                        {"refine_max", &o.refine_max}, {"precision", &o.precision}, {"graphs", &o.graphs},
-                       {"autotune", &o.autotune}};
+                       {"autotune", &o.autotune}, {"ldlt_spec", &o.ldlt_spec}};
     if (is_int) {
         for (auto &e : iopts)
             if (name == e.n) { *e.p = (int64_t)v; return true; }
@@ -1434,6 +1434,7 @@ mdsip_status mdsip_set_option_int(mdsip_problem *hp, const char *name, int64_t v
     return guarded(p->ctx, [&] {
         MDSIP_REQUIRE(set_option(p->opt, name, (double)value, true), MDSIP_ERR_INVALID_ARG,
                       std::string("unknown int option ") + name);
+        if (std::string(name) == "ldlt_spec") p->drop_graphs();   // captured factorizations use the old choice
         MDSIP_REQUIRE(p->opt.path >= 0 && p->opt.path <= 2, MDSIP_ERR_INVALID_ARG, "bad path");
         MDSIP_REQUIRE(p->opt.precision >= 0 && p->opt.precision <= 2, MDSIP_ERR_INVALID_ARG, "bad precision");
     });
@@ -1666,7 +1667,7 @@ mdsip_status mdsip_syrk_scaled_tc(mdsip_ctx *hctx, int64_t m, int64_t n, const d
 
 static mdsip_status ldlt_factor_impl(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld, double zero_tol,
                                      double *L, double *Dd, double *Doff, int32_t *perm, int32_t *kind,
-                                     int32_t *inertia, bool fp32_update);
+                                     int32_t *inertia, bool fp32_update, bool spec = true);
 
 mdsip_status mdsip_ldlt_factor(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld, double zero_tol,
                                double *L, double *Dd, double *Doff, int32_t *perm, int32_t *kind,
@@ -1677,17 +1678,17 @@ mdsip_status mdsip_ldlt_factor(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld
 mdsip_status mdsip_ldlt_factor_ex(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld, double zero_tol,
                                   int32_t flags, double *L, double *Dd, double *Doff, int32_t *perm,
                                   int32_t *kind, int32_t *inertia) {
-    if (flags & ~MDSIP_LDLT_FP32_UPDATES) {
+    if (flags & ~(MDSIP_LDLT_FP32_UPDATES | MDSIP_LDLT_NO_SPECULATION)) {
         if (hctx) C_(hctx)->last_error = "ldlt: unknown flags";
         return MDSIP_ERR_INVALID_ARG;
     }
     return ldlt_factor_impl(hctx, N, S, ld, zero_tol, L, Dd, Doff, perm, kind, inertia,
-                            (flags & MDSIP_LDLT_FP32_UPDATES) != 0);
+                            (flags & MDSIP_LDLT_FP32_UPDATES) != 0, (flags & MDSIP_LDLT_NO_SPECULATION) == 0);
 }
 
 static mdsip_status ldlt_factor_impl(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld, double zero_tol,
                                      double *L, double *Dd, double *Doff, int32_t *perm, int32_t *kind,
-                                     int32_t *inertia, bool fp32_update) {
+                                     int32_t *inertia, bool fp32_update, bool spec) {
     if (!hctx) return MDSIP_ERR_INVALID_ARG;
     Ctx *ctx = C_(hctx);
     return guarded(ctx, [&] {
@@ -1703,18 +1704,27 @@ static mdsip_status ldlt_factor_impl(mdsip_ctx *hctx, int64_t N, double *S, int6
         char *w = static_cast<char *>(ctx->scratch_at_least(ws));
         double *partial = reinterpret_cast<double *>(w + ldlt_scratch_bytes(N) + 64);
         double *maxabs = partial + kRedBlocks;
-        int *err = reinterpret_cast<int *>(w + ldlt_scratch_bytes(N));
+        int *err = reinterpret_cast<int *>(w + ldlt_scratch_bytes(N));   // err, then two panel counts
         MDSIP_REQUIRE((reinterpret_cast<uintptr_t>(partial) & 7) == 0, MDSIP_ERR_INVALID_ARG,
                       "ldlt: misaligned scratch layout");
-        MDSIP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+        MDSIP_CUDA(cudaMemsetAsync(err, 0, 3 * sizeof(int), ctx->stream));
         launch_maxabs_lower(ctx->stream, N, S, ld, partial, maxabs);
-        LdltOut o{L, Dd, Doff, perm, kind, inertia};
-        launch_ldlt(ctx->stream, ctx->num_sms, N, S, ld, maxabs, zero_tol, o, w, err, fp32_update);
-        int herr = 0;
-        MDSIP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        LdltOut o{L, Dd, Doff, perm, kind, inertia, err + 1};
+        launch_ldlt(ctx->stream, ctx->num_sms, N, S, ld, maxabs, zero_tol, o, w, err, fp32_update, 0, spec);
+        int herr[3] = {0, 0, 0};
+        MDSIP_CUDA(cudaMemcpyAsync(herr, err, 3 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
         MDSIP_CUDA(cudaStreamSynchronize(ctx->stream));
-        MDSIP_REQUIRE(herr == 0, MDSIP_ERR_DEVICE, "ldlt: a bounded device wait expired");
+        ctx->ldlt_panels[0] = herr[1];
+        ctx->ldlt_panels[1] = herr[2];
+        MDSIP_REQUIRE(herr[0] == 0, MDSIP_ERR_DEVICE, "ldlt: a bounded device wait expired");
     });
+}
+
+mdsip_status mdsip_ldlt_panel_counts(mdsip_ctx *hctx, int32_t *out2) {
+    if (!hctx || !out2) return MDSIP_ERR_INVALID_ARG;
+    out2[0] = C_(hctx)->ldlt_panels[0];
+    out2[1] = C_(hctx)->ldlt_panels[1];
+    return MDSIP_OK;
 }
 
 mdsip_status mdsip_ldlt_factor_noalloc(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld,

@@ -201,6 +201,11 @@ __global__ void k_scale_rows(int64_t n, int64_t ldt, const float *__restrict__ A
 }
 
 // C[p][q] = beta C[p][q] + sum_split work[split][tile(p,q)][q % 128][p % 128]   (p >= q)
+// The split partials are FP32 tensor-core sums; they are added in FP32 (their
+// own rounding, 2^-24 per addition, is far below the operands' BF16/TF32
+// rounding) and the total enters the FP64 matrix with one conversion and one
+// FP64 addition per entry: GB300 runs FP64 adds and conversions at 1/64 of the
+// FP32 rate, which made an all-FP64 sum of ~20 partials the kernel's cost.
 __global__ void k_tc_reduce(int64_t n, int tiles, int nsplit, const float *__restrict__ work, double beta,
                             double *__restrict__ C, int64_t ldc) {
     for (int64_t q = blockIdx.x; q < n; q += gridDim.x) {
@@ -209,10 +214,17 @@ __global__ void k_tc_reduce(int64_t n, int tiles, int nsplit, const float *__res
             const int tp = (int)(p / TC_TILE);
             const int t = tp * (tp + 1) / 2 + tq;
             const size_t off = (size_t)(q % TC_TILE) * TC_TILE + (size_t)(p % TC_TILE);
-            double s = 0.0;
-            for (int k = 0; k < nsplit; ++k) s += (double)work[((size_t)k * tiles + t) * (TC_TILE * TC_TILE) + off];
+            const size_t stride = (size_t)tiles * (TC_TILE * TC_TILE);
+            const float *w = work + (size_t)t * (TC_TILE * TC_TILE) + off;
+            float s0 = 0.0f, s1 = 0.0f;
+            int k = 0;
+            for (; k + 1 < nsplit; k += 2) {
+                s0 += w[(size_t)k * stride];
+                s1 += w[(size_t)(k + 1) * stride];
+            }
+            if (k < nsplit) s0 += w[(size_t)k * stride];
             double *c = C + p + q * ldc;
-            *c = (beta != 0.0 ? *c : 0.0) + s;
+            *c = (beta != 0.0 ? *c : 0.0) + (double)(s0 + s1);
         }
     }
 }

@@ -227,13 +227,18 @@ def test_direction_parity_tensor_core_refined(ctx, case, prec):
     assert np.linalg.norm(out - ref) / np.linalg.norm(ref) <= 1e-10
 
 
+@pytest.mark.parametrize("spec", [1, 0])
 @pytest.mark.parametrize("prec", TC_PRECS)
-def test_tensor_core_solve_matches_oracle_trajectory(ctx, prec):
+def test_tensor_core_solve_matches_oracle_trajectory(ctx, prec, spec):
+    """The refined tensor-core solve, with (spec = 1, the default) and without
+    the verified no-interchange panels of the FP32-update factorization: the
+    oracle's iteration count, objective and inertia-correction sequence."""
     g = _golden("mds0_full")
     inst = _inst_for(g["case"])
     prob = make_problem(ctx, inst, m.MDSIP_PATH_P2)
     try:
         m.mdsip_set_option_int(prob, "precision", prec, ctx)
+        m.mdsip_set_option_int(prob, "ldlt_spec", spec, ctx)
         st = m.mdsip_solve(prob, ctx)
         stats = m.mdsip_get_stats(prob)
         log = m.mdsip_get_log(prob)

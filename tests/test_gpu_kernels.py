@@ -160,7 +160,108 @@ def test_ldlt_fp32_updates(ctx, N, kind):
     R = K[np.ix_(p, p)] - Lh @ D @ Lh.T
     assert np.abs(R).max() <= 1e-4 * np.abs(K).max()
     with pytest.raises(m.MdsipError):
-        m.mdsip_ldlt_factor_ex(ctx, N, S, N, 1e-14, 2, L, Dd, Doff, perm, kd, inr)
+        m.mdsip_ldlt_factor_ex(ctx, N, S, N, 1e-14, 4, L, Dd, Doff, perm, kd, inr)
+
+
+def _ipm_like(rng, nd, mi):
+    """A Newton-step matrix of the P1 form [[H + Sigma, J^T], [J, -D]]: H + Sigma
+    positive definite and diagonally dominant, J small, D > 0 (the shape of
+    the condensed systems of a convex problem at a usual iterate)."""
+    g = rng.standard_normal((nd, nd)) / np.sqrt(nd)
+    h = g @ g.T + np.diag(rng.uniform(1.0, 3.0, nd))
+    j = 0.1 * rng.standard_normal((mi, nd))
+    out = np.zeros((nd + mi, nd + mi))
+    out[:nd, :nd] = h
+    out[nd:, :nd] = j
+    out[:nd, nd:] = j.T
+    out[nd:, nd:] = -np.diag(rng.uniform(0.5, 2.0, mi))
+    return out
+
+
+def _row_test_matrix(n, second):
+    """Diagonal 10 with, for every 7th column j < n - 60, a_jj = 1, a_rj = 2 in
+    a late row r, and a_rc = `second` in column c = j + 1, a_rr = 100.  At
+    column j the Bunch-Kaufman column test fails (1 < alpha 2); the row test
+    keeps the 1x1 pivot without interchange when second = 3 (rowmax 3) and
+    interchanges j and r when second = 2.1 (rowmax 2.1)."""
+    K = 10.0 * np.eye(n)
+    r = n - 1
+    for j in range(0, n - 60, 7):
+        K[j, j] = 1.0
+        K[r, j] = K[j, r] = 2.0
+        K[r, j + 1] = K[j + 1, r] = second
+        K[r, r] = 100.0
+        r -= 1
+    return K
+
+
+def _fp32_ldlt(ctx, K, flags):
+    torch = torch_cuda()
+    N = K.shape[0]
+    S = dev(np.asfortranarray(np.tril(K)).T.copy())
+    L = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+    Dd = torch.zeros(N, dtype=torch.float64, device="cuda")
+    Doff = torch.zeros(N, dtype=torch.float64, device="cuda")
+    perm = torch.zeros(N, dtype=torch.int32, device="cuda")
+    kd = torch.zeros(N, dtype=torch.int32, device="cuda")
+    inr = torch.zeros(3, dtype=torch.int32, device="cuda")
+    m.mdsip_ldlt_factor_ex(ctx, N, S, N, 1e-14, flags, L, Dd, Doff, perm, kd, inr)
+    torch.cuda.synchronize()
+    out = dict(L=np.tril(L.cpu().numpy().T), Dd=Dd.cpu().numpy(), Doff=Doff.cpu().numpy(),
+               perm=perm.cpu().numpy(), kind=kd.cpu().numpy(),
+               inertia=tuple(int(v) for v in inr.cpu().numpy()), panels=m.mdsip_ldlt_panel_counts(ctx))
+    D = np.diag(out["Dd"]) + np.diag(out["Doff"][:-1], -1) + np.diag(out["Doff"][:-1], 1)
+    p = out["perm"]
+    out["resid"] = np.abs(K[np.ix_(p, p)] - out["L"] @ D @ out["L"].T).max() / np.abs(K).max()
+    return out
+
+
+@pytest.mark.parametrize("N,kind", [(2050, "ipm"), (700, "row_keep"), (700, "row_swap"), (2100, "saddle"),
+                                    (1500, "mixed"), (64, "ipm"), (65, "ipm"), (1, "ipm")])
+def test_ldlt_fp32_speculation(ctx, N, kind):
+    """The mixed-precision factorization with the verified no-interchange
+    panels against the same factorization with every panel pivoting and
+    against the oracle's Bunch-Kaufman: the same inertia, 1x1/2x2 pattern and
+    permutation (the matrices keep every pivot decision far from its
+    threshold), D within FP32 accuracy, the reconstruction at FP32 accuracy,
+    and the panel counts show which path took the panels."""
+    rng = np.random.default_rng(N * 7 + len(kind))
+    if kind == "ipm":
+        K = _ipm_like(rng, N - min(50, N // 3), min(50, N // 3))
+    elif kind == "row_keep":
+        K = _row_test_matrix(N, 3.0)
+    elif kind == "row_swap":
+        K = _row_test_matrix(N, 2.1)
+    elif kind == "mixed":     # a convex block, then a block that pivots
+        K = np.zeros((N, N))
+        K[:900, :900] = _ipm_like(rng, 860, 40)
+        K[900:, 900:] = _sym(rng, N - 900, "saddle")
+    else:
+        K = _sym(rng, N, kind)
+    spec = _fp32_ldlt(ctx, K, m.MDSIP_LDLT_FP32_UPDATES)
+    piv = _fp32_ldlt(ctx, K, m.MDSIP_LDLT_FP32_UPDATES | m.MDSIP_LDLT_NO_SPECULATION)
+    assert piv["panels"] == (0, 0)
+    o = bk_ldlt(K)
+    # FP32 products: a reconstruction error of a few 2^-24 times the growth of
+    # the factors, which interchanges on the saddle matrices make larger
+    tol = 1e-4 if kind in ("saddle", "mixed") else 1e-5
+    for g in (spec, piv):
+        assert g["inertia"] == o["inertia"]
+        if kind != "saddle":   # a random saddle matrix has near-ties in its pivot tests
+            np.testing.assert_array_equal(g["kind"], o["kind"])
+            np.testing.assert_array_equal(g["perm"], o["perm"])
+        assert g["resid"] <= tol, (spec["resid"], piv["resid"])
+    if kind != "saddle":   # (the saddle block's late pivots carry the growth of its interchanges)
+        nd = 900 if kind == "mixed" else N
+        np.testing.assert_allclose(spec["Dd"][:nd], np.diag(o["D"])[:nd], rtol=1e-4, atol=1e-5 * np.abs(K).max())
+    acc, rej = spec["panels"]
+    if kind in ("ipm", "row_keep"):
+        assert acc >= 1 and rej == 0
+        np.testing.assert_array_equal(spec["perm"], np.arange(N))
+    elif kind == "row_swap":
+        assert rej >= 1
+    elif kind == "mixed":
+        assert acc >= 1 and rej >= 1
 
 
 def test_ldlt_singular_and_edge_cases(ctx):
