@@ -51,6 +51,8 @@ struct PanelState {
     int spec;    // 1: the last panel was taken by the verified no-interchange path
     int nacc, nrej;   // panels that path accepted / handed to the pivoting panel
     unsigned done;    // k_bk_spec CTAs done with the current panel (reset by the last)
+    int nfail;        // columns of the pending panel whose row test k_bk_spec_rows evaluates
+    unsigned done2;   // k_bk_spec_rows CTAs done (reset by the last)
 };
 
 struct Cand {                  // one CTA's candidate of a cluster-wide arg-max
@@ -592,10 +594,11 @@ __global__ void __launch_bounds__(kUpdThreads) k_bk_trailing(int N, int NB, doub
 // and that factor needs no cluster-wide arg-max per column: k_bk_spec
 // factors the panel without interchanges (all CTAs, each for a slice of the
 // rows, repeating the short pivot chain of the diagonal block), then its last
-// CTA evaluates the rule for every column from the computed values (column
-// maxima from the CTAs' candidates; the row maxima from row r recomputed with
-// the panel's earlier columns) and either accepts the panel or leaves it to
-// k_bk_panel, which then factors it with interchanges from the unchanged
+// CTA applies the column test to every column (column maxima from the CTAs'
+// candidates).  Columns that fail it go to k_bk_spec_rows, which recomputes
+// row r of the active matrix from the stored matrix and the panel's earlier
+// columns on all SMs and applies the row test.  A panel that passes is kept;
+// otherwise k_bk_panel factors it with interchanges from the unchanged
 // matrix.  Decisions, D and the inertia stay FP64; the chain and the products
 // are FP32 as in the FP32-update panel.  A pivot with |d| <= zero_tol maxabs
 // also hands the panel over, so zero pivots keep the pivoting panel's rules.
@@ -609,6 +612,11 @@ struct ColCand {              // a CTA's maximum of one column
     int pad;
 };
 
+struct RowTest {               // a column that needs the rule's row test
+    int jj, r;                 // column (in the panel) and the row of its column maximum
+    double colmax, absakk;
+};
+
 struct SpecArgs {
     int N, NB;
     const double *A;          // lower triangle, column-major, ld N (not written)
@@ -616,69 +624,130 @@ struct SpecArgs {
     int32_t *kind;
     float *Lf, *Wf;           // FP32 L and W columns of the panel, ld N
     ColCand *cand;            // [gridDim.x + 1][NB]: slot gridDim.x is the diagonal block's
+    RowTest *fail;            // [NB]: the columns whose row test is pending
+    unsigned long long *rowpart;   // [CTAs of k_bk_spec_rows][NB]: partial row maxima (bit patterns)
     PanelState *st;
     const double *maxabs;
     double zero_tol;
 };
 
 size_t spec_smem(int NB) {
-    return (size_t)3 * (NB + kSpecRB) * kSpecP * sizeof(float) + 2 * (size_t)NB * sizeof(double);
+    return 2 * (size_t)NB * sizeof(double) + (size_t)(NB + kSpecRB) * kSpecP * sizeof(double) +
+           (size_t)3 * (NB + kSpecRB) * kSpecP * sizeof(float);
 }
 
-__global__ void __launch_bounds__(kSpecThreads) k_bk_spec(SpecArgs a) {
+// Keep the panel (all threads of the block): 1x1 pivots without interchange,
+// inertia from the signs of D, the next panel starts after it.
+__device__ void spec_accept(const SpecArgs &a, int k, int nb) {
+    int pos = 0;
+    if ((int)threadIdx.x < nb) {
+        a.kind[k + threadIdx.x] = 1;
+        a.Doff[k + threadIdx.x] = 0.0;
+        pos = __ldcg(&a.Dd[k + threadIdx.x]) > 0.0 ? 1 : 0;
+    }
+    const int np = __syncthreads_count(pos);
+    if (threadIdx.x == 0) {
+        a.st->npos += np;
+        a.st->nneg += nb - np;
+        a.st->k = k + nb;
+        a.st->kb = nb;
+        a.st->spec = 1;
+        a.st->nacc += 1;
+    }
+}
+
+__global__ void __launch_bounds__(kSpecThreads, 1) k_bk_spec(SpecArgs a) {
     extern __shared__ double spsm[];
     const int N = a.N, NB = a.NB, G = (int)gridDim.x, g = (int)blockIdx.x;
     const int tid = threadIdx.x;
+    constexpr int P = kSpecP;
     double *dd = spsm;                                      // NB: FP64 pivots
     double *rr = dd + NB;                                   // NB: their reciprocals
-    float *Af = reinterpret_cast<float *>(rr + NB);         // rows x P: raw A, then the W columns
-    float *U = Af + (size_t)(NB + kSpecRB) * kSpecP;        // rows x P: sums of the panel's products
-    float *Ls = U + (size_t)(NB + kSpecRB) * kSpecP;        // rows x P: FP32 L columns
+    double *Ad = rr + NB;                                   // rows x P: the raw values (FP64)
+    float *Wsh = reinterpret_cast<float *>(Ad + (size_t)(NB + kSpecRB) * P);   // rows x P: W columns (FP32)
+    float *U = Wsh + (size_t)(NB + kSpecRB) * P;            // rows x P: sums of the panel's products
+    float *Ls = U + (size_t)(NB + kSpecRB) * P;             // rows x P: FP32 L columns
     __shared__ int s_last;
     const int k = a.st->k;
     const int nb = min(NB, N - k);
     const int rb0 = k + nb + g * kSpecRB;
     const int nown = k < N ? max(0, min(N, rb0 + kSpecRB) - rb0) : 0;
     const int nloc = nb + nown;
-    constexpr int P = kSpecP;
     if (k < N && g > 0 && nown == 0) {           // no rows: empty candidates
         for (int jj = tid; jj < nb; jj += kSpecThreads) a.cand[(size_t)g * NB + jj] = ColCand{0ULL, 0x7fffffff, 0};
     } else if (k < N) {
-        // ---- load: the diagonal block (lower) and this CTA's rows below it
-        for (int e = tid; e < nloc * nb; e += kSpecThreads) {
-            const int c = e / nloc, i = e % nloc;            // rows fastest: coalesced columns
+        // Local rows 0..nb-1: the diagonal block; nb..nloc-1: this CTA's rows
+        // below it.  Thread (tr, tc) keeps the entries (tr + 16 x, tc + 16 y),
+        // x < 6, y < 4, in registers: their raw value and the running sum of
+        // the panel's products (right-looking, one barrier per column).
+        const int tr = tid & 15, tc = tid >> 4;
+        float ar[6][4], u[6][4];
+#pragma unroll
+        for (int x = 0; x < 6; ++x) {
+            const int i = tr + 16 * x;
             const int gi = i < nb ? k + i : rb0 + (i - nb);
-            Af[i * P + c] = (i >= nb || c <= i) ? (float)a.A[gi + (int64_t)(k + c) * N] : 0.0f;
-            U[i * P + c] = 0.0f;
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+                const int c = tc + 16 * y;
+                const bool valid = i < nloc && c < nb && (i >= nb || c <= i);
+                const double v = valid ? a.A[gi + (int64_t)(k + c) * N] : 0.0;
+                ar[x][y] = (float)v;
+                u[x][y] = 0.0f;
+                if (valid) {
+                    Ad[i * P + c] = v;
+                    if (c == 0) Wsh[i * P] = (float)v;   // column 0's working values
+                }
+            }
         }
         __syncthreads();
-        // ---- the chain: column jj's working values sit in Af(:, jj) when step jj starts
-        const int tx = tid & 31, ty = tid >> 5;
         for (int jj = 0; jj < nb; ++jj) {
-            const float rf = __frcp_rn(Af[jj * P + jj]);
-            const int c0 = jj + 1 + tx, c1 = c0 + 32;
-            const float w0 = c0 < nb ? Af[c0 * P + jj] : 0.0f;
-            const float w1 = c1 < nb ? Af[c1 * P + jj] : 0.0f;
-            for (int i = jj + 1 + ty; i < nloc; i += kSpecThreads / 32) {
-                const float lf = Af[i * P + jj] * rf;
-                const int cmax = i < nb ? i : nb - 1;
-                if (c0 <= cmax) {
-                    const float u = fmaf(lf, w0, U[i * P + c0]);
-                    U[i * P + c0] = u;
-                    if (tx == 0) {                            // c0 = jj + 1: column jj + 1 is final
-                        Af[i * P + c0] -= u;
-                        Ls[i * P + jj] = lf;
-                    }
-                } else if (tx == 0) {
-                    Ls[i * P + jj] = lf;
+            const float rf = __frcp_rn(Wsh[jj * P + jj]);
+            float lf[6], wc[4];
+#pragma unroll
+            for (int x = 0; x < 6; ++x) {
+                const int i = tr + 16 * x;
+                lf[x] = (i > jj && i < nloc) ? Wsh[i * P + jj] * rf : 0.0f;
+            }
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+                const int c = tc + 16 * y;
+                wc[y] = (c > jj && c < nb) ? Wsh[c * P + jj] : 0.0f;
+            }
+            if (tc == 0) {
+#pragma unroll
+                for (int x = 0; x < 6; ++x) {
+                    const int i = tr + 16 * x;
+                    if (i > jj && i < nloc) Ls[i * P + jj] = lf[x];
                 }
-                if (c1 <= cmax) U[i * P + c1] = fmaf(lf, w1, U[i * P + c1]);
+            }
+#pragma unroll
+            for (int x = 0; x < 6; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) u[x][y] = fmaf(lf[x], wc[y], u[x][y]);
+            // the owners of column jj + 1 publish its working values
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+                if (tc + 16 * y == jj + 1) {
+#pragma unroll
+                    for (int x = 0; x < 6; ++x) {
+                        const int i = tr + 16 * x;
+                        if (i > jj && i < nloc) Wsh[i * P + jj + 1] = ar[x][y] - u[x][y];
+                    }
+                }
             }
             __syncthreads();
         }
+#pragma unroll
+        for (int x = 0; x < 6; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+                const int i = tr + 16 * x, c = tc + 16 * y;
+                if (i < nloc && c < nb && (i >= nb || c <= i)) U[i * P + c] = u[x][y];
+            }
+        __syncthreads();
         // ---- FP64: pivots, reciprocals, W and L; column candidates
         if (tid < nb) {
-            const double d = a.A[(k + tid) + (int64_t)(k + tid) * N] - (double)U[tid * P + tid];
+            const double d = Ad[tid * P + tid] - (double)U[tid * P + tid];
             dd[tid] = d;
             rr[tid] = rcp_newton(d);
         }
@@ -689,10 +758,10 @@ __global__ void __launch_bounds__(kSpecThreads) k_bk_spec(SpecArgs a) {
             int bi = 0x7fffffff;
             if (lane < nown) {
                 const int li = nb + lane, i = rb0 + lane;
-                const double w = a.A[i + (int64_t)(k + jj) * N] - (double)U[li * P + jj];
+                const double w = Ad[li * P + jj] - (double)U[li * P + jj];
                 a.L[i + (int64_t)(k + jj) * N] = w * rr[jj];
                 a.Lf[i + (int64_t)jj * N] = Ls[li * P + jj];
-                a.Wf[i + (int64_t)jj * N] = Af[li * P + jj];
+                a.Wf[i + (int64_t)jj * N] = Wsh[li * P + jj];
                 b = absbits64(w);
                 bi = i;
             }
@@ -706,13 +775,13 @@ __global__ void __launch_bounds__(kSpecThreads) k_bk_spec(SpecArgs a) {
                     if (li == jj) {
                         a.L[i + (int64_t)i * N] = 1.0;
                         a.Dd[i] = dd[jj];
-                        a.Wf[i + (int64_t)jj * N] = Af[li * P + jj];
+                        a.Wf[i + (int64_t)jj * N] = Wsh[li * P + jj];
                         continue;
                     }
-                    const double w = a.A[i + (int64_t)(k + jj) * N] - (double)U[li * P + jj];
+                    const double w = Ad[li * P + jj] - (double)U[li * P + jj];
                     a.L[i + (int64_t)(k + jj) * N] = w * rr[jj];
                     a.Lf[i + (int64_t)jj * N] = Ls[li * P + jj];
-                    a.Wf[i + (int64_t)jj * N] = Af[li * P + jj];
+                    a.Wf[i + (int64_t)jj * N] = Wsh[li * P + jj];
                     cand_combine(b2, bi2, absbits64(w), i);
                 }
                 warp_cand(b2, bi2);
@@ -735,21 +804,34 @@ __global__ void __launch_bounds__(kSpecThreads) k_bk_spec(SpecArgs a) {
     __shared__ int s_ci[64];
     __shared__ int s_fail[64];
     __shared__ int s_reject;
-    __shared__ unsigned long long s_b[32];
-    __shared__ float s_wr[64];
     const int lane = tid & 31, wid = tid >> 5;
     const double alpha = 0.6403882032022076;   // (1 + sqrt 17) / 8
-    for (int jj = wid; jj < nb; jj += kSpecThreads / 32) {
-        unsigned long long b = 0;
-        int bi = 0x7fffffff;
-        for (int sl = lane; sl <= G; sl += 32) {
-            const ColCand *c = a.cand + (size_t)sl * NB + jj;
-            cand_combine(b, bi, __ldcg(&c->bits), __ldcg(&c->idx));
+    {   // column maxima: warp w combines columns w, w + 8, ... (loads of all its columns in flight)
+        unsigned long long cb[8];
+        int ci[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            cb[m] = 0ULL;
+            ci[m] = 0x7fffffff;
         }
-        warp_cand(b, bi);
-        if (lane == 0) {
-            s_cb[jj] = b;
-            s_ci[jj] = bi;
+        for (int sl = lane; sl <= G; sl += 32) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int jj = wid + 8 * m;
+                if (jj < nb) {
+                    const ColCand *c = a.cand + (size_t)sl * NB + jj;
+                    cand_combine(cb[m], ci[m], __ldcg(&c->bits), __ldcg(&c->idx));
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            warp_cand(cb[m], ci[m]);
+            const int jj = wid + 8 * m;
+            if (lane == 0 && jj < nb) {
+                s_cb[jj] = cb[m];
+                s_ci[jj] = ci[m];
+            }
         }
     }
     if (tid == 0) s_reject = 0;
@@ -765,62 +847,115 @@ __global__ void __launch_bounds__(kSpecThreads) k_bk_spec(SpecArgs a) {
         if (d == 0.0 || fabs(d) <= ztol || !isfinite(d) || !isfinite(colmax)) atomicOr(&s_reject, 1);
     }
     __syncthreads();
-    for (int jj = 0; jj < nb && !s_reject; ++jj) {
-        if (!s_fail[jj]) continue;
-        const int j = k + jj, r = s_ci[jj];
-        if (r <= j || r >= N) {           // no valid row: leave the panel to the pivoting kernel
-            if (tid == 0) s_reject = 1;
-            break;
+    // columns that need the row test: listed for k_bk_spec_rows
+    __shared__ int s_nf;
+    int nf = 0;
+    if (tid == 0) s_nf = 0;
+    if (tid == 0 && !s_reject) {
+        for (int jj = 0; jj < nb; ++jj) {
+            if (!s_fail[jj]) continue;
+            const int r = s_ci[jj];
+            if (r <= k + jj || r >= N) {   // no valid row: leave the panel to the pivoting kernel
+                s_reject = 1;
+                break;
+            }
+            a.fail[nf] = RowTest{jj, r, __longlong_as_double((long long)s_cb[jj]), fabs(__ldcg(&a.Dd[k + jj]))};
+            ++nf;
         }
-        if (tid < jj) s_wr[tid] = __ldcg(&a.Wf[r + (int64_t)tid * N]);
-        __syncthreads();
-        unsigned long long b = 0;   // row r's maximum off the diagonal (bit pattern)
-        for (int c = j + tid; c < N; c += kSpecThreads) {
-            if (c == r) continue;
-            float sf = 0.0f;
-            for (int t = 0; t < jj; ++t) sf = fmaf(__ldcg(&a.Lf[c + (int64_t)t * N]), s_wr[t], sf);
-            const double asym = c < r ? a.A[r + (int64_t)c * N] : a.A[c + (int64_t)r * N];
-            const unsigned long long vb = absbits64(asym - (double)sf);
-            b = vb > b ? vb : b;
-        }
-        {
-            const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(b >> 32));
-            const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(b >> 32) == hi ? (unsigned)b : 0u);
-            if (lane == 0) s_b[wid] = ((unsigned long long)hi << 32) | lo;
-        }
-        __syncthreads();
+        a.st->nfail = s_reject ? 0 : nf;
+        s_nf = nf;
+    }
+    __syncthreads();
+    nf = s_nf;
+    if (s_reject) {
         if (tid == 0) {
-            unsigned long long rb = 0;
-            for (int w = 0; w < kSpecThreads / 32; ++w) rb = rb > s_b[w] ? rb : s_b[w];
-            const double absakk = fabs(__ldcg(&a.Dd[j]));
-            const double colmax = __longlong_as_double((long long)s_cb[jj]);
-            const double rowmax = __longlong_as_double((long long)rb);
-            if (!(absakk >= alpha * colmax * (colmax / rowmax))) s_reject = 1;
+            a.st->spec = 0;
+            a.st->nrej += 1;
+            a.st->nfail = 0;
         }
-        __syncthreads();
+    } else if (nf == 0) {
+        spec_accept(a, k, nb);
+    } else if (tid == 0) {
+        a.st->spec = 0;   // decided by k_bk_spec_rows
+    }
+    if (tid == 0) a.st->done = 0u;
+}
+
+// The row tests of the listed columns: rowmax_r = max over c >= j, c != r of
+// |S(c, r) - sum_{t < jj} L(c, k + t) W(r, t)| (the active matrix's row r
+// after j eliminations, FP32 products as in the panel), partial maxima per CTA
+// over 32 rows c (one per lane; warp w takes the listed columns w, w + 8, ...),
+// then the last CTA applies the rule and keeps or hands over the panel.
+__global__ void __launch_bounds__(kSpecThreads) k_bk_spec_rows(SpecArgs a) {
+    __shared__ float s_w[64 * 64];
+    __shared__ RowTest s_t[64];
+    __shared__ int s_last, s_reject;
+    const int nf = a.st->nfail;
+    if (nf == 0) return;                       // uniform: nothing pending
+    const int N = a.N, NB = a.NB, k = a.st->k, nb = min(NB, N - k);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int G = (int)gridDim.x, g = (int)blockIdx.x;
+    for (int f = tid; f < nf; f += kSpecThreads) s_t[f] = a.fail[f];
+    __syncthreads();
+    for (int e = tid; e < nf * 64; e += kSpecThreads) {
+        const int f = e >> 6, t = e & 63;
+        s_w[e] = t < s_t[f].jj ? __ldcg(&a.Wf[s_t[f].r + (int64_t)t * N]) : 0.0f;
+    }
+    const int c = k + g * 32 + lane;
+    float lf[64];
+#pragma unroll
+    for (int t = 0; t < 64; ++t) lf[t] = (c < N && t < nb) ? __ldcg(&a.Lf[c + (int64_t)t * N]) : 0.0f;
+    __syncthreads();
+    for (int f = wid; f < nf; f += kSpecThreads / 32) {
+        const RowTest rt = s_t[f];
+        const float *wr = s_w + f * 64;
+        unsigned long long b = 0;
+        if (c < N && c >= k + rt.jj && c != rt.r) {
+            float sf = 0.0f;
+#pragma unroll
+            for (int t = 0; t < 64; ++t)
+                if (t < rt.jj) sf = fmaf(lf[t], wr[t], sf);
+            const double asym = c < rt.r ? a.A[rt.r + (int64_t)c * N] : a.A[c + (int64_t)rt.r * N];
+            b = absbits64(asym - (double)sf);
+        }
+        const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(b >> 32));
+        const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(b >> 32) == hi ? (unsigned)b : 0u);
+        if (lane == 0) a.rowpart[(size_t)g * NB + f] = ((unsigned long long)hi << 32) | lo;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(&a.st->done2, 1u) == (unsigned)(G - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (tid == 0) s_reject = 0;
+    __syncthreads();
+    const double alpha = 0.6403882032022076;   // (1 + sqrt 17) / 8
+    for (int f = wid; f < nf; f += kSpecThreads / 32) {
+        unsigned long long b = 0;
+        for (int q = lane; q < G; q += 32) {
+            const unsigned long long v = __ldcg(&a.rowpart[(size_t)q * NB + f]);
+            b = v > b ? v : b;
+        }
+        const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(b >> 32));
+        const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(b >> 32) == hi ? (unsigned)b : 0u);
+        if (lane == 0) {
+            const double rowmax = __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+            const RowTest rt = s_t[f];
+            if (!(rt.absakk >= alpha * rt.colmax * (rt.colmax / rowmax))) atomicOr(&s_reject, 1);
+        }
     }
     __syncthreads();
     if (!s_reject) {
-        int pos = 0;
-        if (tid < nb) {
-            a.kind[k + tid] = 1;
-            a.Doff[k + tid] = 0.0;
-            pos = __ldcg(&a.Dd[k + tid]) > 0.0 ? 1 : 0;
-        }
-        const int np = __syncthreads_count(pos);
-        if (tid == 0) {
-            a.st->npos += np;
-            a.st->nneg += nb - np;
-            a.st->k = k + nb;
-            a.st->kb = nb;
-            a.st->spec = 1;
-            a.st->nacc += 1;
-        }
+        spec_accept(a, k, nb);
     } else if (tid == 0) {
         a.st->spec = 0;
         a.st->nrej += 1;
     }
-    if (tid == 0) a.st->done = 0u;
+    if (tid == 0) {
+        a.st->nfail = 0;
+        a.st->done2 = 0u;
+    }
 }
 
 __global__ void k_bk_init(int N, int32_t *perm, PanelState *st) {
@@ -832,6 +967,8 @@ __global__ void k_bk_init(int N, int32_t *perm, PanelState *st) {
         st->spec = 0;
         st->nacc = st->nrej = 0;
         st->done = 0u;
+        st->nfail = 0;
+        st->done2 = 0u;
     }
 }
 
@@ -914,10 +1051,11 @@ BlockedConfig blocked_config(int64_t N, bool f32, int nb_want = 0) {
 
 // scratch layout: W of the last panel (N x 65 doubles), the panel state, the
 // FP32 L and W columns of the last panel (N x 65 floats each; FP32-update
-// form) and the column candidates of the verified no-interchange panels
-// ((ceil(N / 32) + 2) x 64)
+// form), and for the verified no-interchange panels the column candidates
+// ((ceil(N / 32) + 2) x 64), the pending row tests (64) and their partial
+// row maxima ((ceil(N / 32) + 2) x 64)
 struct BlockedScratch {
-    size_t wg, st, lf, wf, cand, total;
+    size_t wg, st, lf, wf, cand, fail, rowpart, total;
 };
 
 BlockedScratch blocked_scratch(int64_t N) {
@@ -929,7 +1067,9 @@ BlockedScratch blocked_scratch(int64_t N) {
     l.lf = l.st + 256;
     l.wf = l.lf + up(n * 65 * sizeof(float));
     l.cand = l.wf + up(n * 65 * sizeof(float));
-    l.total = l.cand + up(((n + kSpecRB - 1) / kSpecRB + 2) * 64 * sizeof(ColCand));
+    l.fail = l.cand + up(((n + kSpecRB - 1) / kSpecRB + 2) * 64 * sizeof(ColCand));
+    l.rowpart = l.fail + up(64 * sizeof(RowTest));
+    l.total = l.rowpart + up(((n + 31) / 32 + 2) * 64 * sizeof(unsigned long long));
     return l;
 }
 
@@ -1021,6 +1161,8 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
         sa.Lf = a.Lf;
         sa.Wf = a.Wf;
         sa.cand = reinterpret_cast<ColCand *>(w + lay.cand);
+        sa.fail = reinterpret_cast<RowTest *>(w + lay.fail);
+        sa.rowpart = reinterpret_cast<unsigned long long *>(w + lay.rowpart);
         sa.st = st;
         sa.maxabs = maxabs_dev;
         sa.zero_tol = zero_tol;
@@ -1036,6 +1178,10 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
             const int64_t below = N - (int64_t)(p + 1) * cfg.NB;
             const int G = (int)std::max<int64_t>(1, (below + kSpecRB - 1) / kSpecRB);
             k_bk_spec<<<G, kSpecThreads, spec_smem(cfg.NB), s>>>(sa);
+            MDSIP_LAUNCHED();
+            // rows of the active matrix: at most N - p NB
+            const int G2 = (int)std::max<int64_t>(1, (N - (int64_t)p * cfg.NB + 31) / 32);
+            k_bk_spec_rows<<<G2, kSpecThreads, 0, s>>>(sa);
             MDSIP_LAUNCHED();
         }
         if (fp32_update)
