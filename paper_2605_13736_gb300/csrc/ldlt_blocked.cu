@@ -594,8 +594,9 @@ __global__ void __launch_bounds__(kUpdThreads) k_bk_trailing(int N, int NB, doub
 // and that factor needs no cluster-wide arg-max per column: k_bk_spec
 // factors the panel without interchanges (all CTAs, each for a slice of the
 // rows, repeating the short pivot chain of the diagonal block), then its last
-// CTA applies the column test to every column (column maxima from the CTAs'
-// candidates).  Columns that fail it go to k_bk_spec_rows, which recomputes
+// CTA applies the column test to every column (the column maxima gathered by
+// atomicMax; the arg-max row is the first among the entries whose |w| agree
+// to 28 mantissa bits).  Columns that fail it go to k_bk_spec_rows, which recomputes
 // row r of the active matrix from the stored matrix and the panel's earlier
 // columns on all SMs and applies the row test.  A panel that passes is kept;
 // otherwise k_bk_panel factors it with interchanges from the unchanged
@@ -605,12 +606,6 @@ __global__ void __launch_bounds__(kUpdThreads) k_bk_trailing(int N, int NB, doub
 constexpr int kSpecThreads = 256;
 constexpr int kSpecRB = 32;   // rows below the diagonal block per CTA
 constexpr int kSpecP = 65;    // shared-memory row pitch (floats)
-
-struct ColCand {              // a CTA's maximum of one column
-    unsigned long long bits;
-    int idx;
-    int pad;
-};
 
 struct RowTest {               // a column that needs the rule's row test
     int jj, r;                 // column (in the panel) and the row of its column maximum
@@ -623,7 +618,7 @@ struct SpecArgs {
     double *L, *Dd, *Doff;
     int32_t *kind;
     float *Lf, *Wf;           // FP32 L and W columns of the panel, ld N
-    ColCand *cand;            // [gridDim.x + 1][NB]: slot gridDim.x is the diagonal block's
+    unsigned long long *cmax; // [2][64]: per column the maximum |w| (bits) and the arg-max key
     RowTest *fail;            // [NB]: the columns whose row test is pending
     unsigned long long *rowpart;   // [CTAs of k_bk_spec_rows][NB]: partial row maxima (bit patterns)
     PanelState *st;
@@ -667,15 +662,14 @@ __global__ void __launch_bounds__(kSpecThreads, 1) k_bk_spec(SpecArgs a) {
     float *Wsh = reinterpret_cast<float *>(Ad + (size_t)(NB + kSpecRB) * P);   // rows x P: W columns (FP32)
     float *U = Wsh + (size_t)(NB + kSpecRB) * P;            // rows x P: sums of the panel's products
     float *Ls = U + (size_t)(NB + kSpecRB) * P;             // rows x P: FP32 L columns
+    __shared__ float s_rf[64];                              // FP32 reciprocals of the chain's pivots
     __shared__ int s_last;
     const int k = a.st->k;
     const int nb = min(NB, N - k);
     const int rb0 = k + nb + g * kSpecRB;
     const int nown = k < N ? max(0, min(N, rb0 + kSpecRB) - rb0) : 0;
     const int nloc = nb + nown;
-    if (k < N && g > 0 && nown == 0) {           // no rows: empty candidates
-        for (int jj = tid; jj < nb; jj += kSpecThreads) a.cand[(size_t)g * NB + jj] = ColCand{0ULL, 0x7fffffff, 0};
-    } else if (k < N) {
+    if (k < N && (g == 0 || nown > 0)) {        // CTAs beyond the last row have no work
         // Local rows 0..nb-1: the diagonal block; nb..nloc-1: this CTA's rows
         // below it.  Thread (tr, tc) keeps the entries (tr + 16 x, tc + 16 y),
         // x < 6, y < 4, in registers: their raw value and the running sum of
@@ -696,12 +690,13 @@ __global__ void __launch_bounds__(kSpecThreads, 1) k_bk_spec(SpecArgs a) {
                 if (valid) {
                     Ad[i * P + c] = v;
                     if (c == 0) Wsh[i * P] = (float)v;   // column 0's working values
+                    if (i == 0 && c == 0) s_rf[0] = __frcp_rn((float)v);
                 }
             }
         }
         __syncthreads();
         for (int jj = 0; jj < nb; ++jj) {
-            const float rf = __frcp_rn(Wsh[jj * P + jj]);
+            const float rf = s_rf[jj];
             float lf[6], wc[4];
 #pragma unroll
             for (int x = 0; x < 6; ++x) {
@@ -731,7 +726,11 @@ __global__ void __launch_bounds__(kSpecThreads, 1) k_bk_spec(SpecArgs a) {
 #pragma unroll
                     for (int x = 0; x < 6; ++x) {
                         const int i = tr + 16 * x;
-                        if (i > jj && i < nloc) Wsh[i * P + jj + 1] = ar[x][y] - u[x][y];
+                        if (i > jj && i < nloc) {
+                            const float v = ar[x][y] - u[x][y];
+                            Wsh[i * P + jj + 1] = v;
+                            if (i == jj + 1) s_rf[jj + 1] = __frcp_rn(v);   // the next pivot's reciprocal
+                        }
                     }
                 }
             }
@@ -753,6 +752,18 @@ __global__ void __launch_bounds__(kSpecThreads, 1) k_bk_spec(SpecArgs a) {
         }
         __syncthreads();
         const int lane = tid & 31, wid = tid >> 5;
+        const int below = max(0, N - k - nb);
+        const int Gw = max(1, (below + kSpecRB - 1) / kSpecRB);   // CTAs with rows (CTA 0 always)
+        // the column maxima of this CTA's rows, and of the diagonal block's
+        // rows for the columns jj = g, g + Gw, ..., go to the per-column
+        // maxima by atomicMax: the exact |w| bits, and a key whose high bits
+        // are |w| truncated to 28 mantissa bits and whose low 24 bits are the
+        // complemented row (the arg-max, first row among maxima equal to 2^-28)
+        auto put_max = [&](int jj, unsigned long long b, int bi) {
+            if (b == 0ULL) return;
+            atomicMax(&a.cmax[jj], b);
+            atomicMax(&a.cmax[64 + jj], ((b >> 24) << 24) | (unsigned long long)(0xFFFFFFu - (unsigned)bi));
+        };
         for (int jj = wid; jj < nb; jj += kSpecThreads / 32) {
             unsigned long long b = 0;
             int bi = 0x7fffffff;
@@ -766,27 +777,29 @@ __global__ void __launch_bounds__(kSpecThreads, 1) k_bk_spec(SpecArgs a) {
                 bi = i;
             }
             warp_cand(b, bi);
-            if (lane == 0) a.cand[(size_t)g * NB + jj] = ColCand{b, bi, 0};
-            if (g == 0) {                                    // the diagonal block's rows
-                unsigned long long b2 = 0;
-                int bi2 = 0x7fffffff;
-                for (int li = jj + lane; li < nb; li += 32) {
-                    const int i = k + li;
-                    if (li == jj) {
-                        a.L[i + (int64_t)i * N] = 1.0;
-                        a.Dd[i] = dd[jj];
-                        a.Wf[i + (int64_t)jj * N] = Wsh[li * P + jj];
-                        continue;
-                    }
-                    const double w = Ad[li * P + jj] - (double)U[li * P + jj];
-                    a.L[i + (int64_t)(k + jj) * N] = w * rr[jj];
-                    a.Lf[i + (int64_t)jj * N] = Ls[li * P + jj];
+            if (lane == 0) put_max(jj, b, bi);
+        }
+        for (int q = wid;; q += kSpecThreads / 32) {        // the diagonal block's columns
+            const int jj = g + q * Gw;
+            if (jj >= nb) break;
+            unsigned long long b2 = 0;
+            int bi2 = 0x7fffffff;
+            for (int li = jj + lane; li < nb; li += 32) {
+                const int i = k + li;
+                if (li == jj) {
+                    a.L[i + (int64_t)i * N] = 1.0;
+                    a.Dd[i] = dd[jj];
                     a.Wf[i + (int64_t)jj * N] = Wsh[li * P + jj];
-                    cand_combine(b2, bi2, absbits64(w), i);
+                    continue;
                 }
-                warp_cand(b2, bi2);
-                if (lane == 0) a.cand[(size_t)G * NB + jj] = ColCand{b2, bi2, 0};
+                const double w = Ad[li * P + jj] - (double)U[li * P + jj];
+                a.L[i + (int64_t)(k + jj) * N] = w * rr[jj];
+                a.Lf[i + (int64_t)jj * N] = Ls[li * P + jj];
+                a.Wf[i + (int64_t)jj * N] = Wsh[li * P + jj];
+                cand_combine(b2, bi2, absbits64(w), i);
             }
+            warp_cand(b2, bi2);
+            if (lane == 0) put_max(jj, b2, bi2);
         }
     }
     // ---- arrival; the last CTA decides
@@ -800,73 +813,48 @@ __global__ void __launch_bounds__(kSpecThreads, 1) k_bk_spec(SpecArgs a) {
         if (tid == 0) a.st->done = 0u;
         return;
     }
-    __shared__ unsigned long long s_cb[64];
-    __shared__ int s_ci[64];
-    __shared__ int s_fail[64];
-    __shared__ int s_reject;
-    const int lane = tid & 31, wid = tid >> 5;
+    __shared__ int s_reject, s_nf, s_cnt0;
+    const int lane = tid & 31;
     const double alpha = 0.6403882032022076;   // (1 + sqrt 17) / 8
-    {   // column maxima: warp w combines columns w, w + 8, ... (loads of all its columns in flight)
-        unsigned long long cb[8];
-        int ci[8];
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            cb[m] = 0ULL;
-            ci[m] = 0x7fffffff;
-        }
-        for (int sl = lane; sl <= G; sl += 32) {
-#pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                const int jj = wid + 8 * m;
-                if (jj < nb) {
-                    const ColCand *c = a.cand + (size_t)sl * NB + jj;
-                    cand_combine(cb[m], ci[m], __ldcg(&c->bits), __ldcg(&c->idx));
-                }
-            }
-        }
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            warp_cand(cb[m], ci[m]);
-            const int jj = wid + 8 * m;
-            if (lane == 0 && jj < nb) {
-                s_cb[jj] = cb[m];
-                s_ci[jj] = ci[m];
-            }
-        }
+    if (tid == 0) {
+        s_reject = 0;
+        s_nf = 0;
     }
-    if (tid == 0) s_reject = 0;
     __syncthreads();
     const double ztol = a.zero_tol * __ldg(a.maxabs);
-    if (tid < nb) {
-        const double d = __ldcg(&a.Dd[k + tid]);
-        const unsigned long long akb = absbits64(d), cb = s_cb[tid];
-        const double colmax = __longlong_as_double((long long)cb);
-        const bool plain = (akb == 0ULL && cb == 0ULL) || akb >= absbits64(alpha * colmax);
-        s_fail[tid] = plain ? 0 : 1;
-        // zero pivots, and values that are not finite, go to the pivoting panel
-        if (d == 0.0 || fabs(d) <= ztol || !isfinite(d) || !isfinite(colmax)) atomicOr(&s_reject, 1);
-    }
-    __syncthreads();
-    // columns that need the row test: listed for k_bk_spec_rows
-    __shared__ int s_nf;
-    int nf = 0;
-    if (tid == 0) s_nf = 0;
-    if (tid == 0 && !s_reject) {
-        for (int jj = 0; jj < nb; ++jj) {
-            if (!s_fail[jj]) continue;
-            const int r = s_ci[jj];
-            if (r <= k + jj || r >= N) {   // no valid row: leave the panel to the pivoting kernel
-                s_reject = 1;
-                break;
+    bool fail = false;
+    RowTest rt{};
+    if (tid < 64) {
+        const unsigned long long cb = __ldcg(&a.cmax[tid]), key = __ldcg(&a.cmax[64 + tid]);
+        a.cmax[tid] = 0ULL;                  // cleared for the next panel
+        a.cmax[64 + tid] = 0ULL;
+        if (tid < nb) {
+            const double d = __ldcg(&a.Dd[k + tid]);
+            const unsigned long long akb = absbits64(d);
+            const double colmax = __longlong_as_double((long long)cb);
+            const bool plain = (akb == 0ULL && cb == 0ULL) || akb >= absbits64(alpha * colmax);
+            // zero pivots, and values that are not finite, go to the pivoting panel
+            if (d == 0.0 || fabs(d) <= ztol || !isfinite(d) || !isfinite(colmax)) atomicOr(&s_reject, 1);
+            if (!plain) {
+                const int r = (int)(0xFFFFFFu - (unsigned)(key & 0xFFFFFFULL));
+                if (r <= k + tid || r >= N) atomicOr(&s_reject, 1);   // no valid row
+                fail = true;
+                rt = RowTest{tid, r, colmax, fabs(d)};
             }
-            a.fail[nf] = RowTest{jj, r, __longlong_as_double((long long)s_cb[jj]), fabs(__ldcg(&a.Dd[k + jj]))};
-            ++nf;
         }
-        a.st->nfail = s_reject ? 0 : nf;
-        s_nf = nf;
+    }
+    // columns that need the row test: listed (in column order) for k_bk_spec_rows
+    const unsigned bal = __ballot_sync(0xffffffffu, fail);
+    if (tid == 0) s_cnt0 = __popc(bal);
+    __syncthreads();
+    if (fail) {
+        const int pos = __popc(bal & ((1u << lane) - 1u)) + (tid >= 32 ? s_cnt0 : 0);
+        a.fail[pos] = rt;
+        atomicAdd(&s_nf, 1);
     }
     __syncthreads();
-    nf = s_nf;
+    const int nf = s_nf;
+    if (tid == 0) a.st->nfail = s_reject ? 0 : nf;
     if (s_reject) {
         if (tid == 0) {
             a.st->spec = 0;
@@ -958,8 +946,9 @@ __global__ void __launch_bounds__(kSpecThreads) k_bk_spec_rows(SpecArgs a) {
     }
 }
 
-__global__ void k_bk_init(int N, int32_t *perm, PanelState *st) {
+__global__ void k_bk_init(int N, int32_t *perm, PanelState *st, unsigned long long *cmax) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) perm[i] = i;
+    if (blockIdx.x == 0 && threadIdx.x < 128) cmax[threadIdx.x] = 0ULL;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->k = 0;
         st->kb = 0;
@@ -1051,11 +1040,11 @@ BlockedConfig blocked_config(int64_t N, bool f32, int nb_want = 0) {
 
 // scratch layout: W of the last panel (N x 65 doubles), the panel state, the
 // FP32 L and W columns of the last panel (N x 65 floats each; FP32-update
-// form), and for the verified no-interchange panels the column candidates
-// ((ceil(N / 32) + 2) x 64), the pending row tests (64) and their partial
-// row maxima ((ceil(N / 32) + 2) x 64)
+// form), and for the verified no-interchange panels the per-column maxima
+// (2 x 64), the pending row tests (64) and their partial row maxima
+// ((ceil(N / 32) + 2) x 64)
 struct BlockedScratch {
-    size_t wg, st, lf, wf, cand, fail, rowpart, total;
+    size_t wg, st, lf, wf, cmax, fail, rowpart, total;
 };
 
 BlockedScratch blocked_scratch(int64_t N) {
@@ -1066,8 +1055,8 @@ BlockedScratch blocked_scratch(int64_t N) {
     l.st = up(n * 65 * sizeof(double));
     l.lf = l.st + 256;
     l.wf = l.lf + up(n * 65 * sizeof(float));
-    l.cand = l.wf + up(n * 65 * sizeof(float));
-    l.fail = l.cand + up(((n + kSpecRB - 1) / kSpecRB + 2) * 64 * sizeof(ColCand));
+    l.cmax = l.wf + up(n * 65 * sizeof(float));
+    l.fail = l.cmax + up(128 * sizeof(unsigned long long));
     l.rowpart = l.fail + up(64 * sizeof(RowTest));
     l.total = l.rowpart + up(((n + 31) / 32 + 2) * 64 * sizeof(unsigned long long));
     return l;
@@ -1104,7 +1093,8 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
     const BlockedScratch lay = blocked_scratch(N);
     double *Wg = reinterpret_cast<double *>(w + lay.wg);
     PanelState *st = reinterpret_cast<PanelState *>(w + lay.st);
-    k_bk_init<<<std::max(1, std::min(1024, ceil_div(N, 256))), 256, 0, s>>>((int)N, out.perm, st);
+    k_bk_init<<<std::max(1, std::min(1024, ceil_div(N, 256))), 256, 0, s>>>(
+        (int)N, out.perm, st, reinterpret_cast<unsigned long long *>(w + lay.cmax));
     MDSIP_LAUNCHED();
 
     PanelArgs a{};
@@ -1160,7 +1150,7 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
         sa.kind = out.kind;
         sa.Lf = a.Lf;
         sa.Wf = a.Wf;
-        sa.cand = reinterpret_cast<ColCand *>(w + lay.cand);
+        sa.cmax = reinterpret_cast<unsigned long long *>(w + lay.cmax);
         sa.fail = reinterpret_cast<RowTest *>(w + lay.fail);
         sa.rowpart = reinterpret_cast<unsigned long long *>(w + lay.rowpart);
         sa.st = st;
