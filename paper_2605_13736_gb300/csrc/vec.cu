@@ -135,66 +135,44 @@ __global__ void k_jac_hess(Dims D, ModelView M, const double *__restrict__ x,
 // ---------------------------------------------------------------------------
 // A passes
 // ---------------------------------------------------------------------------
-// out = A v: one warp per pair of rows, v staged in shared memory, four
-// 16-byte loads per row and lane in flight, two FP64 accumulators per row.  On
-// GB300 an FP64 pass over A is bound by the DFMA rate (2 flop per 8 bytes);
-// this form reached 0.48 ms for a 100 000 x 2 000 pass (a warp-per-row form
-// 0.56 ms, 32-row register-blocked forms 0.8-0.9 ms at one block per SM).
+// out = A v: one thread per row, v staged in shared memory.  A row's dot
+// product runs in eight independent FP64 accumulators with no reduction
+// across lanes; a warp's 16-byte loads touch 32 rows at once, and each
+// 32-byte sector serves two consecutive loads of its row through L1.  On GB300
+// an FP64 pass over A is bound by the DFMA rate (2 flop per 8 bytes).
 __global__ void __launch_bounds__(NT) k_gemv_rows(const double *__restrict__ A, int64_t m, int64_t n,
                                                   int64_t lda, const double *__restrict__ v,
                                                   double *__restrict__ out) {
-    extern __shared__ double vs[];   // n rounded up to even, zero padded
-    const int64_t n2 = (n + 1) / 2;
-    for (int64_t k = threadIdx.x; k < 2 * n2; k += NT) vs[k] = k < n ? v[k] : 0.0;
+    extern __shared__ double vs[];   // n rounded up to a multiple of 8, zero padded
+    const int64_t n8 = (n + 7) / 8 * 8;
+    for (int64_t k = threadIdx.x; k < n8; k += NT) vs[k] = k < n ? v[k] : 0.0;
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * NT) >> 5;
+    const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (i >= m) return;
+    const double2 *r = reinterpret_cast<const double2 *>(A + i * lda);
     const double2 *x2 = reinterpret_cast<const double2 *>(vs);
-    const bool odd = (n & 1) != 0;
-    for (int64_t i = 2 * gw; i < m; i += 2 * nw) {
-        const bool two = i + 1 < m;
-        const double2 *r0 = reinterpret_cast<const double2 *>(A + i * lda);
-        const double2 *r1 = reinterpret_cast<const double2 *>(A + (two ? i + 1 : i) * lda);
-        double s0 = 0.0, s1 = 0.0, t0 = 0.0, t1 = 0.0;
-        int64_t k = lane;
-        const int64_t n2m = odd ? n2 - 1 : n2;   // the last pair of an odd n goes to the guarded tail
-        for (; k + 96 < n2m; k += 128) {
-            double2 a[4], c[4];
+    double acc[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                a[u] = __ldg(r0 + k + 32 * u);
-                c[u] = __ldg(r1 + k + 32 * u);
-            }
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    const int64_t full = n / 8;          // groups of 8 columns (4 pairs) inside the row
+    for (int64_t g = 0; g < full; ++g) {
+        double2 a[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const double2 b = x2[k + 32 * u];
-                if (u & 1) {
-                    s1 = fma(a[u].x, b.x, fma(a[u].y, b.y, s1));
-                    t1 = fma(c[u].x, b.x, fma(c[u].y, b.y, t1));
-                } else {
-                    s0 = fma(a[u].x, b.x, fma(a[u].y, b.y, s0));
-                    t0 = fma(c[u].x, b.x, fma(c[u].y, b.y, t0));
-                }
-            }
-        }
-        for (; k < n2; k += 32) {
-            const double2 b = x2[k];
-            double2 a0 = __ldg(r0 + k), c0 = __ldg(r1 + k);
-            if (odd && k == n2 - 1) a0.y = c0.y = 0.0;   // the padding column beyond n
-            s0 = fma(a0.x, b.x, fma(a0.y, b.y, s0));
-            t0 = fma(c0.x, b.x, fma(c0.y, b.y, t0));
-        }
-        double s = s0 + s1, t = t0 + t1;
-        for (int o = 16; o > 0; o >>= 1) {
-            s += __shfl_xor_sync(0xffffffffu, s, o);
-            t += __shfl_xor_sync(0xffffffffu, t, o);
-        }
-        if (lane == 0) {
-            out[i] = s;
-            if (two) out[i + 1] = t;
+        for (int u = 0; u < 4; ++u) a[u] = __ldg(r + 4 * g + u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const double2 b = x2[4 * g + u];
+            acc[2 * u] = fma(a[u].x, b.x, acc[2 * u]);
+            acc[2 * u + 1] = fma(a[u].y, b.y, acc[2 * u + 1]);
         }
     }
+    const double *rd = A + i * lda;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {   // ragged tail (fewer than 8 columns)
+        const int64_t c = 8 * full + t;
+        if (c < n) acc[t] = fma(rd[c], vs[c], acc[t]);
+    }
+    out[i] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
 }
 
 // partial[b][p] = sum over the rows of block b of A[i][p] u[i]
@@ -790,20 +768,21 @@ void launch_finalize_min(cudaStream_t s, const double *partial, int nq, double *
 
 static int elem_grid(int64_t n) { return std::max(1, std::min(4096, ceil_div(n, 256))); }
 
-// A: rows 16-byte aligned (lda even, A 16-byte aligned); n <= 24576 (v staged in shared memory)
+// A: rows 16-byte aligned (lda even, A 16-byte aligned); n <= 24568 (v staged in shared memory)
 void launch_gemv_rows(cudaStream_t s, const double *A, int64_t m, int64_t n, int64_t lda,
                       const double *v, double *out) {
     if (m <= 0) return;
     MDSIP_REQUIRE((lda & 1) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0, MDSIP_ERR_INVALID_ARG,
                   "gemv: rows of A must be 16-byte aligned");
-    const size_t smem = (size_t)((n + 1) / 2) * 2 * sizeof(double);
+    const size_t smem = (size_t)((n + 7) / 8) * 8 * sizeof(double);
     MDSIP_REQUIRE(smem <= 192 * 1024, MDSIP_ERR_INVALID_ARG, "gemv: n too large");
     static PerDeviceOnce once;
     MDSIP_CUDA(once.run([] {
         return cudaFuncSetAttribute(k_gemv_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 192 * 1024);
     }));
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(4 * kRedBlocks, ceil_div(m, NT / 16)));
-    k_gemv_rows<<<grid, NT, smem, s>>>(A, m, n, lda, v, out);
+    const int64_t grid = ceil_div(m, NT);
+    MDSIP_REQUIRE(grid <= 0x7fffffff, MDSIP_ERR_INVALID_ARG, "gemv: m too large");
+    k_gemv_rows<<<(unsigned)grid, NT, smem, s>>>(A, m, n, lda, v, out);
     MDSIP_LAUNCHED();
 }
 
