@@ -297,6 +297,200 @@ __global__ void __launch_bounds__(kThreads) k_ldlt_solve_flags(FlagSolve<T> p) {
     }
 }
 
+// FP32 form (the refined mixed-precision path): a block's result travels as
+// 64-bit words (value bits | epoch << 32), so one load both tests that block J
+// is published and delivers x_J, and a CTA fetches up to four published blocks
+// per round trip.  No separate flags, no fences between value and flag.
+struct TagSolve {
+    int N, nblk;
+    const float *F, *Bk;
+    const double *Dd, *Doff;
+    const int32_t *perm;
+    double *b;
+    unsigned long long *xw, *zw;   // tagged block results
+    unsigned *epoch, *done;
+    int *err;
+};
+
+__device__ __forceinline__ unsigned long long tag_word(float v, unsigned e) {
+    return ((unsigned long long)e << 32) | (unsigned long long)__float_as_uint(v);
+}
+
+// value of a tagged word once it carries epoch e (bounded wait; false on expiry)
+__device__ __forceinline__ bool tag_wait(const unsigned long long *w, unsigned e, int *err, float &v) {
+    volatile const unsigned long long *vp = w;
+    unsigned long long x = *vp;
+    if ((unsigned)(x >> 32) != e) {
+        const long long t0 = clock64();
+        do {
+            if (*((volatile int *)err) != 0 || clock64() - t0 > kBarrierLimitCycles) {
+                atomicExch(err, 1);
+                return false;
+            }
+            x = *vp;
+        } while ((unsigned)(x >> 32) != e);
+    }
+    v = __uint_as_float((unsigned)x);
+    return true;
+}
+
+constexpr int kTagBatch = 4;   // published blocks fetched per round trip
+
+__global__ void __launch_bounds__(kThreads) k_ldlt_solve_tagged(TagSolve p) {
+    __shared__ float sv[kTagBatch][kBS];
+    __shared__ float spart[4][kBS];
+    __shared__ unsigned s_e;
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, r = tid & (kBS - 1), q = tid >> 6;
+    const int G = (int)gridDim.x, N = p.N, nblk = p.nblk;
+    if (tid == 0) {
+        s_e = *((volatile unsigned *)p.epoch) + 1u;
+        s_ok = 1;
+    }
+    __syncthreads();
+    const unsigned e = s_e;
+    float reg[kTagBatch][16];
+
+    // sum over J in [J0, J1) of tile(J) * v_J, tiles at tile_of(J), results in words w
+    auto accumulate = [&](auto tile_of, const unsigned long long *w, int J0, int J1, int step, float acc) {
+        for (int J = J0; J != J1 && s_ok;) {
+            const int nbat = min(kTagBatch, (J1 - J) * step);
+#pragma unroll
+            for (int bq = 0; bq < kTagBatch; ++bq)
+                if (bq < nbat) load_quarter(tile_of(J + bq * step), r, q, reg[bq]);
+            {   // thread t fetches word t % 64 of block t / 64
+                const int bq = tid >> 6;
+                if (bq < nbat) {
+                    float v = 0.0f;
+                    if (!tag_wait(w + (int64_t)(J + bq * step) * kBS + r, e, p.err, v)) atomicExch(&s_ok, 0);
+                    sv[bq][r] = v;
+                }
+            }
+            __syncthreads();
+            if (!s_ok) break;
+#pragma unroll
+            for (int bq = 0; bq < kTagBatch; ++bq)
+                if (bq < nbat) acc = dot_quarter(reg[bq], sv[bq], q, acc);
+            __syncthreads();
+            J += nbat * step;
+        }
+        return acc;
+    };
+
+    // ---------------- forward: x_I = inv(L_II) (P b - sum_J<I L_IJ x_J) ----------------
+    for (int I = blockIdx.x; I < nblk && s_ok; I += G) {
+        float acc = accumulate([&](int J) { return p.F + tile_index(I, J) * kTile; }, p.xw, 0, I, 1, 0.0f);
+        if (!s_ok) break;
+        load_quarter(p.F + tile_index(I, I) * kTile, r, q, reg[0]);
+        spart[q][r] = acc;
+        __syncthreads();
+        if (tid < kBS) {
+            const int row = I * kBS + tid;
+            const float y0 = row < N ? (float)p.b[p.perm[row]] : 0.0f;
+            sv[0][tid] = y0 - (spart[0][tid] + spart[1][tid] + spart[2][tid] + spart[3][tid]);
+        }
+        __syncthreads();
+        const float a2 = dot_quarter(reg[0], sv[0], q, 0.0f);
+        __syncthreads();
+        spart[q][r] = a2;
+        __syncthreads();
+        if (tid < kBS)
+            p.xw[(int64_t)I * kBS + tid] = tag_word(spart[0][tid] + spart[1][tid] + spart[2][tid] + spart[3][tid], e);
+        __syncthreads();
+    }
+
+    // ---------------- w = D^-1 x, then z_I = inv(L_II)^T (w_I - sum_J>I L_JI^T z_J) ----------------
+    int last = (int)blockIdx.x;
+    while (last + G < nblk) last += G;
+    for (int I = last; I >= 0 && s_ok && (int)blockIdx.x < nblk; I -= G) {
+        float w = 0.0f;
+        if (tid < kBS) {
+            const int k = I * kBS + tid;
+            if (k < N) {
+                // x of rows k and k + 1 (a 2x2 block may straddle into block I + 1)
+                auto xval = [&](int kk) {
+                    float v = 0.0f;
+                    if (!tag_wait(p.xw + kk, e, p.err, v)) atomicExch(&s_ok, 0);
+                    return (double)v;
+                };
+                const double off = p.Doff[k];
+                if (off != 0.0) {
+                    const double a = p.Dd[k], c = p.Dd[k + 1];
+                    const double u = xval(k), v = xval(k + 1);
+                    w = (float)((c * u - off * v) / (a * c - off * off));
+                } else if (k > 0 && p.Doff[k - 1] != 0.0) {
+                    const double a = p.Dd[k - 1], c = p.Dd[k], o2 = p.Doff[k - 1];
+                    const double u = xval(k - 1), v = xval(k);
+                    w = (float)((a * v - o2 * u) / (a * c - o2 * o2));
+                } else {
+                    w = (float)(xval(k) / p.Dd[k]);
+                }
+            }
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        float acc = accumulate([&](int J) { return p.Bk + tile_index(J, I) * kTile; }, p.zw, nblk - 1, I, -1, 0.0f);
+        if (!s_ok) break;
+        load_quarter(p.Bk + tile_index(I, I) * kTile, r, q, reg[0]);
+        spart[q][r] = acc;
+        __syncthreads();
+        if (tid < kBS) sv[0][tid] = w - (spart[0][tid] + spart[1][tid] + spart[2][tid] + spart[3][tid]);
+        __syncthreads();
+        const float a2 = dot_quarter(reg[0], sv[0], q, 0.0f);
+        __syncthreads();
+        spart[q][r] = a2;
+        __syncthreads();
+        if (tid < kBS) {
+            const float zi = spart[0][tid] + spart[1][tid] + spart[2][tid] + spart[3][tid];
+            p.zw[(int64_t)I * kBS + tid] = tag_word(zi, e);
+            const int row = I * kBS + tid;
+            if (row < N) p.b[p.perm[row]] = (double)zi;
+        }
+        __syncthreads();
+    }
+
+    // the last CTA to finish advances the epoch (every CTA has read it by then)
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const unsigned d = atomicAdd(p.done, 1u);
+        if (d == (unsigned)G - 1u) {
+            atomicExch(p.done, 0u);
+            __threadfence();
+            atomicAdd(p.epoch, 1u);
+        }
+    }
+}
+
+void launch_solve_tagged(cudaStream_t s, int num_sms, int64_t N, const double *Dd, const double *Doff,
+                         const int32_t *perm, int64_t nrhs, double *B, int64_t ldb, char *w, int *err_dev) {
+    const Layout l = layout_for(N);
+    TagSolve p{};
+    p.N = (int)N;
+    p.nblk = l.nblk;
+    p.F = reinterpret_cast<const float *>(w + l.off_F);
+    p.Bk = reinterpret_cast<const float *>(w + l.off_B);
+    p.Dd = Dd;
+    p.Doff = Doff;
+    p.perm = perm;
+    p.xw = reinterpret_cast<unsigned long long *>(w + l.off_x);
+    p.zw = reinterpret_cast<unsigned long long *>(w + l.off_z);
+    p.epoch = reinterpret_cast<unsigned *>(w);
+    p.done = reinterpret_cast<unsigned *>(w + 4);
+    p.err = err_dev;
+    int per_sm = 0;
+    MDSIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ldlt_solve_tagged, kThreads, 0));
+    MDSIP_REQUIRE(per_sm >= 1, MDSIP_ERR_INVALID_ARG, "ldlt_solve: kernel does not fit on an SM");
+    const int grid = (int)std::min<int64_t>(l.nblk, (int64_t)num_sms * per_sm);
+    for (int64_t rr = 0; rr < nrhs; ++rr) {
+        p.b = B + rr * ldb;
+        void *args[] = {&p};
+        MDSIP_CUDA(cudaLaunchCooperativeKernel((const void *)k_ldlt_solve_tagged, dim3(grid), dim3(kThreads), args,
+                                               0, s));
+        count_launch();
+    }
+}
+
 template <typename T>
 void launch_solve_t(cudaStream_t s, int num_sms, int64_t N, const double *Dd, const double *Doff,
                     const int32_t *perm, int64_t nrhs, double *B, int64_t ldb, char *w, int *err_dev) {
@@ -340,7 +534,9 @@ void launch_ldlt_solve_prepare(cudaStream_t s, int64_t N, const double *L, void 
     MDSIP_REQUIRE((reinterpret_cast<uintptr_t>(w) & 255) == 0, MDSIP_ERR_INVALID_ARG,
                   "ldlt_solve: misaligned scratch");
     const Layout l = layout_for(N);
-    MDSIP_CUDA(cudaMemsetAsync(w, 0, l.off_x, s));   // epoch, done counter, flags
+    // epoch, done counter, flags, and the tagged results (a stale word must
+    // not carry an epoch of the new series)
+    MDSIP_CUDA(cudaMemsetAsync(w, 0, l.off_F, s));
     if (fp32)
         k_solve_tiles<float><<<(unsigned)l.ntile, kThreads, 0, s>>>(
             (int)N, L, reinterpret_cast<float *>(w + l.off_F), reinterpret_cast<float *>(w + l.off_B));
@@ -359,7 +555,7 @@ void launch_ldlt_solve_coop(cudaStream_t s, int num_sms, int64_t N, const double
     if (N <= 0 || nrhs <= 0) return;
     char *w = static_cast<char *>(scratch);
     if (fp32)
-        launch_solve_t<float>(s, num_sms, N, Dd, Doff, perm, nrhs, B, ldb, w, err_dev);
+        launch_solve_tagged(s, num_sms, N, Dd, Doff, perm, nrhs, B, ldb, w, err_dev);
     else
         launch_solve_t<double>(s, num_sms, N, Dd, Doff, perm, nrhs, B, ldb, w, err_dev);
 }
