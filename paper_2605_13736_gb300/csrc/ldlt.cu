@@ -704,8 +704,8 @@ void ldlt_factor_fixed_scratch(cudaStream_t s, int device, int num_sms, int64_t 
     MDSIP_REQUIRE(S && out.L && out.Dd && out.Doff && out.perm && out.kind, MDSIP_ERR_INVALID_ARG,
                   "ldlt: null pointer");
     char *base = static_cast<char *>(fixed_scratch_address(device));
-    // layout: [factor scratch | error flag | partials | max |S|]
-    const size_t fs = ldlt_scratch_bytes(N);
+    // layout: [unblocked factor scratch | error flag | partials | max |S|]
+    const size_t fs = ldlt_unblocked_scratch_bytes(N);
     int *err = reinterpret_cast<int *>(base + fs);
     double *partial = reinterpret_cast<double *>(base + fs + 256);
     double *maxabs = partial + kRedBlocks;

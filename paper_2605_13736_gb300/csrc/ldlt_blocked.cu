@@ -44,6 +44,13 @@ constexpr int kPanelThreads = 512;
 constexpr int kUpdThreads = 256;
 constexpr int kUT = 64;   // trailing-update tile edge
 
+// Programmatic dependent launch: the kernels of the panel loop are launched
+// with programmatic stream serialization, so a kernel's launch overlaps the
+// tail of the one before it.  Each waits for its predecessor's completion (and
+// memory) before touching data, then lets its own successor launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 struct PanelState {
     int k;       // first column of the next panel
     int kb;      // columns factored by the last panel
@@ -176,6 +183,8 @@ __device__ bool cluster_cand(cg::cluster_group &cl, Cand *cand, int slot, int C,
 // refined mixed-precision path); pivot tests, D and inertia stay FP64.
 template <bool F32>
 __global__ void __launch_bounds__(kPanelThreads, 1) k_bk_panel(PanelArgs a) {
+    pdl_wait();
+    pdl_release();
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int C = a.C, N = a.N, NB = a.NB, S = NB + 1;
@@ -516,6 +525,22 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_bk_panel(PanelArgs a) {
 // A(i, c) -= sum_{t < kb} L(i, k + t) W(c, t)  for k + kb <= c <= i < N.
 // Block = one 64 x 64 tile of the trailing lower triangle (tiles beyond the
 // actual trailing size return).  256 threads, 4 x 4 outputs each.
+// four consecutive values from 16-byte aligned shared memory
+__device__ __forceinline__ void load4(const float *p, float (&v)[4]) {
+    const float4 x = *reinterpret_cast<const float4 *>(p);
+    v[0] = x.x;
+    v[1] = x.y;
+    v[2] = x.z;
+    v[3] = x.w;
+}
+__device__ __forceinline__ void load4(const double *p, double (&v)[4]) {
+    const double2 x = reinterpret_cast<const double2 *>(p)[0], y = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = x.x;
+    v[1] = x.y;
+    v[2] = y.x;
+    v[3] = y.y;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kUpdThreads) k_bk_trailing(int N, int NB, double *__restrict__ A,
                                                              const double *__restrict__ L,
@@ -523,7 +548,9 @@ __global__ void __launch_bounds__(kUpdThreads) k_bk_trailing(int N, int NB, doub
                                                              const float *__restrict__ Lf,
                                                              const float *__restrict__ Wf,
                                                              const PanelState *__restrict__ st) {
-    extern __shared__ unsigned char usmem[];
+    pdl_wait();
+    pdl_release();
+    extern __shared__ __align__(16) unsigned char usmem[];
     const int S = NB + 1;
     T *Lt = reinterpret_cast<T *>(usmem);          // [S][64]: Lt[t][r]
     T *Wt = Lt + (size_t)S * kUT;                   // [S][64]: Wt[t][c]
@@ -538,19 +565,39 @@ __global__ void __launch_bounds__(kUpdThreads) k_bk_trailing(int N, int NB, doub
     const int i0 = base + tr * kUT, c0 = base + tc * kUT;
     if (i0 >= N) return;
     const int tid = threadIdx.x;
-    for (int e = tid; e < kb * kUT; e += kUpdThreads) {
-        const int t = e / kUT, r = e % kUT;
+    {   // stage the panel's L rows and W rows of this tile: all loads in flight
+        // before the first shared-memory store (thread: row r, columns t0 + 4 j)
+        constexpr int kJ = (65 + 3) / 4;   // panel width <= 65
+        const int r = tid & (kUT - 1), t0 = tid >> 6;
         const int i = i0 + r, c = c0 + r;
-        if constexpr (sizeof(T) == sizeof(float)) {   // the panel's FP32 copies
-            Lt[t * kUT + r] = i < N ? Lf[i + (int64_t)t * N] : 0.0f;
-            Wt[t * kUT + r] = c < N ? Wf[c + (int64_t)t * N] : 0.0f;
-        } else {
-            Lt[t * kUT + r] = (T)(i < N ? L[i + (int64_t)(k0 + t) * N] : 0.0);
-            Wt[t * kUT + r] = (T)(c < N ? Wg[c + (int64_t)t * N] : 0.0);
+        T lv[kJ], wv[kJ];
+#pragma unroll
+        for (int j = 0; j < kJ; ++j) {
+            const int t = t0 + 4 * j;
+            lv[j] = wv[j] = (T)0;
+            if (t < kb) {
+                if constexpr (sizeof(T) == sizeof(float)) {   // the panel's FP32 copies
+                    if (i < N) lv[j] = Lf[i + (int64_t)t * N];
+                    if (c < N) wv[j] = Wf[c + (int64_t)t * N];
+                } else {
+                    if (i < N) lv[j] = (T)L[i + (int64_t)(k0 + t) * N];
+                    if (c < N) wv[j] = (T)Wg[c + (int64_t)t * N];
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kJ; ++j) {
+            const int t = t0 + 4 * j;
+            if (t < kb) {
+                Lt[t * kUT + r] = lv[j];
+                Wt[t * kUT + r] = wv[j];
+            }
         }
     }
     __syncthreads();
-    const int tx = tid & 15, ty = tid >> 4;   // rows tx + 16 u, columns ty + 16 v
+    // rows 4 tx .. 4 tx + 3, columns 4 ty .. 4 ty + 3: each step reads its
+    // four L and four W values as 16-byte shared-memory loads
+    const int tx = tid & 15, ty = tid >> 4;
     T acc[4][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
@@ -558,10 +605,8 @@ __global__ void __launch_bounds__(kUpdThreads) k_bk_trailing(int N, int NB, doub
         for (int v = 0; v < 4; ++v) acc[u][v] = (T)0;
     for (int t = 0; t < kb; ++t) {
         T lv[4], wv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) lv[u] = Lt[t * kUT + tx + 16 * u];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) wv[v] = Wt[t * kUT + ty + 16 * v];
+        load4(Lt + t * kUT + 4 * tx, lv);
+        load4(Wt + t * kUT + 4 * ty, wv);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -569,11 +614,11 @@ __global__ void __launch_bounds__(kUpdThreads) k_bk_trailing(int N, int NB, doub
     }
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-        const int c = c0 + ty + 16 * v;
+        const int c = c0 + 4 * ty + v;
         if (c >= N) continue;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int i = i0 + tx + 16 * u;
+            const int i = i0 + 4 * tx + u;
             if (i < N && i >= c) A[i + (int64_t)c * N] -= (double)acc[u][v];
         }
     }
@@ -652,6 +697,8 @@ __device__ void spec_accept(const SpecArgs &a, int k, int nb) {
 }
 
 __global__ void __launch_bounds__(kSpecThreads, 1) k_bk_spec(SpecArgs a) {
+    pdl_wait();
+    pdl_release();
     extern __shared__ double spsm[];
     const int N = a.N, NB = a.NB, G = (int)gridDim.x, g = (int)blockIdx.x;
     const int tid = threadIdx.x;
@@ -875,6 +922,8 @@ __global__ void __launch_bounds__(kSpecThreads, 1) k_bk_spec(SpecArgs a) {
 // over 32 rows c (one per lane; warp w takes the listed columns w, w + 8, ...),
 // then the last CTA applies the rule and keeps or hands over the panel.
 __global__ void __launch_bounds__(kSpecThreads) k_bk_spec_rows(SpecArgs a) {
+    pdl_wait();
+    pdl_release();
     __shared__ float s_w[64 * 64];
     __shared__ RowTest s_t[64];
     __shared__ int s_last, s_reject;
@@ -962,6 +1011,7 @@ __global__ void k_bk_init(int N, int32_t *perm, PanelState *st, unsigned long lo
 }
 
 __global__ void k_bk_finish(const PanelState *st, int32_t *inertia, int32_t *panels) {
+    pdl_wait();
     inertia[0] = st->npos;
     inertia[1] = st->nneg;
     inertia[2] = st->nzero;
@@ -1036,6 +1086,33 @@ BlockedConfig blocked_config(int64_t N, bool f32, int nb_want = 0) {
     }
     c.C = 0;
     return c;
+}
+
+// launch with programmatic stream serialization (and a cluster when cluster > 1)
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s, int cluster,
+                Args... args) {
+    cudaLaunchConfig_t c{};
+    c.gridDim = dim3(grid);
+    c.blockDim = dim3(block);
+    c.dynamicSmemBytes = smem;
+    c.stream = s;
+    cudaLaunchAttribute at[2];
+    int na = 0;
+    at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+    if (cluster > 1) {
+        at[na].id = cudaLaunchAttributeClusterDimension;
+        at[na].val.clusterDim.x = (unsigned)cluster;
+        at[na].val.clusterDim.y = 1;
+        at[na].val.clusterDim.z = 1;
+        ++na;
+    }
+    c.attrs = at;
+    c.numAttrs = na;
+    MDSIP_CUDA(cudaLaunchKernelEx(&c, kern, args...));
+    count_launch();
 }
 
 // scratch layout: W of the last panel (N x 65 doubles), the panel state, the
@@ -1115,19 +1192,6 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
     a.maxabs = maxabs_dev;
     a.zero_tol = zero_tol;
 
-    cudaLaunchConfig_t lc{};
-    lc.gridDim = dim3(cfg.C);
-    lc.blockDim = dim3(kPanelThreads);
-    lc.dynamicSmemBytes = cfg.smem;
-    lc.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = cfg.C;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    lc.attrs = at;
-    lc.numAttrs = 1;
-
     const size_t usm = 2 * (size_t)(cfg.NB + 1) * kUT * (fp32_update ? sizeof(float) : sizeof(double));
     static PerDeviceOnce once;
     MDSIP_CUDA(once.run([] {
@@ -1167,31 +1231,30 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
             // rows below the diagonal block: at most N - (p + 1) NB (every panel takes >= NB columns)
             const int64_t below = N - (int64_t)(p + 1) * cfg.NB;
             const int G = (int)std::max<int64_t>(1, (below + kSpecRB - 1) / kSpecRB);
-            k_bk_spec<<<G, kSpecThreads, spec_smem(cfg.NB), s>>>(sa);
-            MDSIP_LAUNCHED();
+            launch_pdl(k_bk_spec, (unsigned)G, kSpecThreads, spec_smem(cfg.NB), s, 1, sa);
             // rows of the active matrix: at most N - p NB
             const int G2 = (int)std::max<int64_t>(1, (N - (int64_t)p * cfg.NB + 31) / 32);
-            k_bk_spec_rows<<<G2, kSpecThreads, 0, s>>>(sa);
-            MDSIP_LAUNCHED();
+            launch_pdl(k_bk_spec_rows, (unsigned)G2, kSpecThreads, 0, s, 1, sa);
         }
         if (fp32_update)
-            MDSIP_CUDA(cudaLaunchKernelEx(&lc, k_bk_panel<true>, a));
+            launch_pdl(k_bk_panel<true>, (unsigned)cfg.C, kPanelThreads, cfg.smem, s, cfg.C, a);
         else
-            MDSIP_CUDA(cudaLaunchKernelEx(&lc, k_bk_panel<false>, a));
-        count_launch();
+            launch_pdl(k_bk_panel<false>, (unsigned)cfg.C, kPanelThreads, cfg.smem, s, cfg.C, a);
         // trailing matrix after panel p starts at column >= (p + 1) NB
         const int64_t rest = N - (int64_t)(p + 1) * cfg.NB;
         if (rest <= 0) continue;
         const int64_t nt = (rest + kUT - 1) / kUT;
         const unsigned tiles = (unsigned)(nt * (nt + 1) / 2);
+        const float *cLf = a.Lf, *cWf = a.Wf;
+        const double *cL = out.L, *cWg = Wg;
+        const PanelState *cst = st;
         if (fp32_update)
-            k_bk_trailing<float><<<tiles, kUpdThreads, usm, s>>>((int)N, cfg.NB, S, out.L, Wg, a.Lf, a.Wf, st);
+            launch_pdl(k_bk_trailing<float>, tiles, kUpdThreads, usm, s, 1, (int)N, cfg.NB, S, cL, cWg, cLf, cWf, cst);
         else
-            k_bk_trailing<double><<<tiles, kUpdThreads, usm, s>>>((int)N, cfg.NB, S, out.L, Wg, a.Lf, a.Wf, st);
-        MDSIP_LAUNCHED();
+            launch_pdl(k_bk_trailing<double>, tiles, kUpdThreads, usm, s, 1, (int)N, cfg.NB, S, cL, cWg, cLf, cWf, cst);
     }
-    k_bk_finish<<<1, 1, 0, s>>>(st, out.inertia, out.panels);
-    MDSIP_LAUNCHED();
+    const PanelState *cst = st;
+    launch_pdl(k_bk_finish, 1, 1, 0, s, 1, cst, out.inertia, out.panels);
 }
 
 }  // namespace mdsip
