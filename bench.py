@@ -37,6 +37,7 @@ UNIT = "Newton steps/s"
 # FP64 ALU peak of a GB300: 152 SMs x 2 DFMA/clk (4 flop) x 2.07 GHz.  A DFMA
 # microbenchmark reached 1.20 TFLOP/s at ~1.97 GHz on this machine.
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12   # 128 FP32 lanes per SM, 2 flop per FMA
 # DRAM bytes per launch of the FP64 condensation kernel at n_d = 2000,
 # m_E = 100000, scaled from an ncu capture of the current kernel at m = 20000
 # (profiles/syrk_fp64_m20000_n2000.md): reads of A grow with m, the split
@@ -364,19 +365,26 @@ def run_warmstart(args, m, torch, local):
 
 def cond_ldlt_roofline(inst, syrk_ms, ldlt_ms, precision):
     """Roofline fraction of condensation + LDL^T together: (F_syrk / P_syrk +
-    F_ldlt / P_fp64) / (measured product + factorization time), F_syrk =
+    F_ldlt / P_ldlt) / (measured product + factorization time), F_syrk =
     n_d (n_d + 1) m_E flop, F_ldlt = N^3 / 3 flop (N = n_d + m_I); P_syrk the FP64
-    ALU peak, the measured BF16 peak, or TF32 at half of it."""
+    ALU peak, the measured BF16 peak, or TF32 at half of it; P_ldlt the peak of
+    the arithmetic the factorization's updates use: FP64 on the FP64 path, FP32
+    (derived: 152 SMs x 128 lanes x 2 flop x 2.07 GHz) on the mixed-precision
+    path.  `ldlt_time_vs_fp64_peak` compares the factorization with the time
+    its flops take at the FP64 peak."""
     N = inst.n_d + inst.m_I
     f_syrk = inst.n_d * (inst.n_d + 1) * inst.m_E * 1.0
     f_ldlt = N ** 3 / 3.0
     p64 = FP64_PEAK_TFLOPS * 1e12
     bf16 = (measured_peak("bf16_tflops") or 1900.0) * 1e12
     p_syrk = {"fp64": p64, "bf16": bf16, "tf32": bf16 / 2.0}[precision]
-    t_roof = f_syrk / p_syrk + f_ldlt / p64
+    p_ldlt = p64 if precision == "fp64" else FP32_PEAK_TFLOPS * 1e12
+    t_roof = f_syrk / p_syrk + f_ldlt / p_ldlt
     t_meas = (syrk_ms + ldlt_ms) / 1e3
     return {"t_roof_ms": 1e3 * t_roof, "t_measured_ms": 1e3 * t_meas, "frac": t_roof / t_meas if t_meas else None,
-            "peaks": f"product at {p_syrk / 1e12:.1f} TFLOP/s ({precision}), LDL^T at the FP64 peak"}
+            "peaks": f"product at {p_syrk / 1e12:.1f} TFLOP/s ({precision}), LDL^T at {p_ldlt / 1e12:.1f} TFLOP/s "
+                     f"({'FP64' if precision == 'fp64' else 'FP32, derived'})",
+            "ldlt_time_vs_fp64_peak": (f_ldlt / p64) / (ldlt_ms / 1e3) if ldlt_ms else None}
 
 
 def run_gpu(args):

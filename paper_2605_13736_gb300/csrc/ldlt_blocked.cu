@@ -648,7 +648,10 @@ __global__ void __launch_bounds__(kUpdThreads) k_bk_trailing(int N, int NB, doub
 // matrix.  Decisions, D and the inertia stay FP64; the chain and the products
 // are FP32 as in the FP32-update panel.  A pivot with |d| <= zero_tol maxabs
 // also hands the panel over, so zero pivots keep the pivoting panel's rules.
-constexpr int kSpecThreads = 256;
+constexpr int kSpecThreads = 256;   // k_bk_spec_rows
+constexpr int kSpecChainThreads = 512;                 // k_bk_spec
+constexpr int kSpecTC = kSpecChainThreads / 16;         // column groups of the register tile
+constexpr int kSpecY = 64 / kSpecTC;                    // columns per thread
 constexpr int kSpecRB = 32;   // rows below the diagonal block per CTA
 constexpr int kSpecP = 65;    // shared-memory row pitch (floats)
 
@@ -696,7 +699,7 @@ __device__ void spec_accept(const SpecArgs &a, int k, int nb) {
     }
 }
 
-__global__ void __launch_bounds__(kSpecThreads, 1) k_bk_spec(SpecArgs a) {
+__global__ void __launch_bounds__(kSpecChainThreads, 1) k_bk_spec(SpecArgs a) {
     pdl_wait();
     pdl_release();
     extern __shared__ double spsm[];
@@ -718,18 +721,18 @@ __global__ void __launch_bounds__(kSpecThreads, 1) k_bk_spec(SpecArgs a) {
     const int nloc = nb + nown;
     if (k < N && (g == 0 || nown > 0)) {        // CTAs beyond the last row have no work
         // Local rows 0..nb-1: the diagonal block; nb..nloc-1: this CTA's rows
-        // below it.  Thread (tr, tc) keeps the entries (tr + 16 x, tc + 16 y),
-        // x < 6, y < 4, in registers: their raw value and the running sum of
+        // below it.  Thread (tr, tc) keeps the entries (tr + 16 x, tc + kSpecTC y),
+        // x < 6, y < kSpecY, in registers: their raw value and the running sum of
         // the panel's products (right-looking, one barrier per column).
         const int tr = tid & 15, tc = tid >> 4;
-        float ar[6][4], u[6][4];
+        float ar[6][kSpecY], u[6][kSpecY];
 #pragma unroll
         for (int x = 0; x < 6; ++x) {
             const int i = tr + 16 * x;
             const int gi = i < nb ? k + i : rb0 + (i - nb);
 #pragma unroll
-            for (int y = 0; y < 4; ++y) {
-                const int c = tc + 16 * y;
+            for (int y = 0; y < kSpecY; ++y) {
+                const int c = tc + kSpecTC * y;
                 const bool valid = i < nloc && c < nb && (i >= nb || c <= i);
                 const double v = valid ? a.A[gi + (int64_t)(k + c) * N] : 0.0;
                 ar[x][y] = (float)v;
@@ -744,15 +747,15 @@ __global__ void __launch_bounds__(kSpecThreads, 1) k_bk_spec(SpecArgs a) {
         __syncthreads();
         for (int jj = 0; jj < nb; ++jj) {
             const float rf = s_rf[jj];
-            float lf[6], wc[4];
+            float lf[6], wc[kSpecY];
 #pragma unroll
             for (int x = 0; x < 6; ++x) {
                 const int i = tr + 16 * x;
                 lf[x] = (i > jj && i < nloc) ? Wsh[i * P + jj] * rf : 0.0f;
             }
 #pragma unroll
-            for (int y = 0; y < 4; ++y) {
-                const int c = tc + 16 * y;
+            for (int y = 0; y < kSpecY; ++y) {
+                const int c = tc + kSpecTC * y;
                 wc[y] = (c > jj && c < nb) ? Wsh[c * P + jj] : 0.0f;
             }
             if (tc == 0) {
@@ -765,11 +768,11 @@ __global__ void __launch_bounds__(kSpecThreads, 1) k_bk_spec(SpecArgs a) {
 #pragma unroll
             for (int x = 0; x < 6; ++x)
 #pragma unroll
-                for (int y = 0; y < 4; ++y) u[x][y] = fmaf(lf[x], wc[y], u[x][y]);
+                for (int y = 0; y < kSpecY; ++y) u[x][y] = fmaf(lf[x], wc[y], u[x][y]);
             // the owners of column jj + 1 publish its working values
 #pragma unroll
-            for (int y = 0; y < 4; ++y) {
-                if (tc + 16 * y == jj + 1) {
+            for (int y = 0; y < kSpecY; ++y) {
+                if (tc + kSpecTC * y == jj + 1) {
 #pragma unroll
                     for (int x = 0; x < 6; ++x) {
                         const int i = tr + 16 * x;
@@ -786,8 +789,8 @@ __global__ void __launch_bounds__(kSpecThreads, 1) k_bk_spec(SpecArgs a) {
 #pragma unroll
         for (int x = 0; x < 6; ++x)
 #pragma unroll
-            for (int y = 0; y < 4; ++y) {
-                const int i = tr + 16 * x, c = tc + 16 * y;
+            for (int y = 0; y < kSpecY; ++y) {
+                const int i = tr + 16 * x, c = tc + kSpecTC * y;
                 if (i < nloc && c < nb && (i >= nb || c <= i)) U[i * P + c] = u[x][y];
             }
         __syncthreads();
@@ -811,7 +814,7 @@ __global__ void __launch_bounds__(kSpecThreads, 1) k_bk_spec(SpecArgs a) {
             atomicMax(&a.cmax[jj], b);
             atomicMax(&a.cmax[64 + jj], ((b >> 24) << 24) | (unsigned long long)(0xFFFFFFu - (unsigned)bi));
         };
-        for (int jj = wid; jj < nb; jj += kSpecThreads / 32) {
+        for (int jj = wid; jj < nb; jj += kSpecChainThreads / 32) {
             unsigned long long b = 0;
             int bi = 0x7fffffff;
             if (lane < nown) {
@@ -826,7 +829,7 @@ __global__ void __launch_bounds__(kSpecThreads, 1) k_bk_spec(SpecArgs a) {
             warp_cand(b, bi);
             if (lane == 0) put_max(jj, b, bi);
         }
-        for (int q = wid;; q += kSpecThreads / 32) {        // the diagonal block's columns
+        for (int q = wid;; q += kSpecChainThreads / 32) {   // the diagonal block's columns
             const int jj = g + q * Gw;
             if (jj >= nb) break;
             unsigned long long b2 = 0;
@@ -1231,7 +1234,7 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
             // rows below the diagonal block: at most N - (p + 1) NB (every panel takes >= NB columns)
             const int64_t below = N - (int64_t)(p + 1) * cfg.NB;
             const int G = (int)std::max<int64_t>(1, (below + kSpecRB - 1) / kSpecRB);
-            launch_pdl(k_bk_spec, (unsigned)G, kSpecThreads, spec_smem(cfg.NB), s, 1, sa);
+            launch_pdl(k_bk_spec, (unsigned)G, kSpecChainThreads, spec_smem(cfg.NB), s, 1, sa);
             // rows of the active matrix: at most N - p NB
             const int G2 = (int)std::max<int64_t>(1, (N - (int64_t)p * cfg.NB + 31) / 32);
             launch_pdl(k_bk_spec_rows, (unsigned)G2, kSpecThreads, 0, s, 1, sa);
