@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--batch-max-nd", type=int, default=512)
     ap.add_argument("--batch-concurrency", type=int, default=32,
                     help="batched measurement: problems solved at once (host workers)")
+    ap.add_argument("--batch-option", action="append", default=[],
+                    help="NAME=VALUE integer solver option set on every batched instance (repeatable)")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched measurement and print its own JSON line")
     ap.add_argument("--ws-train", type=int, default=512,
@@ -240,7 +242,9 @@ def run_reference(args):
 # --------------------------------------------------------------------------
 def run_batch(args, m, torch, local):
     """Many independent instances (one IPM solve each): sequential on one stream
-    vs mdsip_batch_solve with one context/stream per instance."""
+    vs mdsip_batch_solve with one context per instance.  The contexts' streams
+    come from torch's stream pool (32 distinct streams per device), so at most
+    32 instances run at once; instances sharing a stream run in turn."""
     import numpy as np
     import synth
     rng = np.random.default_rng(7)
@@ -259,6 +263,9 @@ def run_batch(args, m, torch, local):
         for name, prec in (("fp64", m.MDSIP_PREC_FP64), ("bf16", m.MDSIP_PREC_BF16)):
             for p in probs:
                 m.mdsip_set_option_int(p, "precision", prec)
+                for kv in args.batch_option:
+                    k, v = kv.split("=")
+                    m.mdsip_set_option_int(p, k, int(v))
             # one untimed pass over every instance: workspaces, autotuned shapes
             # (first use per shape) and captured factorization graphs
             m.mdsip_batch_solve(probs, args.batch_concurrency)

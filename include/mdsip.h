@@ -218,11 +218,11 @@ mdsip_status mdsip_set_start_predicted(mdsip_problem *p, const float *pred, doub
 
 /* Solve `count` independent problems concurrently (the "many instances"
  * setting of Section 1.1: one IPM solve per contingency scenario).  Problems
- * that share a context run one after another on its stream; problems on
- * different contexts (each with its own stream) run concurrently, one host
- * worker thread per context, at most `max_concurrent` at a time (<= 0: no
- * limit).  statuses[i] receives problem i's mdsip_solve status.  Returns OK
- * when every problem was attempted (check the statuses), or INVALID_ARG. */
+ * whose contexts share a CUDA stream run one after another on it; problems on
+ * different streams run concurrently, one host worker thread per stream, at
+ * most `max_concurrent` at a time (<= 0: no limit).  statuses[i] receives
+ * problem i's mdsip_solve status.  Returns OK when every problem was attempted
+ * (check the statuses), or INVALID_ARG. */
 mdsip_status mdsip_batch_solve(mdsip_problem *const *problems, int32_t count, int32_t max_concurrent,
                                int32_t *statuses);
 

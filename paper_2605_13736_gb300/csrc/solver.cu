@@ -1554,11 +1554,14 @@ mdsip_status mdsip_batch_solve(mdsip_problem *const *problems, int32_t count, in
     if (count < 0 || (count > 0 && (!problems || !statuses))) return MDSIP_ERR_INVALID_ARG;
     for (int32_t i = 0; i < count; ++i)
         if (!problems[i]) return MDSIP_ERR_INVALID_ARG;
-    // one group per context: a context's stream (and its last-error text) is used by one thread
-    std::map<Ctx *, std::vector<int32_t>> by_ctx;
-    for (int32_t i = 0; i < count; ++i) by_ctx[P_(problems[i])->ctx].push_back(i);
+    // one group per stream: a stream (and so each context on it, with its
+    // last-error text) is used by one thread at a time.  Contexts created on
+    // one stream share it; concurrent use from two threads would, among other
+    // things, let one thread's launches enter another thread's stream capture.
+    std::map<cudaStream_t, std::vector<int32_t>> by_stream;
+    for (int32_t i = 0; i < count; ++i) by_stream[P_(problems[i])->ctx->stream].push_back(i);
     std::vector<std::vector<int32_t>> groups;
-    for (auto &kv : by_ctx) groups.push_back(kv.second);
+    for (auto &kv : by_stream) groups.push_back(kv.second);
     const int ngroups = (int)groups.size();
     int nthreads = max_concurrent > 0 ? std::min<int>(max_concurrent, ngroups) : ngroups;
     nthreads = std::max(1, nthreads);

@@ -55,6 +55,38 @@ def test_batch_equals_individual_solves(prec):
             m.mdsip_ctx_destroy(c)
 
 
+def test_batch_contexts_sharing_a_stream():
+    """Several contexts on one CUDA stream (for instance streams handed out by
+    a framework's pool): their problems are solved in turn by one worker, with
+    the results of solving them alone, while other streams run concurrently;
+    graphs are captured on the shared stream (second and later solves)."""
+    torch = torch_cuda()
+    m.build()
+    insts = _instances()
+    shared = torch.cuda.Stream()
+    other = torch.cuda.Stream()
+    ctxs = [m.mdsip_ctx_create(0, (shared if i % 3 else other).cuda_stream) for i in range(len(insts))]
+    probs = []
+    try:
+        for c, inst in zip(ctxs, insts):
+            p = make_problem(c, inst)
+            m.mdsip_set_option_int(p, "precision", m.MDSIP_PREC_BF16, c)
+            probs.append(p)
+        for rep in range(3):
+            statuses = m.mdsip_batch_solve(probs, max_concurrent=8)
+            assert [m.STATUS[s] for s in statuses] == ["OK"] * len(insts)
+        batched = [m.mdsip_get_stats(p) for p in probs]
+        for i, p in enumerate(probs):
+            assert m.STATUS[m.mdsip_solve(p)] == "OK"
+            st = m.mdsip_get_stats(p)
+            assert st["iters"] == batched[i]["iters"] and st["f"] == batched[i]["f"]
+    finally:
+        for p in probs:
+            m.mdsip_problem_destroy(p)
+        for c in ctxs:
+            m.mdsip_ctx_destroy(c)
+
+
 def test_batch_shared_context_runs_sequentially():
     torch = torch_cuda()
     m.build()

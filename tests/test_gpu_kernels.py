@@ -264,6 +264,22 @@ def test_ldlt_fp32_speculation(ctx, N, kind):
         assert acc >= 1 and rej >= 1
 
 
+@pytest.mark.parametrize("N", [2600, 4200])
+def test_ldlt_fp32_speculation_large(ctx, N):
+    """Orders with many panels and (at 4200) the 32-column panels: every panel
+    of a convex Newton-step matrix is kept without interchanges, the inertia is
+    that of numpy.linalg.eigvalsh, and the reconstruction has FP32 accuracy."""
+    rng = np.random.default_rng(N + 11)
+    K = _ipm_like(rng, N - 50, 50)
+    g = _fp32_ldlt(ctx, K, m.MDSIP_LDLT_FP32_UPDATES)
+    ev = np.linalg.eigvalsh(K)
+    assert g["inertia"] == (int((ev > 0).sum()), int((ev < 0).sum()), 0)
+    acc, rej = g["panels"]
+    assert acc >= N // 64 and rej == 0
+    np.testing.assert_array_equal(g["perm"], np.arange(N))
+    assert g["resid"] <= 1e-5
+
+
 def test_ldlt_singular_and_edge_cases(ctx):
     g = _gpu_ldlt(ctx, np.zeros((5, 5)))
     assert g["inertia"] == (0, 0, 5)
