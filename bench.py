@@ -82,7 +82,8 @@ def parse():
     ap.add_argument("--ws-workers", type=int, default=8, help="concurrent problems (contexts)")
     ap.add_argument("--ws-only", action="store_true",
                     help="run only the learned warm-start measurement and print its own JSON line")
-    ap.add_argument("--kernel", choices=["syrk", "syrk_bf16", "syrk_tf32", "ldlt", "ldlt_solve", "gemm_bf16"],
+    ap.add_argument("--kernel", choices=["syrk", "syrk_bf16", "syrk_tf32", "ldlt", "ldlt_solve", "ldlt_library",
+                                         "gemm_bf16"],
                     default=None,
                     help="time one kernel-level C-ABI call instead of the Newton step")
     ap.add_argument("--m", type=int, default=100000, help="--kernel syrk: rows of A")
@@ -699,6 +700,15 @@ def run_kernel(args):
             def call():
                 S.copy_(S0)
                 m.mdsip_ldlt_factor_ex(ctx, N, S, N, 1e-14, flags, L, Dd, Doff, perm, kind, inr)
+            if args.kernel == "ldlt_library":
+                # context only: the vendor library's Bunch-Kaufman (cuSOLVER sytrf behind
+                # torch.linalg.ldl_factor_ex) on the same matrix, full symmetric storage
+                Kf = torch.as_tensor(K).cuda()
+                Kw = torch.empty_like(Kf)
+
+                def call():
+                    Kw.copy_(Kf)
+                    torch.linalg.ldl_factor_ex(Kw, hermitian=False, check_errors=False)
             if args.kernel == "ldlt_solve":
                 call()
                 rhs = torch.randn((4, N), dtype=torch.float64, device="cuda")
@@ -724,7 +734,7 @@ def run_kernel(args):
     out = {"kernel": args.kernel, "m": args.m, "n": args.n, "ms_median": ms, "ms_all": times, "tflops": tf}
     if panels is not None:
         out["panels_no_interchange_kept_handed_back"] = panels
-    if args.kernel in ("syrk", "ldlt", "ldlt_solve"):
+    if args.kernel in ("syrk", "ldlt", "ldlt_solve", "ldlt_library"):
         out["frac_fp64_peak"] = tf / FP64_PEAK_TFLOPS
     else:
         peak = measured_peak("bf16_tflops")
