@@ -245,7 +245,22 @@ __global__ void __launch_bounds__(256) k_aft_dot(const float *__restrict__ AfT, 
     for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
         const float4 *row = reinterpret_cast<const float4 *>(AfT + p * ldt);
         float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-        for (int64_t k = threadIdx.x; k < q; k += 256) {
+        int64_t k = threadIdx.x;
+        for (; k + 768 < q; k += 1024) {   // four 16-byte loads of the row in flight per thread
+            float4 a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = __ldg(row + k + 256 * u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) b[u] = __ldg(v4 + k + 256 * u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                s0 = fmaf(a[u].x, b[u].x, s0);
+                s1 = fmaf(a[u].y, b[u].y, s1);
+                s2 = fmaf(a[u].z, b[u].z, s2);
+                s3 = fmaf(a[u].w, b[u].w, s3);
+            }
+        }
+        for (; k < q; k += 256) {
             const float4 a = __ldg(row + k), b = __ldg(v4 + k);
             s0 = fmaf(a.x, b.x, s0);
             s1 = fmaf(a.y, b.y, s1);
