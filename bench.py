@@ -26,6 +26,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -144,8 +145,7 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                                 f".clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"mdsip_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -295,7 +295,7 @@ def run_batch(args, m, torch, local):
 
 
 def run_warmstart(args, m, torch, local):
-    """Learned warm start on the parametric family (configs[4] structure:
+    """Learned warm start on the parametric family (the benchmark structure at
     n_d = 512, n_s = 51 200, m_E = 25 600, m_I = 50, b = b0 (1 + 0.2 p),
     p in R^64): cold solves of training members -> network trained on the GPU
     -> warm-started solves of held-out members against their cold solves.

@@ -199,7 +199,7 @@ mdsip_status mdsip_get_iterate(mdsip_problem *p, double *packed, int mem);
 /* ---- Learned warm start (not part of the paper's method) -----------------
  * A network maps the parameters of a parametric family to a predicted
  * packed primal-dual point followed by log mu0 (packed_size + 1 values); the
- * plain method started from it remains the judge of the result (E_0 <= tol).
+ * plain method started from it decides whether the result is accepted (E_0 <= tol).
  *
  * mdsip_warmstart_target: after a solve of p, write the training target for
  * that instance: the final packed iterate, then log of the barrier parameter

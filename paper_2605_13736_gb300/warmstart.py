@@ -14,7 +14,7 @@ libmdsip's kernels):
    forward pass, start each solve from its prediction pushed into the
    interior (``mdsip_set_start_predicted``), and fall back to a cold start for
    any member whose warm-started solve does not end with status OK.  The
-   plain method's own termination test (E_0 <= tol) judges every result.
+   plain method's own termination test (E_0 <= tol) decides every result.
 
 The family is described by a callable ``set_member(problem, p)`` that loads
 member p's data into a problem (for the synthetic family: the equality

@@ -108,8 +108,9 @@ def test_solve_matches_oracle_trajectory(ctx, name, path):
 
 
 def test_directions_along_oracle_trajectory(ctx):
-    """Directions from the oracle's own iterates of configs[0] (P2 condensed
-    oracle for the iterates; full 4x4 solve for the reference direction)."""
+    """Directions from the oracle's own iterates of the small instance (n_d = 32;
+    P2 condensed oracle for the iterates, full 4x4 solve for the reference
+    direction)."""
     inst = synth.make_config(0)
     model = SynthModel(inst)
     opt = ipm.Options(linsolve="p2", max_iter=6)
