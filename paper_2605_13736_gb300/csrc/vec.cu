@@ -135,44 +135,59 @@ __global__ void k_jac_hess(Dims D, ModelView M, const double *__restrict__ x,
 // ---------------------------------------------------------------------------
 // A passes
 // ---------------------------------------------------------------------------
-// out = A v: one thread per row, v staged in shared memory.  A row's dot
-// product runs in eight independent FP64 accumulators with no reduction
-// across lanes; a warp's 16-byte loads touch 32 rows at once, and each
-// 32-byte sector serves two consecutive loads of its row through L1.  On GB300
-// an FP64 pass over A is bound by the DFMA rate (2 flop per 8 bytes).
+// out = A v: two threads per row, v staged in shared memory.  The pair reads
+// alternate 16-byte chunks of its row, so each warp load fills 16 whole
+// 32-byte sectors; each thread keeps eight independent FP64 accumulators and
+// loads the next group of its row before using the current one (a pass over A
+// is bound by memory latency at the ~20 rows per SM that one-thread-per-row
+// occupancy gives, and on GB300 by the DFMA rate next: 2 flop per 8 bytes).
 __global__ void __launch_bounds__(NT) k_gemv_rows(const double *__restrict__ A, int64_t m, int64_t n,
                                                   int64_t lda, const double *__restrict__ v,
                                                   double *__restrict__ out) {
-    extern __shared__ double vs[];   // n rounded up to a multiple of 8, zero padded
-    const int64_t n8 = (n + 7) / 8 * 8;
-    for (int64_t k = threadIdx.x; k < n8; k += NT) vs[k] = k < n ? v[k] : 0.0;
+    extern __shared__ double vs[];   // n rounded up to a multiple of 16, zero padded
+    const int64_t n16 = (n + 15) / 16 * 16;
+    for (int64_t k = threadIdx.x; k < n16; k += NT) vs[k] = k < n ? v[k] : 0.0;
     __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
-    if (i >= m) return;
-    const double2 *r = reinterpret_cast<const double2 *>(A + i * lda);
+    const int64_t gt = (int64_t)blockIdx.x * NT + threadIdx.x;
+    const int64_t i = gt >> 1;
+    const int h = (int)(gt & 1);
+    const bool live = i < m;
+    const double2 *r = reinterpret_cast<const double2 *>(A + (live ? i : 0) * lda);
     const double2 *x2 = reinterpret_cast<const double2 *>(vs);
     double acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.0;
-    const int64_t full = n / 8;          // groups of 8 columns (4 pairs) inside the row
-    for (int64_t g = 0; g < full; ++g) {
-        double2 a[4];
+    const int64_t full = live ? n / 16 : 0;   // groups of 16 columns (8 chunks; 4 per thread)
+    double2 cur[4], nxt[4] = {};
+    if (full > 0) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) a[u] = __ldg(r + 4 * g + u);
+        for (int u = 0; u < 4; ++u) cur[u] = __ldg(r + h + 2 * u);
+    }
+    for (int64_t g = 0; g < full; ++g) {
+        if (g + 1 < full) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) nxt[u] = __ldg(r + 8 * (g + 1) + h + 2 * u);
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const double2 b = x2[4 * g + u];
-            acc[2 * u] = fma(a[u].x, b.x, acc[2 * u]);
-            acc[2 * u + 1] = fma(a[u].y, b.y, acc[2 * u + 1]);
+            const double2 b = x2[8 * g + h + 2 * u];
+            acc[2 * u] = fma(cur[u].x, b.x, acc[2 * u]);
+            acc[2 * u + 1] = fma(cur[u].y, b.y, acc[2 * u + 1]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cur[u] = nxt[u];
+    }
+    if (live && h == 0) {
+        const double *rd = A + i * lda;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {   // ragged tail (fewer than 16 columns)
+            const int64_t c = 16 * full + t;
+            if (c < n) acc[t & 7] = fma(rd[c], vs[c], acc[t & 7]);
         }
     }
-    const double *rd = A + i * lda;
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {   // ragged tail (fewer than 8 columns)
-        const int64_t c = 8 * full + t;
-        if (c < n) acc[t] = fma(rd[c], vs[c], acc[t]);
-    }
-    out[i] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    double sum = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    sum += __shfl_xor_sync(0xffffffffu, sum, 1);   // the pair's halves (every lane reaches this)
+    if (live && h == 0) out[i] = sum;
 }
 
 // partial[b][p] = sum over the rows of block b of A[i][p] u[i]
@@ -768,19 +783,19 @@ void launch_finalize_min(cudaStream_t s, const double *partial, int nq, double *
 
 static int elem_grid(int64_t n) { return std::max(1, std::min(4096, ceil_div(n, 256))); }
 
-// A: rows 16-byte aligned (lda even, A 16-byte aligned); n <= 24568 (v staged in shared memory)
+// A: rows 16-byte aligned (lda even, A 16-byte aligned); n <= 24560 (v staged in shared memory)
 void launch_gemv_rows(cudaStream_t s, const double *A, int64_t m, int64_t n, int64_t lda,
                       const double *v, double *out) {
     if (m <= 0) return;
     MDSIP_REQUIRE((lda & 1) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0, MDSIP_ERR_INVALID_ARG,
                   "gemv: rows of A must be 16-byte aligned");
-    const size_t smem = (size_t)((n + 7) / 8) * 8 * sizeof(double);
+    const size_t smem = (size_t)((n + 15) / 16) * 16 * sizeof(double);
     MDSIP_REQUIRE(smem <= 192 * 1024, MDSIP_ERR_INVALID_ARG, "gemv: n too large");
     static PerDeviceOnce once;
     MDSIP_CUDA(once.run([] {
         return cudaFuncSetAttribute(k_gemv_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 192 * 1024);
     }));
-    const int64_t grid = ceil_div(m, NT);
+    const int64_t grid = (2 * m + NT - 1) / NT;   // two threads per row
     MDSIP_REQUIRE(grid <= 0x7fffffff, MDSIP_ERR_INVALID_ARG, "gemv: m too large");
     k_gemv_rows<<<(unsigned)grid, NT, smem, s>>>(A, m, n, lda, v, out);
     MDSIP_LAUNCHED();
