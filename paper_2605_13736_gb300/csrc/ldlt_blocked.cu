@@ -25,8 +25,12 @@
 //   column updates also take FP32 products (from FP32 shadows of L and of the
 //   broadcast W row): at 1/64 of the FP32 rate, FP64 products were the largest
 //   part of each column's time.
+// Mixed-precision path: each panel is first factored without interchanges and
+// kept when the pivot rule's tests confirm every pivot (k_bk_spec,
+// k_bk_spec_rows, below); k_bk_panel then returns at once.
 // Panel state (next column, inertia counts) lives in device memory, so the
-// host enqueues all panels without reading anything back.
+// host enqueues all panels without reading anything back; the panel loop's
+// kernels use programmatic dependent launch.
 #include <cooperative_groups.h>
 
 #include <algorithm>
