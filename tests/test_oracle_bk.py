@@ -97,3 +97,47 @@ def test_bk_singular_and_special_cases():
     fac = bk_ldlt(np.outer(v, v) + np.outer([1.0, 0, -1.0], [1.0, 0, -1.0]))
     assert fac["inertia"] == (2, 0, 1)
     assert 0.6 < ALPHA < 0.65
+
+
+def _ldlt_no_pivoting(K):
+    """Textbook LDL^T without interchanges (right-looking, 1x1 pivots)."""
+    a = np.array(K, dtype=float)
+    n = a.shape[0]
+    L = np.eye(n)
+    d = np.zeros(n)
+    for j in range(n):
+        d[j] = a[j, j]
+        L[j + 1:, j] = a[j + 1:, j] / d[j]
+        a[j + 1:, j + 1:] -= np.outer(L[j + 1:, j], a[j + 1:, j])
+    return L, d
+
+
+@pytest.mark.parametrize("case", ["dominant", "row_test_keeps"])
+def test_bk_without_interchanges_is_the_unpivoted_factor(case):
+    """The reading behind the mixed-precision factorization's no-interchange
+    panels: when the Bunch-Kaufman rule keeps every diagonal pivot (1x1, no
+    interchange, including columns that pass only the row test), its factor is
+    the LDL^T factor without pivoting."""
+    rng = np.random.default_rng(17)
+    n = 60
+    if case == "dominant":
+        g = rng.standard_normal((n, n))
+        K = 0.1 * (g + g.T) + np.diag(rng.uniform(2.0, 4.0, n))
+    else:
+        # column j: |a_jj| = 1 < alpha * 2 fails the column test; row r = 59 - j
+        # holds 2 at (r, j) and 3 at (r, j + 1), so rowmax 3 passes the row test
+        K = 10.0 * np.eye(n)
+        for j, r in ((0, 59), (7, 58), (14, 57)):
+            K[j, j] = 1.0
+            K[r, j] = K[j, r] = 2.0
+            K[r, j + 1] = K[j + 1, r] = 3.0
+            K[r, r] = 100.0
+    f = bk_ldlt(K)
+    np.testing.assert_array_equal(f["perm"], np.arange(n))
+    assert list(f["kind"]) == [1] * n
+    if case == "row_test_keeps":   # the column test really fails at these columns
+        for j in (0, 7, 14):
+            assert abs(K[j, j]) < ALPHA * 2.0
+    L, d = _ldlt_no_pivoting(K)
+    np.testing.assert_allclose(f["L"], L, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(np.diag(f["D"]), d, rtol=1e-12)
