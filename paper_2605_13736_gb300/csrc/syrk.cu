@@ -109,23 +109,42 @@ __global__ void __launch_bounds__(SYRK_THREADS, 2) k_syrk_fp64(SyrkArgs a) {
 #pragma unroll
         for (int j = 0; j < TM; ++j) acc[i][j] = 0.0;
 
+    // On a diagonal tile (p0 == q0) the accumulators (i, j > i) hold only
+    // entries above the diagonal (q - p = ty - tx + 16 (j - i) > 0): they are
+    // skipped for every thread alike, 40% of the tile's FMAs at TM = 5.
+    const bool diag = tp == tq;
     if (kbeg < kend) load(kbeg);
     for (int64_t k0 = kbeg; k0 < kend; k0 += KB) {
         __syncthreads();
         store();
         __syncthreads();
         if (k0 + KB < kend) load(k0 + KB);
+        if (diag) {
 #pragma unroll
-        for (int kk = 0; kk < KB; ++kk) {
-            double av[TM], bv[TM];
+            for (int kk = 0; kk < KB; ++kk) {
+                double av[TM], bv[TM];
 #pragma unroll
-            for (int i = 0; i < TM; ++i) av[i] = As[kk][tx + 16 * i];
+                for (int i = 0; i < TM; ++i) av[i] = As[kk][tx + 16 * i];
 #pragma unroll
-            for (int j = 0; j < TM; ++j) bv[j] = Bs[kk][ty + 16 * j];
+                for (int j = 0; j < TM; ++j) bv[j] = Bs[kk][ty + 16 * j];
 #pragma unroll
-            for (int i = 0; i < TM; ++i)
+                for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TM; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+                    for (int j = 0; j <= i; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+            }
+        } else {
+#pragma unroll
+            for (int kk = 0; kk < KB; ++kk) {
+                double av[TM], bv[TM];
+#pragma unroll
+                for (int i = 0; i < TM; ++i) av[i] = As[kk][tx + 16 * i];
+#pragma unroll
+                for (int j = 0; j < TM; ++j) bv[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+                for (int i = 0; i < TM; ++i)
+#pragma unroll
+                    for (int j = 0; j < TM; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+            }
         }
     }
     // epilogue: lower triangle only
