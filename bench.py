@@ -43,7 +43,7 @@ FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12   # 128 FP32 lanes per SM, 2 flop p
 # m_E = 100000, scaled from an ncu capture of the current kernel at m = 20000
 # (profiles/syrk_fp64_m20000_n2000.md): reads of A grow with m, the split
 # partial writes do not.
-SYRK_TRAFFIC_BYTES = 5 * 326.235648e6 + 183.443456e6
+SYRK_TRAFFIC_BYTES = 5 * 326.793216e6 + 183.695104e6
 
 
 def measured_peak(key):
