@@ -10,8 +10,9 @@
 // fewest FMAs on the ragged edge and the diagonal tiles), 4x4 or 5x5
 // accumulators per thread, 16-row K slabs staged in shared memory with
 // 16-byte loads and register prefetch, the reciprocals 1/w computed once per
-// call, and split-K chosen so that the (tile, split) work items fill whole
-// waves of the 152 SMs.  Split partials are summed in fixed order
+// call, diagonal tiles skipping the accumulators that hold only entries above
+// the diagonal, and split-K chosen so that the (tile, split) work items fill
+// whole waves of the 152 SMs.  Split partials are summed in fixed order
 // (deterministic).
 #include <algorithm>
 
