@@ -170,14 +170,24 @@ void mdsip_problem_destroy(mdsip_problem *p);
  *           shape; 0: the analytic choices),
  *           ldlt_spec (1, default: the mixed-precision factorization's
  *           panels first try the verified no-interchange path described at
- *           mdsip_ldlt_factor_ex; 0: every panel pivots)
+ *           mdsip_ldlt_factor_ex; 0: every panel pivots),
+ *           direction_check (0, default; 1: every step of a mixed-precision
+ *           solve also computes the FP64 direction from the same iterate and
+ *           shifts and logs the relative gap as dir_err_fp64 -- an extra FP64
+ *           product and factorization per step, counted in the statistics;
+ *           the solve itself takes the mixed-precision direction as before)
  *   double: tol, mu0, kappa_eps, kappa_mu, theta_mu, tau_min, s_max, kappa_1,
  *           kappa_2, kappa_sigma, gamma_theta, gamma_phi, delta, s_theta, s_phi,
  *           eta_phi, gamma_alpha, dw0, dw_min, dw_max, kw_minus, kw_plus,
- *           kw_plus_bar, dc_bar, kappa_c, zero_tol, time_limit_s
- * Unknown names: INVALID_ARG. */
+ *           kw_plus_bar, dc_bar, kappa_c, zero_tol, time_limit_s, refine_tol,
+ *           refine_fallback_tol
+ *   string: path ("auto" | "p1" | "p2"), precision ("fp64" | "tf32" | "bf16"),
+ *           and graphs / autotune / ldlt_spec as "yes" | "no" -- the same
+ *           settings as the int options of those names, by word.
+ * Unknown names or values: INVALID_ARG (the option keeps its value). */
 mdsip_status mdsip_set_option_int(mdsip_problem *p, const char *name, int64_t value);
 mdsip_status mdsip_set_option_double(mdsip_problem *p, const char *name, double value);
+mdsip_status mdsip_set_option_str(mdsip_problem *p, const char *name, const char *value);
 
 /* Packed primal-dual layout used by set_start / get_iterate / debug_direction:
  *   [x (n) | d (m_I) | y_g (m_E) | y_h (m_I) | z_l (n) | z_u (n) | v_l (m_I) | v_u (m_I)]
@@ -258,6 +268,17 @@ typedef struct {
     int32_t n_refine;                   /* refinement sweeps of this step         */
     int32_t fp64_fallback;              /* 1 if the step was re-factored in FP64  */
     double refine_res;                  /* final ||b - K u||inf / (||b|| + ||K u||) */
+    int32_t factor_inertia[3];          /* (pos, neg, zero) of the factor the direction
+                                           was solved with: after an FP64 re-factorization
+                                           that factor's, which must equal the target; when
+                                           it did not, Algorithm IC was rerun on FP64 factors
+                                           and its attempts follow in ic_*                  */
+    int32_t pad_;
+    double dir_err_fp64;                /* with the option direction_check on a
+                                           mixed-precision solve: ||D - D_64||_2 / ||D_64||_2
+                                           between the step's direction D and the FP64
+                                           direction D_64 from the same iterate and shifts
+                                           (FP64 product and factorization); -1 otherwise */
 } mdsip_iter_rec;
 /* Copy up to `cap` per-iteration records; *n receives the number available. */
 mdsip_status mdsip_get_log(mdsip_problem *p, mdsip_iter_rec *buf, int32_t cap, int32_t *n);
@@ -274,6 +295,15 @@ mdsip_status mdsip_debug_direction(mdsip_problem *p, const double *packed, doubl
 
 /* Number of CUDA kernels this library has launched in the process so far. */
 int64_t mdsip_launch_count(void);
+
+/* Measurement aid (the paper has no counterpart): the FP64 fused multiply-add
+ * rate that bounds the FP64 condensation product and factorization.  Launches
+ * `blocks` x 256 threads on the context's stream; every thread performs
+ * iters x 8 independent FP64 FMAs (2 flop each) and writes one double to
+ * sink (device, blocks x 256 doubles, owned by the caller).  Returns once the
+ * launch is enqueued; time it with events on the context's stream.
+ * blocks <= 0, iters <= 0 or sink == NULL: INVALID_ARG. */
+mdsip_status mdsip_probe_fp64_fma(mdsip_ctx *ctx, int32_t blocks, int64_t iters, double *sink);
 
 /* ------------------------------------------------------------------------- */
 /* Kernel-level entry points (device pointers, context stream).              */
@@ -349,7 +379,8 @@ mdsip_status mdsip_ldlt_panel_counts(mdsip_ctx *ctx, int32_t *out2);
  *     library routine);
  *   - the first call on a device looks up the array's device address
  *     (set-up, once per device); make that first call before any stream
- *     capture;
+ *     capture.  The address is kept for the life of the process: after a
+ *     cudaDeviceReset of that device do not call this entry point again;
  *   - every call shares the array: calls that overlap on the GPU (on two
  *     streams, or from two host threads) race and must not be issued.
  * The call returns after the factorization has finished (it reads a device

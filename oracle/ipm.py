@@ -30,9 +30,16 @@ One iteration (W&B Algorithm A, no second-order correction, no restoration):
 
 Readings where the paper is silent are collected in `Options`.
 Pinned by tests/test_oracle_ipm.py: closed-form optima of convex instances
-(equality QP, ball constraint with known multiplier, box projection), KKT
-error at exit, the inertia of every accepted factorization, and the descent
-and sufficient-decrease conditions of every accepted step.
+(equality QP, ball constraint with known multiplier, box projection), a
+library optimizer's optimum, the KKT error at exit and the target inertia of
+every accepted factorization.  The step rules are pinned one by one on
+hand-worked values by tests/test_oracle_ipm_rules.py: `fraction_to_boundary`
+and `step_to_boundary`, `kkt_error`'s s_d/s_c scalings, `next_mu`,
+`alpha_min`, `trial_acceptable` (switching condition, Armijo, sufficient
+decrease, the theta_min branch, theta_max, the filter), `filter_entry`, the
+Algorithm IC shift schedule of `compute_direction`, `_push` and
+`kappa_sigma_safeguard`.  How `solve` strings these together (the order of
+A.3-A.7) is pinned only through the closed-form optima above.
 """
 from __future__ import annotations
 
@@ -243,6 +250,85 @@ def fraction_to_boundary(tau, vals, steps):
     return a
 
 
+def step_to_boundary(P: Problem, pt: Point, dx, dd, dz, tau):
+    """alpha_max and alpha_z of one direction (W&B eqs. (15) and (14b)).
+
+    alpha_max keeps every slack to a finite bound at least (1 - tau) of its
+    current value: x - x^l moves by +dx, x^u - x by -dx, d - h^l by +dd and
+    h^u - d by -dd.  alpha_z does the same for the bound multipliers
+    (z_l, z_u, v_l, v_u) and their steps dz = (dzl, dzu, dvl, dvu).  Entries
+    without a finite bound take no part."""
+    sl, su, tl, tu = P.slacks(pt.x, pt.d)
+    hxl, hxu, hdl, hdu = P.masks()
+    dzl, dzu, dvl, dvu = dz
+    alpha_max = fraction_to_boundary(tau, [sl[hxl], su[hxu], tl[hdl], tu[hdu]],
+                                     [dx[hxl], -dx[hxu], dd[hdl], -dd[hdu]])
+    alpha_z = fraction_to_boundary(tau, [pt.zl[hxl], pt.zu[hxu], pt.vl[hdl], pt.vu[hdu]],
+                                   [dzl[hxl], dzu[hxu], dvl[hdl], dvu[hdu]])
+    return alpha_max, alpha_z
+
+
+def kappa_sigma_safeguard(z, s, mu, kappa_sigma):
+    """Keep each bound multiplier within [mu / (kappa_sigma s), kappa_sigma mu / s]
+    of its slack s (W&B eq. (16)), so that the primal-dual Sigma stays within a
+    factor kappa_sigma of the primal barrier Hessian mu / s^2."""
+    return np.maximum(np.minimum(z, kappa_sigma * mu / s), mu / (kappa_sigma * s))
+
+
+def next_mu(mu, opt: Options):
+    """Barrier parameter after the subproblem for mu is solved (W&B eq. (7)):
+    the smaller of a linear (kappa_mu mu) and a superlinear (mu^theta_mu)
+    decrease, never below tol/10."""
+    return max(opt.tol / 10.0, min(opt.kappa_mu * mu, mu ** opt.theta_mu))
+
+
+def alpha_min(th_k, gphi, theta_min, opt: Options):
+    """Smallest step before the backtracking gives up (W&B eq. (23)).
+
+    With a descent direction (gphi < 0) the bound is gamma_alpha times the
+    smallest of gamma_theta, gamma_phi theta_k / (-gphi) and, when theta_k is
+    already small (<= theta_min), delta theta_k^s_theta / (-gphi)^s_phi;
+    otherwise gamma_alpha gamma_theta."""
+    if gphi < 0 and th_k <= theta_min:
+        return opt.gamma_alpha * min(opt.gamma_theta, opt.gamma_phi * th_k / (-gphi),
+                                     opt.delta * th_k ** opt.s_theta / (-gphi) ** opt.s_phi)
+    if gphi < 0:
+        return opt.gamma_alpha * min(opt.gamma_theta, opt.gamma_phi * th_k / (-gphi))
+    return opt.gamma_alpha * opt.gamma_theta
+
+
+def trial_acceptable(th_t, phi_t, inside, th_k, phi_k, gphi, alpha, theta_min, theta_max, filt,
+                     opt: Options):
+    """Acceptance test of one trial point (W&B Section 2.3, A-5.2 to A-5.4).
+
+    switching condition (eq. (19)): gphi < 0 and alpha (-gphi)^s_phi > delta theta_k^s_theta;
+    Armijo (eq. (20)): phi_t <= phi_k + eta_phi alpha gphi.
+    If theta_k <= theta_min and the switching condition holds, the trial must
+    satisfy Armijo; otherwise it must reduce theta or phi sufficiently
+    (eq. (18): theta_t <= (1 - gamma_theta) theta_k or phi_t <= phi_k - gamma_phi theta_k).
+    In both cases it must lie below theta_max and outside every filter entry
+    (a pair (a, b) excludes theta_t >= a together with phi_t >= b).  A trial
+    outside the bounds (inside = False) or with a non-finite value is rejected.
+    Returns (accepted, switching, armijo)."""
+    ftype = gphi < 0 and alpha * (-gphi) ** opt.s_phi > opt.delta * th_k ** opt.s_theta
+    armijo = phi_t <= phi_k + opt.eta_phi * alpha * gphi
+    ok = False
+    if inside and np.isfinite(phi_t) and np.isfinite(th_t):
+        if th_k <= theta_min and ftype:
+            ok = armijo
+        else:
+            ok = th_t <= (1 - opt.gamma_theta) * th_k or phi_t <= phi_k - opt.gamma_phi * th_k
+        if ok:
+            ok = th_t < theta_max and not any(th_t >= a and phi_t >= b for a, b in filt)
+    return ok, ftype, armijo
+
+
+def filter_entry(th_k, phi_k, opt: Options):
+    """Corner point added to the filter after a step that was not of f-type with
+    Armijo (W&B eq. (22))."""
+    return ((1 - opt.gamma_theta) * th_k, phi_k - opt.gamma_phi * th_k)
+
+
 def compute_direction(P: Problem, pt: Point, ev: Evals, mu, opt: Options, state):
     """W&B Algorithm IC around the chosen linear solve; returns (dir, attempts)."""
     sy = newton_system(P, pt, ev, mu)
@@ -303,7 +389,7 @@ def solve(model, x0=None, opt: Options | None = None, start: Point | None = None
         while True:
             Emu = kkt_error(P, pt, ev, mu, opt)[0]
             if Emu <= opt.kappa_eps * mu:
-                mu_new = max(opt.tol / 10.0, min(opt.kappa_mu * mu, mu ** opt.theta_mu))
+                mu_new = next_mu(mu, opt)
                 if mu_new == mu:
                     break
                 mu = mu_new
@@ -327,23 +413,14 @@ def solve(model, x0=None, opt: Options | None = None, start: Point | None = None
         # A.5 line search
         sl, su, tl, tu = P.slacks(pt.x, pt.d)
         hxl, hxu, hdl, hdu = P.masks()
-        alpha_max = fraction_to_boundary(tau, [sl[hxl], su[hxu], tl[hdl], tu[hdu]],
-                                         [dx[hxl], -dx[hxu], dd[hdl], -dd[hdu]])
-        alpha_z = fraction_to_boundary(tau, [pt.zl[hxl], pt.zu[hxu], pt.vl[hdl], pt.vu[hdu]],
-                                       [dzl[hxl], dzu[hxu], dvl[hdl], dvu[hdu]])
+        alpha_max, alpha_z = step_to_boundary(P, pt, dx, dd, (dzl, dzu, dvl, dvu), tau)
         phi_k = barrier_phi(P, ev.f, pt.x, pt.d, mu)
         th_k = theta(ev)
         # directional derivative of the barrier objective
         gphi_x = ev.grad - np.where(hxl, mu / np.where(hxl, sl, 1.0), 0.0) + np.where(hxu, mu / np.where(hxu, su, 1.0), 0.0)
         gphi_d = -np.where(hdl, mu / np.where(hdl, tl, 1.0), 0.0) + np.where(hdu, mu / np.where(hdu, tu, 1.0), 0.0)
         gphi = float(gphi_x @ dx + gphi_d @ dd)
-        if gphi < 0 and th_k <= theta_min:
-            a_min = opt.gamma_alpha * min(opt.gamma_theta, opt.gamma_phi * th_k / (-gphi),
-                                          opt.delta * th_k ** opt.s_theta / (-gphi) ** opt.s_phi)
-        elif gphi < 0:
-            a_min = opt.gamma_alpha * min(opt.gamma_theta, opt.gamma_phi * th_k / (-gphi))
-        else:
-            a_min = opt.gamma_alpha * opt.gamma_theta
+        a_min = alpha_min(th_k, gphi, theta_min, opt)
         alpha = alpha_max
         n_ls = 0
         accepted = False
@@ -356,16 +433,8 @@ def solve(model, x0=None, opt: Options | None = None, start: Point | None = None
                       and np.all(tl_t[hdl] > 0) and np.all(tu_t[hdu] > 0))
             th_t = theta(evt)
             phi_t = barrier_phi(P, evt.f, xt, dt, mu) if inside else np.inf
-            ftype = gphi < 0 and alpha * (-gphi) ** opt.s_phi > opt.delta * th_k ** opt.s_theta
-            armijo = phi_t <= phi_k + opt.eta_phi * alpha * gphi
-            ok = False
-            if inside and np.isfinite(phi_t) and np.isfinite(th_t):
-                if th_k <= theta_min and ftype:
-                    ok = armijo
-                else:
-                    ok = th_t <= (1 - opt.gamma_theta) * th_k or phi_t <= phi_k - opt.gamma_phi * th_k
-                if ok:
-                    ok = th_t < theta_max and not any(th_t >= a and phi_t >= b for a, b in filt)
+            ok, ftype, armijo = trial_acceptable(th_t, phi_t, inside, th_k, phi_k, gphi, alpha,
+                                                 theta_min, theta_max, filt, opt)
             if ok:
                 accepted = True
                 break
@@ -381,7 +450,7 @@ def solve(model, x0=None, opt: Options | None = None, start: Point | None = None
         rec.update(alpha=alpha, ftype=bool(ftype and armijo))
         # A.7 filter augmentation (before moving the reference point)
         if not (ftype and armijo):
-            filt.append(((1 - opt.gamma_theta) * th_k, phi_k - opt.gamma_phi * th_k))
+            filt.append(filter_entry(th_k, phi_k, opt))
         # A.6 accept
         pt.x, pt.d = xt, dt
         pt.yg = pt.yg + alpha * dyg
@@ -392,10 +461,8 @@ def solve(model, x0=None, opt: Options | None = None, start: Point | None = None
         pt.vu = pt.vu + alpha_z * dvu
         # kappa_Sigma safeguard (W&B eq. (16))
         sl, su, tl, tu = P.slacks(pt.x, pt.d)
-        ks = opt.kappa_sigma
         for z, s, msk in ((pt.zl, sl, hxl), (pt.zu, su, hxu), (pt.vl, tl, hdl), (pt.vu, tu, hdu)):
-            sm = s[msk]
-            z[msk] = np.maximum(np.minimum(z[msk], ks * mu / sm), mu / (ks * sm))
+            z[msk] = kappa_sigma_safeguard(z[msk], s[msk], mu, opt.kappa_sigma)
         ev = evt
         log.append(rec)
         k += 1

@@ -83,7 +83,8 @@ class mdsip_iter_rec(C.Structure):
                 ("alpha_max", C.c_double), ("alpha_z", C.c_double), ("gphi", C.c_double),
                 ("ic_dw", C.c_double * MDSIP_MAX_IC), ("ic_dc", C.c_double * MDSIP_MAX_IC),
                 ("ic_inertia", (C.c_int32 * 3) * MDSIP_MAX_IC),
-                ("n_refine", C.c_int32), ("fp64_fallback", C.c_int32), ("refine_res", C.c_double)]
+                ("n_refine", C.c_int32), ("fp64_fallback", C.c_int32), ("refine_res", C.c_double),
+                ("factor_inertia", C.c_int32 * 3), ("pad_", C.c_int32), ("dir_err_fp64", C.c_double)]
 
 
 _lib = None
@@ -103,6 +104,8 @@ _SIGS = {
     "mdsip_problem_destroy": (None, [C.c_void_p]),
     "mdsip_set_option_int": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int64]),
     "mdsip_set_option_double": (C.c_int, [C.c_void_p, C.c_char_p, C.c_double]),
+    "mdsip_set_option_str": (C.c_int, [C.c_void_p, C.c_char_p, C.c_char_p]),
+    "mdsip_probe_fp64_fma": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_void_p]),
     "mdsip_packed_size": (C.c_int64, [C.c_void_p]),
     "mdsip_set_start": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int]),
     "mdsip_solve": (C.c_int, [C.c_void_p]),
@@ -207,14 +210,57 @@ def mdsip_status_str(status: int) -> str:
     return lib().mdsip_status_str(status).decode()
 
 
-def mdsip_ctx_create(device: int = 0, stream: int | None = None):
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class mdsip_alloc_hooks(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+_HOOKS_KEEPALIVE = {}
+
+
+def torch_alloc_hooks(device: int):
+    """Allocation hooks that take the library's device buffers from torch's
+    caching allocator on the context's stream, so that the library and torch
+    share one pool instead of holding separate cudaMalloc reservations."""
+    import torch
+
+    def alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, int(stream or 0))
+        except Exception:      # out of memory: the library reports MDSIP_ERR_OOM
+            return None
+
+    def free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return mdsip_alloc_hooks(ALLOC_FN(alloc), FREE_FN(free), None)
+
+
+def mdsip_ctx_create(device: int = 0, stream: int | None = None, allocator="torch"):
+    """allocator: "torch" (default: torch's caching allocator through the
+    library's allocation hooks), "cuda" (no hooks: cudaMalloc / cudaFree), or an
+    `mdsip_alloc_hooks` structure of the caller's (kept alive with the context)."""
+    if allocator == "torch":
+        hooks = torch_alloc_hooks(device)
+    elif allocator == "cuda":
+        hooks = None
+    elif isinstance(allocator, mdsip_alloc_hooks):
+        hooks = allocator
+    else:
+        raise ValueError(f"allocator must be 'torch', 'cuda' or mdsip_alloc_hooks, not {allocator!r}")
     h = C.c_void_p()
-    _check(lib().mdsip_ctx_create(device, stream, None, C.byref(h)))
+    _check(lib().mdsip_ctx_create(device, stream, C.byref(hooks) if hooks is not None else None, C.byref(h)))
+    if hooks is not None:
+        _HOOKS_KEEPALIVE[h.value] = hooks
     return h.value
 
 
 def mdsip_ctx_destroy(ctx):
     lib().mdsip_ctx_destroy(ctx)
+    _HOOKS_KEEPALIVE.pop(ctx, None)
 
 
 def mdsip_ctx_last_error(ctx) -> str:
@@ -274,6 +320,14 @@ def mdsip_set_option_double(prob, name: str, value: float, ctx=None):
     _check(lib().mdsip_set_option_double(prob, name.encode(), float(value)), ctx)
 
 
+def mdsip_probe_fp64_fma(ctx, blocks: int, iters: int, sink):
+    _check(lib().mdsip_probe_fp64_fma(ctx, int(blocks), int(iters), _ptr(sink)), ctx)
+
+
+def mdsip_set_option_str(prob, name: str, value: str, ctx=None):
+    _check(lib().mdsip_set_option_str(prob, name.encode(), value.encode()), ctx)
+
+
 def mdsip_packed_size(prob) -> int:
     return lib().mdsip_packed_size(prob)
 
@@ -317,7 +371,9 @@ def mdsip_get_log(prob) -> list:
     _check(lib().mdsip_get_log(prob, buf, n.value, C.byref(n)))
     out = []
     for r in buf[:n.value]:
-        rec = {k: getattr(r, k) for k, _ in mdsip_iter_rec._fields_ if not k.startswith("ic_")}
+        rec = {k: getattr(r, k) for k, _ in mdsip_iter_rec._fields_
+               if not k.startswith("ic_") and k not in ("factor_inertia", "pad_")}
+        rec["factor_inertia"] = tuple(r.factor_inertia)
         k = min(r.n_ic, MDSIP_MAX_IC)
         rec["ic"] = [(r.ic_dw[i], r.ic_dc[i], tuple(r.ic_inertia[i])) for i in range(k)]
         out.append(rec)

@@ -145,6 +145,7 @@ struct Options {
     int64_t graphs = 1;               // 1: replay the factorization phase as a CUDA graph
     int64_t autotune = 1;             // 1: time tile-shape candidates at first use per shape
     int64_t ldlt_spec = 1;            // 1: mixed-precision LDL^T panels try the verified no-interchange path
+    int64_t direction_check = 0;      // 1: each mixed-precision step also forms the FP64 direction and logs the gap
 };
 
 // ---------------------------------------------------------------------------
@@ -297,6 +298,9 @@ struct PerDeviceOnce {
 // Kernel launchers (defined in the .cu files).
 // ---------------------------------------------------------------------------
 // reductions: partial[k * kRedBlocks + b] -> scalars[first + k] (sum / max / min)
+// probe.cu: blocks x 256 threads, each iters x 8 independent FP64 FMAs; sink
+// holds blocks x 256 doubles
+void launch_fp64_fma_probe(cudaStream_t s, int blocks, int64_t iters, double *sink);
 void launch_finalize_sum(cudaStream_t s, const double *partial, int nq, double *out);
 void launch_finalize_max(cudaStream_t s, const double *partial, int nq, double *out);
 void launch_finalize_min(cudaStream_t s, const double *partial, int nq, double *out);

@@ -545,7 +545,7 @@ __global__ void k_maxabs_lower(int64_t N, const double *S, int64_t ld, double *p
 
 }  // namespace
 
-static size_t ldlt_unblocked_scratch_bytes(int64_t N) {
+static constexpr size_t ldlt_unblocked_scratch_bytes(int64_t N) {
     // ping-pong buffer (N x N), then 64 bytes of barrier/flag words, then the
     // per-step pivot slots (N + 1 maxima and indices)
     const size_t b = (size_t)N * (size_t)N * sizeof(double) + 64 +
@@ -661,9 +661,9 @@ void launch_ldlt_solve(cudaStream_t s, int64_t N, const double *L, const double 
 // ---------------------------------------------------------------------------
 constexpr int64_t kNoAllocMaxN = 1024;
 constexpr size_t kNoAllocBytes = (size_t)kNoAllocMaxN * kNoAllocMaxN * sizeof(double) + 16384;
-static_assert((size_t)kNoAllocMaxN * kNoAllocMaxN * sizeof(double) + 64 +
-                      (size_t)(kNoAllocMaxN + 1) * (sizeof(unsigned long long) + sizeof(int)) + 256 + 256 +
-                      (size_t)(kRedBlocks + 1) * sizeof(double) <=
+// the layout below: [factor scratch, rounded up to 256 | error flag (256) |
+// kRedBlocks partials | max |S|], for the largest accepted order
+static_assert(ldlt_unblocked_scratch_bytes(kNoAllocMaxN) + 256 + (size_t)(kRedBlocks + 1) * sizeof(double) <=
                   kNoAllocBytes,
               "fixed scratch too small for the factorization's layout");
 static __device__ __align__(256) unsigned char g_ldlt_fixed_scratch[kNoAllocBytes];
@@ -675,7 +675,10 @@ void *g_fixed_addr[256] = {};  // device address of the array, per device ordina
 
 // Host-side address of the fixed array on `device` (which must be current).
 // The array's name in host code is only a stand-in; the device address comes
-// from cudaGetSymbolAddress, looked up once per device.
+// from cudaGetSymbolAddress, looked up once per device and kept for the
+// process: after cudaDeviceReset (which unloads the module with the array)
+// the kept address is stale, so the entry point must not be called again in
+// that process.
 static void *fixed_scratch_address(int device) {
     MDSIP_REQUIRE(device >= 0 && device < 256, MDSIP_ERR_INVALID_ARG, "device ordinal out of range");
     std::lock_guard<std::mutex> lk(g_fixed_mu);

@@ -81,6 +81,7 @@ enum : int {
     SC_TRIAL = 22,   // 2: sum log s, #non-positive slacks
     SC_MAXABS = 24,
     SC_REF = 25,     // 4: ||r||inf, ||b||inf, ||K u||inf, ||u||inf
+    SC_DCHK = 29,    // 2: sum (mixed - FP64 direction)^2, sum (FP64 direction)^2
     SC_COUNT = 32
 };
 
@@ -101,6 +102,8 @@ struct Problem {
     // iterate, trial, direction
     DBuf bx, bd, byg, byh, bzl, bzu, bvl, bvu, bxt, bdt;
     DBuf bdx, bdd, bdyg, bdyh, bdzl, bdzu, bdvl, bdvu;
+    DBuf bcx, bcd, bcyg, bcyh, bczl, bczu, bcvl, bcvu;   // saved direction of the FP64 check
+    DirView Dchk{};
     // model values and Newton quantities
     DBuf bgrad, bgrad_t, bcg, bcg_t, bch, bch_t, bgl, bATy, bJdh, bHss, bHdd;
     DBuf bsig_x, bq, bsig_d, bw, bbt_g, bu, bATu, brhs, bAdx;
@@ -862,7 +865,8 @@ static void solve_direction(Problem *P, double mu, double dw) {
 struct RefineResult {
     bool ok;
     int sweeps;
-    double res;  // ||b - K u||inf / (||b||inf + ||K u||inf)
+    double res;              // ||b - K u||inf / (||b||inf + ||K u||inf)
+    bool fell_back = false;  // re-factored with the FP64 product after refinement stalled
 };
 
 // Direction through the FP64 residual of the unreduced system, refined with
@@ -949,26 +953,30 @@ static void check_solve_flag(Problem *P) {
     MDSIP_REQUIRE(P->hint[6] == 0, MDSIP_ERR_DEVICE, "LDL^T solve: a bounded device wait expired");
 }
 
-static RefineResult direction_step_(Problem *P, double mu, double dw, double dc);
+static RefineResult direction_step_(Problem *P, double mu, double dw, double dc, bool fp64, Inertia *used);
 
-static RefineResult direction_step(Problem *P, double mu, double dw, double dc) {
-    const RefineResult r = direction_step_(P, mu, dw, dc);
+// `used` holds the inertia of the current factor on entry; after an FP64
+// re-factorization it receives that factor's inertia, which the caller checks
+// against the target before taking the direction.
+static RefineResult direction_step(Problem *P, double mu, double dw, double dc, bool fp64, Inertia *used) {
+    const RefineResult r = direction_step_(P, mu, dw, dc, fp64, used);
     check_solve_flag(P);
     return r;
 }
 
-static RefineResult direction_step_(Problem *P, double mu, double dw, double dc) {
+static RefineResult direction_step_(Problem *P, double mu, double dw, double dc, bool fp64, Inertia *used) {
     if (!use_refined(P)) {
         solve_direction(P, mu, dw);
         return RefineResult{true, 0, 0.0};
     }
     RefineResult rr = solve_direction_refined(P, mu, dw, dc, refine_sweeps(P));
-    if (!rr.ok && P->opt.precision != MDSIP_PREC_FP64) {
-        factor_attempt(P, dw, dc, true);
+    if (!rr.ok && P->opt.precision != MDSIP_PREC_FP64 && !fp64) {
+        *used = factor_attempt(P, dw, dc, true);
         P->stats.n_fp64_fallback++;
         RefineResult r2 = solve_direction_refined(P, mu, dw, dc, std::max(refine_sweeps(P), 3));
         r2.sweeps += rr.sweeps;
         r2.ok = false;  // marks the fallback in the log
+        r2.fell_back = true;
         return r2;
     }
     return rr;
@@ -1005,6 +1013,33 @@ static void swap_trial(Problem *P) {
     std::swap(P->grad, P->grad_t);
     std::swap(P->cg, P->cg_t);
     std::swap(P->ch, P->ch_t);
+}
+
+// Relative distance ||D_mixed - D_fp64||_2 / ||D_fp64||_2 between the
+// direction just computed with the low-precision factor and the FP64 direction
+// (FP64 product and factorization, same iterate and shifts).  P->Dir keeps the
+// low-precision direction: the solve goes on exactly as without the check.
+static double fp64_direction_error(Problem *P, double mu, double dw, double dc) {
+    const Dims &D = P->D;
+    if (!P->Dchk.dx) {
+        DirView &C = P->Dchk;
+        C.dx = dvec(P->ctx, P->bcx, D.n);
+        C.dd = dvec(P->ctx, P->bcd, D.m_I);
+        C.dyg = dvec(P->ctx, P->bcyg, D.m_E);
+        C.dyh = dvec(P->ctx, P->bcyh, D.m_I);
+        C.dzl = dvec(P->ctx, P->bczl, D.n);
+        C.dzu = dvec(P->ctx, P->bczu, D.n);
+        C.dvl = dvec(P->ctx, P->bcvl, D.m_I);
+        C.dvu = dvec(P->ctx, P->bcvu, D.m_I);
+    }
+    P->V.copy_dir(P->Dir, P->Dchk);
+    Inertia in64 = factor_attempt(P, dw, dc, true);
+    direction_step(P, mu, dw, dc, true, &in64);
+    P->V.dir_diff(P->Dchk, P->Dir, P->scal() + SC_DCHK);
+    P->V.copy_dir(P->Dchk, P->Dir);
+    P->sync_scalars();
+    const double *h = P->hscal;
+    return h[SC_DCHK + 1] > 0 ? std::sqrt(h[SC_DCHK] / h[SC_DCHK + 1]) : 0.0;
 }
 
 static mdsip_status run_ipm(Problem *P) {
@@ -1089,26 +1124,51 @@ static mdsip_status run_ipm(Problem *P) {
             }
             rec.n_ic++;
         };
-        Inertia in = factor_attempt(P, dw, dc);
-        record(in);
-        bool ic_failed = false;
-        if (!(in == target)) {
-            if (in.zero > 0) dc = o.dc_bar * std::pow(mu, o.kappa_c);
-            dw = dw_last == 0.0 ? o.dw0 : std::max(o.dw_min, o.kw_minus * dw_last);
-            while (true) {
-                in = factor_attempt(P, dw, dc);
-                record(in);
-                if (in == target) { dw_last = dw; break; }
-                dw = dw_last == 0.0 ? o.kw_plus_bar * dw : o.kw_plus * dw;
-                if (dw > o.dw_max) { ic_failed = true; break; }
+        // A low-precision factor whose refined direction stalls is replaced by the
+        // FP64 factor with the same shifts; if that one misses the target inertia,
+        // Algorithm IC runs again for this iteration on FP64 factors alone.
+        bool ic_failed = false, fp64 = false;
+        const double dw_last0 = dw_last;
+        Inertia used{};
+        RefineResult rr{};
+        while (true) {
+            dw = 0.0;
+            dc = 0.0;
+            Inertia in = factor_attempt(P, dw, dc, fp64);
+            record(in);
+            if (!(in == target)) {
+                if (in.zero > 0) dc = o.dc_bar * std::pow(mu, o.kappa_c);
+                dw = dw_last == 0.0 ? o.dw0 : std::max(o.dw_min, o.kw_minus * dw_last);
+                while (true) {
+                    in = factor_attempt(P, dw, dc, fp64);
+                    record(in);
+                    if (in == target) { dw_last = dw; break; }
+                    dw = dw_last == 0.0 ? o.kw_plus_bar * dw : o.kw_plus * dw;
+                    if (dw > o.dw_max) { ic_failed = true; break; }
+                }
             }
+            if (ic_failed) break;
+            used = in;
+            rr = direction_step(P, mu, dw, dc, fp64, &used);
+            if (rr.fell_back && !(used == target)) {
+                record(used);           // the FP64 factor that missed the target
+                fp64 = true;
+                dw_last = dw_last0;     // as an FP64 run would start this iteration
+                continue;
+            }
+            break;
         }
         if (rec.n_ic > MDSIP_MAX_IC) rec.n_ic = MDSIP_MAX_IC;
         if (ic_failed) { status = MDSIP_ERR_INERTIA; P->log.push_back(rec); break; }
-        const RefineResult rr = direction_step(P, mu, dw, dc);
+        rec.factor_inertia[0] = (int32_t)used.pos;
+        rec.factor_inertia[1] = (int32_t)used.neg;
+        rec.factor_inertia[2] = (int32_t)used.zero;
         rec.n_refine = rr.sweeps;
-        rec.fp64_fallback = rr.ok ? 0 : 1;
+        rec.fp64_fallback = (rr.ok && !fp64) ? 0 : 1;
         rec.refine_res = rr.res;
+        rec.dir_err_fp64 = -1.0;
+        if (o.direction_check && use_refined(P) && P->opt.precision != MDSIP_PREC_FP64 && !fp64 && !rr.fell_back)
+            rec.dir_err_fp64 = fp64_direction_error(P, mu, dw, dc);
         // A.5 line search
         P->V.step_scalars(P->I, P->Dir, P->grad, tau, mu, sc + SC_STEP);
         P->sync_scalars();
@@ -1251,11 +1311,11 @@ static void debug_direction(Problem *P, const double *packed, double mu, double 
     model_f(P, P->I.x, P->grad, sc + SC_F);
     model_cons(P, P->I.x, P->I.d, P->cg, P->ch, sc + SC_THETA);
     eval_derivatives(P);
-    const Inertia in = factor_attempt(P, dw, dc);
+    Inertia in = factor_attempt(P, dw, dc);
     const int64_t saved = P->opt.refine_max;
     if (refine > 0) P->opt.refine_max = refine;
     try {
-        direction_step(P, mu, dw, dc);
+        direction_step(P, mu, dw, dc, false, &in);   // `in`: the factor the direction came from
     } catch (...) {
         P->opt.refine_max = saved;
         throw;
@@ -1288,7 +1348,8 @@ static bool set_option(Options &o, const std::string &name, double v, bool is_in
                        {"refine_fallback_tol", &o.refine_fallback_tol}};
     const I iopts[] = {{"max_iter", &o.max_iter}, {"path", &o.path}, {"max_ls", &o.max_ls},
                        {"refine_max", &o.refine_max}, {"precision", &o.precision}, {"graphs", &o.graphs},
-                       {"autotune", &o.autotune}, {"ldlt_spec", &o.ldlt_spec}};
+                       {"autotune", &o.autotune}, {"ldlt_spec", &o.ldlt_spec},
+                       {"direction_check", &o.direction_check}};
     if (is_int) {
         for (auto &e : iopts)
             if (name == e.n) { *e.p = (int64_t)v; return true; }
@@ -1446,6 +1507,32 @@ mdsip_status mdsip_set_option_double(mdsip_problem *hp, const char *name, double
     return guarded(p->ctx, [&] {
         MDSIP_REQUIRE(set_option(p->opt, name, value, false), MDSIP_ERR_INVALID_ARG,
                       std::string("unknown double option ") + name);
+    });
+}
+
+mdsip_status mdsip_set_option_str(mdsip_problem *hp, const char *name, const char *value) {
+    if (!hp || !name || !value) return MDSIP_ERR_INVALID_ARG;
+    Problem *p = P_(hp);
+    return guarded(p->ctx, [&] {
+        struct W { const char *opt, *word; int64_t v; };
+        static const W words[] = {
+            {"path", "auto", MDSIP_PATH_AUTO},     {"path", "p1", MDSIP_PATH_P1},
+            {"path", "p2", MDSIP_PATH_P2},         {"precision", "fp64", MDSIP_PREC_FP64},
+            {"precision", "tf32", MDSIP_PREC_TF32}, {"precision", "bf16", MDSIP_PREC_BF16},
+            {"graphs", "yes", 1},   {"graphs", "no", 0},   {"autotune", "yes", 1},
+            {"autotune", "no", 0},  {"ldlt_spec", "yes", 1}, {"ldlt_spec", "no", 0}};
+        const std::string n(name), v(value);
+        bool known = false;
+        for (const W &w : words) {
+            if (n != w.opt) continue;
+            known = true;
+            if (v != w.word) continue;
+            set_option(p->opt, n, (double)w.v, true);
+            if (n == "ldlt_spec") p->drop_graphs();
+            return;
+        }
+        MDSIP_REQUIRE(false, MDSIP_ERR_INVALID_ARG,
+                      known ? "bad value '" + v + "' for option " + n : "unknown string option " + n);
     });
 }
 
@@ -1622,6 +1709,16 @@ mdsip_status mdsip_debug_direction(mdsip_problem *hp, const double *packed, doub
 }
 
 int64_t mdsip_launch_count(void) { return (int64_t)g_launches.load(); }
+
+mdsip_status mdsip_probe_fp64_fma(mdsip_ctx *hctx, int32_t blocks, int64_t iters, double *sink) {
+    if (!hctx) return MDSIP_ERR_INVALID_ARG;
+    Ctx *ctx = C_(hctx);
+    return guarded(ctx, [&] {
+        DeviceGuard g(ctx->device);
+        MDSIP_REQUIRE(blocks > 0 && iters > 0 && sink, MDSIP_ERR_INVALID_ARG, "probe: bad arguments");
+        launch_fp64_fma_probe(ctx->stream, blocks, iters, sink);
+    });
+}
 
 mdsip_status mdsip_syrk_scaled(mdsip_ctx *hctx, int64_t m, int64_t n, const double *A, int64_t lda,
                                const double *w, double beta, double *C, int64_t ldc) {

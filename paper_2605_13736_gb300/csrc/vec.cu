@@ -539,6 +539,27 @@ __global__ void k_backsub(Dims D, ModelView M, IterView I, DirView Dir, const do
     }
 }
 
+// Distance between two packed directions: quantities 0 = sum (a - b)^2,
+// 1 = sum b^2 over the eight blocks (dx, dd, dyg, dyh, dzl, dzu, dvl, dvu).
+__global__ void __launch_bounds__(NT) k_dir_diff(Dims D, DirView a, DirView b, double *partial) {
+    __shared__ double sh[32];
+    const double *pa[8] = {a.dx, a.dd, a.dyg, a.dyh, a.dzl, a.dzu, a.dvl, a.dvu};
+    const double *pb[8] = {b.dx, b.dd, b.dyg, b.dyh, b.dzl, b.dzu, b.dvl, b.dvu};
+    const int64_t len[8] = {D.n, D.m_I, D.m_E, D.m_I, D.n, D.n, D.m_I, D.m_I};
+    const int64_t gtid = (int64_t)blockIdx.x * NT + threadIdx.x;
+    const int64_t gsz = (int64_t)gridDim.x * NT;
+    double dd = 0.0, bb = 0.0;
+    for (int k = 0; k < 8; ++k)
+        for (int64_t i = gtid; i < len[k]; i += gsz) {
+            const double y = pb[k][i], e = pa[k][i] - y;
+            dd += e * e;
+            bb += y * y;
+        }
+    double r;
+    r = block_sum<NT>(dd, sh); if (threadIdx.x == 0) *slot(partial, 0) = r;
+    r = block_sum<NT>(bb, sh); if (threadIdx.x == 0) *slot(partial, 1) = r;
+}
+
 __global__ void k_copy(const double *__restrict__ src, double *__restrict__ dst, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -932,6 +953,23 @@ void VecOps::cons_from_values(const double *g, const double *h, const double *d,
     MDSIP_LAUNCHED();
     launch_finalize_sum(st, partial, 1, out2);
     launch_finalize_max(st, partial + kRedBlocks, 1, out2 + 1);
+}
+
+void VecOps::dir_diff(const DirView &a, const DirView &b, double *out2) {
+    k_dir_diff<<<kRedBlocks, NT, 0, st>>>(D, a, b, partial);
+    MDSIP_LAUNCHED();
+    launch_finalize_sum(st, partial, 2, out2);
+}
+
+void VecOps::copy_dir(const DirView &src, const DirView &dst) {
+    copy(src.dx, dst.dx, D.n);
+    copy(src.dd, dst.dd, D.m_I);
+    copy(src.dyg, dst.dyg, D.m_E);
+    copy(src.dyh, dst.dyh, D.m_I);
+    copy(src.dzl, dst.dzl, D.n);
+    copy(src.dzu, dst.dzu, D.n);
+    copy(src.dvl, dst.dvl, D.m_I);
+    copy(src.dvu, dst.dvu, D.m_I);
 }
 
 void VecOps::gather(int64_t n, const double *src, const int32_t *idx, double *dst) {

@@ -57,6 +57,9 @@ struct VecOps {
                           double *out2);
     // dst[i] = src[idx[i]]
     void gather(int64_t n, const double *src, const int32_t *idx, double *dst);
+    // out2 = (sum (a - b)^2, sum b^2) over every block of two directions
+    void dir_diff(const DirView &a, const DirView &b, double *out2);
+    void copy_dir(const DirView &src, const DirView &dst);
 };
 
 // Reduced-matrix assembly (assemble.cu).

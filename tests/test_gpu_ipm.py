@@ -105,6 +105,39 @@ def test_solve_matches_oracle_trajectory(ctx, name, path):
             assert tuple(inr) == tuple(ginr)
             assert dw == pytest.approx(gdw, rel=1e-12, abs=0)
             assert dc == pytest.approx(gdc, rel=1e-12, abs=0)
+    compare_iterations(log, g["log"])
+
+
+# Per-iteration quantities of the trajectory against the oracle's log.  Both
+# sides run the same decisions in FP64 on iterates that differ only by
+# rounding order (the directions agree to ~1e-13 relative, bounded by 1e-10 in
+# the direction tests), so:
+#  * discrete decisions -- backtracking count n_ls, the f-type flag -- match exactly;
+#  * mu is the same sequence of products and powers: 1e-12 relative;
+#  * step lengths alpha_max, alpha_z (minima of ratios of the iterate to the
+#    direction) and alpha = alpha_max / 2^n_ls: 1e-8 relative, the direction
+#    bound amplified by the ratio's conditioning;
+#  * the objective f: 1e-10 relative;
+#  * norms that fall toward zero (E_0, theta, the primal/dual infeasibility,
+#    gphi) lose relative accuracy as they shrink: 1e-6 relative plus an
+#    absolute floor of 1e-12 times their value at the first iteration.
+def compare_iterations(log, glog):
+    assert len(log) == len(glog)
+    first = glog[0]
+    for rec, grec in zip(log, glog):
+        it = rec["iter"]
+        assert it == grec["iter"]
+        assert rec["mu"] == pytest.approx(grec["mu"], rel=1e-12), it
+        assert rec["f"] == pytest.approx(grec["f"], rel=1e-10, abs=1e-12), it
+        for key in ("E0", "theta", "inf_pr", "inf_du"):
+            assert rec[key] == pytest.approx(grec[key], rel=1e-6, abs=1e-12 * abs(first[key])), (it, key)
+        if "alpha" not in grec:          # the last record: the stopping test only
+            continue
+        assert rec["n_ls"] == grec["n_ls"], it
+        assert bool(rec["ftype"]) == bool(grec["ftype"]), it
+        for key in ("alpha_max", "alpha_z", "alpha"):
+            assert rec[key] == pytest.approx(grec[key], rel=1e-8), (it, key)
+        assert rec["gphi"] == pytest.approx(grec["gphi"], rel=1e-6, abs=1e-12 * abs(first["gphi"])), it
 
 
 def test_directions_along_oracle_trajectory(ctx):
@@ -175,7 +208,9 @@ def test_direction_parity_full_size(ctx, mds1):
 
 def test_full_size_solve_reaches_tolerance(ctx, mds1):
     """The benchmark-size solve ends with E_0 <= 1e-8, recomputed by the oracle
-    from the GPU's final iterate (a property that holds at any size)."""
+    from the GPU's final iterate (a property that holds at any size), with the
+    oracle's iteration count, inertia-correction sequence and objective to 1e-8
+    relative (tests/golden/mds1_p2.json, the condensed oracle's solve)."""
     inst = mds1
     prob = make_problem(ctx, inst, m.MDSIP_PATH_P2)
     try:
@@ -199,6 +234,12 @@ def test_full_size_solve_reaches_tolerance(ctx, mds1):
     assert abs(ev.f - stats["f"]) <= 1e-12 * abs(ev.f)
     for rec in log[:-1]:
         assert rec["ic"][-1][2] == (inst.n, inst.m, 0)
+    g = _golden("mds1_p2")
+    assert stats["iters"] == g["iters"]
+    assert abs(stats["f"] - g["f"]) <= 1e-8 * abs(g["f"])
+    for rec, grec in zip(log, g["log"]):
+        assert [tuple(c[2]) for c in rec["ic"]] == [tuple(c[2]) for c in grec.get("ic", [])]
+    compare_iterations(log, g["log"])
 
 
 TC_PRECS = [m.MDSIP_PREC_BF16, m.MDSIP_PREC_TF32]
@@ -252,6 +293,7 @@ def test_tensor_core_solve_matches_oracle_trajectory(ctx, prec, spec):
     for rec, grec in zip(log, g["log"]):
         assert [tuple(c[2]) for c in rec["ic"]] == [tuple(c[2]) for c in grec.get("ic", [])]
     assert sum(r["n_refine"] for r in log) > 0
+    compare_iterations(log, g["log"])
 
 
 @pytest.mark.parametrize("prec", TC_PRECS)
@@ -284,4 +326,58 @@ def test_tensor_core_full_size(ctx, mds1, prec):
     fin = ipm.Point(*(packed[o[i]:o[i + 1]] for i in range(8)))
     ev = ipm.Evals(P, fin.x, fin.d)
     assert ipm.kkt_error(P, fin, ev, 0.0, ipm.Options())[0] <= 1e-8
-    assert abs(ev.f - (-36167.45406568737)) <= 1e-8 * 36167.45406568737
+    g = _golden("mds1_p2")          # the oracle's own solve of this instance
+    assert abs(ev.f - g["f"]) <= 1e-8 * abs(g["f"])
+    assert stats["iters"] == g["iters"]
+
+
+@pytest.mark.parametrize("prec", TC_PRECS)
+def test_fp64_fallback_records_the_factor_used(ctx, prec):
+    """A refinement target below any reachable residual sends every step of the
+    mixed-precision solve to the FP64 re-factorization.  Each step then records
+    the inertia of the FP64 factor its direction came from, which must be the
+    target (n, m, 0), and the solve follows the oracle's trajectory (the
+    nonconvex member, whose steps need inertia correction)."""
+    g = _golden("mds0_nonconvex_full")
+    inst = _inst_for(g["case"])
+    prob = make_problem(ctx, inst, m.MDSIP_PATH_P2)
+    try:
+        m.mdsip_set_option_int(prob, "precision", prec, ctx)
+        m.mdsip_set_option_double(prob, "refine_fallback_tol", 1e-300, ctx)
+        st = m.mdsip_solve(prob, ctx)
+        stats = m.mdsip_get_stats(prob)
+        log = m.mdsip_get_log(prob)
+    finally:
+        m.mdsip_problem_destroy(prob)
+    assert m.STATUS[st] == "OK" and stats["E0"] <= 1e-8
+    assert stats["iters"] == g["iters"]
+    assert abs(stats["f"] - g["f"]) <= 1e-8 * abs(g["f"])
+    assert stats["n_fp64_fallback"] >= stats["iters"]
+    for rec in log[:-1]:
+        assert rec["fp64_fallback"] == 1
+        assert rec["factor_inertia"] == (inst.n, inst.m, 0)
+        assert rec["ic"][-1][2] == (inst.n, inst.m, 0)
+
+
+def test_option_strings(ctx):
+    """mdsip_set_option_str sets the same options as the integer setter, by
+    word, and rejects unknown names and values with INVALID_ARG."""
+    g = _golden("mds0_full")
+    inst = _inst_for(g["case"])
+    prob = make_problem(ctx, inst)
+    try:
+        m.mdsip_set_option_str(prob, "path", "p2", ctx)
+        m.mdsip_set_option_str(prob, "precision", "bf16", ctx)
+        m.mdsip_set_option_str(prob, "ldlt_spec", "no", ctx)
+        for name, value in (("path", "p3"), ("precision", "fp16"), ("colour", "blue")):
+            with pytest.raises(m.MdsipError) as ei:
+                m.mdsip_set_option_str(prob, name, value, ctx)
+            assert ei.value.status == 1
+        st = m.mdsip_solve(prob, ctx)
+        stats = m.mdsip_get_stats(prob)
+    finally:
+        m.mdsip_problem_destroy(prob)
+    assert m.STATUS[st] == "OK"
+    assert stats["path"] == m.MDSIP_PATH_P2 and stats["precision"] == m.MDSIP_PREC_BF16
+    assert stats["iters"] == g["iters"]
+    assert abs(stats["f"] - g["f"]) <= 1e-8 * abs(g["f"])

@@ -6,7 +6,9 @@ that allocating can cause); its scratch is a fixed device array shared by
 every call.  The test checks, through the C ABI, that two calls in a row give
 the results of the allocating mdsip_ldlt_factor on the same inputs (so the
 array's leftover contents from the previous call do not leak into the next),
-and that sizes beyond the fixed limit are rejected.  It lives in its own file,
+that both take the Bunch-Kaufman decisions of the CPU oracle (oracle/bk.py:
+permutation, 1x1/2x2 pattern and inertia bit for bit, D to the rounding bound
+of the other LDL^T tests), and that sizes beyond the fixed limit are rejected.  It lives in its own file,
 collected last, and passes alone in a fresh process as well as after the
 other tests.
 """
@@ -14,6 +16,7 @@ import numpy as np
 import pytest
 
 import paper_2605_13736_gb300 as m
+from oracle.bk import bk_ldlt
 from gpu_util import dev, make_ctx, torch_cuda
 
 pytestmark = pytest.mark.gpu
@@ -61,6 +64,14 @@ def test_noalloc_ldlt_matches_allocating_entry_point():
             np.testing.assert_allclose(got["Doff"], ref["Doff"], rtol=1e-10, atol=tol)
             np.testing.assert_allclose(got["L"], ref["L"], rtol=1e-10, atol=1e-10)
             assert int(got["inertia"].sum()) == N
+            # the oracle's unblocked Bunch-Kaufman on the same matrix
+            o = bk_ldlt(K)
+            assert tuple(int(v) for v in got["inertia"]) == tuple(o["inertia"])
+            np.testing.assert_array_equal(got["kind"], o["kind"])
+            np.testing.assert_array_equal(got["perm"], o["perm"])
+            np.testing.assert_allclose(got["Dd"], np.diag(o["D"]), rtol=1e-10, atol=tol)
+            np.testing.assert_allclose(got["Doff"], np.concatenate([np.diag(o["D"], -1), [0.0]]),
+                                       rtol=1e-10, atol=tol)
         # beyond the fixed limit: a clear error, nothing launched
         torch = torch_cuda()
         N = 1025
