@@ -12,12 +12,22 @@ and the accept/barrier update.
 
 W warm-up steps run from the default starting point; then exactly K steps run
 from the W-th iterate (warm start), timed with CUDA events on the library's
-stream between barriers.  One full solve to E_0 <= 1e-8 is timed after that
-(solves/s).  `e2e` repeats the K steps through the public API with the
-iterate copied from pinned host memory before each step and back after it.
-With N > 1 (torchrun) every rank solves its own instance (independent
-problems, weak scaling); the value is the sum of steps over the max time.
-`--impl reference` times the CPU oracle on the same workload.
+stream between barriers: when the solve reaches E_0 <= 1e-8 before K steps,
+it starts again from the W-th iterate, so the K steps are iterations W+1,
+W+2, ... of the method's own trajectory, repeated.  One full solve to
+E_0 <= 1e-8 is timed after that (solves/s).  `e2e` repeats the K steps
+through the public API with the iterate copied from pinned host memory
+before each step and back after it.  With N > 1 (torchrun) every rank solves
+its own instance (independent problems, weak scaling); the value is the sum
+of steps over the max time.  `--impl reference` times the CPU oracle on the
+same workload and the same steps.
+
+After the headline the default run also measures (rank 0, one GPU): the FP64
+FMA rate (the roofline's FP64 peak, measured), mixed precision on member 2
+(n_d=4000, m_E=200000) with the per-step gap to the FP64 direction and the
+final objective against the oracle's, the batched workload (256 instances,
+n_d in [64, 1024]) and the learned warm start (8192 training and 1024
+held-out members), each against the plain FP64 GPU path.
 """
 from __future__ import annotations
 
@@ -64,27 +74,34 @@ def parse():
     ap.add_argument("--config", type=int, default=1)
     ap.add_argument("--no-solve", action="store_true", help="skip the timed full solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-steps", type=int, default=2, help="oracle steps in the CPU baseline sample")
+    ap.add_argument("--cpu-steps", type=int, default=4,
+                    help="oracle steps in the CPU baseline sample (all cores; the 1-thread sample takes 1)")
+    ap.add_argument("--mixed-config", type=int, default=2,
+                    help="member solved in FP64, BF16 and TF32 with per-step FP64 direction gaps (-1: skip)")
     ap.add_argument("--variants", default="bf16,tf32",
                     help="tensor-core precisions also timed on the same instance (comma list, '' for none)")
-    ap.add_argument("--batch-count", type=int, default=32,
+    ap.add_argument("--batch-count", type=int, default=256,
                     help="instances of the batched measurement (0: skip); n_d ~ U{64..batch-max-nd}")
-    ap.add_argument("--batch-max-nd", type=int, default=512)
+    ap.add_argument("--batch-max-nd", type=int, default=1024)
+    ap.add_argument("--batch-seq-fp64", action="store_true",
+                    help="batched measurement: also time the FP64 instances one after another")
     ap.add_argument("--batch-concurrency", type=int, default=32,
                     help="batched measurement: problems solved at once (host workers)")
     ap.add_argument("--batch-option", action="append", default=[],
                     help="NAME=VALUE integer solver option set on every batched instance (repeatable)")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched measurement and print its own JSON line")
-    ap.add_argument("--ws-train", type=int, default=512,
+    ap.add_argument("--ws-train", type=int, default=8192,
                     help="learned warm start: training solves of the parametric family (0: skip)")
-    ap.add_argument("--ws-eval", type=int, default=64, help="learned warm start: held-out members")
-    ap.add_argument("--ws-epochs", type=int, default=100)
+    ap.add_argument("--ws-eval", type=int, default=1024, help="learned warm start: held-out members")
+    ap.add_argument("--ws-epochs", type=int, default=60)
+    ap.add_argument("--ws-fp64-eval", type=int, default=128,
+                    help="learned warm start: held-out members also solved cold with the plain FP64 path")
     ap.add_argument("--ws-workers", type=int, default=8, help="concurrent problems (contexts)")
     ap.add_argument("--ws-only", action="store_true",
                     help="run only the learned warm-start measurement and print its own JSON line")
     ap.add_argument("--kernel", choices=["syrk", "syrk_bf16", "syrk_tf32", "ldlt", "ldlt_solve", "ldlt_library",
-                                         "gemm_bf16"],
+                                         "gemm_bf16", "dfma"],
                     default=None,
                     help="time one kernel-level C-ABI call instead of the Newton step")
     ap.add_argument("--m", type=int, default=100000, help="--kernel syrk: rows of A")
@@ -94,6 +111,7 @@ def parse():
                     help="--kernel ldlt: the mixed-precision factorization (FP32 update products)")
     ap.add_argument("--no-spec", action="store_true",
                     help="--kernel ldlt --fp32-update: every panel pivots (no verified no-interchange panels)")
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--ldlt-matrix", choices=["kkt", "ipm"], default="kkt",
                     help="--kernel ldlt: kkt = [[H, J^T], [J, -I]] with J ~ N(0, 1) (pivots often); "
                          "ipm = the P1 Newton-step shape of a convex problem (H + Sigma dominant, J small)")
@@ -193,21 +211,118 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline and the reference arm)
 # --------------------------------------------------------------------------
-def oracle_steps(inst, warm: int, steps: int):
-    """Time `steps` IPM iterations of the oracle (condensed P2 form) after `warm`."""
+def blas_info():
+    """BLAS library and thread count of this process's numpy."""
+    try:
+        import threadpoolctl
+        info = [d for d in threadpoolctl.threadpool_info() if d.get("user_api") == "blas"]
+        if info:
+            return {"library": info[0].get("internal_api"), "threads": info[0].get("num_threads")}
+    except ImportError:
+        pass
+    name = None
+    try:
+        import numpy as np
+        name = np.show_config(mode="dicts")["Build Dependencies"]["blas"]["name"]
+    except Exception:
+        pass
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(k):
+            return {"library": name, "threads": int(os.environ[k])}
+    return {"library": name, "threads": os.cpu_count()}
+
+
+ONE_THREAD_ENV = {k: "1" for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS",
+                                   "BLIS_NUM_THREADS", "VECLIB_MAXIMUM_THREADS")}
+
+
+def oracle_warm(inst, warm: int):
+    """The oracle's own W-th iterate (condensed P2 form) and its barrier parameter."""
+    from oracle import ipm
+    from oracle.model import SynthModel
+    if warm <= 0:
+        return None, None
+    r = ipm.solve(SynthModel(inst), opt=ipm.Options(linsolve="p2", max_iter=warm))
+    return r["point"], r["mu"]
+
+
+def oracle_sample(inst, start, mu, steps: int):
+    """Time `steps` oracle iterations from `start` (None: the default start);
+    when the oracle reaches E_0 <= 1e-8 first it starts again from `start`, as
+    the GPU's timed steps do.  Returns (iterations, seconds)."""
     from oracle import ipm
     from oracle.model import SynthModel
     model = SynthModel(inst)
-    opt = ipm.Options(linsolve="p2", max_iter=warm)
-    start, mu = None, None
-    if warm > 0:
-        r = ipm.solve(model, opt=opt)
-        start, mu = r["point"], r["mu"]
-    opt = ipm.Options(linsolve="p2", max_iter=steps)
-    t0 = time.perf_counter()
-    r = ipm.solve(model, opt=opt, start=start, mu0=mu)
-    el = time.perf_counter() - t0
-    return r["iters"], el
+    done, el = 0, 0.0
+    while done < steps:
+        t0 = time.perf_counter()
+        r = ipm.solve(model, opt=ipm.Options(linsolve="p2", max_iter=steps - done), start=start, mu0=mu)
+        el += time.perf_counter() - t0
+        if r["iters"] == 0:
+            break
+        done += r["iters"]
+    return done, el
+
+
+def save_point(path, pt, mu):
+    import numpy as np
+    np.savez(path, mu=mu, **{k: getattr(pt, k) for k in ("x", "d", "yg", "yh", "zl", "zu", "vl", "vu")})
+
+
+def load_point(path):
+    import numpy as np
+    from oracle import ipm
+    z = np.load(path)
+    return ipm.Point(*(z[k] for k in ("x", "d", "yg", "yh", "zl", "zu", "vl", "vu"))), float(z["mu"])
+
+
+def oracle_sample_one_thread(cfg, point_path, steps):
+    """The oracle sample in a child process whose BLAS runs one thread."""
+    env = dict(os.environ, **ONE_THREAD_ENV)
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", point_path, "--config", str(cfg),
+           "--cpu-steps", str(steps)]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else f"rc {r.returncode}"}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_oracle_sample(args):
+    """Child of oracle_sample_one_thread: prints {steps, seconds, blas}."""
+    import synth
+    start, mu = load_point(args.oracle_sample)
+    n, el = oracle_sample(synth.make_config(args.config), start, mu, args.cpu_steps)
+    print(json.dumps({"steps": n, "seconds": el, "blas": blas_info()}))
+
+
+def cpu_baseline(inst, cfg, warm, steps):
+    """The oracle on this host: `steps` iterations after its own `warm` warm-up
+    iterations with the default (multithreaded) BLAS, and one iteration of the
+    same sample with a one-thread BLAS."""
+    start, mu = oracle_warm(inst, warm)
+    n, el = oracle_sample(inst, start, mu, steps)
+    out = {"value": n / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "blas": blas_info(),
+           "sample": f"iterations {warm + 1}..{warm + n} of the FP64 numpy/scipy oracle's own trajectory "
+                     f"(condensed P2 form) from its iterate {warm}, restarted there if it converges first; "
+                     f"the same steps the GPU times"}
+    if start is not None:
+        path = os.path.join(tempfile.gettempdir(), f"mdsip_oracle_point_{os.getpid()}.npz")
+        try:
+            save_point(path, start, mu)
+            one = oracle_sample_one_thread(cfg, path, 1)
+        finally:
+            try:
+                os.remove(path)
+            except OSError:
+                pass
+        if "steps" in one:
+            out["single_thread"] = {"value": one["steps"] / one["seconds"], "unit": UNIT, "cores": 1,
+                                    "blas": one["blas"],
+                                    "sample": f"iteration {warm + 1} of the same trajectory, BLAS limited to "
+                                              f"one thread"}
+        else:
+            out["single_thread"] = one
+    return out
 
 
 def workload_name(cfg):
@@ -223,7 +338,8 @@ def run_reference(args):
         return
     import synth
     inst = synth.make_config(args.config)
-    n, el = oracle_steps(inst, args.warmup, args.steps)
+    start, mu = oracle_warm(inst, args.warmup)
+    n, el = oracle_sample(inst, start, mu, args.steps)
     value = n / el
     cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
@@ -231,9 +347,10 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": workload_name(args.config), "path": "P2 (two-stage elimination)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{n} IPM iterations of the FP64 numpy/scipy oracle (condensed P2 "
-                                       f"form) after {args.warmup} warm-up iterations"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "blas": blas_info(),
+                             "sample": f"iterations {args.warmup + 1}.. of the FP64 numpy/scipy oracle's own "
+                                       f"trajectory (condensed P2 form) from its iterate {args.warmup}, "
+                                       f"restarted there if it converges first: {n} steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -267,25 +384,34 @@ def run_batch(args, m, torch, local):
                 for kv in args.batch_option:
                     k, v = kv.split("=")
                     m.mdsip_set_option_int(p, k, int(v))
-            # one untimed pass over every instance: workspaces, autotuned shapes
-            # (first use per shape) and captured factorization graphs
+            # one untimed pass of two steps over every instance: workspaces, autotuned
+            # shapes (first use per shape) and captured factorization graphs (second use)
+            for p in probs:
+                m.mdsip_set_option_int(p, "max_iter", 2)
             m.mdsip_batch_solve(probs, args.batch_concurrency)
+            for p in probs:
+                m.mdsip_set_option_int(p, "max_iter", 200)
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            seq = [m.mdsip_solve(p) for p in probs]
-            t_seq = time.perf_counter() - t0
-            iters = sum(m.mdsip_get_stats(p)["iters"] for p in probs)
+            seq = []
+            t_seq = None
+            if name != "fp64" or args.batch_seq_fp64:
+                t0 = time.perf_counter()
+                seq = [m.mdsip_solve(p) for p in probs]
+                t_seq = time.perf_counter() - t0
             t0 = time.perf_counter()
             bst = m.mdsip_batch_solve(probs, args.batch_concurrency)
             torch.cuda.synchronize()
             t_bat = time.perf_counter() - t0
-            out[name] = {"sequential_solves_per_s": len(probs) / t_seq, "batched_solves_per_s": len(probs) / t_bat,
+            iters = sum(m.mdsip_get_stats(p)["iters"] for p in probs)
+            out[name] = {"sequential_solves_per_s": len(probs) / t_seq if t_seq else None,
+                         "batched_solves_per_s": len(probs) / t_bat,
                          "batched_newton_steps_per_s": iters / t_bat,
-                         "speedup": t_seq / t_bat,
+                         "speedup": t_seq / t_bat if t_seq else None,
                          "all_ok": all(m.STATUS[x] == "OK" for x in seq + bst),
                          "statuses_sequential": {k: [m.STATUS[x] for x in seq].count(k) for k in set(m.STATUS[x] for x in seq)},
                          "statuses_batched": {k: [m.STATUS[x] for x in bst].count(k) for k in set(m.STATUS[x] for x in bst)},
                          "max_E0": max(m.mdsip_get_stats(p)["E0"] for p in probs)}
+        out["bf16_vs_fp64_batched"] = out["bf16"]["batched_solves_per_s"] / out["fp64"]["batched_solves_per_s"]
     finally:
         for p in probs:
             m.mdsip_problem_destroy(p)
@@ -340,6 +466,15 @@ def run_warmstart(args, m, torch, local):
         t_pred = time.perf_counter() - t0
         cold = ws.solve_cold(probs, set_member, eval_p)
         warm = ws.solve_warm(probs, set_member, eval_p, pred, push=1e-4)
+        # the plain FP64 GPU path on a sample of the same held-out members
+        n64 = min(args.ws_fp64_eval, args.ws_eval)
+        cold64 = None
+        if n64 > 0:
+            for p, c in zip(probs, ctxs):
+                m.mdsip_set_option_int(p, "precision", m.MDSIP_PREC_FP64, c)
+            cold64 = ws.solve_cold(probs, set_member, eval_p[:n64])
+            for p, c in zip(probs, ctxs):
+                m.mdsip_set_option_int(p, "precision", m.MDSIP_PREC_BF16, c)
         frel = np.abs(warm["f"] - cold["f"]) / np.maximum(1.0, np.abs(cold["f"]))
         hist = lambda st: {m.STATUS[k]: int(v) for k, v in zip(*np.unique(st, return_counts=True))}
         return {
@@ -361,6 +496,11 @@ def run_warmstart(args, m, torch, local):
                      "fallbacks": int(warm["fallbacks"]), "statuses": hist(warm["statuses"]),
                      "max_E0": float(warm["E0"].max()), "max_f_rel_diff_vs_cold": float(frel.max())},
             "speedup_solves_per_s": cold["seconds"] / warm["seconds"],
+            "fp64_cold": ({"members": n64, "solves_per_s": n64 / cold64["seconds"],
+                           "mean_iters": float(cold64["iters"].mean()), "statuses": hist(cold64["statuses"]),
+                           "max_E0": float(cold64["E0"].max())} if cold64 else None),
+            "warm_vs_fp64_cold_solves_per_s": ((args.ws_eval / warm["seconds"]) / (n64 / cold64["seconds"])
+                                              if cold64 else None),
         }
     finally:
         if net is not None:
@@ -395,6 +535,136 @@ def cond_ldlt_roofline(inst, syrk_ms, ldlt_ms, precision):
             "ldlt_time_vs_fp64_peak": (f_ldlt / p64) / (ldlt_ms / 1e3) if ldlt_ms else None}
 
 
+def timed_steps(m, prob, ctx, packed, mu_w, K, mem):
+    """Exactly K Newton steps from the W-th iterate `packed` (restarting there
+    when the solve converges first).  Returns (steps, summed statistics)."""
+    done, zero_calls = 0, 0
+    acc = {k: 0.0 for k in ("t_syrk_ms", "n_syrk", "t_ldlt_ms", "n_ldlt", "t_condense_ms", "t_factor_ms",
+                            "t_solve_ms", "t_refine_ms", "t_ls_ms", "n_refine", "n_fp64_fallback")}
+    statuses = []
+    while done < K and zero_calls < 2:
+        m.mdsip_set_option_int(prob, "max_iter", K - done, ctx)
+        m.mdsip_set_start(prob, packed, mu_w, mem, ctx)
+        statuses.append(m.STATUS[m.mdsip_solve(prob, ctx)])
+        st = m.mdsip_get_stats(prob)
+        for k in acc:
+            acc[k] += st[k]
+        zero_calls = zero_calls + 1 if st["iters"] == 0 else 0
+        done += st["iters"]
+    acc["solve_calls"] = len(statuses)
+    acc["statuses"] = sorted(set(statuses))
+    return done, acc
+
+
+def fp64_fma_probe(m, torch, ctx, local):
+    """Measured FP64 FMA rate (TFLOP/s) of this GPU: mdsip_probe_fp64_fma over
+    8 resident blocks per SM, median of 5 timed launches after 2 warm ones."""
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    blocks, iters = 8 * n_sm, 20000
+    sink = torch.empty(blocks * 256, dtype=torch.float64, device=torch.device("cuda", local))
+    times = []
+    for it in range(7):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        m.mdsip_probe_fp64_fma(ctx, blocks, iters, sink)
+        e1.record()
+        torch.cuda.synchronize()
+        if it >= 2:
+            times.append(e0.elapsed_time(e1) / 1e3)
+    flops = blocks * 256.0 * iters * 8 * 2
+    return {"tflops": flops / statistics.median(times) / 1e12, "blocks": blocks, "iters_per_thread": iters,
+            "ms_median": 1e3 * statistics.median(times)}
+
+
+def golden_objective(cfg):
+    """Final objective of the oracle's own solve of member `cfg`
+    (tests/golden/mds{cfg}_p2.json, written by tests/golden/make_golden.py)."""
+    path = os.path.join(ROOT, "tests", "golden", f"mds{cfg}_p2.json")
+    try:
+        with open(path) as fh:
+            g = json.load(fh)
+        return {"f": g["f"], "iters": g["iters"], "E0": g["E0"], "source": os.path.relpath(path, ROOT)}
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def run_mixed(args, m, torch, local):
+    """Member `--mixed-config` (default 2: n_d=4000, n_s=400000, m_E=200000,
+    m_I=50) solved to E_0 <= 1e-8 with the plain FP64 path and with the BF16 and
+    TF32 tensor-core products (FP64 refinement); then the mixed solves once more
+    with every step's direction compared with the FP64 direction from the same
+    iterate (direction_check).  Objectives against the oracle's solve."""
+    import synth
+    cfg = args.mixed_config
+    inst = synth.make_config(cfg)
+    gold = golden_objective(cfg)
+    stream = torch.cuda.current_stream().cuda_stream
+    ctx = m.mdsip_ctx_create(local, stream)
+    prob = m.mdsip_problem_create_synthetic(ctx, **m.synth_arrays(inst))
+    del inst
+    out = {"workload": workload_name(cfg).replace("plain FP64 ", ""), "oracle": gold}
+    try:
+        for name, prec in (("fp64", m.MDSIP_PREC_FP64), ("bf16", m.MDSIP_PREC_BF16), ("tf32", m.MDSIP_PREC_TF32)):
+            m.mdsip_set_option_int(prob, "precision", prec, ctx)
+            m.mdsip_set_option_int(prob, "direction_check", 0, ctx)
+            m.mdsip_set_start(prob, None)
+            m.mdsip_set_option_int(prob, "max_iter", 2, ctx)     # workspaces, tile choices, graphs
+            m.mdsip_solve(prob, ctx)
+            m.mdsip_set_option_int(prob, "max_iter", 200, ctx)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = m.mdsip_solve(prob, ctx)
+            e1.record()
+            torch.cuda.synchronize()
+            ss = m.mdsip_get_stats(prob)
+            sec = e0.elapsed_time(e1) / 1e3
+            rec = {"status": m.STATUS[st], "iters": ss["iters"], "seconds": sec, "solves_per_s": 1.0 / sec,
+                   "newton_steps_per_s": ss["iters"] / sec, "E0": ss["E0"], "f": ss["f"],
+                   "f_rel_err_vs_oracle": abs(ss["f"] - gold["f"]) / abs(gold["f"]) if gold else None,
+                   "iters_oracle": gold["iters"] if gold else None,
+                   "refine_sweeps_per_step": ss["n_refine"] / max(1, ss["iters"]),
+                   "fp64_fallbacks": ss["n_fp64_fallback"],
+                   "phase_ms_per_step": {k: ss[k] / max(1, ss["iters"]) for k in
+                                         ("t_condense_ms", "t_factor_ms", "t_refine_ms", "t_ls_ms",
+                                          "t_syrk_ms", "t_ldlt_ms")},
+                   "condensation_plus_ldlt_roofline": cond_ldlt_roofline(
+                       _dims(cfg),
+                       ss["t_syrk_ms"] / max(1, ss["n_syrk"]), ss["t_ldlt_ms"] / max(1, ss["n_ldlt"]), name)}
+            if name != "fp64":
+                rec["speedup_vs_fp64_solves"] = out["fp64"]["seconds"] / sec
+                # the same solve once more, each step's direction against the FP64 direction
+                m.mdsip_set_option_int(prob, "direction_check", 1, ctx)
+                m.mdsip_set_start(prob, None)
+                cst = m.mdsip_solve(prob, ctx)
+                log = m.mdsip_get_log(prob)
+                cs = m.mdsip_get_stats(prob)
+                errs = [r["dir_err_fp64"] for r in log if r["dir_err_fp64"] >= 0]
+                rec["direction_check"] = {
+                    "status": m.STATUS[cst], "iters": cs["iters"], "f": cs["f"],
+                    "f_rel_err_vs_oracle": abs(cs["f"] - gold["f"]) / abs(gold["f"]) if gold else None,
+                    "rel_err_per_step": errs, "max_rel_err": max(errs) if errs else None,
+                    "fp64_fallbacks": cs["n_fp64_fallback"],
+                    "what": "||D - D_64||_2 / ||D_64||_2 per Newton step: D the refined mixed-precision "
+                            "direction, D_64 the FP64 GPU direction from the same iterate and shifts"}
+                m.mdsip_set_option_int(prob, "direction_check", 0, ctx)
+            out[name] = rec
+    finally:
+        m.mdsip_problem_destroy(prob)
+        m.mdsip_ctx_destroy(ctx)
+    return out
+
+
+class _dims:
+    """n_d, m_E, m_I of a benchmark member without drawing its arrays."""
+
+    def __init__(self, cfg):
+        import synth
+        p = synth.CONFIGS[cfg]
+        self.n_d, self.m_E, self.m_I = p["n_d"], p["m_E"], p["m_I"]
+
+
 def run_gpu(args):
     rank, world, local = dist_env()
     import numpy as np
@@ -414,6 +684,7 @@ def run_gpu(args):
     ctx = m.mdsip_ctx_create(local, stream)
     prob = m.mdsip_problem_create_synthetic(ctx, **m.synth_arrays(inst))
     psize = m.mdsip_packed_size(prob)
+    K = args.steps
     try:
         # warm-up: W steps from the default start
         m.mdsip_set_option_int(prob, "max_iter", args.warmup, ctx)
@@ -423,22 +694,18 @@ def run_gpu(args):
         m.mdsip_get_iterate(prob, packed, m.MDSIP_MEM_DEVICE, ctx)
         mu_w = w_stats["mu"]
         # timed: exactly K steps from the W-th iterate
-        m.mdsip_set_option_int(prob, "max_iter", args.steps, ctx)
-        m.mdsip_set_start(prob, packed, mu_w, m.MDSIP_MEM_DEVICE, ctx)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         launches0 = m.mdsip_launch_count()
         with ClockSampler(local) as clk:
             barrier(world)
             torch.cuda.synchronize()
             e0.record()
-            st = m.mdsip_solve(prob, ctx)
+            steps_done, acc = timed_steps(m, prob, ctx, packed, mu_w, K, m.MDSIP_MEM_DEVICE)
             e1.record()
             torch.cuda.synchronize()
             barrier(world)
         launches = m.mdsip_launch_count() - launches0
-        stats = m.mdsip_get_stats(prob)
         elapsed = e0.elapsed_time(e1) / 1e3
-        steps_done = stats["iters"]
         t_max = reduce_scalar(elapsed, "max", world, dev)
         units = reduce_scalar(steps_done, "sum", world, dev)
         value = units / t_max
@@ -458,26 +725,37 @@ def run_gpu(args):
             ss = m.mdsip_get_stats(prob)
             sec = s0.elapsed_time(s1) / 1e3
             sec_max = reduce_scalar(sec, "max", world, dev)
+            gold = golden_objective(args.config) if rank == 0 else None
             solve = {"status": m.STATUS[sst], "iters": ss["iters"], "E0": ss["E0"], "f": ss["f"],
                      "seconds": sec, "solves_per_s": reduce_scalar(1.0, "sum", world, dev) / sec_max,
                      "newton_steps_per_s": reduce_scalar(ss["iters"], "sum", world, dev) / sec_max,
-                     "factorizations": ss["n_factorizations"]}
+                     "factorizations": ss["n_factorizations"],
+                     "f_rel_err_vs_oracle": abs(ss["f"] - gold["f"]) / abs(gold["f"]) if gold else None,
+                     "iters_oracle": gold["iters"] if gold else None}
 
-        # end to end through the public API with host buffers
+        # end to end through the public API with host buffers: one step per call,
+        # the iterate copied in from pinned memory before and out after it
         host = torch.empty(psize, dtype=torch.float64, pin_memory=True)
         hview = host.numpy()
-        hview[:] = packed.cpu().numpy()
+        w_host = packed.cpu().numpy()
+        hview[:] = w_host
         m.mdsip_set_option_int(prob, "max_iter", 1, ctx)
         mu_e = mu_w
         barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        n_e2e = 0
-        for _ in range(args.steps):
+        n_e2e, idle = 0, 0
+        while n_e2e < K and idle < 2:
             m.mdsip_set_start(prob, hview, mu_e, m.MDSIP_MEM_HOST, ctx)   # H2D from pinned memory
             m.mdsip_solve(prob, ctx)
             m.mdsip_get_iterate(prob, hview, m.MDSIP_MEM_HOST, ctx)       # D2H into pinned memory
             es = m.mdsip_get_stats(prob)
+            if es["iters"] == 0:         # converged: start again from the W-th iterate
+                hview[:] = w_host
+                mu_e = mu_w
+                idle += 1
+                continue
+            idle = 0
             mu_e = es["mu"]
             n_e2e += es["iters"]
         torch.cuda.synchronize()
@@ -490,25 +768,21 @@ def run_gpu(args):
         for name in [v for v in args.variants.split(",") if v]:
             prec = {"bf16": m.MDSIP_PREC_BF16, "tf32": m.MDSIP_PREC_TF32}[name]
             m.mdsip_set_option_int(prob, "precision", prec, ctx)
-            m.mdsip_set_option_int(prob, "max_iter", args.steps, ctx)
-            m.mdsip_set_start(prob, packed, mu_w, m.MDSIP_MEM_DEVICE, ctx)
-            m.mdsip_solve(prob, ctx)                     # warm the tensor-core workspace
-            m.mdsip_set_start(prob, packed, mu_w, m.MDSIP_MEM_DEVICE, ctx)
+            timed_steps(m, prob, ctx, packed, mu_w, min(K, 4), m.MDSIP_MEM_DEVICE)   # warm the workspace
             barrier(world)
             torch.cuda.synchronize()
             v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             v0.record()
-            m.mdsip_solve(prob, ctx)
+            vdone, vs = timed_steps(m, prob, ctx, packed, mu_w, K, m.MDSIP_MEM_DEVICE)
             v1.record()
             torch.cuda.synchronize()
-            vs = m.mdsip_get_stats(prob)
             vt = reduce_scalar(v0.elapsed_time(v1) / 1e3, "max", world, dev)
-            vunits = reduce_scalar(vs["iters"], "sum", world, dev)
-            rec = {"value": vunits / vt, "unit": UNIT, "ms_per_step": 1e3 * vt / max(1, vs["iters"]),
-                   "refine_sweeps_per_step": vs["n_refine"] / max(1, vs["iters"]),
+            vunits = reduce_scalar(vdone, "sum", world, dev)
+            rec = {"value": vunits / vt, "unit": UNIT, "steps": vdone, "ms_per_step": 1e3 * vt / max(1, vdone),
+                   "refine_sweeps_per_step": vs["n_refine"] / max(1, vdone),
                    "fp64_fallbacks": vs["n_fp64_fallback"],
                    "syrk_ms_per_launch": vs["t_syrk_ms"] / max(1, vs["n_syrk"]),
-                   "phase_ms_per_step": {k: vs[k] / max(1, vs["iters"]) for k in
+                   "phase_ms_per_step": {k: vs[k] / max(1, vdone) for k in
                                          ("t_condense_ms", "t_factor_ms", "t_refine_ms", "t_ls_ms",
                                           "t_syrk_ms", "t_ldlt_ms")}}
             if not args.no_solve:
@@ -535,54 +809,61 @@ def run_gpu(args):
                 inst, vs["t_syrk_ms"] / max(1, vs["n_syrk"]), vs["t_ldlt_ms"] / max(1, vs["n_ldlt"]), name)
             variants[name] = rec
             m.mdsip_set_option_int(prob, "precision", m.MDSIP_PREC_FP64, ctx)
+        probe = fp64_fma_probe(m, torch, ctx, local) if rank == 0 else None
     finally:
         m.mdsip_problem_destroy(prob)
         m.mdsip_ctx_destroy(ctx)
 
     if rank != 0:
         return
+    D = dict(n_d=inst.n_d, n_s=inst.n_s, m_E=inst.m_E, m_I=inst.m_I)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(inst, args.config, args.warmup, args.cpu_steps)
+    del inst
+    mixed = run_mixed(args, m, torch, local) if (args.mixed_config >= 0 and world == 1) else None
     batch = run_batch(args, m, torch, local) if (args.batch_count > 0 and world == 1) else None
     wstart = run_warmstart(args, m, torch, local) if (args.ws_train > 0 and world == 1) else None
-    D = dict(n_d=inst.n_d, n_s=inst.n_s, m_E=inst.m_E, m_I=inst.m_I)
     flops = D["n_d"] * (D["n_d"] + 1) / 2 * D["m_E"] * 2.0
-    syrk_ms = stats["t_syrk_ms"] / max(1, stats["n_syrk"])
-    achieved = flops / (syrk_ms / 1e3) / 1e12 if stats["n_syrk"] else None
+    syrk_ms = acc["t_syrk_ms"] / max(1, acc["n_syrk"])
+    achieved = flops / (syrk_ms / 1e3) / 1e12 if acc["n_syrk"] else None
     roofline = {"kernel": "k_syrk_fp64 (A^T W^-1 A, FP64 DFMA)", "bound": "alu",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
                 "traffic": SYRK_TRAFFIC_BYTES if (D["n_d"], D["m_E"]) == (2000, 100000) else None,
                 "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (FP64 is not in MEASURED_PEAKS.json)",
-                "flops_per_launch": flops, "avg_launch_ms": syrk_ms, "launches": stats["n_syrk"],
-                "share_of_step": stats["t_syrk_ms"] / (1e3 * elapsed) if elapsed else None}
-    cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        n_cpu, el = oracle_steps(inst, 0, args.cpu_steps)
-        cpu = {"value": n_cpu / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{n_cpu} IPM iterations from the default start of the FP64 numpy/scipy oracle "
-                         f"(condensed P2 form, multithreaded BLAS) on the same instance"}
+                "peak_probe": probe,
+                "frac_of_probe": achieved / probe["tflops"] if (achieved and probe) else None,
+                "flops_per_launch": flops, "avg_launch_ms": syrk_ms, "launches": int(acc["n_syrk"]),
+                "share_of_step": acc["t_syrk_ms"] / (1e3 * elapsed) if elapsed else None}
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps_done,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / max(1, steps_done),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": workload_name(args.config), "path": "P2 (two-stage elimination)",
-                   "reduced_N": D["n_d"] + D["m_I"], "steps_timed": steps_done, "status": m.STATUS[st],
+                   "reduced_N": D["n_d"] + D["m_I"], "steps_requested": K,
+                   "steps_timed": steps_done, "solve_calls": acc["solve_calls"],
+                   "timed_steps": f"iterations {args.warmup + 1}.. of the solve from its iterate {args.warmup}, "
+                                  f"restarted there when it converges",
+                   "statuses": acc["statuses"],
                    "l2": "no flush: every step streams A (m_E x n_d FP64 = "
                          f"{D['m_E'] * D['n_d'] * 8 / 1e9:.2f} GB) > 135 MB L2",
                    "parallelism": f"replicas x{world} (independent instances)"},
         "roofline": roofline,
         "condensation_plus_ldlt_roofline": cond_ldlt_roofline(
-            inst, syrk_ms, stats["t_ldlt_ms"] / max(1, stats["n_ldlt"]), "fp64"),
+            _dims(args.config), syrk_ms, acc["t_ldlt_ms"] / max(1, acc["n_ldlt"]), "fp64"),
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_units / e2e_max, "unit": UNIT, "h2d_bytes_per_step": psize * 8,
-                "d2h_bytes_per_step": psize * 8},
+                "d2h_bytes_per_step": psize * 8, "steps": n_e2e},
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "solve": solve,
         "variants": variants,
+        "mixed_precision": mixed,
         "batched": batch,
         "warm_start": wstart,
-        "phase_ms_per_step": {k: stats[k] / max(1, steps_done) for k in
+        "phase_ms_per_step": {k: acc[k] / max(1, steps_done) for k in
                               ("t_condense_ms", "t_factor_ms", "t_solve_ms", "t_ls_ms", "t_syrk_ms",
                                "t_ldlt_ms")},
     }
@@ -656,6 +937,13 @@ def run_kernel(args):
             flops = n * (n + 1) / 2 * mm * 2.0
             prec = m.MDSIP_PREC_BF16 if args.kernel == "syrk_bf16" else m.MDSIP_PREC_TF32
             call = lambda: m.mdsip_syrk_scaled_tc(ctx, mm, n, A, n, w, 0.0, Cm, n, prec)
+        elif args.kernel == "dfma":
+            p = fp64_fma_probe(m, torch, ctx, 0)
+            print(json.dumps({"kernel": "dfma", "tflops": p["tflops"], "ms_median": p["ms_median"],
+                              "blocks": p["blocks"], "iters_per_thread": p["iters_per_thread"],
+                              "derived_peak_tflops": FP64_PEAK_TFLOPS,
+                              "frac_of_derived": p["tflops"] / FP64_PEAK_TFLOPS}))
+            return
         elif args.kernel == "gemm_bf16":
             # the warm-start network's output layer: (batch m) x (outputs n) x (hidden k)
             M, N, K = args.m, args.n, args.k
@@ -671,19 +959,38 @@ def run_kernel(args):
             if N <= 4096:
                 G = rng.standard_normal((k, k))
                 H = G @ G.T / k + 0.1 * np.eye(k)
-            else:   # large orders: a shifted random symmetric block (no host matrix product)
-                G = rng.standard_normal((k, k)) / np.sqrt(k)
-                H = 0.5 * (G + G.T) + 3.0 * np.eye(k)
-            J = rng.standard_normal((N - k, k))
-            if args.ldlt_matrix == "ipm":
-                H = H + np.diag(rng.uniform(1.0, 3.0, k))
-                J *= 0.1
-            K = np.zeros((N, N))
-            K[:k, :k] = H
-            K[k:, :k] = J
-            K[:k, k:] = J.T
-            K[k:, k:] = -np.eye(N - k) if args.ldlt_matrix == "kkt" else -np.diag(rng.uniform(0.5, 2.0, N - k))
-            S0 = torch.as_tensor(np.tril(K).T.copy()).cuda()
+                J = rng.standard_normal((N - k, k))
+                if args.ldlt_matrix == "ipm":
+                    H = H + np.diag(rng.uniform(1.0, 3.0, k))
+                    J *= 0.1
+                K = np.zeros((N, N))
+                K[:k, :k] = H
+                K[k:, :k] = J
+                K[:k, k:] = J.T
+                K[k:, k:] = (-np.eye(N - k) if args.ldlt_matrix == "kkt"
+                             else -np.diag(rng.uniform(0.5, 2.0, N - k)))
+                S0 = torch.as_tensor(np.tril(K).T.copy()).cuda()
+            else:
+                # large orders, drawn on the device (seeded): H = 3 I + a symmetric random block
+                # of spectral radius ~1.4, J ~ N(0, 1) (kkt) or 0.1 N(0, 1) plus a diagonal lift (ipm)
+                gen = torch.Generator(device="cuda").manual_seed(N)
+                S0 = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+                B = torch.randn((k, k), dtype=torch.float64, device="cuda", generator=gen) / np.sqrt(k)
+                S0[:k, :k] = 0.5 * (B + B.T)
+                del B
+                S0[:k, :k] += torch.diag(torch.full((k,), 3.0, dtype=torch.float64, device="cuda"))
+                J = torch.randn((N - k, k), dtype=torch.float64, device="cuda", generator=gen)
+                if args.ldlt_matrix == "ipm":
+                    S0[:k, :k] += torch.diag(1.0 + 2.0 * torch.rand(k, dtype=torch.float64, device="cuda",
+                                                                    generator=gen))
+                    J *= 0.1
+                S0[k:, :k] = J
+                S0[:k, k:] = J.T
+                del J
+                S0[k:, k:] = (-torch.eye(N - k, dtype=torch.float64, device="cuda") if args.ldlt_matrix == "kkt"
+                              else -torch.diag(0.5 + 1.5 * torch.rand(N - k, dtype=torch.float64, device="cuda",
+                                                                      generator=gen)))
+                K = None            # symmetric: S0's row-major storage is its column-major lower triangle
             S = torch.empty_like(S0)
             L = torch.empty((N, N), dtype=torch.float64, device="cuda")
             Dd = torch.empty(N, dtype=torch.float64, device="cuda")
@@ -703,7 +1010,7 @@ def run_kernel(args):
             if args.kernel == "ldlt_library":
                 # context only: the vendor library's Bunch-Kaufman (cuSOLVER sytrf behind
                 # torch.linalg.ldl_factor_ex) on the same matrix, full symmetric storage
-                Kf = torch.as_tensor(K).cuda()
+                Kf = torch.as_tensor(K).cuda() if K is not None else S0.clone()
                 Kw = torch.empty_like(Kf)
 
                 def call():
@@ -748,6 +1055,9 @@ def run_kernel(args):
 
 def main():
     args = parse()
+    if args.oracle_sample:
+        run_oracle_sample(args)
+        return
     if args.kernel:
         run_kernel(args)
         return

@@ -320,7 +320,8 @@ mdsip_status mdsip_syrk_scaled(mdsip_ctx *ctx, int64_t m, int64_t n, const doubl
 
 /* The same product on the tensor cores: precision MDSIP_PREC_TF32 or
  * MDSIP_PREC_BF16 operands A[i][p] * w_i^-1/2 (rounded to that type), FP32
- * accumulation over K ranges, FP64 sum of the ranges.  Arguments as above
+ * accumulation over K ranges, the ranges' partial sums added in FP32 and
+ * their total added to C in FP64.  Arguments as above
  * (w > 0 required).  Relative error per entry of order the operand type's
  * unit roundoff times sum_i |A[i][p] A[i][q]| / w_i. */
 mdsip_status mdsip_syrk_scaled_tc(mdsip_ctx *ctx, int64_t m, int64_t n, const double *A, int64_t lda,

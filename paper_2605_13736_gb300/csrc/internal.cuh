@@ -347,6 +347,9 @@ void launch_ldlt(cudaStream_t s, int num_sms, int64_t N, const double *S, int64_
                  int *err_dev, bool fp32_update = false, int nb = 0, bool spec = true);
 size_t ldlt_blocked_scratch_bytes(int64_t N);
 bool ldlt_blocked_available(int64_t N);
+// with speculation on, the blocked factorization first runs its persistent
+// no-interchange kernel and reads back where it stopped (synchronises the stream)
+bool ldlt_persistent_path(int64_t N, bool spec);
 std::vector<int> ldlt_blocked_widths(int64_t N, bool f32);
 void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, const double *maxabs_dev,
                          double zero_tol, LdltOut out, void *scratch, bool fp32_update, int nb = 0,

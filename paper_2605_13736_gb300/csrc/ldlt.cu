@@ -554,6 +554,9 @@ static constexpr size_t ldlt_unblocked_scratch_bytes(int64_t N) {
 }
 
 size_t ldlt_scratch_bytes(int64_t N) {
+    // the unblocked kernel keeps 2 N doubles in shared memory: beyond that order
+    // only the blocked scratch is ever used
+    if (2 * (size_t)N * sizeof(double) > kMaxDynSmem) return ldlt_blocked_scratch_bytes(N);
     return std::max(ldlt_unblocked_scratch_bytes(N), ldlt_blocked_scratch_bytes(N));
 }
 
@@ -625,7 +628,7 @@ static void launch_ldlt_unblocked(cudaStream_t s, int num_sms, int64_t N, const 
 void launch_ldlt(cudaStream_t s, int num_sms, int64_t N, const double *S, int64_t ld,
                  const double *maxabs_dev, double zero_tol, LdltOut out, void *scratch,
                  int *err_dev, bool fp32_update, int nb, bool spec) {
-    if (N > 0 && ld == N && ldlt_blocked_available(N)) {
+    if (N > 0 && ld == N && (ldlt_blocked_available(N) || ldlt_persistent_path(N, spec))) {
         launch_ldlt_blocked(s, num_sms, N, const_cast<double *>(S), maxabs_dev, zero_tol, out, scratch,
                             fp32_update, nb, spec);
         return;

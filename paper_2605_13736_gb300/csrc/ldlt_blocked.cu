@@ -545,27 +545,24 @@ __device__ __forceinline__ void load4(const double *p, double (&v)[4]) {
     v[3] = y.y;
 }
 
+// One 64 x 64 tile (number `tile` in row-major order over the lower
+// triangle of tiles) of the trailing update after a panel of kb columns
+// starting at k0: A(i, c) -= sum_t L(i, k0 + t) W(c, t) for i >= c >= base =
+// k0 + kb.  kUpdThreads threads; smem holds 2 S 64 values of T, S >= kb the
+// pitch the launch sized it for (panel width + 1: a pivoting panel may end
+// with a 2x2 pivot and take one column more).
 template <typename T>
-__global__ void __launch_bounds__(kUpdThreads) k_bk_trailing(int N, int NB, double *__restrict__ A,
-                                                             const double *__restrict__ L,
-                                                             const double *__restrict__ Wg,
-                                                             const float *__restrict__ Lf,
-                                                             const float *__restrict__ Wf,
-                                                             const PanelState *__restrict__ st) {
-    pdl_wait();
-    pdl_release();
-    extern __shared__ __align__(16) unsigned char usmem[];
-    const int S = NB + 1;
+__device__ void trailing_tile(int tile, int N, int kb, int k0, int S, double *__restrict__ A,
+                              const double *__restrict__ L, const double *__restrict__ Wg,
+                              const float *__restrict__ Lf, const float *__restrict__ Wf, unsigned char *usmem) {
     T *Lt = reinterpret_cast<T *>(usmem);          // [S][64]: Lt[t][r]
     T *Wt = Lt + (size_t)S * kUT;                   // [S][64]: Wt[t][c]
-    const int kb = st->kb;
-    const int k0 = st->k - kb;                      // first column of the last panel
-    const int base = st->k;
+    const int base = k0 + kb;
     if (base >= N || kb <= 0) return;
-    int tr = (int)((sqrt(8.0 * (double)blockIdx.x + 1.0) - 1.0) * 0.5);
-    while ((tr + 1) * (tr + 2) / 2 <= (int)blockIdx.x) ++tr;
-    while (tr * (tr + 1) / 2 > (int)blockIdx.x) --tr;
-    const int tc = (int)blockIdx.x - tr * (tr + 1) / 2;
+    int tr = (int)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
+    while ((tr + 1) * (tr + 2) / 2 <= tile) ++tr;
+    while (tr * (tr + 1) / 2 > tile) --tr;
+    const int tc = tile - tr * (tr + 1) / 2;
     const int i0 = base + tr * kUT, c0 = base + tc * kUT;
     if (i0 >= N) return;
     const int tid = threadIdx.x;
@@ -626,6 +623,20 @@ __global__ void __launch_bounds__(kUpdThreads) k_bk_trailing(int N, int NB, doub
             if (i < N && i >= c) A[i + (int64_t)c * N] -= (double)acc[u][v];
         }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kUpdThreads) k_bk_trailing(int N, int NB, double *__restrict__ A,
+                                                             const double *__restrict__ L,
+                                                             const double *__restrict__ Wg,
+                                                             const float *__restrict__ Lf,
+                                                             const float *__restrict__ Wf,
+                                                             const PanelState *__restrict__ st) {
+    pdl_wait();
+    pdl_release();
+    extern __shared__ __align__(16) unsigned char usmem[];
+    const int kb = st->kb;
+    trailing_tile<T>((int)blockIdx.x, N, kb, st->k - kb, NB + 1, A, L, Wg, Lf, Wf, usmem);
 }
 
 // ---------------------------------------------------------------------------
@@ -1002,10 +1013,329 @@ __global__ void __launch_bounds__(kSpecThreads) k_bk_spec_rows(SpecArgs a) {
     }
 }
 
-__global__ void k_bk_init(int N, int32_t *perm, PanelState *st, unsigned long long *cmax) {
+// ---------------------------------------------------------------------------
+// Persistent speculative factorization (one cooperative launch for all panels).
+//
+// The same no-interchange speculation as k_bk_spec, organised so that a kept
+// panel costs no launch: one grid of co-resident CTAs walks the panels of 64
+// columns, with a grid barrier after the panel (all column maxima known) and
+// one after its trailing update.  Per panel:
+//   A1 every CTA factors the 64 x 64 diagonal block in shared memory without
+//      interchanges, in four sub-panels of 16 columns: warp 0 factors the
+//      16 x 16 diagonal sub-block with register shuffles, one thread per row
+//      solves the rows below it, and a rank-16 update brings the rest of the
+//      block up to date (three block barriers per sub-panel instead of one
+//      per column);
+//   A2 each CTA takes a slice of the rows below the block, one thread per
+//      row: the row's 64 values in registers, solved against the block's
+//      factor (right-looking, no barrier); the FP64 values w = A - sum L W,
+//      L = w / d and the column maxima of |w| (exact FP64 bit patterns,
+//      atomicMax) follow;
+//   B  after the grid barrier every CTA applies the rule's column test to the
+//      64 columns with the same data: the panel is kept when every column
+//      keeps its diagonal pivot (|a_jj| >= alpha colmax_j, or a zero column)
+//      and no pivot is within zero_tol max|S| of zero;
+//   C  the trailing update of a kept panel, tiles of the lower triangle over
+//      all CTAs; grid barrier.
+// The first panel that fails the column test (the rule would look at a row
+// or interchange) ends the kernel with st->k at its first column; the host
+// then runs the pivoting panels from there.  Chain arithmetic and the update
+// products are T (FP32 on the refined mixed-precision path, FP64 otherwise);
+// pivots, L, the tests and the inertia are FP64.
+// ---------------------------------------------------------------------------
+constexpr int kPThreads = 256;
+constexpr int kPP = 65;      // shared-memory row pitch of the diagonal block
+
+struct PanelBar {
+    unsigned count, gen;
+    int err, pad;
+};
+
+struct PersistArgs {
+    int N;
+    double *A;                      // lower triangle, column-major, ld N (trailing part updated in place)
+    double *L, *Dd, *Doff;
+    int32_t *kind;
+    double *Wg;                     // FP64 W of the current panel (T = double), ld N
+    float *Lf, *Wf;                 // FP32 L and W of the current panel (T = float), ld N
+    unsigned long long *cmax;       // [2][64]: per-column maxima of |w| (bit patterns), by panel parity
+    PanelState *st;
+    PanelBar *bar;
+    const double *maxabs;
+    double zero_tol;
+    long long wait_ns;              // bound of each grid-barrier wait
+};
+
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier of a cooperative launch (all CTAs co-resident).  Every
+// wait is bounded: a CTA that waits longer than wait_ns sets the error word
+// and returns false, and so does every CTA that sees the word set.
+__device__ bool panel_barrier(PanelBar *b, long long wait_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *vgen = &b->gen;
+        volatile int *verr = &b->err;
+        const unsigned gen = *vgen;
+        __threadfence();
+        if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            const long long t0 = global_ns();
+            while (*vgen == gen) {
+                if (*verr) break;
+                __nanosleep(64);
+                if (global_ns() - t0 > wait_ns) {
+                    atomicExch(&b->err, 1);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        if (*verr) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T chain_rcp(T d) {
+    if constexpr (sizeof(T) == sizeof(float)) return d != 0.0f ? __frcp_rn(d) : 0.0f;
+    else return d != 0.0 ? 1.0 / d : 0.0;
+}
+
+// w in FP64 from a chain value v: for FP32 chains the part of A that the FP32
+// copy dropped is added back (v started as float(A))
+template <typename T>
+__device__ __forceinline__ double chain_w64(T v, double a) {
+    if constexpr (sizeof(T) == sizeof(float)) return (double)v + (a - (double)(float)a);
+    else return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPThreads, 1) k_bk_persist(PersistArgs a) {
+    extern __shared__ __align__(16) unsigned char psm[];
+    T *V = reinterpret_cast<T *>(psm);      // [64][kPP]: the diagonal block; W values once factored
+    __shared__ double s_d[64], s_rd[64];    // FP64 pivots and their reciprocals
+    __shared__ T s_rc[64];                  // the chain's reciprocals
+    __shared__ unsigned long long s_cmax[64];
+    __shared__ int s_keep;
+    const int N = a.N, G = (int)gridDim.x, g = (int)blockIdx.x, tid = threadIdx.x;
+    const int lane = tid & 31;
+    const double alpha = 0.6403882032022076;   // (1 + sqrt 17) / 8
+    const double ztol = a.zero_tol * __ldg(a.maxabs);
+    int p = 0;
+    for (int k = a.st->k; k < N; k += 64, ++p) {
+        const int nb = min(64, N - k);
+        const int buf = p & 1;
+        // ---------------- A1: the diagonal block
+        for (int e = tid; e < 64 * 64; e += kPThreads) {
+            const int c = e >> 6, r = e & 63;
+            T v = (T)0;
+            if (r < nb && c <= r) v = (T)a.A[(int64_t)(k + r) + (int64_t)(k + c) * N];
+            V[r * kPP + c] = v;
+        }
+        if (tid < 64) {
+            s_cmax[tid] = 0ULL;
+            s_rc[tid] = (T)0;      // columns beyond a narrow last panel stay zero
+        }
+        __syncthreads();
+        for (int c0 = 0; c0 < nb; c0 += 16) {
+            const int cw = min(16, nb - c0);
+            if (tid < 32) {   // warp 0: the 16 x 16 sub-block, lane = row c0 + lane
+                T v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = (lane < cw && j <= lane) ? V[(c0 + lane) * kPP + c0 + j] : (T)0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const T dj = __shfl_sync(0xffffffffu, v[j], j);
+                    const T rj = j < cw ? chain_rcp(dj) : (T)0;
+                    const T l = v[j] * rj;
+#pragma unroll
+                    for (int t = j + 1; t < 16; ++t) {
+                        const T wtj = __shfl_sync(0xffffffffu, v[j], t);
+                        if (lane >= t && lane < cw) v[t] = fma(-l, wtj, v[t]);
+                    }
+                    if (lane == j && j < cw) s_rc[c0 + j] = rj;
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (lane < cw && j <= lane) V[(c0 + lane) * kPP + c0 + j] = v[j];
+            }
+            __syncthreads();
+            // rows of the block below the sub-block
+            for (int r = c0 + 16 + tid; r < nb; r += kPThreads) {
+                T v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = j < cw ? V[r * kPP + c0 + j] : (T)0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const T l = j < cw ? v[j] * s_rc[c0 + j] : (T)0;
+#pragma unroll
+                    for (int t = j + 1; t < 16; ++t)
+                        if (t < cw) v[t] = fma(-l, V[(c0 + t) * kPP + c0 + j], v[t]);
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (j < cw) V[r * kPP + c0 + j] = v[j];
+            }
+            __syncthreads();
+            // rank-16 update of the rest of the block (lower triangle)
+            const int m0 = c0 + 16, mw = nb - m0;
+            if (mw > 0) {
+                const int npairs = mw * (mw + 1) / 2;
+                for (int e = tid; e < npairs; e += kPThreads) {
+                    int rr = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+                    while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+                    while (rr * (rr + 1) / 2 > e) --rr;
+                    const int r = m0 + rr, c = m0 + (e - rr * (rr + 1) / 2);
+                    T acc = V[r * kPP + c];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (j < cw) acc = fma(-(V[r * kPP + c0 + j] * s_rc[c0 + j]), V[c * kPP + c0 + j], acc);
+                    V[r * kPP + c] = acc;
+                }
+            }
+            __syncthreads();
+        }
+        // FP64 pivots
+        if (tid < 64) {
+            double d = 0.0, rd = 0.0;
+            if (tid < nb) {
+                d = chain_w64<T>(V[tid * kPP + tid], a.A[(int64_t)(k + tid) * (N + 1)]);
+                rd = rcp_newton(d);
+            }
+            s_d[tid] = d;
+            s_rd[tid] = rd;
+        }
+        __syncthreads();
+        // CTA 0: the block's L and D, and the column maxima of its rows
+        if (g == 0) {
+            for (int e = tid; e < 64 * 64; e += kPThreads) {
+                const int c = e >> 6, r = e & 63;
+                if (r >= nb || c >= nb || r < c) continue;
+                const int64_t o = (int64_t)(k + r) + (int64_t)(k + c) * N;
+                if (r == c) {
+                    a.L[o] = 1.0;
+                    a.Dd[k + c] = s_d[c];
+                } else {
+                    const double w = chain_w64<T>(V[r * kPP + c], a.A[o]);
+                    a.L[o] = w * s_rd[c];
+                    atomicMax(&s_cmax[c], absbits64(w));
+                }
+            }
+        }
+        // ---------------- A2: this CTA's rows below the block
+        const int brow = N - k - nb;
+        const int R = (brow + G - 1) / G;
+        const int r_begin = k + nb + g * R, r_end = min(N, r_begin + R);
+        for (int base = r_begin; base < r_end; base += kPThreads) {
+            const int i = base + tid;
+            const bool act = i < r_end;
+            T v[64];
+#pragma unroll
+            for (int t = 0; t < 64; ++t) v[t] = (act && t < nb) ? (T)a.A[(int64_t)i + (int64_t)(k + t) * N] : (T)0;
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                const T l = v[j] * s_rc[j];
+#pragma unroll
+                for (int t = j + 1; t < 64; ++t) v[t] = fma(-l, V[t * kPP + j], v[t]);
+            }
+#pragma unroll
+            for (int t = 0; t < 64; ++t) {
+                unsigned long long b = 0ULL;
+                if (act && t < nb) {
+                    const int64_t o = (int64_t)i + (int64_t)(k + t) * N;
+                    const double w = chain_w64<T>(v[t], a.A[o]);
+                    const double l = w * s_rd[t];
+                    a.L[o] = l;
+                    if constexpr (sizeof(T) == sizeof(float)) {
+                        a.Lf[(int64_t)i + (int64_t)t * N] = (float)l;
+                        a.Wf[(int64_t)i + (int64_t)t * N] = (float)w;
+                    } else {
+                        a.Wg[(int64_t)i + (int64_t)t * N] = w;
+                    }
+                    b = absbits64(w);
+                }
+                const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(b >> 32));
+                const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(b >> 32) == hi ? (unsigned)b : 0u);
+                if (lane == 0 && (hi | lo)) atomicMax(&s_cmax[t], ((unsigned long long)hi << 32) | lo);
+            }
+        }
+        __syncthreads();
+        if (tid < 64 && s_cmax[tid]) atomicMax(&a.cmax[buf * 64 + tid], s_cmax[tid]);
+        if (!panel_barrier(a.bar, a.wait_ns)) return;
+        // ---------------- B: the rule's column test, the same in every CTA
+        {
+            int keep = 1;
+            if (tid < nb) {
+                const double d = s_d[tid];
+                const unsigned long long cb = __ldcg(&a.cmax[buf * 64 + tid]);
+                const double colmax = __longlong_as_double((long long)cb);
+                const bool diag_ok = absbits64(d) >= absbits64(alpha * colmax);
+                if (!diag_ok || d == 0.0 || fabs(d) <= ztol || !isfinite(d) || !isfinite(colmax)) keep = 0;
+            }
+            keep = __syncthreads_and(keep);
+            if (tid == 0) s_keep = keep;
+        }
+        __syncthreads();
+        if (!s_keep) {
+            if (g == 0 && tid == 0) {   // the panel loop takes over at column k
+                a.st->k = k;
+                a.st->kb = 0;
+                a.st->spec = 0;
+            }
+            return;
+        }
+        if (g == 0) {
+            int pos = 0;
+            if (tid < nb) {
+                a.kind[k + tid] = 1;
+                a.Doff[k + tid] = 0.0;
+                pos = s_d[tid] > 0.0 ? 1 : 0;
+            }
+            if (tid < 64) a.cmax[(buf ^ 1) * 64 + tid] = 0ULL;   // the next panel's maxima start at zero
+            const int np = __syncthreads_count(pos);
+            if (tid == 0) {
+                a.st->npos += np;
+                a.st->nneg += nb - np;
+                a.st->k = k + nb;
+                a.st->kb = nb;
+                a.st->nacc += 1;
+            }
+        }
+        if (k + nb >= N) break;
+        // ---------------- C: trailing update
+        {
+            const int base = k + nb;
+            const int nt = (N - base + kUT - 1) / kUT;
+            const int tiles = nt * (nt + 1) / 2;
+            for (int t = g; t < tiles; t += G) {
+                trailing_tile<T>(t, N, nb, k, 65, a.A, a.L, a.Wg, a.Lf, a.Wf, psm);
+                __syncthreads();
+            }
+        }
+        __threadfence();
+        if (!panel_barrier(a.bar, a.wait_ns)) return;
+    }
+}
+
+__global__ void k_bk_init(int N, int32_t *perm, PanelState *st, unsigned long long *cmax, PanelBar *bar) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) perm[i] = i;
     if (blockIdx.x == 0 && threadIdx.x < 128) cmax[threadIdx.x] = 0ULL;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+        bar->count = 0u;
+        bar->gen = 0u;
+        bar->err = 0;
         st->k = 0;
         st->kb = 0;
         st->npos = st->nneg = st->nzero = 0;
@@ -1148,6 +1478,48 @@ BlockedScratch blocked_scratch(int64_t N) {
 
 }  // namespace
 
+// the grid barrier of the persistent kernel shares the panel state's slot
+PanelBar *grid_bar(char *w, const BlockedScratch &lay) { return reinterpret_cast<PanelBar *>(w + lay.st + 128); }
+
+// dynamic shared memory of k_bk_persist<T>: the diagonal block, or the staged
+// rows of a trailing-update tile
+template <typename T>
+size_t persist_smem() {
+    return std::max((size_t)64 * kPP * sizeof(T), 2 * (size_t)65 * kUT * sizeof(T));
+}
+
+// Run k_bk_persist from column 0; returns the column where it stopped (N: all
+// panels kept).  One cooperative launch; reads two words back (synchronises
+// the stream).
+template <typename T>
+int run_persistent(cudaStream_t s, int num_sms, int N, const PersistArgs &pa, PanelState *st, PanelBar *bar) {
+    static PerDeviceOnce once;
+    MDSIP_CUDA(once.run([] {
+        return cudaFuncSetAttribute(k_bk_persist<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)persist_smem<T>());
+    }));
+    int per_sm = 0;
+    MDSIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bk_persist<T>, kPThreads,
+                                                             persist_smem<T>()));
+    MDSIP_REQUIRE(per_sm >= 1, MDSIP_ERR_CUDA, "ldlt: persistent factorization does not fit an SM");
+    // about three trailing tiles per CTA after the first panel, at most one CTA per SM
+    const int64_t nt = std::max<int64_t>(1, (N - 64 + kUT - 1) / kUT);
+    const int64_t want = std::max<int64_t>(1, (nt * (nt + 1) / 2 + 2) / 3);
+    const int G = (int)std::min<int64_t>(want, (int64_t)num_sms);
+    PersistArgs args = pa;
+    void *kargs[] = {&args};
+    MDSIP_CUDA(cudaLaunchCooperativeKernel((const void *)k_bk_persist<T>, dim3(G), dim3(kPThreads), kargs,
+                                           persist_smem<T>(), s));
+    count_launch();
+    thread_local int *h = nullptr;
+    if (!h) MDSIP_CUDA(cudaMallocHost(&h, 4 * sizeof(int)));
+    MDSIP_CUDA(cudaMemcpyAsync(h, &st->k, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MDSIP_CUDA(cudaMemcpyAsync(h + 1, &bar->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MDSIP_CUDA(cudaStreamSynchronize(s));
+    MDSIP_REQUIRE(h[1] == 0, MDSIP_ERR_DEVICE, "ldlt: a bounded grid-barrier wait expired");
+    return h[0];
+}
+
 size_t ldlt_blocked_scratch_bytes(int64_t N) { return blocked_scratch(N).total; }
 
 // panel widths that fit for order N (widest first)
@@ -1160,6 +1532,12 @@ std::vector<int> ldlt_blocked_widths(int64_t N, bool f32) {
 
 bool ldlt_blocked_available(int64_t N) { return blocked_config(N, true).C > 0 && blocked_config(N, false).C > 0; }
 
+// The persistent no-interchange factorization runs first (and the host reads
+// back where it stopped) whenever speculation is on; it needs no pivoting
+// panel unless a panel fails the column test, so it also serves orders whose
+// pivoting panel does not fit shared memory.
+bool ldlt_persistent_path(int64_t N, bool spec) { return spec && N > 0 && N <= (int64_t)0x7fffffff / 2; }
+
 // S (lower, ld N) is overwritten.  scratch: ldlt_blocked_scratch_bytes(N),
 // 256-byte aligned.  fp32_update: trailing products in FP32.  spec (with
 // fp32_update): each panel first tries the verified no-interchange path.
@@ -1171,15 +1549,43 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
     }
     BlockedConfig cfg = blocked_config(N, fp32_update, nb);
     if (cfg.C == 0) cfg = blocked_config(N, fp32_update);
-    MDSIP_REQUIRE(cfg.C > 0, MDSIP_ERR_INVALID_ARG, "ldlt: N too large for the blocked factorization");
+    const bool persist = ldlt_persistent_path(N, spec);
+    MDSIP_REQUIRE(cfg.C > 0 || persist, MDSIP_ERR_INVALID_ARG, "ldlt: N too large for the blocked factorization");
     char *w = static_cast<char *>(scratch);
     MDSIP_REQUIRE((reinterpret_cast<uintptr_t>(w) & 255) == 0, MDSIP_ERR_INVALID_ARG, "ldlt: misaligned scratch");
     const BlockedScratch lay = blocked_scratch(N);
     double *Wg = reinterpret_cast<double *>(w + lay.wg);
     PanelState *st = reinterpret_cast<PanelState *>(w + lay.st);
+    PanelBar *bar = grid_bar(w, lay);
     k_bk_init<<<std::max(1, std::min(1024, ceil_div(N, 256))), 256, 0, s>>>(
-        (int)N, out.perm, st, reinterpret_cast<unsigned long long *>(w + lay.cmax));
+        (int)N, out.perm, st, reinterpret_cast<unsigned long long *>(w + lay.cmax), bar);
     MDSIP_LAUNCHED();
+    int k0 = 0;   // first column left to the panel loop below
+    if (persist) {
+        PersistArgs pa{};
+        pa.N = (int)N;
+        pa.A = S;
+        pa.L = out.L;
+        pa.Dd = out.Dd;
+        pa.Doff = out.Doff;
+        pa.kind = out.kind;
+        pa.Wg = Wg;
+        pa.Lf = reinterpret_cast<float *>(w + lay.lf);
+        pa.Wf = reinterpret_cast<float *>(w + lay.wf);
+        pa.cmax = reinterpret_cast<unsigned long long *>(w + lay.cmax);
+        pa.st = st;
+        pa.bar = bar;
+        pa.maxabs = maxabs_dev;
+        pa.zero_tol = zero_tol;
+        pa.wait_ns = 20LL * 1000 * 1000 * 1000;   // 20 s: far above the longest phase (FP64 update at N ~ 44000)
+        k0 = fp32_update ? run_persistent<float>(s, num_sms, (int)N, pa, st, bar)
+                         : run_persistent<double>(s, num_sms, (int)N, pa, st, bar);
+        MDSIP_REQUIRE(k0 >= N || cfg.C > 0, MDSIP_ERR_INVALID_ARG,
+                      "ldlt: a panel needs interchanges and N is too large for the pivoting panel");
+        // the panel loop's no-interchange kernels expect their column maxima and
+        // arg-max keys at zero; the rejected panel left its maxima there
+        if (k0 < N) MDSIP_CUDA(cudaMemsetAsync(w + lay.cmax, 0, 128 * sizeof(unsigned long long), s));
+    }
 
     PanelArgs a{};
     a.N = (int)N;
@@ -1209,9 +1615,8 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
                                      (int)(2 * 65 * kUT * sizeof(float)));
         return e;
     }));
-    spec = spec && fp32_update;
     SpecArgs sa{};
-    if (spec) {
+    if (spec && fp32_update) {
         sa.N = (int)N;
         sa.NB = cfg.NB;
         sa.A = S;
@@ -1232,23 +1637,24 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
             return cudaFuncSetAttribute(k_bk_spec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spec_smem(64));
         }));
     }
-    const int npanels = (int)((N + cfg.NB - 1) / cfg.NB);
+    // panels from column k0 on (all of them without the persistent kernel)
+    const int npanels = k0 >= N ? 0 : (int)((N - k0 + cfg.NB - 1) / cfg.NB);
     for (int p = 0; p < npanels; ++p) {
-        if (spec) {
-            // rows below the diagonal block: at most N - (p + 1) NB (every panel takes >= NB columns)
-            const int64_t below = N - (int64_t)(p + 1) * cfg.NB;
+        if (spec && fp32_update) {
+            // rows below the diagonal block: at most N - k0 - (p + 1) NB (every panel takes >= NB columns)
+            const int64_t below = N - k0 - (int64_t)(p + 1) * cfg.NB;
             const int G = (int)std::max<int64_t>(1, (below + kSpecRB - 1) / kSpecRB);
             launch_pdl(k_bk_spec, (unsigned)G, kSpecChainThreads, spec_smem(cfg.NB), s, 1, sa);
-            // rows of the active matrix: at most N - p NB
-            const int G2 = (int)std::max<int64_t>(1, (N - (int64_t)p * cfg.NB + 31) / 32);
+            // rows of the active matrix: at most N - k0 - p NB
+            const int G2 = (int)std::max<int64_t>(1, (N - k0 - (int64_t)p * cfg.NB + 31) / 32);
             launch_pdl(k_bk_spec_rows, (unsigned)G2, kSpecThreads, 0, s, 1, sa);
         }
         if (fp32_update)
             launch_pdl(k_bk_panel<true>, (unsigned)cfg.C, kPanelThreads, cfg.smem, s, cfg.C, a);
         else
             launch_pdl(k_bk_panel<false>, (unsigned)cfg.C, kPanelThreads, cfg.smem, s, cfg.C, a);
-        // trailing matrix after panel p starts at column >= (p + 1) NB
-        const int64_t rest = N - (int64_t)(p + 1) * cfg.NB;
+        // trailing matrix after panel p starts at column >= k0 + (p + 1) NB
+        const int64_t rest = N - k0 - (int64_t)(p + 1) * cfg.NB;
         if (rest <= 0) continue;
         const int64_t nt = (rest + kUT - 1) / kUT;
         const unsigned tiles = (unsigned)(nt * (nt + 1) / 2);

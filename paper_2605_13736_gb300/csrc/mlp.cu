@@ -637,10 +637,14 @@ mdsip_status mdsip_mlp_train_step(mdsip_mlp *hm, const double *X, int64_t ldx, c
         DeviceGuard g(m->ctx->device);
         run_gradient(m, X, ldx, Y, ldy, idx, batch);
         m->t += 1;
-        const double bc1 = 1.0 - std::pow(m->beta1, (double)m->t), bc2 = 1.0 - std::pow(m->beta2, (double)m->t);
+        // the moments decay with the FP32 rates the kernel uses, so the bias
+        // corrections 1 - beta^t take those same rates (Kingma-Ba Algorithm 1);
+        // with the FP64 rates 1 - 0.999 and 1 - fl32(0.999) differ by 1.3e-5
+        const float b1f = (float)m->beta1, b2f = (float)m->beta2;
+        const double bc1 = 1.0 - std::pow((double)b1f, (double)m->t), bc2 = 1.0 - std::pow((double)b2f, (double)m->t);
         mdsip::k_adam<<<mdsip::grid_for(m->n_params, m->ctx->num_sms), 256, 0, m->ctx->stream>>>(
-            m->n_params, m->P(), m->G(), m->m1.as<float>(), m->m2.as<float>(), (float)lr, (float)m->beta1,
-            (float)m->beta2, (float)m->eps, (float)bc1, (float)bc2);
+            m->n_params, m->P(), m->G(), m->m1.as<float>(), m->m2.as<float>(), (float)lr, b1f, b2f,
+            (float)m->eps, (float)bc1, (float)bc2);
         MDSIP_LAUNCHED();
         m->cast_weights();
         if (loss) {

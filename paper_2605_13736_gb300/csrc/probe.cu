@@ -19,7 +19,16 @@ __global__ void __launch_bounds__(kProbeThreads) k_fp64_fma_probe(int64_t iters,
     double v[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) v[k] = 1e-3 * (k + 1) + 1e-6 * blockIdx.x;
-    for (int64_t i = 0; i < iters; ++i) {
+    // eight chain steps per loop trip: the loop's own instructions take a
+    // negligible share of the issue slots
+    int64_t i = 0;
+    for (; i + 8 <= iters; i += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = fma(v[k], a, b);
+    }
+    for (; i < iters; ++i) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) v[k] = fma(v[k], a, b);
     }

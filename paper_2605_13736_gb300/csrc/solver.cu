@@ -660,9 +660,10 @@ static int tuned_syrk_tile(Problem *P) {
 
 // Run the factorization phase `enqueue` on the problem's stream: eagerly on
 // its first use for an order, captured into a CUDA graph on the second (only
-// with the blocked factorization, whose launches need no host state), and as
-// one graph launch afterwards.  A capture that fails falls back to eager
-// launches for good.
+// with the blocked factorization's panel loop, whose launches need no host
+// state; the persistent factorization is a few launches and reads back where
+// it stopped, so it runs eagerly), and as one graph launch afterwards.  A
+// capture that fails falls back to eager launches for good.
 template <class F>
 static void run_factor_phase(Problem *P, int slot, F &&enqueue) {
     Problem::FactorGraph &g = P->fgraph[slot];
@@ -679,7 +680,9 @@ static void run_factor_phase(Problem *P, int slot, F &&enqueue) {
         return;
     }
     ++g.uses;
-    if (!P->opt.graphs || g.disabled || g.uses < 2 || !ldlt_blocked_available(P->N)) {
+    // the persistent factorization reads back where it stopped: nothing to capture
+    if (!P->opt.graphs || g.disabled || g.uses < 2 || !ldlt_blocked_available(P->N) ||
+        ldlt_persistent_path(P->N, P->opt.ldlt_spec != 0)) {
         enqueue();
         return;
     }
@@ -1083,6 +1086,7 @@ static mdsip_status run_ipm(Problem *P) {
         P->sync_scalars();
         Errs e0 = kkt_error(P, 0.0);
         mdsip_iter_rec rec{};
+        rec.dir_err_fp64 = -1.0;
         rec.iter = (int32_t)k;
         rec.mu = mu;
         rec.f = f;
@@ -1166,7 +1170,6 @@ static mdsip_status run_ipm(Problem *P) {
         rec.n_refine = rr.sweeps;
         rec.fp64_fallback = (rr.ok && !fp64) ? 0 : 1;
         rec.refine_res = rr.res;
-        rec.dir_err_fp64 = -1.0;
         if (o.direction_check && use_refined(P) && P->opt.precision != MDSIP_PREC_FP64 && !fp64 && !rr.fell_back)
             rec.dir_err_fp64 = fp64_direction_error(P, mu, dw, dc);
         // A.5 line search

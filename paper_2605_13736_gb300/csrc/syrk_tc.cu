@@ -3,9 +3,10 @@
 //     C[p][q] = beta C[p][q] + sum_i A[i][p] A[i][q] / w_i       (p >= q)
 //
 // computed as C = At At^T with At = (diag(w^-1/2) A)^T in BF16 (kind::f16) or
-// FP32 read as TF32 (kind::tf32), FP32 accumulation in tensor memory, and
-// FP64 summation of the split-K partials.  The FP64 caller wins the accuracy
-// back with iterative refinement of the Newton system.
+// FP32 read as TF32 (kind::tf32), FP32 accumulation in tensor memory, the
+// split-K partials summed in FP32 and their total added to the FP64 matrix
+// with one conversion per entry.  The FP64 caller wins the accuracy back with
+// iterative refinement of the Newton system.
 //
 // Structure (one CTA = one 128x128 lower-triangle tile x one K range):
 //   * warp 0 lane 0 streams 128-byte-wide K slabs of the two row blocks of

@@ -1,12 +1,23 @@
 """Batched solves (mdsip_batch_solve): independent instances of uneven sizes,
 each on its own context/stream, solved concurrently, give exactly the results
-of solving each one alone (the kernels are deterministic)."""
+of solving each one alone (the kernels are deterministic), and each batched
+result is the CPU oracle's own solve of that instance: the same iteration
+count and inertia-correction sequence, the objective to 1e-8 relative."""
 import numpy as np
 import pytest
 
 import paper_2605_13736_gb300 as m
 import synth
+from oracle import ipm
+from oracle.model import SynthModel
 from gpu_util import make_problem, torch_cuda
+
+
+@pytest.fixture(scope="module")
+def oracle_runs():
+    """The oracle's solve of every instance of _instances() (two-stage condensed
+    directions, pinned against the full 4x4 solve by the oracle's own tests)."""
+    return [ipm.solve(SynthModel(inst), opt=ipm.Options(linsolve="p2")) for inst in _instances()]
 
 pytestmark = pytest.mark.gpu
 
@@ -18,7 +29,7 @@ def _instances():
 
 
 @pytest.mark.parametrize("prec", [m.MDSIP_PREC_FP64, m.MDSIP_PREC_BF16])
-def test_batch_equals_individual_solves(prec):
+def test_batch_equals_individual_solves(prec, oracle_runs):
     torch = torch_cuda()
     m.build()
     insts = _instances()
@@ -33,6 +44,13 @@ def test_batch_equals_individual_solves(prec):
         statuses = m.mdsip_batch_solve(probs, max_concurrent=4)
         assert [m.STATUS[s] for s in statuses] == ["OK"] * len(insts)
         batched = [m.mdsip_get_stats(p) for p in probs]
+        for p, st, r in zip(probs, batched, oracle_runs):
+            assert r["status_str"] == "OK"
+            assert st["iters"] == r["iters"]
+            assert abs(st["f"] - r["f"]) <= 1e-8 * abs(r["f"])
+            log = m.mdsip_get_log(p)
+            for rec, orec in zip(log, r["log"]):
+                assert [tuple(c[2]) for c in rec["ic"]] == [tuple(c[2]) for c in orec.get("ic", [])]
         xb = []
         for p in probs:
             buf = np.zeros(m.mdsip_packed_size(p))

@@ -381,3 +381,29 @@ def test_option_strings(ctx):
     assert stats["path"] == m.MDSIP_PATH_P2 and stats["precision"] == m.MDSIP_PREC_BF16
     assert stats["iters"] == g["iters"]
     assert abs(stats["f"] - g["f"]) <= 1e-8 * abs(g["f"])
+
+
+@pytest.mark.parametrize("prec", TC_PRECS)
+def test_direction_check_logs_the_gap_to_fp64(ctx, prec):
+    """With direction_check on, every step of a mixed-precision solve logs the
+    relative gap between its refined direction and the FP64 direction from the
+    same iterate; the refined directions meet the FP64 bound of 1e-10 there,
+    and the check leaves the trajectory as it was (same count, objective and
+    per-iteration record as the oracle's)."""
+    g = _golden("mds0_full")
+    inst = _inst_for(g["case"])
+    prob = make_problem(ctx, inst, m.MDSIP_PATH_P2)
+    try:
+        m.mdsip_set_option_int(prob, "precision", prec, ctx)
+        m.mdsip_set_option_int(prob, "direction_check", 1, ctx)
+        st = m.mdsip_solve(prob, ctx)
+        stats = m.mdsip_get_stats(prob)
+        log = m.mdsip_get_log(prob)
+    finally:
+        m.mdsip_problem_destroy(prob)
+    assert m.STATUS[st] == "OK" and stats["iters"] == g["iters"]
+    assert abs(stats["f"] - g["f"]) <= 1e-8 * abs(g["f"])
+    errs = [r["dir_err_fp64"] for r in log[:-1]]
+    assert len(errs) == g["iters"] and all(0.0 <= e <= 1e-10 for e in errs), errs
+    assert log[-1]["dir_err_fp64"] == -1.0
+    compare_iterations(log, g["log"])

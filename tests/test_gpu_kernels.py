@@ -280,6 +280,99 @@ def test_ldlt_fp32_speculation_large(ctx, N):
     assert g["resid"] <= 1e-5
 
 
+@pytest.mark.parametrize("fp32", [False, True])
+@pytest.mark.parametrize("N", [1, 20, 63, 64, 65, 200, 1033, 2600])
+def test_ldlt_persistent_keeps_every_panel(ctx, N, fp32):
+    """Convex Newton-step matrices (every Bunch-Kaufman decision keeps the
+    diagonal): the persistent no-interchange factorization keeps every panel of
+    64 columns, so no pivoting panel runs; the oracle's permutation (identity),
+    1x1 pivots and inertia, D to rounding (FP64) or FP32 accuracy, and the
+    reconstruction."""
+    rng = np.random.default_rng(N * 13 + fp32)
+    K = _ipm_like(rng, N - min(50, N // 3), min(50, N // 3))
+    g = _fp32_ldlt(ctx, K, m.MDSIP_LDLT_FP32_UPDATES if fp32 else 0)
+    o = bk_ldlt(K)
+    assert g["inertia"] == o["inertia"]
+    np.testing.assert_array_equal(g["kind"], o["kind"])
+    np.testing.assert_array_equal(g["perm"], np.arange(N))
+    np.testing.assert_array_equal(o["perm"], np.arange(N))
+    assert g["panels"] == ((N + 63) // 64, 0)
+    if fp32:
+        np.testing.assert_allclose(g["Dd"], np.diag(o["D"]), rtol=1e-4, atol=1e-5 * np.abs(K).max())
+        assert g["resid"] <= 1e-5
+    else:
+        tol_d = 1e-13 * N * max(1.0, np.abs(K).max())
+        np.testing.assert_allclose(g["Dd"], np.diag(o["D"]), rtol=1e-10, atol=tol_d)
+        assert g["resid"] <= 1e-12 * max(1, N) ** 0.5
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_ldlt_persistent_hands_over_midway(ctx, fp32):
+    """A convex block, then a block whose pivots need interchanges: the
+    persistent kernel keeps the leading panels and stops at the first panel
+    the column test rejects; the pivoting panels finish from there with the
+    oracle's permutation, pivot kinds and inertia.  (The FP32-update form
+    takes a saddle block, whose pivot tests are far from their thresholds; on
+    a random block with a zero diagonal its FP32 products may tip near-ties.)"""
+    rng = np.random.default_rng(91 + fp32)
+    N = 1500
+    K = np.zeros((N, N))
+    K[:900, :900] = _ipm_like(rng, 860, 40)
+    K[900:, 900:] = _sym(rng, N - 900, "saddle" if fp32 else "zero_diag")
+    g = _fp32_ldlt(ctx, K, m.MDSIP_LDLT_FP32_UPDATES if fp32 else 0)
+    o = bk_ldlt(K)
+    assert g["inertia"] == o["inertia"]
+    np.testing.assert_array_equal(g["kind"], o["kind"])
+    np.testing.assert_array_equal(g["perm"], o["perm"])
+    acc, _ = g["panels"]
+    assert 900 // 64 <= acc < (N + 63) // 64
+    assert g["resid"] <= (1e-4 if fp32 else 1e-11)
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_ldlt_order_beyond_the_pivoting_panel(ctx, fp32):
+    """N = 20003, beyond the order whose pivoting panel fits shared memory: a
+    convex Newton-step matrix [[H, J^T], [J, -D]] (H, D positive definite, so
+    its inertia is (n_d, m_I, 0) by Sylvester's law) factors through the
+    persistent kernel alone, with that inertia, the identity permutation, and
+    a solve whose residual is at the factor's precision."""
+    torch = torch_cuda()
+    nd, mi = 19953, 50
+    N = nd + mi
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    K = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+    B = torch.randn((nd, nd), dtype=torch.float64, device="cuda", generator=gen) * (0.5 / np.sqrt(2.0 * nd))
+    K[:nd, :nd] = B + B.T      # spectrum within about [-1, 1]
+    del B
+    K[:nd, :nd] += torch.diag(2.0 + torch.rand(nd, dtype=torch.float64, device="cuda", generator=gen))
+    J = 0.1 * torch.randn((mi, nd), dtype=torch.float64, device="cuda", generator=gen)
+    K[nd:, :nd] = J
+    K[:nd, nd:] = J.T
+    K[nd:, nd:] = -torch.diag(0.5 + 1.5 * torch.rand(mi, dtype=torch.float64, device="cuda", generator=gen))
+    S = K.clone()           # symmetric: its row-major storage is the column-major lower triangle
+    L = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+    Dd = torch.zeros(N, dtype=torch.float64, device="cuda")
+    Doff = torch.zeros(N, dtype=torch.float64, device="cuda")
+    perm = torch.zeros(N, dtype=torch.int32, device="cuda")
+    kd = torch.zeros(N, dtype=torch.int32, device="cuda")
+    inr = torch.zeros(3, dtype=torch.int32, device="cuda")
+    flags = m.MDSIP_LDLT_FP32_UPDATES if fp32 else 0
+    m.mdsip_ldlt_factor_ex(ctx, N, S, N, 1e-14, flags, L, Dd, Doff, perm, kd, inr)
+    torch.cuda.synchronize()
+    del S
+    assert tuple(int(v) for v in inr.cpu().numpy()) == (nd, mi, 0)
+    assert torch.equal(perm.cpu(), torch.arange(N, dtype=torch.int32))
+    assert bool((kd == 1).all())
+    assert m.mdsip_ldlt_panel_counts(ctx) == ((N + 63) // 64, 0)
+    b = torch.randn((1, N), dtype=torch.float64, device="cuda", generator=gen)
+    x = b.clone()
+    m.mdsip_ldlt_solve(ctx, N, L, Dd, Doff, perm, 1, x, N)
+    torch.cuda.synchronize()
+    r = (K @ x[0] - b[0]).abs().max().item()
+    scale = K.abs().max().item() * x.abs().max().item() + b.abs().max().item()
+    assert r <= (1e-4 if fp32 else 1e-11) * scale, r / scale
+
+
 def test_ldlt_singular_and_edge_cases(ctx):
     g = _gpu_ldlt(ctx, np.zeros((5, 5)))
     assert g["inertia"] == (0, 0, 5)

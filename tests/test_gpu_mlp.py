@@ -71,7 +71,81 @@ def _f64(d):
     return {k: np.asarray(v, np.float64) for k, v in d.items()}
 
 
-def test_forward_matches_oracle():
+# Element-wise parity of the network on inputs chosen so that every product
+# and every partial sum of the forward pass is a dyadic rational with few
+# significant bits: inputs in {0, +-1/2, +-1}, first- and second-layer weights
+# in {+-1/8, +-1/4} with at most 8 (W1) or 4 (W2, per row and per column)
+# nonzeros, dense output weights and biases in multiples of 1/16, output
+# scaling by 2.  Then the FP32 tensor-core accumulation is exact in any order,
+# every hidden activation is exactly a bfloat16 number, and the GPU's forward
+# pass must equal the oracle's (bf16 rounding points of oracle/mlp.py) bit for
+# bit.  With targets y + 2 delta (delta in multiples of 1/16) and a batch times
+# outputs a power of two, the output gradient dL/dyn = -2 delta / (B O) is exact
+# too, and so are dW3, db3, the pre-activation gradient of layer 2 and db2; the
+# products that can lose bits (dW2 = dZ2^T h1, dW1 = dZ1^T xn, db1) are held to
+# the FP32 accumulation bound k 2^-24 sum|terms| over their k = B terms, and
+# the second pre-activation gradient, whose sum is exact, is rounded identically
+# on both sides.
+E32 = 2.0 ** -24
+
+
+def _sparse_pm(rng, rows, cols, per_row, vals, perms=False):
+    W = np.zeros((rows, cols), np.float32)
+    if perms:                                   # <= per_row nonzeros in every row and column
+        for _ in range(per_row):
+            pr = rng.permutation(max(rows, cols))
+            for r in range(rows):
+                c = pr[r] % cols
+                W[r, c] = rng.choice(vals)
+    else:
+        for r in range(rows):
+            for c in rng.choice(cols, size=min(per_row, cols), replace=False):
+                W[r, c] = rng.choice(vals)
+    return W
+
+
+def _exact_setup(I, H, O, seed):
+    rng = np.random.default_rng(seed)
+    p = {"W1": _sparse_pm(rng, H, I, 8, [-0.25, -0.125, 0.125, 0.25]),
+         "b1": (rng.integers(-4, 5, H) / 16).astype(np.float32),
+         "W2": _sparse_pm(rng, H, H, 4, [-0.125, 0.125], perms=True),
+         "b2": (rng.integers(-16, 17, H) / 128).astype(np.float32),
+         "W3": (rng.integers(-8, 9, (O, H)) / 16).astype(np.float32),
+         "b3": (rng.integers(-8, 9, O) / 16).astype(np.float32)}
+    sc = dict(in_mean=np.zeros(I, np.float32), in_std=np.ones(I, np.float32),
+              out_mean=(rng.integers(-4, 5, O) / 4).astype(np.float32), out_std=np.full(O, 2.0, np.float32))
+    return p, sc
+
+
+def _exact_inputs(rng, B, I):
+    return rng.choice([-1.0, -0.5, 0.0, 0.5, 1.0], size=(B, I))
+
+
+@pytest.mark.parametrize("I,H,O,B", [(64, 256, 1037, 100), (8, 136, 300, 33), (3, 40, 10, 9)])
+def test_forward_matches_oracle_exactly(I, H, O, B):
+    torch = torch_cuda()
+    p, sc = _exact_setup(I, H, O, I + H)
+    X = _exact_inputs(np.random.default_rng(2), B, I)
+    ctx = make_ctx()
+    net = _net_on_gpu(ctx, p, sc, I, H, O)
+    try:
+        Yd = torch.zeros((B, O + 5), dtype=torch.float32, device="cuda")
+        m.mdsip_mlp_forward(net, torch.from_numpy(X).cuda(), I, B, Yd, O + 5, ctx=ctx)
+        got = Yd[:, :O].cpu().double().numpy()
+        ref = om.predict(_f64(p), X, _f64(sc), bf16=True)
+        # the inputs were built for exact arithmetic: the exact network gives the same
+        assert np.array_equal(ref, om.predict(_f64(p), X, _f64(sc), bf16=False))
+        np.testing.assert_array_equal(got, ref)
+        assert np.all(Yd[:, O:].cpu().numpy() == 0.0)
+    finally:
+        m.mdsip_mlp_destroy(net)
+        m.mdsip_ctx_destroy(ctx)
+
+
+def test_forward_matches_oracle_random():
+    """Random weights and inputs: the forward pass within the BF16 oracle's
+    norm (rounding decisions may differ where FP32 and FP64 sums straddle a
+    bfloat16 boundary; the exact-arithmetic test above pins each element)."""
     torch = torch_cuda()
     I, H, O, B = 64, 256, 1037, 100
     p, sc = _setup(I, H, O, 1)
@@ -84,7 +158,6 @@ def test_forward_matches_oracle():
         got = Yd[:, :O].cpu().double().numpy()
         ref = om.predict(_f64(p), X, _f64(sc), bf16=True)
         assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref)
-        assert np.max(np.abs(got - ref)) <= 1e-2 * np.max(np.abs(ref))
     finally:
         m.mdsip_mlp_destroy(net)
         m.mdsip_ctx_destroy(ctx)
@@ -94,14 +167,15 @@ def _blocks(net, flat, I, H, O):
     return ws.unpack_params(net, flat, I, H, O)
 
 
-@pytest.mark.parametrize("I,H,O,B,rows", [(64, 256, 1037, 100, 150), (8, 128, 300, 64, 64), (3, 40, 10, 9, 20)])
+@pytest.mark.parametrize("I,H,O,B,rows", [(64, 256, 256, 64, 150), (8, 136, 512, 16, 64), (3, 40, 32, 8, 20)])
 def test_gradient_matches_oracle(I, H, O, B, rows):
     torch = torch_cuda()
-    p, sc = _setup(I, H, O, 3)
+    assert (B * O) & (B * O - 1) == 0            # 2 / (B O) exact
+    p, sc = _exact_setup(I, H, O, 3 + I)
     rng = np.random.default_rng(4)
-    X = rng.uniform(-1, 1, (rows, I))
-    # targets near the network's output, so that dL/dyn is not dominated by one scale
-    Y = om.predict(_f64(p), X, _f64(sc)) + rng.normal(size=(rows, O)) * sc["out_std"]
+    X = _exact_inputs(rng, rows, I)
+    delta = rng.integers(-32, 33, (rows, O)) / 16.0
+    Y = om.predict(_f64(p), X, _f64(sc), bf16=True) + 2.0 * delta
     idx = rng.permutation(rows)[:B].astype(np.int32)
     ctx = make_ctx()
     net = _net_on_gpu(ctx, p, sc, I, H, O)
@@ -109,13 +183,48 @@ def test_gradient_matches_oracle(I, H, O, B, rows):
         grad = torch.zeros(m.mdsip_mlp_num_params(net), dtype=torch.float32, device="cuda")
         loss = m.mdsip_mlp_gradient(net, torch.from_numpy(X).cuda(), I, torch.from_numpy(Y).cuda(), O,
                                     torch.from_numpy(idx).cuda(), B, grad, ctx=ctx)
+        g = _f64(_blocks(net, grad.cpu().numpy(), I, H, O))
+        q = _f64(p)
+        L_ref, g_ref = om.loss_and_grad(q, X[idx], Y[idx], _f64(sc), bf16=True)
+        assert loss == pytest.approx(L_ref, rel=1e-12)
+        for k in ("W3", "b3", "b2"):              # exact sums
+            np.testing.assert_array_equal(g[k], g_ref[k], err_msg=k)
+        # FP32 accumulation over the batch (B terms) of exactly equal operands
+        c = om.forward(q, X[idx], _f64(sc)["in_mean"], _f64(sc)["in_std"], bf16=True)
+        gy = 2.0 * (c["yn"] - (Y[idx] - _f64(sc)["out_mean"]) / _f64(sc)["out_std"]) / (B * O)
+        dz2 = om.bf16_round((gy @ c["W3"]) * (c["h2"] > 0))
+        dz1 = om.bf16_round((dz2 @ c["W2"]) * (c["h1"] > 0))
+        bounds = {"W2": B * E32 * (np.abs(dz2).T @ np.abs(c["h1"])),
+                  "W1": B * E32 * (np.abs(dz1).T @ np.abs(c["xn"])),
+                  "b1": B * E32 * np.abs(dz1).sum(axis=0)}
+        for k, bd in bounds.items():
+            d = np.abs(g[k] - g_ref[k])
+            assert np.all(d <= bd), (k, float(np.max(d - bd)))
+        assert np.count_nonzero(g_ref["W1"]) > 0 and np.count_nonzero(g_ref["W2"]) > 0
+    finally:
+        m.mdsip_mlp_destroy(net)
+        m.mdsip_ctx_destroy(ctx)
+
+
+def test_gradient_random_against_exact_network():
+    """Random weights: the BF16 gradient stays within 10% (norm) of the exact
+    FP64 network's gradient, the accuracy the warm start relies on."""
+    torch = torch_cuda()
+    I, H, O, B, rows = 64, 256, 1037, 100, 150
+    p, sc = _setup(I, H, O, 3)
+    rng = np.random.default_rng(4)
+    X = rng.uniform(-1, 1, (rows, I))
+    Y = om.predict(_f64(p), X, _f64(sc)) + rng.normal(size=(rows, O)) * sc["out_std"]
+    idx = rng.permutation(rows)[:B].astype(np.int32)
+    ctx = make_ctx()
+    net = _net_on_gpu(ctx, p, sc, I, H, O)
+    try:
+        grad = torch.zeros(m.mdsip_mlp_num_params(net), dtype=torch.float32, device="cuda")
+        m.mdsip_mlp_gradient(net, torch.from_numpy(X).cuda(), I, torch.from_numpy(Y).cuda(), O,
+                             torch.from_numpy(idx).cuda(), B, grad, ctx=ctx)
         g = _blocks(net, grad.cpu().numpy(), I, H, O)
-        L_ref, g_ref = om.loss_and_grad(_f64(p), X[idx], Y[idx], _f64(sc), bf16=True)
-        L_ex, g_ex = om.loss_and_grad(_f64(p), X[idx], Y[idx], _f64(sc), bf16=False)
-        assert abs(loss - L_ref) <= 1e-3 * L_ref
+        _, g_ex = om.loss_and_grad(_f64(p), X[idx], Y[idx], _f64(sc), bf16=False)
         for k in om.BLOCKS:
-            e = np.linalg.norm(g[k] - g_ref[k]) / np.linalg.norm(g_ref[k])
-            assert e <= 2e-2, (k, e)
             assert np.linalg.norm(g[k] - g_ex[k]) <= 1e-1 * np.linalg.norm(g_ex[k]), k
     finally:
         m.mdsip_mlp_destroy(net)
@@ -123,6 +232,13 @@ def test_gradient_matches_oracle(I, H, O, B, rows):
 
 
 def test_adam_steps_match_oracle():
+    """Two training steps: each one's update equals the oracle's Adam step
+    (Kingma-Ba Algorithm 1) applied to the gradient the GPU takes at the same
+    weights (pinned element-wise above), for every element, within the FP32
+    rounding of the update and of the weight.  Both sides use the constants as
+    the kernel holds them (learning rate, decay rates and epsilon rounded to
+    FP32): 1 - fl32(0.999) differs from 0.001 by 1.3e-5 relative, far above
+    the FP32 rounding this test bounds."""
     torch = torch_cuda()
     I, H, O, B = 16, 128, 200, 64
     p, sc = _setup(I, H, O, 5)
@@ -134,26 +250,29 @@ def test_adam_steps_match_oracle():
     net = _net_on_gpu(ctx, p, sc, I, H, O)
     try:
         Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
-        for _ in range(2):
-            m.mdsip_mlp_train_step(net, Xd, I, Yd, O, None, B, lr, ctx=ctx)
-        flat = np.zeros(m.mdsip_mlp_num_params(net), np.float32)
+        idx = torch.arange(B, dtype=torch.int32, device="cuda")
+        n = m.mdsip_mlp_num_params(net)
+        flat = np.zeros(n, np.float32)
         m.mdsip_mlp_get_params(net, flat, ctx=ctx)
-        got = _blocks(net, flat, I, H, O)
-        q = _f64(p)
-        mom = {k: np.zeros_like(v) for k, v in q.items()}
-        vel = {k: np.zeros_like(v) for k, v in q.items()}
-        grads = []
+        w = _f64(_blocks(net, flat, I, H, O))
+        mom = {k: np.zeros_like(v) for k, v in w.items()}
+        vel = {k: np.zeros_like(v) for k, v in w.items()}
         for t in (1, 2):
-            _, gq = om.loss_and_grad(q, X, Y, _f64(sc), bf16=True)
-            grads.append(gq)
-            q, mom, vel = om.adam_step(q, gq, mom, vel, t, lr)
-        for k in om.BLOCKS:
-            # elements whose gradient sign is unambiguous in both steps
-            rms = [np.sqrt(np.mean(gq[k] ** 2)) for gq in grads]
-            robust = (np.abs(grads[0][k]) > 0.05 * rms[0]) & (np.abs(grads[1][k]) > 0.05 * rms[1])
-            d = np.abs(got[k] - q[k])
-            assert np.all(d[robust] <= 0.05 * lr + 1e-6 * np.abs(q[k][robust])), k
-            assert np.mean(d <= 0.05 * lr + 1e-6 * np.abs(q[k])) >= 0.98, k
+            grad = torch.zeros(n, dtype=torch.float32, device="cuda")
+            m.mdsip_mlp_gradient(net, Xd, I, Yd, O, idx, B, grad, ctx=ctx)
+            g = _f64(_blocks(net, grad.cpu().numpy(), I, H, O))
+            f32 = lambda v: float(np.float32(v))
+            ref, mom, vel = om.adam_step(w, g, mom, vel, t, f32(lr), beta1=f32(0.9), beta2=f32(0.999),
+                                         eps=f32(1e-8))
+            m.mdsip_mlp_train_step(net, Xd, I, Yd, O, idx, B, lr, ctx=ctx)
+            m.mdsip_mlp_get_params(net, flat, ctx=ctx)
+            got = _f64(_blocks(net, flat, I, H, O))
+            for k in om.BLOCKS:
+                step = np.abs(ref[k] - w[k])
+                bound = 2 * E32 * np.abs(ref[k]) + 16 * E32 * step + 1e-30
+                d = np.abs(got[k] - ref[k])
+                assert np.all(d <= bound), (t, k, float(np.max(d / bound)))
+            w = got            # the next step starts from the GPU's weights
     finally:
         m.mdsip_mlp_destroy(net)
         m.mdsip_ctx_destroy(ctx)
