@@ -111,6 +111,8 @@ def parse():
                     help="--kernel ldlt: the mixed-precision factorization (FP32 update products)")
     ap.add_argument("--no-spec", action="store_true",
                     help="--kernel ldlt --fp32-update: every panel pivots (no verified no-interchange panels)")
+    ap.add_argument("--persistent", action="store_true",
+                    help="--kernel ldlt: the persistent no-interchange kernel at any order")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--ldlt-matrix", choices=["kkt", "ipm"], default="kkt",
                     help="--kernel ldlt: kkt = [[H, J^T], [J, -I]] with J ~ N(0, 1) (pivots often); "
@@ -1003,6 +1005,8 @@ def run_kernel(args):
             flags = m.MDSIP_LDLT_FP32_UPDATES if args.fp32_update else 0
             if args.no_spec:
                 flags |= m.MDSIP_LDLT_NO_SPECULATION
+            if args.persistent:
+                flags |= m.MDSIP_LDLT_PERSISTENT
 
             def call():
                 S.copy_(S0)

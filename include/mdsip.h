@@ -170,7 +170,9 @@ void mdsip_problem_destroy(mdsip_problem *p);
  *           shape; 0: the analytic choices),
  *           ldlt_spec (1, default: the mixed-precision factorization's
  *           panels first try the verified no-interchange path described at
- *           mdsip_ldlt_factor_ex; 0: every panel pivots),
+ *           mdsip_ldlt_factor_ex, and from order 2048 on the persistent
+ *           no-interchange kernel runs first in either precision; 2: that
+ *           kernel at every order; 0: every panel pivots),
  *           direction_check (0, default; 1: every step of a mixed-precision
  *           solve also computes the FP64 direction from the same iterate and
  *           shifts and logs the relative gap as dir_err_fp64 -- an extra FP64
@@ -182,8 +184,9 @@ void mdsip_problem_destroy(mdsip_problem *p);
  *           kw_plus_bar, dc_bar, kappa_c, zero_tol, time_limit_s, refine_tol,
  *           refine_fallback_tol
  *   string: path ("auto" | "p1" | "p2"), precision ("fp64" | "tf32" | "bf16"),
- *           and graphs / autotune / ldlt_spec as "yes" | "no" -- the same
- *           settings as the int options of those names, by word.
+ *           graphs / autotune / ldlt_spec as "yes" | "no", ldlt_spec also
+ *           "persistent" (2) -- the same settings as the int options of
+ *           those names, by word.
  * Unknown names or values: INVALID_ARG (the option keeps its value). */
 mdsip_status mdsip_set_option_int(mdsip_problem *p, const char *name, int64_t value);
 mdsip_status mdsip_set_option_double(mdsip_problem *p, const char *name, double value);
@@ -353,9 +356,17 @@ mdsip_status mdsip_ldlt_factor(mdsip_ctx *ctx, int64_t N, double *S, int64_t ld,
  * computed columns, would have chosen a 1x1 pivot without interchange for
  * every column of the panel (and no pivot is below zero_tol times the
  * largest |S_ij|); otherwise the pivoting panel factors it from the
- * unchanged matrix.  The flag makes every panel take the pivoting kernel. */
+ * unchanged matrix.  The flag makes every panel take the pivoting kernel.
+ * From order 2048 on (and wherever the pivoting panel does not fit shared
+ * memory, N above about 16 000), and at any order with MDSIP_LDLT_PERSISTENT,
+ * the no-interchange panels of either precision run in one persistent
+ * cooperative kernel that stops at the first panel the rule would not keep;
+ * the pivoting panels take over from there (beyond the pivoting panel's
+ * limit such a panel is an INVALID_ARG error).  The call then reads a status
+ * word back, so it synchronises the context's stream. */
 #define MDSIP_LDLT_FP32_UPDATES 1
 #define MDSIP_LDLT_NO_SPECULATION 2
+#define MDSIP_LDLT_PERSISTENT 4
 mdsip_status mdsip_ldlt_factor_ex(mdsip_ctx *ctx, int64_t N, double *S, int64_t ld, double zero_tol,
                                   int32_t flags, double *L, double *Dd, double *Doff, int32_t *perm,
                                   int32_t *kind, int32_t *inertia);

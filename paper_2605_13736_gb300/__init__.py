@@ -407,6 +407,7 @@ def mdsip_ldlt_factor(ctx, N, S, ld, zero_tol, L, Dd, Doff, perm, kind, inertia)
 
 MDSIP_LDLT_FP32_UPDATES = 1
 MDSIP_LDLT_NO_SPECULATION = 2
+MDSIP_LDLT_PERSISTENT = 4
 
 
 def mdsip_ldlt_factor_ex(ctx, N, S, ld, zero_tol, flags, L, Dd, Doff, perm, kind, inertia):

@@ -344,16 +344,20 @@ struct LdltOut {
 size_t ldlt_scratch_bytes(int64_t N);
 void launch_ldlt(cudaStream_t s, int num_sms, int64_t N, const double *S, int64_t ld,
                  const double *maxabs_dev, double zero_tol, LdltOut out, void *scratch,
-                 int *err_dev, bool fp32_update = false, int nb = 0, bool spec = true);
+                 int *err_dev, bool fp32_update = false, int nb = 0, int spec = 1);
 size_t ldlt_blocked_scratch_bytes(int64_t N);
 bool ldlt_blocked_available(int64_t N);
-// with speculation on, the blocked factorization first runs its persistent
-// no-interchange kernel and reads back where it stopped (synchronises the stream)
-bool ldlt_persistent_path(int64_t N, bool spec);
+// Speculation mode of the blocked factorization: 0 every panel pivots; 1 (auto)
+// no-interchange panels, the persistent kernel from order kPersistentMinOrder
+// on or where the pivoting panel does not fit; 2 the persistent kernel at any
+// order.  The persistent kernel reads back where it stopped (synchronises the
+// stream).
+constexpr int64_t kPersistentMinOrder = 2048;
+bool ldlt_persistent_path(int64_t N, int spec);
 std::vector<int> ldlt_blocked_widths(int64_t N, bool f32);
 void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, const double *maxabs_dev,
                          double zero_tol, LdltOut out, void *scratch, bool fp32_update, int nb = 0,
-                         bool spec = true);
+                         int spec = 1);
 void launch_ldlt_solve(cudaStream_t s, int64_t N, const double *L, const double *Dd,
                        const double *Doff, const int32_t *perm, int64_t nrhs, double *B,
                        int64_t ldb);

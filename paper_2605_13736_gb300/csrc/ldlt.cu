@@ -627,7 +627,7 @@ static void launch_ldlt_unblocked(cudaStream_t s, int num_sms, int64_t N, const 
 // FP32 (refined mixed-precision path).
 void launch_ldlt(cudaStream_t s, int num_sms, int64_t N, const double *S, int64_t ld,
                  const double *maxabs_dev, double zero_tol, LdltOut out, void *scratch,
-                 int *err_dev, bool fp32_update, int nb, bool spec) {
+                 int *err_dev, bool fp32_update, int nb, int spec) {
     if (N > 0 && ld == N && (ldlt_blocked_available(N) || ldlt_persistent_path(N, spec))) {
         launch_ldlt_blocked(s, num_sms, N, const_cast<double *>(S), maxabs_dev, zero_tol, out, scratch,
                             fp32_update, nb, spec);

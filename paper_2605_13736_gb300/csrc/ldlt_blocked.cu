@@ -1125,6 +1125,7 @@ template <typename T>
 __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist(PersistArgs a) {
     extern __shared__ __align__(16) unsigned char psm[];
     T *V = reinterpret_cast<T *>(psm);      // [64][kPP]: the diagonal block; W values once factored
+                                            // (then [64][kPP]: a chunk of the rows below it)
     __shared__ double s_d[64], s_rd[64];    // FP64 pivots and their reciprocals
     __shared__ T s_rc[64];                  // the chain's reciprocals
     __shared__ unsigned long long s_cmax[64];
@@ -1155,16 +1156,17 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist(PersistArgs a) {
                 T v[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) v[j] = (lane < cw && j <= lane) ? V[(c0 + lane) * kPP + c0 + j] : (T)0;
+                // (lanes that take no part get a zero multiplier: a conditional
+                // update kept v in local memory; the entries above a lane's
+                // diagonal that the zero-free form touches are never read)
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const T dj = __shfl_sync(0xffffffffu, v[j], j);
                     const T rj = j < cw ? chain_rcp(dj) : (T)0;
-                    const T l = v[j] * rj;
+                    const T l = (lane > j && lane < cw) ? v[j] * rj : (T)0;
 #pragma unroll
-                    for (int t = j + 1; t < 16; ++t) {
-                        const T wtj = __shfl_sync(0xffffffffu, v[j], t);
-                        if (lane >= t && lane < cw) v[t] = fma(-l, wtj, v[t]);
-                    }
+                    for (int t = 0; t < 16; ++t)
+                        if (t > j) v[t] = fma(-l, __shfl_sync(0xffffffffu, v[j], t), v[t]);
                     if (lane == j && j < cw) s_rc[c0 + j] = rj;
                 }
 #pragma unroll
@@ -1218,57 +1220,106 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist(PersistArgs a) {
             s_rd[tid] = rd;
         }
         __syncthreads();
-        // CTA 0: the block's L and D, and the column maxima of its rows
-        if (g == 0) {
-            for (int e = tid; e < 64 * 64; e += kPThreads) {
-                const int c = e >> 6, r = e & 63;
-                if (r >= nb || c >= nb || r < c) continue;
+        const int wid = tid >> 5;
+        constexpr int kWarps = kPThreads / 32;
+        // the block's L and D and the column maxima of its rows: column c by
+        // CTA c mod G, one warp per column, lanes over rows (warp maxima)
+        for (int c = g + G * wid; c < nb; c += G * kWarps) {
+            unsigned long long bm = 0ULL;
+            for (int r = c + lane; r < nb; r += 32) {
                 const int64_t o = (int64_t)(k + r) + (int64_t)(k + c) * N;
                 if (r == c) {
                     a.L[o] = 1.0;
                     a.Dd[k + c] = s_d[c];
                 } else {
-                    const double w = chain_w64<T>(V[r * kPP + c], a.A[o]);
-                    a.L[o] = w * s_rd[c];
-                    atomicMax(&s_cmax[c], absbits64(w));
+                    const T w = V[r * kPP + c];
+                    a.L[o] = sizeof(T) == sizeof(float) ? (double)(w * s_rc[c]) : (double)w * s_rd[c];
+                    const unsigned long long bw = absbits64((double)w);
+                    bm = bw > bm ? bw : bm;
                 }
             }
+            const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(bm >> 32));
+            const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(bm >> 32) == hi ? (unsigned)bm : 0u);
+            if (lane == 0 && (hi | lo)) atomicMax(&s_cmax[c], ((unsigned long long)hi << 32) | lo);
         }
-        // ---------------- A2: this CTA's rows below the block
+        // ---------------- A2: this CTA's rows below the block, 64 at a time
+        // in shared memory, solved against the block's factor in the same
+        // 16-column steps (row solves, then a rank-16 update of the rest)
+        T *U = V + 64 * kPP;                  // [64][kPP]: a chunk of rows
         const int brow = N - k - nb;
         const int R = (brow + G - 1) / G;
         const int r_begin = k + nb + g * R, r_end = min(N, r_begin + R);
-        for (int base = r_begin; base < r_end; base += kPThreads) {
-            const int i = base + tid;
-            const bool act = i < r_end;
-            T v[64];
-#pragma unroll
-            for (int t = 0; t < 64; ++t) v[t] = (act && t < nb) ? (T)a.A[(int64_t)i + (int64_t)(k + t) * N] : (T)0;
-#pragma unroll
-            for (int j = 0; j < 64; ++j) {
-                const T l = v[j] * s_rc[j];
-#pragma unroll
-                for (int t = j + 1; t < 64; ++t) v[t] = fma(-l, V[t * kPP + j], v[t]);
+        for (int cb = r_begin; cb < r_end; cb += 64) {
+            const int nr = min(64, r_end - cb);
+            __syncthreads();                   // the previous chunk is written out
+            for (int e = tid; e < 64 * 64; e += kPThreads) {
+                const int c = e >> 6, r = e & 63;
+                U[r * kPP + c] = (r < nr && c < nb) ? (T)a.A[(int64_t)(cb + r) + (int64_t)(k + c) * N] : (T)0;
             }
+            __syncthreads();
+            for (int c0 = 0; c0 < nb; c0 += 16) {
+                const int cw = min(16, nb - c0);
+                for (int r = tid; r < nr; r += kPThreads) {
+                    T v[16];
 #pragma unroll
-            for (int t = 0; t < 64; ++t) {
-                unsigned long long b = 0ULL;
-                if (act && t < nb) {
-                    const int64_t o = (int64_t)i + (int64_t)(k + t) * N;
-                    const double w = chain_w64<T>(v[t], a.A[o]);
-                    const double l = w * s_rd[t];
-                    a.L[o] = l;
-                    if constexpr (sizeof(T) == sizeof(float)) {
-                        a.Lf[(int64_t)i + (int64_t)t * N] = (float)l;
-                        a.Wf[(int64_t)i + (int64_t)t * N] = (float)w;
-                    } else {
-                        a.Wg[(int64_t)i + (int64_t)t * N] = w;
+                    for (int j = 0; j < 16; ++j) v[j] = j < cw ? U[r * kPP + c0 + j] : (T)0;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const T l = j < cw ? v[j] * s_rc[c0 + j] : (T)0;
+#pragma unroll
+                        for (int t = j + 1; t < 16; ++t)
+                            if (t < cw) v[t] = fma(-l, V[(c0 + t) * kPP + c0 + j], v[t]);
                     }
-                    b = absbits64(w);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (j < cw) U[r * kPP + c0 + j] = v[j];
                 }
-                const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(b >> 32));
-                const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(b >> 32) == hi ? (unsigned)b : 0u);
-                if (lane == 0 && (hi | lo)) atomicMax(&s_cmax[t], ((unsigned long long)hi << 32) | lo);
+                __syncthreads();
+                const int m0 = c0 + 16, mw = nb - m0;
+                if (mw > 0) {
+                    for (int e = tid; e < nr * mw; e += kPThreads) {
+                        const int r = e / mw, c = m0 + (e - (e / mw) * mw);
+                        T acc = U[r * kPP + c];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (j < cw) acc = fma(-(U[r * kPP + c0 + j] * s_rc[c0 + j]), V[c * kPP + c0 + j], acc);
+                        U[r * kPP + c] = acc;
+                    }
+                }
+                __syncthreads();
+            }
+            // outputs and column maxima: one warp per column, lanes over rows.
+            // FP64 chains: w and L in FP64.  FP32 chains: L, W and the maxima from
+            // the FP32 values the chain computed (one conversion per element for
+            // the FP64 copy of L; GB300 runs FP64 arithmetic at 1/64 of FP32)
+            for (int c = wid; c < nb; c += kWarps) {
+                if constexpr (sizeof(T) == sizeof(float)) {
+                    unsigned bm = 0u;
+                    for (int r = lane; r < nr; r += 32) {
+                        const int i = cb + r;
+                        const float w = U[r * kPP + c], l = w * s_rc[c];
+                        a.L[(int64_t)i + (int64_t)(k + c) * N] = (double)l;
+                        a.Lf[(int64_t)i + (int64_t)c * N] = l;
+                        a.Wf[(int64_t)i + (int64_t)c * N] = w;
+                        bm = max(bm, __float_as_uint(w) & 0x7fffffffu);
+                    }
+                    bm = __reduce_max_sync(0xffffffffu, bm);
+                    if (lane == 0 && bm) atomicMax(&s_cmax[c], absbits64((double)__uint_as_float(bm)));
+                } else {
+                    unsigned long long bm = 0ULL;
+                    for (int r = lane; r < nr; r += 32) {
+                        const int i = cb + r;
+                        const int64_t o = (int64_t)i + (int64_t)(k + c) * N;
+                        const double w = U[r * kPP + c];
+                        a.L[o] = w * s_rd[c];
+                        a.Wg[(int64_t)i + (int64_t)c * N] = w;
+                        const unsigned long long bw = absbits64(w);
+                        bm = bw > bm ? bw : bm;
+                    }
+                    const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(bm >> 32));
+                    const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(bm >> 32) == hi ? (unsigned)bm : 0u);
+                    if (lane == 0 && (hi | lo)) atomicMax(&s_cmax[c], ((unsigned long long)hi << 32) | lo);
+                }
             }
         }
         __syncthreads();
@@ -1485,7 +1536,7 @@ PanelBar *grid_bar(char *w, const BlockedScratch &lay) { return reinterpret_cast
 // rows of a trailing-update tile
 template <typename T>
 size_t persist_smem() {
-    return std::max((size_t)64 * kPP * sizeof(T), 2 * (size_t)65 * kUT * sizeof(T));
+    return std::max(2 * (size_t)64 * kPP * sizeof(T), 2 * (size_t)65 * kUT * sizeof(T));
 }
 
 // Run k_bk_persist from column 0; returns the column where it stopped (N: all
@@ -1533,16 +1584,24 @@ std::vector<int> ldlt_blocked_widths(int64_t N, bool f32) {
 bool ldlt_blocked_available(int64_t N) { return blocked_config(N, true).C > 0 && blocked_config(N, false).C > 0; }
 
 // The persistent no-interchange factorization runs first (and the host reads
-// back where it stopped) whenever speculation is on; it needs no pivoting
-// panel unless a panel fails the column test, so it also serves orders whose
-// pivoting panel does not fit shared memory.
-bool ldlt_persistent_path(int64_t N, bool spec) { return spec && N > 0 && N <= (int64_t)0x7fffffff / 2; }
+// back where it stopped) in mode 2, and in mode 1 from kPersistentMinOrder on
+// (measured on the convex Newton-step shape, persistent against per-panel
+// launches: N = 2050 FP32 updates 1.65 / 1.73 ms, FP64 8.3 / 11.1 ms; N = 4050
+// 4.8 / 6.0 and 31 / 36 ms; N = 8003 27.5 / 42.9 and 179 / 194 ms) and
+// wherever the pivoting panel does not fit shared memory: it needs no
+// pivoting panel unless a panel fails the column test.  Below that order --
+// the many small instances of a batch among them -- the per-panel launches
+// (captured in a graph from their second use) stay.
+bool ldlt_persistent_path(int64_t N, int spec) {
+    if (spec == 0 || N <= 0 || N > (int64_t)0x7fffffff / 2) return false;
+    return spec == 2 || N >= kPersistentMinOrder || !ldlt_blocked_available(N);
+}
 
 // S (lower, ld N) is overwritten.  scratch: ldlt_blocked_scratch_bytes(N),
 // 256-byte aligned.  fp32_update: trailing products in FP32.  spec (with
 // fp32_update): each panel first tries the verified no-interchange path.
 void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, const double *maxabs_dev,
-                         double zero_tol, LdltOut out, void *scratch, bool fp32_update, int nb, bool spec) {
+                         double zero_tol, LdltOut out, void *scratch, bool fp32_update, int nb, int spec) {
     if (N <= 0) {
         MDSIP_CUDA(cudaMemsetAsync(out.inertia, 0, 3 * sizeof(int32_t), s));
         return;
@@ -1616,7 +1675,7 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
         return e;
     }));
     SpecArgs sa{};
-    if (spec && fp32_update) {
+    if (spec != 0 && fp32_update) {
         sa.N = (int)N;
         sa.NB = cfg.NB;
         sa.A = S;
@@ -1640,7 +1699,7 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
     // panels from column k0 on (all of them without the persistent kernel)
     const int npanels = k0 >= N ? 0 : (int)((N - k0 + cfg.NB - 1) / cfg.NB);
     for (int p = 0; p < npanels; ++p) {
-        if (spec && fp32_update) {
+        if (spec != 0 && fp32_update) {
             // rows below the diagonal block: at most N - k0 - (p + 1) NB (every panel takes >= NB columns)
             const int64_t below = N - k0 - (int64_t)(p + 1) * cfg.NB;
             const int G = (int)std::max<int64_t>(1, (below + kSpecRB - 1) / kSpecRB);

@@ -682,7 +682,7 @@ static void run_factor_phase(Problem *P, int slot, F &&enqueue) {
     ++g.uses;
     // the persistent factorization reads back where it stopped: nothing to capture
     if (!P->opt.graphs || g.disabled || g.uses < 2 || !ldlt_blocked_available(P->N) ||
-        ldlt_persistent_path(P->N, P->opt.ldlt_spec != 0)) {
+        ldlt_persistent_path(P->N, (int)P->opt.ldlt_spec)) {
         enqueue();
         return;
     }
@@ -743,7 +743,7 @@ static int tuned_ldlt_width(Problem *P, bool fp32) {
             LdltOut o{P->bL.as<double>(), P->bDd.as<double>(), P->bDoff.as<double>(), P->bperm.as<int32_t>(),
                       P->bkind.as<int32_t>(), P->binertia.as<int32_t>()};
             launch_ldlt(st, P->ctx->num_sms, N, S, N, sc + SC_MAXABS, P->opt.zero_tol, o, P->bldlt_ws.ptr,
-                        P->berr.as<int>(), fp32, nb, P->opt.ldlt_spec != 0);
+                        P->berr.as<int>(), fp32, nb, (int)P->opt.ldlt_spec);
         });
         MDSIP_CUDA(cudaMemcpyAsync(S, Ssave, (size_t)N * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
         MDSIP_CUDA(cudaStreamSynchronize(st));
@@ -799,7 +799,7 @@ static Inertia factor_attempt(Problem *P, double dw, double dc, bool force_fp64 
         LdltOut o{P->bL.as<double>(), P->bDd.as<double>(), P->bDoff.as<double>(), P->bperm.as<int32_t>(),
                   P->bkind.as<int32_t>(), P->binertia.as<int32_t>()};
         launch_ldlt(st, P->ctx->num_sms, P->N, S, P->N, sc + SC_MAXABS, P->opt.zero_tol, o, P->bldlt_ws.ptr,
-                    P->berr.as<int>(), tc_factor, nb, P->opt.ldlt_spec != 0);
+                    P->berr.as<int>(), tc_factor, nb, (int)P->opt.ldlt_spec);
         launch_ldlt_solve_prepare(st, P->N, P->bL.as<double>(), P->bsolve_ws.ptr, P->solve_fp32);
     };
     run_factor_phase(P, tc_factor ? 1 : 0, factor_phase);
@@ -1501,6 +1501,7 @@ mdsip_status mdsip_set_option_int(mdsip_problem *hp, const char *name, int64_t v
         if (std::string(name) == "ldlt_spec") p->drop_graphs();   // captured factorizations use the old choice
         MDSIP_REQUIRE(p->opt.path >= 0 && p->opt.path <= 2, MDSIP_ERR_INVALID_ARG, "bad path");
         MDSIP_REQUIRE(p->opt.precision >= 0 && p->opt.precision <= 2, MDSIP_ERR_INVALID_ARG, "bad precision");
+        MDSIP_REQUIRE(p->opt.ldlt_spec >= 0 && p->opt.ldlt_spec <= 2, MDSIP_ERR_INVALID_ARG, "bad ldlt_spec");
     });
 }
 
@@ -1523,7 +1524,8 @@ mdsip_status mdsip_set_option_str(mdsip_problem *hp, const char *name, const cha
             {"path", "p2", MDSIP_PATH_P2},         {"precision", "fp64", MDSIP_PREC_FP64},
             {"precision", "tf32", MDSIP_PREC_TF32}, {"precision", "bf16", MDSIP_PREC_BF16},
             {"graphs", "yes", 1},   {"graphs", "no", 0},   {"autotune", "yes", 1},
-            {"autotune", "no", 0},  {"ldlt_spec", "yes", 1}, {"ldlt_spec", "no", 0}};
+            {"autotune", "no", 0},  {"ldlt_spec", "yes", 1}, {"ldlt_spec", "no", 0},
+            {"ldlt_spec", "persistent", 2}};
         const std::string n(name), v(value);
         bool known = false;
         for (const W &w : words) {
@@ -1770,7 +1772,7 @@ mdsip_status mdsip_syrk_scaled_tc(mdsip_ctx *hctx, int64_t m, int64_t n, const d
 
 static mdsip_status ldlt_factor_impl(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld, double zero_tol,
                                      double *L, double *Dd, double *Doff, int32_t *perm, int32_t *kind,
-                                     int32_t *inertia, bool fp32_update, bool spec = true);
+                                     int32_t *inertia, bool fp32_update, int spec = 1);
 
 mdsip_status mdsip_ldlt_factor(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld, double zero_tol,
                                double *L, double *Dd, double *Doff, int32_t *perm, int32_t *kind,
@@ -1781,17 +1783,19 @@ mdsip_status mdsip_ldlt_factor(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld
 mdsip_status mdsip_ldlt_factor_ex(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld, double zero_tol,
                                   int32_t flags, double *L, double *Dd, double *Doff, int32_t *perm,
                                   int32_t *kind, int32_t *inertia) {
-    if (flags & ~(MDSIP_LDLT_FP32_UPDATES | MDSIP_LDLT_NO_SPECULATION)) {
-        if (hctx) C_(hctx)->last_error = "ldlt: unknown flags";
+    if ((flags & ~(MDSIP_LDLT_FP32_UPDATES | MDSIP_LDLT_NO_SPECULATION | MDSIP_LDLT_PERSISTENT)) ||
+        ((flags & MDSIP_LDLT_NO_SPECULATION) && (flags & MDSIP_LDLT_PERSISTENT))) {
+        if (hctx) C_(hctx)->last_error = "ldlt: unknown or contradictory flags";
         return MDSIP_ERR_INVALID_ARG;
     }
+    const int spec = (flags & MDSIP_LDLT_NO_SPECULATION) ? 0 : ((flags & MDSIP_LDLT_PERSISTENT) ? 2 : 1);
     return ldlt_factor_impl(hctx, N, S, ld, zero_tol, L, Dd, Doff, perm, kind, inertia,
-                            (flags & MDSIP_LDLT_FP32_UPDATES) != 0, (flags & MDSIP_LDLT_NO_SPECULATION) == 0);
+                            (flags & MDSIP_LDLT_FP32_UPDATES) != 0, spec);
 }
 
 static mdsip_status ldlt_factor_impl(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld, double zero_tol,
                                      double *L, double *Dd, double *Doff, int32_t *perm, int32_t *kind,
-                                     int32_t *inertia, bool fp32_update, bool spec) {
+                                     int32_t *inertia, bool fp32_update, int spec) {
     if (!hctx) return MDSIP_ERR_INVALID_ARG;
     Ctx *ctx = C_(hctx);
     return guarded(ctx, [&] {

@@ -160,7 +160,10 @@ def test_ldlt_fp32_updates(ctx, N, kind):
     R = K[np.ix_(p, p)] - Lh @ D @ Lh.T
     assert np.abs(R).max() <= 1e-4 * np.abs(K).max()
     with pytest.raises(m.MdsipError):
-        m.mdsip_ldlt_factor_ex(ctx, N, S, N, 1e-14, 4, L, Dd, Doff, perm, kd, inr)
+        m.mdsip_ldlt_factor_ex(ctx, N, S, N, 1e-14, 8, L, Dd, Doff, perm, kd, inr)
+    with pytest.raises(m.MdsipError):     # pivot every panel and run the persistent kernel: contradictory
+        m.mdsip_ldlt_factor_ex(ctx, N, S, N, 1e-14, m.MDSIP_LDLT_NO_SPECULATION | m.MDSIP_LDLT_PERSISTENT,
+                               L, Dd, Doff, perm, kd, inr)
 
 
 def _ipm_like(rng, nd, mi):
@@ -284,13 +287,14 @@ def test_ldlt_fp32_speculation_large(ctx, N):
 @pytest.mark.parametrize("N", [1, 20, 63, 64, 65, 200, 1033, 2600])
 def test_ldlt_persistent_keeps_every_panel(ctx, N, fp32):
     """Convex Newton-step matrices (every Bunch-Kaufman decision keeps the
-    diagonal): the persistent no-interchange factorization keeps every panel of
+    diagonal): the persistent no-interchange factorization (forced below the
+    order where it runs by itself) keeps every panel of
     64 columns, so no pivoting panel runs; the oracle's permutation (identity),
     1x1 pivots and inertia, D to rounding (FP64) or FP32 accuracy, and the
     reconstruction."""
     rng = np.random.default_rng(N * 13 + fp32)
     K = _ipm_like(rng, N - min(50, N // 3), min(50, N // 3))
-    g = _fp32_ldlt(ctx, K, m.MDSIP_LDLT_FP32_UPDATES if fp32 else 0)
+    g = _fp32_ldlt(ctx, K, (m.MDSIP_LDLT_FP32_UPDATES if fp32 else 0) | m.MDSIP_LDLT_PERSISTENT)
     o = bk_ldlt(K)
     assert g["inertia"] == o["inertia"]
     np.testing.assert_array_equal(g["kind"], o["kind"])
@@ -319,7 +323,7 @@ def test_ldlt_persistent_hands_over_midway(ctx, fp32):
     K = np.zeros((N, N))
     K[:900, :900] = _ipm_like(rng, 860, 40)
     K[900:, 900:] = _sym(rng, N - 900, "saddle" if fp32 else "zero_diag")
-    g = _fp32_ldlt(ctx, K, m.MDSIP_LDLT_FP32_UPDATES if fp32 else 0)
+    g = _fp32_ldlt(ctx, K, (m.MDSIP_LDLT_FP32_UPDATES if fp32 else 0) | m.MDSIP_LDLT_PERSISTENT)
     o = bk_ldlt(K)
     assert g["inertia"] == o["inertia"]
     np.testing.assert_array_equal(g["kind"], o["kind"])
