@@ -81,11 +81,13 @@ const char *mdsip_status_str(mdsip_status s);
 /*                                                                            */
 /*   f(x)  = 1/2 x_d^T Q x_d + sum_i 1/4 x_s,i^4 + c^T x                      */
 /*   g(x)  = J_sg x_s + A x_d                (equalities g(x) = g_E)          */
-/*   h_j(x)= sum_{k : h_set[k] == j} x_d,k^2  (h^l <= h <= h^u)                */
+/*   h_j(x)= sum_{k : h_set[k] == j} x_d,k^2 + (J_sh x_s)_j  (h^l <= h <= h^u)  */
 /*                                                                            */
 /* A = J_{x_d} g is dense (m_E x n_d, row-major, Section 3.2.3 container      */
 /* blocks (3,1)/(3,2)); J_sg is given as COO triplets (Section 3.2.3: triplet  */
-/* storage), converted once to CSR/CSC on the device.  J_sh = 0.              */
+/* storage), converted once to CSR/CSC on the device; so is J_sh, the        */
+/* inequalities' constant sparse block (nnz_Jsh = 0 in the benchmark family; */
+/* with J_sh != 0 the two-stage path P2 does not apply and AUTO takes P1).    */
 /* ------------------------------------------------------------------------- */
 typedef struct {
     int64_t n_d, n_s, m_E, m_I;
@@ -101,6 +103,10 @@ typedef struct {
     const double *hl, *hu;    /* m_I                                             */
     const double *xl, *xu;    /* n_s + n_d                                       */
     const double *x0;         /* n_s + n_d starting point (nullable: zeros)      */
+    int64_t nnz_Jsh;          /* entries of J_sh (0: J_sh = 0)                   */
+    const int32_t *Jsh_rows;  /* nnz_Jsh, in [0, m_I)                            */
+    const int32_t *Jsh_cols;  /* nnz_Jsh, in [0, n_s)                            */
+    const double *Jsh_vals;   /* nnz_Jsh (duplicates summed)                     */
 } mdsip_synth_data;
 
 /* Copy the data to the device and build the sparse indices.  `mem` tags all

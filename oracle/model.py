@@ -24,7 +24,10 @@ class SynthModel:
         self.n = inst.n_s + inst.n_d
         self.Jsg = sp.csr_matrix((inst.Jsg_vals, (inst.Jsg_rows, inst.Jsg_cols)),
                                  shape=(inst.m_E, inst.n_s))
-        self.Jsh = sp.csr_matrix((inst.m_I, inst.n_s))
+        # sparse block of the inequalities (zero in the benchmark family); h is
+        # linear in x_s, so it adds nothing to the Hessian
+        self.Jsh = sp.csr_matrix((inst.Jsh_vals, (inst.Jsh_rows, inst.Jsh_cols)),
+                                 shape=(inst.m_I, inst.n_s))
         self.A = inst.A
         self.Q = inst.Q
         self.c = inst.c
@@ -52,7 +55,7 @@ class SynthModel:
 
     def h(self, x):
         xs, xd = self.split(x)
-        return self.E @ (xd * xd)
+        return self.E @ (xd * xd) + self.Jsh @ xs
 
     def jac(self, x):
         """Blocks of the constraint Jacobian: (J_sg, J_sh, J_dg = A, J_dh)."""

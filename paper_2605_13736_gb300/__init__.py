@@ -41,7 +41,9 @@ class mdsip_synth_data(C.Structure):
                 ("Q", C.c_void_p), ("c", C.c_void_p), ("A", C.c_void_p), ("gE", C.c_void_p),
                 ("Jsg_rows", C.c_void_p), ("Jsg_cols", C.c_void_p), ("Jsg_vals", C.c_void_p),
                 ("h_set", C.c_void_p), ("hl", C.c_void_p), ("hu", C.c_void_p),
-                ("xl", C.c_void_p), ("xu", C.c_void_p), ("x0", C.c_void_p)]
+                ("xl", C.c_void_p), ("xu", C.c_void_p), ("x0", C.c_void_p),
+                ("nnz_Jsh", C.c_int64), ("Jsh_rows", C.c_void_p), ("Jsh_cols", C.c_void_p),
+                ("Jsh_vals", C.c_void_p)]
 
 
 EVAL_F = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p)
@@ -268,10 +270,14 @@ def mdsip_ctx_last_error(ctx) -> str:
 
 
 def mdsip_problem_create_synthetic(ctx, *, n_d, n_s, m_E, m_I, Q, c, A, gE, Jsg_rows, Jsg_cols,
-                                   Jsg_vals, h_set, hl, hu, xl, xu, x0=None, mem=MDSIP_MEM_HOST):
+                                   Jsg_vals, h_set, hl, hu, xl, xu, x0=None, Jsh_rows=None, Jsh_cols=None,
+                                   Jsh_vals=None, mem=MDSIP_MEM_HOST):
+    nnz_h = 0 if Jsh_vals is None else len(Jsh_vals)
     d = mdsip_synth_data(n_d, n_s, m_E, m_I, len(Jsg_vals), _ptr(Q), _ptr(c), _ptr(A), _ptr(gE),
                          _ptr(Jsg_rows), _ptr(Jsg_cols), _ptr(Jsg_vals), _ptr(h_set), _ptr(hl),
-                         _ptr(hu), _ptr(xl), _ptr(xu), _ptr(x0))
+                         _ptr(hu), _ptr(xl), _ptr(xu), _ptr(x0), nnz_h,
+                         _ptr(Jsh_rows) if nnz_h else None, _ptr(Jsh_cols) if nnz_h else None,
+                         _ptr(Jsh_vals) if nnz_h else None)
     h = C.c_void_p()
     _check(lib().mdsip_problem_create_synthetic(ctx, C.byref(d), mem, C.byref(h)), ctx)
     return h.value
@@ -520,10 +526,15 @@ def mdsip_mlp_train_step(mlp, X, ldx, Y, ldy, idx, batch, lr, want_loss=True, ct
 
 def synth_arrays(inst) -> dict:
     """Keyword arguments of mdsip_problem_create_synthetic from an object with
-    the instance fields (n_d, n_s, m_E, m_I, Q, c, A, b, Jsg_*, h_set, hl, hu, xl, xu, x0)."""
+    the instance fields (n_d, n_s, m_E, m_I, Q, c, A, b, Jsg_*, h_set, hl, hu, xl, xu, x0,
+    and optionally Jsh_*)."""
     f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
     i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
-    return dict(n_d=inst.n_d, n_s=inst.n_s, m_E=inst.m_E, m_I=inst.m_I, Q=f64(inst.Q), c=f64(inst.c),
-                A=f64(inst.A), gE=f64(inst.b), Jsg_rows=i32(inst.Jsg_rows), Jsg_cols=i32(inst.Jsg_cols),
-                Jsg_vals=f64(inst.Jsg_vals), h_set=i32(inst.h_set), hl=f64(inst.hl), hu=f64(inst.hu),
-                xl=f64(inst.xl), xu=f64(inst.xu), x0=f64(inst.x0))
+    out = dict(n_d=inst.n_d, n_s=inst.n_s, m_E=inst.m_E, m_I=inst.m_I, Q=f64(inst.Q), c=f64(inst.c),
+               A=f64(inst.A), gE=f64(inst.b), Jsg_rows=i32(inst.Jsg_rows), Jsg_cols=i32(inst.Jsg_cols),
+               Jsg_vals=f64(inst.Jsg_vals), h_set=i32(inst.h_set), hl=f64(inst.hl), hu=f64(inst.hu),
+               xl=f64(inst.xl), xu=f64(inst.xu), x0=f64(inst.x0))
+    jv = getattr(inst, "Jsh_vals", None)
+    if jv is not None and len(jv):
+        out.update(Jsh_rows=i32(inst.Jsh_rows), Jsh_cols=i32(inst.Jsh_cols), Jsh_vals=f64(jv))
+    return out

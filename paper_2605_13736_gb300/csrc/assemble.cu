@@ -3,14 +3,15 @@
 // Path P1: the compressed 3x3 block matrix of Eq. (compressed) (Section 2.2),
 // with the inertia-correction shifts of Section 2.1:
 //
-//   M = [ Q_d    A^T                        Jdh^T                          ]
-//       [ A      -J_sg Q_s^-1 J_sg^T - dc I   0                              ]
-//       [ Jdh    0                          -Dh^-1 - dc I                  ]
+//   M = [ Q_d    A^T                          Jdh^T                              ]
+//       [ A      -J_sg Q_s^-1 J_sg^T - dc I   -J_sg Q_s^-1 J_sh^T                ]
+//       [ Jdh    -J_sh Q_s^-1 J_sg^T          -J_sh Q_s^-1 J_sh^T - Dh^-1 - dc I ]
 //
-// (J_sh = 0), Q_d = H_dd + Sigma_xd + dw I, Dh = Sigma_d + dw.  The sparse
-// product J_sg Q_s^-1 J_sg^T is the K3 kernel of Section 2.3, here computed
-// row by row from the CSR/CSC indices (each thread owns one output row, so
-// the accumulation order is fixed).
+// Q_d = H_dd + Sigma_xd + dw I, Dh = Sigma_d + dw; the J_sh blocks vanish in
+// the benchmark family.  The sparse product J_s Q_s^-1 J_s^T (J_s = [J_sg;
+// J_sh]) is the K3 kernel of Section 2.3, here computed row by row from the
+// CSR/CSC indices (each thread owns one output row, so the accumulation
+// order is fixed).
 //
 // Path P2: S = [[Q_d, Jdh^T], [Jdh, -Dh^-1 - dc I]]; the SYRK adds A^T W^-1 A.
 //
@@ -87,6 +88,29 @@ __global__ void k_assemble_M_sparse(Dims D, ModelView Mv, const double *__restri
     }
 }
 
+// the h rows of J_s Q_s^-1 J_s^T: for each entry (j, k) of J_sh, with
+// f = J_sh[j,k] / q_k, M[h0 + j][n_d + r] -= f J_sg[r,k] for every r of column
+// k of J_sg, and M[h0 + j][h0 + j2] -= f J_sh[j2,k] for j2 <= j
+__global__ void k_assemble_M_sparse_h(Dims D, ModelView Mv, const double *__restrict__ q,
+                                      double *__restrict__ Mat) {
+    const int64_t N = D.n_d + D.m;
+    const int64_t h0 = D.n_d + D.m_E;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < D.m_I;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        for (int e = Mv.hsr_ptr[j]; e < Mv.hsr_ptr[j + 1]; ++e) {
+            const int k = Mv.hsr_col[e];
+            const double f = Mv.hsr_val[e] / q[k];
+            for (int e2 = Mv.csc_ptr[k]; e2 < Mv.csc_ptr[k + 1]; ++e2)
+                Mat[(h0 + j) + (D.n_d + (int64_t)Mv.csc_row[e2]) * N] -= f * Mv.csc_val[e2];
+            for (int e2 = Mv.hsc_ptr[k]; e2 < Mv.hsc_ptr[k + 1]; ++e2) {
+                const int64_t j2 = Mv.hsc_row[e2];
+                if (j2 > j) continue;
+                Mat[(h0 + j) + (h0 + j2) * N] -= f * Mv.hsc_val[e2];
+            }
+        }
+    }
+}
+
 }  // namespace
 
 void launch_assemble_S(cudaStream_t s, const Dims &D, const double *Hdd, const double *sig_xd,
@@ -109,6 +133,10 @@ void launch_assemble_M(cudaStream_t s, const Dims &D, const ModelView &Mv, const
     if (D.m_E > 0) {
         k_assemble_M_sparse<<<std::max(1, std::min(4096, ceil_div(D.m_E, 256))), 256, 0, s>>>(D, Mv, q,
                                                                                               Mat);
+        MDSIP_LAUNCHED();
+    }
+    if (D.m_I > 0 && Mv.hsr_ptr) {
+        k_assemble_M_sparse_h<<<std::max(1, std::min(4096, ceil_div(D.m_I, 128))), 128, 0, s>>>(D, Mv, q, Mat);
         MDSIP_LAUNCHED();
     }
 }

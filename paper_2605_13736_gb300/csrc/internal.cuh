@@ -163,6 +163,12 @@ struct ModelView {
     const double *csr_val;
     const int32_t *csc_ptr, *csc_row;  // J_sg by columns (n_s + 1, nnz)
     const double *csc_val;
+    // J_sh (the inequalities' sparse block): by rows (m_I + 1) and by columns
+    // (n_s + 1); all null when J_sh = 0 (the benchmark family)
+    const int32_t *hsr_ptr, *hsr_col;
+    const double *hsr_val;
+    const int32_t *hsc_ptr, *hsc_row;
+    const double *hsc_val;
 };
 
 // Number of per-block partial slots used by the reduction kernels.

@@ -103,6 +103,8 @@ struct Problem {
     DBuf bx, bd, byg, byh, bzl, bzu, bvl, bvu, bxt, bdt;
     DBuf bdx, bdd, bdyg, bdyh, bdzl, bdzu, bdvl, bdvu;
     DBuf bcx, bcd, bcyg, bcyh, bczl, bczu, bcvl, bcvu;   // saved direction of the FP64 check
+    DBuf bhsr_ptr, bhsr_col, bhsr_val, bhsc_ptr, bhsc_row, bhsc_val;   // J_sh by rows and by columns
+    int64_t nnz_jsh = 0;
     DirView Dchk{};
     // model values and Newton quantities
     DBuf bgrad, bgrad_t, bcg, bcg_t, bch, bch_t, bgl, bATy, bJdh, bHss, bHdd;
@@ -221,13 +223,15 @@ struct SparseBuild {
     bool p2_ok = true;
 };
 
+// (nrows x n_s block: J_sg with nrows = m_E, J_sh with nrows = m_I)
 static SparseBuild build_sparse(const Dims &D, const std::vector<int32_t> &rows, const std::vector<int32_t> &cols,
-                                const std::vector<double> &vals) {
+                                const std::vector<double> &vals, int64_t nrows = -1, const char *what = "J_sg") {
     SparseBuild b;
+    if (nrows < 0) nrows = D.m_E;
     const int64_t n_in = (int64_t)rows.size();
     for (int64_t e = 0; e < n_in; ++e)
-        MDSIP_REQUIRE(rows[e] >= 0 && rows[e] < D.m_E && cols[e] >= 0 && cols[e] < D.n_s, MDSIP_ERR_INVALID_ARG,
-                      "J_sg index out of range");
+        MDSIP_REQUIRE(rows[e] >= 0 && rows[e] < nrows && cols[e] >= 0 && cols[e] < D.n_s, MDSIP_ERR_INVALID_ARG,
+                      std::string(what) + " index out of range");
     std::vector<int64_t> order((size_t)n_in);
     std::iota(order.begin(), order.end(), 0);
     std::sort(order.begin(), order.end(), [&](int64_t a, int64_t c) {
@@ -247,7 +251,7 @@ static SparseBuild build_sparse(const Dims &D, const std::vector<int32_t> &rows,
         }
     }
     const int64_t nnz = (int64_t)r2.size();
-    b.csr_ptr.assign(D.m_E + 1, 0);
+    b.csr_ptr.assign(nrows + 1, 0);
     b.csc_ptr.assign(D.n_s + 1, 0);
     b.csc_row.resize(nnz);
     b.csc_val.resize(nnz);
@@ -256,7 +260,7 @@ static SparseBuild build_sparse(const Dims &D, const std::vector<int32_t> &rows,
         b.csr_ptr[r2[e] + 1]++;
         b.csc_ptr[c2[e] + 1]++;
     }
-    for (int64_t i = 0; i < D.m_E; ++i) b.csr_ptr[i + 1] += b.csr_ptr[i];
+    for (int64_t i = 0; i < nrows; ++i) b.csr_ptr[i + 1] += b.csr_ptr[i];
     for (int64_t k = 0; k < D.n_s; ++k) b.csc_ptr[k + 1] += b.csc_ptr[k];
     std::vector<int32_t> fill(b.csc_ptr.begin(), b.csc_ptr.end() - 1);
     for (int64_t e = 0; e < nnz; ++e) {  // rows ascending within each column
@@ -431,6 +435,23 @@ static Problem *create_synthetic(Ctx *ctx, const mdsip_synth_data *dat, int mem)
         for (int64_t k = 0; k < D.n_d; ++k)
             MDSIP_REQUIRE(hset[k] >= -1 && hset[k] < D.m_I, MDSIP_ERR_INVALID_ARG, "h_set out of range");
         ModelView &M = P->Mv;
+        MDSIP_REQUIRE(dat->nnz_Jsh >= 0, MDSIP_ERR_INVALID_ARG, "negative nnz_Jsh");
+        if (dat->nnz_Jsh > 0) {   // the inequalities' sparse block: P2's precondition no longer holds
+            MDSIP_REQUIRE(dat->Jsh_rows && dat->Jsh_cols && dat->Jsh_vals, MDSIP_ERR_INVALID_ARG, "null J_sh");
+            auto hr = fetch(dat->Jsh_rows, dat->nnz_Jsh, mem);
+            auto hc = fetch(dat->Jsh_cols, dat->nnz_Jsh, mem);
+            auto hv = fetch(dat->Jsh_vals, dat->nnz_Jsh, mem);
+            SparseBuild hb = build_sparse(D, hr, hc, hv, D.m_I, "J_sh");
+            const int64_t nz = (int64_t)hb.csr_val.size();
+            P->nnz_jsh = nz;
+            M.hsr_ptr = upload(ctx, P->bhsr_ptr, hb.csr_ptr, D.m_I + 1);
+            M.hsr_col = upload(ctx, P->bhsr_col, hb.csr_col, nz);
+            M.hsr_val = upload(ctx, P->bhsr_val, hb.csr_val, nz);
+            M.hsc_ptr = upload(ctx, P->bhsc_ptr, hb.csc_ptr, D.n_s + 1);
+            M.hsc_row = upload(ctx, P->bhsc_row, hb.csc_row, nz);
+            M.hsc_val = upload(ctx, P->bhsc_val, hb.csc_val, nz);
+            P->p2_ok = false;
+        }
         fill(ctx, P->bc, c, n);
         fill(ctx, P->bhset, hset, D.n_d);
         const auto kind = mem == MDSIP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -531,7 +552,7 @@ static void prepare_path(Problem *P) {
     int path = (int)P->opt.path;
     if (path == MDSIP_PATH_AUTO) path = P->p2_ok ? MDSIP_PATH_P2 : MDSIP_PATH_P1;
     MDSIP_REQUIRE(path != MDSIP_PATH_P2 || P->p2_ok, MDSIP_ERR_PRECONDITION,
-                  "path P2 needs J_sg rows with disjoint column supports");
+                  P->nnz_jsh > 0 ? "path P2 needs J_sh = 0" : "path P2 needs J_sg rows with disjoint column supports");
     const int64_t N = path == MDSIP_PATH_P2 ? D.n_d + D.m_I : D.n_d + D.m;
     MDSIP_REQUIRE(2 * N * (int64_t)sizeof(double) <= 200 * 1024 || ldlt_blocked_available(N), MDSIP_ERR_INVALID_ARG,
                   "reduced matrix too large for the dense factorization");
@@ -850,7 +871,7 @@ static void solve_direction(Problem *P, double mu, double dw) {
     MDSIP_CUDA(cudaEventRecord(P->ev[3], st));
     P->V.rhs_y(P->I, gl, P->cg, q, p2 ? w : nullptr, mu, bt_g, p2 ? u : nullptr);
     if (p2) launch_gemv_t(st, P->Mv.A, D.m_E, D.n_d, D.lda, u, P->V.colpart, ATu);
-    P->V.rhs_reduced(P->I, gl, P->ch, sig_d, ATu, bt_g, mu, dw, !p2, rhs);
+    P->V.rhs_reduced(P->I, gl, P->ch, sig_d, ATu, bt_g, q, mu, dw, !p2, rhs);
     launch_ldlt_solve_coop(st, P->ctx->num_sms, P->N, P->bDd.as<double>(), P->bDoff.as<double>(),
                            P->bperm.as<int32_t>(), 1, rhs, P->N, P->bsolve_ws.ptr, P->bsolve_err.as<int>(),
                            P->solve_fp32);

@@ -99,6 +99,8 @@ __global__ void __launch_bounds__(NT) k_eval_cons(Dims D, ModelView M, const dou
             if (M.h_set[k] == j) s += xd[k] * xd[k];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) {
+            if (M.hsr_ptr)   // the sparse x_s part of the inequality (J_sh x_s)_j
+                for (int e = M.hsr_ptr[j]; e < M.hsr_ptr[j + 1]; ++e) s += M.hsr_val[e] * x[M.hsr_col[e]];
             const double r = s - d[j];
             ch[j] = r;
             s1 += fabs(r);
@@ -276,6 +278,8 @@ __global__ void k_lagrangian_grad(Dims D, ModelView M, const double *__restrict_
     for (int64_t i = gtid; i < D.n_s; i += gsz) {
         double s = grad[i];
         for (int e = M.csc_ptr[i]; e < M.csc_ptr[i + 1]; ++e) s += M.csc_val[e] * yg[M.csc_row[e]];
+        if (M.hsc_ptr)
+            for (int e = M.hsc_ptr[i]; e < M.hsc_ptr[i + 1]; ++e) s += M.hsc_val[e] * yh[M.hsc_row[e]];
         gl[i] = s;
     }
     for (int64_t k = gtid; k < D.n_d; k += gsz) {
@@ -458,10 +462,12 @@ __global__ void k_rhs_y(Dims D, ModelView M, IterView I, const double *__restric
 
 // P2: rhs_S[0:n_d] = -rN_xd + ATu ; rhs_S[n_d + j] = -(ch + r_d / Dh)
 // P1: rhs_M[0:n_d] = -rN_xd ; rhs_M[n_d + i] = bt_g[i] ; rhs_M[n_d + m_E + j] = -(ch + r_d/Dh)
+// (with J_sh != 0, P1's h rows also take -J_sh (b_s / q))
 __global__ void k_rhs_reduced(Dims D, ModelView M, IterView I, const double *__restrict__ gl,
                               const double *__restrict__ ch, const double *__restrict__ sig_d,
                               const double *__restrict__ ATu, const double *__restrict__ bt_g,
-                              double mu, double dw, int p1, double *__restrict__ rhs) {
+                              const double *__restrict__ q, double mu, double dw, int p1,
+                              double *__restrict__ rhs) {
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = gtid; k < D.n_d; k += gsz) {
@@ -470,8 +476,15 @@ __global__ void k_rhs_reduced(Dims D, ModelView M, IterView I, const double *__r
         rhs[k] = r;
     }
     const int64_t off_h = p1 ? D.n_d + D.m_E : D.n_d;
-    for (int64_t j = gtid; j < D.m_I; j += gsz)
-        rhs[off_h + j] = -(ch[j] + r_dslack(M, I, mu, j) / (sig_d[j] + dw));
+    for (int64_t j = gtid; j < D.m_I; j += gsz) {
+        double r = -(ch[j] + r_dslack(M, I, mu, j) / (sig_d[j] + dw));
+        if (p1 && M.hsr_ptr)
+            for (int e = M.hsr_ptr[j]; e < M.hsr_ptr[j + 1]; ++e) {
+                const int64_t c = M.hsr_col[e];
+                r += M.hsr_val[e] * rN_x(M, I, gl, mu, c) / q[c];   // -J_sh (b_s/q), b_s = -rN_s
+            }
+        rhs[off_h + j] = r;
+    }
     if (p1)
         for (int64_t i = gtid; i < D.m_E; i += gsz) rhs[D.n_d + i] = bt_g[i];
 }
@@ -499,6 +512,8 @@ __global__ void k_backsub(Dims D, ModelView M, IterView I, DirView Dir, const do
             double s = -rN_x(M, I, gl, mu, i);
             for (int e = M.csc_ptr[i]; e < M.csc_ptr[i + 1]; ++e)
                 s -= M.csc_val[e] * Dir.dyg[M.csc_row[e]];
+            if (M.hsc_ptr)   // J_sh^T dy_h (dy_h from the reduced solution: Dir.dyh is written below)
+                for (int e = M.hsc_ptr[i]; e < M.hsc_ptr[i + 1]; ++e) s -= M.hsc_val[e] * sol_dyh[M.hsc_row[e]];
             dx = s / q[i];
         } else {
             dx = sol_dxd[i - D.n_s];
@@ -886,9 +901,9 @@ void VecOps::rhs_y(const IterView &I, const double *gl, const double *cg, const 
 }
 
 void VecOps::rhs_reduced(const IterView &I, const double *gl, const double *ch, const double *sig_d,
-                         const double *ATu, const double *bt_g, double mu, double dw, bool p1,
+                         const double *ATu, const double *bt_g, const double *q, double mu, double dw, bool p1,
                          double *rhs) {
-    k_rhs_reduced<<<elem_grid(std::max(D.n_d, D.m_E)), 256, 0, st>>>(D, M, I, gl, ch, sig_d, ATu, bt_g,
+    k_rhs_reduced<<<elem_grid(std::max(D.n_d, D.m_E)), 256, 0, st>>>(D, M, I, gl, ch, sig_d, ATu, bt_g, q,
                                                                      mu, dw, p1 ? 1 : 0, rhs);
     MDSIP_LAUNCHED();
 }

@@ -34,7 +34,7 @@ struct VecOps {
     void rhs_y(const IterView &I, const double *gl, const double *cg, const double *q,
                const double *w, double mu, double *bt_g, double *u);
     void rhs_reduced(const IterView &I, const double *gl, const double *ch, const double *sig_d,
-                     const double *ATu, const double *bt_g, double mu, double dw, bool p1,
+                     const double *ATu, const double *bt_g, const double *q, double mu, double dw, bool p1,
                      double *rhs);
     void dyg_p2(const double *Adx, const double *bt_g, const double *w, double *dyg);
     void copy(const double *src, double *dst, int64_t n);

@@ -49,6 +49,10 @@ class Instance:
     xu: np.ndarray         # (n,) upper bounds (+inf = none)
     x0: np.ndarray         # (n,) starting point
     name: str = ""
+    # sparse block J_sh of the inequalities (COO, empty in the benchmark family)
+    Jsh_rows: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0, np.int32))
+    Jsh_cols: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0, np.int32))
+    Jsh_vals: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))
 
     @property
     def n(self) -> int:
@@ -74,12 +78,19 @@ FAMILY = dict(config=4, n_p=64, amplitude=0.2)
 
 
 def make_instance(n_d: int, m_E: int, m_I: int, sigma_a: float, seed: int,
-                  name: str = "", q_shift: float = 0.1) -> Instance:
+                  name: str = "", q_shift: float = 0.1, jsh_per_row: int = 0) -> Instance:
     """Draw one instance.  Everything is a pure function of the arguments.
 
     q_shift is the multiple of I added to G^T G / n_d (0.1 in the benchmark
     family); a negative value makes Q indefinite, a nonconvex variant whose
     x_d is still confined by the inequalities when every x_d is covered.
+
+    jsh_per_row > 0 adds a sparse linear part to every inequality,
+    h_j(x) = ||x_d[S_j]||^2 + sum_{a in T_j} e_ja x_s,a, with T_j that many
+    distinct x_s indices and e_ja ~ U(-0.5, 0.5): a nonzero J_sh (its Hessian
+    stays zero, so assumption A2 holds).  Those draws come from a stream of
+    their own (seeded by (seed, 1)), so the rest of the instance is the same
+    as without them.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     n_s = 2 * m_E
@@ -110,9 +121,16 @@ def make_instance(n_d: int, m_E: int, m_I: int, sigma_a: float, seed: int,
     xl = np.concatenate([-np.ones(n_s), np.full(n_d, -np.inf)])
     xu = np.concatenate([np.ones(n_s), np.full(n_d, np.inf)])
     x0 = np.zeros(n)
-    return Instance(n_d=n_d, n_s=n_s, m_E=m_E, m_I=m_I, Q=Q, c=c, A=np.ascontiguousarray(A),
+    inst = Instance(n_d=n_d, n_s=n_s, m_E=m_E, m_I=m_I, Q=Q, c=c, A=np.ascontiguousarray(A),
                     b=b, Jsg_rows=rows, Jsg_cols=cols, Jsg_vals=vals, h_set=h_set, hu=hu,
                     hl=hl, xl=xl, xu=xu, x0=x0, name=name)
+    if jsh_per_row > 0 and m_I > 0 and n_s > 0:
+        rh = np.random.Generator(np.random.PCG64([seed, 1]))
+        k = min(jsh_per_row, n_s)
+        inst.Jsh_rows = np.repeat(np.arange(m_I), k).astype(np.int32)
+        inst.Jsh_cols = np.concatenate([rh.choice(n_s, size=k, replace=False) for _ in range(m_I)]).astype(np.int32)
+        inst.Jsh_vals = rh.uniform(-0.5, 0.5, size=m_I * k)
+    return inst
 
 
 def make_config(k: int, seed: int | None = None) -> Instance:

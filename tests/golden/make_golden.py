@@ -22,6 +22,12 @@ CASES = {
     # nonconvex variant of the same shape (Q shifted by -20 I): exercises inertia correction
     "mds0_nonconvex_full": dict(kind="inst", n_d=32, m_E=1000, m_I=1, sigma_a=0.1, seed=0,
                                 q_shift=-20.0, linsolve="full"),
+    # the member-0 shape with four inequalities that also carry a sparse x_s part
+    # (J_sh != 0, six terms each), nonconvex (Q shifted by -20 I) so that all four
+    # inequalities are active and inertia correction runs: path P1's general
+    # sparse condensation
+    "mds0_jsh_full": dict(kind="inst", n_d=32, m_E=1000, m_I=4, sigma_a=0.1, seed=0,
+                          q_shift=-20.0, jsh_per_row=6, linsolve="full"),
     # benchmark family member 1: n_d=2000, n_s=200000, m_E=100000, m_I=50; the 4x4 matrix
     # (302050^2) does not fit, so the two-stage condensed solve (itself pinned against the full
     # 4x4 solve on small inputs) gives each direction
@@ -36,7 +42,8 @@ def instance_for(case):
     if case["kind"] == "config":
         return synth.make_config(case["k"])
     return synth.make_instance(case["n_d"], case["m_E"], case["m_I"], case["sigma_a"],
-                               seed=case["seed"], q_shift=case["q_shift"])
+                               seed=case["seed"], q_shift=case["q_shift"],
+                               jsh_per_row=case.get("jsh_per_row", 0))
 
 
 def run(name):

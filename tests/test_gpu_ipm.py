@@ -407,3 +407,71 @@ def test_direction_check_logs_the_gap_to_fp64(ctx, prec):
     assert len(errs) == g["iters"] and all(0.0 <= e <= 1e-10 for e in errs), errs
     assert log[-1]["dir_err_fp64"] == -1.0
     compare_iterations(log, g["log"])
+
+
+# ---------------------------------------------------------------- J_sh != 0
+
+JSH_CASES = [
+    # (n_d, m_E, m_I, sigma_a, seed, q_shift, jsh_per_row)
+    (4, 6, 2, 0.3, 1, 0.1, 2),
+    (33, 70, 5, 0.1, 3, 0.1, 4),
+    (6, 9, 3, 0.3, 4, -3.0, 3),     # indefinite Q
+    (70, 130, 7, 0.05, 5, 0.1, 6),
+]
+
+
+@pytest.mark.parametrize("case", JSH_CASES)
+@pytest.mark.parametrize("dw,dc", [(0.0, 0.0), (1e-4, 0.0), (3.0, 1e-7)])
+def test_direction_parity_sparse_inequality_block(ctx, case, dw, dc):
+    """Inequalities with a sparse x_s part (J_sh != 0): path AUTO takes P1, whose
+    compressed matrix carries the J_sh blocks of J_s Q_s^-1 J_s^T; the direction
+    equals the oracle's full 4x4 solve to 1e-10 with the same inertia."""
+    n_d, m_E, m_I, sa, seed, qs, jsh = case
+    inst = synth.make_instance(n_d, m_E, m_I, sa, seed=seed, q_shift=qs, jsh_per_row=jsh)
+    model = SynthModel(inst)
+    pt = _point(synth.random_iterate(inst, seed + 100))
+    mu = 0.05
+    want = ipm.direction_at(model, pt, mu, dw, dc, "full")
+    prob = make_problem(ctx, inst)
+    try:
+        out = np.zeros(m.mdsip_packed_size(prob))
+        inertia = m.mdsip_debug_direction(prob, pt.packed(), mu, dw, dc, out, ctx=ctx)
+        assert m.mdsip_get_stats(prob)["path"] in (0, m.MDSIP_PATH_P1)
+        m.mdsip_set_option_int(prob, "path", m.MDSIP_PATH_P2, ctx)
+        with pytest.raises(m.MdsipError) as ei:      # P2's precondition: J_sh = 0
+            m.mdsip_debug_direction(prob, pt.packed(), mu, dw, dc, out, ctx=ctx)
+        assert ei.value.status == 10 and "J_sh" in str(ei.value)
+    finally:
+        m.mdsip_problem_destroy(prob)
+    assert inertia == tuple(want["inertia"])
+    ref = pack_dir(want)
+    assert np.linalg.norm(out - ref) / np.linalg.norm(ref) <= 1e-10
+
+
+def test_sparse_inequality_block_trajectory(ctx):
+    """The member-0 shape with four active inequalities carrying a sparse x_s
+    part (nonconvex, so inertia correction runs): the oracle's iteration
+    count, inertia-correction sequence, per-iteration record and objective."""
+    g = _golden("mds0_jsh_full")
+    c = g["case"]
+    inst = synth.make_instance(c["n_d"], c["m_E"], c["m_I"], c["sigma_a"], seed=c["seed"],
+                               q_shift=c["q_shift"], jsh_per_row=c["jsh_per_row"])
+    prob = make_problem(ctx, inst)
+    try:
+        st = m.mdsip_solve(prob, ctx)
+        stats = m.mdsip_get_stats(prob)
+        log = m.mdsip_get_log(prob)
+    finally:
+        m.mdsip_problem_destroy(prob)
+    assert m.STATUS[st] == g["status"] == "OK"
+    assert stats["path"] == m.MDSIP_PATH_P1
+    assert stats["iters"] == g["iters"]
+    assert abs(stats["f"] - g["f"]) <= 1e-8 * abs(g["f"])
+    for rec, grec in zip(log, g["log"]):
+        want = grec.get("ic", [])
+        assert len(rec["ic"]) == len(want), (rec["iter"], rec["ic"], want)
+        for (dw, dc, inr), (gdw, gdc, ginr) in zip(rec["ic"], want):
+            assert tuple(inr) == tuple(ginr)
+            assert dw == pytest.approx(gdw, rel=1e-12, abs=0)
+            assert dc == pytest.approx(gdc, rel=1e-12, abs=0)
+    compare_iterations(log, g["log"])

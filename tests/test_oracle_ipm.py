@@ -155,3 +155,18 @@ def test_nonconvex_synthetic_uses_inertia_correction():
     # library optimizer started from the same solution
     ref = _scipy_opt(inst)
     assert r["f"] <= ref.fun + 1e-6 * max(1.0, abs(ref.fun))
+
+
+def test_sparse_inequality_block_matches_library_optimizer():
+    """Inequalities with a sparse x_s part (J_sh != 0, path P1 and the full
+    solve): the oracle's optimum equals scipy's trust-constr optimum, and every
+    accepted factorization has the target inertia."""
+    inst = synth.make_instance(4, 6, 2, 0.3, seed=3, jsh_per_row=2)
+    ref = _scipy_opt(inst)
+    for ls in ("full", "p1"):
+        r = ipm.solve(SynthModel(inst), opt=ipm.Options(linsolve=ls))
+        assert r["status"] == 0 and r["E0"] <= 1e-8
+        assert abs(r["f"] - ref.fun) <= 1e-6 * max(1.0, abs(ref.fun))
+        np.testing.assert_allclose(r["point"].x, ref.x, atol=1e-4)
+        for rec in r["log"][:-1]:
+            assert rec["ic"][-1][2] == (inst.n, inst.m, 0)

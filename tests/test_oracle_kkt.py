@@ -16,8 +16,8 @@ from oracle import kkt, ipm
 from oracle.model import SynthModel
 
 
-def _setup(n_d=4, m_E=6, m_I=2, seed=5, q_shift=0.1, spread=1.0):
-    inst = synth.make_instance(n_d, m_E, m_I, 0.3, seed=seed, q_shift=q_shift)
+def _setup(n_d=4, m_E=6, m_I=2, seed=5, q_shift=0.1, spread=1.0, jsh=0):
+    inst = synth.make_instance(n_d, m_E, m_I, 0.3, seed=seed, q_shift=q_shift, jsh_per_row=jsh)
     model = SynthModel(inst)
     it = synth.random_iterate(inst, seed + 1, spread=spread)
     pt = ipm.Point(it["x"], it["d"], it["yg"], it["yh"], it["zl"], it["zu"], it["vl"], it["vu"])
@@ -138,3 +138,46 @@ def test_nonconvex_needs_correction():
     for (a, _, _), (b, _, _) in zip(attempts[1:], attempts[2:]):
         assert b == pytest.approx(100.0 * a)         # first-time growth factor
     assert state["dw_last"] == attempts[-1][0]
+
+
+# ---------------------------------------------------------------- J_sh != 0
+
+@pytest.mark.parametrize("dw,dc", [(0.0, 0.0), (1e-3, 0.0), (0.5, 1e-6)])
+def test_sparse_inequality_block_directions_agree(dw, dc):
+    """Inequalities with a sparse x_s part (J_sh != 0): the full and compressed
+    solves agree with the unreduced system, the two-stage form does not apply
+    (J_s Q_s^-1 J_s^T couples g and h rows), and both inertias are the
+    eigenvalue inertia of the 4x4 matrix."""
+    inst, model, P, pt, ev = _setup(n_d=5, m_E=7, m_I=3, seed=31, jsh=3)
+    sy = ipm.newton_system(P, pt, ev, mu=0.05)
+    assert sy.Jsh.nnz == 9
+    assert not kkt.p2_applicable(sy.Jsg, sy.Jsh)
+    ref = _unreduced(sy, dw, dc)
+    want = np.concatenate([ref["dx"], ref["dd"], ref["dyg"], ref["dyh"]])
+    K, _ = kkt.assemble_k4(sy, dw, dc)
+    for name in ("full", "p1"):
+        r = kkt.DIRECTIONS[name](sy, dw, dc)
+        got = np.concatenate([r["dxs"], r["dxd"], r["dd"], r["dyg"], r["dyh"]])
+        assert np.linalg.norm(got - want) <= 1e-11 * np.linalg.norm(want), name
+        assert r["inertia"] == _eig_inertia(K), name
+
+
+def test_sparse_inequality_block_newton_step():
+    """With J_sh != 0 the direction is still the Newton step on the perturbed
+    KKT conditions (Jacobian by finite differences)."""
+    inst, model, P, pt, ev = _setup(n_d=3, m_E=4, m_I=2, seed=13, jsh=2)
+    assert model.Jsh.nnz == 4
+    mu = 0.03
+    n, m_I, m_E = P.n, P.m_I, P.m_E
+    v0 = pt.packed()
+    F0 = _kkt_F(P, model, v0, mu, (n, m_I, m_E))
+    J = np.zeros((F0.size, v0.size))
+    eps = 1e-6
+    for i in range(v0.size):
+        e = np.zeros_like(v0)
+        e[i] = eps
+        J[:, i] = (_kkt_F(P, model, v0 + e, mu, (n, m_I, m_E)) - _kkt_F(P, model, v0 - e, mu, (n, m_I, m_E))) / (2 * eps)
+    newton = np.linalg.solve(J, -F0)
+    r = ipm.direction_at(model, pt, mu, 0.0, 0.0, "p1")
+    ours = np.concatenate([r["dx"], r["dd"], r["dyg"], r["dyh"], r["dzl"], r["dzu"], r["dvl"], r["dvu"]])
+    np.testing.assert_allclose(ours, newton, rtol=1e-6, atol=1e-7 * np.abs(newton).max())

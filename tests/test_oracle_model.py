@@ -14,8 +14,12 @@ def _fd(fun, x, eps=1e-6):
     return np.stack(cols, axis=-1)
 
 
-def test_derivatives_match_finite_differences():
-    inst = synth.make_instance(5, 6, 2, 0.3, seed=11)
+import pytest
+
+
+@pytest.mark.parametrize("jsh", [0, 3])
+def test_derivatives_match_finite_differences(jsh):
+    inst = synth.make_instance(5, 6, 2, 0.3, seed=11, jsh_per_row=jsh)
     m = SynthModel(inst)
     rng = np.random.default_rng(0)
     x = rng.uniform(-0.8, 0.8, size=m.n)
@@ -59,3 +63,23 @@ def test_instance_structure():
     small = synth.make_instance(100, 10, 5, 0.01, seed=1)
     counts = np.bincount(small.h_set[small.h_set >= 0], minlength=5)
     assert np.all(counts == 20)
+
+
+def test_sparse_inequality_part():
+    """jsh_per_row adds h_j += sum e_ja x_s,a with that many distinct indices per
+    row, and leaves every other array of the instance as it was."""
+    a = synth.make_instance(8, 20, 3, 0.1, seed=5)
+    b = synth.make_instance(8, 20, 3, 0.1, seed=5, jsh_per_row=4)
+    for k in ("Q", "c", "A", "b", "h_set", "hu", "xl", "xu"):
+        np.testing.assert_array_equal(getattr(a, k), getattr(b, k))
+    assert a.Jsh_rows.size == 0 and b.Jsh_rows.size == 12
+    for j in range(3):
+        cols = b.Jsh_cols[b.Jsh_rows == j]
+        assert cols.size == 4 and np.unique(cols).size == 4
+    m = SynthModel(b)
+    x = np.random.default_rng(1).uniform(-0.5, 0.5, m.n)
+    xs, xd = x[:m.n_s], x[m.n_s:]
+    h = np.array([np.sum(xd[b.h_set == j] ** 2) for j in range(3)])
+    for r, c, v in zip(b.Jsh_rows, b.Jsh_cols, b.Jsh_vals):
+        h[r] += v * xs[c]
+    np.testing.assert_allclose(m.h(x), h, rtol=1e-15, atol=1e-15)
