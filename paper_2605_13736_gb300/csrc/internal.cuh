@@ -314,6 +314,16 @@ void launch_finalize_min(cudaStream_t s, const double *partial, int nq, double *
 // A passes (row-major A, m x n, leading dimension lda)
 void launch_gemv_rows(cudaStream_t s, const double *A, int64_t m, int64_t n, int64_t lda,
                       const double *v, double *out);  // out = A v
+// out[p] = sum_b partial[b][p] (fixed order); partial: nparts x n
+void launch_colsum(cudaStream_t s, const double *partial, int nparts, int64_t n, double *out);
+// gemv_df.cu: passes over A = A_hi + A_lo (FP32 pair, m x lda) in double-float
+// arithmetic with FP64 accuracy; xs / ys: scratch of n / m float2
+void launch_split_matrix(cudaStream_t s, const double *A, int64_t m, int64_t n, int64_t lda, float *hi,
+                         float *lo);
+void launch_gemv_rows_df(cudaStream_t s, const float *Ahi, const float *Alo, int64_t m, int64_t n, int64_t lda,
+                         const double *x, float2 *xs, double *out);
+void launch_gemv_t_df(cudaStream_t s, const float *Ahi, const float *Alo, int64_t m, int64_t n, int64_t lda,
+                      const double *y, float2 *ys, double *partial, double *out);
 void launch_gemv_t(cudaStream_t s, const double *A, int64_t m, int64_t n, int64_t lda,
                    const double *u, double *partial, double *out);  // out = A^T u
 

@@ -225,7 +225,8 @@ void Refiner::approx_solve(const double *b, double *sol) {
     k_rhs_S<<<grid_for(std::max(D.n_d, D.m_I)), 256, 0, st>>>(D, b, tmp_nd, rhsS);
     MDSIP_LAUNCHED();
     launch_ldlt_solve_coop(st, num_sms, N, Dd, Doff, perm, 1, rhsS, N, solve_ws, solve_err, solve_fp32);
-    launch_gemv_rows(st, M.A, D.m_E, D.n_d, D.lda, rhsS, tmp_m);
+    if (Ahi) launch_gemv_rows_df(st, Ahi, Alo, D.m_E, D.n_d, D.lda, rhsS, split, tmp_m);
+    else launch_gemv_rows(st, M.A, D.m_E, D.n_d, D.lda, rhsS, tmp_m);
     k_sol_gdh<<<grid_for(std::max(D.m_E, D.n_d)), 256, 0, st>>>(D, tmp_m, bt_g, w, rhsS, sol);
     MDSIP_LAUNCHED();
     k_sol_s<<<grid_for(D.n_s), 256, 0, st>>>(D, M, b, q, sol);
@@ -241,7 +242,8 @@ void Refiner::track_Au(bool init) {
 }
 
 void Refiner::residual(const double *b, const double *u, double dw, double dc, double *r, double *out4) {
-    launch_gemv_t(st, M.A, D.m_E, D.n_d, D.lda, u + D.n, colpart, tmp_nd);     // A^T u_g
+    if (Ahi) launch_gemv_t_df(st, Ahi, Alo, D.m_E, D.n_d, D.lda, u + D.n, split, colpart, tmp_nd);   // A^T u_g
+    else launch_gemv_t(st, M.A, D.m_E, D.n_d, D.lda, u + D.n, colpart, tmp_nd);
     k_hdd_gemv<<<std::max(1, std::min(4096, ceil_div((D.n_d + D.m_I) * 32, 256))), 256, 0, st>>>(
         D.n_d, D.m_I, Hdd, Jdh, u + D.n_s, tmp_nd2);
     MDSIP_LAUNCHED();

@@ -26,6 +26,9 @@ struct Refiner {
     // scratch: bt_g, tmp_m (m_E), tmp_nd (n_d), tmp_nd2 (n_d + m_I), rhsS (N), colpart, partial
     double *bt_g, *tmp_m, *tmp_nd, *tmp_nd2, *rhsS, *colpart, *partial;
     double *Au_run;   // A u_d of the current solution, kept as a running sum (m_E)
+    // A as an FP32 pair for the passes in double-float arithmetic (null: FP64 passes)
+    const float *Ahi, *Alo;
+    float2 *split;    // max(m_E, n_d) float2
 
     // b = right-hand side of Eq. (linsys4x4), packed [s | d | g | h]
     void rhs(const IterView &I, const double *gl, const double *cg, const double *ch, const double *sig_d,

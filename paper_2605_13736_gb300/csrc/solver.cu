@@ -114,6 +114,8 @@ struct Problem {
     // tensor-core condensation and refinement
     DBuf bAfT, bvf, btc_ws, btc_err, bref_b, bref_u, bref_r, bref_d, btmp_nd2, bsolve_ws, bsolve_err, bAu_run;
     bool aft_ready = false;
+    DBuf bAhi, bAlo, bsplit;   // A as an FP32 pair (mixed path's double-float passes) and vector scratch
+    bool df_ready = false;
     int64_t tc_prec = -1;
     DBuf bscal, bpartial, bcolpart, browtmp;
     double *hscal = nullptr;  // pinned mirror of the scalars
@@ -544,6 +546,9 @@ static void model_jac_hess(Problem *P, const double *x, const double *yg, const 
     cb_check(P->cb.eval_hess(P->user, st, x, yg, yh, P->bHss.as<double>(), P->bHdd.as<double>(), D.n_d),
              "eval_hess");
     P->aft_ready = false;  // the tensor-core copy of A follows the Jacobian
+    if (P->df_ready)       // so does its FP32 pair
+        launch_split_matrix(P->ctx->stream, P->bA.as<double>(), D.m_E, D.n_d, D.lda, P->bAhi.as<float>(),
+                            P->bAlo.as<float>());
 }
 
 // allocate the reduced matrix and factor storage for the chosen path
@@ -591,9 +596,23 @@ static void prepare_path(Problem *P) {
 // for the model family) and the per-call workspace.
 static void prepare_tc(Problem *P) {
     const int prec = (int)P->opt.precision;
+    P->V.Ahi = P->V.Alo = nullptr;
+    P->V.split = nullptr;
     if (prec == MDSIP_PREC_FP64 || P->path != MDSIP_PATH_P2) return;
     Ctx *ctx = P->ctx;
     const Dims &D = P->D;
+    if (!P->df_ready && D.m_E > 0 && D.n_d > 0) {   // A as an FP32 pair (once: A follows the Jacobian)
+        P->bAhi.get<float>(ctx, (size_t)D.m_E * D.lda);
+        P->bAlo.get<float>(ctx, (size_t)D.m_E * D.lda);
+        P->bsplit.get<float2>(ctx, (size_t)std::max(D.m_E, D.n_d));
+        launch_split_matrix(ctx->stream, P->Mv.A, D.m_E, D.n_d, D.lda, P->bAhi.as<float>(), P->bAlo.as<float>());
+        P->df_ready = true;
+    }
+    if (P->df_ready) {
+        P->V.Ahi = P->bAhi.as<float>();
+        P->V.Alo = P->bAlo.as<float>();
+        P->V.split = P->bsplit.as<float2>();
+    }
     const TcPlan pl = syrk_tc_plan(D.m_E, D.n_d, ctx->num_sms, prec);
     if (!P->bAfT.ptr) P->bAfT.get<float>(ctx, (size_t)std::max<int64_t>(D.n_d, 1) * pl.ldt);
     if (!P->bvf.ptr) P->bvf.get<float>(ctx, (size_t)pl.ldt);
@@ -929,6 +948,9 @@ static RefineResult solve_direction_refined(Problem *P, double mu, double dw, do
     R.colpart = P->V.colpart;
     R.partial = P->V.partial;
     R.Au_run = P->bAu_run.as<double>();
+    R.Ahi = P->V.Ahi;
+    R.Alo = P->V.Alo;
+    R.split = P->V.split;
     double *b = P->bref_b.as<double>(), *u = P->bref_u.as<double>(), *r = P->bref_r.as<double>(),
            *d = P->bref_d.as<double>();
     const double *h = P->hscal;

@@ -837,6 +837,12 @@ void launch_gemv_rows(cudaStream_t s, const double *A, int64_t m, int64_t n, int
     MDSIP_LAUNCHED();
 }
 
+void launch_colsum(cudaStream_t s, const double *partial, int nparts, int64_t n, double *out) {
+    if (n <= 0) return;
+    k_colsum<<<(unsigned)ceil_div(n, 32), 256, 0, s>>>(partial, nparts, n, out);
+    MDSIP_LAUNCHED();
+}
+
 void launch_gemv_t(cudaStream_t s, const double *A, int64_t m, int64_t n, int64_t lda,
                    const double *u, double *partial, double *out) {
     if (n <= 0) return;
@@ -857,7 +863,10 @@ void VecOps::eval_f(const double *x, double *grad, double *out_scalar) {
 }
 
 void VecOps::eval_cons(const double *x, const double *d, double *cg, double *ch, double *out2) {
-    if (D.m_E > 0) launch_gemv_rows(st, M.A, D.m_E, D.n_d, D.lda, x + D.n_s, rowtmp);
+    if (D.m_E > 0) {
+        if (Ahi) launch_gemv_rows_df(st, Ahi, Alo, D.m_E, D.n_d, D.lda, x + D.n_s, split, rowtmp);
+        else launch_gemv_rows(st, M.A, D.m_E, D.n_d, D.lda, x + D.n_s, rowtmp);
+    }
     k_eval_cons<<<kRedBlocks, NT, 0, st>>>(D, M, x, rowtmp, d, cg, ch, partial);
     MDSIP_LAUNCHED();
     launch_finalize_sum(st, partial, 1, out2);
@@ -871,7 +880,8 @@ void VecOps::jac_hess(const double *x, const double *yh, double *Jdh, double *Hs
 
 void VecOps::lagrangian_grad(const IterView &I, const double *grad, const double *Jdh, double *ATy,
                              double *gl) {
-    launch_gemv_t(st, M.A, D.m_E, D.n_d, D.lda, I.yg, colpart, ATy);
+    if (Ahi) launch_gemv_t_df(st, Ahi, Alo, D.m_E, D.n_d, D.lda, I.yg, split, colpart, ATy);
+    else launch_gemv_t(st, M.A, D.m_E, D.n_d, D.lda, I.yg, colpart, ATy);
     k_lagrangian_grad<<<elem_grid(std::max(D.n_s, D.n_d)), 256, 0, st>>>(D, M, grad, I.yg, I.yh, Jdh,
                                                                          ATy, gl);
     MDSIP_LAUNCHED();

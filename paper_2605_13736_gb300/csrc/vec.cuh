@@ -21,6 +21,11 @@ struct VecOps {
     double *partial;
     double *colpart;
     double *rowtmp;   // m_E doubles: A x_d of the constraint evaluation
+    // mixed-precision path: A as an FP32 pair (A_hi + A_lo) for the passes over A
+    // in double-float arithmetic, and their vector scratch (max(m_E, n_d) float2);
+    // null on the plain FP64 path
+    const float *Ahi = nullptr, *Alo = nullptr;
+    float2 *split = nullptr;
 
     void eval_f(const double *x, double *grad, double *out_scalar);
     void eval_cons(const double *x, const double *d, double *cg, double *ch, double *out2);
