@@ -360,23 +360,61 @@ def run_reference(args):
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
-def run_batch(args, m, torch, local):
+def partition_instances(costs, world):
+    """Instances (by index) over ranks: longest-processing-time first, each to
+    the least-loaded rank (ties to the lower rank), so every rank gets a
+    deterministic share whose summed cost is within the largest single cost
+    of the mean.  Returns one sorted index list per rank."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    loads = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda q: (loads[q], q))
+        parts[r].append(i)
+        loads[r] += costs[i]
+    return [sorted(p) for p in parts]
+
+
+def batch_aggregate(local, world, device=None):
+    """Whole-job figures of a partitioned batch from each rank's own: time =
+    max over ranks (every rank starts after a barrier), counts summed, worst
+    KKT error max'ed."""
+    return {"t_seq": reduce_scalar(local["t_seq"], "max", world, device) if local["t_seq"] is not None else None,
+            "t_bat": reduce_scalar(local["t_bat"], "max", world, device),
+            "n": reduce_scalar(local["n"], "sum", world, device),
+            "n_ok": reduce_scalar(local["n_ok"], "sum", world, device),
+            "iters": reduce_scalar(local["iters"], "sum", world, device),
+            "max_E0": reduce_scalar(local["max_E0"], "max", world, device)}
+
+
+def run_batch(args, m, torch, local, rank=0, world=1):
     """Many independent instances (one IPM solve each): sequential on one stream
     vs mdsip_batch_solve with one context per instance.  The contexts' streams
     come from torch's stream pool (32 distinct streams per device), so at most
-    32 instances run at once; instances sharing a stream run in turn."""
+    32 instances run at once; instances sharing a stream run in turn.  With
+    several ranks the instances are partitioned over them (partition_instances
+    on n_d^3, the order of both the product and the factorization) and every
+    rank solves its share on its own GPU; no data crosses ranks."""
     import numpy as np
     import synth
+    dev = torch.device("cuda", local)
     rng = np.random.default_rng(7)
     sizes = rng.integers(64, args.batch_max_nd + 1, size=args.batch_count)
+    parts = partition_instances([float(nd) ** 3 for nd in sizes], world)
+    mine = parts[rank]
     out = {"instances": len(sizes), "n_d_range": [int(sizes.min()), int(sizes.max())],
            "shape": "n_s = 100 n_d, m_E = 50 n_d, m_I = 50, a_i ~ N(0, 0.01^2), seeds 1000+i",
-           "fp64_jacobian_gb": float(sum(50.0 * int(nd) * int(nd) * 8 for nd in sizes) / 1e9)}
-    streams = [torch.cuda.Stream(device=local) for _ in sizes]
+           "fp64_jacobian_gb": float(sum(50.0 * int(nd) * int(nd) * 8 for nd in sizes) / 1e9),
+           "partition": {"ranks": world, "rule": "longest processing time first on n_d^3",
+                         "instances_per_rank": [len(p) for p in parts],
+                         "max_over_mean_load": (max(sum(float(sizes[i]) ** 3 for i in p) for p in parts) /
+                                                (sum(float(nd) ** 3 for nd in sizes) / world))}}
+    streams = [torch.cuda.Stream(device=local) for _ in mine]
     ctxs = [m.mdsip_ctx_create(local, st.cuda_stream) for st in streams]
     probs = []
-    for i, (c, nd) in enumerate(zip(ctxs, sizes)):   # one host instance at a time
-        inst = synth.make_instance(int(nd), int(50 * nd), 50, 0.01, seed=1000 + i)
+    for c, i in zip(ctxs, mine):   # one host instance at a time
+        nd = int(sizes[i])
+        inst = synth.make_instance(nd, 50 * nd, 50, 0.01, seed=1000 + i)
         probs.append(m.mdsip_problem_create_synthetic(c, **m.synth_arrays(inst)))
         del inst
     try:
@@ -397,22 +435,31 @@ def run_batch(args, m, torch, local):
             seq = []
             t_seq = None
             if name != "fp64" or args.batch_seq_fp64:
+                barrier(world)
                 t0 = time.perf_counter()
                 seq = [m.mdsip_solve(p) for p in probs]
                 t_seq = time.perf_counter() - t0
+            barrier(world)
             t0 = time.perf_counter()
             bst = m.mdsip_batch_solve(probs, args.batch_concurrency)
             torch.cuda.synchronize()
             t_bat = time.perf_counter() - t0
-            iters = sum(m.mdsip_get_stats(p)["iters"] for p in probs)
-            out[name] = {"sequential_solves_per_s": len(probs) / t_seq if t_seq else None,
-                         "batched_solves_per_s": len(probs) / t_bat,
-                         "batched_newton_steps_per_s": iters / t_bat,
-                         "speedup": t_seq / t_bat if t_seq else None,
-                         "all_ok": all(m.STATUS[x] == "OK" for x in seq + bst),
+            agg = batch_aggregate({"t_seq": t_seq, "t_bat": t_bat, "n": len(probs),
+                                   "n_ok": sum(m.STATUS[x] == "OK" for x in bst) + sum(m.STATUS[x] == "OK" for x in seq),
+                                   "iters": sum(m.mdsip_get_stats(p)["iters"] for p in probs),
+                                   "max_E0": max([m.mdsip_get_stats(p)["E0"] for p in probs] or [0.0])}, world, dev)
+            n_runs = agg["n"] * (2 if seq else 1)
+            out[name] = {"sequential_solves_per_s": agg["n"] / agg["t_seq"] if agg["t_seq"] else None,
+                         "batched_solves_per_s": agg["n"] / agg["t_bat"],
+                         "batched_newton_steps_per_s": agg["iters"] / agg["t_bat"],
+                         "speedup": agg["t_seq"] / agg["t_bat"] if agg["t_seq"] else None,
+                         "all_ok": agg["n_ok"] == n_runs,
+                         "solves_ok": f"{int(agg['n_ok'])} of {int(n_runs)}",
                          "statuses_sequential": {k: [m.STATUS[x] for x in seq].count(k) for k in set(m.STATUS[x] for x in seq)},
                          "statuses_batched": {k: [m.STATUS[x] for x in bst].count(k) for k in set(m.STATUS[x] for x in bst)},
-                         "max_E0": max(m.mdsip_get_stats(p)["E0"] for p in probs)}
+                         "max_E0": agg["max_E0"]}
+            if world > 1:
+                out[name]["statuses_rank0_only"] = True
         out["bf16_vs_fp64_batched"] = out["bf16"]["batched_solves_per_s"] / out["fp64"]["batched_solves_per_s"]
     finally:
         for p in probs:
@@ -816,6 +863,8 @@ def run_gpu(args):
         m.mdsip_problem_destroy(prob)
         m.mdsip_ctx_destroy(ctx)
 
+    # the batched workload on every rank (its instances partitioned over them)
+    batch = run_batch(args, m, torch, local, rank, world) if args.batch_count > 0 else None
     if rank != 0:
         return
     D = dict(n_d=inst.n_d, n_s=inst.n_s, m_E=inst.m_E, m_I=inst.m_I)
@@ -824,7 +873,6 @@ def run_gpu(args):
         cpu = cpu_baseline(inst, args.config, args.warmup, args.cpu_steps)
     del inst
     mixed = run_mixed(args, m, torch, local) if (args.mixed_config >= 0 and world == 1) else None
-    batch = run_batch(args, m, torch, local) if (args.batch_count > 0 and world == 1) else None
     wstart = run_warmstart(args, m, torch, local) if (args.ws_train > 0 and world == 1) else None
     flops = D["n_d"] * (D["n_d"] + 1) / 2 * D["m_E"] * 2.0
     syrk_ms = acc["t_syrk_ms"] / max(1, acc["n_syrk"])

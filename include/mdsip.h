@@ -337,6 +337,24 @@ mdsip_status mdsip_syrk_scaled_tc(mdsip_ctx *ctx, int64_t m, int64_t n, const do
                                   const double *w, double beta, double *C, int64_t ldc,
                                   int precision);
 
+/* The two products with the dense Jacobian block that the FP64 residual of
+ * Eq. (linsys4x4) needs (the A u_d and A^T u_g terms), from one pass over A in
+ * double-float arithmetic (the form the refined mixed-precision path uses):
+ *   Ax[i] = sum_p A[i][p] x[p]  (i < m),   ATv[p] = sum_i A[i][p] v[i]  (p < n).
+ * A: m x n row-major, leading dimension lda (lda >= n, lda % 4 == 0, 16-byte
+ * aligned); x: n, v: m; Ax: m, ATv: n; all device pointers owned by the
+ * caller.  A is split once into A_hi = fl32(A), A_lo = fl32(A - A_hi) (library
+ * scratch); every product is formed exactly on the FP32 pipes and the sums
+ * are folded into FP64 every 16 terms.  Worst case, each result is within
+ * 2^-36 sum_p |A[i][p] x[p]| (resp. sum_i |A[i][p] v[i]|) of the exact value
+ * for n, m <= 2^20 (split and cross terms 7 2^-48, FP32 carries of a 16-term
+ * block and of the block reduction about 1100 2^-48, FP64 folds n/16 2^-53,
+ * each times that sum); typical errors are those of an FP64 product.
+ * Returns after the results are written (synchronises the context's stream).
+ * Errors: INVALID_ARG (sizes, alignment, null pointers), OOM. */
+mdsip_status mdsip_gemv_pair_df(mdsip_ctx *ctx, int64_t m, int64_t n, const double *A, int64_t lda,
+                                const double *x, const double *v, double *Ax, double *ATv);
+
 /* Bunch-Kaufman LDL^T (Section 2.3) of the symmetric N x N matrix whose lower
  * triangle is in S (column-major, leading dimension ld).  S is overwritten
  * (used as work space).  Outputs (device):

@@ -123,6 +123,8 @@ _SIGS = {
                                     C.c_void_p, C.c_double, C.c_void_p, C.c_int64]),
     "mdsip_syrk_scaled_tc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int64,
                                        C.c_void_p, C.c_double, C.c_void_p, C.c_int64, C.c_int]),
+    "mdsip_gemv_pair_df": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int64,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mdsip_ldlt_factor": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_double,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p]),
@@ -404,6 +406,10 @@ def mdsip_syrk_scaled(ctx, m, n, A, lda, w, beta, Cmat, ldc):
 def mdsip_syrk_scaled_tc(ctx, m, n, A, lda, w, beta, Cmat, ldc, precision):
     _check(lib().mdsip_syrk_scaled_tc(ctx, m, n, _ptr(A), lda, _ptr(w), float(beta), _ptr(Cmat), ldc,
                                       int(precision)), ctx)
+
+
+def mdsip_gemv_pair_df(ctx, m, n, A, lda, x, v, Ax, ATv):
+    _check(lib().mdsip_gemv_pair_df(ctx, m, n, _ptr(A), lda, _ptr(x), _ptr(v), _ptr(Ax), _ptr(ATv)), ctx)
 
 
 def mdsip_ldlt_factor(ctx, N, S, ld, zero_tol, L, Dd, Doff, perm, kind, inertia):

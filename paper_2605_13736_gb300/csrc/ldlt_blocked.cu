@@ -1047,7 +1047,8 @@ constexpr int kPThreads = 256;
 constexpr int kPP = 65;      // shared-memory row pitch of the diagonal block
 
 struct PanelBar {
-    unsigned count, gen;
+    unsigned count;   // grid-barrier arrivals of the current launch
+    unsigned pad0;
     int err, pad;
 };
 
@@ -1064,6 +1065,7 @@ struct PersistArgs {
     const double *maxabs;
     double zero_tol;
     long long wait_ns;              // bound of each grid-barrier wait
+    float *Af;                      // FP32 copy of the lower triangle, ld N (FP32-update kernel)
 };
 
 __device__ __forceinline__ long long global_ns() {
@@ -1072,35 +1074,40 @@ __device__ __forceinline__ long long global_ns() {
     return t;
 }
 
-// Grid-wide barrier of a cooperative launch (all CTAs co-resident).  Every
-// wait is bounded: a CTA that waits longer than wait_ns sets the error word
-// and returns false, and so does every CTA that sees the word set.
-__device__ bool panel_barrier(PanelBar *b, long long wait_ns) {
+// Grid-wide barrier of a cooperative launch (all CTAs co-resident).  The
+// arrival counter only grows within a launch (k_bk_init clears it): the
+// barrier numbered `epoch` (counted by each CTA's thread 0) completes when
+// the counter reaches epoch x gridDim.x, so arriving is one release-add with
+// no reply to wait for and nobody resets anything.  Every wait is bounded: a
+// CTA that waits longer than wait_ns sets the error word and returns false,
+// and so does every CTA that sees the word set.
+__device__ bool panel_barrier(PanelBar *b, unsigned &epoch, long long wait_ns) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned *vgen = &b->gen;
-        volatile int *verr = &b->err;
-        const unsigned gen = *vgen;
+        const unsigned target = ++epoch * gridDim.x;
         __threadfence();
-        if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
-            atomicExch(&b->count, 0u);
-            __threadfence();
-            atomicAdd(&b->gen, 1u);
-        } else {
-            const long long t0 = global_ns();
-            while (*vgen == gen) {
-                if (*verr) break;
-                __nanosleep(64);
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&b->count) : "memory");
+        const long long t0 = global_ns();
+        for (unsigned it = 0;; ++it) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&b->count) : "memory");
+            if ((int)(v - target) >= 0) break;
+            if ((it & 63) == 63) {
+                if (*(volatile int *)&b->err) {
+                    ok = 0;
+                    break;
+                }
                 if (global_ns() - t0 > wait_ns) {
                     atomicExch(&b->err, 1);
+                    ok = 0;
                     break;
                 }
             }
         }
         __threadfence();
-        if (*verr) ok = 0;
+        if (*(volatile int *)&b->err) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
@@ -1121,6 +1128,43 @@ __device__ __forceinline__ double chain_w64(T v, double a) {
     else return v;
 }
 
+// The rule's column test for the panel at k (all threads of every CTA take
+// the same decision from the FP64 pivots s_d and the gathered maxima); CTA 0
+// records a kept panel (kind, inertia, next column) and clears the next
+// panel's maxima.  Returns whether the panel is kept.
+__device__ bool persist_keep(const PersistArgs &a, int k, int nb, int buf, double ztol, const double *s_d) {
+    const double alpha = 0.6403882032022076;   // (1 + sqrt 17) / 8
+    const int tid = threadIdx.x;
+    int keep = 1;
+    if (tid < nb) {
+        const double d = s_d[tid];
+        const unsigned long long cb = __ldcg(&a.cmax[buf * 64 + tid]);
+        const double colmax = __longlong_as_double((long long)cb);
+        const bool diag_ok = absbits64(d) >= absbits64(alpha * colmax);
+        if (!diag_ok || d == 0.0 || fabs(d) <= ztol || !isfinite(d) || !isfinite(colmax)) keep = 0;
+    }
+    keep = __syncthreads_and(keep);
+    if (!keep) return false;
+    if (blockIdx.x == 0) {
+        int pos = 0;
+        if (tid < nb) {
+            a.kind[k + tid] = 1;
+            a.Doff[k + tid] = 0.0;
+            pos = s_d[tid] > 0.0 ? 1 : 0;
+        }
+        if (tid < 64) a.cmax[(buf ^ 1) * 64 + tid] = 0ULL;   // the next panel's maxima start at zero
+        const int np = __syncthreads_count(pos);
+        if (tid == 0) {
+            a.st->npos += np;
+            a.st->nneg += nb - np;
+            a.st->k = k + nb;
+            a.st->kb = nb;
+            a.st->nacc += 1;
+        }
+    }
+    return true;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist(PersistArgs a) {
     extern __shared__ __align__(16) unsigned char psm[];
@@ -1129,11 +1173,10 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist(PersistArgs a) {
     __shared__ double s_d[64], s_rd[64];    // FP64 pivots and their reciprocals
     __shared__ T s_rc[64];                  // the chain's reciprocals
     __shared__ unsigned long long s_cmax[64];
-    __shared__ int s_keep;
     const int N = a.N, G = (int)gridDim.x, g = (int)blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31;
-    const double alpha = 0.6403882032022076;   // (1 + sqrt 17) / 8
     const double ztol = a.zero_tol * __ldg(a.maxabs);
+    unsigned epoch = 0;   // grid barriers passed (thread 0)
     int p = 0;
     for (int k = a.st->k; k < N; k += 64, ++p) {
         const int nb = min(64, N - k);
@@ -1324,45 +1367,15 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist(PersistArgs a) {
         }
         __syncthreads();
         if (tid < 64 && s_cmax[tid]) atomicMax(&a.cmax[buf * 64 + tid], s_cmax[tid]);
-        if (!panel_barrier(a.bar, a.wait_ns)) return;
+        if (!panel_barrier(a.bar, epoch, a.wait_ns)) return;
         // ---------------- B: the rule's column test, the same in every CTA
-        {
-            int keep = 1;
-            if (tid < nb) {
-                const double d = s_d[tid];
-                const unsigned long long cb = __ldcg(&a.cmax[buf * 64 + tid]);
-                const double colmax = __longlong_as_double((long long)cb);
-                const bool diag_ok = absbits64(d) >= absbits64(alpha * colmax);
-                if (!diag_ok || d == 0.0 || fabs(d) <= ztol || !isfinite(d) || !isfinite(colmax)) keep = 0;
-            }
-            keep = __syncthreads_and(keep);
-            if (tid == 0) s_keep = keep;
-        }
-        __syncthreads();
-        if (!s_keep) {
+        if (!persist_keep(a, k, nb, buf, ztol, s_d)) {
             if (g == 0 && tid == 0) {   // the panel loop takes over at column k
                 a.st->k = k;
                 a.st->kb = 0;
                 a.st->spec = 0;
             }
             return;
-        }
-        if (g == 0) {
-            int pos = 0;
-            if (tid < nb) {
-                a.kind[k + tid] = 1;
-                a.Doff[k + tid] = 0.0;
-                pos = s_d[tid] > 0.0 ? 1 : 0;
-            }
-            if (tid < 64) a.cmax[(buf ^ 1) * 64 + tid] = 0ULL;   // the next panel's maxima start at zero
-            const int np = __syncthreads_count(pos);
-            if (tid == 0) {
-                a.st->npos += np;
-                a.st->nneg += nb - np;
-                a.st->k = k + nb;
-                a.st->kb = nb;
-                a.st->nacc += 1;
-            }
         }
         if (k + nb >= N) break;
         // ---------------- C: trailing update
@@ -1376,7 +1389,395 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist(PersistArgs a) {
             }
         }
         __threadfence();
-        if (!panel_barrier(a.bar, a.wait_ns)) return;
+        if (!panel_barrier(a.bar, epoch, a.wait_ns)) return;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent no-interchange factorization, FP32-update form (the refined
+// mixed-precision path).  The same panel sequence, column test and hand-over
+// as k_bk_persist, with the arithmetic of the loop in FP32 only:
+//   - the prologue copies the lower triangle of S into Af (FP32, ld N); the
+//     trailing updates run on Af in place, and the FP64 matrix keeps S;
+//   - each 64-column panel is factored in two 32-column sub-panels.  A warp
+//     holds the sub-panel's 32 diagonal-block rows (lane = row) and 32 rows
+//     below them (lane = row) in registers and runs the 32-step pivot chain
+//     with warp shuffles; every warp repeats the short diagonal chain for its
+//     own rows, so no barrier is needed per column.  A rank-32 update
+//     (2 x 4 outputs per thread, from shared memory) brings the second
+//     sub-panel's columns up to date;
+//   - the FP64 pivot is the chain's FP32 value plus the part of S's diagonal
+//     that the FP32 copy dropped; L (FP64 copy), W and the column maxima come
+//     from the FP32 chain values.
+// On a rejected panel every CTA writes the FP32 updates of the trailing
+// matrix back into the FP64 matrix (A += Af - fl32(A)) before the pivoting
+// panels take over.
+// ---------------------------------------------------------------------------
+// Sub-panel width Q (16 or 32): a warp holds the Q diagonal-block rows of a
+// sub-panel and 32 rows below them.  Own rows staged per pass: what the warps
+// left after the block's target groups take (at most 8 groups in all).
+constexpr int kPersistQ = 16;   // sub-panel width of the FP32-update kernel
+template <int Q> constexpr int own_rows() { return (8 - (64 - Q + 31) / 32) * 32; }
+constexpr int kRowsBuf = 64 + own_rows<32>();   // the larger of the two (224 own rows)
+
+// Pivot chain of one Q-column sub-panel in one warp.  vA: the sub-block's row
+// `lane` (lanes >= Q hold zeros), vB: one row below it (zeros where a lane
+// has no row).  With `factored`, vA holds the factored sub-block (its W
+// values) and rcl the reciprocal pivot of column `lane`: vA is only read.  On
+// return vB holds the row's W values (L = W / d); the result is the
+// reciprocal pivot of column `lane`.
+template <int Q>
+__device__ __forceinline__ float chain_q(float (&vA)[Q], float (&vB)[Q], bool factored, float rcl, int cw,
+                                         int lane) {
+    float rc = 0.0f;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        float rj;
+        if (factored) {
+            rj = __shfl_sync(0xffffffffu, rcl, j);
+        } else {
+            const float dj = __shfl_sync(0xffffffffu, vA[j], j);
+            rj = (j < cw && dj != 0.0f) ? __frcp_rn(dj) : 0.0f;
+        }
+        // zero multipliers, not conditional updates: v stays in registers
+        const float lA = (!factored && lane > j) ? vA[j] * rj : 0.0f;
+        const float lB = vB[j] * rj;
+#pragma unroll
+        for (int t = j + 1; t < Q; ++t) {
+            const float w = __shfl_sync(0xffffffffu, vA[j], t);
+            vA[t] = fmaf(-lA, w, vA[t]);
+            vB[t] = fmaf(-lB, w, vB[t]);
+        }
+        rc = lane == j ? rj : rc;
+    }
+    return rc;
+}
+
+// One sub-panel (columns c0 .. c0 + cw - 1 of the staged rows Rb, pitch kPP):
+// the targets are the block rows c0 + Q .. nb - 1 (when `blk`) and the nr
+// staged own rows (Rb rows 64 ..).  Each warp takes one group of 32 targets;
+// warp 0 also keeps the factored sub-block and writes it back, with its
+// reciprocal pivots, after every warp has read it.
+template <int Q>
+__device__ void persist_subpanel(float *Rb, float *s_rc, int c0, int cw, int nb, bool blk, int nr,
+                                 bool factored) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int gb = blk ? max(0, nb - c0 - Q + 31) / 32 : 0;   // groups of block rows
+    const int ng = gb + (nr + 31) / 32;                       // <= 8 by the staging size
+    float vA[Q], vB[Q];
+    float rc = 0.0f;
+    if (wid < ng || wid == 0) {
+        int row = -1;
+        if (wid < gb) {
+            const int r = c0 + Q + 32 * wid + lane;
+            if (r < nb) row = r;
+        } else if (wid < ng) {
+            const int r = 32 * (wid - gb) + lane;
+            if (r < nr) row = 64 + r;
+        }
+#pragma unroll
+        for (int t = 0; t < Q; ++t) {
+            vA[t] = (lane < cw && t <= lane) ? Rb[(c0 + lane) * kPP + c0 + t] : 0.0f;
+            vB[t] = (row >= 0 && t < cw) ? Rb[row * kPP + c0 + t] : 0.0f;
+        }
+        const float rcl = (factored && lane < Q) ? s_rc[c0 + lane] : 0.0f;
+        rc = chain_q<Q>(vA, vB, factored, rcl, cw, lane);
+        if (row >= 0) {
+#pragma unroll
+            for (int t = 0; t < Q; ++t)
+                if (t < cw) Rb[row * kPP + c0 + t] = vB[t];
+        }
+    }
+    __syncthreads();   // every warp has read the sub-block
+    if (wid == 0 && !factored) {
+#pragma unroll
+        for (int t = 0; t < Q; ++t)
+            if (lane < cw && t <= lane) Rb[(c0 + lane) * kPP + c0 + t] = vA[t];
+        if (lane < cw) s_rc[c0 + lane] = rc;
+    }
+    __syncthreads();
+}
+
+// Rank-Q update of columns c0 + Q .. nb - 1 with the sub-panel at c0: block
+// rows c0 + Q .. nb - 1 (lower triangle, when `blk`) and the nr staged own
+// rows.  2 rows x 4 columns per thread.
+template <int Q>
+__device__ void persist_rank_q(float *Rb, const float *s_rc, int c0, int nb, bool blk, int nr) {
+    const int m0 = c0 + Q;                    // first row / column updated
+    const int ncq = (64 - m0) / 4;            // column quads
+    const int nbp = blk ? (64 - m0) / 2 : 0;  // row pairs of the block
+    const int items = (nbp + (nr + 1) / 2) * ncq;
+    for (int it = threadIdx.x; it < items; it += kPThreads) {
+        const int rp = it / ncq, cq = it - rp * ncq;
+        const int r0 = rp < nbp ? m0 + 2 * rp : 64 + 2 * (rp - nbp);
+        const int col0 = m0 + 4 * cq;
+        if (col0 >= nb || (rp < nbp && (r0 + 1 < col0 || r0 >= nb))) continue;   // nothing of it is kept
+        float acc[2][4];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const float rcj = s_rc[c0 + j];
+            const float l0 = Rb[r0 * kPP + c0 + j] * rcj, l1 = Rb[(r0 + 1) * kPP + c0 + j] * rcj;
+            float w[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) w[v] = Rb[(col0 + v) * kPP + c0 + j];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                acc[0][v] = fmaf(l0, w[v], acc[0][v]);
+                acc[1][v] = fmaf(l1, w[v], acc[1][v]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int r = r0 + u;
+            const bool live = rp < nbp ? r < nb : r - 64 < nr;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int c = col0 + v;
+                if (live && c < nb && (rp >= nbp || c <= r)) Rb[r * kPP + c] -= acc[u][v];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// One 64 x 64 tile of the trailing lower triangle on the FP32 copy:
+// Af(i, c) -= sum_t Lf(i, t) Wf(c, t), i >= c >= k0 + kb (tile numbering as
+// trailing_tile).  smem: 2 x 64 x 64 floats.
+__device__ void trailing_tile_f32(int tile, int N, int kb, int k0, float *__restrict__ Af,
+                                  const float *__restrict__ Lf, const float *__restrict__ Wf,
+                                  unsigned char *usmem) {
+    float *Lt = reinterpret_cast<float *>(usmem);   // [64][64]: Lt[t][r]
+    float *Wt = Lt + 64 * kUT;                      // [64][64]: Wt[t][c]
+    const int base = k0 + kb;
+    if (base >= N || kb <= 0) return;
+    int tr = (int)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
+    while ((tr + 1) * (tr + 2) / 2 <= tile) ++tr;
+    while (tr * (tr + 1) / 2 > tile) --tr;
+    const int tc = tile - tr * (tr + 1) / 2;
+    const int i0 = base + tr * kUT, c0 = base + tc * kUT;
+    if (i0 >= N) return;
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    // this thread's 16 entries of the tile, loaded ahead of the products
+    float cur[4][4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int c = c0 + 4 * ty + v;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + 4 * tx + u;
+            cur[u][v] = (i < N && c < N && i >= c) ? Af[i + (int64_t)c * N] : 0.0f;
+        }
+    }
+    {
+        const int r = tid & (kUT - 1), t0 = tid >> 6;
+        const int i = i0 + r, c = c0 + r;
+        float lv[16], wv[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int t = t0 + 4 * j;
+            lv[j] = (t < kb && i < N) ? Lf[i + (int64_t)t * N] : 0.0f;
+            wv[j] = (t < kb && c < N) ? Wf[c + (int64_t)t * N] : 0.0f;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int t = t0 + 4 * j;
+            Lt[t * kUT + r] = lv[j];
+            Wt[t * kUT + r] = wv[j];
+        }
+    }
+    __syncthreads();
+    float acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+    for (int t = 0; t < kb; ++t) {
+        float lv[4], wv[4];
+        load4(Lt + t * kUT + 4 * tx, lv);
+        load4(Wt + t * kUT + 4 * ty, wv);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(lv[u], wv[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int c = c0 + 4 * ty + v;
+        if (c >= N) continue;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + 4 * tx + u;
+            if (i < N && i >= c) Af[i + (int64_t)c * N] = cur[u][v] - acc[u][v];
+        }
+    }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kPThreads, 1) k_bk_persist32(PersistArgs a) {
+    constexpr int kOwn = own_rows<Q>();
+    extern __shared__ __align__(16) unsigned char psm[];
+    float *Rb = reinterpret_cast<float *>(psm);   // [kRowsBuf][kPP]: block rows 0..63, then own rows
+    __shared__ double s_d[64];
+    __shared__ float s_rc[64];
+    __shared__ unsigned long long s_cmax[64];
+    const int N = a.N, G = (int)gridDim.x, g = (int)blockIdx.x, tid = threadIdx.x;
+    const int lane = tid & 31, wid = tid >> 5;
+    constexpr int kWarps = kPThreads / 32;
+    const double ztol = a.zero_tol * __ldg(a.maxabs);
+    const int kstart = a.st->k;
+    unsigned epoch = 0;   // grid barriers passed (thread 0)
+    // prologue: the FP32 copy of columns kstart .. N - 1 (whole columns: the
+    // entries above the diagonal are copied too and never read), eight
+    // 16-byte loads in flight per thread
+    {
+        const int64_t e0 = (int64_t)kstart * N, total = (int64_t)N * N;
+        const int64_t stride = (int64_t)G * kPThreads;
+        const int64_t first = (int64_t)g * kPThreads + tid;
+        if (((reinterpret_cast<uintptr_t>(a.A) | reinterpret_cast<uintptr_t>(a.Af)) & 15) == 0 && (e0 & 1) == 0) {
+            const double2 *src = reinterpret_cast<const double2 *>(a.A + e0);
+            float2 *dst = reinterpret_cast<float2 *>(a.Af + e0);
+            const int64_t n2 = (total - e0) / 2;
+            for (int64_t e = first; e < n2; e += 8 * stride) {
+                double2 x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (e + u * stride < n2) x[u] = __ldcs(src + e + u * stride);
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (e + u * stride < n2) dst[e + u * stride] = make_float2((float)x[u].x, (float)x[u].y);
+            }
+            if (g == 0 && tid == 0 && ((total - e0) & 1)) a.Af[total - 1] = (float)a.A[total - 1];
+        } else {
+            for (int64_t e = e0 + first; e < total; e += stride) a.Af[e] = (float)a.A[e];
+        }
+    }
+    __threadfence();
+    if (!panel_barrier(a.bar, epoch, a.wait_ns)) return;
+    int p = 0;
+    for (int k = kstart; k < N; k += 64, ++p) {
+        const int nb = min(64, N - k);
+        const int buf = p & 1;
+        if (tid < 64) {
+            s_cmax[tid] = 0ULL;
+            s_rc[tid] = 0.0f;
+        }
+        // S's diagonal of the block (for the FP64 pivots), loaded ahead of the chains
+        const double adiag = tid < nb ? a.A[(int64_t)(k + tid) * (N + 1)] : 0.0;
+        const int brow = N - k - nb;
+        const int R = (brow + G - 1) / G;
+        const int r_begin = k + nb + g * R, r_end = min(N, r_begin + R);
+        for (int cb = r_begin, pass = 0; pass == 0 || cb < r_end; cb += kOwn, ++pass) {
+            const int nr = max(0, min(kOwn, r_end - cb));
+            const bool blk = pass == 0;   // the diagonal block is factored in the first pass
+            // ---- stage: warp w takes columns w, w + 8, ..; lanes over rows
+            // (block rows c..nb-1 of column c on the first pass, then own rows)
+            __syncthreads();
+#pragma unroll
+            for (int cc = 0; cc < 64 / kWarps; ++cc) {
+                const int c = wid + kWarps * cc;
+                constexpr int kR = (64 + kOwn + 31) / 32;
+                float v[kR];
+#pragma unroll
+                for (int q = 0; q < kR; ++q) {
+                    const int rr = lane + 32 * q;
+                    v[q] = 0.0f;
+                    if (c < nb) {
+                        if (rr < 64) {
+                            if (blk && rr < nb && rr >= c) v[q] = a.Af[(int64_t)(k + rr) + (int64_t)(k + c) * N];
+                        } else if (rr - 64 < nr) {
+                            v[q] = a.Af[(int64_t)(cb + rr - 64) + (int64_t)(k + c) * N];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kR; ++q) {
+                    const int rr = lane + 32 * q;
+                    if ((rr < 64 && blk) || (rr >= 64 && rr - 64 < nr)) Rb[rr * kPP + c] = v[q];
+                }
+            }
+            __syncthreads();
+            // ---- the sub-panels, each followed by the update of the columns after it
+            for (int c0 = 0; c0 < nb; c0 += Q) {
+                persist_subpanel<Q>(Rb, s_rc, c0, min(Q, nb - c0), nb, blk, nr, !blk);
+                if (c0 + Q < nb) persist_rank_q<Q>(Rb, s_rc, c0, nb, blk, nr);
+            }
+            if (blk) {
+                // FP64 pivots, then the block's L and D and the column maxima of
+                // its rows: column c by CTA c mod G, one warp per column
+                if (tid < 64) {
+                    double d = 0.0;
+                    if (tid < nb) d = chain_w64<float>(Rb[tid * kPP + tid], adiag);
+                    s_d[tid] = d;
+                }
+                __syncthreads();
+                for (int c = g + G * wid; c < nb; c += G * kWarps) {
+                    unsigned bm = 0u;
+                    for (int r = c + lane; r < nb; r += 32) {
+                        const int64_t o = (int64_t)(k + r) + (int64_t)(k + c) * N;
+                        if (r == c) {
+                            a.L[o] = 1.0;
+                            a.Dd[k + c] = s_d[c];
+                        } else {
+                            const float w = Rb[r * kPP + c];
+                            a.L[o] = (double)(w * s_rc[c]);
+                            bm = max(bm, __float_as_uint(w) & 0x7fffffffu);
+                        }
+                    }
+                    bm = __reduce_max_sync(0xffffffffu, bm);
+                    if (lane == 0 && bm) atomicMax(&s_cmax[c], absbits64((double)__uint_as_float(bm)));
+                }
+            }
+            // own rows: L (FP64 copy), the FP32 L and W columns, column maxima
+            for (int c = wid; c < nb; c += kWarps) {
+                unsigned bm = 0u;
+                for (int r = lane; r < nr; r += 32) {
+                    const int i = cb + r;
+                    const float w = Rb[(64 + r) * kPP + c], l = w * s_rc[c];
+                    a.L[(int64_t)i + (int64_t)(k + c) * N] = (double)l;
+                    a.Lf[(int64_t)i + (int64_t)c * N] = l;
+                    a.Wf[(int64_t)i + (int64_t)c * N] = w;
+                    bm = max(bm, __float_as_uint(w) & 0x7fffffffu);
+                }
+                bm = __reduce_max_sync(0xffffffffu, bm);
+                if (lane == 0 && bm) atomicMax(&s_cmax[c], absbits64((double)__uint_as_float(bm)));
+            }
+        }
+        __syncthreads();
+        if (tid < 64 && s_cmax[tid]) atomicMax(&a.cmax[buf * 64 + tid], s_cmax[tid]);
+        if (!panel_barrier(a.bar, epoch, a.wait_ns)) return;
+        if (!persist_keep(a, k, nb, buf, ztol, s_d)) {
+            // hand over at column k: the FP64 matrix takes the FP32 updates
+            for (int c = k + g; c < N; c += G)
+                for (int i = c + tid; i < N; i += kPThreads) {
+                    const int64_t o = i + (int64_t)c * N;
+                    const double s0 = a.A[o];
+                    a.A[o] = s0 + ((double)a.Af[o] - (double)(float)s0);
+                }
+            if (g == 0 && tid == 0) {
+                a.st->k = k;
+                a.st->kb = 0;
+                a.st->spec = 0;
+            }
+            return;
+        }
+        if (k + nb >= N) break;
+        // ---------------- trailing update on the FP32 copy
+        {
+            const int base = k + nb;
+            const int nt = (N - base + kUT - 1) / kUT;
+            const int tiles = nt * (nt + 1) / 2;
+            for (int t = g; t < tiles; t += G) {
+                trailing_tile_f32(t, N, nb, k, a.Af, a.Lf, a.Wf, psm);
+                __syncthreads();
+            }
+        }
+        __threadfence();
+        if (!panel_barrier(a.bar, epoch, a.wait_ns)) return;
     }
 }
 
@@ -1385,7 +1786,6 @@ __global__ void k_bk_init(int N, int32_t *perm, PanelState *st, unsigned long lo
     if (blockIdx.x == 0 && threadIdx.x < 128) cmax[threadIdx.x] = 0ULL;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         bar->count = 0u;
-        bar->gen = 0u;
         bar->err = 0;
         st->k = 0;
         st->kb = 0;
@@ -1509,7 +1909,7 @@ void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t sm
 // (2 x 64), the pending row tests (64) and their partial row maxima
 // ((ceil(N / 32) + 2) x 64)
 struct BlockedScratch {
-    size_t wg, st, lf, wf, cmax, fail, rowpart, total;
+    size_t wg, st, lf, wf, cmax, fail, rowpart, af, total;
 };
 
 BlockedScratch blocked_scratch(int64_t N) {
@@ -1523,7 +1923,8 @@ BlockedScratch blocked_scratch(int64_t N) {
     l.cmax = l.wf + up(n * 65 * sizeof(float));
     l.fail = l.cmax + up(128 * sizeof(unsigned long long));
     l.rowpart = l.fail + up(64 * sizeof(RowTest));
-    l.total = l.rowpart + up(((n + 31) / 32 + 2) * 64 * sizeof(unsigned long long));
+    l.af = l.rowpart + up(((n + 31) / 32 + 2) * 64 * sizeof(unsigned long long));
+    l.total = l.af + up(n * n * sizeof(float));   // the FP32 copy of the persistent FP32-update kernel
     return l;
 }
 
@@ -1536,7 +1937,15 @@ PanelBar *grid_bar(char *w, const BlockedScratch &lay) { return reinterpret_cast
 // rows of a trailing-update tile
 template <typename T>
 size_t persist_smem() {
+    if constexpr (sizeof(T) == sizeof(float))   // k_bk_persist32: staged rows, or a trailing tile's panel rows
+        return std::max((size_t)kRowsBuf * kPP * sizeof(float), 2 * (size_t)64 * kUT * sizeof(float));
     return std::max(2 * (size_t)64 * kPP * sizeof(T), 2 * (size_t)65 * kUT * sizeof(T));
+}
+
+template <typename T>
+const void *persist_kernel() {
+    if constexpr (sizeof(T) == sizeof(float)) return (const void *)k_bk_persist32<kPersistQ>;
+    else return (const void *)k_bk_persist<double>;
 }
 
 // Run k_bk_persist from column 0; returns the column where it stopped (N: all
@@ -1546,11 +1955,11 @@ template <typename T>
 int run_persistent(cudaStream_t s, int num_sms, int N, const PersistArgs &pa, PanelState *st, PanelBar *bar) {
     static PerDeviceOnce once;
     MDSIP_CUDA(once.run([] {
-        return cudaFuncSetAttribute(k_bk_persist<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        return cudaFuncSetAttribute(persist_kernel<T>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)persist_smem<T>());
     }));
     int per_sm = 0;
-    MDSIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bk_persist<T>, kPThreads,
+    MDSIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persist_kernel<T>(), kPThreads,
                                                              persist_smem<T>()));
     MDSIP_REQUIRE(per_sm >= 1, MDSIP_ERR_CUDA, "ldlt: persistent factorization does not fit an SM");
     // about three trailing tiles per CTA after the first panel, at most one CTA per SM
@@ -1559,7 +1968,7 @@ int run_persistent(cudaStream_t s, int num_sms, int N, const PersistArgs &pa, Pa
     const int G = (int)std::min<int64_t>(want, (int64_t)num_sms);
     PersistArgs args = pa;
     void *kargs[] = {&args};
-    MDSIP_CUDA(cudaLaunchCooperativeKernel((const void *)k_bk_persist<T>, dim3(G), dim3(kPThreads), kargs,
+    MDSIP_CUDA(cudaLaunchCooperativeKernel(persist_kernel<T>(), dim3(G), dim3(kPThreads), kargs,
                                            persist_smem<T>(), s));
     count_launch();
     thread_local int *h = nullptr;
@@ -1636,6 +2045,7 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
         pa.bar = bar;
         pa.maxabs = maxabs_dev;
         pa.zero_tol = zero_tol;
+        pa.Af = reinterpret_cast<float *>(w + lay.af);
         pa.wait_ns = 20LL * 1000 * 1000 * 1000;   // 20 s: far above the longest phase (FP64 update at N ~ 44000)
         k0 = fp32_update ? run_persistent<float>(s, num_sms, (int)N, pa, st, bar)
                          : run_persistent<double>(s, num_sms, (int)N, pa, st, bar);

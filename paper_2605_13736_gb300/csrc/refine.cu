@@ -225,7 +225,7 @@ void Refiner::approx_solve(const double *b, double *sol) {
     k_rhs_S<<<grid_for(std::max(D.n_d, D.m_I)), 256, 0, st>>>(D, b, tmp_nd, rhsS);
     MDSIP_LAUNCHED();
     launch_ldlt_solve_coop(st, num_sms, N, Dd, Doff, perm, 1, rhsS, N, solve_ws, solve_err, solve_fp32);
-    if (Ahi) launch_gemv_rows_df(st, Ahi, Alo, D.m_E, D.n_d, D.lda, rhsS, split, tmp_m);
+    if (Ahi) launch_gemv_rows_f32(st, Ahi, D.m_E, D.n_d, D.lda, rhsS, tmp_m);
     else launch_gemv_rows(st, M.A, D.m_E, D.n_d, D.lda, rhsS, tmp_m);
     k_sol_gdh<<<grid_for(std::max(D.m_E, D.n_d)), 256, 0, st>>>(D, tmp_m, bt_g, w, rhsS, sol);
     MDSIP_LAUNCHED();
@@ -234,6 +234,7 @@ void Refiner::approx_solve(const double *b, double *sol) {
 }
 
 void Refiner::track_Au(bool init) {
+    if (Ahi) return;   // the residual forms A u_d itself
     if (init) {
         MDSIP_CUDA(cudaMemcpyAsync(Au_run, tmp_m, D.m_E * sizeof(double), cudaMemcpyDeviceToDevice, st));
     } else {
@@ -242,12 +243,18 @@ void Refiner::track_Au(bool init) {
 }
 
 void Refiner::residual(const double *b, const double *u, double dw, double dc, double *r, double *out4) {
-    if (Ahi) launch_gemv_t_df(st, Ahi, Alo, D.m_E, D.n_d, D.lda, u + D.n, split, colpart, tmp_nd);   // A^T u_g
-    else launch_gemv_t(st, M.A, D.m_E, D.n_d, D.lda, u + D.n, colpart, tmp_nd);
+    const double *Au = Au_run;
+    if (Ahi) {   // A u_d and A^T u_g from one double-float pass
+        launch_gemv_both_df(st, Ahi, Alo, D.m_E, D.n_d, D.lda, u + D.n_s, u + D.n, split, split + D.n_d, colpart,
+                            tmp_m, tmp_nd);
+        Au = tmp_m;
+    } else {
+        launch_gemv_t(st, M.A, D.m_E, D.n_d, D.lda, u + D.n, colpart, tmp_nd);   // A^T u_g
+    }
     k_hdd_gemv<<<std::max(1, std::min(4096, ceil_div((D.n_d + D.m_I) * 32, 256))), 256, 0, st>>>(
         D.n_d, D.m_I, Hdd, Jdh, u + D.n_s, tmp_nd2);
     MDSIP_LAUNCHED();
-    k_residual<<<kRedBlocks, NT, 0, st>>>(D, M, b, u, q, sig_xd, sig_d, Jdh, Au_run, tmp_nd, tmp_nd2, dw, dc,
+    k_residual<<<kRedBlocks, NT, 0, st>>>(D, M, b, u, q, sig_xd, sig_d, Jdh, Au, tmp_nd, tmp_nd2, dw, dc,
                                           r, partial);
     MDSIP_LAUNCHED();
     launch_finalize_max(st, partial, 4, out4);

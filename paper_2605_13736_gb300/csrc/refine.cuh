@@ -26,18 +26,21 @@ struct Refiner {
     // scratch: bt_g, tmp_m (m_E), tmp_nd (n_d), tmp_nd2 (n_d + m_I), rhsS (N), colpart, partial
     double *bt_g, *tmp_m, *tmp_nd, *tmp_nd2, *rhsS, *colpart, *partial;
     double *Au_run;   // A u_d of the current solution, kept as a running sum (m_E)
-    // A as an FP32 pair for the passes in double-float arithmetic (null: FP64 passes)
+    // A as an FP32 pair (null: FP64 passes).  With it the approximate solves
+    // take FP32 products with A_hi and the residual takes A u_d and A^T u_g
+    // from one double-float pass over (A_hi, A_lo)
     const float *Ahi, *Alo;
-    float2 *split;    // max(m_E, n_d) float2
+    float2 *split;    // m_E + n_d float2
 
     // b = right-hand side of Eq. (linsys4x4), packed [s | d | g | h]
     void rhs(const IterView &I, const double *gl, const double *cg, const double *ch, const double *sig_d,
              double mu, double dw, double *b);
     // sol = S~^-1-based solve of K sol = b (two-stage elimination with the factor)
     void approx_solve(const double *b, double *sol);
-    // after approx_solve: Au_run = A sol_d (init) or Au_run += A sol_d
+    // after approx_solve: Au_run = A sol_d (init) or Au_run += A sol_d (FP64 passes only)
     void track_Au(bool init);
-    // r = b - K u in FP64 (A u_d taken from Au_run); out4 = (||r||inf, ||b||inf, ||K u||inf, ||u||inf)
+    // r = b - K u in FP64 (A u_d from Au_run, or from the double-float pass);
+    // out4 = (||r||inf, ||b||inf, ||K u||inf, ||u||inf)
     void residual(const double *b, const double *u, double dw, double dc, double *r, double *out4);
     void axpy(int64_t n, const double *x, double *y);
     // full direction (incl. dd and the bound-multiplier steps) from the packed solution

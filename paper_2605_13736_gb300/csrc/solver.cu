@@ -604,7 +604,7 @@ static void prepare_tc(Problem *P) {
     if (!P->df_ready && D.m_E > 0 && D.n_d > 0) {   // A as an FP32 pair (once: A follows the Jacobian)
         P->bAhi.get<float>(ctx, (size_t)D.m_E * D.lda);
         P->bAlo.get<float>(ctx, (size_t)D.m_E * D.lda);
-        P->bsplit.get<float2>(ctx, (size_t)std::max(D.m_E, D.n_d));
+        P->bsplit.get<float2>(ctx, (size_t)(D.m_E + D.n_d));
         launch_split_matrix(ctx->stream, P->Mv.A, D.m_E, D.n_d, D.lda, P->bAhi.as<float>(), P->bAlo.as<float>());
         P->df_ready = true;
     }
@@ -1810,6 +1810,34 @@ mdsip_status mdsip_syrk_scaled_tc(mdsip_ctx *hctx, int64_t m, int64_t n, const d
         MDSIP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
         MDSIP_CUDA(cudaStreamSynchronize(ctx->stream));
         MDSIP_REQUIRE(herr == 0, MDSIP_ERR_DEVICE, "syrk_tc: a bounded device wait expired");
+    });
+}
+
+mdsip_status mdsip_gemv_pair_df(mdsip_ctx *hctx, int64_t m, int64_t n, const double *A, int64_t lda,
+                                const double *x, const double *v, double *Ax, double *ATv) {
+    if (!hctx) return MDSIP_ERR_INVALID_ARG;
+    Ctx *ctx = C_(hctx);
+    return guarded(ctx, [&] {
+        DeviceGuard g(ctx->device);
+        MDSIP_REQUIRE(m >= 0 && n >= 0 && lda >= n && lda % 4 == 0 && m <= (1 << 20) && n <= (1 << 20),
+                      MDSIP_ERR_INVALID_ARG, "gemv_pair_df: bad sizes");
+        if (m == 0 && n == 0) return;
+        MDSIP_REQUIRE((m == 0 || Ax) && (n == 0 || ATv), MDSIP_ERR_INVALID_ARG, "gemv_pair_df: null output");
+        if (m > 0 && n > 0)
+            MDSIP_REQUIRE(A && x && v && (reinterpret_cast<uintptr_t>(A) & 15) == 0, MDSIP_ERR_INVALID_ARG,
+                          "gemv_pair_df: null or misaligned input");
+        auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+        const size_t nA = (size_t)m * (size_t)lda;
+        const size_t o_lo = up(nA * sizeof(float)), o_xs = o_lo + up(nA * sizeof(float));
+        const size_t o_ys = o_xs + up((size_t)n * sizeof(float2)), o_part = o_ys + up((size_t)m * sizeof(float2));
+        const size_t total = o_part + up((size_t)kRedBlocks * (size_t)n * sizeof(double));
+        char *base = static_cast<char *>(ctx->scratch_at_least(total));
+        float *hi = reinterpret_cast<float *>(base), *lo = reinterpret_cast<float *>(base + o_lo);
+        if (m > 0 && n > 0) launch_split_matrix(ctx->stream, A, m, n, lda, hi, lo);
+        launch_gemv_both_df(ctx->stream, hi, lo, m, n, lda, x, v, reinterpret_cast<float2 *>(base + o_xs),
+                            reinterpret_cast<float2 *>(base + o_ys), reinterpret_cast<double *>(base + o_part), Ax,
+                            ATv);
+        MDSIP_CUDA(cudaStreamSynchronize(ctx->stream));
     });
 }
 

@@ -55,6 +55,66 @@ def test_two_rank_aggregation():
     assert total / t_max == 7.5
 
 
+def _batch_rank_main(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank),
+                      MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import numpy as np
+    import bench
+    r, w, _ = bench.dist_env()
+    bench.dist_init(w, "gloo")
+    sizes = np.random.default_rng(7).integers(64, 1025, size=256)   # the batched workload's sizes
+    parts = bench.partition_instances([float(nd) ** 3 for nd in sizes], w)
+    mine = parts[r]
+    # stand-in per-rank results: time proportional to the rank's load, one
+    # failed solve on rank 1, a worst KKT error per rank
+    local = {"t_seq": None, "t_bat": sum(float(sizes[i]) ** 3 for i in mine) / 1e9, "n": len(mine),
+             "n_ok": len(mine) - (1 if r == 1 else 0), "iters": 15 * len(mine), "max_E0": 1e-9 * (r + 1)}
+    agg = bench.batch_aggregate(local, w)
+    bench.barrier(w)
+    import torch.distributed as dist
+    dist.destroy_process_group()
+    q.put((r, mine, local["t_bat"], agg))
+
+
+def test_batch_partition_over_two_ranks():
+    """The batched workload split over two gloo ranks: each instance solved on
+    exactly one rank, the loads balanced, and the whole-job figures (max time,
+    summed counts, max error) the same on both ranks."""
+    mp = pytest.importorskip("torch.multiprocessing")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_batch_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted((q.get(timeout=120) for _ in procs), key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (r0, mine0, t0, agg0), (r1, mine1, t1, agg1) = out
+    assert sorted(mine0 + mine1) == list(range(256)) and not set(mine0) & set(mine1)
+    assert agg0 == agg1
+    assert agg0["t_bat"] == max(t0, t1) and agg0["n"] == 256 and agg0["n_ok"] == 255
+    assert agg0["iters"] == 15 * 256 and agg0["max_E0"] == 2e-9 and agg0["t_seq"] is None
+
+
+def test_partition_is_balanced_and_complete():
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    rng = np.random.default_rng(3)
+    for world in (1, 2, 3, 4, 8):
+        costs = [float(c) for c in rng.integers(1, 1000, size=97) ** 3]
+        parts = bench.partition_instances(costs, world)
+        assert len(parts) == world
+        assert sorted(i for p in parts for i in p) == list(range(97))
+        loads = [sum(costs[i] for i in p) for p in parts]
+        assert max(loads) - min(loads) <= max(costs)        # the greedy bound
+        assert parts == bench.partition_instances(costs, world)   # deterministic
+    assert bench.partition_instances([5.0, 1.0, 1.0, 1.0], 2) == [[0], [1, 2, 3]]
+
+
 def test_single_rank_is_identity():
     sys.path.insert(0, ROOT)
     import bench

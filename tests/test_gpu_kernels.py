@@ -283,6 +283,50 @@ def test_ldlt_fp32_speculation_large(ctx, N):
     assert g["resid"] <= 1e-5
 
 
+@pytest.mark.parametrize("mrows,n", [(1, 1), (5, 3), (1000, 2000), (3001, 2500), (700, 4100), (20011, 64)])
+def test_gemv_pair_df_within_bound(ctx, mrows, n):
+    """A x and A^T v from the double-float pass against the exact products
+    (FP64 products summed exactly by math.fsum: their own error is below
+    2^-53 of the sum of |terms|), element by element, with entries spread over
+    2^-20 .. 2^20 so that the low halves of A and x matter."""
+    import math
+    torch = torch_cuda()
+    rng = np.random.default_rng(mrows * 7 + n)
+    A = rng.standard_normal((mrows, n)) * np.exp2(rng.integers(-20, 21, (mrows, n)))
+    x = rng.standard_normal(n) * np.exp2(rng.integers(-20, 21, n))
+    v = rng.standard_normal(mrows) * np.exp2(rng.integers(-20, 21, mrows))
+    lda = (n + 3) // 4 * 4
+    Ap = np.zeros((mrows, lda))
+    Ap[:, :n] = A
+    Ax, ATv = dev(np.full(mrows, np.nan)), dev(np.full(n, np.nan))
+    m.mdsip_gemv_pair_df(ctx, mrows, n, dev(Ap), lda, dev(x), dev(v), Ax, ATv)
+    torch.cuda.synchronize()
+    Ax, ATv = Ax.cpu().numpy(), ATv.cpu().numpy()
+    P, Q = A * x[None, :], A * v[:, None]
+    ex_r = np.array([math.fsum(P[i]) for i in range(mrows)])
+    ex_c = np.array([math.fsum(Q[:, p]) for p in range(n)])
+    S_r, S_c = np.abs(P).sum(axis=1), np.abs(Q).sum(axis=0)
+    err_r, err_c = np.abs(Ax - ex_r) / S_r, np.abs(ATv - ex_c) / S_c
+    assert err_r.max() <= 2.0 ** -36 and err_c.max() <= 2.0 ** -36
+    # typical errors: the split and cross-term roundings, about 2^-49 of each
+    # term (an FP64 product of these sizes errs by up to 2^-53 per term plus
+    # n 2^-53 in its sum); a dropped low half or cross term would leave
+    # errors near 2^-24
+    assert np.median(err_r) <= 2.0 ** -46 and np.median(err_c) <= 2.0 ** -46
+
+
+def test_gemv_pair_df_rejects_bad_arguments(ctx):
+    torch = torch_cuda()
+    A = dev(np.zeros((4, 8)))
+    out = dev(np.zeros(8))
+    with pytest.raises(m.MdsipError):   # lda not a multiple of 4
+        m.mdsip_gemv_pair_df(ctx, 4, 6, A, 6, out, out, out, out)
+    with pytest.raises(m.MdsipError):   # lda < n
+        m.mdsip_gemv_pair_df(ctx, 4, 8, A, 4, out, out, out, out)
+    m.mdsip_gemv_pair_df(ctx, 0, 0, None, 4, None, None, None, None)
+    torch.cuda.synchronize()
+
+
 @pytest.mark.parametrize("fp32", [False, True])
 @pytest.mark.parametrize("N", [1, 20, 63, 64, 65, 200, 1033, 2600])
 def test_ldlt_persistent_keeps_every_panel(ctx, N, fp32):

@@ -22,7 +22,9 @@ def r8(v):
 
 
 @pytest.mark.parametrize("M,N,K", [(1, 1, 1), (100, 37, 8), (128, 128, 64), (300, 200, 1000),
-                                   (256, 512, 20000), (5000, 64, 256), (257, 129, 65)])
+                                   (256, 512, 20000), (5000, 64, 256), (257, 129, 65),
+                                   # M <= 256 with a column tile per SM: the persistent wide-M kernel
+                                   (1, 19457, 64), (100, 19500, 200), (255, 20000, 1), (256, 40001, 512)])
 def test_gemm_bf16_matches_definition(M, N, K):
     torch = torch_cuda()
     ctx = make_ctx()
