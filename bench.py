@@ -101,7 +101,7 @@ def parse():
     ap.add_argument("--ws-only", action="store_true",
                     help="run only the learned warm-start measurement and print its own JSON line")
     ap.add_argument("--kernel", choices=["syrk", "syrk_bf16", "syrk_tf32", "ldlt", "ldlt_solve", "ldlt_library",
-                                         "gemm_bf16", "dfma"],
+                                         "gemm_bf16", "dfma", "gemv_pair_df"],
                     default=None,
                     help="time one kernel-level C-ABI call instead of the Newton step")
     ap.add_argument("--m", type=int, default=100000, help="--kernel syrk: rows of A")
@@ -994,6 +994,19 @@ def run_kernel(args):
                               "derived_peak_tflops": FP64_PEAK_TFLOPS,
                               "frac_of_derived": p["tflops"] / FP64_PEAK_TFLOPS}))
             return
+        elif args.kernel == "gemv_pair_df":
+            # the refinement residual's two products with A (m_E x n_d) in double-float,
+            # one call = split of A into FP32 halves + the fused pass
+            mm, n = args.m, args.n
+            lda = (n + 3) // 4 * 4
+            A = torch.zeros((mm, lda), dtype=torch.float64, device="cuda")
+            A[:, :n] = torch.randn((mm, n), dtype=torch.float64, device="cuda") * 0.01
+            x = torch.randn(n, dtype=torch.float64, device="cuda")
+            v = torch.randn(mm, dtype=torch.float64, device="cuda")
+            Ax = torch.empty(mm, dtype=torch.float64, device="cuda")
+            ATv = torch.empty(n, dtype=torch.float64, device="cuda")
+            flops = 4.0 * mm * n
+            call = lambda: m.mdsip_gemv_pair_df(ctx, mm, n, A, lda, x, v, Ax, ATv)
         elif args.kernel == "gemm_bf16":
             # the warm-start network's output layer: (batch m) x (outputs n) x (hidden k)
             M, N, K = args.m, args.n, args.k
@@ -1093,7 +1106,9 @@ def run_kernel(args):
     out = {"kernel": args.kernel, "m": args.m, "n": args.n, "ms_median": ms, "ms_all": times, "tflops": tf}
     if panels is not None:
         out["panels_no_interchange_kept_handed_back"] = panels
-    if args.kernel in ("syrk", "ldlt", "ldlt_solve", "ldlt_library"):
+    if args.kernel == "gemv_pair_df":
+        out["bytes_per_call"] = {"split_read_write": 16.0 * args.m * args.n, "pass_read": 8.0 * args.m * args.n}
+    elif args.kernel in ("syrk", "ldlt", "ldlt_solve", "ldlt_library"):
         out["frac_fp64_peak"] = tf / FP64_PEAK_TFLOPS
     else:
         peak = measured_peak("bf16_tflops")

@@ -38,16 +38,18 @@ __device__ __forceinline__ void df_acc(float ah, float al, float xh, float xl, f
     c += e + sm;
 }
 
+// rows by block, columns by thread; the padding columns n .. lda - 1 become zeros
 __global__ void k_split_matrix(const double *__restrict__ A, int64_t m, int64_t n, int64_t lda,
                                float *__restrict__ hi, float *__restrict__ lo) {
-    const int64_t total = m * lda;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = e % lda;
-        const double a = c < n ? A[e] : 0.0;
-        const float h = (float)a;
-        hi[e] = h;
-        lo[e] = (float)(a - (double)h);
+    for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
+        const double *row = A + i * lda;
+        float *rh = hi + i * lda, *rl = lo + i * lda;
+        for (int64_t c = threadIdx.x; c < lda; c += blockDim.x) {
+            const double a = c < n ? __ldcs(row + c) : 0.0;
+            const float h = (float)a;
+            rh[c] = h;
+            rl[c] = (float)(a - (double)h);
+        }
     }
 }
 
@@ -362,8 +364,7 @@ void launch_gemv_rows_f32(cudaStream_t s, const float *Ahi, int64_t m, int64_t n
 void launch_split_matrix(cudaStream_t s, const double *A, int64_t m, int64_t n, int64_t lda, float *hi,
                          float *lo) {
     if (m <= 0 || lda <= 0) return;
-    const int64_t total = m * lda;
-    k_split_matrix<<<(unsigned)std::min<int64_t>(8192, (total + NT - 1) / NT), NT, 0, s>>>(A, m, n, lda, hi, lo);
+    k_split_matrix<<<(unsigned)std::min<int64_t>(65535, m), NT, 0, s>>>(A, m, n, lda, hi, lo);
     MDSIP_LAUNCHED();
 }
 

@@ -1014,7 +1014,8 @@ __global__ void __launch_bounds__(kSpecThreads) k_bk_spec_rows(SpecArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Persistent speculative factorization (one cooperative launch for all panels).
+// Persistent speculative factorization (one cooperative launch for all panels),
+// FP64 form (the FP32-update form is k_bk_persist32 below).
 //
 // The same no-interchange speculation as k_bk_spec, organised so that a kept
 // panel costs no launch: one grid of co-resident CTAs walks the panels of 64
@@ -1027,8 +1028,8 @@ __global__ void __launch_bounds__(kSpecThreads) k_bk_spec_rows(SpecArgs a) {
 //      block up to date (three block barriers per sub-panel instead of one
 //      per column);
 //   A2 each CTA takes a slice of the rows below the block, one thread per
-//      row: the row's 64 values in registers, solved against the block's
-//      factor (right-looking, no barrier); the FP64 values w = A - sum L W,
+//      row: 64-row chunks in shared memory, solved against the block's
+//      factor in the same 16-column steps; the FP64 values w = A - sum L W,
 //      L = w / d and the column maxima of |w| (exact FP64 bit patterns,
 //      atomicMax) follow;
 //   B  after the grid barrier every CTA applies the rule's column test to the
@@ -1039,9 +1040,7 @@ __global__ void __launch_bounds__(kSpecThreads) k_bk_spec_rows(SpecArgs a) {
 //      all CTAs; grid barrier.
 // The first panel that fails the column test (the rule would look at a row
 // or interchange) ends the kernel with st->k at its first column; the host
-// then runs the pivoting panels from there.  Chain arithmetic and the update
-// products are T (FP32 on the refined mixed-precision path, FP64 otherwise);
-// pivots, L, the tests and the inertia are FP64.
+// then runs the pivoting panels from there.  All arithmetic is FP64.
 // ---------------------------------------------------------------------------
 constexpr int kPThreads = 256;
 constexpr int kPP = 65;      // shared-memory row pitch of the diagonal block
@@ -1066,6 +1065,8 @@ struct PersistArgs {
     double zero_tol;
     long long wait_ns;              // bound of each grid-barrier wait
     float *Af;                      // FP32 copy of the lower triangle, ld N (FP32-update kernel)
+    float *Lf2, *Wf2;               // FP32-update kernel: the odd panels' L and W columns (ld N)
+    unsigned *colcnt;               // FP32-update kernel: per 64-column block, trailing tiles updated
 };
 
 __device__ __forceinline__ long long global_ns() {
@@ -1114,6 +1115,36 @@ __device__ bool panel_barrier(PanelBar *b, unsigned &epoch, long long wait_ns) {
     return s_ok != 0;
 }
 
+// Wait (thread 0, then the whole CTA) until *cnt reaches target; bounded like
+// panel_barrier and sharing its error word.
+__device__ bool wait_count(const unsigned *cnt, unsigned target, PanelBar *b, long long wait_ns) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const long long t0 = global_ns();
+        for (unsigned it = 0;; ++it) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(cnt) : "memory");
+            if ((int)(v - target) >= 0) break;
+            if ((it & 63) == 63) {
+                if (*(volatile int *)&b->err) {
+                    ok = 0;
+                    break;
+                }
+                if (global_ns() - t0 > wait_ns) {
+                    atomicExch(&b->err, 1);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 template <typename T>
 __device__ __forceinline__ T chain_rcp(T d) {
     if constexpr (sizeof(T) == sizeof(float)) return d != 0.0f ? __frcp_rn(d) : 0.0f;
@@ -1129,10 +1160,10 @@ __device__ __forceinline__ double chain_w64(T v, double a) {
 }
 
 // The rule's column test for the panel at k (all threads of every CTA take
-// the same decision from the FP64 pivots s_d and the gathered maxima); CTA 0
-// records a kept panel (kind, inertia, next column) and clears the next
-// panel's maxima.  Returns whether the panel is kept.
-__device__ bool persist_keep(const PersistArgs &a, int k, int nb, int buf, double ztol, const double *s_d) {
+// the same decision from the FP64 pivots s_d and the maxima gathered in
+// cmax[buf]); CTA 0 records a kept panel (kind, inertia, next column) and
+// clears cmax[clear] for a later panel.  Returns whether the panel is kept.
+__device__ bool persist_keep(const PersistArgs &a, int k, int nb, int buf, int clear, double ztol, const double *s_d) {
     const double alpha = 0.6403882032022076;   // (1 + sqrt 17) / 8
     const int tid = threadIdx.x;
     int keep = 1;
@@ -1152,7 +1183,7 @@ __device__ bool persist_keep(const PersistArgs &a, int k, int nb, int buf, doubl
             a.Doff[k + tid] = 0.0;
             pos = s_d[tid] > 0.0 ? 1 : 0;
         }
-        if (tid < 64) a.cmax[(buf ^ 1) * 64 + tid] = 0ULL;   // the next panel's maxima start at zero
+        if (tid < 64) a.cmax[clear * 64 + tid] = 0ULL;   // a later panel's maxima start at zero
         const int np = __syncthreads_count(pos);
         if (tid == 0) {
             a.st->npos += np;
@@ -1165,8 +1196,8 @@ __device__ bool persist_keep(const PersistArgs &a, int k, int nb, int buf, doubl
     return true;
 }
 
-template <typename T>
 __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist(PersistArgs a) {
+    using T = double;
     extern __shared__ __align__(16) unsigned char psm[];
     T *V = reinterpret_cast<T *>(psm);      // [64][kPP]: the diagonal block; W values once factored
                                             // (then [64][kPP]: a chunk of the rows below it)
@@ -1276,7 +1307,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist(PersistArgs a) {
                     a.Dd[k + c] = s_d[c];
                 } else {
                     const T w = V[r * kPP + c];
-                    a.L[o] = sizeof(T) == sizeof(float) ? (double)(w * s_rc[c]) : (double)w * s_rd[c];
+                    a.L[o] = w * s_rd[c];
                     const unsigned long long bw = absbits64((double)w);
                     bm = bw > bm ? bw : bm;
                 }
@@ -1331,45 +1362,28 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist(PersistArgs a) {
                 }
                 __syncthreads();
             }
-            // outputs and column maxima: one warp per column, lanes over rows.
-            // FP64 chains: w and L in FP64.  FP32 chains: L, W and the maxima from
-            // the FP32 values the chain computed (one conversion per element for
-            // the FP64 copy of L; GB300 runs FP64 arithmetic at 1/64 of FP32)
+            // outputs and column maxima: one warp per column, lanes over rows
             for (int c = wid; c < nb; c += kWarps) {
-                if constexpr (sizeof(T) == sizeof(float)) {
-                    unsigned bm = 0u;
-                    for (int r = lane; r < nr; r += 32) {
-                        const int i = cb + r;
-                        const float w = U[r * kPP + c], l = w * s_rc[c];
-                        a.L[(int64_t)i + (int64_t)(k + c) * N] = (double)l;
-                        a.Lf[(int64_t)i + (int64_t)c * N] = l;
-                        a.Wf[(int64_t)i + (int64_t)c * N] = w;
-                        bm = max(bm, __float_as_uint(w) & 0x7fffffffu);
-                    }
-                    bm = __reduce_max_sync(0xffffffffu, bm);
-                    if (lane == 0 && bm) atomicMax(&s_cmax[c], absbits64((double)__uint_as_float(bm)));
-                } else {
-                    unsigned long long bm = 0ULL;
-                    for (int r = lane; r < nr; r += 32) {
-                        const int i = cb + r;
-                        const int64_t o = (int64_t)i + (int64_t)(k + c) * N;
-                        const double w = U[r * kPP + c];
-                        a.L[o] = w * s_rd[c];
-                        a.Wg[(int64_t)i + (int64_t)c * N] = w;
-                        const unsigned long long bw = absbits64(w);
-                        bm = bw > bm ? bw : bm;
-                    }
-                    const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(bm >> 32));
-                    const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(bm >> 32) == hi ? (unsigned)bm : 0u);
-                    if (lane == 0 && (hi | lo)) atomicMax(&s_cmax[c], ((unsigned long long)hi << 32) | lo);
+                unsigned long long bm = 0ULL;
+                for (int r = lane; r < nr; r += 32) {
+                    const int i = cb + r;
+                    const int64_t o = (int64_t)i + (int64_t)(k + c) * N;
+                    const double w = U[r * kPP + c];
+                    a.L[o] = w * s_rd[c];
+                    a.Wg[(int64_t)i + (int64_t)c * N] = w;
+                    const unsigned long long bw = absbits64(w);
+                    bm = bw > bm ? bw : bm;
                 }
+                const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(bm >> 32));
+                const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(bm >> 32) == hi ? (unsigned)bm : 0u);
+                if (lane == 0 && (hi | lo)) atomicMax(&s_cmax[c], ((unsigned long long)hi << 32) | lo);
             }
         }
         __syncthreads();
         if (tid < 64 && s_cmax[tid]) atomicMax(&a.cmax[buf * 64 + tid], s_cmax[tid]);
         if (!panel_barrier(a.bar, epoch, a.wait_ns)) return;
         // ---------------- B: the rule's column test, the same in every CTA
-        if (!persist_keep(a, k, nb, buf, ztol, s_d)) {
+        if (!persist_keep(a, k, nb, buf, buf ^ 1, ztol, s_d)) {
             if (g == 0 && tid == 0) {   // the panel loop takes over at column k
                 a.st->k = k;
                 a.st->kb = 0;
@@ -1409,9 +1423,14 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist(PersistArgs a) {
 //   - the FP64 pivot is the chain's FP32 value plus the part of S's diagonal
 //     that the FP32 copy dropped; L (FP64 copy), W and the column maxima come
 //     from the FP32 chain values.
-// On a rejected panel every CTA writes the FP32 updates of the trailing
-// matrix back into the FP64 matrix (A += Af - fl32(A)) before the pivoting
-// panels take over.
+// One grid barrier per panel (after its rows, for the column test); the
+// trailing update has none: its 64 x 64 blocks are spread over the CTAs with
+// the blocks of the next panel's columns first, those count themselves done,
+// and the next panel starts on that count while the remaining blocks are
+// still being updated (L and W of successive panels alternate between two
+// buffers, the column maxima rotate over three).  On a rejected panel every
+// CTA writes the FP32 updates of the trailing matrix back into the FP64
+// matrix (A += Af - fl32(A)) before the pivoting panels take over.
 // ---------------------------------------------------------------------------
 // Sub-panel width Q (16 or 32): a warp holds the Q diagonal-block rows of a
 // sub-panel and 32 rows below them.  Own rows staged per pass: what the warps
@@ -1422,31 +1441,50 @@ constexpr int kRowsBuf = 64 + own_rows<32>();   // the larger of the two (224 ow
 
 // Pivot chain of one Q-column sub-panel in one warp.  vA: the sub-block's row
 // `lane` (lanes >= Q hold zeros), vB: one row below it (zeros where a lane
-// has no row).  With `factored`, vA holds the factored sub-block (its W
-// values) and rcl the reciprocal pivot of column `lane`: vA is only read.  On
-// return vB holds the row's W values (L = W / d); the result is the
-// reciprocal pivot of column `lane`.
+// has no row).  Before step j the sub-block's lanes put column j (their
+// vA[j]) into the warp's slot `col` (Q floats, 16-byte aligned) and every
+// lane reads it back as 16-byte broadcasts: the loads issue back to back,
+// where Q - j - 1 shuffles per step had their latencies exposed one after
+// another.  The reciprocal pivot is the hardware approximation (about one
+// unit in the last place; the factor is refined against the FP64 operator).
+// With `factored`, vA holds the factored sub-block (its W values) and rcl the
+// reciprocal pivot of column `lane`: vA is only read.  On return vB holds the
+// row's W values (L = W / d); the result is the reciprocal pivot of column
+// `lane`.
+__device__ __forceinline__ float rcp_approx(float d) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+    return r;
+}
+
 template <int Q>
 __device__ __forceinline__ float chain_q(float (&vA)[Q], float (&vB)[Q], bool factored, float rcl, int cw,
-                                         int lane) {
+                                         int lane, float *col) {
     float rc = 0.0f;
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
-        float rj;
-        if (factored) {
-            rj = __shfl_sync(0xffffffffu, rcl, j);
-        } else {
-            const float dj = __shfl_sync(0xffffffffu, vA[j], j);
-            rj = (j < cw && dj != 0.0f) ? __frcp_rn(dj) : 0.0f;
+        if (lane < Q) col[lane] = vA[j];
+        __syncwarp();
+        float w[Q];
+#pragma unroll
+        for (int t = 0; t < Q; t += 4) {
+            const float4 x = *reinterpret_cast<const float4 *>(col + t);
+            w[t] = x.x;
+            w[t + 1] = x.y;
+            w[t + 2] = x.z;
+            w[t + 3] = x.w;
         }
+        __syncwarp();   // every lane has read the column before the next one is written
+        float rj;
+        if (factored) rj = __shfl_sync(0xffffffffu, rcl, j);
+        else rj = (j < cw && w[j] != 0.0f) ? rcp_approx(w[j]) : 0.0f;
         // zero multipliers, not conditional updates: v stays in registers
         const float lA = (!factored && lane > j) ? vA[j] * rj : 0.0f;
         const float lB = vB[j] * rj;
 #pragma unroll
         for (int t = j + 1; t < Q; ++t) {
-            const float w = __shfl_sync(0xffffffffu, vA[j], t);
-            vA[t] = fmaf(-lA, w, vA[t]);
-            vB[t] = fmaf(-lB, w, vB[t]);
+            vA[t] = fmaf(-lA, w[t], vA[t]);
+            vB[t] = fmaf(-lB, w[t], vB[t]);
         }
         rc = lane == j ? rj : rc;
     }
@@ -1459,7 +1497,7 @@ __device__ __forceinline__ float chain_q(float (&vA)[Q], float (&vB)[Q], bool fa
 // warp 0 also keeps the factored sub-block and writes it back, with its
 // reciprocal pivots, after every warp has read it.
 template <int Q>
-__device__ void persist_subpanel(float *Rb, float *s_rc, int c0, int cw, int nb, bool blk, int nr,
+__device__ void persist_subpanel(float *Rb, float *s_rc, float *s_col, int c0, int cw, int nb, bool blk, int nr,
                                  bool factored) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gb = blk ? max(0, nb - c0 - Q + 31) / 32 : 0;   // groups of block rows
@@ -1481,7 +1519,7 @@ __device__ void persist_subpanel(float *Rb, float *s_rc, int c0, int cw, int nb,
             vB[t] = (row >= 0 && t < cw) ? Rb[row * kPP + c0 + t] : 0.0f;
         }
         const float rcl = (factored && lane < Q) ? s_rc[c0 + lane] : 0.0f;
-        rc = chain_q<Q>(vA, vB, factored, rcl, cw, lane);
+        rc = chain_q<Q>(vA, vB, factored, rcl, cw, lane, s_col + wid * Q);
         if (row >= 0) {
 #pragma unroll
             for (int t = 0; t < Q; ++t)
@@ -1544,22 +1582,14 @@ __device__ void persist_rank_q(float *Rb, const float *s_rc, int c0, int nb, boo
     __syncthreads();
 }
 
-// One 64 x 64 tile of the trailing lower triangle on the FP32 copy:
-// Af(i, c) -= sum_t Lf(i, t) Wf(c, t), i >= c >= k0 + kb (tile numbering as
-// trailing_tile).  smem: 2 x 64 x 64 floats.
-__device__ void trailing_tile_f32(int tile, int N, int kb, int k0, float *__restrict__ Af,
-                                  const float *__restrict__ Lf, const float *__restrict__ Wf,
-                                  unsigned char *usmem) {
+// The 64 x 64 block of the lower triangle at rows i0.., columns c0.. of the
+// FP32 copy: Af(i, c) -= sum_{t < kb} Lf(i, t) Wf(c, t) for i >= c.
+// smem: 2 x 64 x 64 floats.
+__device__ void block_update_f32(int i0, int c0, int N, int kb, float *__restrict__ Af,
+                                 const float *__restrict__ Lf, const float *__restrict__ Wf,
+                                 unsigned char *usmem) {
     float *Lt = reinterpret_cast<float *>(usmem);   // [64][64]: Lt[t][r]
     float *Wt = Lt + 64 * kUT;                      // [64][64]: Wt[t][c]
-    const int base = k0 + kb;
-    if (base >= N || kb <= 0) return;
-    int tr = (int)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
-    while ((tr + 1) * (tr + 2) / 2 <= tile) ++tr;
-    while (tr * (tr + 1) / 2 > tile) --tr;
-    const int tc = tile - tr * (tr + 1) / 2;
-    const int i0 = base + tr * kUT, c0 = base + tc * kUT;
-    if (i0 >= N) return;
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     // this thread's 16 entries of the tile, loaded ahead of the products
@@ -1624,7 +1654,11 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist32(PersistArgs a) {
     float *Rb = reinterpret_cast<float *>(psm);   // [kRowsBuf][kPP]: block rows 0..63, then own rows
     __shared__ double s_d[64];
     __shared__ float s_rc[64];
-    __shared__ unsigned long long s_cmax[64];
+    __shared__ __align__(16) float s_col[kPThreads / 32 * Q];   // each warp's pivot-chain column
+    // column maxima of |w| as FP32 bit patterns: the diagonal block's rows
+    // (written by the one warp that outputs the column) and this CTA's rows
+    // (one warp per column): plain stores, no shared atomics
+    __shared__ unsigned s_cmax_blk[64], s_cmax_own[64];
     const int N = a.N, G = (int)gridDim.x, g = (int)blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, wid = tid >> 5;
     constexpr int kWarps = kPThreads / 32;
@@ -1658,12 +1692,17 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist32(PersistArgs a) {
     }
     __threadfence();
     if (!panel_barrier(a.bar, epoch, a.wait_ns)) return;
+    const int nbk = (N + 63) / 64;   // 64 x 64 blocks per row / column
     int p = 0;
     for (int k = kstart; k < N; k += 64, ++p) {
         const int nb = min(64, N - k);
-        const int buf = p & 1;
+        const int kblk = k / 64;
+        const int buf = p % 3;                       // column maxima of this panel
+        float *Lfp = (p & 1) ? a.Lf2 : a.Lf, *Wfp = (p & 1) ? a.Wf2 : a.Wf;
+        // this panel's columns have taken every earlier panel's update
+        if (p > 0 && !wait_count(&a.colcnt[kblk], (unsigned)(nbk - kblk), a.bar, a.wait_ns)) return;
         if (tid < 64) {
-            s_cmax[tid] = 0ULL;
+            s_cmax_blk[tid] = s_cmax_own[tid] = 0u;
             s_rc[tid] = 0.0f;
         }
         // S's diagonal of the block (for the FP64 pivots), loaded ahead of the chains
@@ -1703,7 +1742,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist32(PersistArgs a) {
             __syncthreads();
             // ---- the sub-panels, each followed by the update of the columns after it
             for (int c0 = 0; c0 < nb; c0 += Q) {
-                persist_subpanel<Q>(Rb, s_rc, c0, min(Q, nb - c0), nb, blk, nr, !blk);
+                persist_subpanel<Q>(Rb, s_rc, s_col, c0, min(Q, nb - c0), nb, blk, nr, !blk);
                 if (c0 + Q < nb) persist_rank_q<Q>(Rb, s_rc, c0, nb, blk, nr);
             }
             if (blk) {
@@ -1729,7 +1768,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist32(PersistArgs a) {
                         }
                     }
                     bm = __reduce_max_sync(0xffffffffu, bm);
-                    if (lane == 0 && bm) atomicMax(&s_cmax[c], absbits64((double)__uint_as_float(bm)));
+                    if (lane == 0) s_cmax_blk[c] = bm;
                 }
             }
             // own rows: L (FP64 copy), the FP32 L and W columns, column maxima
@@ -1739,18 +1778,21 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist32(PersistArgs a) {
                     const int i = cb + r;
                     const float w = Rb[(64 + r) * kPP + c], l = w * s_rc[c];
                     a.L[(int64_t)i + (int64_t)(k + c) * N] = (double)l;
-                    a.Lf[(int64_t)i + (int64_t)c * N] = l;
-                    a.Wf[(int64_t)i + (int64_t)c * N] = w;
+                    Lfp[(int64_t)i + (int64_t)c * N] = l;
+                    Wfp[(int64_t)i + (int64_t)c * N] = w;
                     bm = max(bm, __float_as_uint(w) & 0x7fffffffu);
                 }
                 bm = __reduce_max_sync(0xffffffffu, bm);
-                if (lane == 0 && bm) atomicMax(&s_cmax[c], absbits64((double)__uint_as_float(bm)));
+                if (lane == 0) s_cmax_own[c] = max(s_cmax_own[c], bm);
             }
         }
         __syncthreads();
-        if (tid < 64 && s_cmax[tid]) atomicMax(&a.cmax[buf * 64 + tid], s_cmax[tid]);
+        if (tid < 64) {
+            const unsigned bm = max(s_cmax_blk[tid], s_cmax_own[tid]);
+            if (bm) atomicMax(&a.cmax[buf * 64 + tid], absbits64((double)__uint_as_float(bm)));
+        }
         if (!panel_barrier(a.bar, epoch, a.wait_ns)) return;
-        if (!persist_keep(a, k, nb, buf, ztol, s_d)) {
+        if (!persist_keep(a, k, nb, buf, (p + 2) % 3, ztol, s_d)) {
             // hand over at column k: the FP64 matrix takes the FP32 updates
             for (int c = k + g; c < N; c += G)
                 for (int i = c + tid; i < N; i += kPThreads) {
@@ -1766,24 +1808,46 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist32(PersistArgs a) {
             return;
         }
         if (k + nb >= N) break;
-        // ---------------- trailing update on the FP32 copy
+        // ---------------- trailing update on the FP32 copy.  The panel's blocks
+        // are numbered with those of the next panel's columns first (n1 of
+        // them, counted as they finish: the next panel starts when its column
+        // is complete) and the rest after (row-major over their triangle);
+        // CTA g takes numbers g, g + G, ...  Every block's update of the
+        // previous panel finished before this panel's grid barrier, so any
+        // CTA may take any block.
         {
-            const int base = k + nb;
-            const int nt = (N - base + kUT - 1) / kUT;
-            const int tiles = nt * (nt + 1) / 2;
-            for (int t = g; t < tiles; t += G) {
-                trailing_tile_f32(t, N, nb, k, a.Af, a.Lf, a.Wf, psm);
+            const int n1 = nbk - kblk - 1, m2 = nbk - kblk - 2;
+            const int nblocks = n1 + (m2 > 0 ? m2 * (m2 + 1) / 2 : 0);
+            for (int b = g; b < nblocks; b += G) {
+                int I, J;
+                if (b < n1) {
+                    I = kblk + 1 + b;
+                    J = kblk + 1;
+                } else {
+                    const int lin = b - n1;
+                    int r = (int)((sqrtf(8.0f * (float)lin + 1.0f) - 1.0f) * 0.5f);
+                    while ((r + 1) * (r + 2) / 2 <= lin) ++r;
+                    while (r * (r + 1) / 2 > lin) --r;
+                    I = kblk + 2 + r;
+                    J = kblk + 2 + (lin - r * (r + 1) / 2);
+                }
+                block_update_f32(64 * I, 64 * J, N, nb, a.Af, Lfp, Wfp, psm);
                 __syncthreads();
+                if (b < n1 && tid == 0) {
+                    __threadfence();
+                    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&a.colcnt[J]) : "memory");
+                }
             }
         }
-        __threadfence();
-        if (!panel_barrier(a.bar, epoch, a.wait_ns)) return;
     }
 }
 
-__global__ void k_bk_init(int N, int32_t *perm, PanelState *st, unsigned long long *cmax, PanelBar *bar) {
+__global__ void k_bk_init(int N, int32_t *perm, PanelState *st, unsigned long long *cmax, PanelBar *bar,
+                          unsigned *colcnt) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) perm[i] = i;
-    if (blockIdx.x == 0 && threadIdx.x < 128) cmax[threadIdx.x] = 0ULL;
+    if (blockIdx.x == 0 && threadIdx.x < 192) cmax[threadIdx.x] = 0ULL;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (N + 63) / 64 + 1; i += gridDim.x * blockDim.x)
+        colcnt[i] = 0u;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         bar->count = 0u;
         bar->err = 0;
@@ -1909,7 +1973,7 @@ void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t sm
 // (2 x 64), the pending row tests (64) and their partial row maxima
 // ((ceil(N / 32) + 2) x 64)
 struct BlockedScratch {
-    size_t wg, st, lf, wf, cmax, fail, rowpart, af, total;
+    size_t wg, st, lf, wf, cmax, fail, rowpart, af, lf2, wf2, colcnt, total;
 };
 
 BlockedScratch blocked_scratch(int64_t N) {
@@ -1921,10 +1985,13 @@ BlockedScratch blocked_scratch(int64_t N) {
     l.lf = l.st + 256;
     l.wf = l.lf + up(n * 65 * sizeof(float));
     l.cmax = l.wf + up(n * 65 * sizeof(float));
-    l.fail = l.cmax + up(128 * sizeof(unsigned long long));
+    l.fail = l.cmax + up(192 * sizeof(unsigned long long));
     l.rowpart = l.fail + up(64 * sizeof(RowTest));
     l.af = l.rowpart + up(((n + 31) / 32 + 2) * 64 * sizeof(unsigned long long));
-    l.total = l.af + up(n * n * sizeof(float));   // the FP32 copy of the persistent FP32-update kernel
+    l.lf2 = l.af + up(n * n * sizeof(float));   // the FP32 copy of the persistent FP32-update kernel
+    l.wf2 = l.lf2 + up(n * 64 * sizeof(float));
+    l.colcnt = l.wf2 + up(n * 64 * sizeof(float));
+    l.total = l.colcnt + up(((n + 63) / 64 + 1) * sizeof(unsigned));
     return l;
 }
 
@@ -1945,7 +2012,7 @@ size_t persist_smem() {
 template <typename T>
 const void *persist_kernel() {
     if constexpr (sizeof(T) == sizeof(float)) return (const void *)k_bk_persist32<kPersistQ>;
-    else return (const void *)k_bk_persist<double>;
+    else return (const void *)k_bk_persist;
 }
 
 // Run k_bk_persist from column 0; returns the column where it stopped (N: all
@@ -2026,7 +2093,8 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
     PanelState *st = reinterpret_cast<PanelState *>(w + lay.st);
     PanelBar *bar = grid_bar(w, lay);
     k_bk_init<<<std::max(1, std::min(1024, ceil_div(N, 256))), 256, 0, s>>>(
-        (int)N, out.perm, st, reinterpret_cast<unsigned long long *>(w + lay.cmax), bar);
+        (int)N, out.perm, st, reinterpret_cast<unsigned long long *>(w + lay.cmax), bar,
+        reinterpret_cast<unsigned *>(w + lay.colcnt));
     MDSIP_LAUNCHED();
     int k0 = 0;   // first column left to the panel loop below
     if (persist) {
@@ -2046,6 +2114,9 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
         pa.maxabs = maxabs_dev;
         pa.zero_tol = zero_tol;
         pa.Af = reinterpret_cast<float *>(w + lay.af);
+        pa.Lf2 = reinterpret_cast<float *>(w + lay.lf2);
+        pa.Wf2 = reinterpret_cast<float *>(w + lay.wf2);
+        pa.colcnt = reinterpret_cast<unsigned *>(w + lay.colcnt);
         pa.wait_ns = 20LL * 1000 * 1000 * 1000;   // 20 s: far above the longest phase (FP64 update at N ~ 44000)
         k0 = fp32_update ? run_persistent<float>(s, num_sms, (int)N, pa, st, bar)
                          : run_persistent<double>(s, num_sms, (int)N, pa, st, bar);
@@ -2053,7 +2124,7 @@ void launch_ldlt_blocked(cudaStream_t s, int num_sms, int64_t N, double *S, cons
                       "ldlt: a panel needs interchanges and N is too large for the pivoting panel");
         // the panel loop's no-interchange kernels expect their column maxima and
         // arg-max keys at zero; the rejected panel left its maxima there
-        if (k0 < N) MDSIP_CUDA(cudaMemsetAsync(w + lay.cmax, 0, 128 * sizeof(unsigned long long), s));
+        if (k0 < N) MDSIP_CUDA(cudaMemsetAsync(w + lay.cmax, 0, 192 * sizeof(unsigned long long), s));
     }
 
     PanelArgs a{};
