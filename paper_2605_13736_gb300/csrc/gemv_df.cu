@@ -19,6 +19,7 @@
 // The iterative refinement of the mixed-precision path and that path's
 // constraint and gradient passes use these; the plain FP64 path keeps FP64.
 #include "internal.cuh"
+#include "tc.cuh"
 
 namespace mdsip {
 
@@ -163,120 +164,219 @@ __global__ void __launch_bounds__(NT) k_gemv_t_df(const float *__restrict__ Ahi,
 
 // Both products of the residual in one read of A: out[i] = sum_p A[i][p] x[p]
 // for this block's rows and partial[b][p] = sum_{i of block b} A[i][p] y[i].
-// Thread t owns columns 4t .. 4t + 3 and 1024 + 4t .. 1024 + 4t + 3 of each
-// 2048-column pass (16-byte loads of A_hi and A_lo); rows go in batches of
-// eight, whose per-thread row sums are reduced over the block as
-// double-float pairs (warp shuffles, then one slot per warp).
-constexpr int kBothCols = 8 * NT;   // columns per pass
+// One CTA of 512 threads per SM.  Rows stream through shared memory in
+// batches of kBR rows (a 2048-column slice of A_hi and of A_lo per row, by
+// bulk asynchronous copies into a kBS-stage ring completed on mbarriers), so
+// the copies of the next batches are in flight while the current one is
+// computed.  Thread t owns columns 4t .. 4t + 3 of each slice (16 warps per
+// SM: the double-float arithmetic, not the memory, sets the pace, and it
+// needs the warps for its dependent chains); the per-thread row sums of a
+// batch are reduced over the block as double-float pairs (warp shuffles,
+// then one slot per warp).  Waits are bounded: on expiry the kernel sets
+// *err and stops.
+constexpr int kBothThreads = 512;
+constexpr int kBothCols = 4 * kBothThreads;   // columns per slice
+constexpr int kBR = 4;                        // rows per stage
+constexpr int kBS = 3;                        // stages
+constexpr size_t kBothSmem = (size_t)kBS * kBR * 2 * kBothCols * sizeof(float) + 256;
 __device__ __forceinline__ void df_add(float &s, float &c, float s2, float c2) {
     const float t = s + s2, bb = t - s;
     const float e = (s - (t - bb)) + (s2 - bb);
     s = t;
     c = c + c2 + e;
 }
-__global__ void __launch_bounds__(NT, 1) k_gemv_both_df(const float *__restrict__ Ahi, const float *__restrict__ Alo,
-                                                     int64_t m, int64_t n, int64_t lda,
-                                                     const float2 *__restrict__ xs, const float2 *__restrict__ ys,
-                                                     double *__restrict__ out, double *__restrict__ partial) {
-    __shared__ float2 red[2][8][NT / 32];   // [batch parity][row][warp]
+// df_acc on two lanes at once with the packed FP32 instructions (each lane
+// rounded exactly as the scalar form; a - b as fma(b, -1, a))
+__device__ __forceinline__ void df_acc2(float2 ah, float2 al, float2 xh, float2 xl, float2 &s, float2 &c) {
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 p = __fmul2_rn(ah, xh);
+    const float2 pe = __ffma2_rn(ah, xh, __fmul2_rn(p, m1));           // exact error of the product
+    const float2 sm = __ffma2_rn(ah, xl, __ffma2_rn(al, xh, pe));       // the small terms
+    const float2 t = __fadd2_rn(s, p);                                  // two-sum: s + p = t + e
+    const float2 bb = __ffma2_rn(s, m1, t);
+    const float2 e = __fadd2_rn(__ffma2_rn(__ffma2_rn(bb, m1, t), m1, s), __ffma2_rn(bb, m1, p));
+    s = t;
+    c = __fadd2_rn(c, __fadd2_rn(e, sm));
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     tc::smem_u32(dst)),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(tc::smem_u32(bar))
+                 : "memory");
+}
+__global__ void __launch_bounds__(kBothThreads, 1)
+    k_gemv_both_df(const float *__restrict__ Ahi, const float *__restrict__ Alo, int64_t m, int64_t n, int64_t lda,
+                   const float2 *__restrict__ xs, const float2 *__restrict__ ys, double *__restrict__ out,
+                   double *__restrict__ partial, int *err) {
+    extern __shared__ __align__(128) unsigned char bsm[];
+    float *ring = reinterpret_cast<float *>(bsm);   // [kBS][kBR][2][kBothCols]
+    uint64_t *full = reinterpret_cast<uint64_t *>(bsm + (size_t)kBS * kBR * 2 * kBothCols * sizeof(float));
+    constexpr int kW = kBothThreads / 32;
+    __shared__ float2 red[2][kBR][kW];   // [batch parity][row][warp]
+    __shared__ int s_stop;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t rows_per = (m + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per;
     const int64_t r1 = min(m, r0 + rows_per);
+    const int nbat = r1 > r0 ? (int)((r1 - r0 + kBR - 1) / kBR) : 0;
+    if (tid == 0) {
+        for (int st = 0; st < kBS; ++st) tc::mbar_init(&full[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_stop = 0;
+    }
+    __syncthreads();
+    int gb = 0;   // batches issued/consumed over all slices (stage and phase)
     int parity = 0;
     for (int64_t cp = 0; cp < n; cp += kBothCols) {
-        int64_t p[2];
-        bool on[2];
-        float xh[8], xl[8];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            p[h] = cp + 4 * tid + (int64_t)h * (kBothCols / 2);
-            on[h] = p[h] < n && p[h] < lda;   // lda is a multiple of 4: the 16-byte chunk stays in the row
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float2 x = (p[h] + q < n) ? xs[p[h] + q] : make_float2(0.0f, 0.0f);
-                xh[4 * h + q] = x.x;
-                xl[4 * h + q] = x.y;
+        const uint32_t width = (uint32_t)min((int64_t)kBothCols, lda - cp);   // a multiple of 4 floats
+        // thread 0 fills stage (gb + b) % kBS with batch b of this slice
+        auto issue = [&](int b) {
+            const int st = (gb + b) % kBS;
+            uint32_t bytes = 0;
+            for (int rr = 0; rr < kBR; ++rr)
+                if (r0 + (int64_t)b * kBR + rr < r1) bytes += 2 * width * (uint32_t)sizeof(float);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc::mbar_expect_tx(&full[st], bytes);
+            for (int rr = 0; rr < kBR; ++rr) {
+                const int64_t i = r0 + (int64_t)b * kBR + rr;
+                if (i >= r1) break;
+                float *dst = ring + ((size_t)st * kBR + rr) * 2 * kBothCols;
+                bulk_g2s(dst, Ahi + i * lda + cp, width * (uint32_t)sizeof(float), &full[st]);
+                bulk_g2s(dst + kBothCols, Alo + i * lda + cp, width * (uint32_t)sizeof(float), &full[st]);
             }
-        }
-        float cs[8], cc[8];
-        double cacc[8];
+        };
+        if (tid == 0)
+            for (int b = 0; b < min(kBS, nbat); ++b) issue(b);
+        // this thread's chunk: inside the copied width whenever it starts below n
+        // (lda is a multiple of 4), with A's padding columns n .. lda - 1 zero
+        const int64_t p0 = cp + 4 * tid;
+        const bool on = p0 < n;
+        float xh[4], xl[4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            cs[q] = cc[q] = 0.0f;
+        for (int q = 0; q < 4; ++q) {
+            const float2 x = (p0 + q < n) ? xs[p0 + q] : make_float2(0.0f, 0.0f);
+            xh[q] = x.x;
+            xl[q] = x.y;
+        }
+        // column sums: a double-float pair per 16 rows, added into a second
+        // pair, which goes into FP64 every 256 rows (the FP64 pipe runs at
+        // 1/64 of the FP32 rate)
+        float cs[4], cc[4], CS[4], CC[4];
+        double cacc[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            cs[q] = cc[q] = CS[q] = CC[q] = 0.0f;
             cacc[q] = 0.0;
         }
-        int cnt = 0;
-        for (int64_t i0 = r0; i0 < r1; i0 += 8) {
-            // all 32 16-byte loads of the batch in flight before the arithmetic
-            float4 ah[8][2], al[8][2];
-            float2 y[8];
-#pragma unroll
-            for (int rr = 0; rr < 8; ++rr) {
-                const int64_t i = i0 + rr;
-                const bool live = i < r1;
-                y[rr] = live ? ys[i] : make_float2(0.0f, 0.0f);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    ah[rr][h] = al[rr][h] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                    if (live && on[h]) {
-                        ah[rr][h] = __ldcs(reinterpret_cast<const float4 *>(Ahi + i * lda + p[h]));
-                        al[rr][h] = __ldcs(reinterpret_cast<const float4 *>(Alo + i * lda + p[h]));
-                    }
-                }
+        int cnt = 0, cnt2 = 0;
+        for (int b = 0; b < nbat; ++b) {
+            const int st = (gb + b) % kBS;
+            const uint32_t ph = (uint32_t)(((gb + b) / kBS) & 1);
+            if (!tc::mbar_wait(&full[st], ph)) {   // bounded; every thread stops at the barrier below
+                atomicExch(err, 1);
+                s_stop = 1;
             }
-            float rs[8], rc[8];
+            const int64_t i0 = r0 + (int64_t)b * kBR;
+            float rs[kBR], rc[kBR];
 #pragma unroll
-            for (int rr = 0; rr < 8; ++rr) {
+            for (int rr = 0; rr < kBR; ++rr) {
                 rs[rr] = rc[rr] = 0.0f;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float a_h[4] = {ah[rr][h].x, ah[rr][h].y, ah[rr][h].z, ah[rr][h].w};
-                    const float a_l[4] = {al[rr][h].x, al[rr][h].y, al[rr][h].z, al[rr][h].w};
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {   // zero entries (dead rows, columns past n) add nothing
-                        df_acc(a_h[q], a_l[q], xh[4 * h + q], xl[4 * h + q], rs[rr], rc[rr]);
-                        df_acc(a_h[q], a_l[q], y[rr].x, y[rr].y, cs[4 * h + q], cc[4 * h + q]);
-                    }
-                }
+                if (!on || i0 + rr >= r1) continue;
+                const float2 y = ys[i0 + rr];
+                const float2 yh = make_float2(y.x, y.x), yl = make_float2(y.y, y.y);
+                const float *row = ring + ((size_t)st * kBR + rr) * 2 * kBothCols;
+                const float4 ah = *reinterpret_cast<const float4 *>(row + 4 * tid);
+                const float4 al = *reinterpret_cast<const float4 *>(row + kBothCols + 4 * tid);
+                // columns (0, 1) and (2, 3) as lane pairs: the row sum in two
+                // partial pairs, the column sums in their own pairs
+                float2 rsp = make_float2(0.0f, 0.0f), rcp = make_float2(0.0f, 0.0f);
+                df_acc2(make_float2(ah.x, ah.y), make_float2(al.x, al.y), make_float2(xh[0], xh[1]),
+                        make_float2(xl[0], xl[1]), rsp, rcp);
+                df_acc2(make_float2(ah.z, ah.w), make_float2(al.z, al.w), make_float2(xh[2], xh[3]),
+                        make_float2(xl[2], xl[3]), rsp, rcp);
+                float2 c01s = make_float2(cs[0], cs[1]), c01c = make_float2(cc[0], cc[1]);
+                float2 c23s = make_float2(cs[2], cs[3]), c23c = make_float2(cc[2], cc[3]);
+                df_acc2(make_float2(ah.x, ah.y), make_float2(al.x, al.y), yh, yl, c01s, c01c);
+                df_acc2(make_float2(ah.z, ah.w), make_float2(al.z, al.w), yh, yl, c23s, c23c);
+                cs[0] = c01s.x;
+                cs[1] = c01s.y;
+                cs[2] = c23s.x;
+                cs[3] = c23s.y;
+                cc[0] = c01c.x;
+                cc[1] = c01c.y;
+                cc[2] = c23c.x;
+                cc[3] = c23c.y;
+                rs[rr] = rsp.x;
+                rc[rr] = rcp.x;
+                df_add(rs[rr], rc[rr], rsp.y, rcp.y);
             }
-            if (++cnt == 2) {   // every 16 rows: the column sums into FP64
+            if (++cnt == 4) {   // every 16 rows
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    cacc[q] += (double)cs[q];
-                    cacc[q] += (double)cc[q];
+                for (int q = 0; q < 4; ++q) {
+                    df_add(CS[q], CC[q], cs[q], cc[q]);
                     cs[q] = cc[q] = 0.0f;
                 }
                 cnt = 0;
-            }
-            // the eight row sums over the block
+                if (++cnt2 == 16) {   // every 256 rows
 #pragma unroll
-            for (int rr = 0; rr < 8; ++rr) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float s2 = __shfl_xor_sync(0xffffffffu, rs[rr], o);
-                    const float c2 = __shfl_xor_sync(0xffffffffu, rc[rr], o);
-                    df_add(rs[rr], rc[rr], s2, c2);
+                    for (int q = 0; q < 4; ++q) {
+                        cacc[q] += (double)CS[q];
+                        cacc[q] += (double)CC[q];
+                        CS[q] = CC[q] = 0.0f;
+                    }
+                    cnt2 = 0;
                 }
-                if (lane == 0) red[parity][rr][wid] = make_float2(rs[rr], rc[rr]);
             }
-            __syncthreads();
-            if (tid < 8 && i0 + tid < r1) {
+            // the four row sums over the warp by halving exchanges: after the
+            // xor-16 and xor-8 steps each lane holds one row (row 2 bit4 +
+            // bit3 of the lane), summed over its 8 lanes by three more steps
+            {
+                static_assert(kBR == 4, "the exchange below is written for four rows");
+                const bool u16 = (lane & 16) != 0, u8 = (lane & 8) != 0;
+                float sa = u16 ? rs[0] : rs[2], ca = u16 ? rc[0] : rc[2];
+                float sb = u16 ? rs[1] : rs[3], cb = u16 ? rc[1] : rc[3];
+                float ka = u16 ? rs[2] : rs[0], kc = u16 ? rc[2] : rc[0];
+                float kb = u16 ? rs[3] : rs[1], kd = u16 ? rc[3] : rc[1];
+                sa = __shfl_xor_sync(0xffffffffu, sa, 16);
+                ca = __shfl_xor_sync(0xffffffffu, ca, 16);
+                sb = __shfl_xor_sync(0xffffffffu, sb, 16);
+                cb = __shfl_xor_sync(0xffffffffu, cb, 16);
+                df_add(ka, kc, sa, ca);   // row 0 (lower half) or 2 (upper)
+                df_add(kb, kd, sb, cb);   // row 1 or 3
+                float ss = u8 ? ka : kb, sc = u8 ? kc : kd;
+                float vs = u8 ? kb : ka, vc = u8 ? kd : kc;
+                ss = __shfl_xor_sync(0xffffffffu, ss, 8);
+                sc = __shfl_xor_sync(0xffffffffu, sc, 8);
+                df_add(vs, vc, ss, sc);
+#pragma unroll
+                for (int o = 4; o > 0; o >>= 1) {
+                    const float s2 = __shfl_xor_sync(0xffffffffu, vs, o);
+                    const float c2 = __shfl_xor_sync(0xffffffffu, vc, o);
+                    df_add(vs, vc, s2, c2);
+                }
+                if ((lane & 7) == 0) red[parity][2 * (lane >> 4) + ((lane >> 3) & 1)][wid] = make_float2(vs, vc);
+            }
+            __syncthreads();   // the stage is consumed, the batch's row sums are in red
+            if (s_stop) break;
+            if (tid == 0 && b + kBS < nbat) issue(b + kBS);
+            if (tid < kBR && i0 + tid < r1) {
                 float s = 0.0f, c = 0.0f;
 #pragma unroll
-                for (int w = 0; w < NT / 32; ++w) df_add(s, c, red[parity][tid][w].x, red[parity][tid][w].y);
+                for (int w = 0; w < kW; ++w) df_add(s, c, red[parity][tid][w].x, red[parity][tid][w].y);
                 const double v = (double)s + (double)c;
                 out[i0 + tid] = cp == 0 ? v : out[i0 + tid] + v;
             }
             parity ^= 1;   // the other slot set next batch: one barrier per batch
         }
+        if (s_stop) return;
+        gb += nbat;
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int64_t c = p[h] + q;
-                if (c < n) partial[(size_t)blockIdx.x * n + c] = cacc[4 * h + q] + (double)cs[4 * h + q] + (double)cc[4 * h + q];
-            }
+        for (int q = 0; q < 4; ++q) {
+            const int64_t c = p0 + q;
+            if (c < n)
+                partial[(size_t)blockIdx.x * n + c] =
+                    cacc[q] + (double)CS[q] + (double)CC[q] + (double)cs[q] + (double)cc[q];
+        }
     }
 }
 
@@ -315,10 +415,10 @@ __global__ void __launch_bounds__(NT) k_gemv_rows_f32(const float *__restrict__ 
 
 // out_rows = A x, out_cols = A^T y in one pass (double-float); xs: n float2,
 // ys: m float2 of scratch; partial: kRedBlocks x n doubles (at most one row
-// per SM is used)
+// per SM is used); err: device int set to 1 when a bounded wait expires
 void launch_gemv_both_df(cudaStream_t s, const float *Ahi, const float *Alo, int64_t m, int64_t n, int64_t lda,
                          const double *x, const double *y, float2 *xs, float2 *ys, double *partial,
-                         double *out_rows, double *out_cols) {
+                         double *out_rows, double *out_cols, int *err) {
     if (n <= 0) {
         if (m > 0) MDSIP_CUDA(cudaMemsetAsync(out_rows, 0, m * sizeof(double), s));
         return;
@@ -333,12 +433,16 @@ void launch_gemv_both_df(cudaStream_t s, const float *Ahi, const float *Alo, int
     MDSIP_LAUNCHED();
     k_split_vector<<<(unsigned)std::min<int64_t>(4096, (m + NT - 1) / NT), NT, 0, s>>>(y, m, ys);
     MDSIP_LAUNCHED();
-    // one CTA per SM (the batch's loads take most of the registers)
+    // one CTA per SM (the staging ring takes most of the shared memory)
     int dev = 0, sms = 0;
     MDSIP_CUDA(cudaGetDevice(&dev));
     MDSIP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int grid = std::max(1, std::min(sms, kRedBlocks));
-    k_gemv_both_df<<<grid, NT, 0, s>>>(Ahi, Alo, m, n, lda, xs, ys, out_rows, partial);
+    static PerDeviceOnce once;
+    MDSIP_CUDA(once.run([] {
+        return cudaFuncSetAttribute(k_gemv_both_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBothSmem);
+    }));
+    k_gemv_both_df<<<grid, kBothThreads, kBothSmem, s>>>(Ahi, Alo, m, n, lda, xs, ys, out_rows, partial, err);
     MDSIP_LAUNCHED();
     launch_colsum(s, partial, grid, n, out_cols);
 }

@@ -327,7 +327,7 @@ void launch_gemv_t_df(cudaStream_t s, const float *Ahi, const float *Alo, int64_
 // out_rows = A x and out_cols = A^T y from one read of A
 void launch_gemv_both_df(cudaStream_t s, const float *Ahi, const float *Alo, int64_t m, int64_t n, int64_t lda,
                          const double *x, const double *y, float2 *xs, float2 *ys, double *partial,
-                         double *out_rows, double *out_cols);
+                         double *out_rows, double *out_cols, int *err);
 // out = A_hi x with FP32 products and sums
 void launch_gemv_rows_f32(cudaStream_t s, const float *Ahi, int64_t m, int64_t n, int64_t lda, const double *x,
                           double *out);

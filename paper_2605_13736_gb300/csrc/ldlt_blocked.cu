@@ -1582,66 +1582,84 @@ __device__ void persist_rank_q(float *Rb, const float *s_rc, int c0, int nb, boo
     __syncthreads();
 }
 
-// The 64 x 64 block of the lower triangle at rows i0.., columns c0.. of the
-// FP32 copy: Af(i, c) -= sum_{t < kb} Lf(i, t) Wf(c, t) for i >= c.
-// smem: 2 x 64 x 64 floats.
+// The TE x TE block (TE = 64 or 32) of the lower triangle at rows i0..,
+// columns c0.. of the FP32 copy: Af(i, c) -= sum_{t < kb} Lf(i, t) Wf(c, t)
+// for i >= c.  256 threads, (TE / 16)^2 outputs each; smem: 2 x 64 x TE floats.
+template <int P>
+__device__ __forceinline__ void load_p(const float *p, float (&v)[P]) {
+    if constexpr (P == 4) {
+        const float4 x = *reinterpret_cast<const float4 *>(p);
+        v[0] = x.x;
+        v[1] = x.y;
+        v[2] = x.z;
+        v[3] = x.w;
+    } else {
+        const float2 x = *reinterpret_cast<const float2 *>(p);
+        v[0] = x.x;
+        v[1] = x.y;
+    }
+}
+
+template <int TE>
 __device__ void block_update_f32(int i0, int c0, int N, int kb, float *__restrict__ Af,
                                  const float *__restrict__ Lf, const float *__restrict__ Wf,
                                  unsigned char *usmem) {
-    float *Lt = reinterpret_cast<float *>(usmem);   // [64][64]: Lt[t][r]
-    float *Wt = Lt + 64 * kUT;                      // [64][64]: Wt[t][c]
+    constexpr int P = TE / 16;      // outputs per thread along rows and along columns
+    constexpr int RS = 256 / TE;    // panel columns staged per pass of the threads
+    float *Lt = reinterpret_cast<float *>(usmem);   // [64][TE]: Lt[t][r]
+    float *Wt = Lt + 64 * TE;                       // [64][TE]: Wt[t][c]
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    // this thread's 16 entries of the tile, loaded ahead of the products
-    float cur[4][4];
+    // this thread's entries of the block, loaded ahead of the products
+    float cur[P][P];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const int c = c0 + 4 * ty + v;
+    for (int v = 0; v < P; ++v) {
+        const int c = c0 + P * ty + v;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = i0 + 4 * tx + u;
+        for (int u = 0; u < P; ++u) {
+            const int i = i0 + P * tx + u;
             cur[u][v] = (i < N && c < N && i >= c) ? Af[i + (int64_t)c * N] : 0.0f;
         }
     }
     {
-        const int r = tid & (kUT - 1), t0 = tid >> 6;
+        const int r = tid % TE, t0 = tid / TE;
         const int i = i0 + r, c = c0 + r;
-        float lv[16], wv[16];
+        float lv[64 / RS], wv[64 / RS];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int t = t0 + 4 * j;
+        for (int j = 0; j < 64 / RS; ++j) {
+            const int t = t0 + RS * j;
             lv[j] = (t < kb && i < N) ? Lf[i + (int64_t)t * N] : 0.0f;
             wv[j] = (t < kb && c < N) ? Wf[c + (int64_t)t * N] : 0.0f;
         }
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int t = t0 + 4 * j;
-            Lt[t * kUT + r] = lv[j];
-            Wt[t * kUT + r] = wv[j];
+        for (int j = 0; j < 64 / RS; ++j) {
+            const int t = t0 + RS * j;
+            Lt[t * TE + r] = lv[j];
+            Wt[t * TE + r] = wv[j];
         }
     }
     __syncthreads();
-    float acc[4][4];
+    float acc[P][P];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < P; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+        for (int v = 0; v < P; ++v) acc[u][v] = 0.0f;
     for (int t = 0; t < kb; ++t) {
-        float lv[4], wv[4];
-        load4(Lt + t * kUT + 4 * tx, lv);
-        load4(Wt + t * kUT + 4 * ty, wv);
+        float lv[P], wv[P];
+        load_p<P>(Lt + t * TE + P * tx, lv);
+        load_p<P>(Wt + t * TE + P * ty, wv);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < P; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(lv[u], wv[v], acc[u][v]);
+            for (int v = 0; v < P; ++v) acc[u][v] = fmaf(lv[u], wv[v], acc[u][v]);
     }
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const int c = c0 + 4 * ty + v;
+    for (int v = 0; v < P; ++v) {
+        const int c = c0 + P * ty + v;
         if (c >= N) continue;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = i0 + 4 * tx + u;
+        for (int u = 0; u < P; ++u) {
+            const int i = i0 + P * tx + u;
             if (i < N && i >= c) Af[i + (int64_t)c * N] = cur[u][v] - acc[u][v];
         }
     }
@@ -1700,7 +1718,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist32(PersistArgs a) {
         const int buf = p % 3;                       // column maxima of this panel
         float *Lfp = (p & 1) ? a.Lf2 : a.Lf, *Wfp = (p & 1) ? a.Wf2 : a.Wf;
         // this panel's columns have taken every earlier panel's update
-        if (p > 0 && !wait_count(&a.colcnt[kblk], (unsigned)(nbk - kblk), a.bar, a.wait_ns)) return;
+        if (p > 0 && !wait_count(&a.colcnt[kblk], 4u * (unsigned)(nbk - kblk), a.bar, a.wait_ns)) return;
         if (tid < 64) {
             s_cmax_blk[tid] = s_cmax_own[tid] = 0u;
             s_rc[tid] = 0.0f;
@@ -1808,35 +1826,35 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist32(PersistArgs a) {
             return;
         }
         if (k + nb >= N) break;
-        // ---------------- trailing update on the FP32 copy.  The panel's blocks
-        // are numbered with those of the next panel's columns first (n1 of
-        // them, counted as they finish: the next panel starts when its column
-        // is complete) and the rest after (row-major over their triangle);
-        // CTA g takes numbers g, g + G, ...  Every block's update of the
-        // previous panel finished before this panel's grid barrier, so any
-        // CTA may take any block.
+        // ---------------- trailing update on the FP32 copy.  The next panel's
+        // column of 64 x 64 blocks goes first, as 4 n1 quarter blocks (it is
+        // on the critical path: the next panel starts when all of them have
+        // counted themselves done), then the other blocks whole (row-major over
+        // their triangle); CTA g takes items g, g + G, ...  Every block's update
+        // of the previous panel finished before this panel's grid barrier, so
+        // any CTA may take any block.
         {
             const int n1 = nbk - kblk - 1, m2 = nbk - kblk - 2;
-            const int nblocks = n1 + (m2 > 0 ? m2 * (m2 + 1) / 2 : 0);
-            for (int b = g; b < nblocks; b += G) {
-                int I, J;
-                if (b < n1) {
-                    I = kblk + 1 + b;
-                    J = kblk + 1;
-                } else {
-                    const int lin = b - n1;
-                    int r = (int)((sqrtf(8.0f * (float)lin + 1.0f) - 1.0f) * 0.5f);
-                    while ((r + 1) * (r + 2) / 2 <= lin) ++r;
-                    while (r * (r + 1) / 2 > lin) --r;
-                    I = kblk + 2 + r;
-                    J = kblk + 2 + (lin - r * (r + 1) / 2);
-                }
-                block_update_f32(64 * I, 64 * J, N, nb, a.Af, Lfp, Wfp, psm);
+            const int nitems = 4 * n1 + (m2 > 0 ? m2 * (m2 + 1) / 2 : 0);
+            int b = g;
+            for (; b < nitems && b < 4 * n1; b += G) {
+                const int I = kblk + 1 + (b >> 2), J = kblk + 1, q = b & 3;
+                const int i0 = 64 * I + 32 * (q >> 1), c0 = 64 * J + 32 * (q & 1);
+                if (i0 + 31 >= c0) block_update_f32<32>(i0, c0, N, nb, a.Af, Lfp, Wfp, psm);
                 __syncthreads();
-                if (b < n1 && tid == 0) {
+                if (tid == 0) {
                     __threadfence();
                     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&a.colcnt[J]) : "memory");
                 }
+            }
+            for (; b < nitems; b += G) {   // whole blocks
+                const int lin = b - 4 * n1;
+                int r = (int)((sqrtf(8.0f * (float)lin + 1.0f) - 1.0f) * 0.5f);
+                while ((r + 1) * (r + 2) / 2 <= lin) ++r;
+                while (r * (r + 1) / 2 > lin) --r;
+                const int I = kblk + 2 + r, J = kblk + 2 + (lin - r * (r + 1) / 2);
+                block_update_f32<64>(64 * I, 64 * J, N, nb, a.Af, Lfp, Wfp, psm);
+                __syncthreads();
             }
         }
     }

@@ -246,7 +246,7 @@ void Refiner::residual(const double *b, const double *u, double dw, double dc, d
     const double *Au = Au_run;
     if (Ahi) {   // A u_d and A^T u_g from one double-float pass
         launch_gemv_both_df(st, Ahi, Alo, D.m_E, D.n_d, D.lda, u + D.n_s, u + D.n, split, split + D.n_d, colpart,
-                            tmp_m, tmp_nd);
+                            tmp_m, tmp_nd, solve_err);
         Au = tmp_m;
     } else {
         launch_gemv_t(st, M.A, D.m_E, D.n_d, D.lda, u + D.n, colpart, tmp_nd);   // A^T u_g

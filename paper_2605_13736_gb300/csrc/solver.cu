@@ -996,7 +996,8 @@ static void check_solve_flag(Problem *P) {
     MDSIP_CUDA(cudaMemcpyAsync(P->hint + 6, P->bsolve_err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost,
                                P->ctx->stream));
     MDSIP_CUDA(cudaStreamSynchronize(P->ctx->stream));
-    MDSIP_REQUIRE(P->hint[6] == 0, MDSIP_ERR_DEVICE, "LDL^T solve: a bounded device wait expired");
+    MDSIP_REQUIRE(P->hint[6] == 0, MDSIP_ERR_DEVICE,
+                  "LDL^T solve or residual pass: a bounded device wait expired");
 }
 
 static RefineResult direction_step_(Problem *P, double mu, double dw, double dc, bool fp64, Inertia *used);
@@ -1830,14 +1831,20 @@ mdsip_status mdsip_gemv_pair_df(mdsip_ctx *hctx, int64_t m, int64_t n, const dou
         const size_t nA = (size_t)m * (size_t)lda;
         const size_t o_lo = up(nA * sizeof(float)), o_xs = o_lo + up(nA * sizeof(float));
         const size_t o_ys = o_xs + up((size_t)n * sizeof(float2)), o_part = o_ys + up((size_t)m * sizeof(float2));
-        const size_t total = o_part + up((size_t)kRedBlocks * (size_t)n * sizeof(double));
+        const size_t o_err = o_part + up((size_t)kRedBlocks * (size_t)n * sizeof(double));
+        const size_t total = o_err + 256;
         char *base = static_cast<char *>(ctx->scratch_at_least(total));
         float *hi = reinterpret_cast<float *>(base), *lo = reinterpret_cast<float *>(base + o_lo);
+        int *err = reinterpret_cast<int *>(base + o_err);
+        MDSIP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
         if (m > 0 && n > 0) launch_split_matrix(ctx->stream, A, m, n, lda, hi, lo);
         launch_gemv_both_df(ctx->stream, hi, lo, m, n, lda, x, v, reinterpret_cast<float2 *>(base + o_xs),
                             reinterpret_cast<float2 *>(base + o_ys), reinterpret_cast<double *>(base + o_part), Ax,
-                            ATv);
+                            ATv, err);
+        int herr = 0;
+        MDSIP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
         MDSIP_CUDA(cudaStreamSynchronize(ctx->stream));
+        MDSIP_REQUIRE(herr == 0, MDSIP_ERR_DEVICE, "gemv_pair_df: a bounded device wait expired");
     });
 }
 
