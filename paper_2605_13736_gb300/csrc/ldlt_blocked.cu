@@ -1413,13 +1413,13 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist(PersistArgs a) {
 // as k_bk_persist, with the arithmetic of the loop in FP32 only:
 //   - the prologue copies the lower triangle of S into Af (FP32, ld N); the
 //     trailing updates run on Af in place, and the FP64 matrix keeps S;
-//   - each 64-column panel is factored in two 32-column sub-panels.  A warp
-//     holds the sub-panel's 32 diagonal-block rows (lane = row) and 32 rows
-//     below them (lane = row) in registers and runs the 32-step pivot chain
-//     with warp shuffles; every warp repeats the short diagonal chain for its
-//     own rows, so no barrier is needed per column.  A rank-32 update
-//     (2 x 4 outputs per thread, from shared memory) brings the second
-//     sub-panel's columns up to date;
+//   - each 64-column panel is factored in Q-column sub-panels (Q = 16).  A
+//     warp holds the sub-panel's Q diagonal-block rows (lane = row) and 32
+//     rows below them (lane = row) in registers and runs the Q-step pivot
+//     chain, each step's column broadcast through shared memory; every warp
+//     repeats the short diagonal chain for its own rows, so no block barrier
+//     is needed per column.  A rank-Q update (2 x 4 outputs per thread, from
+//     shared memory) brings the later columns up to date;
 //   - the FP64 pivot is the chain's FP32 value plus the part of S's diagonal
 //     that the FP32 copy dropped; L (FP64 copy), W and the column maxima come
 //     from the FP32 chain values.
@@ -1432,9 +1432,11 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist(PersistArgs a) {
 // CTA writes the FP32 updates of the trailing matrix back into the FP64
 // matrix (A += Af - fl32(A)) before the pivoting panels take over.
 // ---------------------------------------------------------------------------
-// Sub-panel width Q (16 or 32): a warp holds the Q diagonal-block rows of a
-// sub-panel and 32 rows below them.  Own rows staged per pass: what the warps
-// left after the block's target groups take (at most 8 groups in all).
+// Sub-panel width Q (16 or 32; 16 measured faster: 32-step chains are twice
+// as long per column and the rank updates do not shrink in proportion): a
+// warp holds the Q diagonal-block rows of a sub-panel and 32 rows below
+// them.  Own rows staged per pass: what the warps left after the block's
+// target groups take (at most 8 groups in all).
 constexpr int kPersistQ = 16;   // sub-panel width of the FP32-update kernel
 template <int Q> constexpr int own_rows() { return (8 - (64 - Q + 31) / 32) * 32; }
 constexpr int kRowsBuf = 64 + own_rows<32>();   // the larger of the two (224 own rows)
