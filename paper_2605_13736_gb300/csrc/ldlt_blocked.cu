@@ -37,6 +37,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "tc.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -1667,6 +1668,108 @@ __device__ void block_update_f32(int i0, int c0, int N, int kb, float *__restric
     }
 }
 
+// Two vertically adjacent 64 x 64 blocks of the trailing update on the tensor
+// cores: rows i0 .. i0 + 127, columns c0 .. c0 + 63 of the FP32 copy,
+// Af(i, c) -= sum_{t < 64} Lf(i, t) Wf(c, t) for i >= c.  One tcgen05.mma of
+// shape 128 x 64 per 8-wide K step (kind::tf32), in three products
+// (hi hi + hi lo + lo hi, x = hi + lo with hi = x cut to the TF32 mantissa):
+// about 2^-21 relative per product, the FP32 accuracy of the CUDA-core form,
+// instead of TF32's 2^-11.  All 256 threads stage L and W in shared memory in
+// the 128-byte-swizzled K-major layout; one thread issues the 24 MMAs into a
+// 64-column FP32 accumulator in TMEM and commits them to an mbarrier; the
+// eight warps read the accumulator back (warp w: TMEM lanes 32 (w mod 4) ..,
+// columns 32 (w / 4) ..) and write Af.  Returns false when the bounded wait
+// for the MMAs expires.
+constexpr int kTcA = 128 * 128;   // bytes per K slab of the 128 L rows (32 floats per row)
+constexpr int kTcB = 64 * 128;    // bytes per K slab of the 64 W rows
+constexpr size_t kTcSmem = 2 * 2 * (size_t)kTcA + 2 * 2 * (size_t)kTcB + 1024;   // hi and lo, two slabs each, alignment
+
+__device__ __forceinline__ uint32_t sw128_off(int r, int chunk) {
+    return (uint32_t)(r * 128 + (((chunk ^ r) & 7) << 4));
+}
+
+__device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
+    hi = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+    lo = x - hi;
+}
+
+__device__ bool pair_update_tc(int i0, int c0, int N, float *__restrict__ Af, const float *__restrict__ Lf,
+                               const float *__restrict__ Wf, unsigned char *usmem, uint32_t tmem, uint64_t *bar,
+                               uint32_t &phase) {
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(usmem) + 1023) & ~uintptr_t(1023));
+    unsigned char *Ahi = base, *Alo = Ahi + 2 * kTcA, *Bhi = Alo + 2 * kTcA, *Blo = Bhi + 2 * kTcB;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    // stage: L rows (128 x 16 chunks of 4 K values), W rows (64 x 16 chunks)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int r = tid & 127, ch = (tid >> 7) + 2 * j;
+        const int i = i0 + r;
+        float h[4], l[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) tf32_split(i < N ? Lf[i + (int64_t)(4 * ch + u) * N] : 0.0f, h[u], l[u]);
+        const uint32_t off = (uint32_t)(ch >> 3) * kTcA + sw128_off(r, ch & 7);
+        *reinterpret_cast<float4 *>(Ahi + off) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4 *>(Alo + off) = make_float4(l[0], l[1], l[2], l[3]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int r = tid & 63, ch = (tid >> 6) + 4 * j;
+        const int c = c0 + r;
+        float h[4], l[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) tf32_split(c < N ? Wf[c + (int64_t)(4 * ch + u) * N] : 0.0f, h[u], l[u]);
+        const uint32_t off = (uint32_t)(ch >> 3) * kTcB + sw128_off(r, ch & 7);
+        *reinterpret_cast<float4 *>(Bhi + off) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4 *>(Blo + off) = make_float4(l[0], l[1], l[2], l[3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the tensor core reads what the threads wrote
+    __syncthreads();
+    if (tid == 0) {
+        tc::fence_after();
+        constexpr uint32_t kIdesc = tc::instr_desc(true, 128, 64);
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {   // four K steps of 8 TF32 values (32 bytes) per slab
+                const uint32_t ao = (uint32_t)s * kTcA + 32 * k, bo = (uint32_t)s * kTcB + 32 * k;
+                const uint64_t ah = tc::sw128_kmajor_desc(tc::smem_u32(Ahi + ao));
+                const uint64_t al = tc::sw128_kmajor_desc(tc::smem_u32(Alo + ao));
+                const uint64_t bh = tc::sw128_kmajor_desc(tc::smem_u32(Bhi + bo));
+                const uint64_t bl = tc::sw128_kmajor_desc(tc::smem_u32(Blo + bo));
+                tc::mma<true, kIdesc>(tmem, ah, bh, (s > 0 || k > 0) ? 1u : 0u);
+                tc::mma<true, kIdesc>(tmem, ah, bl, 1u);
+                tc::mma<true, kIdesc>(tmem, al, bh, 1u);
+            }
+        tc::commit(bar);
+    }
+    __syncwarp();
+    const bool ok = tc::mbar_wait(bar, phase);
+    phase ^= 1u;
+    tc::fence_after();
+    if (ok) {
+        const int q = wid & 3, h = wid >> 2;
+        uint32_t v[32];
+        tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h), v);
+        const int i = i0 + 32 * q + lane;
+        if (i < N) {
+            float cur[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int c = c0 + 32 * h + j;
+                cur[j] = (c < N && i >= c) ? Af[i + (int64_t)c * N] : 0.0f;
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int c = c0 + 32 * h + j;
+                if (c < N && i >= c) Af[i + (int64_t)c * N] = cur[j] - __uint_as_float(v[j]);
+            }
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    return ok;
+}
+
 template <int Q>
 __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist32(PersistArgs a) {
     constexpr int kOwn = own_rows<Q>();
@@ -1679,12 +1782,31 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist32(PersistArgs a) {
     // (written by the one warp that outputs the column) and this CTA's rows
     // (one warp per column): plain stores, no shared atomics
     __shared__ unsigned s_cmax_blk[64], s_cmax_own[64];
+    __shared__ __align__(8) uint64_t s_mma_bar;   // completion of a trailing block pair's MMAs
+    __shared__ uint32_t s_tmem;
     const int N = a.N, G = (int)gridDim.x, g = (int)blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, wid = tid >> 5;
     constexpr int kWarps = kPThreads / 32;
     const double ztol = a.zero_tol * __ldg(a.maxabs);
     const int kstart = a.st->k;
     unsigned epoch = 0;   // grid barriers passed (thread 0)
+    // 64 TMEM columns for the trailing block pairs' accumulator (one CTA per SM),
+    // released on every way out
+    if (tid == 0) {
+        tc::mbar_init(&s_mma_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (wid == 0) tc::tmem_alloc(&s_tmem, 64);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = s_tmem;
+    uint32_t mma_phase = 0;
+    auto release = [&]() {
+        tc::fence_before();
+        __syncthreads();
+        if (wid == 0) tc::tmem_dealloc(tmem, 64);
+    };
     // prologue: the FP32 copy of columns kstart .. N - 1 (whole columns: the
     // entries above the diagonal are copied too and never read), eight
     // 16-byte loads in flight per thread
@@ -1711,7 +1833,10 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist32(PersistArgs a) {
         }
     }
     __threadfence();
-    if (!panel_barrier(a.bar, epoch, a.wait_ns)) return;
+    if (!panel_barrier(a.bar, epoch, a.wait_ns)) {
+        release();
+        return;
+    }
     const int nbk = (N + 63) / 64;   // 64 x 64 blocks per row / column
     int p = 0;
     for (int k = kstart; k < N; k += 64, ++p) {
@@ -1720,7 +1845,10 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist32(PersistArgs a) {
         const int buf = p % 3;                       // column maxima of this panel
         float *Lfp = (p & 1) ? a.Lf2 : a.Lf, *Wfp = (p & 1) ? a.Wf2 : a.Wf;
         // this panel's columns have taken every earlier panel's update
-        if (p > 0 && !wait_count(&a.colcnt[kblk], 4u * (unsigned)(nbk - kblk), a.bar, a.wait_ns)) return;
+        if (p > 0 && !wait_count(&a.colcnt[kblk], 4u * (unsigned)(nbk - kblk), a.bar, a.wait_ns)) {
+            release();
+            return;
+        }
         if (tid < 64) {
             s_cmax_blk[tid] = s_cmax_own[tid] = 0u;
             s_rc[tid] = 0.0f;
@@ -1811,7 +1939,10 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist32(PersistArgs a) {
             const unsigned bm = max(s_cmax_blk[tid], s_cmax_own[tid]);
             if (bm) atomicMax(&a.cmax[buf * 64 + tid], absbits64((double)__uint_as_float(bm)));
         }
-        if (!panel_barrier(a.bar, epoch, a.wait_ns)) return;
+        if (!panel_barrier(a.bar, epoch, a.wait_ns)) {
+            release();
+            return;
+        }
         if (!persist_keep(a, k, nb, buf, (p + 2) % 3, ztol, s_d)) {
             // hand over at column k: the FP64 matrix takes the FP32 updates
             for (int c = k + g; c < N; c += G)
@@ -1825,19 +1956,31 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist32(PersistArgs a) {
                 a.st->kb = 0;
                 a.st->spec = 0;
             }
+            release();
             return;
         }
         if (k + nb >= N) break;
         // ---------------- trailing update on the FP32 copy.  The next panel's
-        // column of 64 x 64 blocks goes first, as 4 n1 quarter blocks (it is
-        // on the critical path: the next panel starts when all of them have
-        // counted themselves done), then the other blocks whole (row-major over
-        // their triangle); CTA g takes items g, g + G, ...  Every block's update
-        // of the previous panel finished before this panel's grid barrier, so
-        // any CTA may take any block.
+        // column of 64 x 64 blocks goes first, as 4 n1 quarter blocks on the CUDA
+        // cores (it is on the critical path: the next panel starts when all of
+        // them have counted themselves done), then the other blocks: in
+        // vertically adjacent pairs on the tensor cores, column by column,
+        // while there are more than four blocks per CTA; else one per item on
+        // the CUDA cores (a pair's staging and read-back cost about as much as
+        // two blocks' FMAs, so pairs pay only where they halve the number of
+        // items a CTA works through: measured at N = 2050 0.85 ms with blocks
+        // against 0.88 ms with pairs, at N = 8003 11.4 against 9.9 ms).
+        // CTA g takes items g, g + G, ...  Every block's update of the previous
+        // panel finished before this panel's grid barrier, so any CTA may take
+        // any block.
         {
             const int n1 = nbk - kblk - 1, m2 = nbk - kblk - 2;
-            const int nitems = 4 * n1 + (m2 > 0 ? m2 * (m2 + 1) / 2 : 0);
+            const int nwhole = m2 > 0 ? m2 * (m2 + 1) / 2 : 0;
+            const bool pairs = nwhole > 4 * G;
+            int npairs = 0;
+            if (pairs)
+                for (int J = kblk + 2; J < nbk; ++J) npairs += (nbk - J + 1) / 2;
+            const int nitems = 4 * n1 + (pairs ? npairs : nwhole);
             int b = g;
             for (; b < nitems && b < 4 * n1; b += G) {
                 const int I = kblk + 1 + (b >> 2), J = kblk + 1, q = b & 3;
@@ -1849,17 +1992,34 @@ __global__ void __launch_bounds__(kPThreads, 1) k_bk_persist32(PersistArgs a) {
                     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&a.colcnt[J]) : "memory");
                 }
             }
-            for (; b < nitems; b += G) {   // whole blocks
-                const int lin = b - 4 * n1;
-                int r = (int)((sqrtf(8.0f * (float)lin + 1.0f) - 1.0f) * 0.5f);
-                while ((r + 1) * (r + 2) / 2 <= lin) ++r;
-                while (r * (r + 1) / 2 > lin) --r;
-                const int I = kblk + 2 + r, J = kblk + 2 + (lin - r * (r + 1) / 2);
-                block_update_f32<64>(64 * I, 64 * J, N, nb, a.Af, Lfp, Wfp, psm);
-                __syncthreads();
+            if (!pairs) {
+                for (; b < nitems; b += G) {   // whole blocks, row-major over their triangle
+                    const int lin = b - 4 * n1;
+                    int r = (int)((sqrtf(8.0f * (float)lin + 1.0f) - 1.0f) * 0.5f);
+                    while ((r + 1) * (r + 2) / 2 <= lin) ++r;
+                    while (r * (r + 1) / 2 > lin) --r;
+                    const int I = kblk + 2 + r, J = kblk + 2 + (lin - r * (r + 1) / 2);
+                    block_update_f32<64>(64 * I, 64 * J, N, nb, a.Af, Lfp, Wfp, psm);
+                    __syncthreads();
+                }
+            } else {
+                int J = kblk + 2, first = 4 * n1;   // first item of column J
+                for (; b < nitems; b += G) {
+                    while (J < nbk - 1 && (b - first) >= (nbk - J + 1) / 2) {
+                        first += (nbk - J + 1) / 2;
+                        ++J;
+                    }
+                    const int I0 = J + 2 * (b - first);
+                    if (!pair_update_tc(64 * I0, 64 * J, N, a.Af, Lfp, Wfp, psm, tmem, &s_mma_bar, mma_phase)) {
+                        if (tid == 0) atomicExch(&a.bar->err, 1);
+                        release();
+                        return;
+                    }
+                }
             }
         }
     }
+    release();
 }
 
 __global__ void k_bk_init(int N, int32_t *perm, PanelState *st, unsigned long long *cmax, PanelBar *bar,
@@ -2025,7 +2185,7 @@ PanelBar *grid_bar(char *w, const BlockedScratch &lay) { return reinterpret_cast
 template <typename T>
 size_t persist_smem() {
     if constexpr (sizeof(T) == sizeof(float))   // k_bk_persist32: staged rows, or a trailing tile's panel rows
-        return std::max((size_t)kRowsBuf * kPP * sizeof(float), 2 * (size_t)64 * kUT * sizeof(float));
+        return std::max({(size_t)kRowsBuf * kPP * sizeof(float), 2 * (size_t)64 * kUT * sizeof(float), kTcSmem});
     return std::max(2 * (size_t)64 * kPP * sizeof(T), 2 * (size_t)65 * kUT * sizeof(T));
 }
 
