@@ -386,8 +386,11 @@ mdsip_status mdsip_ldlt_factor(mdsip_ctx *ctx, int64_t N, double *S, int64_t ld,
  * the no-interchange panels of either precision run in one persistent
  * cooperative kernel that stops at the first panel the rule would not keep;
  * the pivoting panels take over from there (beyond the pivoting panel's
- * limit such a panel is an INVALID_ARG error).  The call then reads a status
- * word back, so it synchronises the context's stream. */
+ * limit such a panel is an INVALID_ARG error).  With FP32 updates that
+ * kernel works on an FP32 copy of S (the FP32 updates are written back into
+ * S before a hand-over; large trailing matrices are updated on the tensor
+ * cores with a three-product TF32 split, about FP32 accuracy).  The call then
+ * reads a status word back, so it synchronises the context's stream. */
 #define MDSIP_LDLT_FP32_UPDATES 1
 #define MDSIP_LDLT_NO_SPECULATION 2
 #define MDSIP_LDLT_PERSISTENT 4
