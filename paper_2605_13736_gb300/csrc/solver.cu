@@ -115,6 +115,15 @@ struct Problem {
     DBuf bAfT, bvf, btc_ws, btc_err, bref_b, bref_u, bref_r, bref_d, btmp_nd2, bsolve_ws, bsolve_err, bAu_run;
     bool aft_ready = false;
     DBuf bAhi, bAlo, bsplit;   // A as an FP32 pair (mixed path's double-float passes) and vector scratch
+    // Products with A carried from step to step on the mixed path of a data-given
+    // problem, whose constraints are linear in x_d: A x_d of the iterate and of
+    // the trial, A dx_d and A^T dy_g of the direction (from the refinement's last
+    // residual pass); A^T y_g of the iterate lives in bATy.
+    DBuf bAx_a, bAx_b, bdAx, bdATy;
+    double *ax_cur = nullptr, *ax_t = nullptr;
+    bool lin_ax = false;    // ax_cur holds A x_d of the iterate
+    bool lin_aty = false;   // bATy holds A^T y_g of the iterate
+    bool dir_prod = false;  // bAdx / bATu hold A dx_d and A^T dy_g of the direction just computed
     bool df_ready = false;
     int64_t tc_prec = -1;
     DBuf bscal, bpartial, bcolpart, browtmp;
@@ -975,6 +984,9 @@ static RefineResult solve_direction_refined(Problem *P, double mu, double dw, do
         rprev = rinf;
     }
     out.ok = std::isfinite(out.res) && out.res <= P->opt.refine_fallback_tol;
+    // the loop ends right after a residual, whose double-float pass left A u_d in
+    // tmp_m and A^T u_g in tmp_nd for the final u: the direction's products
+    P->dir_prod = R.Ahi != nullptr;
     R.direction(P->I, P->Dir, u, mu, dw);
     MDSIP_CUDA(cudaEventRecord(P->ev[4], st));
     P->stats.n_refine += out.sweeps;
@@ -1030,10 +1042,21 @@ static RefineResult direction_step_(Problem *P, double mu, double dw, double dc,
 }
 
 // model derivatives and the Lagrangian gradient at the current point
+// (A^T y_g taken from bATy when it is carried for this iterate)
 static void eval_derivatives(Problem *P) {
     model_jac_hess(P, P->I.x, P->I.yg, P->I.yh);
+    if (P->lin_aty) {
+        P->V.lagrangian_grad_aty(P->I, P->grad, P->bJdh.as<double>(), P->bATy.as<double>(), P->bgl.as<double>());
+        return;
+    }
     P->V.lagrangian_grad(P->I, P->grad, P->bJdh.as<double>(), P->bATy.as<double>(), P->bgl.as<double>());
 }
+
+// Data-given problems on the mixed path: the constraints are linear in x_d and
+// the refinement's last residual pass forms A dx_d and A^T dy_g of the
+// direction anyway, so the line search's trial constraints (A x_t = A x +
+// alpha A dx) and the next iterate's A^T y_g need no pass over A.
+static bool carry_products(const Problem *P) { return P->model_kind == 0 && P->V.Ahi != nullptr && P->D.m_E > 0; }
 
 struct Errs {
     double E, dual, primal, comp;
@@ -1114,6 +1137,15 @@ static mdsip_status run_ipm(Problem *P) {
     double tau = std::max(o.tau_min, 1.0 - mu);
     model_f(P, P->I.x, P->grad, sc + SC_F);
     model_cons(P, P->I.x, P->I.d, P->cg, P->ch, sc + SC_THETA);
+    P->lin_ax = P->lin_aty = P->dir_prod = false;
+    if (carry_products(P)) {
+        P->ax_cur = P->bAx_a.get<double>(P->ctx, D.m_E);
+        P->ax_t = P->bAx_b.get<double>(P->ctx, D.m_E);
+        P->bdAx.get<double>(P->ctx, D.m_E);
+        P->bdATy.get<double>(P->ctx, std::max<int64_t>(D.n_d, 1));
+        P->V.copy(P->V.rowtmp, P->ax_cur, D.m_E);   // A x_d of the start, from the evaluation above
+        P->lin_ax = true;
+    }
     P->sync_scalars();
     double f = h[SC_F], th = h[SC_THETA];
     const double theta_max = o.theta_max_fact * std::max(1.0, th);
@@ -1126,6 +1158,7 @@ static mdsip_status run_ipm(Problem *P) {
 
     while (true) {
         eval_derivatives(P);
+        if (carry_products(P)) P->lin_aty = true;   // bATy now holds A^T y_g of this iterate
         P->V.errors(P->I, P->bgl.as<double>(), P->cg, P->ch, sc + SC_E);
         P->sync_scalars();
         Errs e0 = kkt_error(P, 0.0);
@@ -1179,6 +1212,7 @@ static mdsip_status run_ipm(Problem *P) {
         const double dw_last0 = dw_last;
         Inertia used{};
         RefineResult rr{};
+        P->dir_prod = false;
         while (true) {
             dw = 0.0;
             dc = 0.0;
@@ -1214,6 +1248,13 @@ static mdsip_status run_ipm(Problem *P) {
         rec.n_refine = rr.sweeps;
         rec.fp64_fallback = (rr.ok && !fp64) ? 0 : 1;
         rec.refine_res = rr.res;
+        // the direction's products with A, kept before anything else uses the
+        // refinement's buffers (the FP64 check below computes a direction of its own)
+        const bool lin_step = carry_products(P) && P->lin_ax && P->dir_prod;
+        if (lin_step) {
+            P->V.copy(P->bAdx.as<double>(), P->bdAx.as<double>(), D.m_E);
+            P->V.copy(P->bATu.as<double>(), P->bdATy.as<double>(), D.n_d);
+        }
         if (o.direction_check && use_refined(P) && P->opt.precision != MDSIP_PREC_FP64 && !fp64 && !rr.fell_back)
             rec.dir_err_fp64 = fp64_direction_error(P, mu, dw, dc);
         // A.5 line search
@@ -1246,7 +1287,12 @@ static mdsip_status run_ipm(Problem *P) {
         while (true) {
             P->V.trial(P->I, P->Dir, alpha, P->xt, P->dt, sc + SC_TRIAL);
             model_f(P, P->xt, P->grad_t, sc + SC_TF);
-            model_cons(P, P->xt, P->dt, P->cg_t, P->ch_t, sc + SC_TTHETA);
+            if (lin_step) {   // A x_t = A x + alpha A dx (the same trial point)
+                P->V.axpby(D.m_E, P->ax_cur, alpha, P->bdAx.as<double>(), P->ax_t);
+                P->V.eval_cons_ax(P->xt, P->ax_t, P->dt, P->cg_t, P->ch_t, sc + SC_TTHETA);
+            } else {
+                model_cons(P, P->xt, P->dt, P->cg_t, P->ch_t, sc + SC_TTHETA);
+            }
             P->sync_scalars();
             f_t = h[SC_TF];
             th_t = h[SC_TTHETA];
@@ -1292,6 +1338,14 @@ static mdsip_status run_ipm(Problem *P) {
         // A.6 accept: the trial becomes the iterate
         swap_trial(P);
         P->V.accept(P->I, P->Dir, alpha, alpha_z, mu, o.kappa_sigma);
+        if (lin_step) {   // y_g moved by alpha dy_g (k_accept): A^T y_g and A x_d follow
+            std::swap(P->ax_cur, P->ax_t);
+            P->V.axpby(D.n_d, P->bATy.as<double>(), alpha, P->bdATy.as<double>(), P->bATy.as<double>());
+        } else if (carry_products(P)) {   // the accepted trial's constraints were formed from x_t
+            P->V.copy(P->V.rowtmp, P->ax_cur, D.m_E);
+            P->lin_ax = true;
+            P->lin_aty = false;
+        }
         f = f_t;
         th = th_t;
         P->log.push_back(rec);
@@ -1357,6 +1411,7 @@ static void debug_direction(Problem *P, const double *packed, double mu, double 
     MDSIP_REQUIRE(P->bounds_set, MDSIP_ERR_INVALID_ARG, "bounds not set (mdsip_set_bounds)");
     model_f(P, P->I.x, P->grad, sc + SC_F);
     model_cons(P, P->I.x, P->I.d, P->cg, P->ch, sc + SC_THETA);
+    P->lin_ax = P->lin_aty = P->dir_prod = false;   // the carried products belong to a solve
     eval_derivatives(P);
     Inertia in = factor_attempt(P, dw, dc);
     const int64_t saved = P->opt.refine_max;

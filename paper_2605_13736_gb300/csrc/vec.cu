@@ -873,6 +873,28 @@ void VecOps::eval_cons(const double *x, const double *d, double *cg, double *ch,
     launch_finalize_max(st, partial + kRedBlocks, 1, out2 + 1);
 }
 
+void VecOps::eval_cons_ax(const double *x, const double *Ax, const double *d, double *cg, double *ch,
+                          double *out2) {
+    k_eval_cons<<<kRedBlocks, NT, 0, st>>>(D, M, x, Ax, d, cg, ch, partial);
+    MDSIP_LAUNCHED();
+    launch_finalize_sum(st, partial, 1, out2);
+    launch_finalize_max(st, partial + kRedBlocks, 1, out2 + 1);
+}
+
+namespace {
+__global__ void k_axpby(int64_t n, const double *__restrict__ a, double alpha, const double *__restrict__ b,
+                        double *__restrict__ y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = a[i] + alpha * b[i];
+}
+}  // namespace
+
+void VecOps::axpby(int64_t n, const double *a, double alpha, const double *b, double *y) {
+    if (n <= 0) return;
+    k_axpby<<<elem_grid(n), 256, 0, st>>>(n, a, alpha, b, y);
+    MDSIP_LAUNCHED();
+}
+
 void VecOps::jac_hess(const double *x, const double *yh, double *Jdh, double *Hss, double *Hdd) {
     k_jac_hess<<<elem_grid(std::max(D.n_s, D.n_d * D.n_d)), 256, 0, st>>>(D, M, x, yh, Jdh, Hss, Hdd);
     MDSIP_LAUNCHED();
@@ -882,6 +904,13 @@ void VecOps::lagrangian_grad(const IterView &I, const double *grad, const double
                              double *gl) {
     if (Ahi) launch_gemv_t_df(st, Ahi, Alo, D.m_E, D.n_d, D.lda, I.yg, split, colpart, ATy);
     else launch_gemv_t(st, M.A, D.m_E, D.n_d, D.lda, I.yg, colpart, ATy);
+    k_lagrangian_grad<<<elem_grid(std::max(D.n_s, D.n_d)), 256, 0, st>>>(D, M, grad, I.yg, I.yh, Jdh,
+                                                                         ATy, gl);
+    MDSIP_LAUNCHED();
+}
+
+void VecOps::lagrangian_grad_aty(const IterView &I, const double *grad, const double *Jdh, const double *ATy,
+                                 double *gl) {
     k_lagrangian_grad<<<elem_grid(std::max(D.n_s, D.n_d)), 256, 0, st>>>(D, M, grad, I.yg, I.yh, Jdh,
                                                                          ATy, gl);
     MDSIP_LAUNCHED();

@@ -29,9 +29,16 @@ struct VecOps {
 
     void eval_f(const double *x, double *grad, double *out_scalar);
     void eval_cons(const double *x, const double *d, double *cg, double *ch, double *out2);
+    // the same with A x_d given (Ax, m_E doubles) instead of formed from x
+    void eval_cons_ax(const double *x, const double *Ax, const double *d, double *cg, double *ch, double *out2);
+    // y = a + alpha b (n doubles)
+    void axpby(int64_t n, const double *a, double alpha, const double *b, double *y);
     void jac_hess(const double *x, const double *yh, double *Jdh, double *Hss, double *Hdd);
     void lagrangian_grad(const IterView &I, const double *grad, const double *Jdh, double *ATy,
                          double *gl);
+    // the same with ATy = A^T y_g already in place
+    void lagrangian_grad_aty(const IterView &I, const double *grad, const double *Jdh, const double *ATy,
+                             double *gl);
     void errors(const IterView &I, const double *gl, const double *cg, const double *ch,
                 double *out7);
     void newton_diag(const IterView &I, const double *Hss, double dw, double dc, bool want_w,
