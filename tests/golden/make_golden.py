@@ -33,7 +33,7 @@ CASES = {
     # 4x4 solve on small inputs) gives each direction
     "mds1_p2": dict(kind="config", k=1, linsolve="p2"),
     # member 2 (n_d=4000, n_s=400000, m_E=200000, m_I=50), condensed as above: the final objective
-    # the mixed-precision solves are judged against
+    # the mixed-precision solves are compared against
     "mds2_p2": dict(kind="config", k=2, linsolve="p2"),
 }
 
