@@ -113,6 +113,8 @@ def parse():
                     help="--kernel ldlt --fp32-update: every panel pivots (no verified no-interchange panels)")
     ap.add_argument("--persistent", action="store_true",
                     help="--kernel ldlt: the persistent no-interchange kernel at any order")
+    ap.add_argument("--refine-study", action="store_true",
+                    help="refinement convergence of the mixed-precision direction on --config (one JSON line)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--ldlt-matrix", choices=["kkt", "ipm"], default="kkt",
                     help="--kernel ldlt: kkt = [[H, J^T], [J, -I]] with J ~ N(0, 1) (pivots often); "
@@ -957,6 +959,84 @@ def run_batch_only(args):
                       "clocks": clk.summary(), "batched": b}))
 
 
+def run_refine_study(args):
+    """How the mixed-precision direction converges under refinement, on member
+    `--config`: at iterates 3, 9 and 14 of the FP64 trajectory, the relative
+    gap between the direction after k = 1 .. 4 sweeps (BF16 and TF32 factors,
+    stopping test off, no FP64 fallback) and the FP64 direction from the same
+    iterate; then BF16 solves with refine_tol 1e-14 (the default) and 1e-12:
+    sweeps, solve time, final residuals and the per-step gap to FP64."""
+    import numpy as np
+    import torch
+    import paper_2605_13736_gb300 as m
+    import synth
+    m.build()
+    torch.cuda.set_device(0)
+    inst = synth.make_config(args.config)
+    ctx = m.mdsip_ctx_create(0, torch.cuda.current_stream().cuda_stream)
+    prob = m.mdsip_problem_create_synthetic(ctx, **m.synth_arrays(inst))
+    del inst
+    psize = m.mdsip_packed_size(prob)
+    precs = (("bf16", m.MDSIP_PREC_BF16), ("tf32", m.MDSIP_PREC_TF32))
+    points, solves = [], []
+    try:
+        for it in (3, 9, 14):
+            m.mdsip_set_option_int(prob, "precision", m.MDSIP_PREC_FP64, ctx)
+            m.mdsip_set_start(prob, None)
+            m.mdsip_set_option_int(prob, "max_iter", it, ctx)
+            m.mdsip_solve(prob, ctx)
+            mu = m.mdsip_get_stats(prob)["mu"]
+            pk, d64 = np.zeros(psize), np.zeros(psize)
+            m.mdsip_get_iterate(prob, pk, m.MDSIP_MEM_HOST, ctx)
+            m.mdsip_debug_direction(prob, pk, mu, 0.0, 0.0, d64, ctx=ctx)
+            rec = {"iterate": it, "mu": mu}
+            for name, prec in precs:
+                m.mdsip_set_option_int(prob, "precision", prec, ctx)
+                m.mdsip_set_option_double(prob, "refine_tol", 0.0, ctx)
+                m.mdsip_set_option_double(prob, "refine_fallback_tol", 1.0, ctx)
+                gaps = []
+                for k in (1, 2, 3, 4):
+                    d = np.zeros(psize)
+                    m.mdsip_debug_direction(prob, pk, mu, 0.0, 0.0, d, refine=k, ctx=ctx)
+                    gaps.append(float(np.linalg.norm(d - d64) / np.linalg.norm(d64)))
+                rec[name + "_gap_after_k_sweeps"] = gaps
+            m.mdsip_set_option_double(prob, "refine_tol", 1e-14, ctx)
+            m.mdsip_set_option_double(prob, "refine_fallback_tol", 1e-10, ctx)
+            points.append(rec)
+        m.mdsip_set_option_int(prob, "precision", m.MDSIP_PREC_BF16, ctx)
+        for tol in (1e-14, 1e-12):
+            m.mdsip_set_option_double(prob, "refine_tol", tol, ctx)
+            m.mdsip_set_option_int(prob, "direction_check", 0, ctx)
+            m.mdsip_set_option_int(prob, "max_iter", 200, ctx)
+            m.mdsip_set_start(prob, None)
+            m.mdsip_solve(prob, ctx)   # warm: workspaces, tiles
+            m.mdsip_set_start(prob, None)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = m.mdsip_solve(prob, ctx)
+            e1.record()
+            torch.cuda.synchronize()
+            ss = m.mdsip_get_stats(prob)
+            log = m.mdsip_get_log(prob)
+            rec = {"refine_tol": tol, "status": m.STATUS[st], "iters": ss["iters"], "f": ss["f"],
+                   "solve_ms": e0.elapsed_time(e1), "sweeps_per_step": ss["n_refine"] / max(1, ss["iters"]),
+                   "refine_ms_per_step": ss["t_refine_ms"] / max(1, ss["iters"]),
+                   "final_residual_per_step": [r["refine_res"] for r in log[:-1]]}
+            m.mdsip_set_option_int(prob, "direction_check", 1, ctx)
+            m.mdsip_set_start(prob, None)
+            m.mdsip_solve(prob, ctx)
+            rec["gap_to_fp64_per_step"] = [r["dir_err_fp64"] for r in m.mdsip_get_log(prob)[:-1]]
+            solves.append(rec)
+        m.mdsip_set_option_double(prob, "refine_tol", 1e-14, ctx)
+        m.mdsip_set_option_int(prob, "direction_check", 0, ctx)
+    finally:
+        m.mdsip_problem_destroy(prob)
+        m.mdsip_ctx_destroy(ctx)
+    print(json.dumps({"study": "refinement sweeps", "workload": workload_name(args.config),
+                      "points": points, "solves": solves}))
+
+
 def run_kernel(args):
     """Kernel-level timing: `--kernel syrk` (A^T diag(1/w) A, FP64, m x n) or
     `--kernel ldlt` (Bunch-Kaufman LDL^T of an N x N KKT-like matrix)."""
@@ -1127,6 +1207,9 @@ def main():
         return
     if args.kernel:
         run_kernel(args)
+        return
+    if args.refine_study:
+        run_refine_study(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -355,6 +355,23 @@ mdsip_status mdsip_syrk_scaled_tc(mdsip_ctx *ctx, int64_t m, int64_t n, const do
 mdsip_status mdsip_gemv_pair_df(mdsip_ctx *ctx, int64_t m, int64_t n, const double *A, int64_t lda,
                                 const double *x, const double *v, double *Ax, double *ATv);
 
+/* The same pass with the first half of the refinement's next approximate
+ * solve folded in (the FP32 A^T product of the two-stage elimination of
+ * Section 2.3, whose input needs the whole row sum of A x).  Besides Ax and
+ * ATv as in mdsip_gemv_pair_df it writes
+ *   ATw[p] = sum_i A_hi[i][p] w[i],   A_hi = fl32(A),   w[i] = fl32(d[i] fl32(winv[i])),
+ * d[i] the difference cpre[i] - Ax[i] formed in double-float from cpre split
+ * into FP32 halves and the pass's own row sum, rounded to FP32
+ * (|d[i] - (cpre[i] - Ax[i])| <= 2^-23 |cpre[i] - Ax[i]| + 2^-46 |cpre[i]|);
+ * FP32 products and FP32 sums over blocks of at most ceil(m / number of SMs)
+ * consecutive rows, the block sums added in FP64.  cpre, winv: m; ATw: n; device pointers owned by the caller;
+ * 1 <= n <= 2048 (one slice of the pass holds a row).  Returns after the
+ * results are written.  Errors: as mdsip_gemv_pair_df, and INVALID_ARG for
+ * n outside 1 .. 2048 or a null operand. */
+mdsip_status mdsip_gemv_pair_df_next(mdsip_ctx *ctx, int64_t m, int64_t n, const double *A, int64_t lda,
+                                     const double *x, const double *v, const double *cpre,
+                                     const double *winv, double *Ax, double *ATv, double *ATw);
+
 /* Bunch-Kaufman LDL^T (Section 2.3) of the symmetric N x N matrix whose lower
  * triangle is in S (column-major, leading dimension ld).  S is overwritten
  * (used as work space).  Outputs (device):

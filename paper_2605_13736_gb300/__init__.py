@@ -125,6 +125,9 @@ _SIGS = {
                                        C.c_void_p, C.c_double, C.c_void_p, C.c_int64, C.c_int]),
     "mdsip_gemv_pair_df": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int64,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mdsip_gemv_pair_df_next": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int64,
+                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p]),
     "mdsip_ldlt_factor": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_double,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p]),
@@ -410,6 +413,11 @@ def mdsip_syrk_scaled_tc(ctx, m, n, A, lda, w, beta, Cmat, ldc, precision):
 
 def mdsip_gemv_pair_df(ctx, m, n, A, lda, x, v, Ax, ATv):
     _check(lib().mdsip_gemv_pair_df(ctx, m, n, _ptr(A), lda, _ptr(x), _ptr(v), _ptr(Ax), _ptr(ATv)), ctx)
+
+
+def mdsip_gemv_pair_df_next(ctx, m, n, A, lda, x, v, cpre, winv, Ax, ATv, ATw):
+    _check(lib().mdsip_gemv_pair_df_next(ctx, m, n, _ptr(A), lda, _ptr(x), _ptr(v), _ptr(cpre), _ptr(winv),
+                                         _ptr(Ax), _ptr(ATv), _ptr(ATw)), ctx)
 
 
 def mdsip_ldlt_factor(ctx, N, S, ld, zero_tol, L, Dd, Doff, perm, kind, inertia):

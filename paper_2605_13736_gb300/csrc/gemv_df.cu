@@ -54,6 +54,11 @@ __global__ void k_split_matrix(const double *__restrict__ A, int64_t m, int64_t 
     }
 }
 
+__global__ void k_round_vector(const double *__restrict__ v, int64_t n, float *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)v[i];
+}
+
 __global__ void k_split_vector(const double *__restrict__ v, int64_t n, float2 *__restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double a = v[i];
@@ -173,7 +178,11 @@ __global__ void __launch_bounds__(NT) k_gemv_t_df(const float *__restrict__ Ahi,
 // needs the warps for its dependent chains); the per-thread row sums of a
 // batch are reduced over the block as double-float pairs (warp shuffles,
 // then one slot per warp).  Waits are bounded: on expiry the kernel sets
-// *err and stops.
+// *err and stops.  The fused form (kFuse, one slice) also takes the first
+// half of the refinement's next approximate solve: each finished row sum
+// gives v_i (BothNext), and A_hi^T v accumulates in FP32 one batch behind,
+// from the previous batch's A_hi chunk kept in registers (its stage is
+// already being refilled), so the batch keeps its single barrier.
 constexpr int kBothThreads = 512;
 constexpr int kBothCols = 4 * kBothThreads;   // columns per slice
 constexpr int kBR = 4;                        // rows per stage
@@ -198,21 +207,34 @@ __device__ __forceinline__ void df_acc2(float2 ah, float2 al, float2 xh, float2 
     s = t;
     c = __fadd2_rn(c, __fadd2_rn(e, sm));
 }
+// Operands of the fused form, which also takes the first half of the next
+// approximate solve: from the row sum (A x)_i = s + c (double-float) it forms
+// v_i = fl32(bt_i wf_i), bt_i = (cw_i.x + cw_i.y) - (s + c) in double-float
+// (cw = cpre split into FP32 halves, wf = fl32(winv)), and accumulates
+// A_hi^T v in FP32 into vpart (one row of n per block).  One slice only
+// (n <= kBothCols): v_i needs the whole row.
+struct BothNext {
+    const float2 *cw;
+    const float *wf;
+    double *vpart;
+};
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      tc::smem_u32(dst)),
                  "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(tc::smem_u32(bar))
                  : "memory");
 }
+template <bool kFuse>
 __global__ void __launch_bounds__(kBothThreads, 1)
     k_gemv_both_df(const float *__restrict__ Ahi, const float *__restrict__ Alo, int64_t m, int64_t n, int64_t lda,
                    const float2 *__restrict__ xs, const float2 *__restrict__ ys, double *__restrict__ out,
-                   double *__restrict__ partial, int *err) {
+                   double *__restrict__ partial, int *err, BothNext nx) {
     extern __shared__ __align__(128) unsigned char bsm[];
     float *ring = reinterpret_cast<float *>(bsm);   // [kBS][kBR][2][kBothCols]
     uint64_t *full = reinterpret_cast<uint64_t *>(bsm + (size_t)kBS * kBR * 2 * kBothCols * sizeof(float));
     constexpr int kW = kBothThreads / 32;
     __shared__ float2 red[2][kBR][kW];   // [batch parity][row][warp]
+    __shared__ float4 s_v[2];            // fused form: v of the batch's kBR rows, [batch parity]
     __shared__ int s_stop;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t rows_per = (m + gridDim.x - 1) / gridDim.x;
@@ -223,6 +245,7 @@ __global__ void __launch_bounds__(kBothThreads, 1)
         for (int st = 0; st < kBS; ++st) tc::mbar_init(&full[st], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_stop = 0;
+        s_v[0] = s_v[1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     __syncthreads();
     int gb = 0;   // batches issued/consumed over all slices (stage and phase)
@@ -268,15 +291,35 @@ __global__ void __launch_bounds__(kBothThreads, 1)
             cs[q] = cc[q] = CS[q] = CC[q] = 0.0f;
             cacc[q] = 0.0;
         }
+        // fused form: A_hi^T v in FP32, v known one batch late (after the
+        // batch's row sums), so each batch's A_hi chunk is kept for one batch
+        // (a chunk array only ever holds A_hi values or zero: a row past the
+        // block's end keeps a stale chunk, which meets v = 0)
+        float2 cv01 = make_float2(0.0f, 0.0f), cv23 = make_float2(0.0f, 0.0f);
+        float4 ahA[kBR], ahB[kBR];   // fused form: A_hi chunks of alternate batches
+#pragma unroll
+        for (int rr = 0; rr < kBR; ++rr) ahA[rr] = ahB[rr] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         int cnt = 0, cnt2 = 0;
-        for (int b = 0; b < nbat; ++b) {
+        // one batch: its chunk into cur, the previous batch's chunk in prev;
+        // true when a bounded wait expired (every thread then stops)
+        auto batch = [&](int b, float4(&cur)[kBR], float4(&prev)[kBR]) -> bool {
             const int st = (gb + b) % kBS;
             const uint32_t ph = (uint32_t)(((gb + b) / kBS) & 1);
+            const int64_t i0 = r0 + (int64_t)b * kBR;
+            // fused form: the row's cpre and winv, loaded now so that their
+            // latency passes under the batch's products
+            [[maybe_unused]] float2 cw_i = make_float2(0.0f, 0.0f);
+            [[maybe_unused]] float wf_i = 0.0f;
+            if constexpr (kFuse) {
+                if (tid < kBR && i0 + tid < r1) {
+                    cw_i = nx.cw[i0 + tid];
+                    wf_i = nx.wf[i0 + tid];
+                }
+            }
             if (!tc::mbar_wait(&full[st], ph)) {   // bounded; every thread stops at the barrier below
                 atomicExch(err, 1);
                 s_stop = 1;
             }
-            const int64_t i0 = r0 + (int64_t)b * kBR;
             float rs[kBR], rc[kBR];
 #pragma unroll
             for (int rr = 0; rr < kBR; ++rr) {
@@ -287,6 +330,7 @@ __global__ void __launch_bounds__(kBothThreads, 1)
                 const float *row = ring + ((size_t)st * kBR + rr) * 2 * kBothCols;
                 const float4 ah = *reinterpret_cast<const float4 *>(row + 4 * tid);
                 const float4 al = *reinterpret_cast<const float4 *>(row + kBothCols + 4 * tid);
+                if constexpr (kFuse) cur[rr] = ah;
                 // columns (0, 1) and (2, 3) as lane pairs: the row sum in two
                 // partial pairs, the column sums in their own pairs
                 float2 rsp = make_float2(0.0f, 0.0f), rcp = make_float2(0.0f, 0.0f);
@@ -357,25 +401,73 @@ __global__ void __launch_bounds__(kBothThreads, 1)
                 if ((lane & 7) == 0) red[parity][2 * (lane >> 4) + ((lane >> 3) & 1)][wid] = make_float2(vs, vc);
             }
             __syncthreads();   // the stage is consumed, the batch's row sums are in red
-            if (s_stop) break;
+            if (s_stop) return true;
             if (tid == 0 && b + kBS < nbat) issue(b + kBS);
-            if (tid < kBR && i0 + tid < r1) {
-                float s = 0.0f, c = 0.0f;
+            if constexpr (kFuse) {   // the previous batch's v is in s_v[parity ^ 1]
+                const float4 v4 = s_v[parity ^ 1];
+                const float vr[kBR] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
-                for (int w = 0; w < kW; ++w) df_add(s, c, red[parity][tid][w].x, red[parity][tid][w].y);
-                const double v = (double)s + (double)c;
-                out[i0 + tid] = cp == 0 ? v : out[i0 + tid] + v;
+                for (int rr = 0; rr < kBR; ++rr) {
+                    const float2 v2 = make_float2(vr[rr], vr[rr]);
+                    cv01 = __ffma2_rn(make_float2(prev[rr].x, prev[rr].y), v2, cv01);
+                    cv23 = __ffma2_rn(make_float2(prev[rr].z, prev[rr].w), v2, cv23);
+                }
+            }
+            if (tid < kBR) {
+                [[maybe_unused]] float vf = 0.0f;
+                if (i0 + tid < r1) {
+                    float s = 0.0f, c = 0.0f;
+#pragma unroll
+                    for (int w = 0; w < kW; ++w) df_add(s, c, red[parity][tid][w].x, red[parity][tid][w].y);
+                    const double v = (double)s + (double)c;
+                    out[i0 + tid] = cp == 0 ? v : out[i0 + tid] + v;
+                    if constexpr (kFuse) {   // one slice: (s, c) is the whole row sum
+                        float bs = cw_i.x, bc = cw_i.y;
+                        df_add(bs, bc, -s, -c);
+                        vf = (bs + bc) * wf_i;
+                    }
+                }
+                if constexpr (kFuse) reinterpret_cast<float *>(&s_v[parity])[tid] = vf;
             }
             parity ^= 1;   // the other slot set next batch: one barrier per batch
+            return false;
+        };
+        bool stopped = false;
+        if constexpr (kFuse) {   // two batches per trip: the chunk arrays swap roles without copies
+            int b = 0;
+            for (; b + 1 < nbat && !stopped; b += 2) stopped = batch(b, ahA, ahB) || batch(b + 1, ahB, ahA);
+            if (!stopped && b < nbat) stopped = batch(b, ahA, ahB);
+        } else {
+            for (int b = 0; b < nbat && !stopped; ++b) stopped = batch(b, ahA, ahB);
+        }
+        if constexpr (kFuse) {   // the last batch's v
+            __syncthreads();
+            if (!s_stop && nbat > 0) {   // the last batch's chunk: ahA for an even index, ahB for odd
+                const bool odd = ((nbat - 1) & 1) != 0;
+                const float4 v4 = s_v[parity ^ 1];
+                const float vr[kBR] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+                for (int rr = 0; rr < kBR; ++rr) {
+                    const float4 a = odd ? ahB[rr] : ahA[rr];
+                    const float2 v2 = make_float2(vr[rr], vr[rr]);
+                    cv01 = __ffma2_rn(make_float2(a.x, a.y), v2, cv01);
+                    cv23 = __ffma2_rn(make_float2(a.z, a.w), v2, cv23);
+                }
+            }
         }
         if (s_stop) return;
         gb += nbat;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int64_t c = p0 + q;
-            if (c < n)
+            if (c < n) {
                 partial[(size_t)blockIdx.x * n + c] =
                     cacc[q] + (double)CS[q] + (double)CC[q] + (double)cs[q] + (double)cc[q];
+                if constexpr (kFuse) {
+                    const float cvq = q == 0 ? cv01.x : q == 1 ? cv01.y : q == 2 ? cv23.x : cv23.y;
+                    nx.vpart[(size_t)blockIdx.x * n + c] = (double)cvq;
+                }
+            }
         }
     }
 }
@@ -413,18 +505,26 @@ __global__ void __launch_bounds__(NT) k_gemv_rows_f32(const float *__restrict__ 
 
 }  // namespace
 
+bool gemv_both_fusable(int64_t n) { return n > 0 && n <= kBothCols; }
+
 // out_rows = A x, out_cols = A^T y in one pass (double-float); xs: n float2,
-// ys: m float2 of scratch; partial: kRedBlocks x n doubles (at most one row
-// per SM is used); err: device int set to 1 when a bounded wait expires
+// ys: m float2 of scratch; partial: kRedBlocks x n doubles (at most two rows
+// per SM are used); err: device int set to 1 when a bounded wait expires.
+// With nx (cw non-null; gemv_both_fusable(n)) the same pass also writes
+// out_v = A_hi^T v (FP32 products and block sums, see BothNext).
 void launch_gemv_both_df(cudaStream_t s, const float *Ahi, const float *Alo, int64_t m, int64_t n, int64_t lda,
                          const double *x, const double *y, float2 *xs, float2 *ys, double *partial,
-                         double *out_rows, double *out_cols, int *err) {
+                         double *out_rows, double *out_cols, int *err, const BothNextArgs *nx) {
+    const bool fuse = nx != nullptr && nx->cw != nullptr;
+    MDSIP_REQUIRE(!fuse || gemv_both_fusable(n), MDSIP_ERR_INVALID_ARG,
+                  "gemv (double-float, fused): n must be in 1 .. 2048");
     if (n <= 0) {
         if (m > 0) MDSIP_CUDA(cudaMemsetAsync(out_rows, 0, m * sizeof(double), s));
         return;
     }
     if (m <= 0) {
         MDSIP_CUDA(cudaMemsetAsync(out_cols, 0, n * sizeof(double), s));
+        if (fuse) MDSIP_CUDA(cudaMemsetAsync(nx->out_v, 0, n * sizeof(double), s));
         return;
     }
     MDSIP_REQUIRE((lda & 3) == 0 && ((reinterpret_cast<uintptr_t>(Ahi) | reinterpret_cast<uintptr_t>(Alo)) & 15) == 0,
@@ -437,13 +537,26 @@ void launch_gemv_both_df(cudaStream_t s, const float *Ahi, const float *Alo, int
     int dev = 0, sms = 0;
     MDSIP_CUDA(cudaGetDevice(&dev));
     MDSIP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int grid = std::max(1, std::min(sms, kRedBlocks));
+    const int grid = std::max(1, std::min(sms, kRedBlocks / 2));   // rows grid .. 2 grid - 1: A_hi^T v
     static PerDeviceOnce once;
     MDSIP_CUDA(once.run([] {
-        return cudaFuncSetAttribute(k_gemv_both_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBothSmem);
+        cudaError_t e = cudaFuncSetAttribute(k_gemv_both_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kBothSmem);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(k_gemv_both_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kBothSmem);
     }));
-    k_gemv_both_df<<<grid, kBothThreads, kBothSmem, s>>>(Ahi, Alo, m, n, lda, xs, ys, out_rows, partial, err);
-    MDSIP_LAUNCHED();
+    if (fuse) {
+        double *vpart = partial + (size_t)grid * n;
+        k_gemv_both_df<true><<<grid, kBothThreads, kBothSmem, s>>>(Ahi, Alo, m, n, lda, xs, ys, out_rows, partial,
+                                                                   err, BothNext{nx->cw, nx->wf, vpart});
+        MDSIP_LAUNCHED();
+        launch_colsum(s, vpart, grid, n, nx->out_v);
+    } else {
+        k_gemv_both_df<false><<<grid, kBothThreads, kBothSmem, s>>>(Ahi, Alo, m, n, lda, xs, ys, out_rows, partial,
+                                                                    err, BothNext{});
+        MDSIP_LAUNCHED();
+    }
     launch_colsum(s, partial, grid, n, out_cols);
 }
 
@@ -462,6 +575,18 @@ void launch_gemv_rows_f32(cudaStream_t s, const float *Ahi, int64_t m, int64_t n
     const int64_t grid = (2 * m + NT - 1) / NT;
     MDSIP_REQUIRE(grid <= 0x7fffffff, MDSIP_ERR_INVALID_ARG, "gemv (FP32): m too large");
     k_gemv_rows_f32<<<(unsigned)grid, NT, smem, s>>>(Ahi, m, n, lda, x, out);
+    MDSIP_LAUNCHED();
+}
+
+void launch_split_vector(cudaStream_t s, const double *v, int64_t n, float2 *out) {
+    if (n <= 0) return;
+    k_split_vector<<<(unsigned)std::min<int64_t>(4096, (n + NT - 1) / NT), NT, 0, s>>>(v, n, out);
+    MDSIP_LAUNCHED();
+}
+
+void launch_round_vector(cudaStream_t s, const double *v, int64_t n, float *out) {
+    if (n <= 0) return;
+    k_round_vector<<<(unsigned)std::min<int64_t>(4096, (n + NT - 1) / NT), NT, 0, s>>>(v, n, out);
     MDSIP_LAUNCHED();
 }
 

@@ -324,10 +324,23 @@ void launch_gemv_rows_df(cudaStream_t s, const float *Ahi, const float *Alo, int
                          const double *x, float2 *xs, double *out);
 void launch_gemv_t_df(cudaStream_t s, const float *Ahi, const float *Alo, int64_t m, int64_t n, int64_t lda,
                       const double *y, float2 *ys, double *partial, double *out);
-// out_rows = A x and out_cols = A^T y from one read of A
+// out_rows = A x and out_cols = A^T y from one read of A.  With nx, the same
+// read also gives out_v = A_hi^T v, v_i = fl32((cpre_i - (A x)_i) wf_i) with
+// the difference in double-float (FP32 products and sums): the first half of
+// the refinement's next approximate solve.  cw = cpre as FP32 halves
+// (launch_split_vector), wf = fl32(1 / w) (launch_round_vector).  The fused
+// form needs the whole row in one slice: gemv_both_fusable(n).
+struct BothNextArgs {
+    const float2 *cw;   // m
+    const float *wf;    // m
+    double *out_v;      // n
+};
+void launch_split_vector(cudaStream_t s, const double *v, int64_t n, float2 *out);   // out = (fl32(v), fl32(v - hi))
+void launch_round_vector(cudaStream_t s, const double *v, int64_t n, float *out);    // out = fl32(v)
+bool gemv_both_fusable(int64_t n);
 void launch_gemv_both_df(cudaStream_t s, const float *Ahi, const float *Alo, int64_t m, int64_t n, int64_t lda,
                          const double *x, const double *y, float2 *xs, float2 *ys, double *partial,
-                         double *out_rows, double *out_cols, int *err);
+                         double *out_rows, double *out_cols, int *err, const BothNextArgs *nx = nullptr);
 // out = A_hi x with FP32 products and sums
 void launch_gemv_rows_f32(cudaStream_t s, const float *Ahi, int64_t m, int64_t n, int64_t lda, const double *x,
                           double *out);

@@ -7,6 +7,9 @@
 // (diagonal Q_s, dense Q_d, sparse J_sg, dense A and J_dh) and the
 // approximate solve S~^-1 is the same two-stage elimination used for the
 // direction itself.  Vectors are packed as [u_s (n_s) | u_d (n_d) | u_g (m_E) | u_h (m_I)].
+// With a tensor-core factor and n_d <= 2048 the residual's double-float pass
+// over A also forms the FP32 A^T (bt_g / w) of the approximate solve that
+// follows it, so that solve reads A once (for A sol_d) instead of twice.
 #include "refine.cuh"
 
 namespace mdsip {
@@ -59,6 +62,31 @@ __global__ void k_prep_g(Dims D, ModelView M, const double *__restrict__ b, cons
     }
 }
 
+// The part of bt_g that does not involve A, for the residual r = b - K u that
+// the next pass forms: with r_s = b_s - Q_s u_s - J_sg^T u_g,
+// bt_g = r_g - J_sg (r_s / q) = cpre - A u_d, where
+// cpre = b_g + dc u_g - J_sg u_s - J_sg (r_s / q); also cpre as FP32 halves
+// (cw) and wf = fl32(1 / w) for the pass
+__global__ void k_pre_bt(Dims D, ModelView M, const double *__restrict__ b, const double *__restrict__ u,
+                         const double *__restrict__ q, const double *__restrict__ w, double dc,
+                         double *__restrict__ cpre, float2 *__restrict__ cw, float *__restrict__ wf) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < D.m_E; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = b[D.n + i] + dc * u[D.n + i];
+        for (int e = M.csr_ptr[i]; e < M.csr_ptr[i + 1]; ++e) {
+            const int c = M.csr_col[e];
+            double Ku = q[c] * u[c];
+            for (int f = M.csc_ptr[c]; f < M.csc_ptr[c + 1]; ++f) Ku += M.csc_val[f] * u[D.n + M.csc_row[f]];
+            const double rs = b[c] - Ku;
+            s -= M.csr_val[e] * u[c];
+            s -= M.csr_val[e] * rs / q[c];
+        }
+        cpre[i] = s;
+        const float h = (float)s;
+        cw[i] = make_float2(h, (float)(s - (double)h));
+        wf[i] = (float)(1.0 / w[i]);
+    }
+}
+
 // rhs_S = [b_d + A^T u; b_h]
 __global__ void k_rhs_S(Dims D, const double *__restrict__ b, const double *__restrict__ ATu,
                         double *__restrict__ rhsS) {
@@ -72,6 +100,16 @@ __global__ void k_sol_gdh(Dims D, const double *__restrict__ Adx, const double *
                           const double *__restrict__ w, const double *__restrict__ rhsS, double *__restrict__ sol) {
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gsz = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = gtid; i < D.m_E; i += gsz) sol[D.n + i] = (Adx[i] - bt_g[i]) / w[i];
+    for (int64_t k = gtid; k < D.n_d; k += gsz) sol[D.n_s + k] = rhsS[k];
+    for (int64_t j = gtid; j < D.m_I; j += gsz) sol[D.n + D.m_E + j] = rhsS[D.n_d + j];
+}
+
+// k_sol_gdh after the fused residual pass, with bt_g = cpre - A u_d formed here
+__global__ void k_sol_gdh_pre(Dims D, const double *__restrict__ Adx, const double *__restrict__ cpre,
+                              const double *__restrict__ Au, const double *__restrict__ w,
+                              const double *__restrict__ rhsS, double *__restrict__ sol) {
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gsz = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = gtid; i < D.m_E; i += gsz) sol[D.n + i] = (Adx[i] - (cpre[i] - Au[i])) / w[i];
     for (int64_t k = gtid; k < D.n_d; k += gsz) sol[D.n_s + k] = rhsS[k];
     for (int64_t j = gtid; j < D.m_I; j += gsz) sol[D.n + D.m_E + j] = rhsS[D.n_d + j];
 }
@@ -215,19 +253,33 @@ void Refiner::rhs(const IterView &I, const double *gl, const double *cg, const d
     MDSIP_LAUNCHED();
 }
 
+bool Refiner::fuse_pass() const { return cpre && Ahi && solve_fp32 && AfT && gemv_both_fusable(D.n_d); }
+
 void Refiner::approx_solve(const double *b, double *sol) {
-    k_prep_g<<<grid_for(D.m_E), 256, 0, st>>>(D, M, b, q, w, bt_g, tmp_m);
-    MDSIP_LAUNCHED();
-    if (solve_fp32 && AfT)   // approximate solve of a low-precision factor: FP32 A^T product
-        launch_aft_dot(st, num_sms, AfT, ldt, D.m_E, D.n_d, tmp_m, vf, tmp_nd);
-    else
-        launch_gemv_t(st, M.A, D.m_E, D.n_d, D.lda, tmp_m, colpart, tmp_nd);
-    k_rhs_S<<<grid_for(std::max(D.n_d, D.m_I)), 256, 0, st>>>(D, b, tmp_nd, rhsS);
+    const double *ATu = tmp_nd;
+    const bool pre = pre_for != nullptr && pre_for == b;
+    if (pre) {   // A_hi^T (bt_g / w) came with the residual b; bt_g = cpre - A u_d (tmp_m)
+        ATu = ATv;
+    } else {
+        k_prep_g<<<grid_for(D.m_E), 256, 0, st>>>(D, M, b, q, w, bt_g, tmp_m);
+        MDSIP_LAUNCHED();
+        if (solve_fp32 && AfT)   // approximate solve of a low-precision factor: FP32 A^T product
+            launch_aft_dot(st, num_sms, AfT, ldt, D.m_E, D.n_d, tmp_m, vf, tmp_nd);
+        else
+            launch_gemv_t(st, M.A, D.m_E, D.n_d, D.lda, tmp_m, colpart, tmp_nd);
+    }
+    pre_for = nullptr;
+    k_rhs_S<<<grid_for(std::max(D.n_d, D.m_I)), 256, 0, st>>>(D, b, ATu, rhsS);
     MDSIP_LAUNCHED();
     launch_ldlt_solve_coop(st, num_sms, N, Dd, Doff, perm, 1, rhsS, N, solve_ws, solve_err, solve_fp32);
-    if (Ahi) launch_gemv_rows_f32(st, Ahi, D.m_E, D.n_d, D.lda, rhsS, tmp_m);
-    else launch_gemv_rows(st, M.A, D.m_E, D.n_d, D.lda, rhsS, tmp_m);
-    k_sol_gdh<<<grid_for(std::max(D.m_E, D.n_d)), 256, 0, st>>>(D, tmp_m, bt_g, w, rhsS, sol);
+    if (pre) {
+        launch_gemv_rows_f32(st, Ahi, D.m_E, D.n_d, D.lda, rhsS, Asd);
+        k_sol_gdh_pre<<<grid_for(std::max(D.m_E, D.n_d)), 256, 0, st>>>(D, Asd, cpre, tmp_m, w, rhsS, sol);
+    } else {
+        if (Ahi) launch_gemv_rows_f32(st, Ahi, D.m_E, D.n_d, D.lda, rhsS, tmp_m);
+        else launch_gemv_rows(st, M.A, D.m_E, D.n_d, D.lda, rhsS, tmp_m);
+        k_sol_gdh<<<grid_for(std::max(D.m_E, D.n_d)), 256, 0, st>>>(D, tmp_m, bt_g, w, rhsS, sol);
+    }
     MDSIP_LAUNCHED();
     k_sol_s<<<grid_for(D.n_s), 256, 0, st>>>(D, M, b, q, sol);
     MDSIP_LAUNCHED();
@@ -244,10 +296,18 @@ void Refiner::track_Au(bool init) {
 
 void Refiner::residual(const double *b, const double *u, double dw, double dc, double *r, double *out4) {
     const double *Au = Au_run;
+    pre_for = nullptr;
     if (Ahi) {   // A u_d and A^T u_g from one double-float pass
+        const bool fuse = fuse_pass();
+        BothNextArgs nx{cw, wf, ATv};
+        if (fuse) {
+            k_pre_bt<<<grid_for(D.m_E), 256, 0, st>>>(D, M, b, u, q, w, dc, cpre, cw, wf);
+            MDSIP_LAUNCHED();
+        }
         launch_gemv_both_df(st, Ahi, Alo, D.m_E, D.n_d, D.lda, u + D.n_s, u + D.n, split, split + D.n_d, colpart,
-                            tmp_m, tmp_nd, solve_err);
+                            tmp_m, tmp_nd, solve_err, fuse ? &nx : nullptr);
         Au = tmp_m;
+        if (fuse) pre_for = r;
     } else {
         launch_gemv_t(st, M.A, D.m_E, D.n_d, D.lda, u + D.n, colpart, tmp_nd);   // A^T u_g
     }

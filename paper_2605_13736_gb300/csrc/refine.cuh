@@ -31,16 +31,28 @@ struct Refiner {
     // from one double-float pass over (A_hi, A_lo)
     const float *Ahi, *Alo;
     float2 *split;    // m_E + n_d float2
+    // With a tensor-core factor and n_d <= 2048 (one slice of the pass), the
+    // residual's pass over A also forms A_hi^T (bt_g / w) for the approximate
+    // solve of that residual, bt_g = cpre - A u_d: cpre (m_E), its FP32 halves
+    // cw (m_E), wf = fl32(1 / w) (m_E), the product ATv (n_d) and that solve's
+    // A sol_d in Asd (m_E); null cpre: separate passes
+    double *cpre, *ATv, *Asd;
+    float2 *cw;
+    float *wf;
+    const double *pre_for;   // the residual whose first solve half is ready (else null)
 
     // b = right-hand side of Eq. (linsys4x4), packed [s | d | g | h]
     void rhs(const IterView &I, const double *gl, const double *cg, const double *ch, const double *sig_d,
              double mu, double dw, double *b);
-    // sol = S~^-1-based solve of K sol = b (two-stage elimination with the factor)
+    // sol = S~^-1-based solve of K sol = b (two-stage elimination with the factor);
+    // b the last residual: its first half came with that residual's pass (fuse_pass)
     void approx_solve(const double *b, double *sol);
+    bool fuse_pass() const;
     // after approx_solve: Au_run = A sol_d (init) or Au_run += A sol_d (FP64 passes only)
     void track_Au(bool init);
     // r = b - K u in FP64 (A u_d from Au_run, or from the double-float pass);
-    // out4 = (||r||inf, ||b||inf, ||K u||inf, ||u||inf)
+    // out4 = (||r||inf, ||b||inf, ||K u||inf, ||u||inf).  The approximate solve
+    // of r that may follow has to come next (its first half is in bt_g / ATv)
     void residual(const double *b, const double *u, double dw, double dc, double *r, double *out4);
     void axpy(int64_t n, const double *x, double *y);
     // full direction (incl. dd and the bound-multiplier steps) from the packed solution

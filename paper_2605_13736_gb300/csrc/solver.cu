@@ -113,6 +113,7 @@ struct Problem {
     DBuf bS, bL, bDd, bDoff, bperm, bkind, binertia, bldlt_ws, berr, bsyrk_ws, btune;
     // tensor-core condensation and refinement
     DBuf bAfT, bvf, btc_ws, btc_err, bref_b, bref_u, bref_r, bref_d, btmp_nd2, bsolve_ws, bsolve_err, bAu_run;
+    DBuf bcpre, bcw, bwf, bATv, bAsd;   // the refinement's fused residual pass
     bool aft_ready = false;
     DBuf bAhi, bAlo, bsplit;   // A as an FP32 pair (mixed path's double-float passes) and vector scratch
     // Products with A carried from step to step on the mixed path of a data-given
@@ -598,6 +599,11 @@ static void prepare_path(Problem *P) {
         dvec(ctx, P->bref_d, nm);
         dvec(ctx, P->btmp_nd2, D.n_d + D.m_I);
         dvec(ctx, P->bAu_run, D.m_E);
+        dvec(ctx, P->bcpre, D.m_E);
+        dvec(ctx, P->bcw, D.m_E);    // m_E float2
+        dvec(ctx, P->bwf, D.m_E);    // m_E floats (room for m_E doubles)
+        dvec(ctx, P->bATv, D.n_d);
+        dvec(ctx, P->bAsd, D.m_E);
     }
 }
 
@@ -960,6 +966,11 @@ static RefineResult solve_direction_refined(Problem *P, double mu, double dw, do
     R.Ahi = P->V.Ahi;
     R.Alo = P->V.Alo;
     R.split = P->V.split;
+    R.cpre = P->bcpre.as<double>();
+    R.cw = P->bcw.as<float2>();
+    R.wf = P->bwf.as<float>();
+    R.ATv = P->bATv.as<double>();
+    R.Asd = P->bAsd.as<double>();
     double *b = P->bref_b.as<double>(), *u = P->bref_u.as<double>(), *r = P->bref_r.as<double>(),
            *d = P->bref_d.as<double>();
     const double *h = P->hscal;
@@ -1869,14 +1880,19 @@ mdsip_status mdsip_syrk_scaled_tc(mdsip_ctx *hctx, int64_t m, int64_t n, const d
     });
 }
 
-mdsip_status mdsip_gemv_pair_df(mdsip_ctx *hctx, int64_t m, int64_t n, const double *A, int64_t lda,
-                                const double *x, const double *v, double *Ax, double *ATv) {
+// fused: cpre, winv (m) and ATw (n) given (mdsip_gemv_pair_df_next)
+static mdsip_status gemv_pair_df_impl(mdsip_ctx *hctx, int64_t m, int64_t n, const double *A, int64_t lda,
+                                      const double *x, const double *v, double *Ax, double *ATv, bool fused,
+                                      const double *cpre, const double *winv, double *ATw) {
     if (!hctx) return MDSIP_ERR_INVALID_ARG;
     Ctx *ctx = C_(hctx);
     return guarded(ctx, [&] {
         DeviceGuard g(ctx->device);
         MDSIP_REQUIRE(m >= 0 && n >= 0 && lda >= n && lda % 4 == 0 && m <= (1 << 20) && n <= (1 << 20),
                       MDSIP_ERR_INVALID_ARG, "gemv_pair_df: bad sizes");
+        if (fused)
+            MDSIP_REQUIRE(gemv_both_fusable(n) && (m == 0 || (cpre && winv)) && ATw, MDSIP_ERR_INVALID_ARG,
+                          "gemv_pair_df_next: n must be in 1 .. 2048, null operand");
         if (m == 0 && n == 0) return;
         MDSIP_REQUIRE((m == 0 || Ax) && (n == 0 || ATv), MDSIP_ERR_INVALID_ARG, "gemv_pair_df: null output");
         if (m > 0 && n > 0)
@@ -1886,21 +1902,39 @@ mdsip_status mdsip_gemv_pair_df(mdsip_ctx *hctx, int64_t m, int64_t n, const dou
         const size_t nA = (size_t)m * (size_t)lda;
         const size_t o_lo = up(nA * sizeof(float)), o_xs = o_lo + up(nA * sizeof(float));
         const size_t o_ys = o_xs + up((size_t)n * sizeof(float2)), o_part = o_ys + up((size_t)m * sizeof(float2));
-        const size_t o_err = o_part + up((size_t)kRedBlocks * (size_t)n * sizeof(double));
+        const size_t o_cw = o_part + up((size_t)kRedBlocks * (size_t)n * sizeof(double));
+        const size_t o_wf = o_cw + up((size_t)m * sizeof(float2));
+        const size_t o_err = o_wf + up((size_t)m * sizeof(float));
         const size_t total = o_err + 256;
         char *base = static_cast<char *>(ctx->scratch_at_least(total));
         float *hi = reinterpret_cast<float *>(base), *lo = reinterpret_cast<float *>(base + o_lo);
         int *err = reinterpret_cast<int *>(base + o_err);
         MDSIP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
         if (m > 0 && n > 0) launch_split_matrix(ctx->stream, A, m, n, lda, hi, lo);
+        BothNextArgs nx{reinterpret_cast<float2 *>(base + o_cw), reinterpret_cast<float *>(base + o_wf), ATw};
+        if (fused) {
+            launch_split_vector(ctx->stream, cpre, m, reinterpret_cast<float2 *>(base + o_cw));
+            launch_round_vector(ctx->stream, winv, m, reinterpret_cast<float *>(base + o_wf));
+        }
         launch_gemv_both_df(ctx->stream, hi, lo, m, n, lda, x, v, reinterpret_cast<float2 *>(base + o_xs),
                             reinterpret_cast<float2 *>(base + o_ys), reinterpret_cast<double *>(base + o_part), Ax,
-                            ATv, err);
+                            ATv, err, fused ? &nx : nullptr);
         int herr = 0;
         MDSIP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
         MDSIP_CUDA(cudaStreamSynchronize(ctx->stream));
         MDSIP_REQUIRE(herr == 0, MDSIP_ERR_DEVICE, "gemv_pair_df: a bounded device wait expired");
     });
+}
+
+mdsip_status mdsip_gemv_pair_df(mdsip_ctx *hctx, int64_t m, int64_t n, const double *A, int64_t lda,
+                                const double *x, const double *v, double *Ax, double *ATv) {
+    return gemv_pair_df_impl(hctx, m, n, A, lda, x, v, Ax, ATv, false, nullptr, nullptr, nullptr);
+}
+
+mdsip_status mdsip_gemv_pair_df_next(mdsip_ctx *hctx, int64_t m, int64_t n, const double *A, int64_t lda,
+                                     const double *x, const double *v, const double *cpre, const double *winv,
+                                     double *Ax, double *ATv, double *ATw) {
+    return gemv_pair_df_impl(hctx, m, n, A, lda, x, v, Ax, ATv, true, cpre, winv, ATw);
 }
 
 static mdsip_status ldlt_factor_impl(mdsip_ctx *hctx, int64_t N, double *S, int64_t ld, double zero_tol,

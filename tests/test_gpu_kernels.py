@@ -315,6 +315,64 @@ def test_gemv_pair_df_within_bound(ctx, mrows, n):
     assert np.median(err_r) <= 2.0 ** -46 and np.median(err_c) <= 2.0 ** -46
 
 
+@pytest.mark.parametrize("mrows,n", [(1, 1), (5, 3), (150, 7), (1000, 2000), (3001, 2048), (20011, 64)])
+def test_gemv_pair_df_next_folds_the_solve_half(ctx, mrows, n):
+    """The fused form of the pass: A x and A^T v bit for bit as the plain pass,
+    and A_hi^T w, w_i = fl32(d_i fl32(winv_i)) with d_i the double-float
+    difference cpre_i - (A x)_i rounded to FP32, within its stated bound of
+    sum_i A_hi[i][p] (cpre_i - (A x)_i) winv_i: the FP32 block sums, the
+    roundings of d_i, winv_i and w_i (2^-22 of |w|), and 2^-46 |cpre_i| winv_i.
+    A_hi times a float64 is summed exactly by math.fsum.  cpre is A x plus a
+    small offset on half of the rows, so that the difference cancels; the
+    magnitudes are of order one, so that a row paired with another row's w
+    (the pass learns w one batch late) misses the bound by orders of
+    magnitude."""
+    import math
+    torch = torch_cuda()
+    rng = np.random.default_rng(mrows * 11 + n)
+    A = rng.standard_normal((mrows, n)) * np.exp2(rng.integers(-3, 4, (mrows, n)))
+    x, v = rng.standard_normal(n), rng.standard_normal(mrows)
+    winv = rng.uniform(0.5, 2.0, mrows)
+    lda = (n + 3) // 4 * 4
+    Ap = np.zeros((mrows, lda))
+    Ap[:, :n] = A
+    dA, dx, dv = dev(Ap), dev(x), dev(v)
+    Ax0, ATv0 = dev(np.full(mrows, np.nan)), dev(np.full(n, np.nan))
+    m.mdsip_gemv_pair_df(ctx, mrows, n, dA, lda, dx, dv, Ax0, ATv0)
+    torch.cuda.synchronize()
+    Ax0 = Ax0.cpu().numpy()
+    cpre = np.where(rng.random(mrows) < 0.5, Ax0 * (1.0 + 1e-6 * rng.standard_normal(mrows)),
+                    4.0 * rng.standard_normal(mrows))
+    Ax, ATv, ATw = dev(np.full(mrows, np.nan)), dev(np.full(n, np.nan)), dev(np.full(n, np.nan))
+    m.mdsip_gemv_pair_df_next(ctx, mrows, n, dA, lda, dx, dv, dev(cpre), dev(winv), Ax, ATv, ATw)
+    torch.cuda.synchronize()
+    Ax, ATv, ATw = (t.cpu().numpy() for t in (Ax, ATv, ATw))
+    np.testing.assert_array_equal(Ax, Ax0)
+    np.testing.assert_array_equal(ATv, ATv0.cpu().numpy())
+    Ah = np.abs(A.astype(np.float32).astype(np.float64))
+    w_ref = (cpre - Ax) * winv
+    Q = A.astype(np.float32).astype(np.float64) * w_ref[:, None]
+    ex = np.array([math.fsum(Q[:, p]) for p in range(n)])
+    S = Ah.T @ np.abs(w_ref)
+    S3 = Ah.T @ (np.abs(cpre) * winv)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    rows = -(-mrows // min(sms, 152))
+    err = np.abs(ATw - ex)
+    bound = (rows + 7) * 2.0 ** -24 * S + 2.0 ** -45 * S3
+    assert np.all(err <= bound), float((err / bound).max())
+
+
+def test_gemv_pair_df_next_rejects_a_row_wider_than_a_slice(ctx):
+    torch = torch_cuda()
+    A = dev(np.zeros((4, 2052)))
+    out = dev(np.zeros(2052))
+    with pytest.raises(m.MdsipError):   # n > 2048
+        m.mdsip_gemv_pair_df_next(ctx, 4, 2049, A, 2052, out, out, out, out, out, out, out)
+    with pytest.raises(m.MdsipError):   # n = 0
+        m.mdsip_gemv_pair_df_next(ctx, 4, 0, A, 4, out, out, out, out, out, out, out)
+    torch.cuda.synchronize()
+
+
 def test_gemv_pair_df_rejects_bad_arguments(ctx):
     torch = torch_cuda()
     A = dev(np.zeros((4, 8)))
