@@ -90,6 +90,40 @@ __global__ void __launch_bounds__(kThreads) k_solve_tiles(int N, const double *_
     }
     // diagonal block: inverse of the unit lower triangle, column c by forward substitution
     const int jb = I * kBS, bw = min(kBS, N - jb);
+    if constexpr (sizeof(T) == sizeof(float)) {
+        // FP32 tiles (the refined path's approximate solves): the inverse in FP32 arithmetic,
+        // four partial sums per entry.  On the FP64 pipe (1/64 of the FP32 rate) the 2016
+        // dependent products of a column made this launch take about 0.1 ms at N = 2050.
+        float(*sf)[kBS + 1] = reinterpret_cast<float(*)[kBS + 1]>(&s[0][0]);   // s's storage
+        for (int e = tid; e < kTile; e += kThreads) {
+            const int r = e & (kBS - 1), c = e >> 6;
+            sf[r][c] = (r < bw && c < bw) ? (float)L[(jb + r) + (int64_t)(jb + c) * N] : 0.0f;
+        }
+        __syncthreads();
+        float xf[kBS];
+        const int c = tid;
+        if (c < kBS) {
+#pragma unroll
+            for (int i = 0; i < kBS; ++i) {
+                float v[4] = {(i == c) ? 1.0f : 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int j = 0; j < i; ++j) v[j & 3] = fmaf(-sf[i][j], xf[j], v[j & 3]);
+                xf[i] = i < c ? 0.0f : (v[0] + v[1]) + (v[2] + v[3]);
+            }
+        }
+        __syncthreads();
+        if (c < kBS) {
+#pragma unroll
+            for (int i = 0; i < kBS; ++i) sf[i][c] = (i < bw && c < bw) ? xf[i] : 0.0f;
+        }
+        __syncthreads();
+        for (int e = tid; e < kTile; e += kThreads) {
+            const int r = e & (kBS - 1), cc = e >> 6;
+            f[cc * kBS + r] = (T)sf[r][cc];    // F(I, I)(r, c) = inv(L_II)[r][c]
+            bk[cc * kBS + r] = (T)sf[cc][r];   // B(I, I)(r, c) = inv(L_II)[c][r]
+        }
+        return;
+    }
     for (int e = tid; e < kTile; e += kThreads) {
         const int r = e & (kBS - 1), c = e >> 6;
         s[r][c] = (r < bw && c < bw) ? L[(jb + r) + (int64_t)(jb + c) * N] : 0.0;
