@@ -113,6 +113,8 @@ def parse():
                     help="--kernel ldlt --fp32-update: every panel pivots (no verified no-interchange panels)")
     ap.add_argument("--persistent", action="store_true",
                     help="--kernel ldlt: the persistent no-interchange kernel at any order")
+    ap.add_argument("--fused", action="store_true",
+                    help="--kernel gemv_pair_df: the fused form (mdsip_gemv_pair_df_next, n <= 2048)")
     ap.add_argument("--refine-study", action="store_true",
                     help="refinement convergence of the mixed-precision direction on --config (one JSON line)")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
@@ -1087,6 +1089,12 @@ def run_kernel(args):
             ATv = torch.empty(n, dtype=torch.float64, device="cuda")
             flops = 4.0 * mm * n
             call = lambda: m.mdsip_gemv_pair_df(ctx, mm, n, A, lda, x, v, Ax, ATv)
+            if args.fused:   # the form that also takes the next approximate solve's A^T product
+                cpre = torch.randn(mm, dtype=torch.float64, device="cuda")
+                winv = torch.rand(mm, dtype=torch.float64, device="cuda") + 0.5
+                ATw = torch.empty(n, dtype=torch.float64, device="cuda")
+                flops = 6.0 * mm * n
+                call = lambda: m.mdsip_gemv_pair_df_next(ctx, mm, n, A, lda, x, v, cpre, winv, Ax, ATv, ATw)
         elif args.kernel == "gemm_bf16":
             # the warm-start network's output layer: (batch m) x (outputs n) x (hidden k)
             M, N, K = args.m, args.n, args.k
