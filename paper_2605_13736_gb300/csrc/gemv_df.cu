@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(kBothThreads, 1)
             const int st = (gb + b) % kBS;
             const uint32_t ph = (uint32_t)(((gb + b) / kBS) & 1);
             const int64_t i0 = r0 + (int64_t)b * kBR;
-            // fused form: the row's cpre and winv, loaded now so that their
+            // fused form: the row's cw and wf, loaded now so that their
             // latency passes under the batch's products
             [[maybe_unused]] float2 cw_i = make_float2(0.0f, 0.0f);
             [[maybe_unused]] float wf_i = 0.0f;

@@ -52,7 +52,7 @@ struct Refiner {
     void track_Au(bool init);
     // r = b - K u in FP64 (A u_d from Au_run, or from the double-float pass);
     // out4 = (||r||inf, ||b||inf, ||K u||inf, ||u||inf).  The approximate solve
-    // of r that may follow has to come next (its first half is in bt_g / ATv)
+    // of r that may follow has to come next (its first half is in cpre / ATv)
     void residual(const double *b, const double *u, double dw, double dc, double *r, double *out4);
     void axpy(int64_t n, const double *x, double *y);
     // full direction (incl. dd and the bound-multiplier steps) from the packed solution
